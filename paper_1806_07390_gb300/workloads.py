@@ -1,0 +1,269 @@
+"""Seeded synthetic workloads for the multigroup M1 radiation-hydrodynamics stage update.
+
+This module only builds inputs: grid parameters and the primitive initial fields
+(rho, p, physical velocity, radiation temperature).  It holds none of the method's arithmetic;
+turning primitives into the conserved state (including the Planck group energies) is done by
+the CUDA library and, independently, by the CPU oracle.
+
+The five workloads follow the structure of the paper's radiation-hydrodynamics applications
+(Sec. 3.2, Sec. 4: 8-20 logarithmically spaced groups, power-law absorption opacities, 2-d
+spherical grids of a few hundred by ~128 zones).  The paper's own core-collapse progenitors,
+nuclear equations of state and neutrino opacity tables are not available, so these seeded
+fields stand in for them.
+
+Units are dimensionless: k_B = mu = 1, T = p / rho, photon energies in units of k T0 = 1,
+radiation constant a_R = 0.1, and the (reduced) speed of light c = 10 max(|v| + a_s) over the
+initial state (the paper's example choice c = 10 (v0 + a0), Sec. 9.5).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional, Tuple
+
+import numpy as np
+
+BC_CODES = {"outflow": 0, "periodic": 1, "reflect": 2, "axis": 3}
+GEOM_CODES = {"cart": 0, "sph": 1}
+MAP_CODES = {"id": 0, "exp": 1}
+
+
+@dataclasses.dataclass
+class Problem:
+    """Grid, physics and run parameters of one workload (shared by the library and the oracle)."""
+
+    name: str
+    dims: int
+    n: Tuple[int, int, int]
+    x_lo: Tuple[float, float, float]
+    x_hi: Tuple[float, float, float]
+    bc_lo: Tuple[str, str, str]
+    bc_hi: Tuple[str, str, str]
+    ngroups: int
+    gamma: float
+    kappa0: float
+    kap_rho_exp: float
+    kap_T_exp: float
+    kap_eps_exp: float
+    eps_min: float = 0.01
+    eps_max: float = 10.0
+    sigma0: float = 0.0
+    a_rad: float = 0.1
+    c_light: float = 0.0
+    geom: str = "cart"
+    map1: str = "id"
+    rad_recon_order: int = 1
+    couple: int = 1
+    newton_maxit: int = 50
+    bisect_maxit: int = 200
+    newton_rtol: float = 1e-13
+    rho_floor: float = 1e-12
+    p_floor: float = 1e-12
+    E_floor: float = 1e-31
+    cfl: float = 0.5
+    dt: float = 0.0
+    nsteps: int = 1
+    precision: str = "fp64"
+
+    @property
+    def ncell(self) -> int:
+        return int(np.prod(self.n[: self.dims]))
+
+    @property
+    def nvar(self) -> int:
+        return 2 + self.dims + self.ngroups * (1 + self.dims)
+
+    @property
+    def shape(self) -> Tuple[int, ...]:
+        """numpy shape of one cell field, slowest axis first (z, y, x)."""
+        return tuple(reversed(self.n[: self.dims]))
+
+    def state_size(self) -> int:
+        return self.ncell * self.nvar
+
+    def cell_centres(self, d: int) -> np.ndarray:
+        lo, hi, n = self.x_lo[d], self.x_hi[d], self.n[d]
+        return lo + (np.arange(n) + 0.5) * (hi - lo) / n
+
+    def cell_lower_faces(self, d: int) -> np.ndarray:
+        lo, hi, n = self.x_lo[d], self.x_hi[d], self.n[d]
+        return lo + np.arange(n) * (hi - lo) / n
+
+    def zone_groups(self) -> int:
+        return self.ncell * self.ngroups
+
+
+def _finish(pb: Problem, prim: np.ndarray) -> Tuple[Problem, np.ndarray]:
+    """Set c from the initial state (c = 10 max(|v| + a_s)) and dt from the light-crossing limit."""
+    D = pb.dims
+    rho, p = prim[0], prim[1]
+    vmag = np.sqrt(sum(prim[2 + q] ** 2 for q in range(D)))
+    a_s = np.sqrt(pb.gamma * p / rho)
+    if pb.c_light <= 0.0:
+        pb.c_light = float(10.0 * np.max(vmag + a_s))
+    pb.dt = float(pb.cfl / _max_inverse_crossing(pb, prim))
+    return pb, prim
+
+
+def _max_inverse_crossing(pb: Problem, prim: np.ndarray) -> float:
+    """max over cells of sum_d lambda_d / (h_d dx^d), lambda_d = max(|v_d| + a_s, c)."""
+    D = pb.dims
+    rho, p = prim[0], prim[1]
+    a_s = np.sqrt(pb.gamma * p / rho)
+    tot = np.zeros(pb.shape)
+    for d in range(D):
+        dx = (pb.x_hi[d] - pb.x_lo[d]) / pb.n[d]
+        lam = np.maximum(np.abs(prim[2 + d]).reshape(pb.shape) + a_s.reshape(pb.shape), pb.c_light)
+        if pb.geom == "sph":
+            xl = pb.cell_lower_faces(0)
+            r = np.exp(xl) if pb.map1 == "exp" else np.maximum(xl, 1e-300)
+            dr = np.exp(xl) if pb.map1 == "exp" else np.ones_like(xl)
+            h = dr if d == 0 else r  # h_1 = dr/dx1, h_2 = r (identity theta map)
+            hb = np.broadcast_to(h[np.newaxis, :], pb.shape) if D > 1 else h
+            tot = tot + lam / (hb * dx)
+        else:
+            tot = tot + lam / dx
+    return float(np.max(tot))
+
+
+def _flat(*fields: np.ndarray) -> np.ndarray:
+    return np.stack([np.ascontiguousarray(f, dtype=np.float64).reshape(-1) for f in fields])
+
+
+# ---------------------------------------------------------------------------------------------
+# The five workloads.  Each returns (Problem, prim) with prim of shape (3 + D, ncell):
+# rows rho, p, vhat_1..vhat_D, T_rad; cells in x-fastest order.
+# ---------------------------------------------------------------------------------------------
+def sod_1d(n: int = 512, ngroups: int = 12, nsteps: int = 200, gamma: float = 5.0 / 3.0,
+           precision: str = "fp64") -> Tuple[Problem, np.ndarray]:
+    """Sod-like 1-d shock tube with multigroup radiation in local equilibrium (Sec. 8.3 states)."""
+    pb = Problem(name=f"sod1d_{n}x{ngroups}g", dims=1, n=(n, 1, 1), x_lo=(0.0, 0.0, 0.0),
+                 x_hi=(1.0, 1.0, 1.0), bc_lo=("outflow",) * 3, bc_hi=("outflow",) * 3,
+                 ngroups=ngroups, gamma=gamma, kappa0=1.0, kap_rho_exp=1.0, kap_T_exp=-1.5,
+                 kap_eps_exp=-2.0, nsteps=nsteps, precision=precision)
+    x = pb.cell_centres(0)
+    left = x < 0.5
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    v = np.zeros(n)
+    return _finish(pb, _flat(rho, p, v, p / rho))
+
+
+def kh_2d(nx: int = 1024, ny: int = 1024, ngroups: int = 16, nsteps: int = 100, seed: int = 1,
+          precision: str = "fp64") -> Tuple[Problem, np.ndarray]:
+    """Periodic Kelvin-Helmholtz shear layer (a variant of Sec. 8.6) with equilibrium radiation."""
+    pb = Problem(name=f"kh2d_{nx}x{ny}x{ngroups}g", dims=2, n=(nx, ny, 1), x_lo=(0.0, 0.0, 0.0),
+                 x_hi=(1.0, 1.0, 1.0), bc_lo=("periodic",) * 3, bc_hi=("periodic",) * 3,
+                 ngroups=ngroups, gamma=1.4, kappa0=10.0, kap_rho_exp=1.0, kap_T_exp=-1.5,
+                 kap_eps_exp=-2.0, nsteps=nsteps, precision=precision)
+    rng = np.random.default_rng(seed)
+    y = pb.cell_centres(1)[:, None] * np.ones((1, nx))
+    band = (y >= 0.25) & (y < 0.75)
+    rho = np.where(band, 2.0, 1.0)
+    vx = np.where(band, 0.5, -0.5)
+    vy = 0.01 * rng.uniform(-1.0, 1.0, size=(ny, nx))
+    p = np.full((ny, nx), 2.5)
+    return _finish(pb, _flat(rho, p, vx, vy, p / rho))
+
+
+def gaussian_random_field(shape: Tuple[int, ...], slope: float, seed: int) -> np.ndarray:
+    """Periodic Gaussian random field with power spectrum P(k) ~ k^slope, zero mean, unit std."""
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal(shape)
+    kk = np.meshgrid(*[np.fft.fftfreq(m) * m for m in shape], indexing="ij")
+    k = np.sqrt(sum(q ** 2 for q in kk))
+    amp = np.zeros_like(k)
+    nz = k > 0
+    amp[nz] = k[nz] ** (slope / 2.0)
+    field = np.real(np.fft.ifftn(np.fft.fftn(white) * amp))
+    field -= field.mean()
+    return field / field.std()
+
+
+def lognormal_3d(n: int = 256, ngroups: int = 12, nsteps: int = 20, seed: int = 2,
+                 shape: Optional[Tuple[int, int, int]] = None,
+                 precision: str = "fp32") -> Tuple[Problem, np.ndarray]:
+    """Periodic 3-d lognormal density (k^-11/3 spectrum), uniform p, radiation at twice T."""
+    nx, ny, nz = shape if shape is not None else (n, n, n)
+    pb = Problem(name=f"lognormal3d_{nx}x{ny}x{nz}x{ngroups}g", dims=3, n=(nx, ny, nz),
+                 x_lo=(0.0, 0.0, 0.0), x_hi=(1.0, 1.0, 1.0), bc_lo=("periodic",) * 3,
+                 bc_hi=("periodic",) * 3, ngroups=ngroups, gamma=5.0 / 3.0, kappa0=1.0,
+                 kap_rho_exp=1.0, kap_T_exp=-3.5, kap_eps_exp=-3.0, nsteps=nsteps,
+                 precision=precision)
+    delta = gaussian_random_field((nz, ny, nx), -11.0 / 3.0, seed)
+    rho = np.exp(delta - 0.5)
+    p = np.ones_like(rho)
+    z = np.zeros_like(rho)
+    return _finish(pb, _flat(rho, p, z, z, z, 2.0 * p / rho))
+
+
+def blobs_2d(n: int = 512, ngroups: int = 8, nsteps: int = 50, seed: int = 3, nblobs: int = 16,
+             shape: Optional[Tuple[int, int]] = None,
+             precision: str = "fp32") -> Tuple[Problem, np.ndarray]:
+    """Gaussian density blobs in a uniform medium; kappa ~ rho^3 gives a 1e3 thin/thick contrast."""
+    nx, ny = shape if shape is not None else (n, n)
+    pb = Problem(name=f"blobs2d_{nx}x{ny}x{ngroups}g", dims=2, n=(nx, ny, 1), x_lo=(0.0, 0.0, 0.0),
+                 x_hi=(1.0, 1.0, 1.0), bc_lo=("outflow", "periodic", "periodic"),
+                 bc_hi=("outflow", "periodic", "periodic"), ngroups=ngroups, gamma=5.0 / 3.0,
+                 kappa0=1.0, kap_rho_exp=3.0, kap_T_exp=-1.5, kap_eps_exp=-2.0, nsteps=nsteps,
+                 precision=precision)
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.2, 0.8, size=(nblobs, 2))
+    x = pb.cell_centres(0)[None, :]
+    y = pb.cell_centres(1)[:, None]
+    rho = np.ones((ny, nx))
+    for cx, cy in centres:
+        rho = rho + 9.0 * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2.0 * 0.03 ** 2))
+    p = np.ones_like(rho)
+    z = np.zeros_like(rho)
+    return _finish(pb, _flat(rho, p, z, z, p / rho))
+
+
+def spherical_2d(nr: int = 640, nth: int = 128, ngroups: int = 20, nsteps: int = 200,
+                 seed: int = 4, precision: str = "fp32") -> Tuple[Problem, np.ndarray]:
+    """2-d spherical (r, theta) atmosphere, log-r grid over [1, 1000], rho ~ r^-2, p ~ r^-2.5."""
+    pb = Problem(name=f"sph2d_{nr}x{nth}x{ngroups}g", dims=2, n=(nr, nth, 1),
+                 x_lo=(0.0, 0.0, 0.0), x_hi=(math.log(1000.0), math.pi, 1.0),
+                 bc_lo=("reflect", "axis", "periodic"), bc_hi=("outflow", "axis", "periodic"),
+                 ngroups=ngroups, gamma=5.0 / 3.0, kappa0=1e3, kap_rho_exp=2.0, kap_T_exp=-1.5,
+                 kap_eps_exp=-2.0, geom="sph", map1="exp", nsteps=nsteps, precision=precision)
+    rng = np.random.default_rng(seed)
+    xi = rng.uniform(-1.0, 1.0, size=nth)
+    r = np.exp(pb.cell_centres(0))[None, :]
+    rho = r ** -2.0 * (1.0 + 1e-3 * xi[:, None])
+    p = r ** -2.5 * np.ones((nth, 1))
+    z = np.zeros_like(rho)
+    return _finish(pb, _flat(rho, p, z, z, p / rho))
+
+
+WORKLOADS = {
+    "sod1d": sod_1d,
+    "kh2d": kh_2d,
+    "lognormal3d": lognormal_3d,
+    "blobs2d": blobs_2d,
+    "sph2d": spherical_2d,
+}
+
+
+def random_state(pb: Problem, seed: int, flux_frac: float = 0.5) -> np.ndarray:
+    """A generic random conserved state (external layout) for unit-level parity tests.
+
+    rho in [0.5, 2], physical velocity in [-0.3, 0.3], internal energy in [0.5, 2], E_g in
+    [0.05, 1] and |F| up to flux_frac * c * E.  Covariant momentum/flux for Cartesian grids only.
+    """
+    rng = np.random.default_rng(seed)
+    D, G, N = pb.dims, pb.ngroups, pb.ncell
+    rho = rng.uniform(0.5, 2.0, N)
+    v = rng.uniform(-0.3, 0.3, (D, N))
+    u = rng.uniform(0.5, 2.0, N)
+    out = [rho]
+    for q in range(D):
+        out.append(rho * v[q])
+    out.append(u + 0.5 * rho * (v ** 2).sum(0))
+    gas = np.stack(out).reshape(-1)
+    E = rng.uniform(0.05, 1.0, (N, G))
+    dirs = rng.standard_normal((D, N, G))
+    dirs /= np.maximum(np.sqrt((dirs ** 2).sum(0)), 1e-12)
+    mag = rng.uniform(0.0, flux_frac, (N, G)) * pb.c_light * E
+    rad = [E.reshape(-1)] + [(dirs[q] * mag).reshape(-1) for q in range(D)]
+    return np.concatenate([gas, np.concatenate(rad)])

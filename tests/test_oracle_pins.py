@@ -1,0 +1,580 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU.  None compares the oracle with itself: each checks a closed
+form, a textbook solution, an independent quadrature, an invariant or a limit that the paper
+states, chosen so that a dropped term, a wrong sign or index, or a transposed operand in the
+oracle fails at least one of them.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_1806_07390_gb300 import workloads as W
+from tests import exact_riemann
+
+PI4_15 = math.pi ** 4 / 15.0
+
+
+def planck_integrand(t):
+    return t ** 3 / math.expm1(t) if t > 0 else 0.0
+
+
+def quad_band(a, b):
+    val, _ = integrate.quad(planck_integrand, a, b, epsabs=1e-300, epsrel=1e-13, limit=200)
+    return val
+
+
+def hydro_problem(n, gamma=1.4, bc="outflow", dims=1, ny=1):
+    return W.Problem(name="hydro", dims=dims, n=(n, ny, 1), x_lo=(0.0, 0.0, 0.0),
+                     x_hi=(1.0, 1.0, 1.0), bc_lo=(bc,) * 3, bc_hi=(bc,) * 3, ngroups=0,
+                     gamma=gamma, kappa0=0.0, kap_rho_exp=0.0, kap_T_exp=0.0, kap_eps_exp=0.0,
+                     c_light=1.0, couple=0)
+
+
+def gas_state(pb, rho, u, p, v=None):
+    NG = 2 + pb.dims
+    s = np.zeros(pb.state_size())
+    s[: pb.ncell] = rho
+    s[pb.ncell: 2 * pb.ncell] = rho * u
+    ke = 0.5 * rho * u * u
+    if pb.dims > 1:
+        vv = np.zeros_like(rho) if v is None else v
+        s[2 * pb.ncell: 3 * pb.ncell] = rho * vv
+        ke = ke + 0.5 * rho * vv * vv
+    s[(NG - 1) * pb.ncell: NG * pb.ncell] = p / (pb.gamma - 1.0) + ke
+    return s
+
+
+# ------------------------------------------------------------------ Planck group integrals (R14)
+def test_planck_series_are_complementary():
+    # the Bernoulli (lower) and exponential (upper) series are independent expansions; their sum
+    # must be the total integral pi^4/15 wherever both converge
+    L = oracle.lib()
+    for x in np.linspace(0.3, 3.0, 28):
+        tot = L.orc_planck_lower(x) + L.orc_planck_upper(x)
+        assert abs(tot - PI4_15) <= 2e-15 * PI4_15, x
+
+
+@pytest.mark.parametrize("a,b", [(1e-3, 1.78e-3), (0.01, 0.0178), (0.5, 1.9), (1.5, 2.5),
+                                 (2.0, 3.0), (3.0, 30.0), (0.2, 12.0), (40.0, 80.0)])
+def test_planck_band_matches_quadrature(a, b):
+    ref = quad_band(a, b)
+    got = oracle.lib().orc_planck_band(a, b)
+    assert abs(got - ref) <= 1e-13 * ref
+
+
+def test_planck_groups_sum_to_stefan_boltzmann():
+    pb, _ = W.sod_1d(n=8, ngroups=24)
+    pb.eps_min, pb.eps_max = 1e-5, 400.0
+    T = 1.3
+    tot = sum(oracle.planck_group(pb, g, T)[0] for g in range(pb.ngroups))
+    assert abs(tot - pb.a_rad * T ** 4) <= 1e-12 * pb.a_rad * T ** 4
+    # derivative against a central difference of the group energy
+    for g in (0, 7, 16):
+        h = 1e-5
+        fd = (oracle.planck_group(pb, g, T + h)[0] - oracle.planck_group(pb, g, T - h)[0]) / (2 * h)
+        assert abs(oracle.planck_group(pb, g, T)[1] - fd) <= 1e-8 * abs(fd)
+
+
+def test_init_equilibrium_matches_quadrature():
+    pb, prim = W.sod_1d(n=16, ngroups=12)
+    s = oracle.init_equilibrium(pb, prim)
+    gas, rad = oracle.split_state(pb, s)
+    edges = pb.eps_min * (pb.eps_max / pb.eps_min) ** (np.arange(pb.ngroups + 1) / pb.ngroups)
+    for c in (0, 15):
+        T = prim[-1, c]
+        for g in range(pb.ngroups):
+            ref = pb.a_rad * T ** 4 * 15 / math.pi ** 4 * quad_band(edges[g] / T, edges[g + 1] / T)
+            assert abs(rad[0, c, g] - ref) <= 1e-12 * ref
+    assert np.all(rad[1:] == 0.0)
+    np.testing.assert_allclose(gas[2], prim[1] / (pb.gamma - 1.0), rtol=1e-15)
+
+
+# ------------------------------------------------------------------ M1 closure (R7, Eq. 29)
+def test_m1_eddington_limits():
+    L = oracle.lib()
+    assert abs(L.orc_m1_chi(0.0) - 1.0 / 3.0) < 1e-16
+    assert abs(L.orc_m1_chi(1.0) - 1.0) < 1e-16
+    f = np.linspace(0, 1, 101)
+    chi = np.array([L.orc_m1_chi(x) for x in f])
+    assert np.all(np.diff(chi) > 0)
+    # P = E/3 delta for F = 0 (Eddington, Sec. 5.3)
+    c, E = 3.0, 2.0
+    for n in range(3):
+        row = oracle.m1_pressure_row(3, c, E, [0.0, 0.0, 0.0], n)
+        np.testing.assert_allclose(row, [E / 3.0 if q == n else 0.0 for q in range(3)], atol=1e-16)
+    # free streaming along x: P_xx = E, other rows zero; trace P = E for any f
+    row = oracle.m1_pressure_row(2, c, E, [c * E, 0.0], 0)
+    np.testing.assert_allclose(row, [E, 0.0], atol=1e-15)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        F = rng.standard_normal(3)
+        F *= rng.uniform(0, 1) * c * E / np.linalg.norm(F)
+        tr = sum(oracle.m1_pressure_row(3, c, E, F, n)[n] for n in range(3))
+        assert abs(tr - E) <= 1e-14 * E
+
+
+# ------------------------------------------------------------------ reconstruction (Sec. 5.1)
+def _exact_cell_averages(f_int, faces, weight_int=None):
+    """cell averages of f from its antiderivative (Cartesian) or of f*w / w (curvilinear)."""
+    if weight_int is None:
+        return (f_int(faces[1:]) - f_int(faces[:-1])) / (faces[1:] - faces[:-1])
+    return (f_int(faces[1:]) - f_int(faces[:-1])) / (weight_int(faces[1:]) - weight_int(faces[:-1]))
+
+
+def test_recon_reproduces_linear_and_monotone_quadratic():
+    pb = hydro_problem(32)
+    faces = np.linspace(0, 1, 33)
+    # monotone quadratic on [0,1]: q(x) = 1 + 2x + 0.5x^2
+    Q = lambda x: x + x ** 2 + x ** 3 / 6.0
+    avg = _exact_cell_averages(Q, faces)
+    q = lambda x: 1 + 2 * x + 0.5 * x * x
+    for i in range(2, 30):
+        a, b = oracle.recon_cell(pb, 0, i, avg[i - 1], avg[i], avg[i + 1], kind=2)
+        assert abs(a - q(faces[i])) < 1e-13 and abs(b - q(faces[i + 1])) < 1e-13
+        # linear MC reproduces linear data exactly
+        la, lb = oracle.recon_cell(pb, 0, i, 2 * i - 2.0, 2.0 * i, 2 * i + 2.0, kind=1)
+        assert abs(la - (2 * i - 1.0)) < 1e-13 and abs(lb - (2 * i + 1.0)) < 1e-13
+
+
+def test_recon_curvilinear_moments_reproduce_quadratic():
+    # log-radius spherical grid: averages with the r^3 weight in x1 = ln r (Eq. 14)
+    pb, _ = W.spherical_2d(nr=40, nth=8, ngroups=1)
+    faces = np.linspace(pb.x_lo[0], pb.x_hi[0], 41)
+    # q(x) = 2 + x + 0.1 x^2 (monotone on [0, ln 1000]); weight w = exp(3x)
+    Wint = lambda x: np.exp(3 * x) / 3.0
+
+    def Qw(x):  # antiderivative of q(x) exp(3x)
+        e = np.exp(3 * x)
+        return e * ((2 + x + 0.1 * x * x) / 3.0 - (1 + 0.2 * x) / 9.0 + 0.2 / 27.0)
+
+    avg = _exact_cell_averages(Qw, faces, Wint)
+    q = lambda x: 2 + x + 0.1 * x * x
+    for i in range(3, 37):
+        a, b = oracle.recon_cell(pb, 0, i, avg[i - 1], avg[i], avg[i + 1], kind=2)
+        assert abs(a - q(faces[i])) < 1e-11 * q(faces[i]), (i, a, q(faces[i]))
+        assert abs(b - q(faces[i + 1])) < 1e-11 * q(faces[i + 1])
+
+
+def test_recon_third_order_on_smooth_data():
+    # monotone smooth profile: face errors fall by ~8 per halving (Sec. 5.1, third order)
+    errs = []
+    for n in (40, 80, 160):
+        pb = hydro_problem(n)
+        faces = np.linspace(0, 1, n + 1)
+        F = lambda x: np.log(np.cosh(4 * (x - 0.5))) / 4.0 + x  # antiderivative of tanh(4(x-.5)) + 1
+        f = lambda x: np.tanh(4 * (x - 0.5)) + 1
+        avg = _exact_cell_averages(F, faces)
+        e = 0.0
+        for i in range(n // 4, 3 * n // 4):
+            a, b = oracle.recon_cell(pb, 0, i, avg[i - 1], avg[i], avg[i + 1], kind=2)
+            e = max(e, abs(a - f(faces[i])), abs(b - f(faces[i + 1])))
+        errs.append(e)
+    order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(order > 2.7), (errs, order)
+
+
+def _end_slopes(a, m, b):
+    # uniform cell, unit width: parabola with face values a, b and mean m; slopes at both faces
+    return -4 * a - 2 * b + 6 * m, 2 * a + 4 * b - 6 * m
+
+
+def test_recon_is_bounded_by_neighbours():
+    # TVD property (Sec. 2): every face value lies within the data of the cells beside that face,
+    # and the final parabola is monotone in the cell (R3, PPM-consistent reading)
+    pb = hydro_problem(16)
+    rng = np.random.default_rng(5)
+    for _ in range(4000):
+        pm, p0, pp = rng.uniform(0, 1, 3)
+        for kind in (1, 2):
+            a, b = oracle.recon_cell(pb, 0, 8, pm, p0, pp, kind=kind)
+            assert min(pm, p0) - 1e-15 <= a <= max(pm, p0) + 1e-15
+            assert min(pp, p0) - 1e-15 <= b <= max(pp, p0) + 1e-15
+            if kind == 2:
+                sl, sr = _end_slopes(a, p0, b)
+                assert sl * sr >= -1e-12, (pm, p0, pp, a, b)
+        # literal reading of the in-cell reset: still monotone in the cell, but not TVD
+        a, b = oracle.recon_cell(pb, 0, 8, pm, p0, pp, kind=2, r3_literal=1)
+        sl, sr = _end_slopes(a, p0, b)
+        assert sl * sr >= -1e-12
+    # extrema of the data give piecewise constant states (R4)
+    assert oracle.recon_cell(pb, 0, 8, 0.2, 0.9, 0.3, kind=2) == (0.9, 0.9)
+    assert oracle.recon_cell(pb, 0, 8, 0.2, 0.9, 0.3, kind=1) == (0.9, 0.9)
+
+
+def test_recon_in_cell_extremum_reset_gives_zero_end_slope():
+    # data whose system-1 parabola peaks inside the cell near the upper face (PPM-consistent R3):
+    # the lower face is moved so that the slope vanishes at the upper face
+    pb = hydro_problem(16)
+    pm, p0, pp = 0.0, 0.9, 1.0
+    a, b = oracle.recon_cell(pb, 0, 8, pm, p0, pp, kind=2)
+    # uniform cell of width w: parabola with a, mean p0, b; slope at upper face is 6p0-2a-4b
+    assert abs(6 * p0 - 2 * a - 4 * b) < 1e-13
+    assert abs(b - 0.975) < 1e-14  # face-interval reset value p_{i+1} - (p_{i+1}-p_i)/4
+
+
+# ------------------------------------------------------------------ HLLC (Sec. 5.2)
+def euler_flux(D, gam, W):
+    rho, p = W[0], W[1]
+    v = np.array(W[2:2 + D])
+    E = p / (gam - 1) + 0.5 * rho * v @ v
+    f = [rho * v[0]] + [rho * v[0] * v[q] + (p if q == 0 else 0.0) for q in range(D)]
+    return np.array(f + [(E + p) * v[0]])
+
+
+def test_hllc_consistency_and_upwinding():
+    gam = 1.4
+    rng = np.random.default_rng(1)
+    for D in (1, 2, 3):
+        for _ in range(50):
+            Wd = [rng.uniform(0.1, 2), rng.uniform(0.1, 2)] + list(rng.uniform(-1, 1, D))
+            f, vs = oracle.hllc(D, gam, Wd, Wd)
+            np.testing.assert_allclose(f, euler_flux(D, gam, Wd), rtol=1e-13, atol=1e-14)
+            assert abs(vs - Wd[2]) < 1e-13
+        # supersonic to the right: flux is the left physical flux
+        WL = [1.0, 1.0, 5.0] + [0.3] * (D - 1)
+        WR = [0.5, 0.2, 4.0] + [-0.2] * (D - 1)
+        f, _ = oracle.hllc(D, gam, WL, WR)
+        np.testing.assert_allclose(f, euler_flux(D, gam, WL), rtol=1e-14)
+
+
+def test_hllc_stationary_contact_and_mirror_symmetry():
+    gam = 5.0 / 3.0
+    f, vs = oracle.hllc(2, gam, [1.0, 0.7, 0.0, 0.2], [0.1, 0.7, 0.0, -0.4])
+    np.testing.assert_allclose(f, [0.0, 0.7, 0.0, 0.0], atol=1e-15)
+    assert vs == 0.0
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        WL = [rng.uniform(0.1, 2), rng.uniform(0.1, 2), rng.uniform(-1, 1), rng.uniform(-1, 1)]
+        WR = [rng.uniform(0.1, 2), rng.uniform(0.1, 2), rng.uniform(-1, 1), rng.uniform(-1, 1)]
+        f, vs = oracle.hllc(2, gam, WL, WR)
+        mL = [WR[0], WR[1], -WR[2], WR[3]]
+        mR = [WL[0], WL[1], -WL[2], WL[3]]
+        g, ws = oracle.hllc(2, gam, mL, mR)
+        np.testing.assert_allclose(g, [-f[0], f[1], -f[2], -f[3]], rtol=1e-12, atol=1e-14)
+        assert abs(ws + vs) < 1e-13
+
+
+# ------------------------------------------------------------------ Sod shock tube (Sec. 8.3)
+def run_sod(n, t_end=0.2, cfl=0.4):
+    pb = hydro_problem(n)
+    x = (np.arange(n) + 0.5) / n
+    rho = np.where(x < 0.5, 1.0, 0.125)
+    p = np.where(x < 0.5, 1.0, 0.1)
+    s = gas_state(pb, rho, np.zeros(n), p)
+    dt = cfl / n / 2.0
+    nsteps = int(round(t_end / dt))
+    out, st = oracle.run(pb, s, t_end / nsteps, nsteps)
+    assert st == 0
+    return pb, out
+
+
+def test_sod_converges_to_exact_riemann_solution():
+    errs = []
+    for n in (64, 128, 256, 512):
+        pb, out = run_sod(n)
+        exact = exact_riemann.cell_averages(np.linspace(0, 1, n + 1), 0.2, 0.5, (1.0, 0.0, 1.0),
+                                            (0.125, 0.0, 0.1), 1.4)
+        errs.append(np.mean(np.abs(out[:n] - exact[0])))
+    order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[-1] < 2.5e-3 and np.all(order > 0.6), (errs, order)
+    # quality bar at 64 zones (Sec. 8.3): shock within ~2-3 zones, contact within ~4-6 zones
+    pb, out = run_sod(64)
+    rho = out[:64]
+    x = (np.arange(64) + 0.5) / 64
+    shock = (x > 0.8) & (x < 0.9)
+    in_shock = np.sum((rho > 0.13) & (rho < 0.26) & shock)
+    assert in_shock <= 3
+    contact = (x > 0.62) & (x < 0.76)
+    in_contact = np.sum((rho > 0.27) & (rho < 0.42) & contact)
+    assert in_contact <= 6
+
+
+def test_smooth_advection_is_third_order():
+    # rho = 2 + tanh((x - x0 - t)/w), v = 1, p = 1 is an exact contact solution; dt ~ dx^1.5 so
+    # that the second-order time error stays below the third-order spatial error
+    errs = []
+    for n in (64, 128, 256):
+        pb = hydro_problem(n, gamma=1.4)
+        faces = np.linspace(0, 1, n + 1)
+        w, x0, t_end = 0.08, 0.35, 0.1
+        avg = lambda s: 2.0 + w * (np.log(np.cosh((faces[1:] - s) / w)) -
+                                   np.log(np.cosh((faces[:-1] - s) / w))) / (1.0 / n)
+        s = gas_state(pb, avg(x0), np.ones(n), np.ones(n))
+        dt0 = 0.3 * (1.0 / n) ** 1.5
+        nsteps = int(math.ceil(t_end / dt0))
+        out, st = oracle.run(pb, s, t_end / nsteps, nsteps)
+        mid = slice(int(0.3 * n), int(0.7 * n))
+        errs.append(np.mean(np.abs(out[:n][mid] - avg(x0 + t_end)[mid])))
+    order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(order > 2.6), (errs, order)
+
+
+# ------------------------------------------------------------------ conservation (Sec. 4, Eq. 8)
+def test_periodic_conservation_to_round_off():
+    pb, prim = W.kh_2d(nx=12, ny=10, ngroups=3)
+    pb.couple = 0
+    pb.c_light = 5.0
+    s = W.random_state(pb, seed=3)
+    t0 = oracle.totals(pb, s)
+    out, st = oracle.run(pb, s, 2e-3, 3)
+    t1 = oracle.totals(pb, out)
+    scale = np.array([t0[0], t0[0], t0[0], t0[0], t0[4], t0[5]])
+    assert np.all(np.abs(t1 - t0) <= 2e-15 * scale * 12 * 10), (t1 - t0) / scale
+
+
+def test_3d_periodic_conservation_and_axis_permutation():
+    pb, prim = W.lognormal_3d(shape=(6, 5, 4), ngroups=2)
+    pb.couple = 0
+    pb.c_light = 4.0
+    s = W.random_state(pb, seed=8)
+    t0 = oracle.totals(pb, s)
+    out, _ = oracle.run(pb, s, 1e-3, 2)
+    t1 = oracle.totals(pb, out)
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * abs(t0[4]))
+
+
+def test_coupling_conserves_energy_and_momentum():
+    pb, prim = W.kh_2d(nx=8, ny=6, ngroups=5)
+    pb.c_light = 20.0
+    s = W.random_state(pb, seed=4)
+    gas0, rad0 = oracle.split_state(pb, s)
+    out, st = oracle.couple(pb, s, 0.01)
+    assert st == 0
+    gas1, rad1 = oracle.split_state(pb, out)
+    c2 = pb.c_light ** 2
+    # momentum: m + sum_g F/c^2 unchanged cell by cell (Eq. 31)
+    for q in range(2):
+        np.testing.assert_allclose(gas1[1 + q] + rad1[1 + q].sum(1) / c2,
+                                   gas0[1 + q] + rad0[1 + q].sum(1) / c2, rtol=0, atol=1e-14)
+    # energy: rho e + sum E changes only by the work term of Eq. 32
+    vcon = gas0[1:3] / gas0[0]
+    work = (vcon[:, :, None] * (rad1[1:] - rad0[1:])).sum((0, 2)) / c2
+    np.testing.assert_allclose(gas1[3] + rad1[0].sum(1) + work, gas0[3] + rad0[0].sum(1),
+                               rtol=1e-14)
+
+
+def test_coupled_state_solves_the_implicit_system():
+    # independent check of Eqs. 24c/25 at the converged temperature with quadrature Planck bands
+    pb, prim = W.sod_1d(n=4, ngroups=6)
+    pb.c_light = 30.0
+    s = W.random_state(pb, seed=7, flux_frac=0.0)
+    dt = 0.02
+    out, st = oracle.couple(pb, s, dt)
+    assert st == 0
+    gas0, rad0 = oracle.split_state(pb, s)
+    gas1, rad1 = oracle.split_state(pb, out)
+    edges = pb.eps_min * (pb.eps_max / pb.eps_min) ** (np.arange(pb.ngroups + 1) / pb.ngroups)
+    cen = np.sqrt(edges[1:] * edges[:-1])
+    for c in range(pb.ncell):
+        rho = gas1[0, c]
+        u = gas1[2, c] - 0.5 * gas1[1, c] ** 2 / rho
+        T = u * (pb.gamma - 1) / rho
+        for g in range(pb.ngroups):
+            B = pb.a_rad * T ** 4 * 15 / math.pi ** 4 * quad_band(edges[g] / T, edges[g + 1] / T)
+            kap = pb.kappa0 * rho * T ** -1.5 * cen[g] ** -2.0
+            tau = pb.c_light * dt * kap
+            ref = (rad0[0, c, g] + tau * B) / (1 + tau)
+            assert abs(rad1[0, c, g] - ref) <= 1e-11 * ref, (c, g, rad1[0, c, g], ref)
+
+
+def _one_cell_gray(rho, T0, Tr, kappa):
+    pb = W.Problem(name="gray", dims=1, n=(1, 1, 1), x_lo=(0, 0, 0), x_hi=(1, 1, 1),
+                   bc_lo=("periodic",) * 3, bc_hi=("periodic",) * 3, ngroups=1, gamma=5.0 / 3.0,
+                   kappa0=kappa, kap_rho_exp=0.0, kap_T_exp=0.0, kap_eps_exp=0.0,
+                   eps_min=1e-7, eps_max=2e3, c_light=10.0)
+    s = np.zeros(pb.state_size())
+    s[0] = rho
+    s[2] = rho * T0 / (pb.gamma - 1)
+    s[3] = pb.a_rad * Tr ** 4
+    return pb, s
+
+
+def test_turner_stone_relaxation_closed_form():
+    # gas heated by a dominant radiation reservoir: rho c_v dT/dt = c kappa a (Tr^4 - T^4), whose
+    # solution t(T) has the closed form below; backward Euler converges to it at first order
+    rho, T0, Tr, kappa = 1e-6, 0.2, 1.0, 3.0
+    cv = 1.5
+
+    def t_of_T(T):
+        pref = rho * cv / (10.0 * kappa * 0.1) / (4 * Tr ** 3)
+        return pref * (math.log((Tr + T) / (Tr - T)) + 2 * math.atan(T / Tr))
+
+    t_end = t_of_T(0.9) - t_of_T(T0)
+    errs = []
+    for nstep in (50, 100, 200, 400):
+        pb, s = _one_cell_gray(rho, T0, Tr, kappa)
+        dt = t_end / nstep
+        for _ in range(nstep):
+            s, st = oracle.couple(pb, s, dt)
+            assert st == 0
+        T = s[2] * (pb.gamma - 1) / s[0]
+        # reservoir depletion: u + E conserved; E changes by -(u - u0) (tiny), correct Tr for it
+        errs.append(abs(T - 0.9))
+    order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[-1] < 2e-3 and np.all(np.abs(order - 1.0) < 0.15), (errs, order)
+
+
+def test_equilibrium_is_a_fixed_point_and_stiff_limit():
+    pb, s = _one_cell_gray(1.0, 0.7, 0.7, 2.0)
+    out, st = oracle.couple(pb, s, 0.3)
+    np.testing.assert_allclose(out, s, rtol=1e-13, atol=0)
+    # very large c dt kappa: E -> B(T_new) (Eq. 25 limit)
+    pb, s = _one_cell_gray(1.0, 0.5, 1.1, 1e12)
+    out, st = oracle.couple(pb, s, 1.0)
+    T = out[2] * (pb.gamma - 1) / out[0]
+    assert st == 0
+    assert abs(out[3] - pb.a_rad * T ** 4) <= 1e-10 * out[3]
+    assert abs((out[2] + out[3]) - (s[2] + s[3])) <= 1e-15 * (s[2] + s[3])
+
+
+def test_fick_limit_of_operator_split_flux_update():
+    # Sec. 5.3, Eq. 30: in a static, optically thick medium the explicit flux update followed by
+    # the implicit absorption gives F = -c/(3 kappa) dE/dx as c dt kappa >> 1
+    n, G = 256, 1
+    pb = W.Problem(name="fick", dims=1, n=(n, 1, 1), x_lo=(0, 0, 0), x_hi=(1, 1, 1),
+                   bc_lo=("periodic",) * 3, bc_hi=("periodic",) * 3, ngroups=G, gamma=5 / 3,
+                   kappa0=1e6, kap_rho_exp=0.0, kap_T_exp=0.0, kap_eps_exp=0.0, eps_min=1e-7,
+                   eps_max=2e3, c_light=10.0, couple=1)
+    x = (np.arange(n) + 0.5) / n
+    faces = np.linspace(0, 1, n + 1)
+    amp = 0.05
+    # cell averages of 0.1 (1 + amp cos(2 pi x))
+    Eavg = 0.1 * (1 + amp * (np.sin(2 * np.pi * faces[1:]) - np.sin(2 * np.pi * faces[:-1])) * n / (2 * np.pi))
+    T = (Eavg / pb.a_rad) ** 0.25
+    s = np.zeros(pb.state_size())
+    s[:n] = 1.0
+    s[2 * n: 3 * n] = T / (pb.gamma - 1)
+    s[3 * n: 4 * n] = Eavg
+    dt = 0.2 / n / pb.c_light
+    L = oracle.rhs(pb, s)
+    s1 = s + dt * L
+    out, st = oracle.couple(pb, s1, dt)
+    F = out[4 * n:]
+    dEdx = -0.1 * amp * 2 * np.pi * np.sin(2 * np.pi * x)
+    fick = -pb.c_light / (3 * pb.kappa0) * dEdx
+    # MC clipping at the extrema of E leaves first-order errors there; the bulk is second order
+    assert np.max(np.abs(F - fick)) <= 0.015 * np.max(np.abs(fick))
+    assert np.sum(np.abs(F - fick)) <= 0.003 * np.sum(np.abs(fick))
+
+
+def test_hll_correction_scales_dissipation_by_inverse_depth():
+    # F = 0, v = 0, jump in E: the energy flux is pure HLL dissipation, so dE/dt scales with
+    # eps = min(1, 1/tau) (Eqs. 17-18); tau <= 1 gives the uncorrected HLL flux
+    n = 16
+
+    def dEdt(kappa0):
+        pb = W.Problem(name="hll", dims=1, n=(n, 1, 1), x_lo=(0, 0, 0), x_hi=(1, 1, 1),
+                       bc_lo=("periodic",) * 3, bc_hi=("periodic",) * 3, ngroups=1, gamma=5 / 3,
+                       kappa0=kappa0, kap_rho_exp=0.0, kap_T_exp=0.0, kap_eps_exp=0.0,
+                       c_light=10.0, couple=0)
+        s = np.zeros(pb.state_size())
+        s[:n] = 1.0
+        s[2 * n: 3 * n] = 1.0
+        s[3 * n: 4 * n] = np.where(np.arange(n) < n // 2, 1.0, 0.5)
+        return oracle.rhs(pb, s)[3 * n: 4 * n]
+
+    thin_a, thin_b = dEdt(1.0), dEdt(8.0)  # tau = kappa dx = 1/16 and 1/2: both uncorrected
+    np.testing.assert_array_equal(thin_a, thin_b)
+    thick = dEdt(64.0)  # tau = 4
+    np.testing.assert_allclose(thick, thin_a / 4.0, rtol=1e-14, atol=1e-14)
+
+
+# ------------------------------------------------------------------ geometry (Appendices A-D)
+def test_spherical_geometry_closed_forms():
+    pb, _ = W.spherical_2d(nr=16, nth=8, ngroups=1)
+    vol_r, cen_r, _ = oracle.geometry(pb, 0)
+    xf = np.linspace(pb.x_lo[0], pb.x_hi[0], 17)
+    np.testing.assert_allclose(vol_r, (np.exp(3 * xf[1:]) - np.exp(3 * xf[:-1])) / 3.0, rtol=1e-13)
+    vol_t, cen_t, _ = oracle.geometry(pb, 1)
+    tf = np.linspace(0, np.pi, 9)
+    np.testing.assert_allclose(vol_t, np.cos(tf[:-1]) - np.cos(tf[1:]), rtol=1e-13)
+    G = oracle.christoffel(pb)
+    # exponential radial map: <(dr/dx1)/r> = 1, <r/(dr/dx1)> = 1; identity theta: <G^2_22> = 0
+    np.testing.assert_allclose(G["G221"], 1.0, rtol=1e-13)
+    np.testing.assert_allclose(G["G122"], -1.0, rtol=1e-13)
+    np.testing.assert_allclose(G["G111"], 1.0, rtol=1e-12)
+    np.testing.assert_allclose(G["G222"], 0.0, atol=1e-12)
+    np.testing.assert_allclose(G["G332"], (np.sin(tf[1:]) - np.sin(tf[:-1])) / vol_t, rtol=1e-12,
+                               atol=1e-14)
+
+
+def test_spherical_static_atmosphere_stays_static():
+    # uniform p and E, v = F = 0: flux divergence and geometric sources cancel (Eqs. 84-85)
+    pb, _ = W.spherical_2d(nr=20, nth=12, ngroups=3)
+    pb.couple = 0
+    N = pb.ncell
+    s = np.zeros(pb.state_size())
+    s[:N] = np.linspace(0.5, 2.0, N)  # density need not be uniform for a static balance
+    s[3 * N: 4 * N] = 0.7 / (pb.gamma - 1)
+    s[4 * N: 4 * N + N * 3] = 0.3
+    L = oracle.rhs(pb, s)
+    gasL, radL = oracle.split_state(pb, L)
+    assert np.max(np.abs(gasL)) < 1e-12
+    assert np.max(np.abs(radL)) < 1e-11 * pb.c_light ** 2
+
+
+def test_unsplit_update_is_symmetric_under_axis_swap():
+    # Sec. 8.7: data symmetric about y = x stays exactly symmetric
+    pb, _ = W.kh_2d(nx=10, ny=10, ngroups=2)
+    pb.c_light = 8.0
+    s = W.random_state(pb, seed=11)
+    N, G = pb.ncell, pb.ngroups
+    gas, rad = oracle.split_state(pb, s)
+    sym = lambda f: 0.5 * (f.reshape(10, 10) + f.reshape(10, 10).T).reshape(-1)
+    gas[0] = sym(gas[0])
+    gas[3] = sym(gas[3])
+    mx = gas[1].reshape(10, 10)
+    mxs = 0.5 * (mx + gas[2].reshape(10, 10).T)
+    gas[1] = mxs.reshape(-1)
+    gas[2] = mxs.T.reshape(-1)
+    for g in range(G):
+        rad[0, :, g] = sym(rad[0, :, g])
+        fx = 0.5 * (rad[1, :, g].reshape(10, 10) + rad[2, :, g].reshape(10, 10).T)
+        rad[1, :, g] = fx.reshape(-1)
+        rad[2, :, g] = fx.T.reshape(-1)
+    out, st = oracle.run(pb, s, 1e-3, 1)
+    g2, r2 = oracle.split_state(pb, out)
+    np.testing.assert_array_equal(g2[0].reshape(10, 10), g2[0].reshape(10, 10).T)
+    np.testing.assert_array_equal(g2[1].reshape(10, 10), g2[2].reshape(10, 10).T)
+    np.testing.assert_array_equal(r2[1, :, 1].reshape(10, 10), r2[2, :, 1].reshape(10, 10).T)
+
+
+def test_free_streaming_front_moves_at_c():
+    n = 200
+    pb = W.Problem(name="beam", dims=1, n=(n, 1, 1), x_lo=(0, 0, 0), x_hi=(1, 1, 1),
+                   bc_lo=("outflow",) * 3, bc_hi=("outflow",) * 3, ngroups=1, gamma=5 / 3,
+                   kappa0=0.0, kap_rho_exp=0.0, kap_T_exp=0.0, kap_eps_exp=0.0, c_light=1.0,
+                   couple=0)
+    x = (np.arange(n) + 0.5) / n
+    E = 1e-6 + np.exp(-((x - 0.2) / 0.03) ** 2)
+    s = np.zeros(pb.state_size())
+    s[:n] = 1.0
+    s[2 * n: 3 * n] = 1.0
+    s[3 * n: 4 * n] = E
+    s[4 * n:] = E * pb.c_light
+    dt = 0.4 / n
+    out, _ = oracle.run(pb, s, dt, 250)
+    Eo = out[3 * n: 4 * n]
+    moved = (x @ Eo) / Eo.sum() - (x @ E) / E.sum()
+    assert abs(moved - 250 * dt * pb.c_light) < 2e-3
+
+
+def test_reflecting_walls_conserve_mass_and_energy():
+    # Sec. 7.5: mirrored ghosts make the wall flux of mass and energy vanish exactly
+    pb, _ = W.blobs_2d(shape=(10, 8), ngroups=2)
+    pb.bc_lo = ("reflect", "reflect", "periodic")
+    pb.bc_hi = ("reflect", "reflect", "periodic")
+    pb.couple = 0
+    pb.c_light = 6.0
+    s = W.random_state(pb, seed=21)
+    t0 = oracle.totals(pb, s)
+    out, _ = oracle.run(pb, s, 1e-3, 2)
+    t1 = oracle.totals(pb, out)
+    assert abs(t1[0] - t0[0]) <= 1e-14 * t0[0]
+    assert abs(t1[4] - t0[4]) <= 1e-14 * t0[4]
+    assert abs(t1[5] - t0[5]) <= 1e-14 * t0[5]
