@@ -1,0 +1,158 @@
+/* fx.h -- C ABI of the GB300 (sm_103a) multigroup two-moment (M1) radiation-hydrodynamics
+ * stage update.
+ *
+ * The method is the explicit transport + implicit interaction update of Skinner, Dolence,
+ * Burrows, Radice & Vartanyan (2019), "FORNAX: a Flexible Code for Multiphysics Astrophysical
+ * Simulations":
+ *   - covariant Newtonian hydrodynamics and comoving multigroup radiation moments (Sec. 3,
+ *     Eqs. 1-5, 11-12), finite-volume discretisation (Sec. 4, Eqs. 8-9);
+ *   - coordinate-moment, TVD-limited parabolic reconstruction (Sec. 5.1, Eqs. 13-16), linear
+ *     reconstruction of the radiation moments (Sec. 2);
+ *   - HLLC gas fluxes, M1-closure HLL radiation fluxes with the diffusion-limit correction and
+ *     contact-velocity upwinded advection (Sec. 5.2, Eqs. 17-19);
+ *   - SSP-RK2 (Sec. 4) with the operator-split implicit energy and momentum coupling (Sec. 5.3,
+ *     Eqs. 24-32; Sec. 6) after each stage.
+ *
+ * Every call returns an fx_status.  No exception or signal crosses the boundary.  Errors are
+ * sticky per handle: once a call fails, later calls return the same status until
+ * fx_clear_error().  fx_last_error() gives a human-readable reason.
+ *
+ * Threading: a handle is not thread-safe; use one handle per host thread.  All device work of a
+ * handle runs on the CUDA stream given to fx_bind_workspace().
+ */
+#ifndef FX_H
+#define FX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fx_grid fx_grid; /* opaque; created and owned by the library */
+
+typedef enum {
+  FX_OK = 0,
+  FX_ERR_ARG = -1,         /* invalid argument or parameter combination                    */
+  FX_ERR_CUDA = -2,        /* a CUDA runtime call or kernel launch failed                  */
+  FX_ERR_WORKSPACE = -3,   /* no workspace bound, or the bound one is too small/misaligned */
+  FX_ERR_NEWTON = -4,      /* the coupling's Newton and bisection failed in some cell      */
+  FX_ERR_FLOOR = -5,       /* a density, pressure or radiation-energy floor was applied   */
+  FX_ERR_NONFINITE = -6,   /* a non-finite value appeared in the state                     */
+  FX_ERR_UNSUPPORTED = -7  /* parameters outside what this build supports                  */
+} fx_status;
+
+enum { FX_OUTFLOW = 0, FX_PERIODIC = 1, FX_REFLECT = 2, FX_AXIS = 3 }; /* Sec. 7.5 */
+enum { FX_CART = 0, FX_SPH = 1 };       /* Cartesian, or spherical (x1 -> r, x2 -> theta)  */
+enum { FX_MAP_ID = 0, FX_MAP_EXP = 1 }; /* radial map r = x1 or r = exp(x1) (Appendix A)   */
+enum { FX_FP64 = 0, FX_FP32 = 1 };      /* state/transport precision                        */
+enum { FX_NTOTALS = 6 };
+
+/* Grid, physics and solver parameters (plain data, copied at fx_grid_create).
+ *   dims, n[d]         number of dimensions (1..3) and cells per direction (n[d] ignored for
+ *                      d >= dims); each direction is uniform in its generic coordinate x^d
+ *                      on [x_lo[d], x_hi[d]].
+ *   geom, map1         FX_CART, or FX_SPH with dims == 2: x1 -> r through map1, x2 = theta.
+ *   bc_lo/bc_hi        boundary condition per direction and side.
+ *   ngroups            energy groups (1..32), logarithmically spaced edges
+ *                      eps_min (eps_max/eps_min)^(g/ngroups) (Sec. 4).
+ *   gamma              ideal-gas adiabatic index; c_v = 1/(gamma-1), T = p/rho.
+ *   c_light, a_rad     (reduced) speed of light and radiation constant.
+ *   kappa0, kap_*_exp  absorption opacity kappa_g = kappa0 rho^a T^b eps_g^d with
+ *                      eps_g = sqrt(edge_g edge_g+1); a and b must be multiples of 1/2.
+ *   sigma0             scattering opacity sigma = sigma0 rho.
+ *   precision          FX_FP64 (plain FP64 path) or FX_FP32 (FP32 state, reconstruction and
+ *                      fluxes; FP64 temperature/energy bookkeeping in the coupling and FP64
+ *                      conserved totals).
+ *   rad_recon_order    1 = linear + MC limiter (the paper's choice for radiation).
+ *   couple             1 = apply the implicit interaction after each RK stage.
+ *   newton_maxit, bisect_maxit, newton_rtol
+ *                      coupling iteration caps and the relative temperature step tolerance.
+ *   rho_floor, p_floor, E_floor
+ *                      floors; applying one sets FX_ERR_FLOOR.
+ */
+typedef struct {
+  int dims;
+  int64_t n[3];
+  int geom;
+  int map1;
+  double x_lo[3], x_hi[3];
+  int bc_lo[3], bc_hi[3];
+  int ngroups;
+  double eps_min, eps_max;
+  double gamma, c_light, a_rad;
+  double kappa0, kap_rho_exp, kap_T_exp, kap_eps_exp, sigma0;
+  int precision;
+  int rad_recon_order;
+  int couple;
+  int newton_maxit, bisect_maxit;
+  double newton_rtol;
+  double rho_floor, p_floor, E_floor;
+} fx_params;
+
+/* State layout (upload, download, and the device copy inside the workspace): ncell = prod n[d],
+ * cells in x-fastest order.  Gas block [2+dims][ncell]: rho, covariant momentum rho v_1..v_D,
+ * total energy rho e.  Then the radiation block [1+dims][ncell][ngroups] (group innermost):
+ * E_g, covariant F_g1..F_gD.  fx_state_elems() gives the element count. */
+
+/* Validate parameters, build the geometry and reconstruction tables (host, FP64) and return the
+ * workspace size in bytes the caller must provide.  *out receives the new handle (NULL on
+ * error).  No device memory is allocated by the library for the state; small read-only
+ * geometry tables are copied to the device at fx_bind_workspace. */
+fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspace_bytes);
+
+/* Bind caller-owned device memory (e.g. a torch tensor) of at least `bytes` as the workspace,
+ * 256-byte aligned, and the CUDA stream (cudaStream_t, may be NULL for the default stream) on
+ * which all later work of this handle is enqueued.  The caller keeps ownership and must keep
+ * the memory alive until fx_grid_destroy. */
+fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_stream);
+
+/* Number of elements of the state in the layout above. */
+size_t fx_state_elems(const fx_grid* h);
+
+/* Copy a full state into the workspace.  src holds fx_state_elems() elements of type
+ * src_precision (FX_FP64 = double, FX_FP32 = float) in host memory (src_is_device = 0,
+ * synchronous) or device memory (src_is_device = 1, enqueued on the bound stream). */
+fx_status fx_state_upload(fx_grid* h, const void* src, int src_precision, int src_is_device);
+
+/* Build the state from primitives (Sec. 5.1 variables): prim is [3+dims][ncell] doubles with
+ * rows rho, p, vhat_1..vhat_D (physical velocity), T_rad.  Radiation starts in local
+ * equilibrium, E_g = B_g(T_rad) (Planck group energy), F_g = 0.  Host or device pointer. */
+fx_status fx_state_init_equilibrium(fx_grid* h, const double* prim, int prim_is_device);
+
+/* Enqueue nsteps SSP-RK2 steps of size dt on the bound stream (asynchronous).  Returns FX_OK
+ * unless arguments are invalid, a launch fails or an earlier error is pending; device-side
+ * conditions (Newton failure, floors, non-finite values) are reported by fx_sync(). */
+fx_status fx_step(fx_grid* h, double dt, int nsteps);
+
+/* Wait for the bound stream and return the sticky status, including device-side conditions
+ * raised by earlier fx_step calls. */
+fx_status fx_sync(fx_grid* h);
+
+/* Conserved totals over the grid (synchronises): out[0] mass, out[1..3] momentum components
+ * including the radiation momentum sum_g F_g/c^2, out[4] total energy rho e + sum_g E_g,
+ * out[5] radiation energy sum_g E_g; each sum_cells V (...) in FP64 with compensated
+ * summation. */
+fx_status fx_conserved_totals(fx_grid* h, double out[FX_NTOTALS]);
+
+/* Copy the state out, converting to dst_precision, to host (synchronous) or device memory. */
+fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is_device);
+
+/* Number of stage-kernel launches enqueued by one fx_step(dt, 1) call. */
+int fx_launches_per_step(const fx_grid* h);
+
+/* Host-side inspection (no GPU needed): the FP64 reconstruction/divergence table of direction d,
+ * fx_debug_ntab() entries of n[d] + 4 rows each (padded cells -2 .. n+1), entry-major.  Returns
+ * the number of doubles (copied only when cap is large enough), or -1 for a bad argument. */
+int fx_debug_table(const fx_grid* h, int d, double* out, size_t cap);
+int fx_debug_ntab(void);
+
+const char* fx_last_error(const fx_grid* h);
+void fx_clear_error(fx_grid* h);
+void fx_grid_destroy(fx_grid* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FX_H */

@@ -1,0 +1,702 @@
+// Host driver and C ABI of the stage update (declared in include/fx.h).
+//
+// fx_grid_create builds, in FP64 on the host, the 1-d reconstruction/divergence tables of every
+// direction from the coordinate moments <(x - x_c)^j> of each cell (Sec. 5.1, Eq. 14), the group
+// edges and the Planck-series coefficients.  The caller provides all device memory (the
+// workspace) at fx_bind_workspace; the library never allocates device memory itself.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fx.h"
+#include "fx_launch.h"
+
+using namespace fx;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// -------------------------------------------------------------------------------------------
+// Coordinate moments of one cell, normalised: m_j = Int xi^j w dx / Int w dx, xi = x - x_c,
+// for the 1-d volume weight w of a direction (Cartesian 1; spherical r: r^2 dr/dx1; theta:
+// |sin theta|).  Closed-form series on the symmetric interval [-h/2, h/2].
+// -------------------------------------------------------------------------------------------
+// S_m = Int_{-h/2}^{h/2} xi^m dxi
+double sym_power_integral(int m, double h) {
+  if (m % 2) return 0.0;
+  return 2.0 * std::pow(0.5 * h, m + 1) / (m + 1);
+}
+
+struct Moments { double w0, m1, m2; };
+
+// weight exp(a xi) (times a constant): Int xi^j e^{a xi} = sum_k a^k/k! S_{j+k}
+Moments moments_exp(double a, double h) {
+  double M[3] = {0, 0, 0};
+  for (int j = 0; j < 3; ++j) {
+    double term = 1.0, s = 0.0;
+    for (int k = 0; k < 60; ++k) {
+      if (k > 0) term *= a / k;
+      s += term * sym_power_integral(j + k, h);
+    }
+    M[j] = s;
+  }
+  return {M[0], M[1] / M[0], M[2] / M[0]};
+}
+// weight (x_c + xi)^2 (identity radial map)
+Moments moments_r2(double xc, double h) {
+  double M[3];
+  for (int j = 0; j < 3; ++j)
+    M[j] = xc * xc * sym_power_integral(j, h) + 2.0 * xc * sym_power_integral(j + 1, h) +
+           sym_power_integral(j + 2, h);
+  return {std::fabs(M[0]), M[1] / M[0], M[2] / M[0]};
+}
+// weight sin(theta_c + xi) = sin(theta_c) cos(xi) + cos(theta_c) sin(xi); the sign of the weight
+// is constant on every cell (ghost cells beyond the axis mirror it), so normalised moments follow
+Moments moments_sin(double tc, double h) {
+  double M[3];
+  for (int j = 0; j < 3; ++j) {
+    double c = 0.0, s = 0.0, fc = 1.0, fs = 1.0;
+    for (int k = 0; k < 30; ++k) {
+      if (k > 0) { fc /= (2.0 * k - 1.0) * (2.0 * k); }
+      fs = fc / (2.0 * k + 1.0);
+      double sg = (k % 2) ? -1.0 : 1.0;
+      c += sg * fc * sym_power_integral(j + 2 * k, h);
+      s += sg * fs * sym_power_integral(j + 2 * k + 1, h);
+    }
+    M[j] = std::sin(tc) * c + std::cos(tc) * s;
+  }
+  return {std::fabs(M[0]), M[1] / M[0], M[2] / M[0]};
+}
+
+// 3x3 solve A^T y = e (returns the row vector e^T A^{-1}), Gaussian elimination with pivoting.
+void solve_row(const double A[3][3], const double e[3], double y[3]) {
+  double M[3][4];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) M[r][c] = A[c][r];
+    M[r][3] = e[r];
+  }
+  for (int c = 0; c < 3; ++c) {
+    int p = c;
+    for (int r = c + 1; r < 3; ++r) if (std::fabs(M[r][c]) > std::fabs(M[p][c])) p = r;
+    for (int q = 0; q < 4; ++q) std::swap(M[p][q], M[c][q]);
+    for (int r = 0; r < 3; ++r) {
+      if (r == c) continue;
+      double f = M[r][c] / M[c][c];
+      for (int q = c; q < 4; ++q) M[r][q] -= f * M[c][q];
+    }
+  }
+  for (int r = 0; r < 3; ++r) y[r] = M[r][3] / M[r][r];
+}
+
+}  // namespace
+
+struct fx_grid {
+  fx_params P{};
+  DevGrid dg{};
+  int D = 0, G = 0, GP = 0, NV = 0;
+  int64_t ncell = 0;
+  std::vector<double> tab[3];  // [NTAB][n+4] per direction (FP64 master copy)
+  GroupConst gc{};
+  PlanckParams pk{};
+  // workspace layout (byte offsets)
+  size_t ws_bytes = 0, off_status = 0, off_tab[3] = {0, 0, 0}, off_gc = 0, off_A = 0, off_B = 0,
+         off_tot = 0;
+  size_t state_bytes = 0, elem = 8;
+  unsigned char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  int chunk = 32;
+  fx_status sticky = FX_OK;
+  std::string err;
+  unsigned* h_status = nullptr;  // pinned
+};
+
+namespace {
+
+fx_status fail(fx_grid* h, fx_status s, const std::string& msg) {
+  if (h) {
+    if (h->sticky == FX_OK) h->sticky = s;
+    h->err = msg;
+  }
+  return s;
+}
+fx_status cuda_fail(fx_grid* h, cudaError_t e, const char* where) {
+  return fail(h, FX_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool half_integer(double x) { return std::fabs(2.0 * x - std::round(2.0 * x)) < 1e-12; }
+
+// Radial map r(x1) and its derivative.
+double rmap(int map1, double x) { return map1 == FX_MAP_EXP ? std::exp(x) : x; }
+double drmap(int map1, double x) { return map1 == FX_MAP_EXP ? std::exp(x) : 1.0; }
+
+Moments cell_moments(const fx_params& P, int d, double xc, double h) {
+  if (P.geom == FX_CART || d >= 2) return {h, 0.0, h * h / 12.0};
+  if (d == 0) {
+    if (P.map1 == FX_MAP_EXP) {
+      Moments m = moments_exp(3.0, h);
+      m.w0 *= std::exp(3.0 * xc);
+      return m;
+    }
+    return moments_r2(xc, h);
+  }
+  return moments_sin(xc, h);
+}
+
+// Build the reconstruction/divergence table of direction d (padded cells -2 .. n+1).
+void build_table(const fx_params& P, int d, std::vector<double>& T) {
+  const int n = (int)P.n[d], np = n + 4;
+  const double h = (P.x_hi[d] - P.x_lo[d]) / n;
+  T.assign((size_t)NTAB * np, 0.0);
+  std::vector<Moments> mo(np + 2);
+  std::vector<double> xc(np + 2);
+  for (int i = -1; i <= np; ++i) {  // one extra cell on each side for the stencil of ghosts
+    double c = P.x_lo[d] + (i - 2 + 0.5) * h;
+    xc[i + 1] = c;
+    mo[i + 1] = cell_moments(P, d, c, h);
+  }
+  auto put = [&](int e, int ip, double v) { T[(size_t)e * np + ip] = v; };
+  for (int ip = 0; ip < np; ++ip) {
+    // moments of cells ip-1, ip, ip+1 in the frame of cell ip (scaled by h)
+    double mu1[3], mu2[3];
+    for (int k = -1; k <= 1; ++k) {
+      const Moments& m = mo[ip + 1 + k];
+      double s = (xc[ip + 1 + k] - xc[ip + 1]) / h;
+      double a1 = m.m1 / h, a2 = m.m2 / (h * h);
+      mu1[k + 1] = s + a1;
+      mu2[k + 1] = s * s + 2.0 * s * a1 + a2;
+    }
+    const double xl = -0.5, xr = 0.5;  // faces in units of h
+    // system 1 (Eq. 15): face values as weights of the three averages
+    double A1[3][3];
+    for (int k = 0; k < 3; ++k) { A1[k][0] = 1.0; A1[k][1] = mu1[k]; A1[k][2] = mu2[k]; }
+    double el[3] = {1.0, xl, xl * xl}, er[3] = {1.0, xr, xr * xr}, w[3];
+    solve_row(A1, el, w);
+    put(T_WA0, ip, w[0]); put(T_WA1, ip, w[1]); put(T_WA2, ip, w[2]);
+    solve_row(A1, er, w);
+    put(T_WB0, ip, w[0]); put(T_WB1, ip, w[1]); put(T_WB2, ip, w[2]);
+    // face-interval reset (R2)
+    double sL = (xl - mu1[0]) / (mu1[1] - mu1[0]);
+    double sR = (xr - mu1[1]) / (mu1[2] - mu1[1]);
+    put(T_SL2, ip, sL * sL); put(T_TL2, ip, (1.0 - sL) * (1.0 - sL));
+    put(T_SR2, ip, sR * sR); put(T_TR2, ip, (1.0 - sR) * (1.0 - sR));
+    // system 2 (Eq. 16): end slopes as weights of (a, mean, b)
+    double A2[3][3] = {{1.0, xl, xl * xl}, {1.0, mu1[1], mu2[1]}, {1.0, xr, xr * xr}};
+    double dl[3] = {0.0, 1.0, 2.0 * xl}, dr[3] = {0.0, 1.0, 2.0 * xr};
+    solve_row(A2, dl, w);
+    put(T_AL0, ip, w[0]); put(T_AL1, ip, w[1]); put(T_AL2, ip, w[2]);
+    solve_row(A2, dr, w);
+    put(T_AR0, ip, w[0]); put(T_AR1, ip, w[1]); put(T_AR2, ip, w[2]);
+    double M2L = mu2[1] - 2.0 * xl * mu1[1] + xl * xl;
+    double M2R = mu2[1] - 2.0 * xr * mu1[1] + xr * xr;
+    put(T_RHL, ip, 1.0 / M2L);  // w^2 = 1 in units of h
+    put(T_RHR, ip, 1.0 / M2R);
+    // linear MC on centroid gaps (absolute units)
+    put(T_IL, ip, 1.0 / (h * (mu1[1] - mu1[0])));
+    put(T_IR, ip, 1.0 / (h * (mu1[2] - mu1[1])));
+    put(T_IC, ip, 1.0 / (h * (mu1[2] - mu1[0])));
+    put(T_DL, ip, h * (xl - mu1[1]));
+    put(T_DR, ip, h * (xr - mu1[1]));
+    // divergence factors and the optical-depth length of the lower face (Cartesian)
+    put(T_FL, ip, 1.0 / h);
+    put(T_FR, ip, 1.0 / h);
+    put(T_ELL, ip, h * (mu1[1] - mu1[0]));
+    put(T_VOL, ip, mo[ip + 1].w0);
+  }
+}
+
+// Bernoulli numbers over factorials b_k = B_k/k! from the generating function t/(e^t - 1):
+// sum_{j=0}^{k} b_j / (k+1-j)! = 0 for k >= 1.
+void planck_coefficients(PlanckParams& pk) {
+  const int K = 2 * NPLANCK_LO + 2;
+  std::vector<double> b(K + 1, 0.0), ifact(K + 3, 1.0);
+  for (int i = 1; i <= K + 2; ++i) ifact[i] = ifact[i - 1] / i;
+  b[0] = 1.0;
+  for (int k = 1; k <= K; ++k) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += b[j] * ifact[k + 1 - j];
+    b[k] = -s;  // the j = k term has coefficient 1/1!
+  }
+  for (int m = 1; m <= NPLANCK_LO; ++m) {
+    pk.c64.lo[m - 1] = b[2 * m] / (2.0 * m + 3.0);
+    pk.c64.wd[m - 1] = b[2 * m];
+  }
+  for (int m = 1; m <= NPLANCK_LO32; ++m) {
+    pk.lo32[m - 1] = (float)pk.c64.lo[m - 1];
+    pk.wd32[m - 1] = (float)pk.c64.wd[m - 1];
+  }
+}
+
+template <class R> const R* dev_tab(const fx_grid* h, int d) {
+  return reinterpret_cast<const R*>(h->ws + h->off_tab[d]);
+}
+
+// ------------------------------------------------------------------ helper kernels
+template <class R>
+__global__ void k_init_equilibrium(const double* prim, R* out, DevGrid g, const GroupConst* gcp,
+                                   const R* tab0, const R* tab1, PlanckParams pk, int geom) {
+  const int64_t ncell = g.ncell;
+  const int G = g.G, D = g.D, NG = 2 + D;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ncell * (G + 1)) return;
+  int64_t c = t / (G + 1);
+  int j = (int)(t % (G + 1));
+  double rho = prim[c], p = prim[ncell + c], Tr = prim[(int64_t)(2 + D) * ncell + c];
+  if (j == G) {  // gas of this cell
+    double ke = 0.0;
+    out[c] = (R)rho;
+    for (int q = 0; q < D; ++q) {
+      double vh = prim[(int64_t)(2 + q) * ncell + c];
+      out[(int64_t)(1 + q) * ncell + c] = (R)(rho * vh);
+      ke += 0.5 * rho * vh * vh;
+    }
+    out[(int64_t)(NG - 1) * ncell + c] = (R)(p / (g.gamma - 1.0) + ke);
+    return;
+  }
+  const GroupConst& gc = *gcp;
+  double invT = 1.0 / Tr;
+  PlanckEdge<double> lo = planck_edge64(gc.edge[j] * invT, pk.c64);
+  PlanckEdge<double> hi = planck_edge64(gc.edge[j + 1] * invT, pk.c64);
+  double B = g.a_rad * 0.15398973382026502 * Tr * Tr * Tr * Tr * planck_band(lo, hi);
+  out[(int64_t)NG * ncell + c * G + j] = (R)B;
+  for (int q = 0; q < D; ++q) out[(int64_t)NG * ncell + ((int64_t)(1 + q) * ncell + c) * G + j] = R(0);
+  (void)tab0; (void)tab1; (void)geom;
+}
+
+template <class S, class T>
+__global__ void k_convert(const S* in, T* out, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (T)in[i];
+}
+
+// Neumaier pair
+struct KS { double s, c; };
+__device__ __forceinline__ void ks_add(KS& a, double x) {
+  double t = a.s + x;
+  if (fabs(a.s) >= fabs(x)) a.c += (a.s - t) + x; else a.c += (x - t) + a.s;
+  a.s = t;
+}
+__device__ __forceinline__ void ks_merge(KS& a, const KS& b) {
+  ks_add(a, b.s);
+  a.c += b.c;
+}
+
+constexpr int TOT_BLOCKS = 512, TOT_THREADS = 256;
+
+template <class R>
+__global__ void __launch_bounds__(TOT_THREADS)
+k_totals_partial(const R* U, DevGrid g, const double* vol0, const double* vol1, const double* vol2,
+                 double* part) {
+  const int64_t ncell = g.ncell;
+  const int G = g.G, D = g.D, NG = 2 + D;
+  const double ic2 = 1.0 / (g.c * g.c);
+  KS acc[FX_NTOTALS];
+  for (int q = 0; q < FX_NTOTALS; ++q) acc[q] = {0.0, 0.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int ix = (int)(c % g.n[0]);
+    int iy = (int)((c / g.n[0]) % g.n[1]);
+    int iz = (int)(c / ((int64_t)g.n[0] * g.n[1]));
+    double V = vol0[ix + 2] * (D > 1 ? vol1[iy + 2] : 1.0) * (D > 2 ? vol2[iz + 2] : 1.0);
+    double Es = 0.0, Fs[3] = {0.0, 0.0, 0.0};
+    const R* E = U + (int64_t)NG * ncell + c * G;
+    for (int j = 0; j < G; ++j) Es += (double)E[j];
+    for (int q = 0; q < D; ++q) {
+      const R* F = U + (int64_t)NG * ncell + ((int64_t)(1 + q) * ncell + c) * G;
+      for (int j = 0; j < G; ++j) Fs[q] += (double)F[j];
+    }
+    ks_add(acc[0], V * (double)U[c]);
+    for (int q = 0; q < D; ++q) ks_add(acc[1 + q], V * ((double)U[(int64_t)(1 + q) * ncell + c] + Fs[q] * ic2));
+    ks_add(acc[4], V * ((double)U[(int64_t)(NG - 1) * ncell + c] + Es));
+    ks_add(acc[5], V * Es);
+  }
+  __shared__ KS sh[TOT_THREADS];
+  for (int q = 0; q < FX_NTOTALS; ++q) {
+    sh[threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int s = TOT_THREADS / 2; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) ks_merge(sh[threadIdx.x], sh[threadIdx.x + s]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      part[(blockIdx.x * FX_NTOTALS + q) * 2 + 0] = sh[0].s;
+      part[(blockIdx.x * FX_NTOTALS + q) * 2 + 1] = sh[0].c;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_totals_final(const double* part, int nblocks, double* out) {
+  int q = threadIdx.x;
+  if (q >= FX_NTOTALS) return;
+  KS a = {0.0, 0.0};
+  for (int b = 0; b < nblocks; ++b) {
+    KS p = {part[(b * FX_NTOTALS + q) * 2 + 0], part[(b * FX_NTOTALS + q) * 2 + 1]};
+    ks_merge(a, p);
+  }
+  out[q] = a.s + a.c;
+}
+
+bool has_ws(fx_grid* h) { return h && h->ws; }
+
+template <class R>
+fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
+  StageArgs<R> a{};
+  a.g = h->dg;
+  for (int d = 0; d < 3; ++d) a.tab[d] = dev_tab<R>(h, d < h->D ? d : 0);
+  a.gc = reinterpret_cast<const GroupConst*>(h->ws + h->off_gc);
+  a.pk = h->pk;
+  a.status = reinterpret_cast<unsigned*>(h->ws + h->off_status);
+  a.chunk = h->chunk;
+  a.dt = dt;
+  R* A = reinterpret_cast<R*>(h->ws + h->off_A);
+  R* B = reinterpret_cast<R*>(h->ws + h->off_B);
+  for (int s = 0; s < nsteps; ++s) {
+    // stage 1: U1 = U0 + dt L(U0), then the interaction with dt
+    a.in = A; a.base = nullptr; a.out = B; a.dts = dt; a.alpha = 0.0;
+    cudaError_t e;
+    switch (h->D) {
+      case 1: e = launch_stage<R, 1>(a, h->GP, h->stream); break;
+      case 2: e = launch_stage<R, 2>(a, h->GP, h->stream); break;
+      default: e = launch_stage<R, 3>(a, h->GP, h->stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "stage 1 launch");
+    // stage 2: U = U0/2 + (U1 + dt L(U1))/2, then the interaction with dt/2 (reading R10)
+    a.in = B; a.base = A; a.out = A; a.dts = 0.5 * dt; a.alpha = 0.5;
+    switch (h->D) {
+      case 1: e = launch_stage<R, 1>(a, h->GP, h->stream); break;
+      case 2: e = launch_stage<R, 2>(a, h->GP, h->stream); break;
+      default: e = launch_stage<R, 3>(a, h->GP, h->stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "stage 2 launch");
+  }
+  return FX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspace_bytes) {
+  if (out) *out = nullptr;
+  if (!params || !out || !workspace_bytes) return FX_ERR_ARG;
+  const fx_params& P = *params;
+  if (P.dims < 1 || P.dims > 3) return FX_ERR_ARG;
+  if (P.ngroups < 1 || P.ngroups > MAXG) return FX_ERR_UNSUPPORTED;
+  for (int d = 0; d < P.dims; ++d) {
+    if (P.n[d] < 4 || P.n[d] > (int64_t)1 << 30) return FX_ERR_ARG;
+    if (!(P.x_hi[d] > P.x_lo[d])) return FX_ERR_ARG;
+    for (int s = 0; s < 2; ++s) {
+      int bc = s ? P.bc_hi[d] : P.bc_lo[d];
+      if (bc < FX_OUTFLOW || bc > FX_AXIS) return FX_ERR_ARG;
+    }
+    if ((P.bc_lo[d] == FX_PERIODIC) != (P.bc_hi[d] == FX_PERIODIC)) return FX_ERR_ARG;
+  }
+  if (P.geom != FX_CART) return FX_ERR_UNSUPPORTED;  // spherical geometry: not in this build yet
+  if (P.precision != FX_FP64 && P.precision != FX_FP32) return FX_ERR_ARG;
+  if (P.rad_recon_order != 1) return FX_ERR_UNSUPPORTED;
+  if (!(P.gamma > 1.0) || !(P.c_light > 0.0) || !(P.a_rad > 0.0)) return FX_ERR_ARG;
+  if (!half_integer(P.kap_rho_exp) || !half_integer(P.kap_T_exp)) return FX_ERR_UNSUPPORTED;
+  if (!(P.eps_min > 0.0) || !(P.eps_max > P.eps_min)) return FX_ERR_ARG;
+  if (P.newton_maxit < 1 || P.bisect_maxit < 0 || !(P.newton_rtol > 0.0)) return FX_ERR_ARG;
+  if (!(P.rho_floor > 0.0) || !(P.p_floor > 0.0) || !(P.E_floor > 0.0)) return FX_ERR_ARG;
+  {
+    const int GP = P.ngroups <= 8 ? 8 : (P.ngroups <= 16 ? 16 : 32);
+    size_t smem = 0;
+    if (P.precision == FX_FP64)
+      smem = P.dims == 1 ? stage_smem<double, 1>(GP, P.ngroups)
+           : P.dims == 2 ? stage_smem<double, 2>(GP, P.ngroups) : stage_smem<double, 3>(GP, P.ngroups);
+    else
+      smem = P.dims == 1 ? stage_smem<float, 1>(GP, P.ngroups)
+           : P.dims == 2 ? stage_smem<float, 2>(GP, P.ngroups) : stage_smem<float, 3>(GP, P.ngroups);
+    if (smem > 227 * 1024) return FX_ERR_UNSUPPORTED;  // per-block shared memory of sm_103a
+  }
+
+  fx_grid* h = new fx_grid();
+  h->P = P;
+  h->D = P.dims;
+  h->G = P.ngroups;
+  h->GP = P.ngroups <= 8 ? 8 : (P.ngroups <= 16 ? 16 : 32);
+  h->NV = 2 + P.dims + P.ngroups * (1 + P.dims);
+  h->ncell = 1;
+  for (int d = 0; d < P.dims; ++d) h->ncell *= P.n[d];
+  h->elem = P.precision == FX_FP64 ? 8 : 4;
+
+  DevGrid& g = h->dg;
+  g.D = P.dims;
+  g.G = P.ngroups;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = d < P.dims ? (int)P.n[d] : 1;
+    g.bc_lo[d] = d < P.dims ? P.bc_lo[d] : FX_PERIODIC;
+    g.bc_hi[d] = d < P.dims ? P.bc_hi[d] : FX_PERIODIC;
+  }
+  g.geom = P.geom;
+  g.ncell = h->ncell;
+  g.gamma = P.gamma;
+  g.c = P.c_light;
+  g.a_rad = P.a_rad;
+  g.kappa0 = P.kappa0;
+  g.sigma0 = P.sigma0;
+  g.kap_rho_h = (int)std::lround(2.0 * P.kap_rho_exp);
+  g.kap_T_h = (int)std::lround(2.0 * P.kap_T_exp);
+  g.rho_floor = P.rho_floor;
+  g.p_floor = P.p_floor;
+  g.E_floor = P.E_floor;
+  g.newton_maxit = P.newton_maxit;
+  g.bisect_maxit = P.bisect_maxit;
+  g.newton_rtol = P.newton_rtol;
+  g.couple = P.couple;
+
+  for (int d = 0; d < P.dims; ++d) build_table(P, d, h->tab[d]);
+  for (int j = 0; j <= h->G; ++j)
+    h->gc.edge[j] = P.eps_min * std::pow(P.eps_max / P.eps_min, (double)j / h->G);
+  for (int j = 0; j < h->G; ++j)
+    h->gc.efac[j] = std::pow(std::sqrt(h->gc.edge[j] * h->gc.edge[j + 1]), P.kap_eps_exp);
+  planck_coefficients(h->pk);
+
+  // chunk length along the march axis
+  if (P.dims >= 2) {
+    int nm = (int)P.n[P.dims - 1];
+    h->chunk = std::min(nm, 32);
+  }
+  // workspace layout
+  size_t off = 0;
+  h->off_status = off; off = align_up(off + 64);
+  for (int d = 0; d < P.dims; ++d) { h->off_tab[d] = off; off = align_up(off + h->tab[d].size() * h->elem); }
+  h->off_gc = off; off = align_up(off + sizeof(GroupConst));
+  h->state_bytes = (size_t)h->ncell * h->NV * h->elem;
+  h->off_A = off; off = align_up(off + h->state_bytes);
+  h->off_B = off; off = align_up(off + h->state_bytes);
+  h->off_tot = off; off = align_up(off + (size_t)(TOT_BLOCKS * FX_NTOTALS * 2 + FX_NTOTALS) * sizeof(double));
+  size_t vol_bytes = 0;
+  for (int d = 0; d < P.dims; ++d) vol_bytes += align_up((size_t)(P.n[d] + 4) * sizeof(double));
+  off += vol_bytes;
+  h->ws_bytes = off;
+  *workspace_bytes = off;
+  *out = h;
+  return FX_OK;
+}
+
+size_t fx_state_elems(const fx_grid* h) { return h ? (size_t)h->ncell * h->NV : 0; }
+
+int fx_launches_per_step(const fx_grid* h) { return h ? 2 : 0; }
+
+fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_stream) {
+  if (!h) return FX_ERR_ARG;
+  if (!dev_ptr || bytes < h->ws_bytes || (reinterpret_cast<uintptr_t>(dev_ptr) % kAlign) != 0)
+    return fail(h, FX_ERR_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
+  h->ws = static_cast<unsigned char*>(dev_ptr);
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e;
+  if (!h->h_status) {
+    e = cudaMallocHost(&h->h_status, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(h, e, "pinned status word");
+  }
+  e = cudaMemsetAsync(h->ws + h->off_status, 0, 64, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
+  for (int d = 0; d < h->D; ++d) {
+    const std::vector<double>& T = h->tab[d];
+    if (h->elem == 8) {
+      e = cudaMemcpyAsync(h->ws + h->off_tab[d], T.data(), T.size() * 8, cudaMemcpyHostToDevice, h->stream);
+    } else {
+      std::vector<float> f(T.begin(), T.end());
+      e = cudaMemcpyAsync(h->ws + h->off_tab[d], f.data(), f.size() * 4, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "table upload");
+  }
+  // FP64 cell volumes for the totals (after the totals scratch)
+  size_t off = h->off_tot + align_up((size_t)(TOT_BLOCKS * FX_NTOTALS * 2 + FX_NTOTALS) * sizeof(double));
+  std::vector<double> vol;
+  for (int d = 0; d < h->D; ++d) {
+    const int np = (int)h->P.n[d] + 4;
+    vol.assign(h->tab[d].begin() + (size_t)T_VOL * np, h->tab[d].begin() + (size_t)(T_VOL + 1) * np);
+    e = cudaMemcpyAsync(h->ws + off, vol.data(), np * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "volume upload");
+    off += align_up((size_t)np * sizeof(double));
+  }
+  e = cudaMemcpyAsync(h->ws + h->off_gc, &h->gc, sizeof(GroupConst), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "group constants upload");
+  return FX_OK;
+}
+
+fx_status fx_state_upload(fx_grid* h, const void* src, int src_precision, int src_is_device) {
+  if (!h || !src) return FX_ERR_ARG;
+  if (h->sticky != FX_OK) return h->sticky;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  const int64_t n = (int64_t)h->ncell * h->NV;
+  void* dst = h->ws + h->off_A;
+  const int my = h->P.precision;
+  cudaError_t e = cudaSuccess;
+  if (src_precision == my) {
+    e = cudaMemcpyAsync(dst, src, h->state_bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+    if (!src_is_device && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  } else if (!src_is_device) {
+    if (my == FX_FP32) {
+      std::vector<float> f((const double*)src, (const double*)src + n);
+      e = cudaMemcpyAsync(dst, f.data(), n * 4, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    } else {
+      std::vector<double> f((const float*)src, (const float*)src + n);
+      e = cudaMemcpyAsync(dst, f.data(), n * 8, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+  } else {
+    int nb = (int)((n + 255) / 256);
+    if (my == FX_FP32) k_convert<double, float><<<nb, 256, 0, h->stream>>>((const double*)src, (float*)dst, n);
+    else k_convert<float, double><<<nb, 256, 0, h->stream>>>((const float*)src, (double*)dst, n);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "state upload");
+  return FX_OK;
+}
+
+fx_status fx_state_init_equilibrium(fx_grid* h, const double* prim, int prim_is_device) {
+  if (!h || !prim) return FX_ERR_ARG;
+  if (h->sticky != FX_OK) return h->sticky;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  const int D = h->D;
+  const size_t pbytes = (size_t)(3 + D) * h->ncell * sizeof(double);
+  const double* dprim = prim;
+  cudaError_t e;
+  if (!prim_is_device) {
+    // stage the primitives in the second state buffer (free between steps)
+    if (pbytes > h->state_bytes) return fail(h, FX_ERR_UNSUPPORTED, "primitives do not fit the scratch buffer; pass a device pointer");
+    e = cudaMemcpyAsync(h->ws + h->off_B, prim, pbytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "primitive upload");
+    dprim = reinterpret_cast<const double*>(h->ws + h->off_B);
+  }
+  const int64_t nt = h->ncell * (h->G + 1);
+  const int nb = (int)((nt + 255) / 256);
+  const GroupConst* gc = reinterpret_cast<const GroupConst*>(h->ws + h->off_gc);
+  if (h->elem == 8)
+    k_init_equilibrium<double><<<nb, 256, 0, h->stream>>>(dprim, (double*)(h->ws + h->off_A), h->dg, gc,
+                                                          nullptr, nullptr, h->pk, h->P.geom);
+  else
+    k_init_equilibrium<float><<<nb, 256, 0, h->stream>>>(dprim, (float*)(h->ws + h->off_A), h->dg, gc,
+                                                         nullptr, nullptr, h->pk, h->P.geom);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && !prim_is_device) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "equilibrium initialisation");
+  return FX_OK;
+}
+
+fx_status fx_step(fx_grid* h, double dt, int nsteps) {
+  if (!h) return FX_ERR_ARG;
+  if (h->sticky != FX_OK) return h->sticky;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  if (!(dt > 0.0) || nsteps < 0) return fail(h, FX_ERR_ARG, "dt must be > 0 and nsteps >= 0");
+  return h->elem == 8 ? enqueue_steps<double>(h, dt, nsteps) : enqueue_steps<float>(h, dt, nsteps);
+}
+
+fx_status fx_sync(fx_grid* h) {
+  if (!h) return FX_ERR_ARG;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  cudaError_t e = cudaMemcpyAsync(h->h_status, h->ws + h->off_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "synchronise");
+  unsigned s = *h->h_status;
+  if (s & ST_NONFINITE) return fail(h, FX_ERR_NONFINITE, "non-finite value in the state");
+  if (s & ST_NEWTON) return fail(h, FX_ERR_NEWTON, "coupling Newton/bisection did not converge");
+  if (s & ST_FLOOR) return fail(h, FX_ERR_FLOOR, "a density, pressure or radiation floor was applied");
+  return h->sticky;
+}
+
+fx_status fx_conserved_totals(fx_grid* h, double out[FX_NTOTALS]) {
+  if (!h || !out) return FX_ERR_ARG;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  double* part = reinterpret_cast<double*>(h->ws + h->off_tot);
+  double* res = part + TOT_BLOCKS * FX_NTOTALS * 2;
+  size_t off = h->off_tot + align_up((size_t)(TOT_BLOCKS * FX_NTOTALS * 2 + FX_NTOTALS) * sizeof(double));
+  const double* vol[3] = {nullptr, nullptr, nullptr};
+  for (int d = 0; d < h->D; ++d) {
+    vol[d] = reinterpret_cast<const double*>(h->ws + off);
+    off += align_up((size_t)(h->P.n[d] + 4) * sizeof(double));
+  }
+  for (int d = h->D; d < 3; ++d) vol[d] = vol[0];
+  if (h->elem == 8)
+    k_totals_partial<double><<<TOT_BLOCKS, TOT_THREADS, 0, h->stream>>>((const double*)(h->ws + h->off_A), h->dg, vol[0], vol[1], vol[2], part);
+  else
+    k_totals_partial<float><<<TOT_BLOCKS, TOT_THREADS, 0, h->stream>>>((const float*)(h->ws + h->off_A), h->dg, vol[0], vol[1], vol[2], part);
+  k_totals_final<<<1, 32, 0, h->stream>>>(part, TOT_BLOCKS, res);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, FX_NTOTALS * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "totals");
+  for (int q = h->D; q < 3; ++q) out[1 + q] = 0.0;
+  return FX_OK;
+}
+
+fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is_device) {
+  if (!h || !dst) return FX_ERR_ARG;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  const int64_t n = (int64_t)h->ncell * h->NV;
+  const void* src = h->ws + h->off_A;
+  const int my = h->P.precision;
+  cudaError_t e = cudaSuccess;
+  if (dst_precision == my) {
+    e = cudaMemcpyAsync(dst, src, h->state_bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+    if (!dst_is_device && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  } else if (!dst_is_device) {
+    if (my == FX_FP32) {
+      std::vector<float> f(n);
+      e = cudaMemcpyAsync(f.data(), src, n * 4, cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      double* d = (double*)dst;
+      for (int64_t i = 0; i < n; ++i) d[i] = f[i];
+    } else {
+      std::vector<double> f(n);
+      e = cudaMemcpyAsync(f.data(), src, n * 8, cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      float* d = (float*)dst;
+      for (int64_t i = 0; i < n; ++i) d[i] = (float)f[i];
+    }
+  } else {
+    int nb = (int)((n + 255) / 256);
+    if (my == FX_FP32) k_convert<float, double><<<nb, 256, 0, h->stream>>>((const float*)src, (double*)dst, n);
+    else k_convert<double, float><<<nb, 256, 0, h->stream>>>((const double*)src, (float*)dst, n);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "state download");
+  return FX_OK;
+}
+
+const char* fx_last_error(const fx_grid* h) { return h ? h->err.c_str() : "null handle"; }
+
+void fx_clear_error(fx_grid* h) {
+  if (!h) return;
+  h->sticky = FX_OK;
+  h->err.clear();
+  if (h->ws) {
+    cudaMemsetAsync(h->ws + h->off_status, 0, 64, h->stream);
+    cudaStreamSynchronize(h->stream);
+  }
+}
+
+void fx_grid_destroy(fx_grid* h) {
+  if (!h) return;
+  if (h->h_status) cudaFreeHost(h->h_status);
+  delete h;
+}
+
+// Host-side inspection of the reconstruction table of direction d (FP64 master copy):
+// out receives NTAB * (n[d] + 4) doubles (entry-major).  Needs no GPU.
+int fx_debug_table(const fx_grid* h, int d, double* out, size_t cap) {
+  if (!h || d < 0 || d >= h->D) return -1;
+  const std::vector<double>& T = h->tab[d];
+  if (cap < T.size()) return (int)T.size();
+  std::memcpy(out, T.data(), T.size() * sizeof(double));
+  return (int)T.size();
+}
+int fx_debug_ntab(void) { return NTAB; }
+
+}  // extern "C"

@@ -1,0 +1,289 @@
+// Device building blocks of the stage update: reconstruction from precomputed 1-d geometry
+// tables, HLLC, the M1 closure, Planck group integrals and opacities.
+//
+// All functions are templated on the transport precision R (double for the plain FP64 path,
+// float for the FP32 form).  Coupling arithmetic that the FP32 form keeps in FP64 takes double.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fx_types.h"
+
+namespace fx {
+
+// ---------------------------------------------------------------------------------------------
+// Per-cell reconstruction/divergence table (one row per padded cell and direction), built on the
+// host in FP64 from the coordinate moments <x^j> of each cell (Sec. 5.1, Eq. 14).
+// ---------------------------------------------------------------------------------------------
+enum TabEntry {
+  T_WA0, T_WA1, T_WA2,  // system 1 (Eq. 15): lower-face value = WA . (p[i-1], p[i], p[i+1])
+  T_WB0, T_WB1, T_WB2,  // system 1: upper-face value
+  T_SL2, T_TL2,         // face-interval reset on (centroid i-1, centroid i): s^2 and (1-s)^2
+  T_SR2, T_TR2,         // same on (centroid i, centroid i+1)
+  T_AL0, T_AL1, T_AL2,  // system 2 (Eq. 16) slope at the lower face = AL . (a, m, b)
+  T_AR0, T_AR1, T_AR2,  // slope at the upper face
+  T_RHL, T_RHR,         // zero-slope resets: w^2/<(x-x_L)^2>, w^2/<(x-x_R)^2>
+  T_IL, T_IR, T_IC,     // linear MC: 1/(c_i - c_{i-1}), 1/(c_{i+1} - c_i), 1/(c_{i+1} - c_{i-1})
+  T_DL, T_DR,           // x_L - c_i, x_R - c_i   (c = centroid)
+  T_FL, T_FR,           // divergence factor of the lower / upper face (area / volume)
+  T_ELL,                // optical-depth length of the lower face (R9)
+  T_VOL,                // 1-d volume factor of the cell
+  NTAB
+};
+
+template <class R> struct Tab {
+  const R* p;  // [NTAB][np] for one direction, np = n + 4 (two ghost layers each side)
+  int np;
+  // rows outside the table (cells of a tile that overhang the grid; never used) are clamped so
+  // that every read stays inside the array
+  __device__ __forceinline__ R operator()(int e, int ip) const {
+    ip = ip < 0 ? 0 : (ip >= np ? np - 1 : ip);
+    return __ldg(p + e * np + ip);
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Parabolic (n = 2) reconstruction of one variable in one cell (Sec. 5.1; readings R2-R4).
+// ip: padded index of the cell (cell i -> i + 2).
+// ---------------------------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void recon_parabolic(const Tab<R>& t, int ip, R pm, R p0, R pp, R& a, R& b) {
+  R dl = p0 - pm, dr = pp - p0;
+  if (dl * dr <= R(0)) { a = p0; b = p0; return; }  // extremum of the data (R4)
+  a = t(T_WA0, ip) * pm + t(T_WA1, ip) * p0 + t(T_WA2, ip) * pp;
+  b = t(T_WB0, ip) * pm + t(T_WB1, ip) * p0 + t(T_WB2, ip) * pp;
+  // face-interval monotonicity (R2): clamp between the zero-slope values at the two centroids
+  {
+    R lo = pm + dl * t(T_SL2, ip), hi = p0 - dl * t(T_TL2, ip);
+    if (dl < R(0)) { R s = lo; lo = hi; hi = s; }
+    a = a < lo ? lo : (a > hi ? hi : a);
+  }
+  {
+    R lo = p0 + dr * t(T_SR2, ip), hi = pp - dr * t(T_TR2, ip);
+    if (dr < R(0)) { R s = lo; lo = hi; hi = s; }
+    b = b < lo ? lo : (b > hi ? hi : b);
+  }
+  // system 2 end slopes; opposite signs mean an extremum inside the cell (R3)
+  R sl = t(T_AL0, ip) * a + t(T_AL1, ip) * p0 + t(T_AL2, ip) * b;
+  R sr = t(T_AR0, ip) * a + t(T_AR1, ip) * p0 + t(T_AR2, ip) * b;
+  if (sl * sr >= R(0)) return;
+  R asl = fabs(sl), asr = fabs(sr);
+  if (asl == asr) { a = p0; b = p0; return; }
+  if (asl < asr) b = a + (p0 - a) * t(T_RHL, ip);  // zero slope at the lower face
+  else a = b + (p0 - b) * t(T_RHR, ip);            // zero slope at the upper face
+}
+
+// Linear reconstruction with the MC limiter on centroid gaps (radiation; reading R1).
+template <class R>
+__device__ __forceinline__ void recon_linear(const Tab<R>& t, int ip, R pm, R p0, R pp, R& a, R& b) {
+  R sL = (p0 - pm) * t(T_IL, ip);
+  R sR = (pp - p0) * t(T_IR, ip);
+  R s = R(0);
+  if (sL * sR > R(0)) {
+    R sC = (pp - pm) * t(T_IC, ip);
+    R m = fmin(fmin(R(2) * fabs(sL), R(2) * fabs(sR)), fabs(sC));
+    s = sC > R(0) ? m : -m;
+  }
+  a = p0 + s * t(T_DL, ip);
+  b = p0 + s * t(T_DR, ip);
+}
+
+// ---------------------------------------------------------------------------------------------
+// HLLC (Sec. 5.2; Toro, Spruce & Speares 1994 with Batten et al. 1997 / Einfeldt speed bounds,
+// reading R6).  States are primitive (rho, p, u_n, u_t1, u_t2) in the face-normal frame.
+// Output: fluxes of (rho, rho u_n, rho u_t1, rho u_t2, rho e) per unit physical area and the
+// contact speed (the particle velocity used to upwind radiation advection, Eq. 19).
+// ---------------------------------------------------------------------------------------------
+template <class R, int D>
+__device__ __forceinline__ void hllc(R gam, const R* L, const R* Rs, R* f, R& vstar) {
+  const R gm1 = gam - R(1);
+  R rl = L[0], pl = L[1], ul = L[2];
+  R rr = Rs[0], pr = Rs[1], ur = Rs[2];
+  R kl = ul * ul, kr = ur * ur;
+#pragma unroll
+  for (int q = 1; q < D; ++q) { kl += L[2 + q] * L[2 + q]; kr += Rs[2 + q] * Rs[2 + q]; }
+  R El = pl / gm1 + R(0.5) * rl * kl;
+  R Er = pr / gm1 + R(0.5) * rr * kr;
+  R al = sqrt(gam * pl / rl), ar = sqrt(gam * pr / rr);
+  R sl = sqrt(rl), sr = sqrt(rr);
+  R iw = R(1) / (sl + sr);
+  R Ht = (sl * ((El + pl) / rl) + sr * ((Er + pr) / rr)) * iw;
+  R ut = (sl * ul + sr * ur) * iw;
+  R v2 = ut * ut;
+#pragma unroll
+  for (int q = 1; q < D; ++q) { R vq = (sl * L[2 + q] + sr * Rs[2 + q]) * iw; v2 += vq * vq; }
+  R at2 = gm1 * (Ht - R(0.5) * v2);
+  R at = sqrt(at2 > R(0) ? at2 : R(0));
+  R SL = fmin(ul - al, ut - at);
+  R SR = fmax(ur + ar, ut + at);
+  R dl = rl * (SL - ul), dr = rr * (SR - ur);
+  R Ss = (pr - pl + ul * dl - ur * dr) / (dl - dr);
+  vstar = Ss;
+  if (SL >= R(0)) {
+    f[0] = rl * ul;
+    f[1] = rl * ul * ul + pl;
+#pragma unroll
+    for (int q = 1; q < D; ++q) f[1 + q] = rl * ul * L[2 + q];
+    f[1 + D] = (El + pl) * ul;
+    return;
+  }
+  if (SR < R(0)) {
+    f[0] = rr * ur;
+    f[1] = rr * ur * ur + pr;
+#pragma unroll
+    for (int q = 1; q < D; ++q) f[1 + q] = rr * ur * Rs[2 + q];
+    f[1 + D] = (Er + pr) * ur;
+    return;
+  }
+  const bool left = Ss >= R(0);
+  const R* W = left ? L : Rs;
+  R rk = W[0], pk = W[1], uk = W[2], Ek = left ? El : Er, Sk = left ? SL : SR;
+  R sku = Sk - uk;
+  R fac = rk * sku / (Sk - Ss);
+  // F* = F_k + S_k (U*_k - U_k)
+  f[0] = rk * uk + Sk * (fac - rk);
+  f[1] = rk * uk * uk + pk + Sk * (fac * Ss - rk * uk);
+#pragma unroll
+  for (int q = 1; q < D; ++q) f[1 + q] = rk * uk * W[2 + q] + Sk * (fac * W[2 + q] - rk * W[2 + q]);
+  R Es = fac * (Ek / rk + (Ss - uk) * (Ss + pk / (rk * sku)));
+  f[1 + D] = (Ek + pk) * uk + Sk * (Es - Ek);
+}
+
+// ---------------------------------------------------------------------------------------------
+// M1 closure (Levermore / Dubroca-Feugeas Eddington factor; reading R7): the row n of the
+// radiation pressure tensor P_{n q} for a state (E, physical F).
+// ---------------------------------------------------------------------------------------------
+template <class R, int D>
+__device__ __forceinline__ void m1_row(R c, R E, const R* F, int n, R* P) {
+  R F2 = F[0] * F[0];
+#pragma unroll
+  for (int q = 1; q < D; ++q) F2 += F[q] * F[q];
+  if (F2 <= R(0) || E <= R(0)) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) P[q] = q == n ? E * R(1.0 / 3.0) : R(0);
+    return;
+  }
+  R Fm = sqrt(F2);
+  R f = Fm / (c * E);
+  f = f > R(1) ? R(1) : f;
+  R f2 = f * f;
+  R chi = (R(3) + R(4) * f2) / (R(5) + R(2) * sqrt(R(4) - R(3) * f2));
+  R ca = R(0.5) * (R(1) - chi), cb = R(0.5) * (R(3) * chi - R(1));
+  R s = E * cb * F[n] / F2;
+#pragma unroll
+  for (int q = 0; q < D; ++q) P[q] = s * F[q] + (q == n ? E * ca : R(0));
+}
+
+// Full diagonal and the (0,1) entry of P, for the geometric sources of curvilinear grids.
+template <class R, int D>
+__device__ __forceinline__ void m1_full(R c, R E, const R* F, R* Pd, R& P01) {
+  R F2 = F[0] * F[0];
+#pragma unroll
+  for (int q = 1; q < D; ++q) F2 += F[q] * F[q];
+  P01 = R(0);
+  if (F2 <= R(0) || E <= R(0)) { Pd[0] = Pd[1] = Pd[2] = E * R(1.0 / 3.0); return; }
+  R f = sqrt(F2) / (c * E);
+  f = f > R(1) ? R(1) : f;
+  R f2 = f * f;
+  R chi = (R(3) + R(4) * f2) / (R(5) + R(2) * sqrt(R(4) - R(3) * f2));
+  R ca = R(0.5) * (R(1) - chi), cb = R(0.5) * (R(3) * chi - R(1));
+#pragma unroll
+  for (int q = 0; q < 3; ++q) Pd[q] = E * (ca + (q < D ? cb * F[q] * F[q] / F2 : R(0)));
+  if (D >= 2) P01 = E * cb * F[0] * F[1 < D ? 1 : 0] / F2;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Powers with half-integer exponents, evaluated with correctly rounded operations only.
+// ---------------------------------------------------------------------------------------------
+template <class R> __device__ __forceinline__ R ipow(R x, int n) {
+  R r = R(1), b = x;
+  int m = n < 0 ? -n : n;
+  while (m) { if (m & 1) r *= b; b *= b; m >>= 1; }
+  return n < 0 ? R(1) / r : r;
+}
+// x^(h/2) for integer h (exponent in halves)
+template <class R> __device__ __forceinline__ R hpow(R x, int h) {
+  if (h % 2 == 0) return ipow(x, h / 2);
+  int k = (h - 1) / 2;  // h = 2k + 1 -> x^k sqrt(x)
+  R s = sqrt(x);
+  return k >= 0 ? ipow(x, k) * s : s / ipow(x, -k);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Planck integrals per group edge.  For an edge at x = eps/T the device evaluates
+//   Q(x) = Int_0^x t^3/(e^t-1) dt   (x < XSPLIT, Bernoulli-number power series)
+//   Q(x) = Int_x^inf t^3/(e^t-1) dt (x >= XSPLIT, sum_n e^{-nx} (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4))
+// and w(x) = x^4/(e^x - 1) (for dB/dT).  A group band then combines its two edges without
+// cancelling large tails.  Coefficients b_k = B_k/k! are generated on the host.
+// ---------------------------------------------------------------------------------------------
+struct PlanckCoef {
+  double lo[NPLANCK_LO];  // b_{2m}/(2m+3), m = 1..NPLANCK_LO (D series, beyond 1/3 - x/8)
+  double wd[NPLANCK_LO];  // b_{2m}, m = 1..NPLANCK_LO (w series, beyond 1 - x/2)
+};
+
+template <class R> struct PlanckEdge { R Q, w; bool upper; };
+
+// FP64 edge evaluation (used by the FP64 path and the final FP64 coupling arithmetic).
+__device__ __forceinline__ PlanckEdge<double> planck_edge64(double x, const PlanckCoef& pc) {
+  PlanckEdge<double> e;
+  if (x < XSPLIT) {
+    double x2 = x * x, x3 = x2 * x;
+    double sd = pc.lo[NPLANCK_LO - 1], sw = pc.wd[NPLANCK_LO - 1];
+#pragma unroll
+    for (int m = NPLANCK_LO - 2; m >= 0; --m) { sd = fma(sd, x2, pc.lo[m]); sw = fma(sw, x2, pc.wd[m]); }
+    e.Q = x3 * (1.0 / 3.0 - 0.125 * x + x2 * sd);
+    e.w = x3 * (1.0 - 0.5 * x + x2 * sw);
+    e.upper = false;
+  } else {
+    double y = exp(-x), yn = y, x2 = x * x, x3 = x2 * x, s = 0.0;
+    for (int n = 1; n <= 64; ++n) {
+      double rn = 1.0 / (double)n;
+      double t = yn * rn * (x3 + rn * (3.0 * x2 + rn * (6.0 * x + 6.0 * rn)));
+      s += t;
+      if (t <= 1e-17 * s) break;
+      yn *= y;
+    }
+    e.Q = s;
+    e.w = x3 * x * y / (1.0 - y);
+    e.upper = true;
+  }
+  return e;
+}
+
+// FP32 edge evaluation (Newton iterations of the FP32 form).
+__device__ __forceinline__ PlanckEdge<float> planck_edge32(float x, const float* lo32, const float* wd32) {
+  PlanckEdge<float> e;
+  if (x < float(XSPLIT)) {
+    float x2 = x * x, x3 = x2 * x;
+    float sd = lo32[NPLANCK_LO32 - 1], sw = wd32[NPLANCK_LO32 - 1];
+#pragma unroll
+    for (int m = NPLANCK_LO32 - 2; m >= 0; --m) { sd = fmaf(sd, x2, lo32[m]); sw = fmaf(sw, x2, wd32[m]); }
+    e.Q = x3 * (1.0f / 3.0f - 0.125f * x + x2 * sd);
+    e.w = x3 * (1.0f - 0.5f * x + x2 * sw);
+    e.upper = false;
+  } else {
+    float y = __expf(-x), yn = y, x2 = x * x, x3 = x2 * x, s = 0.0f;
+    for (int n = 1; n <= 16; ++n) {
+      float rn = 1.0f / (float)n;
+      float t = yn * rn * (x3 + rn * (3.0f * x2 + rn * (6.0f * x + 6.0f * rn)));
+      s += t;
+      if (t <= 3e-8f * s) break;
+      yn *= y;
+    }
+    e.Q = s;
+    e.w = x3 * x * y / (1.0f - y);
+    e.upper = true;
+  }
+  return e;
+}
+
+// Band integral Int_{x_lo}^{x_hi} t^3/(e^t-1) dt from the two edge evaluations.
+template <class R>
+__device__ __forceinline__ R planck_band(const PlanckEdge<R>& lo, const PlanckEdge<R>& hi) {
+  const R total = R(6.4939394022668291491);  // pi^4/15
+  if (!lo.upper && !hi.upper) return hi.Q - lo.Q;
+  if (lo.upper && hi.upper) return lo.Q - hi.Q;
+  return (total - lo.Q) - hi.Q;
+}
+
+}  // namespace fx

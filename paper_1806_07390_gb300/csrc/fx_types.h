@@ -1,0 +1,36 @@
+// Internal types shared by the host driver and the kernels of the stage update.
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+
+namespace fx {
+
+constexpr int MAXG = 32;          // groups per cell handled by one lane segment
+constexpr int NPLANCK_LO = 27;    // FP64 Bernoulli-series terms (x < XSPLIT, error < 1e-17)
+constexpr int NPLANCK_LO32 = 13;  // FP32 Bernoulli-series terms (error < 1e-8)
+constexpr double XSPLIT = 3.0;    // lower/upper Planck series switch
+
+// Status bits raised by kernels (atomicOr into the workspace status word).
+enum : unsigned {
+  ST_NEWTON = 1u,     // Newton and bisection did not converge in some cell
+  ST_FLOOR = 2u,      // a floor was applied
+  ST_NONFINITE = 4u,  // a non-finite value was produced
+};
+
+// Kernel-side description of the grid (passed by value to every launch).
+struct DevGrid {
+  int D, G;
+  int n[3];          // cells per direction (1 for inactive directions)
+  int bc_lo[3], bc_hi[3];
+  int geom;
+  int64_t ncell;
+  double gamma, c, a_rad;
+  double kappa0, sigma0;
+  int kap_rho_h, kap_T_h;  // opacity exponents in halves
+  double rho_floor, p_floor, E_floor;
+  int newton_maxit, bisect_maxit;
+  double newton_rtol;
+  int couple;
+};
+
+}  // namespace fx

@@ -1,0 +1,221 @@
+"""Thin Python binding of the C ABI in include/fx.h (argument marshalling only).
+
+Every step of the stage update runs in the CUDA library libfx.so; this module only converts
+arguments, owns the torch-allocated workspace and forwards calls.  Importing it does not need a
+GPU; creating a bound Grid does, and fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from .workloads import BC_CODES, GEOM_CODES, MAP_CODES, Problem
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfx.so")
+
+FX_OK = 0
+STATUS_NAMES = {0: "FX_OK", -1: "FX_ERR_ARG", -2: "FX_ERR_CUDA", -3: "FX_ERR_WORKSPACE",
+                -4: "FX_ERR_NEWTON", -5: "FX_ERR_FLOOR", -6: "FX_ERR_NONFINITE",
+                -7: "FX_ERR_UNSUPPORTED"}
+FX_FP64, FX_FP32 = 0, 1
+NTOTALS = 6
+
+# every symbol include/fx.h declares
+EXPORTS = ["fx_grid_create", "fx_bind_workspace", "fx_state_elems", "fx_state_upload",
+           "fx_state_init_equilibrium", "fx_step", "fx_sync", "fx_conserved_totals",
+           "fx_state_download", "fx_launches_per_step", "fx_debug_table", "fx_debug_ntab",
+           "fx_last_error", "fx_clear_error", "fx_grid_destroy"]
+
+
+class FxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class FxParams(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("geom", ctypes.c_int),
+        ("map1", ctypes.c_int), ("x_lo", ctypes.c_double * 3), ("x_hi", ctypes.c_double * 3),
+        ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3), ("ngroups", ctypes.c_int),
+        ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("c_light", ctypes.c_double), ("a_rad", ctypes.c_double), ("kappa0", ctypes.c_double),
+        ("kap_rho_exp", ctypes.c_double), ("kap_T_exp", ctypes.c_double),
+        ("kap_eps_exp", ctypes.c_double), ("sigma0", ctypes.c_double), ("precision", ctypes.c_int),
+        ("rad_recon_order", ctypes.c_int), ("couple", ctypes.c_int),
+        ("newton_maxit", ctypes.c_int), ("bisect_maxit", ctypes.c_int),
+        ("newton_rtol", ctypes.c_double), ("rho_floor", ctypes.c_double),
+        ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfx.so; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing: build it with "
+                               "paper_1806_07390_gb300.build.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz, dp = ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)
+        L.fx_grid_create.argtypes = [ctypes.POINTER(FxParams), ctypes.POINTER(vp), ctypes.POINTER(sz)]
+        L.fx_bind_workspace.argtypes = [vp, vp, sz, vp]
+        L.fx_state_elems.argtypes = [vp]
+        L.fx_state_elems.restype = sz
+        L.fx_state_upload.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
+        L.fx_state_init_equilibrium.argtypes = [vp, vp, ctypes.c_int]
+        L.fx_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+        L.fx_sync.argtypes = [vp]
+        L.fx_conserved_totals.argtypes = [vp, dp]
+        L.fx_state_download.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
+        L.fx_launches_per_step.argtypes = [vp]
+        L.fx_debug_table.argtypes = [vp, ctypes.c_int, dp, sz]
+        L.fx_debug_ntab.argtypes = []
+        L.fx_last_error.argtypes = [vp]
+        L.fx_last_error.restype = ctypes.c_char_p
+        L.fx_clear_error.argtypes = [vp]
+        L.fx_grid_destroy.argtypes = [vp]
+        for f in ("fx_grid_create", "fx_bind_workspace", "fx_state_upload",
+                  "fx_state_init_equilibrium", "fx_step", "fx_sync", "fx_conserved_totals",
+                  "fx_state_download"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def params(pb: Problem) -> FxParams:
+    P = FxParams()
+    P.dims = pb.dims
+    for d in range(3):
+        P.n[d] = pb.n[d] if d < pb.dims else 1
+        P.x_lo[d], P.x_hi[d] = pb.x_lo[d], pb.x_hi[d]
+        P.bc_lo[d], P.bc_hi[d] = BC_CODES[pb.bc_lo[d]], BC_CODES[pb.bc_hi[d]]
+    P.geom, P.map1 = GEOM_CODES[pb.geom], MAP_CODES[pb.map1]
+    P.ngroups, P.eps_min, P.eps_max = pb.ngroups, pb.eps_min, pb.eps_max
+    P.gamma, P.c_light, P.a_rad = pb.gamma, pb.c_light, pb.a_rad
+    P.kappa0, P.kap_rho_exp, P.kap_T_exp = pb.kappa0, pb.kap_rho_exp, pb.kap_T_exp
+    P.kap_eps_exp, P.sigma0 = pb.kap_eps_exp, pb.sigma0
+    P.precision = FX_FP64 if pb.precision == "fp64" else FX_FP32
+    P.rad_recon_order, P.couple = pb.rad_recon_order, pb.couple
+    P.newton_maxit, P.bisect_maxit, P.newton_rtol = pb.newton_maxit, pb.bisect_maxit, pb.newton_rtol
+    P.rho_floor, P.p_floor, P.E_floor = pb.rho_floor, pb.p_floor, pb.E_floor
+    return P
+
+
+class Grid:
+    """One handle of the CUDA stage update with a torch-owned workspace on `device`."""
+
+    def __init__(self, pb: Problem, device: str = "cuda", stream=None, bind: bool = True):
+        import torch
+
+        self.pb = pb
+        self.L = lib()
+        self._P = params(pb)
+        h = ctypes.c_void_p()
+        ws = ctypes.c_size_t()
+        st = self.L.fx_grid_create(ctypes.byref(self._P), ctypes.byref(h), ctypes.byref(ws))
+        if st != FX_OK:
+            raise FxError(st, "fx_grid_create rejected the parameters")
+        self.h = h
+        self.ws_bytes = ws.value
+        self.workspace = None
+        if bind:
+            self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.workspace.device)
+            self._check(self.L.fx_bind_workspace(h, ctypes.c_void_p(self.workspace.data_ptr()),
+                                                 self.ws_bytes, ctypes.c_void_p(self.stream.cuda_stream)))
+
+    # -- helpers
+    def _check(self, st: int) -> None:
+        if st != FX_OK:
+            msg = self.L.fx_last_error(self.h).decode()
+            raise FxError(st, msg)
+
+    @property
+    def nelem(self) -> int:
+        return int(self.L.fx_state_elems(self.h))
+
+    @property
+    def np_dtype(self):
+        return np.float64 if self.pb.precision == "fp64" else np.float32
+
+    def debug_table(self, d: int) -> np.ndarray:
+        ntab = self.L.fx_debug_ntab()
+        n = ntab * (self.pb.n[d] + 4)
+        out = np.zeros(n)
+        self.L.fx_debug_table(self.h, d, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+        return out.reshape(ntab, self.pb.n[d] + 4)
+
+    # -- state
+    def init_equilibrium(self, prim) -> None:
+        import torch
+
+        if isinstance(prim, torch.Tensor):
+            assert prim.dtype == torch.float64 and prim.is_contiguous() and prim.is_cuda
+            self._check(self.L.fx_state_init_equilibrium(self.h, ctypes.c_void_p(prim.data_ptr()), 1))
+        else:
+            p = np.ascontiguousarray(prim, dtype=np.float64)
+            self._check(self.L.fx_state_init_equilibrium(self.h, p.ctypes.data_as(ctypes.c_void_p), 0))
+
+    def upload(self, state) -> None:
+        import torch
+
+        if isinstance(state, torch.Tensor):
+            assert state.is_contiguous() and state.is_cuda and state.numel() == self.nelem
+            prec = FX_FP64 if state.dtype == torch.float64 else FX_FP32
+            self._check(self.L.fx_state_upload(self.h, ctypes.c_void_p(state.data_ptr()), prec, 1))
+        else:
+            s = np.ascontiguousarray(state)
+            assert s.size == self.nelem
+            prec = FX_FP64 if s.dtype == np.float64 else FX_FP32
+            self._check(self.L.fx_state_upload(self.h, s.ctypes.data_as(ctypes.c_void_p), prec, 0))
+
+    def download(self, out=None, precision: Optional[int] = None) -> np.ndarray:
+        import torch
+
+        if isinstance(out, torch.Tensor):
+            prec = FX_FP64 if out.dtype == torch.float64 else FX_FP32
+            self._check(self.L.fx_state_download(self.h, ctypes.c_void_p(out.data_ptr()), prec, 1))
+            return out
+        prec = FX_FP64 if precision is None else precision
+        arr = np.empty(self.nelem, dtype=np.float64 if prec == FX_FP64 else np.float32)
+        self._check(self.L.fx_state_download(self.h, arr.ctypes.data_as(ctypes.c_void_p), prec, 0))
+        return arr
+
+    def step(self, dt: float, nsteps: int = 1) -> None:
+        self._check(self.L.fx_step(self.h, float(dt), int(nsteps)))
+
+    def sync(self) -> None:
+        self._check(self.L.fx_sync(self.h))
+
+    def status(self) -> int:
+        return int(self.L.fx_sync(self.h))
+
+    def totals(self) -> np.ndarray:
+        out = np.zeros(NTOTALS)
+        self._check(self.L.fx_conserved_totals(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def launches_per_step(self) -> int:
+        return int(self.L.fx_launches_per_step(self.h))
+
+    def clear_error(self) -> None:
+        self.L.fx_clear_error(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.L.fx_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

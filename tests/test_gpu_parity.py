@@ -1,0 +1,172 @@
+"""Parity of the CUDA stage update (through the C ABI) with the FP64 CPU oracle.
+
+Bar (FP64 path): relative L1 error <= 1e-10 and max-norm error <= 1e-8 per field; conserved
+totals <= 1e-13.  FP32 form: relative L1 <= 1e-5 on smooth problems and <= 1e-4 with shocks.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_07390_gb300 import workloads as W
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+FP64_L1, FP64_MAX, TOT = 1e-10, 1e-8, 1e-13
+
+
+@pytest.fixture(scope="module")
+def fxmod():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_07390_gb300 import build, fx
+    build.build()
+    return fx
+
+
+def run_gpu(fxmod, pb, prim=None, state=None, nsteps=None, dt=None):
+    g = fxmod.Grid(pb)
+    if state is not None:
+        g.upload(np.asarray(state, dtype=np.float64))
+    else:
+        g.init_equilibrium(prim)
+    g.step(pb.dt if dt is None else dt, pb.nsteps if nsteps is None else nsteps)
+    st = g.status()
+    out = g.download()
+    tot = g.totals()
+    g.close()
+    return out, st, tot
+
+
+def run_oracle(pb, prim=None, state=None, nsteps=None, dt=None):
+    s0 = oracle.init_equilibrium(pb, prim) if state is None else np.asarray(state, dtype=np.float64)
+    out, st = oracle.run(pb, s0, pb.dt if dt is None else dt, pb.nsteps if nsteps is None else nsteps,
+                         nthreads=8)
+    return out, st
+
+
+def check_totals(pb, tot_gpu, out_ref):
+    ref = oracle.totals(pb, out_ref)
+    scale = np.array([abs(ref[0]), abs(ref[0]), abs(ref[0]), abs(ref[0]), abs(ref[4]), abs(ref[5])])
+    err = np.abs(tot_gpu - ref) / scale
+    assert np.all(err[[0, 4, 5]] <= TOT), (tot_gpu, ref, err)
+
+
+def test_sod1d_full_config_fp64(fxmod):
+    # 512 cells, 12 groups, 200 steps (the 1-d workload at full size)
+    pb, prim = W.sod_1d()
+    got, st, tot = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
+    # totals of the GPU state by the library vs the oracle's on the oracle state
+    check_totals(pb, tot, ref)
+
+
+@pytest.mark.parametrize("shape,G,steps", [((40, 36), 16, 4), ((37, 70), 5, 3), ((21, 19), 20, 3),
+                                           ((33, 9), 12, 2)])
+def test_kh2d_small_fp64(fxmod, shape, G, steps):
+    # ragged tiles, several march chunks (ny > 32), all lane-segment widths (G = 5, 12, 16, 20)
+    pb, prim = W.kh_2d(nx=shape[0], ny=shape[1], ngroups=G, nsteps=steps)
+    got, st, tot = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
+    check_totals(pb, tot, ref)
+
+
+def test_blobs2d_outflow_periodic_fp64(fxmod):
+    pb, prim = W.blobs_2d(shape=(36, 34), ngroups=8, nsteps=3, precision="fp64")
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
+
+
+def test_lognormal3d_small_fp64(fxmod):
+    pb, prim = W.lognormal_3d(shape=(14, 10, 9), ngroups=12, nsteps=2, precision="fp64")
+    got, st, tot = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
+    check_totals(pb, tot, ref)
+
+
+def test_reflecting_walls_and_random_state_fp64(fxmod):
+    pb, _ = W.kh_2d(nx=20, ny=18, ngroups=6, nsteps=2)
+    pb.bc_lo = ("reflect", "outflow", "periodic")
+    pb.bc_hi = ("reflect", "reflect", "periodic")
+    pb.c_light = 12.0
+    pb.dt = 2e-4
+    s = W.random_state(pb, seed=5)
+    got, st, _ = run_gpu(fxmod, pb, state=s)
+    ref, rst = run_oracle(pb, state=s)
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
+
+
+@pytest.mark.parametrize("maker,tol", [("kh", 1e-4), ("blobs", 1e-4), ("lognormal", 1e-5)])
+def test_fp32_form_small(fxmod, maker, tol):
+    if maker == "kh":
+        pb, prim = W.kh_2d(nx=48, ny=40, ngroups=16, nsteps=4, precision="fp32")
+    elif maker == "blobs":
+        pb, prim = W.blobs_2d(shape=(40, 36), ngroups=8, nsteps=4, precision="fp32")
+    else:
+        pb, prim = W.lognormal_3d(shape=(12, 10, 9), ngroups=12, nsteps=2, precision="fp32")
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, tol)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32", 1e-4)])
+def test_kh2d_full_size_sampled_windows(fxmod, precision, tol):
+    # 1024^2 x 16 groups, one step in the benchmark's launch configuration; windows of 8x8 cells
+    # (+4 halo: the two-stage dependency radius) recomputed by the oracle
+    pb, prim = W.kh_2d(precision=precision)
+    g = fxmod.Grid(pb)
+    g.init_equilibrium(prim)
+    g.step(pb.dt, 1)
+    assert g.status() == 0
+    out = g.download()
+    g.close()
+    rng = np.random.default_rng(7)
+    starts = [(0, 0), (1016, 1016), (508, 252)] + [tuple(rng.integers(0, 1017, 2)) for _ in range(3)]
+    for start in starts:
+        sub, sprim = H.window(pb, prim, start, (8, 8), 4)
+        ref, _ = run_oracle(sub, sprim, nsteps=1)
+        r = H.gather_cells(sub, ref, H.sub_cells(sub, (8, 8), 4))
+        gcell = H.gather_cells(pb, out, H.window_cells(pb, start, (8, 8)))
+        small = W.Problem(**{**sub.__dict__, "n": (8, 8, 1)})
+        H.assert_parity(small, gcell, r, tol, FP64_MAX if precision == "fp64" else None)
+
+
+def test_nonfinite_state_is_reported(fxmod):
+    pb, prim = W.kh_2d(nx=16, ny=16, ngroups=4, nsteps=1)
+    s = oracle.init_equilibrium(pb, prim)
+    s[5] = np.nan
+    g = fxmod.Grid(pb)
+    g.upload(s)
+    g.step(pb.dt, 1)
+    assert g.status() == -6
+    g.close()
+
+
+def test_newton_failure_is_reported(fxmod):
+    # an opacity far too large for a two-iteration cap and no bisection: the status says so and
+    # the GPU stays usable
+    pb, prim = W.kh_2d(nx=16, ny=16, ngroups=4, nsteps=1)
+    pb.kappa0 = 1e9
+    pb.newton_maxit = 1
+    pb.bisect_maxit = 0
+    prim = prim.copy()
+    prim[-1] *= 3.0  # radiation far from equilibrium
+    g = fxmod.Grid(pb)
+    g.init_equilibrium(prim)
+    g.step(pb.dt, 1)
+    assert g.status() == -4
+    g.close()
+    pb2, prim2 = W.kh_2d(nx=16, ny=16, ngroups=4, nsteps=1)
+    out, st, _ = run_gpu(fxmod, pb2, prim2)
+    assert st == 0
