@@ -46,7 +46,7 @@ typedef enum {
 enum { FX_OUTFLOW = 0, FX_PERIODIC = 1, FX_REFLECT = 2, FX_AXIS = 3 }; /* Sec. 7.5 */
 enum { FX_CART = 0, FX_SPH = 1 };       /* Cartesian, or spherical (x1 -> r, x2 -> theta)  */
 enum { FX_MAP_ID = 0, FX_MAP_EXP = 1 }; /* radial map r = x1 or r = exp(x1) (Appendix A)   */
-enum { FX_FP64 = 0, FX_FP32 = 1 };      /* state/transport precision                        */
+enum { FX_FP64 = 0, FX_FP32 = 1, FX_FP32_F64NEWTON = 2 }; /* precision forms (see fx_params)  */
 enum { FX_NTOTALS = 6 };
 
 /* Grid, physics and solver parameters (plain data, copied at fx_grid_create).
@@ -62,15 +62,20 @@ enum { FX_NTOTALS = 6 };
  *   kappa0, kap_*_exp  absorption opacity kappa_g = kappa0 rho^a T^b eps_g^d with
  *                      eps_g = sqrt(edge_g edge_g+1); a and b must be multiples of 1/2.
  *   sigma0             scattering opacity sigma = sigma0 rho.
- *   precision          FX_FP64 (plain FP64 path) or FX_FP32 (FP32 state, reconstruction and
- *                      fluxes; FP64 temperature/energy bookkeeping in the coupling and FP64
- *                      conserved totals).
+ *   precision          FX_FP64: plain FP64 path.
+ *                      FX_FP32: FP32 state, reconstruction, fluxes and coupling (the Newton
+ *                      iterates on T - T^- so that FP32 resolves the change of T); FP64
+ *                      conserved totals.
+ *                      FX_FP32_F64NEWTON: as FX_FP32, but the temperature iterate, residual
+ *                      and energy/momentum bookkeeping of the coupling in FP64.
+ *                      State buffers are double for FX_FP64 and float otherwise.
  *   rad_recon_order    1 = linear + MC limiter (the paper's choice for radiation).
  *   couple             1 = apply the implicit interaction after each RK stage.
  *   newton_maxit, bisect_maxit, newton_rtol
  *                      coupling iteration caps and the relative temperature step tolerance.
  *   rho_floor, p_floor, E_floor
- *                      floors; applying one sets FX_ERR_FLOOR.
+ *                      floors; applying the density or pressure floor sets FX_ERR_FLOOR, the
+ *                      radiation-energy floor is a silent positivity floor.
  */
 typedef struct {
   int dims;

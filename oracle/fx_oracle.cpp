@@ -37,7 +37,7 @@
 //   R14 truncated Planck groups, Kirchhoff emissivity j = c kappa B.
 //   R15 volume-averaged Christoffel symbols with the pressure-balance corrections in r and theta.
 //   R16 D momentum components; T^3_3 = p enters the sources.
-//   R18 floors on rho, p, E.
+//   R18 floors on rho and p (reported) and a silent positivity floor on E_g.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -689,7 +689,7 @@ static int couple_cell(const orc_params& P, const Groups& gr, int D, const doubl
   S Esum = 0.0;
   for (int g = 0; g < G; ++g) {
     S& E = U[NG + g * NRV];
-    if (val(E) < P.E_floor) { E = P.E_floor; status |= 2; }
+    if (val(E) < P.E_floor) E = P.E_floor;  // positivity floor; tiny Wien-tail energies are physical
     Em[g] = E;
     Esum += E;
   }
@@ -838,6 +838,10 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
     int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
     net[d].assign(dU.size(), S(0.0));
     std::vector<S>& acc = net[d];
+    // rows along d are independent: each touches only its own cells
+    const int nthreads = P.nthreads > 0 ? P.nthreads : 1;
+    (void)nthreads;
+#pragma omp parallel for collapse(2) schedule(static) num_threads(nthreads) if (nthreads > 1)
     for (int b = L.ng[o2]; b < L.ng[o2] + L.n[o2]; ++b)
       for (int a = L.ng[o1]; a < L.ng[o1] + L.n[o1]; ++a) {
         // faces f = ng .. ng+n along d (lower face of padded cell f)

@@ -227,6 +227,7 @@ void planck_coefficients(PlanckParams& pk) {
     pk.c64.lo[m - 1] = b[2 * m] / (2.0 * m + 3.0);
     pk.c64.wd[m - 1] = b[2 * m];
   }
+  for (int n = 1; n <= NPLANCK_UP; ++n) pk.c64.rn[n - 1] = 1.0 / n;
   for (int m = 1; m <= NPLANCK_LO32; ++m) {
     pk.lo32[m - 1] = (float)pk.c64.lo[m - 1];
     pk.wd32[m - 1] = (float)pk.c64.wd[m - 1];
@@ -345,7 +346,35 @@ __global__ void k_totals_final(const double* part, int nblocks, double* out) {
 
 bool has_ws(fx_grid* h) { return h && h->ws; }
 
-template <class R>
+// Per-launch scalar constants, computed once in FP64 and rounded to the kernel types.
+template <class T>
+Consts<T> make_consts(const fx_grid* h, double dt, double dts, double alpha, bool fp32_newton) {
+  const fx_params& P = h->P;
+  Consts<T> k;
+  k.gamma = (T)P.gamma;
+  k.gm1 = (T)(P.gamma - 1.0);
+  k.cv = (T)(1.0 / (P.gamma - 1.0));
+  k.c = (T)P.c_light;
+  k.ic2 = (T)(1.0 / (P.c_light * P.c_light));
+  k.hc = (T)(0.5 * P.c_light);
+  k.hc2 = (T)(0.5 * P.c_light * P.c_light);
+  k.kappa0 = (T)P.kappa0;
+  k.sigma0 = (T)P.sigma0;
+  k.rho_floor = (T)P.rho_floor;
+  k.u_floor = (T)(P.p_floor / (P.gamma - 1.0));
+  k.E_floor = (T)std::max(P.E_floor, sizeof(T) == 4 ? 1e-37 : 1e-300);
+  k.aN = (T)(P.a_rad * 15.0 / std::pow(M_PI, 4));
+  k.cdts = (T)(P.c_light * dts);
+  k.dt = (T)dt;
+  k.alpha = (T)alpha;
+  k.beta = (T)(1.0 - alpha);
+  // FP32 iterates stop at FP32 resolution (the paper's own tolerance is 1e-6, Sec. 5.3)
+  k.rtol = (T)(fp32_newton ? std::max(P.newton_rtol, 2e-7) : P.newton_rtol);
+  k.atol = (T)(fp32_newton ? 1e-7 : 1e-14);
+  return k;
+}
+
+template <class R, class NT>
 fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
   StageArgs<R> a{};
   a.g = h->dg;
@@ -357,22 +386,27 @@ fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
   a.dt = dt;
   R* A = reinterpret_cast<R*>(h->ws + h->off_A);
   R* B = reinterpret_cast<R*>(h->ws + h->off_B);
+  const bool f32n = sizeof(R) == 4;  // FP32 group sums bound the attainable residual
+  const Consts<double> kd1 = make_consts<double>(h, dt, dt, 0.0, f32n);
+  const Consts<float> kf1 = make_consts<float>(h, dt, dt, 0.0, f32n);
+  const Consts<double> kd2 = make_consts<double>(h, dt, 0.5 * dt, 0.5, f32n);
+  const Consts<float> kf2 = make_consts<float>(h, dt, 0.5 * dt, 0.5, f32n);
   for (int s = 0; s < nsteps; ++s) {
     // stage 1: U1 = U0 + dt L(U0), then the interaction with dt
-    a.in = A; a.base = nullptr; a.out = B; a.dts = dt; a.alpha = 0.0;
+    a.in = A; a.base = nullptr; a.out = B; a.dts = dt; a.alpha = 0.0; a.kd = kd1; a.kf = kf1;
     cudaError_t e;
     switch (h->D) {
-      case 1: e = launch_stage<R, 1>(a, h->GP, h->stream); break;
-      case 2: e = launch_stage<R, 2>(a, h->GP, h->stream); break;
-      default: e = launch_stage<R, 3>(a, h->GP, h->stream); break;
+      case 1: e = launch_stage<R, 1, NT>(a, h->GP, h->stream); break;
+      case 2: e = launch_stage<R, 2, NT>(a, h->GP, h->stream); break;
+      default: e = launch_stage<R, 3, NT>(a, h->GP, h->stream); break;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "stage 1 launch");
     // stage 2: U = U0/2 + (U1 + dt L(U1))/2, then the interaction with dt/2 (reading R10)
-    a.in = B; a.base = A; a.out = A; a.dts = 0.5 * dt; a.alpha = 0.5;
+    a.in = B; a.base = A; a.out = A; a.dts = 0.5 * dt; a.alpha = 0.5; a.kd = kd2; a.kf = kf2;
     switch (h->D) {
-      case 1: e = launch_stage<R, 1>(a, h->GP, h->stream); break;
-      case 2: e = launch_stage<R, 2>(a, h->GP, h->stream); break;
-      default: e = launch_stage<R, 3>(a, h->GP, h->stream); break;
+      case 1: e = launch_stage<R, 1, NT>(a, h->GP, h->stream); break;
+      case 2: e = launch_stage<R, 2, NT>(a, h->GP, h->stream); break;
+      default: e = launch_stage<R, 3, NT>(a, h->GP, h->stream); break;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "stage 2 launch");
   }
@@ -399,7 +433,8 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
     if ((P.bc_lo[d] == FX_PERIODIC) != (P.bc_hi[d] == FX_PERIODIC)) return FX_ERR_ARG;
   }
   if (P.geom != FX_CART) return FX_ERR_UNSUPPORTED;  // spherical geometry: not in this build yet
-  if (P.precision != FX_FP64 && P.precision != FX_FP32) return FX_ERR_ARG;
+  if (P.precision != FX_FP64 && P.precision != FX_FP32 && P.precision != FX_FP32_F64NEWTON)
+    return FX_ERR_ARG;
   if (P.rad_recon_order != 1) return FX_ERR_UNSUPPORTED;
   if (!(P.gamma > 1.0) || !(P.c_light > 0.0) || !(P.a_rad > 0.0)) return FX_ERR_ARG;
   if (!half_integer(P.kap_rho_exp) || !half_integer(P.kap_T_exp)) return FX_ERR_UNSUPPORTED;
@@ -458,6 +493,8 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
     h->gc.edge[j] = P.eps_min * std::pow(P.eps_max / P.eps_min, (double)j / h->G);
   for (int j = 0; j < h->G; ++j)
     h->gc.efac[j] = std::pow(std::sqrt(h->gc.edge[j] * h->gc.edge[j + 1]), P.kap_eps_exp);
+  for (int j = 0; j <= MAXG; ++j) h->gc.edge32[j] = (float)h->gc.edge[j];
+  for (int j = 0; j < MAXG; ++j) h->gc.efac32[j] = (float)h->gc.efac[j];
   planck_coefficients(h->pk);
 
   // chunk length along the march axis
@@ -534,7 +571,7 @@ fx_status fx_state_upload(fx_grid* h, const void* src, int src_precision, int sr
   if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
   const int64_t n = (int64_t)h->ncell * h->NV;
   void* dst = h->ws + h->off_A;
-  const int my = h->P.precision;
+  const int my = h->elem == 8 ? FX_FP64 : FX_FP32;  // element type of the device state
   cudaError_t e = cudaSuccess;
   if (src_precision == my) {
     e = cudaMemcpyAsync(dst, src, h->state_bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
@@ -595,7 +632,9 @@ fx_status fx_step(fx_grid* h, double dt, int nsteps) {
   if (h->sticky != FX_OK) return h->sticky;
   if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
   if (!(dt > 0.0) || nsteps < 0) return fail(h, FX_ERR_ARG, "dt must be > 0 and nsteps >= 0");
-  return h->elem == 8 ? enqueue_steps<double>(h, dt, nsteps) : enqueue_steps<float>(h, dt, nsteps);
+  if (h->elem == 8) return enqueue_steps<double, double>(h, dt, nsteps);
+  if (h->P.precision == FX_FP32_F64NEWTON) return enqueue_steps<float, double>(h, dt, nsteps);
+  return enqueue_steps<float, float>(h, dt, nsteps);
 }
 
 fx_status fx_sync(fx_grid* h) {
@@ -641,7 +680,7 @@ fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is
   if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
   const int64_t n = (int64_t)h->ncell * h->NV;
   const void* src = h->ws + h->off_A;
-  const int my = h->P.precision;
+  const int my = h->elem == 8 ? FX_FP64 : FX_FP32;  // element type of the device state
   cudaError_t e = cudaSuccess;
   if (dst_precision == my) {
     e = cudaMemcpyAsync(dst, src, h->state_bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);

@@ -149,29 +149,37 @@ __device__ __forceinline__ void hllc(R gam, const R* L, const R* Rs, R* f, R& vs
   f[1 + D] = (Ek + pk) * uk + Sk * (Es - Ek);
 }
 
+// Reciprocal: IEEE division in FP64, the correctly rounded reciprocal instruction sequence in FP32.
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
+
 // ---------------------------------------------------------------------------------------------
-// M1 closure (Levermore / Dubroca-Feugeas Eddington factor; reading R7): the row n of the
-// radiation pressure tensor P_{n q} for a state (E, physical F).
+// M1 closure (Levermore / Dubroca-Feugeas Eddington factor chi(f) = (3+4f^2)/(5+2 sqrt(4-3f^2)),
+// reading R7): the row n of the radiation pressure tensor P_{nq} for a state (E, physical F).
+// With s = sqrt(4 - 3f^2) the closure's two coefficients reduce exactly to
+//   (1 - chi)/2 = 1/3 - f^2/(2+s),   (3 chi - 1)/2 = 3 f^2/(2+s),
+// so P_{nq} = E [1/3 - f^2/(2+s)] delta_{nq} + 3 F_n F_q / ((2+s) c^2 E): one reciprocal of E, one
+// square root and one reciprocal per state, and F = 0 needs no special case.
 // ---------------------------------------------------------------------------------------------
 template <class R, int D>
-__device__ __forceinline__ void m1_row(R c, R E, const R* F, int n, R* P) {
-  R F2 = F[0] * F[0];
-#pragma unroll
-  for (int q = 1; q < D; ++q) F2 += F[q] * F[q];
-  if (F2 <= R(0) || E <= R(0)) {
+__device__ __forceinline__ void m1_row(R ic2, R E, const R* F, int n, R* P) {
+  if (!(E > R(0))) {
 #pragma unroll
     for (int q = 0; q < D; ++q) P[q] = q == n ? E * R(1.0 / 3.0) : R(0);
     return;
   }
-  R Fm = sqrt(F2);
-  R f = Fm / (c * E);
-  f = f > R(1) ? R(1) : f;
-  R f2 = f * f;
-  R chi = (R(3) + R(4) * f2) / (R(5) + R(2) * sqrt(R(4) - R(3) * f2));
-  R ca = R(0.5) * (R(1) - chi), cb = R(0.5) * (R(3) * chi - R(1));
-  R s = E * cb * F[n] / F2;
+  R F2 = F[0] * F[0];
 #pragma unroll
-  for (int q = 0; q < D; ++q) P[q] = s * F[q] + (q == n ? E * ca : R(0));
+  for (int q = 1; q < D; ++q) F2 += F[q] * F[q];
+  const R iE = frcp(E);
+  R f2 = F2 * iE * iE * ic2;
+  R scale = R(1);
+  if (f2 > R(1)) { scale = frcp(f2); f2 = R(1); }  // |F| > cE: keep the direction, clamp f to 1
+  const R qd = frcp(R(2) + sqrt(R(4) - R(3) * f2));
+  const R diag = E * (R(1.0 / 3.0) - f2 * qd);
+  const R w = R(3) * qd * iE * ic2 * scale * F[n];
+#pragma unroll
+  for (int q = 0; q < D; ++q) P[q] = w * F[q] + (q == n ? diag : R(0));
 }
 
 // Full diagonal and the (0,1) entry of P, for the geometric sources of curvilinear grids.
@@ -219,6 +227,7 @@ template <class R> __device__ __forceinline__ R hpow(R x, int h) {
 struct PlanckCoef {
   double lo[NPLANCK_LO];  // b_{2m}/(2m+3), m = 1..NPLANCK_LO (D series, beyond 1/3 - x/8)
   double wd[NPLANCK_LO];  // b_{2m}, m = 1..NPLANCK_LO (w series, beyond 1 - x/2)
+  double rn[NPLANCK_UP];  // 1/n, n = 1..NPLANCK_UP (exponential series)
 };
 
 template <class R> struct PlanckEdge { R Q, w; bool upper; };
@@ -236,9 +245,10 @@ __device__ __forceinline__ PlanckEdge<double> planck_edge64(double x, const Plan
     e.upper = false;
   } else {
     double y = exp(-x), yn = y, x2 = x * x, x3 = x2 * x, s = 0.0;
-    for (int n = 1; n <= 64; ++n) {
-      double rn = 1.0 / (double)n;
-      double t = yn * rn * (x3 + rn * (3.0 * x2 + rn * (6.0 * x + 6.0 * rn)));
+    const double a2 = 3.0 * x2, a1 = 6.0 * x;
+    for (int n = 1; n <= NPLANCK_UP; ++n) {
+      const double rn = pc.rn[n - 1];
+      double t = yn * rn * (x3 + rn * (a2 + rn * (a1 + 6.0 * rn)));
       s += t;
       if (t <= 1e-17 * s) break;
       yn *= y;
@@ -263,15 +273,16 @@ __device__ __forceinline__ PlanckEdge<float> planck_edge32(float x, const float*
     e.upper = false;
   } else {
     float y = __expf(-x), yn = y, x2 = x * x, x3 = x2 * x, s = 0.0f;
+    const float a2 = 3.0f * x2, a1 = 6.0f * x;
     for (int n = 1; n <= 16; ++n) {
-      float rn = 1.0f / (float)n;
-      float t = yn * rn * (x3 + rn * (3.0f * x2 + rn * (6.0f * x + 6.0f * rn)));
+      float rn = __frcp_rn((float)n);
+      float t = yn * rn * (x3 + rn * (a2 + rn * (a1 + 6.0f * rn)));
       s += t;
       if (t <= 3e-8f * s) break;
       yn *= y;
     }
     e.Q = s;
-    e.w = x3 * x * y / (1.0f - y);
+    e.w = __fdividef(x3 * x * y, 1.0f - y);
     e.upper = true;
   }
   return e;

@@ -14,12 +14,20 @@ template <int D, int GP> struct TileShape {
   static constexpr int TY = TC / TX;
 };
 
-// Enqueue one stage.  nmarch: cells along the march axis; returns the CUDA error of the launch.
-template <class R, int D>
+// Enqueue one stage (state type R, D dimensions, Newton/bookkeeping type NT); returns the CUDA
+// error of the launch.
+template <class R, int D, class NT>
 cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s);
 
-// Dynamic shared memory the stage kernel needs for these parameters (0 if unsupported).
+// Dynamic shared memory of the stage kernel (tile shape from D and GP).
 template <class R, int D>
-size_t stage_smem(int GP, int G);
+inline size_t stage_smem(int GP, int G) {
+  switch (GP) {
+    case 8: return stage_smem_bytes<R, D, TileShape<D, 8>::TX, TileShape<D, 8>::TY>(G);
+    case 16: return stage_smem_bytes<R, D, TileShape<D, 16>::TX, TileShape<D, 16>::TY>(G);
+    case 32: return stage_smem_bytes<R, D, TileShape<D, 32>::TX, TileShape<D, 32>::TY>(G);
+    default: return 0;
+  }
+}
 
 }  // namespace fx

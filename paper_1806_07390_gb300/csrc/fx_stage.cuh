@@ -9,6 +9,8 @@
 // in registers to the next step.  Ghost cells are produced at load time from the boundary
 // conditions (Sec. 7.5), so no separate ghost-fill pass touches HBM.
 #pragma once
+#include <type_traits>
+
 #include "fx_device.cuh"
 
 namespace fx {
@@ -17,6 +19,21 @@ namespace fx {
 struct GroupConst {
   double edge[MAXG + 1];   // eps_{g-1/2}, g = 0..G
   double efac[MAXG];       // eps_g^kap_eps_exp
+  float edge32[MAXG + 1];
+  float efac32[MAXG];
+  __device__ __forceinline__ double edge_of(int j, double) const { return edge[j]; }
+  __device__ __forceinline__ float edge_of(int j, float) const { return edge32[j]; }
+  __device__ __forceinline__ double efac_of(int j, double) const { return efac[j]; }
+  __device__ __forceinline__ float efac_of(int j, float) const { return efac32[j]; }
+};
+
+// Scalar constants of one launch in the arithmetic type T (filled on the host in FP64 and
+// rounded once), so kernels never convert or divide doubles per cell.
+template <class T> struct Consts {
+  T gamma, gm1, cv, c, ic2, hc, hc2;       // gamma, gamma-1, 1/(gamma-1), c, 1/c^2, c/2, c^2/2
+  T kappa0, sigma0, rho_floor, u_floor, E_floor, aN;  // aN = a_R 15/pi^4
+  T cdts, dt, alpha, beta;                 // c * coupling step, stage step, RK weights
+  T rtol, atol;                            // coupling convergence tolerances
 };
 
 // Planck series coefficients (universal constants), passed by value in the kernel parameters.
@@ -39,6 +56,10 @@ template <class R> struct StageArgs {
   double dts;          // coupling step (dt after stage 1, dt/2 after stage 2; reading R10)
   double alpha;        // 0 (stage 1) or 1/2 (stage 2)
   int chunk;           // planes per block along the march axis
+  Consts<double> kd;
+  Consts<float> kf;
+  __device__ __forceinline__ const Consts<double>& k(double) const { return kd; }
+  __device__ __forceinline__ const Consts<float>& k(float) const { return kf; }
 };
 
 __device__ __forceinline__ int bc_pad(int i) { return i + 2; }  // padded table row of cell i
@@ -60,7 +81,7 @@ __device__ __forceinline__ int bc_map(int i, int n, int lo, int hi, bool& flip) 
   return i;
 }
 
-template <int GP> __device__ __forceinline__ double seg_sum(double v) {
+template <int GP, class V> __device__ __forceinline__ V seg_sum(V v) {
 #pragma unroll
   for (int o = GP / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, GP);
   return v;
@@ -71,180 +92,195 @@ template <int GP> __device__ __forceinline__ double seg_sum(double v) {
 // an outer Newton iteration on T (Eqs. 26-27; reading R11), energy update by conservation (R12),
 // then the flux absorption update and its momentum/energy feedback (Eqs. 28, 31, 32).
 // Executed by all GP lanes of a cell; the loop is warp-uniform so that shuffles stay converged.
+//
+// LT: type of the per-group arithmetic (Planck band, opacity, backward Euler).
+// NT: type of the temperature iterate, the residual and the energy/momentum bookkeeping.
+// The Newton variable is dl = T - T^-, with T^- = u^-/(rho c_v): the residual
+//   r = rho c_v dl + sum_g (E_g(T) - E_g^-)
+// is the paper's r_E (u^k - u^- + dE^k, Eq. 27) without the cancellation of u(T) against u^-, so
+// an FP32 iterate resolves T to FP32 precision of the change, not of T itself.
 // ---------------------------------------------------------------------------------------------
-template <class R, int D, int GP, bool F64GROUP>
+template <int GP, class LT, class NT>
 struct Coupler {
   const DevGrid& g;
-  const GroupConst& gc;
   const PlanckParams& pk;
-  int lane;       // group index of this lane
   bool has;       // lane < G
   bool top2;      // this lane also evaluates the top edge (G == GP)
-  double rho, rcv, u_m, K, Sg, dts, Em, aN;
+  NT rcv, Tm;
+  LT K, Sg, cdts, Em, aN, efac, elo, etop;
 
-  __device__ __forceinline__ void eval(double T, double& r, double& dr, double& Eg) const {
-    const int G = g.G;
-    double Tb = hpow(T, g.kap_T_h);
-    double invT = 1.0 / T;
-    double Bq, dBq, kap;
-    if (F64GROUP) {
-      double x = gc.edge[lane <= G ? lane : G] * invT;
-      PlanckEdge<double> lo = planck_edge64(x, pk.c64);
+  // residual and derivative at T = Tm + dl; this lane's E_g(T) and dE_g/dT
+  __device__ __forceinline__ void eval(NT dl, NT& r, NT& dr, LT& Eg, LT& dEg) const {
+    LT Tl = (LT)(Tm + dl);
+    LT invT = frcp(Tl);
+    LT Bq, dBq;
+    if (sizeof(LT) == 8) {
+      PlanckEdge<double> lo = planck_edge64((double)(elo * invT), pk.c64);
       PlanckEdge<double> hi;
       hi.Q = __shfl_down_sync(0xffffffffu, lo.Q, 1, GP);
       hi.w = __shfl_down_sync(0xffffffffu, lo.w, 1, GP);
       hi.upper = __shfl_down_sync(0xffffffffu, (int)lo.upper, 1, GP) != 0;
-      if (top2) hi = planck_edge64(gc.edge[G] * invT, pk.c64);
-      double I = planck_band(lo, hi);
-      double T3 = T * T * T;
-      Bq = aN * T3 * T * I;
-      dBq = aN * T3 * (4.0 * I + (lo.w - hi.w));
-      kap = K * Tb * gc.efac[has ? lane : 0];
+      if (top2) hi = planck_edge64((double)(etop * invT), pk.c64);
+      LT I = (LT)planck_band(lo, hi);
+      LT T3 = Tl * Tl * Tl;
+      Bq = aN * T3 * Tl * I;
+      dBq = aN * T3 * (LT(4) * I + (LT)(lo.w - hi.w));
     } else {
-      float invTf = (float)invT;
-      float x = (float)gc.edge[lane <= G ? lane : G] * invTf;
-      PlanckEdge<float> lo = planck_edge32(x, pk.lo32, pk.wd32);
+      PlanckEdge<float> lo = planck_edge32((float)(elo * invT), pk.lo32, pk.wd32);
       PlanckEdge<float> hi;
       hi.Q = __shfl_down_sync(0xffffffffu, lo.Q, 1, GP);
       hi.w = __shfl_down_sync(0xffffffffu, lo.w, 1, GP);
       hi.upper = __shfl_down_sync(0xffffffffu, (int)lo.upper, 1, GP) != 0;
-      if (top2) hi = planck_edge32((float)gc.edge[G] * invTf, pk.lo32, pk.wd32);
-      float I = planck_band(lo, hi);
-      float Tf = (float)T, T3 = Tf * Tf * Tf;
-      Bq = (double)((float)aN * T3 * Tf * I);
-      dBq = (double)((float)aN * T3 * (4.0f * I + (lo.w - hi.w)));
-      kap = (double)((float)K * (float)Tb * (float)gc.efac[has ? lane : 0]);
+      if (top2) hi = planck_edge32((float)(etop * invT), pk.lo32, pk.wd32);
+      LT I = (LT)planck_band(lo, hi);
+      LT T3 = Tl * Tl * Tl;
+      Bq = aN * T3 * Tl * I;
+      dBq = aN * T3 * (LT(4) * I + (LT)(lo.w - hi.w));
     }
-    double tau = g.c * dts * kap;
-    double dtau = tau * (0.5 * g.kap_T_h) * invT;
-    double inv = 1.0 / (1.0 + tau);
+    LT kap = K * hpow(Tl, g.kap_T_h) * efac;
+    LT tau = cdts * kap;
+    LT dtau = tau * (LT(0.5) * (LT)g.kap_T_h) * invT;
+    LT inv = frcp(LT(1) + tau);
     Eg = (Em + tau * Bq) * inv;
-    double dEg = (tau * dBq + dtau * (Bq - Eg)) * inv;
-    double s1 = seg_sum<GP>(has ? Eg - Em : 0.0);
-    double s2 = seg_sum<GP>(has ? dEg : 0.0);
-    r = rcv * T - u_m + s1;
-    dr = rcv + s2;
+    dEg = (tau * dBq + dtau * (Bq - Eg)) * inv;
+    LT s1 = seg_sum<GP>(has ? Eg - Em : LT(0));
+    LT s2 = seg_sum<GP>(has ? dEg : LT(0));
+    r = rcv * dl + (NT)s1;
+    dr = rcv + (NT)s2;
   }
 };
 
-template <class R, int D, int GP, bool F64GROUP>
+template <int D, int GP, class LT, class NT>
 __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupConst& gc,
-                                                const PlanckParams& pk, bool active,
-                                                int lane, const double* h, double& rho, double* m,
-                                                double& rhoe, double& E, double* F, double dts) {
+                                                const PlanckParams& pk, const Consts<NT>& kn,
+                                                const Consts<LT>& kl, bool active,
+                                                int lane, const NT* h, NT& rho, NT* m,
+                                                NT& rhoe, NT& E, NT* F) {
   const int G = g.G;
   unsigned st = 0;
-  const double cv = 1.0 / (g.gamma - 1.0);
-  if (rho < g.rho_floor) { rho = g.rho_floor; st |= ST_FLOOR; }
-  double ke = 0.0;
+  const NT cv = kn.cv;
+  if (rho < kn.rho_floor) { rho = kn.rho_floor; st |= ST_FLOOR; }
+  const NT irho = frcp(rho);
+  NT ke = NT(0);
 #pragma unroll
-  for (int q = 0; q < D; ++q) { double vh = m[q] / (rho * h[q]); ke += 0.5 * rho * vh * vh; }
-  double u_m = rhoe - ke;
-  const double u_floor = g.p_floor * cv;
-  if (u_m < u_floor) { u_m = u_floor; rhoe = ke + u_m; st |= ST_FLOOR; }
+  for (int q = 0; q < D; ++q) { NT mh = m[q] * frcp(h[q]); ke += NT(0.5) * mh * mh * irho; }
+  NT u_m = rhoe - ke;
+  if (u_m < kn.u_floor) { u_m = kn.u_floor; rhoe = ke + u_m; st |= ST_FLOOR; }
   const bool has = lane < G;
-  double Em = has ? E : 0.0;
-  if (has && Em < g.E_floor) { Em = g.E_floor; st |= ST_FLOOR; }
-  const double Esum = seg_sum<GP>(Em);
+  NT Em = has ? E : NT(0);
+  if (has && Em < kn.E_floor) Em = kn.E_floor;  // silent positivity floor (Wien tails)
+  const NT Esum = seg_sum<GP>(Em);
+  const NT rcv = rho * cv;
 
-  Coupler<R, D, GP, F64GROUP> cp{g, gc, pk, lane, has, (G == GP) && (lane == G - 1),
-                                 rho, rho * cv, u_m, g.kappa0 * hpow(rho, g.kap_rho_h),
-                                 g.sigma0 * rho, dts, Em,
-                                 g.a_rad * 0.15398973382026502 /* 15/pi^4 */};
-  double T = u_m / (rho * cv);
-  double r, dr, Eg;
-  cp.eval(T, r, dr, Eg);
-  const double scale = u_m + Esum;
+  Coupler<GP, LT, NT> cp{g, pk, has, (G == GP) && (lane == G - 1), rcv, u_m * frcp(rcv),
+                         (LT)(kn.kappa0 * hpow(rho, g.kap_rho_h)), (LT)(kn.sigma0 * rho),
+                         kl.cdts, (LT)Em, kl.aN,
+                         gc.efac_of(has ? lane : 0, LT(0)), gc.edge_of(lane <= G ? lane : G, LT(0)),
+                         gc.edge_of(G, LT(0))};
+  NT dl = NT(0);
+  NT r, dr;
+  LT Eg, dEg;
+  cp.eval(dl, r, dr, Eg, dEg);
+  const NT scale = u_m + Esum;
+  // FP32 iterates stop at FP32 resolution (the paper's own tolerance is 1e-6, Sec. 5.3)
+  const NT rtol = kn.rtol, atol = kn.atol;
   bool done = !active, ok = !active, need_dir = true;
   int it = 0, ls = 0;
-  double dT = 0.0, lam = 1.0;
+  NT dT = NT(0), lam = NT(1);
   const int guard = g.newton_maxit * 41 + 2;
   for (int k = 0; k < guard; ++k) {
     if (!done && need_dir) {
       if (it >= g.newton_maxit) { done = true; }
-      else if (fabs(r) <= 1e-14 * scale) { done = true; ok = true; }
+      else if (fabs(r) <= atol * scale) { done = true; ok = true; }
       else {
         dT = -r / dr;
         ++it;
-        if (fabs(dT) <= g.newton_rtol * T) { T += dT; done = true; ok = true; }
-        else { lam = 1.0; ls = 0; need_dir = false; }
+        if (fabs(dT) <= rtol * (cp.Tm + dl)) {
+          // converged: the group energies at T + dT follow from the linearisation, exact to
+          // O(dT^2) (relative 1e-26 at the FP64 tolerance)
+          dl += dT;
+          Eg += dEg * (LT)dT;
+          done = true;
+          ok = true;
+        } else { lam = NT(1); ls = 0; need_dir = false; }
       }
     }
     if (__all_sync(0xffffffffu, done)) break;
-    double Tt = T + lam * dT;
-    bool valid = !done && Tt > 0.0;
-    double rt, drt, Et;
-    cp.eval(valid ? Tt : T, rt, drt, Et);
+    NT dt_ = dl + lam * dT;
+    bool valid = !done && (cp.Tm + dt_) > NT(0);
+    NT rt, drt;
+    LT Et, dEt;
+    cp.eval(valid ? dt_ : dl, rt, drt, Et, dEt);
     if (!done) {
-      if (valid && fabs(rt) < fabs(r)) { T = Tt; r = rt; dr = drt; need_dir = true; }
-      else { lam *= 0.5; if (++ls >= 40) done = true; }
+      if (valid && fabs(rt) < fabs(r)) { dl = dt_; r = rt; dr = drt; Eg = Et; dEg = dEt; need_dir = true; }
+      else { lam *= NT(0.5); if (++ls >= 40) done = true; }
     }
   }
-  // bisection fallback on a bracket around [T^-, T_rad] (reading R11)
+  // bisection fallback on a bracket around [T^-, T_rad] (reading R11), in T - T^-
   if (__any_sync(0xffffffffu, active && !ok)) {
     bool need = active && !ok;
-    double Tm = u_m / (rho * cv);
-    double Tr = sqrt(sqrt(Esum / g.a_rad));
-    double lo = fmin(fmin(T, Tr), Tm), hi = fmax(fmax(T, Tr), Tm);
+    NT Tm = cp.Tm;
+    NT Tr = sqrt(sqrt(Esum * frcp(kn.aN * NT(6.4939394022668291491))));  // (sum E / a_R)^(1/4)
+    NT T = Tm + dl;
+    NT lo = fmin(fmin(T, Tr), Tm) - Tm, hi = fmax(fmax(T, Tr), Tm) - Tm;
     int phase = need ? 0 : 3, cnt = 0;
     bool brk = false;
-    double rr, dd, ee;
+    NT rr, dd;
+    LT ee, de;
     for (int k = 0; k < 400 + g.bisect_maxit + 4; ++k) {
       if (__all_sync(0xffffffffu, phase == 3)) break;
-      double Te = phase == 0 ? lo : (phase == 1 ? hi : (phase == 2 ? 0.5 * (lo + hi) : T));
-      cp.eval(Te, rr, dd, ee);
+      NT Te = phase == 0 ? lo : (phase == 1 ? hi : (phase == 2 ? NT(0.5) * (lo + hi) : dl));
+      cp.eval(Te, rr, dd, ee, de);
       if (phase == 0) {
-        if (rr > 0.0 && cnt < 200) { lo *= 0.5; ++cnt; } else { phase = 1; cnt = 0; brk = rr <= 0.0; }
+        if (rr > NT(0) && cnt < 200) { lo = NT(0.5) * (lo + Tm) - Tm; ++cnt; }  // T_lo /= 2
+        else { phase = 1; cnt = 0; brk = rr <= NT(0); }
       } else if (phase == 1) {
-        if (rr < 0.0 && cnt < 200) { hi *= 2.0; ++cnt; }
+        if (rr < NT(0) && cnt < 200) { hi = NT(2) * (hi + Tm) - Tm; ++cnt; }   // T_hi *= 2
         else {
-          brk = brk && rr >= 0.0;
+          brk = brk && rr >= NT(0);
           cnt = 0;
           phase = brk ? (g.bisect_maxit > 0 ? 2 : 3) : 3;
         }
       } else if (phase == 2) {
-        if (rr > 0.0) hi = Te; else lo = Te;
+        if (rr > NT(0)) hi = Te; else lo = Te;
         ++cnt;
-        if (hi - lo <= g.newton_rtol * hi) { ok = true; phase = 3; }
+        if (hi - lo <= rtol * (hi + Tm)) { ok = true; phase = 3; }
         else if (cnt >= g.bisect_maxit) phase = 3;
       }
     }
-    if (need && brk) T = 0.5 * (lo + hi);
+    if (need && brk) dl = NT(0.5) * (lo + hi);
+    NT r2, d2;
+    LT e2, de2;
+    cp.eval(dl, r2, d2, e2, de2);
+    if (need) Eg = e2;
   }
   if (active && !ok) st |= ST_NEWTON;
-  // group energies at the accepted temperature; energy update by conservation (R12)
-  cp.eval(T, r, dr, Eg);
-  double dEsum = seg_sum<GP>(has ? Eg - Em : 0.0);
-  double u_new = u_m - dEsum;
-  rhoe = ke + u_new;
-  if (has) E = Eg;
+  // energy update by conservation (R12)
+  NT dEsum = seg_sum<GP>(has ? (NT)Eg - Em : NT(0));
+  rhoe = ke + (u_m - dEsum);
+  if (has) E = (NT)Eg;
   // momentum coupling at the converged temperature (Eq. 28; Eqs. 31-32)
-  double kap;
-  if (F64GROUP) kap = cp.K * hpow(T, g.kap_T_h) * gc.efac[has ? lane : 0];
-  else kap = (double)((float)cp.K * hpow((float)T, g.kap_T_h) * (float)gc.efac[has ? lane : 0]);
-  double fac = 1.0 / (1.0 + g.c * dts * (kap + cp.Sg));
-  double vcon[3];
-#pragma unroll
-  for (int q = 0; q < D; ++q) vcon[q] = m[q] / (rho * h[q] * h[q]);
-  double dwork = 0.0;
-  double dF[3];
+  LT kap = cp.K * hpow((LT)(cp.Tm + dl), g.kap_T_h) * cp.efac;
+  LT fac = frcp(LT(1) + cp.cdts * (kap + cp.Sg));
+  NT dF[3] = {NT(0), NT(0), NT(0)};
+  NT dwork = NT(0);
 #pragma unroll
   for (int q = 0; q < D; ++q) {
-    double Fn = has ? F[q] * fac : 0.0;
-    dF[q] = has ? Fn - F[q] : 0.0;
-    if (has) F[q] = Fn;
-    dwork += vcon[q] * dF[q];
+    if (has) {
+      LT Fq = (LT)F[q];
+      LT Fn = Fq * fac;
+      dF[q] = (NT)(Fn - Fq);
+      F[q] = (NT)Fn;
+    }
+    dwork += m[q] * irho * frcp(h[q] * h[q]) * dF[q];
   }
-  const double ic2 = 1.0 / (g.c * g.c);
+  const NT ic2 = kn.ic2;
 #pragma unroll
   for (int q = 0; q < D; ++q) m[q] -= seg_sum<GP>(dF[q]) * ic2;
   rhoe -= seg_sum<GP>(dwork) * ic2;
   return st;
 }
 
-// ---------------------------------------------------------------------------------------------
-// The stage kernel.
-// ---------------------------------------------------------------------------------------------
 // Shared-memory bytes of stage_kernel for G groups (must mirror the carve-up in the kernel).
 template <class R, int D, int TX, int TY>
 inline size_t stage_smem_bytes(int G) {
@@ -259,10 +295,10 @@ inline size_t stage_smem_bytes(int G) {
   return n * sizeof(R) + 16 + sizeof(GroupConst);
 }
 
-template <class R, int D, int GP, int TX, int TY, bool F64GROUP>
-__global__ void __launch_bounds__(TX * TY * GP)
+template <class R, int D, int GP, int TX, int TY, class LT, class NT>
+__global__ void __launch_bounds__(TX * TY * GP, sizeof(R) == 4 ? 3 : 2)
 stage_kernel(const StageArgs<R> A) {
-  constexpr int NT = TX * TY * GP;
+  constexpr int NTH = TX * TY * GP;  // threads per block
   constexpr int NG = 2 + D;          // gas conserved variables
   constexpr int NW = 2 + D;          // gas primitives reconstructed: rho, p, vhat_1..D
   constexpr int NRV = 1 + D;         // radiation variables per group
@@ -278,6 +314,7 @@ stage_kernel(const StageArgs<R> A) {
   constexpr int MD = D - 1;          // march direction (D >= 2)
 
   const DevGrid& g = A.g;
+  const Consts<R>& KR = A.k(R(0));
   const int G = g.G;
   const int NV = NG + NRV * G;
   const int tid = threadIdx.x;
@@ -294,7 +331,7 @@ stage_kernel(const StageArgs<R> A) {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* st = reinterpret_cast<R*>(smem_raw);                 // [NSLOT][NV][PC] (rad: [v][cell][G])
-  R* pr = st + (size_t)NSLOT * NV * PC;                     // [NSLOT][NPR][PC]
+  R* pr = st + (int)NSLOT * NV * PC;                     // [NSLOT][NPR][PC]
   R* grx = pr + NSLOT * NPR * PC;                           // [NIP][NW][PC][2]
   R* grm = grx + NIP * NW * PC * 2;                         // [2][NW][TC][2]
   R* gfx = grm + 2 * NW * TC * 2;                           // [NG+1][NFX]
@@ -306,8 +343,8 @@ stage_kernel(const StageArgs<R> A) {
   GroupConst* sgc = reinterpret_cast<GroupConst*>(
       (reinterpret_cast<uintptr_t>(tail) + 15) & ~static_cast<uintptr_t>(15));
 
-  for (int i = tid; i < (int)(sizeof(GroupConst) / sizeof(double)); i += NT)
-    reinterpret_cast<double*>(sgc)[i] = reinterpret_cast<const double*>(A.gc)[i];
+  for (int i = tid; i < (int)(sizeof(GroupConst) / sizeof(int)); i += NTH)
+    reinterpret_cast<int*>(sgc)[i] = reinterpret_cast<const int*>(A.gc)[i];
 
   const Tab<R> tx{A.tab[0], nx + 4};
   const Tab<R> ty{A.tab[D >= 2 ? 1 : 0], (D >= 2 ? ny : nx) + 4};
@@ -337,9 +374,9 @@ stage_kernel(const StageArgs<R> A) {
   // converting to primitives) and radiation (one element per thread, coalesced along x, g).
   // Cell list: `ncl` cells enumerated by `cell_of(i, sx, sy)`.
   auto load_cells = [&](int slot, int k, int ncl, auto cell_of) {
-    R* S = st + (size_t)slot * NV * PC;
+    R* S = st + (int)slot * NV * PC;
     R* P = pr + slot * NPR * PC;
-    for (int i = tid; i < ncl; i += NT) {
+    for (int i = tid; i < ncl; i += NTH) {
       int sx, sy;
       cell_of(i, sx, sy);
       bool fl[3];
@@ -357,27 +394,29 @@ stage_kernel(const StageArgs<R> A) {
       R ke = R(0);
 #pragma unroll
       for (int q = 0; q < D; ++q) { R vh = u[1 + q] / rho; P[(2 + q) * PC + sc] = vh; ke += R(0.5) * rho * vh * vh; }
-      R p = R(g.gamma - 1.0) * (u[NG - 1] - ke);
+      R p = KR.gm1 * (u[NG - 1] - ke);
       P[0 * PC + sc] = rho;
       P[1 * PC + sc] = p;
       R T = p / rho;
-      R K = (T > R(0)) ? R(g.kappa0) * hpow(rho, g.kap_rho_h) * hpow(T, g.kap_T_h) : R(0);
+      R K = (T > R(0)) ? KR.kappa0 * hpow(rho, g.kap_rho_h) * hpow(T, g.kap_T_h) : R(0);
       P[NW * PC + sc] = K;
-      P[(NW + 1) * PC + sc] = R(g.sigma0) * rho;
+      P[(NW + 1) * PC + sc] = KR.sigma0 * rho;
     }
-    const int nel = NRV * ncl * G;
-    for (int e = tid; e < nel; e += NT) {
-      int gg = e % G;
-      int r = e / G;
-      int i = r % ncl;
-      int v = r / ncl;
+    // radiation: segment of GP lanes per cell, lane = group (coalesced runs of G per cell)
+    for (int t = tid; t < ncl * GP; t += NTH) {
+      const int i = t / GP, gg = t % GP;  // GP is a power of two: shifts and masks
+      if (gg >= G) continue;
       int sx, sy;
       cell_of(i, sx, sy);
       bool fl[3];
       int64_t gc_ = map_cell(sx, sy, k, fl);
-      R val = A.in[(int64_t)NG * ncell + ((int64_t)v * ncell + gc_) * G + gg];
-      if (v >= 1 && fl[v - 1]) val = -val;
-      S[NG * PC + ((size_t)v * PC + scell(sx, sy)) * G + gg] = val;
+      const int so = NG * PC + scell(sx, sy) * G + gg;
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) {
+        R val = A.in[(int64_t)NG * ncell + ((int64_t)v * ncell + gc_) * G + gg];
+        if (v >= 1 && fl[v - 1]) val = -val;
+        S[so + v * PC * G] = val;
+      }
     }
   };
   auto interior_of = [&](int i, int& sx, int& sy) { sx = i % TX; sy = i / TX; };
@@ -409,7 +448,7 @@ stage_kernel(const StageArgs<R> A) {
     L[0] = WL[0]; L[1] = WL[1]; Rr[0] = WR[0]; Rr[1] = WR[1];
 #pragma unroll
     for (int q = 0; q < D; ++q) { L[2 + q] = WL[2 + (d + q) % D]; Rr[2 + q] = WR[2 + (d + q) % D]; }
-    hllc<R, D>(R(g.gamma), L, Rr, f, vs);
+    hllc<R, D>(KR.gamma, L, Rr, f, vs);
     out[0] = f[0];
 #pragma unroll
     for (int q = 0; q < D; ++q) out[(1 + (d + q) % D) * stride] = f[1 + q];
@@ -420,23 +459,22 @@ stage_kernel(const StageArgs<R> A) {
   // radiation flux through a face along direction d for group gg: left cell values (E, Fhat)
   // reconstructed to its upper face and right cell values to its lower face.
   auto rad_face = [&](int d, const R* QL, const R* QR, R chiL, R chiR, R ell, R vstar, R* out) {
-    const R c = R(g.c);
     R PL[3], PR[3];
-    m1_row<R, D>(c, QL[0], QL + 1, d, PL);
-    m1_row<R, D>(c, QR[0], QR + 1, d, PR);
+    m1_row<R, D>(KR.ic2, QL[0], QL + 1, d, PL);
+    m1_row<R, D>(KR.ic2, QR[0], QR + 1, d, PR);
     R tau = R(0.5) * (chiL + chiR) * ell;
-    R eps = tau > R(1) ? R(1) / tau : R(1);
+    R eps = tau > R(1) ? frcp(tau) : R(1);
     const R* Qu = vstar >= R(0) ? QL : QR;
-    out[0] = R(0.5) * (QL[1 + d] + QR[1 + d]) - R(0.5) * eps * c * (QR[0] - QL[0]) + vstar * Qu[0];
+    out[0] = R(0.5) * (QL[1 + d] + QR[1 + d]) - eps * KR.hc * (QR[0] - QL[0]) + vstar * Qu[0];
 #pragma unroll
     for (int q = 0; q < D; ++q)
-      out[1 + q] = R(0.5) * c * c * (PL[q] + PR[q]) - R(0.5) * c * (QR[1 + q] - QL[1 + q]) + vstar * Qu[1 + q];
+      out[1 + q] = KR.hc2 * (PL[q] + PR[q]) - KR.hc * (QR[1 + q] - QL[1 + q]) + vstar * Qu[1 + q];
   };
 
   // radiation primitives of a slot cell for group gg: E, Fhat (Cartesian: F)
   auto rad_vals = [&](const R* S, int sc, int gg, R* Q) {
 #pragma unroll
-    for (int v = 0; v < NRV; ++v) Q[v] = S[NG * PC + ((size_t)v * PC + sc) * G + gg];
+    for (int v = 0; v < NRV; ++v) Q[v] = S[NG * PC + ((int)v * PC + sc) * G + gg];
   };
 
   const bool cell_ok = (x0 + lx < nx) && (D < 3 || y0 + ly < ny);
@@ -452,7 +490,7 @@ stage_kernel(const StageArgs<R> A) {
   __syncthreads();
   if (D >= 2) {
     // march-direction reconstruction of planes kbeg-1 and kbeg, then the face kbeg-1/2
-    for (int i = tid; i < 2 * TC; i += NT) {
+    for (int i = tid; i < 2 * TC; i += NTH) {
       int which = i / TC, c = i % TC;
       int k = kbeg - 1 + which;
       int sx = c % TX, sy = c / TX;
@@ -462,7 +500,7 @@ stage_kernel(const StageArgs<R> A) {
                 pr + ((k + 1) & 3) * NPR * PC, sc, sc, sc, grm + ((k & 1) * NW * TC + c) * 2, TC * 2);
     }
     __syncthreads();
-    for (int c = tid; c < TC; c += NT) {
+    for (int c = tid; c < TC; c += NTH) {
       R WL[NW], WR[NW];
       const R* ab_lo = grm + (((kbeg - 1) & 1) * NW * TC + c) * 2;
       const R* ab_hi = grm + ((kbeg & 1) * NW * TC + c) * 2;
@@ -475,10 +513,10 @@ stage_kernel(const StageArgs<R> A) {
       int sc = scell(lx, ly);
       int k = kbeg;
       R Qm2[NRV], Qm1[NRV], Q0[NRV], Qp1[NRV], QL[NRV], QR[NRV], tmp[NRV];
-      rad_vals(st + (size_t)((k - 2) & 3) * NV * PC, sc, lane, Qm2);
-      rad_vals(st + (size_t)((k - 1) & 3) * NV * PC, sc, lane, Qm1);
-      rad_vals(st + (size_t)(k & 3) * NV * PC, sc, lane, Q0);
-      rad_vals(st + (size_t)((k + 1) & 3) * NV * PC, sc, lane, Qp1);
+      rad_vals(st + (int)((k - 2) & 3) * NV * PC, sc, lane, Qm2);
+      rad_vals(st + (int)((k - 1) & 3) * NV * PC, sc, lane, Qm1);
+      rad_vals(st + (int)(k & 3) * NV * PC, sc, lane, Q0);
+      rad_vals(st + (int)((k + 1) & 3) * NV * PC, sc, lane, Qp1);
       int ipl = bc_pad(k - 1), ipr = bc_pad(k);
 #pragma unroll
       for (int v = 0; v < NRV; ++v) {
@@ -504,14 +542,14 @@ stage_kernel(const StageArgs<R> A) {
       load_cells(s0, k, NHALO, halo_of);
     }
     __syncthreads();
-    const R* S0 = st + (size_t)s0 * NV * PC;
+    const R* S0 = st + (int)s0 * NV * PC;
     const R* P0 = pr + s0 * NPR * PC;
     // ---- gas reconstruction: in-plane faces of plane k, march direction of plane k+1
     {
       constexpr int NXR = (TX + 2) * TY;
       constexpr int NYR = (D == 3) ? TX * (TY + 2) : 0;
       const int NMR = (D >= 2) ? TC : 0;
-      for (int i = tid; i < NXR + NYR + NMR; i += NT) {
+      for (int i = tid; i < NXR + NYR + NMR; i += NTH) {
         if (i < NXR) {
           int sx = i % (TX + 2) - 1, sy = i / (TX + 2);
           int sc = scell(sx, sy);
@@ -535,7 +573,7 @@ stage_kernel(const StageArgs<R> A) {
     {
       const int NMF = (D >= 2) ? TC : 0;
       const int NYF = (D == 3) ? NFY : 0;
-      for (int i = tid; i < NFX + NYF + NMF; i += NT) {
+      for (int i = tid; i < NFX + NYF + NMF; i += NTH) {
         R WL[NW], WR[NW];
         if (i < NFX) {
           int fx = i % (TX + 1), fy = i / (TX + 1);
@@ -588,7 +626,7 @@ stage_kernel(const StageArgs<R> A) {
         R out[NRV];
         rad_face(0, QL, QR, chi_of(P0, scl), chi_of(P0, scr), tx(T_ELL, ipr), gfx[NG * NFX + f], out);
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rfx[((size_t)v * NFX + f) * G + gg] = out[v];
+        for (int v = 0; v < NRV; ++v) rfx[((int)v * NFX + f) * G + gg] = out[v];
       }
       if (D == 3) {
         for (int side = 0; side < ((ly == TY - 1 || gy == ny - 1) ? 2 : 1); ++side) {
@@ -609,17 +647,17 @@ stage_kernel(const StageArgs<R> A) {
           R out[NRV];
           rad_face(1, QL, QR, chi_of(P0, scl), chi_of(P0, scr), ty(T_ELL, ipr), gfy[NG * NFY + f], out);
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rfy[((size_t)v * NFY + f) * G + gg] = out[v];
+          for (int v = 0; v < NRV; ++v) rfy[((int)v * NFY + f) * G + gg] = out[v];
         }
       }
       if (D >= 2) {
         // march face k+1/2: cells k-1 .. k+2 of this column
         int sc = scell(lx, ly);
         R Qa[NRV], Qb[NRV], Qc[NRV], Qd[NRV], QL[NRV], QR[NRV], tmp[NRV];
-        rad_vals(st + (size_t)((k - 1) & 3) * NV * PC, sc, gg, Qa);
+        rad_vals(st + (int)((k - 1) & 3) * NV * PC, sc, gg, Qa);
         rad_vals(S0, sc, gg, Qb);
-        rad_vals(st + (size_t)((k + 1) & 3) * NV * PC, sc, gg, Qc);
-        rad_vals(st + (size_t)((k + 2) & 3) * NV * PC, sc, gg, Qd);
+        rad_vals(st + (int)((k + 1) & 3) * NV * PC, sc, gg, Qc);
+        rad_vals(st + (int)((k + 2) & 3) * NV * PC, sc, gg, Qd);
         int ipl = bc_pad(k), ipr = bc_pad(k + 1);
 #pragma unroll
         for (int v = 0; v < NRV; ++v) {
@@ -644,9 +682,9 @@ stage_kernel(const StageArgs<R> A) {
       const int64_t cidx = (D == 1) ? (int64_t)gx
                          : (D == 2) ? (int64_t)k * nx + gx
                                     : ((int64_t)k * ny + gy) * nx + gx;
-      const R dt = R(A.dt);
+      const R dt = KR.dt;
       // gas (every lane of the cell computes the same values)
-      double gas[NG];
+      NT gas[NG];
 #pragma unroll
       for (int v = 0; v < NG; ++v) {
         R net = (gfx[v * NFX + fxa + 1] * fxr - gfx[v * NFX + fxa] * fxl);
@@ -657,31 +695,32 @@ stage_kernel(const StageArgs<R> A) {
           net = net + (gm_hi[v * TC + tcell] * fmr - gm_lo[v * TC + tcell] * fml);
         }
         R u1 = S0[v * PC + sc] + dt * (-net);
-        if (A.base != nullptr && cell_ok) u1 = R(A.alpha) * A.base[v * ncell + cidx] + R(1.0 - A.alpha) * u1;
-        gas[v] = (double)u1;
+        if (A.base != nullptr && cell_ok) u1 = KR.alpha * A.base[v * ncell + cidx] + KR.beta * u1;
+        gas[v] = (NT)u1;
       }
       // radiation of this lane's group
-      double E = 0.0, F[3] = {0.0, 0.0, 0.0};
+      NT E = NT(0), F[3] = {NT(0), NT(0), NT(0)};
       if (lane < G && cell_ok) {
 #pragma unroll
         for (int v = 0; v < NRV; ++v) {
-          R net = (rfx[((size_t)v * NFX + fxa + 1) * G + lane] * fxr - rfx[((size_t)v * NFX + fxa) * G + lane] * fxl);
-          if (D == 3) net = net + (rfy[((size_t)v * NFY + fya + TX) * G + lane] * fyr - rfy[((size_t)v * NFY + fya) * G + lane] * fyl);
+          R net = (rfx[((int)v * NFX + fxa + 1) * G + lane] * fxr - rfx[((int)v * NFX + fxa) * G + lane] * fxl);
+          if (D == 3) net = net + (rfy[((int)v * NFY + fya + TX) * G + lane] * fyr - rfy[((int)v * NFY + fya) * G + lane] * fyl);
           if (D >= 2) net = net + (rfm_new[v] * fmr - rfm_old[v] * fml);
-          R u1 = S0[NG * PC + ((size_t)v * PC + sc) * G + lane] + dt * (-net);
+          R u1 = S0[NG * PC + ((int)v * PC + sc) * G + lane] + dt * (-net);
           if (A.base != nullptr) {
             R b = A.base[(int64_t)NG * ncell + ((int64_t)v * ncell + cidx) * G + lane];
-            u1 = R(A.alpha) * b + R(1.0 - A.alpha) * u1;
+            u1 = KR.alpha * b + KR.beta * u1;
           }
-          if (v == 0) E = (double)u1; else F[v - 1] = (double)u1;
+          if (v == 0) E = (NT)u1; else F[v - 1] = (NT)u1;
         }
       }
       unsigned stbits = 0;
       if (g.couple) {
-        double h[3] = {1.0, 1.0, 1.0};
-        double m[3] = {gas[1], D > 1 ? gas[2] : 0.0, D > 2 ? gas[3] : 0.0};
-        double rho = gas[0], rhoe = gas[NG - 1];
-        stbits = couple_cell<R, D, GP, F64GROUP>(g, *sgc, A.pk, cell_ok, lane, h, rho, m, rhoe, E, F, A.dts);
+        NT h[3] = {NT(1), NT(1), NT(1)};
+        NT m[3] = {gas[1], D > 1 ? gas[2] : NT(0), D > 2 ? gas[3] : NT(0)};
+        NT rho = gas[0], rhoe = gas[NG - 1];
+        stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.k(NT(0)), A.k(LT(0)), cell_ok, lane, h,
+                                            rho, m, rhoe, E, F);
         gas[0] = rho;
 #pragma unroll
         for (int q = 0; q < D; ++q) gas[1 + q] = m[q];
@@ -690,7 +729,7 @@ stage_kernel(const StageArgs<R> A) {
       if (cell_ok) {
         bool bad = false;
         if (lane < NG) {
-          double val = gas[0];
+          NT val = gas[0];
 #pragma unroll
           for (int v = 1; v < NG; ++v) if (lane == v) val = gas[v];
           A.out[(int64_t)lane * ncell + cidx] = R(val);
@@ -699,7 +738,7 @@ stage_kernel(const StageArgs<R> A) {
         if (lane < G) {
 #pragma unroll
           for (int v = 0; v < NRV; ++v) {
-            double val = v == 0 ? E : F[v - 1];
+            NT val = v == 0 ? E : F[v - 1];
             A.out[(int64_t)NG * ncell + ((int64_t)v * ncell + cidx) * G + lane] = R(val);
             bad |= !isfinite(val);
           }

@@ -1,4 +1,4 @@
-// Stage kernel instantiations: float, 1-d.
+// Stage kernel instantiations: state float, group arithmetic float, Newton/bookkeeping float, 1-d.
 #include "fx_launch.h"
 
 namespace fx {
@@ -6,9 +6,12 @@ namespace fx {
 template <int GP>
 static cudaError_t launch_gp(const StageArgs<float>& a, cudaStream_t s) {
   using TS = TileShape<1, GP>;
-  auto kern = stage_kernel<float, 1, GP, TS::TX, TS::TY, false>;
+  auto kern = stage_kernel<float, 1, GP, TS::TX, TS::TY, float, float>;
   const size_t smem = stage_smem_bytes<float, 1, TS::TX, TS::TY>(a.g.G);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   dim3 grid((a.g.n[0] + TS::TX - 1) / TS::TX, 1, 1);
   if (1 == 2) grid.y = (a.g.n[1] + a.chunk - 1) / a.chunk;
@@ -21,22 +24,12 @@ static cudaError_t launch_gp(const StageArgs<float>& a, cudaStream_t s) {
 }
 
 template <>
-cudaError_t launch_stage<float, 1>(const StageArgs<float>& a, int GP, cudaStream_t s) {
+cudaError_t launch_stage<float, 1, float>(const StageArgs<float>& a, int GP, cudaStream_t s) {
   switch (GP) {
     case 8: return launch_gp<8>(a, s);
     case 16: return launch_gp<16>(a, s);
     case 32: return launch_gp<32>(a, s);
     default: return cudaErrorInvalidValue;
-  }
-}
-
-template <>
-size_t stage_smem<float, 1>(int GP, int G) {
-  switch (GP) {
-    case 8: return stage_smem_bytes<float, 1, TileShape<1, 8>::TX, TileShape<1, 8>::TY>(G);
-    case 16: return stage_smem_bytes<float, 1, TileShape<1, 16>::TX, TileShape<1, 16>::TY>(G);
-    case 32: return stage_smem_bytes<float, 1, TileShape<1, 32>::TX, TileShape<1, 32>::TY>(G);
-    default: return 0;
   }
 }
 

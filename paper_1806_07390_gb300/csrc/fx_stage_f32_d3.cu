@@ -1,4 +1,4 @@
-// Stage kernel instantiations: float, 3-d.
+// Stage kernel instantiations: state float, group arithmetic float, Newton/bookkeeping float, 3-d.
 #include "fx_launch.h"
 
 namespace fx {
@@ -6,9 +6,12 @@ namespace fx {
 template <int GP>
 static cudaError_t launch_gp(const StageArgs<float>& a, cudaStream_t s) {
   using TS = TileShape<3, GP>;
-  auto kern = stage_kernel<float, 3, GP, TS::TX, TS::TY, false>;
+  auto kern = stage_kernel<float, 3, GP, TS::TX, TS::TY, float, float>;
   const size_t smem = stage_smem_bytes<float, 3, TS::TX, TS::TY>(a.g.G);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   dim3 grid((a.g.n[0] + TS::TX - 1) / TS::TX, 1, 1);
   if (3 == 2) grid.y = (a.g.n[1] + a.chunk - 1) / a.chunk;
@@ -21,22 +24,12 @@ static cudaError_t launch_gp(const StageArgs<float>& a, cudaStream_t s) {
 }
 
 template <>
-cudaError_t launch_stage<float, 3>(const StageArgs<float>& a, int GP, cudaStream_t s) {
+cudaError_t launch_stage<float, 3, float>(const StageArgs<float>& a, int GP, cudaStream_t s) {
   switch (GP) {
     case 8: return launch_gp<8>(a, s);
     case 16: return launch_gp<16>(a, s);
     case 32: return launch_gp<32>(a, s);
     default: return cudaErrorInvalidValue;
-  }
-}
-
-template <>
-size_t stage_smem<float, 3>(int GP, int G) {
-  switch (GP) {
-    case 8: return stage_smem_bytes<float, 3, TileShape<3, 8>::TX, TileShape<3, 8>::TY>(G);
-    case 16: return stage_smem_bytes<float, 3, TileShape<3, 16>::TX, TileShape<3, 16>::TY>(G);
-    case 32: return stage_smem_bytes<float, 3, TileShape<3, 32>::TX, TileShape<3, 32>::TY>(G);
-    default: return 0;
   }
 }
 

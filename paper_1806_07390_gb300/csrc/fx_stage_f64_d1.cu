@@ -1,4 +1,4 @@
-// Stage kernel instantiations: double, 1-d.
+// Stage kernel instantiations: state double, group arithmetic double, Newton/bookkeeping double, 1-d.
 #include "fx_launch.h"
 
 namespace fx {
@@ -6,9 +6,12 @@ namespace fx {
 template <int GP>
 static cudaError_t launch_gp(const StageArgs<double>& a, cudaStream_t s) {
   using TS = TileShape<1, GP>;
-  auto kern = stage_kernel<double, 1, GP, TS::TX, TS::TY, true>;
+  auto kern = stage_kernel<double, 1, GP, TS::TX, TS::TY, double, double>;
   const size_t smem = stage_smem_bytes<double, 1, TS::TX, TS::TY>(a.g.G);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   dim3 grid((a.g.n[0] + TS::TX - 1) / TS::TX, 1, 1);
   if (1 == 2) grid.y = (a.g.n[1] + a.chunk - 1) / a.chunk;
@@ -21,22 +24,12 @@ static cudaError_t launch_gp(const StageArgs<double>& a, cudaStream_t s) {
 }
 
 template <>
-cudaError_t launch_stage<double, 1>(const StageArgs<double>& a, int GP, cudaStream_t s) {
+cudaError_t launch_stage<double, 1, double>(const StageArgs<double>& a, int GP, cudaStream_t s) {
   switch (GP) {
     case 8: return launch_gp<8>(a, s);
     case 16: return launch_gp<16>(a, s);
     case 32: return launch_gp<32>(a, s);
     default: return cudaErrorInvalidValue;
-  }
-}
-
-template <>
-size_t stage_smem<double, 1>(int GP, int G) {
-  switch (GP) {
-    case 8: return stage_smem_bytes<double, 1, TileShape<1, 8>::TX, TileShape<1, 8>::TY>(G);
-    case 16: return stage_smem_bytes<double, 1, TileShape<1, 16>::TX, TileShape<1, 16>::TY>(G);
-    case 32: return stage_smem_bytes<double, 1, TileShape<1, 32>::TX, TileShape<1, 32>::TY>(G);
-    default: return 0;
   }
 }
 

@@ -1,4 +1,4 @@
-// Stage kernel instantiations: double, 3-d.
+// Stage kernel instantiations: state double, group arithmetic double, Newton/bookkeeping double, 3-d.
 #include "fx_launch.h"
 
 namespace fx {
@@ -6,9 +6,12 @@ namespace fx {
 template <int GP>
 static cudaError_t launch_gp(const StageArgs<double>& a, cudaStream_t s) {
   using TS = TileShape<3, GP>;
-  auto kern = stage_kernel<double, 3, GP, TS::TX, TS::TY, true>;
+  auto kern = stage_kernel<double, 3, GP, TS::TX, TS::TY, double, double>;
   const size_t smem = stage_smem_bytes<double, 3, TS::TX, TS::TY>(a.g.G);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   dim3 grid((a.g.n[0] + TS::TX - 1) / TS::TX, 1, 1);
   if (3 == 2) grid.y = (a.g.n[1] + a.chunk - 1) / a.chunk;
@@ -21,22 +24,12 @@ static cudaError_t launch_gp(const StageArgs<double>& a, cudaStream_t s) {
 }
 
 template <>
-cudaError_t launch_stage<double, 3>(const StageArgs<double>& a, int GP, cudaStream_t s) {
+cudaError_t launch_stage<double, 3, double>(const StageArgs<double>& a, int GP, cudaStream_t s) {
   switch (GP) {
     case 8: return launch_gp<8>(a, s);
     case 16: return launch_gp<16>(a, s);
     case 32: return launch_gp<32>(a, s);
     default: return cudaErrorInvalidValue;
-  }
-}
-
-template <>
-size_t stage_smem<double, 3>(int GP, int G) {
-  switch (GP) {
-    case 8: return stage_smem_bytes<double, 3, TileShape<3, 8>::TX, TileShape<3, 8>::TY>(G);
-    case 16: return stage_smem_bytes<double, 3, TileShape<3, 16>::TX, TileShape<3, 16>::TY>(G);
-    case 32: return stage_smem_bytes<double, 3, TileShape<3, 32>::TX, TileShape<3, 32>::TY>(G);
-    default: return 0;
   }
 }
 

@@ -8,6 +8,7 @@ namespace fx {
 constexpr int MAXG = 32;          // groups per cell handled by one lane segment
 constexpr int NPLANCK_LO = 27;    // FP64 Bernoulli-series terms (x < XSPLIT, error < 1e-17)
 constexpr int NPLANCK_LO32 = 13;  // FP32 Bernoulli-series terms (error < 1e-8)
+constexpr int NPLANCK_UP = 48;    // cap of the FP64 exponential series (x >= XSPLIT: 14 terms)
 constexpr double XSPLIT = 3.0;    // lower/upper Planck series switch
 
 // Status bits raised by kernels (atomicOr into the workspace status word).

@@ -21,7 +21,7 @@ FX_OK = 0
 STATUS_NAMES = {0: "FX_OK", -1: "FX_ERR_ARG", -2: "FX_ERR_CUDA", -3: "FX_ERR_WORKSPACE",
                 -4: "FX_ERR_NEWTON", -5: "FX_ERR_FLOOR", -6: "FX_ERR_NONFINITE",
                 -7: "FX_ERR_UNSUPPORTED"}
-FX_FP64, FX_FP32 = 0, 1
+FX_FP64, FX_FP32, FX_FP32_F64NEWTON = 0, 1, 2
 NTOTALS = 6
 
 # every symbol include/fx.h declares
@@ -102,7 +102,7 @@ def params(pb: Problem) -> FxParams:
     P.gamma, P.c_light, P.a_rad = pb.gamma, pb.c_light, pb.a_rad
     P.kappa0, P.kap_rho_exp, P.kap_T_exp = pb.kappa0, pb.kap_rho_exp, pb.kap_T_exp
     P.kap_eps_exp, P.sigma0 = pb.kap_eps_exp, pb.sigma0
-    P.precision = FX_FP64 if pb.precision == "fp64" else FX_FP32
+    P.precision = {"fp64": FX_FP64, "fp32": FX_FP32, "fp32n64": FX_FP32_F64NEWTON}[pb.precision]
     P.rad_recon_order, P.couple = pb.rad_recon_order, pb.couple
     P.newton_maxit, P.bisect_maxit, P.newton_rtol = pb.newton_maxit, pb.bisect_maxit, pb.newton_rtol
     P.rho_floor, P.p_floor, P.E_floor = pb.rho_floor, pb.p_floor, pb.E_floor

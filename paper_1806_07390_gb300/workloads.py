@@ -59,7 +59,7 @@ class Problem:
     newton_rtol: float = 1e-13
     rho_floor: float = 1e-12
     p_floor: float = 1e-12
-    E_floor: float = 1e-31
+    E_floor: float = 1e-300
     cfl: float = 0.5
     dt: float = 0.0
     nsteps: int = 1

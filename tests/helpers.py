@@ -21,20 +21,35 @@ def fields(pb: Problem, state: np.ndarray):
         yield f"F{q}", rad[1 + q].reshape(-1)
 
 
-def field_errors(pb: Problem, got: np.ndarray, ref: np.ndarray):
-    """Per field: (relative L1 error, max-norm error relative to max |ref|)."""
+def natural_scales(pb: Problem, ref: np.ndarray):
+    """Per field, the magnitude each field is naturally measured against: rho, rho e and E
+    themselves; momentum against sqrt(rho * rho e); radiation flux against c E."""
+    f = dict(fields(pb, ref))
+    mom = np.sqrt(np.abs(f["rho"] * f["rhoe"]))
+    sc = {"rho": f["rho"], "rhoe": f["rhoe"], "E": f["E"]}
+    for q in range(pb.dims):
+        sc[f"m{q}"] = mom
+        sc[f"F{q}"] = pb.c_light * f["E"]
+    return sc
+
+
+def field_errors(pb: Problem, got: np.ndarray, ref: np.ndarray, natural: bool = False):
+    """Per field: (L1 error, max-norm error), relative to the field itself, or with
+    natural=True relative to the field's natural scale (see natural_scales)."""
     out = {}
+    sc = natural_scales(pb, ref) if natural else None
     for (name, a), (_, b) in zip(fields(pb, np.asarray(got, dtype=np.float64)), fields(pb, ref)):
-        den1 = np.sum(np.abs(b))
-        denm = np.max(np.abs(b)) if b.size else 0.0
+        s = sc[name] if natural else b
+        den1 = np.sum(np.abs(s))
+        denm = np.max(np.abs(s)) if s.size else 0.0
         l1 = np.sum(np.abs(a - b)) / den1 if den1 > 0 else np.max(np.abs(a - b))
         mx = np.max(np.abs(a - b)) / denm if denm > 0 else np.max(np.abs(a - b))
         out[name] = (float(l1), float(mx))
     return out
 
 
-def assert_parity(pb, got, ref, l1_tol, max_tol=None, skip=()):
-    errs = field_errors(pb, got, ref)
+def assert_parity(pb, got, ref, l1_tol, max_tol=None, skip=(), natural=False):
+    errs = field_errors(pb, got, ref, natural=natural)
     bad = {k: v for k, v in errs.items() if k not in skip and (v[0] > l1_tol or (max_tol is not None and v[1] > max_tol))}
     assert not bad, f"parity failed (l1 tol {l1_tol}, max tol {max_tol}): {bad}; all: {errs}"
     return errs

@@ -1,7 +1,10 @@
 """Parity of the CUDA stage update (through the C ABI) with the FP64 CPU oracle.
 
 Bar (FP64 path): relative L1 error <= 1e-10 and max-norm error <= 1e-8 per field; conserved
-totals <= 1e-13.  FP32 form: relative L1 <= 1e-5 on smooth problems and <= 1e-4 with shocks.
+totals <= 1e-13.  FP32 form: L1 error <= 1e-5 on smooth problems and <= 1e-4 with shocks, each
+field measured against its natural scale (momentum against sqrt(rho rho e), radiation flux
+against c E): near equilibrium the flux is many orders below c E and below FP32 resolution, so
+an error relative to the flux itself would measure FP32 rounding noise, not the method.
 """
 import numpy as np
 import pytest
@@ -106,18 +109,19 @@ def test_reflecting_walls_and_random_state_fp64(fxmod):
     H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
 
 
+@pytest.mark.parametrize("form", ["fp32", "fp32n64"])
 @pytest.mark.parametrize("maker,tol", [("kh", 1e-4), ("blobs", 1e-4), ("lognormal", 1e-5)])
-def test_fp32_form_small(fxmod, maker, tol):
+def test_fp32_form_small(fxmod, maker, tol, form):
     if maker == "kh":
-        pb, prim = W.kh_2d(nx=48, ny=40, ngroups=16, nsteps=4, precision="fp32")
+        pb, prim = W.kh_2d(nx=48, ny=40, ngroups=16, nsteps=4, precision=form)
     elif maker == "blobs":
-        pb, prim = W.blobs_2d(shape=(40, 36), ngroups=8, nsteps=4, precision="fp32")
+        pb, prim = W.blobs_2d(shape=(40, 36), ngroups=8, nsteps=4, precision=form)
     else:
-        pb, prim = W.lognormal_3d(shape=(12, 10, 9), ngroups=12, nsteps=2, precision="fp32")
+        pb, prim = W.lognormal_3d(shape=(12, 10, 9), ngroups=12, nsteps=2, precision=form)
     got, st, _ = run_gpu(fxmod, pb, prim)
     ref, rst = run_oracle(pb, prim)
     assert st == 0 and rst == 0
-    H.assert_parity(pb, got, ref, tol)
+    H.assert_parity(pb, got, ref, tol, natural=True)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32", 1e-4)])
@@ -139,7 +143,10 @@ def test_kh2d_full_size_sampled_windows(fxmod, precision, tol):
         r = H.gather_cells(sub, ref, H.sub_cells(sub, (8, 8), 4))
         gcell = H.gather_cells(pb, out, H.window_cells(pb, start, (8, 8)))
         small = W.Problem(**{**sub.__dict__, "n": (8, 8, 1)})
-        H.assert_parity(small, gcell, r, tol, FP64_MAX if precision == "fp64" else None)
+        if precision == "fp64":
+            H.assert_parity(small, gcell, r, tol, FP64_MAX)
+        else:
+            H.assert_parity(small, gcell, r, tol, natural=True)
 
 
 def test_nonfinite_state_is_reported(fxmod):
