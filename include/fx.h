@@ -144,7 +144,8 @@ fx_status fx_conserved_totals(fx_grid* h, double out[FX_NTOTALS]);
 /* Copy the state out, converting to dst_precision, to host (synchronous) or device memory. */
 fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is_device);
 
-/* Number of stage-kernel launches enqueued by one fx_step(dt, 1) call. */
+/* Number of kernel launches enqueued by one fx_step(dt, 1) call (per RK stage: the gas face
+ * kernel and the radiation/update kernel). */
 int fx_launches_per_step(const fx_grid* h);
 
 /* Host-side inspection (no GPU needed): the FP64 reconstruction/divergence table of direction d,
@@ -152,6 +153,12 @@ int fx_launches_per_step(const fx_grid* h);
  * the number of doubles (copied only when cap is large enough), or -1 for a bad argument. */
 int fx_debug_table(const fx_grid* h, int d, double* out, size_t cap);
 int fx_debug_ntab(void);
+
+/* Host-side inspection of the FP32 Planck band tables: for group g and node i (u = log2 T =
+ * *u0 + i/32), with L = log2 of the band integral Int t^3/(e^t-1) dt over the group's edges
+ * divided by T: out[4(g*nu + i) + {0,1,2,3}] = L - floor(L), (dL/du)/32, floor(L), 0.  Returns
+ * the number of floats (copied only when cap is large enough), or -1 for a null handle. */
+int fx_debug_planck_table(const fx_grid* h, float* out, size_t cap, int* nu, float* u0);
 
 const char* fx_last_error(const fx_grid* h);
 void fx_clear_error(fx_grid* h);

@@ -3,6 +3,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
 import subprocess
 import sys
@@ -20,14 +21,21 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
+# The FP32 translation units use the hardware reciprocal and square-root approximations (a few
+# ulp) and flush denormals; the FP32 form's accuracy bar is far above that.  FP64 units keep IEEE.
+FP32_FLAGS = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+
+
 def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    fp32 = os.path.basename(src).startswith("fx_stage_f32")
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *(FP32_FLAGS if fp32 else []), *extra, "-c", src]
+    tag = hashlib.sha1(" ".join(cmd[1:]).encode()).hexdigest()[:10]
+    obj = os.path.join(BUILD, f"{os.path.basename(src)}.{tag}.o")
     deps = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + [
         os.path.join(HERE, "..", "include", "fx.h"), src]
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
-    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    r = subprocess.run(cmd + ["-o", obj], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
     return obj

@@ -97,6 +97,7 @@ void solve_row(const double A[3][3], const double e[3], double y[3]) {
 
 }  // namespace
 
+struct PlanckTableHost;
 struct fx_grid {
   fx_params P{};
   DevGrid dg{};
@@ -115,6 +116,13 @@ struct fx_grid {
   fx_status sticky = FX_OK;
   std::string err;
   unsigned* h_status = nullptr;  // pinned
+  std::vector<float4> ptab;       // FP32 Planck band tables [G][ptab_nu] (see PlanckTable)
+  int ptab_nu = 0;
+  float ptab_u0 = 0.0f;
+  size_t off_ptab = 0;
+  size_t off_faces = 0;           // gas face buffer [dir][NG+1][faces of dir]
+  int64_t face_off[3] = {0, 0, 0};
+  bool uniform[3] = {false, false, false};
 };
 
 namespace {
@@ -232,6 +240,64 @@ void planck_coefficients(PlanckParams& pk) {
     pk.lo32[m - 1] = (float)pk.c64.lo[m - 1];
     pk.wd32[m - 1] = (float)pk.c64.wd[m - 1];
   }
+}
+
+// Host FP64 Planck integrals for the FP32 band tables: D(x) = Int_0^x (Bernoulli series in
+// b_k = B_k/k!, x < XSPLIT) and P(x) = Int_x^inf (exponential series), as on the device.
+double host_planck_lower(const PlanckParams& pk, double x) {
+  double x2 = x * x, sd = 0.0;
+  for (int m = NPLANCK_LO - 1; m >= 0; --m) sd = sd * x2 + pk.c64.lo[m];
+  return x2 * x * (1.0 / 3.0 - 0.125 * x + x2 * sd);
+}
+double host_planck_upper(double x) {
+  double y = std::exp(-x), yn = y, s = 0.0;
+  for (int n = 1; n <= 200; ++n) {
+    double rn = 1.0 / n;
+    double t = yn * rn * (x * x * x + rn * (3.0 * x * x + rn * (6.0 * x + 6.0 * rn)));
+    s += t;
+    if (t <= 1e-18 * s) break;
+    yn *= y;
+  }
+  return s;
+}
+double host_band(const PlanckParams& pk, double a, double b) {
+  const double total = std::pow(M_PI, 4) / 15.0;
+  bool alo = a < XSPLIT, blo = b < XSPLIT;
+  if (alo && blo) return host_planck_lower(pk, b) - host_planck_lower(pk, a);
+  if (!alo && !blo) return host_planck_upper(a) - host_planck_upper(b);
+  return (total - host_planck_lower(pk, a)) - host_planck_upper(b);
+}
+double host_w(double x) { return x > 700.0 ? 0.0 : x * x * x * x / std::expm1(x); }
+
+}  // namespace
+struct PlanckTableHost { std::vector<float4> tab; int nu = 0; float u0 = 0.0f; };
+namespace {
+
+void build_planck_table(const fx_params& P, const GroupConst& gc, const PlanckParams& pk,
+                        PlanckTableHost& T) {
+  const int G = P.ngroups;
+  const double u0 = std::floor(std::log2(P.eps_min / PTAB_XMAX));
+  const double u1 = std::ceil(std::log2(P.eps_max / PTAB_XMIN));
+  T.nu = (int)((u1 - u0) * PTAB_PER_OCT) + 2;
+  T.u0 = (float)u0;
+  T.tab.assign((size_t)G * T.nu, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+  const double h = 1.0 / PTAB_PER_OCT;
+  for (int g = 0; g < G; ++g)
+    for (int i = 0; i < T.nu; ++i) {
+      const double Tt = std::exp2(u0 + i * h);
+      const double a = gc.edge[g] / Tt, b = gc.edge[g + 1] / Tt;
+      const double I = host_band(pk, a, b);
+      double L, m;
+      if (I > std::exp2(-200.0)) {
+        L = std::log2(I);
+        m = h * (host_w(a) - host_w(b)) / I;  // h dL/du, L = log2 I, u = log2 T
+      } else {
+        L = -200.0;
+        m = -h * a;  // the band underflows in FP32 here; keep the table smooth and negative
+      }
+      const double k = std::floor(L);
+      T.tab[(size_t)g * T.nu + i] = make_float4((float)(L - k), (float)m, (float)k, 0.0f);
+    }
 }
 
 template <class R> const R* dev_tab(const fx_grid* h, int d) {
@@ -380,6 +446,17 @@ fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
   a.g = h->dg;
   for (int d = 0; d < 3; ++d) a.tab[d] = dev_tab<R>(h, d < h->D ? d : 0);
   a.gc = reinterpret_cast<const GroupConst*>(h->ws + h->off_gc);
+  a.faces = reinterpret_cast<const R*>(h->ws + h->off_faces);
+  a.faces_out = reinterpret_cast<R*>(h->ws + h->off_faces);
+  for (int d = 0; d < 3; ++d) {
+    a.face_off[d] = h->face_off[d];
+    a.uniform[d] = d < h->D && h->uniform[d];
+    for (int e = 0; e < NTAB; ++e)
+      a.urow[d][e] = d < h->D ? (R)h->tab[d][(size_t)e * (h->P.n[d] + 4)] : R(0);
+  }
+  a.ptab.tab = reinterpret_cast<const float4*>(h->ws + h->off_ptab);
+  a.ptab.nu = h->ptab_nu;
+  a.ptab.u0 = h->ptab_u0;
   a.pk = h->pk;
   a.status = reinterpret_cast<unsigned*>(h->ws + h->off_status);
   a.chunk = h->chunk;
@@ -462,6 +539,11 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   h->ncell = 1;
   for (int d = 0; d < P.dims; ++d) h->ncell *= P.n[d];
   h->elem = P.precision == FX_FP64 ? 8 : 4;
+  // kernels index the state and the gas face buffer with 32-bit element offsets
+  if ((double)h->ncell * h->NV >= 4294967295.0 || (double)h->ncell * (3 + P.dims) * P.dims * 1.01 >= 4294967295.0) {
+    delete h;
+    return FX_ERR_UNSUPPORTED;
+  }
 
   DevGrid& g = h->dg;
   g.D = P.dims;
@@ -496,6 +578,13 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   for (int j = 0; j <= MAXG; ++j) h->gc.edge32[j] = (float)h->gc.edge[j];
   for (int j = 0; j < MAXG; ++j) h->gc.efac32[j] = (float)h->gc.efac[j];
   planck_coefficients(h->pk);
+  {
+    PlanckTableHost T;
+    build_planck_table(P, h->gc, h->pk, T);
+    h->ptab.swap(T.tab);
+    h->ptab_nu = T.nu;
+    h->ptab_u0 = T.u0;
+  }
 
   // chunk length along the march axis
   if (P.dims >= 2) {
@@ -507,6 +596,24 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   h->off_status = off; off = align_up(off + 64);
   for (int d = 0; d < P.dims; ++d) { h->off_tab[d] = off; off = align_up(off + h->tab[d].size() * h->elem); }
   h->off_gc = off; off = align_up(off + sizeof(GroupConst));
+  h->off_ptab = off; off = align_up(off + h->ptab.size() * sizeof(float4));
+  {
+    int64_t fo = 0;
+    for (int d = 0; d < P.dims; ++d) {
+      h->face_off[d] = fo;
+      fo += (int64_t)(2 + P.dims + 1) * faces_along(g.n, d);
+    }
+    h->off_faces = off;
+    off = align_up(off + (size_t)fo * h->elem);
+  }
+  // directions whose table rows are all equal (uniform Cartesian spacing) read one row
+  for (int d = 0; d < P.dims; ++d) {
+    const int np = (int)P.n[d] + 4;
+    bool uni = true;
+    for (int e = 0; e < NTAB && uni; ++e)
+      for (int i = 1; i < np && uni; ++i) uni = h->tab[d][(size_t)e * np + i] == h->tab[d][(size_t)e * np];
+    h->uniform[d] = uni;
+  }
   h->state_bytes = (size_t)h->ncell * h->NV * h->elem;
   h->off_A = off; off = align_up(off + h->state_bytes);
   h->off_B = off; off = align_up(off + h->state_bytes);
@@ -522,7 +629,7 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
 
 size_t fx_state_elems(const fx_grid* h) { return h ? (size_t)h->ncell * h->NV : 0; }
 
-int fx_launches_per_step(const fx_grid* h) { return h ? 2 : 0; }
+int fx_launches_per_step(const fx_grid* h) { return h ? 4 : 0; }
 
 fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_stream) {
   if (!h) return FX_ERR_ARG;
@@ -559,6 +666,10 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
     if (e != cudaSuccess) return cuda_fail(h, e, "volume upload");
     off += align_up((size_t)np * sizeof(double));
   }
+  e = cudaMemcpyAsync(h->ws + h->off_ptab, h->ptab.data(), h->ptab.size() * sizeof(float4),
+                      cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "Planck table upload");
   e = cudaMemcpyAsync(h->ws + h->off_gc, &h->gc, sizeof(GroupConst), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "group constants upload");
@@ -737,5 +848,14 @@ int fx_debug_table(const fx_grid* h, int d, double* out, size_t cap) {
   return (int)T.size();
 }
 int fx_debug_ntab(void) { return NTAB; }
+
+int fx_debug_planck_table(const fx_grid* h, float* out, size_t cap, int* nu, float* u0) {
+  if (!h) return -1;
+  if (nu) *nu = h->ptab_nu;
+  if (u0) *u0 = h->ptab_u0;
+  const size_t n = h->ptab.size() * 4;
+  if (out && cap >= n) std::memcpy(out, h->ptab.data(), n * sizeof(float));
+  return (int)n;
+}
 
 }  // extern "C"

@@ -32,11 +32,13 @@ enum TabEntry {
 };
 
 template <class R> struct Tab {
-  const R* p;  // [NTAB][np] for one direction, np = n + 4 (two ghost layers each side)
+  const R* p;    // [NTAB][np] for one direction, np = n + 4 (two ghost layers each side)
   int np;
+  const R* cst;  // the single row of a direction whose rows are all equal (uniform grids), else null
   // rows outside the table (cells of a tile that overhang the grid; never used) are clamped so
   // that every read stays inside the array
   __device__ __forceinline__ R operator()(int e, int ip) const {
+    if (cst) return cst[e];
     ip = ip < 0 ? 0 : (ip >= np ? np - 1 : ip);
     return __ldg(p + e * np + ip);
   }
@@ -71,6 +73,26 @@ __device__ __forceinline__ void recon_parabolic(const Tab<R>& t, int ip, R pm, R
   if (asl == asr) { a = p0; b = p0; return; }
   if (asl < asr) b = a + (p0 - a) * t(T_RHL, ip);  // zero slope at the lower face
   else a = b + (p0 - b) * t(T_RHR, ip);            // zero slope at the upper face
+}
+
+// Coefficients of the linear MC reconstruction of one cell (shared by all its variables and
+// groups): inverse centroid gaps and the face offsets from the centroid.
+template <class R> struct MCCoef { R il, ir, ic, dl, dr; };
+template <class R> __device__ __forceinline__ MCCoef<R> mc_coef(const Tab<R>& t, int ip) {
+  return {t(T_IL, ip), t(T_IR, ip), t(T_IC, ip), t(T_DL, ip), t(T_DR, ip)};
+}
+template <class R>
+__device__ __forceinline__ void recon_linear_c(const MCCoef<R>& c, R pm, R p0, R pp, R& a, R& b) {
+  R sL = (p0 - pm) * c.il;
+  R sR = (pp - p0) * c.ir;
+  R s = R(0);
+  if (sL * sR > R(0)) {
+    R sC = (pp - pm) * c.ic;
+    R m = fmin(fmin(R(2) * fabs(sL), R(2) * fabs(sR)), fabs(sC));
+    s = sC > R(0) ? m : -m;
+  }
+  a = p0 + s * c.dl;
+  b = p0 + s * c.dr;
 }
 
 // Linear reconstruction with the MC limiter on centroid gaps (radiation; reading R1).
@@ -149,9 +171,9 @@ __device__ __forceinline__ void hllc(R gam, const R* L, const R* Rs, R* f, R& vs
   f[1 + D] = (Ek + pk) * uk + Sk * (Es - Ek);
 }
 
-// Reciprocal: IEEE division in FP64, the correctly rounded reciprocal instruction sequence in FP32.
+// Reciprocal: IEEE division in FP64; the hardware approximation (2 ulp) in FP32.
 __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 
 // ---------------------------------------------------------------------------------------------
 // M1 closure (Levermore / Dubroca-Feugeas Eddington factor chi(f) = (3+4f^2)/(5+2 sqrt(4-3f^2)),

@@ -1,0 +1,80 @@
+// Gas face kernel: for every cell face of every direction, the coordinate-moment parabolic
+// reconstruction of the two neighbouring cells (Sec. 5.1) and the HLLC flux with its contact
+// speed (Sec. 5.2).  One thread per face; the four cells of the stencil are read through L1.
+// The stage kernel then uses the fluxes for the gas divergence and the contact speeds to upwind
+// the radiation advection (Eq. 19).
+#pragma once
+#include "fx_device.cuh"
+
+namespace fx {
+
+// number of faces along direction d of an n[0] x n[1] x n[2] grid
+__host__ __device__ inline int64_t faces_along(const int* n, int d) {
+  return (int64_t)(n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2));
+}
+
+// Flux through one face of direction DIR (compile-time, so all index arrays stay in registers).
+template <class R, int D, int DIR>
+__device__ __forceinline__ void gas_face_dir(const StageArgs<R>& A, int64_t f) {
+  constexpr int NG = 2 + D, NW = 2 + D;
+  const auto& g = A.g;
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const int nd = DIR == 0 ? n0 : (DIR == 1 ? n1 : n2);
+  const int ex = n0 + (DIR == 0), ey = n1 + (DIR == 1);
+  const int64_t nf = (int64_t)ex * ey * (n2 + (DIR == 2));
+  if (f >= nf) return;
+  const int i0 = (int)(f % ex), i1 = (int)((f / ex) % ey), i2 = (int)(f / ((int64_t)ex * ey));
+  const int id = DIR == 0 ? i0 : (DIR == 1 ? i1 : i2);
+  const int64_t ncell = g.ncell;
+  const auto& KR = A.k(R(0));
+  // primitives of the cells id-2 .. id+1 along DIR (ghosts from the boundary rules)
+  R W[4][NW];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    bool flip = false;
+    const int cd = min(max(bc_map(id - 2 + m, nd, g.bc_lo[DIR], g.bc_hi[DIR], flip), 0), nd - 1);
+    const int c0 = DIR == 0 ? cd : i0, c1 = DIR == 1 ? cd : i1, c2 = DIR == 2 ? cd : i2;
+    const int64_t ci = ((int64_t)c2 * n1 + c1) * n0 + c0;
+    R u[NG];
+#pragma unroll
+    for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + ci];
+    if (flip) u[1 + DIR] = -u[1 + DIR];
+    const R rho = u[0], irho = frcp(rho);
+    R ke = R(0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) { W[m][2 + q] = u[1 + q] * irho; ke += u[1 + q] * W[m][2 + q]; }
+    W[m][0] = rho;
+    W[m][1] = KR.gm1 * (u[NG - 1] - R(0.5) * ke);
+  }
+  const Tab<R> t{A.tab[DIR], nd + 4, A.uniform[DIR] ? A.urow[DIR] : nullptr};
+  // left state: upper face of cell id-1; right state: lower face of cell id; velocity
+  // component 0 of the rotated states is the face normal
+  R Lr[5], Rr[5], fl[5], vs;
+#pragma unroll
+  for (int v = 0; v < NW; ++v) {
+    R a, b, a2, b2;
+    recon_parabolic(t, bc_pad(id - 1), W[0][v], W[1][v], W[2][v], a, b);
+    recon_parabolic(t, bc_pad(id), W[1][v], W[2][v], W[3][v], a2, b2);
+    const int slot = v < 2 ? v : 2 + (v - 2 - DIR + D) % D;  // rotated position of variable v
+    Lr[slot] = b;
+    Rr[slot] = a2;
+  }
+  hllc<R, D>(KR.gamma, Lr, Rr, fl, vs);
+  R* out = A.faces_out + A.face_off[DIR];
+  out[f] = fl[0];
+#pragma unroll
+  for (int q = 0; q < D; ++q) out[(int64_t)(1 + (DIR + q) % D) * nf + f] = fl[1 + q];
+  out[(int64_t)(NG - 1) * nf + f] = fl[1 + D];
+  out[(int64_t)NG * nf + f] = vs;
+}
+
+template <class R, int D>
+__global__ void __launch_bounds__(256)
+gas_face_kernel(const __grid_constant__ StageArgs<R> A) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (blockIdx.y == 0) gas_face_dir<R, D, 0>(A, f);
+  else if (D >= 2 && blockIdx.y == 1) gas_face_dir<R, D, (D >= 2 ? 1 : 0)>(A, f);
+  else if (D >= 3) gas_face_dir<R, D, (D >= 3 ? 2 : 0)>(A, f);
+}
+
+}  // namespace fx

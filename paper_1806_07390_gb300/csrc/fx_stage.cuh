@@ -43,8 +43,23 @@ struct PlanckParams {
   float wd32[NPLANCK_LO32];
 };
 
+// FP32 Planck band tables: for group g and u = log2 T on nodes u0 + i/PTAB_PER_OCT, the pair
+// (L, h dL/du) with L = log2 Int_{eps_g-1/2/T}^{eps_g+1/2/T} t^3/(e^t-1) dt, built on the host in
+// FP64 and interpolated with cubic Hermite polynomials.
+struct PlanckTable {
+  const float4* tab;  // [G][nu]: (L - floor(L), h dL/du, floor(L), 0)
+  int nu;
+  float u0;
+};
+
 template <class R> struct StageArgs {
   DevGrid g;
+  PlanckTable ptab;
+  const R* faces;      // gas face fluxes and contact speeds [dir][NG+1][faces of dir]
+  R* faces_out;        // the same buffer, written by gas_face_kernel
+  int64_t face_off[3]; // element offset of each direction's block in `faces`
+  R urow[3][NTAB];     // the common table row of a uniform direction
+  int uniform[3];      // direction d has identical table rows (Cartesian grids)
   const R* in;         // state the stencil reads (U^n in stage 1, U^(1) in stage 2)
   const R* base;       // U^n for the stage-2 combination (nullptr in stage 1)
   R* out;              // result (may alias neither input)
@@ -81,6 +96,10 @@ __device__ __forceinline__ int bc_map(int i, int n, int lo, int hi, bool& flip) 
   return i;
 }
 
+}  // namespace fx
+#include "fx_gas.cuh"
+namespace fx {
+
 template <int GP, class V> __device__ __forceinline__ V seg_sum(V v) {
 #pragma unroll
   for (int o = GP / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, GP);
@@ -104,34 +123,64 @@ template <int GP, class LT, class NT>
 struct Coupler {
   const DevGrid& g;
   const PlanckParams& pk;
+  const PlanckTable& ptab;
+  int lane;
   bool has;       // lane < G
   bool top2;      // this lane also evaluates the top edge (G == GP)
   NT rcv, Tm;
   LT K, Sg, cdts, Em, aN, efac, elo, etop;
+
+  // FP32 group energy B_g(T) and T dB_g/dT from the band table of this lane's group
+  __device__ __forceinline__ void planck_tab(float T, float invT, float& B, float& dB) const {
+    const float s = (__log2f(T) - ptab.u0) * float(PTAB_PER_OCT);
+    float I, dLdu;
+    if (s < 0.0f) {
+      I = 0.0f;  // every band of this group is deep in the Wien tail
+      dLdu = 0.0f;
+    } else if (s >= float(ptab.nu - 1)) {
+      // very hot: x = eps/T < 2^-14, so Int t^3/(e^t-1) = x^3/3 - x^4/8 + O(x^5)
+      const float a = (float)elo * invT, b = (float)etop * invT;
+      const float a3 = a * a * a, b3 = b * b * b;
+      I = (b3 - a3) * (1.0f / 3.0f) - (b3 * b - a3 * a) * 0.125f;
+      dLdu = ((a3 * a * (1.0f - 0.5f * a)) - (b3 * b * (1.0f - 0.5f * b))) * frcp(I);
+    } else {
+      const int i = (int)s;
+      const float t = s - (float)i;
+      const float4 p0 = __ldg(ptab.tab + lane * ptab.nu + i);
+      const float4 p1 = __ldg(ptab.tab + lane * ptab.nu + i + 1);
+      const float t2 = t * t, t3 = t2 * t;
+      // node values relative to floor(L) of the left node: small numbers, full FP32 precision
+      const float d1 = (p1.z - p0.z) + p1.x;
+      const float Lr = (2.0f * t3 - 3.0f * t2 + 1.0f) * p0.x + (t3 - 2.0f * t2 + t) * p0.y +
+                       (3.0f * t2 - 2.0f * t3) * d1 + (t3 - t2) * p1.y;
+      const float dLdt = (6.0f * t2 - 6.0f * t) * (p0.x - d1) + (3.0f * t2 - 4.0f * t + 1.0f) * p0.y +
+                         (3.0f * t2 - 2.0f * t) * p1.y;
+      I = ldexpf(exp2f(Lr), (int)p0.z);
+      dLdu = dLdt * float(PTAB_PER_OCT);
+    }
+    const float T2 = T * T, T3 = T2 * T;
+    B = (float)aN * T3 * T * I;
+    dB = (float)aN * T3 * I * (4.0f + dLdu);  // d/dT (T^4 I) = T^3 I (4 + d ln I / d ln T)
+  }
 
   // residual and derivative at T = Tm + dl; this lane's E_g(T) and dE_g/dT
   __device__ __forceinline__ void eval(NT dl, NT& r, NT& dr, LT& Eg, LT& dEg) const {
     LT Tl = (LT)(Tm + dl);
     LT invT = frcp(Tl);
     LT Bq, dBq;
-    if (sizeof(LT) == 8) {
+    if (sizeof(LT) == 4) {
+      float B_, dB_;
+      if (has) planck_tab((float)Tl, (float)invT, B_, dB_);
+      else { B_ = 0.0f; dB_ = 0.0f; }
+      Bq = (LT)B_;
+      dBq = (LT)dB_;
+    } else {
       PlanckEdge<double> lo = planck_edge64((double)(elo * invT), pk.c64);
       PlanckEdge<double> hi;
       hi.Q = __shfl_down_sync(0xffffffffu, lo.Q, 1, GP);
       hi.w = __shfl_down_sync(0xffffffffu, lo.w, 1, GP);
       hi.upper = __shfl_down_sync(0xffffffffu, (int)lo.upper, 1, GP) != 0;
       if (top2) hi = planck_edge64((double)(etop * invT), pk.c64);
-      LT I = (LT)planck_band(lo, hi);
-      LT T3 = Tl * Tl * Tl;
-      Bq = aN * T3 * Tl * I;
-      dBq = aN * T3 * (LT(4) * I + (LT)(lo.w - hi.w));
-    } else {
-      PlanckEdge<float> lo = planck_edge32((float)(elo * invT), pk.lo32, pk.wd32);
-      PlanckEdge<float> hi;
-      hi.Q = __shfl_down_sync(0xffffffffu, lo.Q, 1, GP);
-      hi.w = __shfl_down_sync(0xffffffffu, lo.w, 1, GP);
-      hi.upper = __shfl_down_sync(0xffffffffu, (int)lo.upper, 1, GP) != 0;
-      if (top2) hi = planck_edge32((float)(etop * invT), pk.lo32, pk.wd32);
       LT I = (LT)planck_band(lo, hi);
       LT T3 = Tl * Tl * Tl;
       Bq = aN * T3 * Tl * I;
@@ -152,7 +201,8 @@ struct Coupler {
 
 template <int D, int GP, class LT, class NT>
 __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupConst& gc,
-                                                const PlanckParams& pk, const Consts<NT>& kn,
+                                                const PlanckParams& pk, const PlanckTable& ptab,
+                                                const Consts<NT>& kn,
                                                 const Consts<LT>& kl, bool active,
                                                 int lane, const NT* h, NT& rho, NT* m,
                                                 NT& rhoe, NT& E, NT* F) {
@@ -172,7 +222,7 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
   const NT Esum = seg_sum<GP>(Em);
   const NT rcv = rho * cv;
 
-  Coupler<GP, LT, NT> cp{g, pk, has, (G == GP) && (lane == G - 1), rcv, u_m * frcp(rcv),
+  Coupler<GP, LT, NT> cp{g, pk, ptab, lane, has, (G == GP) && (lane == G - 1), rcv, u_m * frcp(rcv),
                          (LT)(kn.kappa0 * hpow(rho, g.kap_rho_h)), (LT)(kn.sigma0 * rho),
                          kl.cdts, (LT)Em, kl.aN,
                          gc.efac_of(has ? lane : 0, LT(0)), gc.edge_of(lane <= G ? lane : G, LT(0)),
@@ -281,42 +331,59 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
   return st;
 }
 
-// Shared-memory bytes of stage_kernel for G groups (must mirror the carve-up in the kernel).
+// Shared-memory layout of stage_kernel (offsets in elements of R; used by the kernel and by the
+// host to size the launch).
+template <int D, int TX, int TY>
+struct StageLayout {
+  static constexpr int NG = 2 + D, NRV = 1 + D;
+  static constexpr int PX = TX + 4, PY = (D == 3) ? TY + 4 : 1, PC = PX * PY;
+  static constexpr int NSLOT = (D >= 2) ? 4 : 1, TC = TX * TY;
+  static constexpr int NFX = (TX + 1) * TY, NFY = (D == 3) ? TX * (TY + 1) : 0;
+  int st, pk, rbx, rax, rby, ray, rfx, rfy, end;
+  __host__ __device__ explicit StageLayout(int G) {
+    st = 0;
+    pk = st + NSLOT * NRV * PC * G;       // radiation ring [slot][NRV][PC][G]
+    rbx = pk + NSLOT * 2 * PC;            // opacity factors ring [slot][K, S][PC]
+    rax = rbx + NRV * NFX * G;            // left state of every x face [NRV][NFX][G]
+    rby = rax + NRV * TY * G;             // right state of the last x face of each row
+    ray = rby + NRV * NFY * G;            // left state of every y face (3-d)
+    rfx = ray + (D == 3 ? NRV * TX * G : 0);  // right state of the last y face (3-d)
+    rfy = rfx + NRV * NFX * G;            // radiation x-face fluxes [NRV][NFX][G]
+    end = rfy + NRV * NFY * G;            // radiation y-face fluxes (3-d)
+  }
+};
+
 template <class R, int D, int TX, int TY>
 inline size_t stage_smem_bytes(int G) {
-  const int NG = 2 + D, NW = 2 + D, NRV = 1 + D, NPR = NW + 2;
-  const int PX = TX + 4, PY = (D == 3) ? TY + 4 : 1, PC = PX * PY;
-  const int NSLOT = (D >= 2) ? 4 : 1, NIP = (D == 3) ? 2 : 1, TC = TX * TY;
-  const int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-  const int NV = NG + NRV * G;
-  size_t n = (size_t)NSLOT * NV * PC + NSLOT * NPR * PC + NIP * NW * PC * 2 + 2 * NW * TC * 2 +
-             (NG + 1) * NFX + (D == 3 ? (NG + 1) * NFY : 0) + 2 * (NG + 1) * TC + NRV * NFX * G +
-             (D == 3 ? NRV * NFY * G : 0);
-  return n * sizeof(R) + 16 + sizeof(GroupConst);
+  StageLayout<D, TX, TY> L(G);
+  return (size_t)L.end * sizeof(R) + 16 + sizeof(GroupConst);
 }
 
+// ---------------------------------------------------------------------------------------------
+// The radiation/update kernel (one launch per RK stage, after gas_face_kernel).  A block owns a
+// tile of TX x TY cells and marches along the slowest axis; a thread serves one (cell, group).
+// Per plane k, between three barriers:
+//   A  its own radiation values of plane k+2 (prefetched into registers one step ahead) and the
+//      in-plane halo of plane k go to a four-plane shared ring; the cell's opacity factors are
+//      formed from its gas variables (held by lanes 0..NG-1);
+//   B  each cell is reconstructed once per direction: in-plane from shared memory, along the
+//      march from a register window of its own column;
+//   C  the M1/HLL radiation fluxes of the cell's lower faces and of its march face k+1/2, using
+//      the contact speeds of the gas faces (Eq. 19);
+//   D  divergence (gas fluxes from the face buffer), RK combine, coupling, store of plane k.
+// ---------------------------------------------------------------------------------------------
 template <class R, int D, int GP, int TX, int TY, class LT, class NT>
 __global__ void __launch_bounds__(TX * TY * GP, sizeof(R) == 4 ? 3 : 2)
-stage_kernel(const StageArgs<R> A) {
+stage_kernel(const __grid_constant__ StageArgs<R> A) {
+  using LY = StageLayout<D, TX, TY>;
   constexpr int NTH = TX * TY * GP;  // threads per block
-  constexpr int NG = 2 + D;          // gas conserved variables
-  constexpr int NW = 2 + D;          // gas primitives reconstructed: rho, p, vhat_1..D
-  constexpr int NRV = 1 + D;         // radiation variables per group
-  constexpr int NPR = NW + 2;        // + K (kappa0 rho^a T^b) and S (sigma0 rho)
-  constexpr int PX = TX + 4;
-  constexpr int PY = (D == 3) ? TY + 4 : 1;
-  constexpr int PC = PX * PY;        // cells per plane slot (with in-plane halo)
-  constexpr int NSLOT = (D >= 2) ? 4 : 1;
-  constexpr int NIP = (D == 3) ? 2 : 1;  // in-plane directions
-  constexpr int TC = TX * TY;        // tile cells
-  constexpr int NFX = (TX + 1) * TY; // x faces per plane
-  constexpr int NFY = TX * (TY + 1); // y faces per plane (3-d)
-  constexpr int MD = D - 1;          // march direction (D >= 2)
+  constexpr int NG = LY::NG, NRV = LY::NRV;
+  constexpr int PX = LY::PX, PC = LY::PC, TC = LY::TC, NFX = LY::NFX, NFY = LY::NFY;
+  constexpr int MD = D - 1;  // march direction (D >= 2)
 
   const DevGrid& g = A.g;
   const Consts<R>& KR = A.k(R(0));
   const int G = g.G;
-  const int NV = NG + NRV * G;
   const int tid = threadIdx.x;
   const int lane = tid % GP;
   const int tcell = tid / GP;  // tile cell of this thread
@@ -327,137 +394,155 @@ stage_kernel(const StageArgs<R> A) {
   const int nmarch = (D == 1) ? 1 : g.n[MD];
   const int kbeg = (D == 1) ? 0 : ((D == 2) ? blockIdx.y : blockIdx.z) * A.chunk;
   const int kend = (D == 1) ? 1 : min(kbeg + A.chunk, nmarch);
-  const int64_t ncell = g.ncell;
+  const uint32_t ncell = (uint32_t)g.ncell;  // the host keeps every state offset below 2^32
+  const bool has = lane < G;
+  const int gsel = has ? lane : 0;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* st = reinterpret_cast<R*>(smem_raw);                 // [NSLOT][NV][PC] (rad: [v][cell][G])
-  R* pr = st + (int)NSLOT * NV * PC;                     // [NSLOT][NPR][PC]
-  R* grx = pr + NSLOT * NPR * PC;                           // [NIP][NW][PC][2]
-  R* grm = grx + NIP * NW * PC * 2;                         // [2][NW][TC][2]
-  R* gfx = grm + 2 * NW * TC * 2;                           // [NG+1][NFX]
-  R* gfy = gfx + (NG + 1) * NFX;                            // [NG+1][NFY] (3-d)
-  R* gfm = gfy + (D == 3 ? (NG + 1) * NFY : 0);             // [2][NG+1][TC]
-  R* rfx = gfm + 2 * (NG + 1) * TC;                         // [NRV][NFX][G]
-  R* rfy = rfx + NRV * NFX * G;                             // [NRV][NFY][G] (3-d)
-  R* tail = rfy + (D == 3 ? NRV * NFY * G : 0);
+  R* const sm = reinterpret_cast<R*>(smem_raw);
+  const LY L(G);
+  R* const st = sm + L.st;
+  R* const pk = sm + L.pk;
+  R* const rbx = sm + L.rbx;
+  R* const rax = sm + L.rax;
+  R* const rby = sm + L.rby;
+  R* const ray = sm + L.ray;
+  R* const rfx = sm + L.rfx;
+  R* const rfy = sm + L.rfy;
   GroupConst* sgc = reinterpret_cast<GroupConst*>(
-      (reinterpret_cast<uintptr_t>(tail) + 15) & ~static_cast<uintptr_t>(15));
-
+      (reinterpret_cast<uintptr_t>(sm + L.end) + 15) & ~static_cast<uintptr_t>(15));
   for (int i = tid; i < (int)(sizeof(GroupConst) / sizeof(int)); i += NTH)
     reinterpret_cast<int*>(sgc)[i] = reinterpret_cast<const int*>(A.gc)[i];
+  __syncthreads();
 
-  const Tab<R> tx{A.tab[0], nx + 4};
-  const Tab<R> ty{A.tab[D >= 2 ? 1 : 0], (D >= 2 ? ny : nx) + 4};
-  const Tab<R> tz{A.tab[D >= 3 ? 2 : 0], (D >= 3 ? nz : nx) + 4};
+  const Tab<R> tx{A.tab[0], nx + 4, A.uniform[0] ? A.urow[0] : nullptr};
+  const Tab<R> ty{A.tab[D >= 2 ? 1 : 0], (D >= 2 ? ny : nx) + 4,
+                  A.uniform[D >= 2 ? 1 : 0] ? A.urow[D >= 2 ? 1 : 0] : nullptr};
+  const Tab<R> tz{A.tab[D >= 3 ? 2 : 0], (D >= 3 ? nz : nx) + 4,
+                  A.uniform[D >= 3 ? 2 : 0] ? A.urow[D >= 3 ? 2 : 0] : nullptr};
   const Tab<R>& tm = (D == 3) ? tz : ty;  // march-direction table
 
-  // global coordinates of a slot cell (sx, sy in [-2, TX+2) x [-2, TY+2)) on plane k,
-  // mapped into the domain; flips[d] set where a reflecting boundary mirrors direction d.
-  auto map_cell = [&](int sx, int sy, int k, bool* flips) -> int64_t {
+  // global index of slot cell (sx, sy) on plane k, mapped into the domain (Sec. 7.5); flips[d]
+  // is set where a reflecting boundary mirrors direction d.  Tiles may overhang the grid by up
+  // to TX-1 cells; those cells are never used and the clamps keep every read inside the array.
+  auto map_cell = [&](int sx, int sy, int k, bool* flips) -> uint32_t {
     flips[0] = flips[1] = flips[2] = false;
-    // tiles may overhang the grid by up to TX-1 cells; those cells are never used, and the
-    // clamps keep every read inside the array
-    int gx = min(max(bc_map(x0 + sx, nx, g.bc_lo[0], g.bc_hi[0], flips[0]), 0), nx - 1);
-    if (D == 1) return gx;
+    int gx_ = min(max(bc_map(x0 + sx, nx, g.bc_lo[0], g.bc_hi[0], flips[0]), 0), nx - 1);
+    if (D == 1) return gx_;
     if (D == 2) {
-      int gy = min(max(bc_map(k, ny, g.bc_lo[1], g.bc_hi[1], flips[1]), 0), ny - 1);
-      return (int64_t)gy * nx + gx;
+      int gy_ = min(max(bc_map(k, ny, g.bc_lo[1], g.bc_hi[1], flips[1]), 0), ny - 1);
+      return (uint32_t)gy_ * nx + gx_;
     }
-    int gy = min(max(bc_map(y0 + sy, ny, g.bc_lo[1], g.bc_hi[1], flips[1]), 0), ny - 1);
-    int gz = min(max(bc_map(k, nz, g.bc_lo[2], g.bc_hi[2], flips[2]), 0), nz - 1);
-    return ((int64_t)gz * ny + gy) * nx + gx;
+    int gy_ = min(max(bc_map(y0 + sy, ny, g.bc_lo[1], g.bc_hi[1], flips[1]), 0), ny - 1);
+    int gz_ = min(max(bc_map(k, nz, g.bc_lo[2], g.bc_hi[2], flips[2]), 0), nz - 1);
+    return ((uint32_t)gz_ * ny + gy_) * nx + gx_;
   };
-  // slot cell index of (sx, sy)
   auto scell = [&](int sx, int sy) -> int { return (D == 3 ? (sy + 2) * PX : 0) + sx + 2; };
+  auto rad_at = [&](int slot, int v, int sc, int gg) -> R& {
+    return st[((slot * NRV + v) * PC + sc) * G + gg];
+  };
+  // opacity factors K = kappa0 rho^a T^b and S = sigma0 rho of one cell from its gas variables
+  auto opac = [&](const R* u, int slot, int sc) {
+    R rho = u[0], irho = frcp(rho), ke = R(0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) ke += u[1 + q] * u[1 + q];
+    R T = KR.gm1 * (u[NG - 1] - R(0.5) * ke * irho) * irho;
+    pk[(slot * 2 + 0) * PC + sc] = (T > R(0)) ? KR.kappa0 * hpow(rho, g.kap_rho_h) * hpow(T, g.kap_T_h) : R(0);
+    pk[(slot * 2 + 1) * PC + sc] = KR.sigma0 * rho;
+  };
 
-  // Load a list of cells of plane k into ring slot `slot`: gas (one thread per cell, also
-  // converting to primitives) and radiation (one element per thread, coalesced along x, g).
-  // Cell list: `ncl` cells enumerated by `cell_of(i, sx, sy)`.
+  // Load `ncl` cells of plane k (enumerated by cell_of) into ring slot `slot`: gas (one thread
+  // per cell, for the opacity factors), radiation with GP lanes per cell, lane = group.
   auto load_cells = [&](int slot, int k, int ncl, auto cell_of) {
-    R* S = st + (int)slot * NV * PC;
-    R* P = pr + slot * NPR * PC;
     for (int i = tid; i < ncl; i += NTH) {
       int sx, sy;
       cell_of(i, sx, sy);
       bool fl[3];
-      int64_t gc_ = map_cell(sx, sy, k, fl);
-      int sc = scell(sx, sy);
+      const uint32_t gc_ = map_cell(sx, sy, k, fl);
       R u[NG];
 #pragma unroll
       for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + gc_];
-#pragma unroll
-      for (int q = 0; q < D; ++q) if (fl[q]) u[1 + q] = -u[1 + q];
-#pragma unroll
-      for (int v = 0; v < NG; ++v) S[v * PC + sc] = u[v];
-      // primitives (Cartesian scale factors are 1)
-      R rho = u[0];
-      R ke = R(0);
-#pragma unroll
-      for (int q = 0; q < D; ++q) { R vh = u[1 + q] / rho; P[(2 + q) * PC + sc] = vh; ke += R(0.5) * rho * vh * vh; }
-      R p = KR.gm1 * (u[NG - 1] - ke);
-      P[0 * PC + sc] = rho;
-      P[1 * PC + sc] = p;
-      R T = p / rho;
-      R K = (T > R(0)) ? KR.kappa0 * hpow(rho, g.kap_rho_h) * hpow(T, g.kap_T_h) : R(0);
-      P[NW * PC + sc] = K;
-      P[(NW + 1) * PC + sc] = KR.sigma0 * rho;
+      opac(u, slot, scell(sx, sy));
     }
-    // radiation: segment of GP lanes per cell, lane = group (coalesced runs of G per cell)
     for (int t = tid; t < ncl * GP; t += NTH) {
-      const int i = t / GP, gg = t % GP;  // GP is a power of two: shifts and masks
+      const int i = t / GP, gg = t % GP;
       if (gg >= G) continue;
       int sx, sy;
       cell_of(i, sx, sy);
       bool fl[3];
-      int64_t gc_ = map_cell(sx, sy, k, fl);
-      const int so = NG * PC + scell(sx, sy) * G + gg;
+      const uint32_t gc_ = map_cell(sx, sy, k, fl);
+      const int sc = scell(sx, sy);
 #pragma unroll
       for (int v = 0; v < NRV; ++v) {
-        R val = A.in[(int64_t)NG * ncell + ((int64_t)v * ncell + gc_) * G + gg];
+        R val = A.in[NG * ncell + (v * ncell + gc_) * G + gg];
         if (v >= 1 && fl[v - 1]) val = -val;
-        S[so + v * PC * G] = val;
+        rad_at(slot, v, sc, gg) = val;
       }
     }
   };
   auto interior_of = [&](int i, int& sx, int& sy) { sx = i % TX; sy = i / TX; };
-  // in-plane halo: x halo (4 per tile row), then y halo (3-d: 4 per tile column)
-  constexpr int NHALO = 4 * TY + (D == 3 ? 4 * TX : 0);
+  constexpr int NHALO = 4 * TY + (D == 3 ? 4 * TX : 0);  // x halo of every row, y halo (3-d)
   auto halo_of = [&](int i, int& sx, int& sy) {
     if (i < 4 * TY) { int r = i / 4, c = i % 4; sy = r; sx = c < 2 ? c - 2 : TX + (c - 2); }
     else { int j = i - 4 * TY; int c = j / 4, r = j % 4; sx = c; sy = r < 2 ? r - 2 : TY + (r - 2); }
   };
   auto all_of = [&](int i, int& sx, int& sy) { sx = i - 2; sy = 0; };  // 1-d: TX + 4 cells
 
-  // gas primitive reconstruction of slot cell sc along table t at padded index ip; stencil
-  // neighbours at slot cells sm / sp of slots (for the march direction, different slots)
-  auto recon_gas = [&](const Tab<R>& t, int ip, const R* Pm, const R* P0, const R* Pp, int cm, int c0,
-                       int cp, R* ab, int vstride) {
+  const bool cell_in = (x0 + lx < nx) && (D < 3 || y0 + ly < ny);
+  const int gx = x0 + lx, gy = y0 + ly;
+  const int sc_own = scell(lx, ly);
+  // own radiation values (this thread's cell and group) and own gas variable (lanes 0..NG-1)
+  // of plane k, from global memory (mirror ghosts negate the normal components)
+  // the in-plane part of this thread's cell index and its mirror flips are fixed along the march
+  bool own_fl[3] = {false, false, false};
+  const uint32_t own_xy = [&]() {
+    bool f3[3];
+    const uint32_t c = map_cell(lx, ly, D >= 2 ? 0 : 0, f3);
+    own_fl[0] = f3[0];
+    own_fl[1] = D == 3 ? f3[1] : false;
+    return D == 1 ? c : D == 2 ? c % (uint32_t)nx : c % ((uint32_t)nx * ny);
+  }();
+  auto own_idx = [&](int k, bool* fl) -> uint32_t {
+    fl[0] = own_fl[0];
+    fl[1] = own_fl[1];
+    fl[2] = false;
+    if (D == 1) return own_xy;
+    bool fm = false;
+    const int km = min(max(bc_map(k, nmarch, g.bc_lo[MD], g.bc_hi[MD], fm), 0), nmarch - 1);
+    fl[MD] = fm;
+    return own_xy + (uint32_t)km * (D == 2 ? (uint32_t)nx : (uint32_t)nx * ny);
+  };
+  auto own_rad = [&](int k, R* Q) {
+    bool fl[3];
+    const uint32_t gc_ = own_idx(k, fl);
 #pragma unroll
-    for (int v = 0; v < NW; ++v) {
-      R a, b;
-      recon_parabolic(t, ip, Pm[v * PC + cm], P0[v * PC + c0], Pp[v * PC + cp], a, b);
-      ab[v * vstride + 0] = a;
-      ab[v * vstride + 1] = b;
+    for (int v = 0; v < NRV; ++v) {
+      R val = A.in[NG * ncell + (v * ncell + gc_) * G + gsel];
+      Q[v] = (v >= 1 && fl[v - 1]) ? -val : val;
     }
   };
-
-  // HLLC through a face with normal along direction d (0..D-1): L/R primitives in physical
-  // components; writes NG fluxes (rho, momentum components in global order, energy) + v*.
-  auto gas_face = [&](int d, const R* WL, const R* WR, R* out, int stride) {
-    R L[5], Rr[5], f[5], vs;
-    L[0] = WL[0]; L[1] = WL[1]; Rr[0] = WR[0]; Rr[1] = WR[1];
+  const int gvar = lane < NG ? lane : 0;
+  auto own_gas = [&](int k) -> R {
+    bool fl[3];
+    const uint32_t gc_ = own_idx(k, fl);
+    R val = A.in[gvar * ncell + gc_];
+    return (gvar >= 1 && gvar <= D && fl[gvar - 1]) ? -val : val;
+  };
+  // store prefetched own values of plane k into slot `slot`; the cell's lane 0 gathers the gas
+  // variables from lanes 0..NG-1 and forms the opacity factors
+  auto store_own = [&](int slot, const R* Q, R gv) {
+    if (has) {
 #pragma unroll
-    for (int q = 0; q < D; ++q) { L[2 + q] = WL[2 + (d + q) % D]; Rr[2 + q] = WR[2 + (d + q) % D]; }
-    hllc<R, D>(KR.gamma, L, Rr, f, vs);
-    out[0] = f[0];
+      for (int v = 0; v < NRV; ++v) rad_at(slot, v, sc_own, lane) = Q[v];
+    }
+    R u[NG];
 #pragma unroll
-    for (int q = 0; q < D; ++q) out[(1 + (d + q) % D) * stride] = f[1 + q];
-    out[(NG - 1) * stride] = f[1 + D];
-    out[NG * stride] = vs;
+    for (int v = 0; v < NG; ++v) u[v] = __shfl_sync(0xffffffffu, gv, v, GP);
+    if (lane == 0) opac(u, slot, sc_own);
   };
 
-  // radiation flux through a face along direction d for group gg: left cell values (E, Fhat)
-  // reconstructed to its upper face and right cell values to its lower face.
+  // radiation flux through a face along d: QL = left cell's upper-face state, QR = right cell's
+  // lower-face state (E, physical F), chi = total opacity of the two cells (reading R9)
   auto rad_face = [&](int d, const R* QL, const R* QR, R chiL, R chiR, R ell, R vstar, R* out) {
     R PL[3], PR[3];
     m1_row<R, D>(KR.ic2, QL[0], QL + 1, d, PL);
@@ -470,247 +555,262 @@ stage_kernel(const StageArgs<R> A) {
     for (int q = 0; q < D; ++q)
       out[1 + q] = KR.hc2 * (PL[q] + PR[q]) - KR.hc * (QR[1 + q] - QL[1 + q]) + vstar * Qu[1 + q];
   };
-
-  // radiation primitives of a slot cell for group gg: E, Fhat (Cartesian: F)
-  auto rad_vals = [&](const R* S, int sc, int gg, R* Q) {
+  const R ef = R(sgc->efac_of(gsel, R(0)));
+  auto chi_of = [&](int slot, int sc) { return pk[(slot * 2) * PC + sc] * ef + pk[(slot * 2 + 1) * PC + sc]; };
+  auto recon_rad = [&](const MCCoef<R>& c, const R* Qm, const R* Q0, const R* Qp, R* a, R* b) {
 #pragma unroll
-    for (int v = 0; v < NRV; ++v) Q[v] = S[NG * PC + ((int)v * PC + sc) * G + gg];
+    for (int v = 0; v < NRV; ++v) recon_linear_c(c, Qm[v], Q0[v], Qp[v], a[v], b[v]);
+  };
+  auto rad_cell = [&](int slot, int sc, R* Q) {
+#pragma unroll
+    for (int v = 0; v < NRV; ++v) Q[v] = rad_at(slot, v, sc, gsel);
   };
 
-  const bool cell_ok = (x0 + lx < nx) && (D < 3 || y0 + ly < ny);
-  const int gx = x0 + lx, gy = y0 + ly;
-  R rfm_old[NRV];  // radiation flux through the lower march face of the current plane
+  // gas face buffer: lower-face index of cell (gx, gy, k) along direction d
+  // (cells of a tile that overhang the grid use the last column/row; their values are unused)
+  // Positions are clamped to the last cell, face indices along their own direction to the last
+  // face: the first overhanging cell of a tile computes the domain's upper boundary face.
+  const int gxc = min(gx, nx - 1), gyc = min(gy, ny - 1);
+  const int gxf = min(gx, nx), gyf = min(gy, ny);
+  const int fx_nx = nx + 1;
+  auto face_x = [&](int k) -> uint32_t {
+    return D == 1 ? (uint32_t)gxf : D == 2 ? (uint32_t)k * fx_nx + gxf : ((uint32_t)k * ny + gyc) * fx_nx + gxf;
+  };
+  auto face_y3 = [&](int k) -> uint32_t { return ((uint32_t)k * (ny + 1) + gyf) * nx + gxc; };
+  auto face_m = [&](int k) -> uint32_t { return D == 2 ? (uint32_t)k * nx + gxc : ((uint32_t)k * ny + gyc) * nx + gxc; };
+  // number of faces of each direction, and the gas face buffer read
+  const uint32_t nfd[3] = {(uint32_t)(nx + 1) * (D > 1 ? ny : 1) * (D > 2 ? nz : 1),
+                           (uint32_t)nx * (ny + 1) * (D > 2 ? nz : 1), (uint32_t)nx * ny * (nz + 1)};
+  auto gface = [&](int d, int v, uint32_t f) -> R {
+    return __ldg(A.faces + (uint32_t)A.face_off[d] + v * nfd[d] + f);
+  };
+
+  R Q0[NRV] = {}, Q1[NRV] = {}, Qn[NRV] = {};  // own radiation values: plane k, k+1, prefetch
+  R bm0[NRV] = {};                             // own march-direction upper-face state, plane k
+  R rfm_old[NRV] = {};                         // radiation flux through the lower march face
+  R g0 = R(0), g1 = R(0), gn = R(0);           // own gas variable (lanes < NG): k, k+1, prefetch
+  R b0[NRV] = {}, bg0 = R(0);                  // stage-2 base values of plane k
 
   // ---------------------------------------------------------------- prologue
   if (D == 1) {
     load_cells(0, 0, TX + 4, all_of);
+    own_rad(0, Q0);
+    g0 = own_gas(0);
+    __syncthreads();
   } else {
-    for (int k = kbeg - 2; k <= kbeg + 1; ++k) load_cells(k & 3, k, TC, interior_of);
-  }
-  __syncthreads();
-  if (D >= 2) {
-    // march-direction reconstruction of planes kbeg-1 and kbeg, then the face kbeg-1/2
-    for (int i = tid; i < 2 * TC; i += NTH) {
-      int which = i / TC, c = i % TC;
-      int k = kbeg - 1 + which;
-      int sx = c % TX, sy = c / TX;
-      int sc = scell(sx, sy);
-      int ip = bc_pad(k);
-      recon_gas(tm, ip, pr + ((k - 1) & 3) * NPR * PC, pr + (k & 3) * NPR * PC,
-                pr + ((k + 1) & 3) * NPR * PC, sc, sc, sc, grm + ((k & 1) * NW * TC + c) * 2, TC * 2);
-    }
+    for (int k = kbeg - 1; k <= kbeg + 1; ++k) load_cells(k & 3, k, TC, interior_of);
+    R Qm1[NRV], Qm2[NRV];
+    own_rad(kbeg - 2, Qm2);
+    own_rad(kbeg - 1, Qm1);
+    own_rad(kbeg, Q0);
+    own_rad(kbeg + 1, Q1);
+    own_rad(kbeg + 2, Qn);
+    g0 = own_gas(kbeg);
+    g1 = own_gas(kbeg + 1);
+    gn = own_gas(kbeg + 2);
     __syncthreads();
-    for (int c = tid; c < TC; c += NTH) {
-      R WL[NW], WR[NW];
-      const R* ab_lo = grm + (((kbeg - 1) & 1) * NW * TC + c) * 2;
-      const R* ab_hi = grm + ((kbeg & 1) * NW * TC + c) * 2;
-#pragma unroll
-      for (int v = 0; v < NW; ++v) { WL[v] = ab_lo[v * TC * 2 + 1]; WR[v] = ab_hi[v * TC * 2]; }
-      gas_face(MD, WL, WR, gfm + (kbeg & 1) * (NG + 1) * TC + c, TC);
-    }
-    __syncthreads();
-    if (cell_ok && lane < G) {
-      int sc = scell(lx, ly);
-      int k = kbeg;
-      R Qm2[NRV], Qm1[NRV], Q0[NRV], Qp1[NRV], QL[NRV], QR[NRV], tmp[NRV];
-      rad_vals(st + (int)((k - 2) & 3) * NV * PC, sc, lane, Qm2);
-      rad_vals(st + (int)((k - 1) & 3) * NV * PC, sc, lane, Qm1);
-      rad_vals(st + (int)(k & 3) * NV * PC, sc, lane, Q0);
-      rad_vals(st + (int)((k + 1) & 3) * NV * PC, sc, lane, Qp1);
-      int ipl = bc_pad(k - 1), ipr = bc_pad(k);
-#pragma unroll
-      for (int v = 0; v < NRV; ++v) {
-        recon_linear(tm, ipl, Qm2[v], Qm1[v], Q0[v], tmp[v], QL[v]);
-        recon_linear(tm, ipr, Qm1[v], Q0[v], Qp1[v], QR[v], tmp[v]);
-      }
-      const R* Pl = pr + ((k - 1) & 3) * NPR * PC;
-      const R* Pr = pr + (k & 3) * NPR * PC;
-      R ef = R(sgc->efac[lane]);
-      R chiL = Pl[NW * PC + sc] * ef + Pl[(NW + 1) * PC + sc];
-      R chiR = Pr[NW * PC + sc] * ef + Pr[(NW + 1) * PC + sc];
-      R vs = gfm[(k & 1) * (NG + 1) * TC + NG * TC + tcell];
-      rad_face(MD, QL, QR, chiL, chiR, tm(T_ELL, ipr), vs, rfm_old);
-    }
+    // march reconstruction of planes kbeg-1 (upper face) and kbeg, and the face kbeg-1/2
+    R a_[NRV], bprev[NRV];
+    recon_rad(mc_coef(tm, bc_pad(kbeg - 1)), Qm2, Qm1, Q0, a_, bprev);
+    recon_rad(mc_coef(tm, bc_pad(kbeg)), Qm1, Q0, Q1, a_, bm0);
+    const R vs = gface(MD, NG, face_m(kbeg));
+    rad_face(MD, bprev, a_, chi_of((kbeg - 1) & 3, sc_own), chi_of(kbeg & 3, sc_own),
+             tm(T_ELL, bc_pad(kbeg)), vs, rfm_old);
   }
+  if (A.base != nullptr && cell_in) {
+    const uint32_t c0 = D == 1 ? gx : D == 2 ? (uint32_t)kbeg * nx + gx : ((uint32_t)kbeg * ny + gy) * nx + gx;
+#pragma unroll
+    for (int v = 0; v < NRV; ++v) b0[v] = A.base[NG * ncell + (v * ncell + c0) * G + gsel];
+    bg0 = A.base[gvar * ncell + c0];
+  }
+  const int ipx = bc_pad(gx);  // the x-direction table row of this cell
+  // x-direction coefficients of this cell do not change along the march
+  const MCCoef<R> mcx = mc_coef(tx, ipx);
+  const R fxl = tx(T_FL, ipx), fxr = tx(T_FR, ipx), ellx = tx(T_ELL, ipx);
 
   // ---------------------------------------------------------------- march
   for (int k = kbeg; k < kend; ++k) {
     const int s0 = k & 3;
+    // ---- A: plane k+2 (prefetched last step) and the in-plane halo of plane k.  Slot (k+2)&3
+    // held plane k-2, last read in step k-1 before its barrier C; halo positions of slot k are
+    // read only in this step.
     if (D >= 2) {
-      __syncthreads();
-      load_cells((k + 2) & 3, k + 2, TC, interior_of);
+      store_own((k + 2) & 3, Qn, gn);
       load_cells(s0, k, NHALO, halo_of);
     }
-    __syncthreads();
-    const R* S0 = st + (int)s0 * NV * PC;
-    const R* P0 = pr + s0 * NPR * PC;
-    // ---- gas reconstruction: in-plane faces of plane k, march direction of plane k+1
-    {
-      constexpr int NXR = (TX + 2) * TY;
-      constexpr int NYR = (D == 3) ? TX * (TY + 2) : 0;
-      const int NMR = (D >= 2) ? TC : 0;
-      for (int i = tid; i < NXR + NYR + NMR; i += NTH) {
-        if (i < NXR) {
-          int sx = i % (TX + 2) - 1, sy = i / (TX + 2);
-          int sc = scell(sx, sy);
-          recon_gas(tx, bc_pad(x0 + sx), P0, P0, P0, sc - 1, sc, sc + 1, grx + sc * 2, PC * 2);
-        } else if (i < NXR + NYR) {
-          int j = i - NXR;
-          int sx = j % TX, sy = j / TX - 1;
-          int sc = scell(sx, sy);
-          recon_gas(ty, bc_pad(y0 + sy), P0, P0, P0, sc - PX, sc, sc + PX, grx + (NW * PC + sc) * 2, PC * 2);
-        } else {
-          int c = i - NXR - NYR;
-          int sc = scell(c % TX, c / TX);
-          int k1 = k + 1;
-          recon_gas(tm, bc_pad(k1), pr + (k & 3) * NPR * PC, pr + (k1 & 3) * NPR * PC,
-                    pr + ((k1 + 1) & 3) * NPR * PC, sc, sc, sc, grm + ((k1 & 1) * NW * TC + c) * 2, TC * 2);
-        }
-      }
+    // gas face data of this plane: the cell's lower faces and the march face k+1/2
+    const R vsx = gface(0, NG, face_x(k));
+    const R vsx1 = (lx == TX - 1 && gx < nx) ? gface(0, NG, face_x(k) + 1) : R(0);
+    const R vsm = (D >= 2) ? gface(MD, NG, face_m(k + 1)) : R(0);
+    R vsy = R(0), vsy1 = R(0);
+    if (D == 3) {
+      vsy = gface(1, NG, face_y3(k));
+      vsy1 = (ly == TY - 1 && gy < ny) ? gface(1, NG, face_y3(k) + nx) : R(0);
     }
-    __syncthreads();
-    // ---- gas fluxes: x faces, y faces (3-d), march face k+1/2
-    {
-      const int NMF = (D >= 2) ? TC : 0;
-      const int NYF = (D == 3) ? NFY : 0;
-      for (int i = tid; i < NFX + NYF + NMF; i += NTH) {
-        R WL[NW], WR[NW];
-        if (i < NFX) {
-          int fx = i % (TX + 1), fy = i / (TX + 1);
-          int scl = scell(fx - 1, fy), scr = scell(fx, fy);
-          const R* ab = grx;
-#pragma unroll
-          for (int v = 0; v < NW; ++v) { WL[v] = ab[(v * PC + scl) * 2 + 1]; WR[v] = ab[(v * PC + scr) * 2]; }
-          gas_face(0, WL, WR, gfx + i, NFX);
-        } else if (i < NFX + NYF) {
-          int j = i - NFX;
-          int fx = j % TX, fy = j / TX;
-          int scl = scell(fx, fy - 1), scr = scell(fx, fy);
-          const R* ab = grx + NW * PC * 2;
-#pragma unroll
-          for (int v = 0; v < NW; ++v) { WL[v] = ab[(v * PC + scl) * 2 + 1]; WR[v] = ab[(v * PC + scr) * 2]; }
-          gas_face(1, WL, WR, gfy + j, NFY);
-        } else {
-          int c = i - NFX - NYF;
-          const R* ab_lo = grm + ((k & 1) * NW * TC + c) * 2;
-          const R* ab_hi = grm + (((k + 1) & 1) * NW * TC + c) * 2;
-#pragma unroll
-          for (int v = 0; v < NW; ++v) { WL[v] = ab_lo[v * TC * 2 + 1]; WR[v] = ab_hi[v * TC * 2]; }
-          gas_face(MD, WL, WR, gfm + ((k + 1) & 1) * (NG + 1) * TC + c, TC);
-        }
-      }
-    }
-    __syncthreads();
-    // ---- radiation fluxes (lane = group)
-    R rfm_new[NRV];
-    if (cell_ok && lane < G) {
-      const int gg = lane;
-      const R ef = R(sgc->efac[gg]);
-      auto chi_of = [&](const R* P, int sc) { return P[NW * PC + sc] * ef + P[(NW + 1) * PC + sc]; };
-      // x faces: lower face of this cell (and the upper face for the last tile column)
-      for (int side = 0; side < ((lx == TX - 1 || gx == nx - 1) ? 2 : 1); ++side) {
-        int fx = lx + side;  // face index: lower face of slot cell fx
-        int scl = scell(fx - 1, ly), scr = scell(fx, ly);
-        R Qa[NRV], Qb[NRV], Qc[NRV], Qd[NRV], QL[NRV], QR[NRV], tmp[NRV];
-        rad_vals(S0, scl - 1, gg, Qa);
-        rad_vals(S0, scl, gg, Qb);
-        rad_vals(S0, scr, gg, Qc);
-        rad_vals(S0, scr + 1, gg, Qd);
-        int ipl = bc_pad(x0 + fx - 1), ipr = bc_pad(x0 + fx);
-#pragma unroll
-        for (int v = 0; v < NRV; ++v) {
-          recon_linear(tx, ipl, Qa[v], Qb[v], Qc[v], tmp[v], QL[v]);
-          recon_linear(tx, ipr, Qb[v], Qc[v], Qd[v], QR[v], tmp[v]);
-        }
-        int f = ly * (TX + 1) + fx;
-        R out[NRV];
-        rad_face(0, QL, QR, chi_of(P0, scl), chi_of(P0, scr), tx(T_ELL, ipr), gfx[NG * NFX + f], out);
-#pragma unroll
-        for (int v = 0; v < NRV; ++v) rfx[((int)v * NFX + f) * G + gg] = out[v];
-      }
+    R gnet = R(0);
+    if (cell_in) {  // (an overhanging cell's upper face would lie past the last face)
+      const uint32_t fxk = face_x(k);
+      gnet = gface(0, gvar, fxk + 1) * fxr - gface(0, gvar, fxk) * fxl;
       if (D == 3) {
-        for (int side = 0; side < ((ly == TY - 1 || gy == ny - 1) ? 2 : 1); ++side) {
-          int fy = ly + side;
-          int scl = scell(lx, fy - 1), scr = scell(lx, fy);
-          R Qa[NRV], Qb[NRV], Qc[NRV], Qd[NRV], QL[NRV], QR[NRV], tmp[NRV];
-          rad_vals(S0, scl - PX, gg, Qa);
-          rad_vals(S0, scl, gg, Qb);
-          rad_vals(S0, scr, gg, Qc);
-          rad_vals(S0, scr + PX, gg, Qd);
-          int ipl = bc_pad(y0 + fy - 1), ipr = bc_pad(y0 + fy);
-#pragma unroll
-          for (int v = 0; v < NRV; ++v) {
-            recon_linear(ty, ipl, Qa[v], Qb[v], Qc[v], tmp[v], QL[v]);
-            recon_linear(ty, ipr, Qb[v], Qc[v], Qd[v], QR[v], tmp[v]);
-          }
-          int f = fy * TX + lx;
-          R out[NRV];
-          rad_face(1, QL, QR, chi_of(P0, scl), chi_of(P0, scr), ty(T_ELL, ipr), gfy[NG * NFY + f], out);
-#pragma unroll
-          for (int v = 0; v < NRV; ++v) rfy[((int)v * NFY + f) * G + gg] = out[v];
-        }
+        const uint32_t fyk = face_y3(k);
+        gnet = gnet + (gface(1, gvar, fyk + nx) * ty(T_FR, bc_pad(gy)) - gface(1, gvar, fyk) * ty(T_FL, bc_pad(gy)));
       }
-      if (D >= 2) {
-        // march face k+1/2: cells k-1 .. k+2 of this column
-        int sc = scell(lx, ly);
-        R Qa[NRV], Qb[NRV], Qc[NRV], Qd[NRV], QL[NRV], QR[NRV], tmp[NRV];
-        rad_vals(st + (int)((k - 1) & 3) * NV * PC, sc, gg, Qa);
-        rad_vals(S0, sc, gg, Qb);
-        rad_vals(st + (int)((k + 1) & 3) * NV * PC, sc, gg, Qc);
-        rad_vals(st + (int)((k + 2) & 3) * NV * PC, sc, gg, Qd);
-        int ipl = bc_pad(k), ipr = bc_pad(k + 1);
-#pragma unroll
-        for (int v = 0; v < NRV; ++v) {
-          recon_linear(tm, ipl, Qa[v], Qb[v], Qc[v], tmp[v], QL[v]);
-          recon_linear(tm, ipr, Qb[v], Qc[v], Qd[v], QR[v], tmp[v]);
-        }
-        R vs = gfm[((k + 1) & 1) * (NG + 1) * TC + NG * TC + tcell];
-        rad_face(MD, QL, QR, chi_of(P0, sc), chi_of(pr + ((k + 1) & 3) * NPR * PC, sc), tm(T_ELL, ipr), vs, rfm_new);
-      }
+      if (D >= 2)
+        gnet = gnet + (gface(MD, gvar, face_m(k + 1)) * tm(T_FR, bc_pad(k)) - gface(MD, gvar, face_m(k)) * tm(T_FL, bc_pad(k)));
     }
     __syncthreads();
-    // ---- update: divergence, RK combine, coupling, store
+    R Q2[NRV];
+#pragma unroll
+    for (int v = 0; v < NRV; ++v) Q2[v] = Qn[v];
+    const R g2 = gn;  // own gas variable of plane k+2 (gn is refilled with plane k+3 below)
+    // ---- B: reconstructions
+    R ax[NRV], bx[NRV], am1[NRV], bm1[NRV], ay[NRV], by[NRV];
     {
-      const int sc = scell(lx, ly);
-      const int ipx = gx + 2, ipy = gy + 2, ipm = k + 2;
-      const R fxl = tx(T_FL, ipx), fxr = tx(T_FR, ipx);
+      R Qa[NRV], Qb[NRV];
+      rad_cell(s0, sc_own - 1, Qa);
+      rad_cell(s0, sc_own + 1, Qb);
+      recon_rad(mcx, Qa, Q0, Qb, ax, bx);
+      if (has) {
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1) + lx + 1) * G + lane] = bx[v];
+      }
+      if (lx == 0) {  // halo cell -1: its upper-face state is the left state of face 0
+        R Qc[NRV], ta[NRV], tb[NRV];
+        rad_cell(s0, sc_own - 2, Qc);
+        recon_rad(mc_coef(tx, bc_pad(gx - 1)), Qc, Qa, Q0, ta, tb);
+        if (has) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * G + lane] = tb[v];
+        }
+      }
+      if (lx == TX - 1) {  // halo cell TX: its lower-face state is the right state of face TX
+        R Qc[NRV], ta[NRV], tb[NRV];
+        rad_cell(s0, sc_own + 2, Qc);
+        recon_rad(mc_coef(tx, bc_pad(gx + 1)), Q0, Qb, Qc, ta, tb);
+        if (has) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * G + lane] = ta[v];
+        }
+      }
+    }
+    if (D == 3) {
+      R Qa[NRV], Qb[NRV];
+      rad_cell(s0, sc_own - PX, Qa);
+      rad_cell(s0, sc_own + PX, Qb);
+      recon_rad(mc_coef(ty, bc_pad(gy)), Qa, Q0, Qb, ay, by);
+      if (has) {
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rby[(v * NFY + (ly + 1) * TX + lx) * G + lane] = by[v];
+      }
+      if (ly == 0) {
+        R Qc[NRV], ta[NRV], tb[NRV];
+        rad_cell(s0, sc_own - 2 * PX, Qc);
+        recon_rad(mc_coef(ty, bc_pad(gy - 1)), Qc, Qa, Q0, ta, tb);
+        if (has) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) rby[(v * NFY + lx) * G + lane] = tb[v];
+        }
+      }
+      if (ly == TY - 1) {
+        R Qc[NRV], ta[NRV], tb[NRV];
+        rad_cell(s0, sc_own + 2 * PX, Qc);
+        recon_rad(mc_coef(ty, bc_pad(gy + 1)), Q0, Qb, Qc, ta, tb);
+        if (has) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) ray[(v * TX + lx) * G + lane] = ta[v];
+        }
+      }
+    }
+    if (D >= 2) recon_rad(mc_coef(tm, bc_pad(k + 1)), Q0, Q1, Q2, am1, bm1);
+    __syncthreads();
+    // ---- C: radiation face fluxes
+    R rfm_new[NRV] = {};
+    {
+      const int fx = ly * (TX + 1) + lx;
+      R QL[NRV], out[NRV];
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) QL[v] = rbx[(v * NFX + fx) * G + gsel];
+      rad_face(0, QL, ax, chi_of(s0, sc_own - 1), chi_of(s0, sc_own), ellx, vsx, out);
+      if (has) {
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx) * G + lane] = out[v];
+      }
+      if (lx == TX - 1) {
+        R QR[NRV];
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) QR[v] = rax[(v * TY + ly) * G + gsel];
+        rad_face(0, bx, QR, chi_of(s0, sc_own), chi_of(s0, sc_own + 1), tx(T_ELL, ipx + 1), vsx1, out);
+        if (has) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx + 1) * G + lane] = out[v];
+        }
+      }
+    }
+    if (D == 3) {
+      const int fy = ly * TX + lx;
+      R QL[NRV], out[NRV];
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) QL[v] = rby[(v * NFY + fy) * G + gsel];
+      rad_face(1, QL, ay, chi_of(s0, sc_own - PX), chi_of(s0, sc_own), ty(T_ELL, bc_pad(gy)), vsy, out);
+      if (has) {
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy) * G + lane] = out[v];
+      }
+      if (ly == TY - 1) {
+        R QR[NRV];
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) QR[v] = ray[(v * TX + lx) * G + gsel];
+        rad_face(1, by, QR, chi_of(s0, sc_own), chi_of(s0, sc_own + PX), ty(T_ELL, bc_pad(gy + 1)), vsy1, out);
+        if (has) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy + TX) * G + lane] = out[v];
+        }
+      }
+    }
+    if (D >= 2)
+      rad_face(MD, bm0, am1, chi_of(s0, sc_own), chi_of((k + 1) & 3, sc_own), tm(T_ELL, bc_pad(k + 1)),
+               vsm, rfm_new);
+    __syncthreads();
+    // prefetch: own values of plane k+3 and the stage-2 base of plane k+1
+    R b1[NRV] = {}, bg1 = R(0);
+    if (D >= 2 && k + 1 < kend) {
+      own_rad(k + 3, Qn);
+      gn = own_gas(k + 3);
+      if (A.base != nullptr && cell_in) {
+        const uint32_t c1 = D == 2 ? (uint32_t)(k + 1) * nx + gx : ((uint32_t)(k + 1) * ny + gy) * nx + gx;
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) b1[v] = A.base[NG * ncell + (v * ncell + c1) * G + gsel];
+        bg1 = A.base[gvar * ncell + c1];
+      }
+    }
+    // ---- D: update: divergence, RK combine, coupling, store
+    {
+      const int ipy = gy + 2, ipm = k + 2;
       R fyl = R(0), fyr = R(0), fml = R(0), fmr = R(0);
       if (D == 3) { fyl = ty(T_FL, ipy); fyr = ty(T_FR, ipy); }
       if (D >= 2) { fml = tm(T_FL, ipm); fmr = tm(T_FR, ipm); }
       const int fxa = ly * (TX + 1) + lx;
       const int fya = ly * TX + lx;
-      const int64_t cidx = (D == 1) ? (int64_t)gx
-                         : (D == 2) ? (int64_t)k * nx + gx
-                                    : ((int64_t)k * ny + gy) * nx + gx;
+      const uint32_t cidx = (D == 1) ? (uint32_t)gx
+                          : (D == 2) ? (uint32_t)k * nx + gx
+                                     : ((uint32_t)k * ny + gy) * nx + gx;
       const R dt = KR.dt;
-      // gas (every lane of the cell computes the same values)
+      const bool stage2 = A.base != nullptr;
+      // gas: lane v < NG updates variable v, then the segment shares the cell's gas state
+      R ug = g0 + dt * (-gnet);
+      if (stage2) ug = KR.alpha * bg0 + KR.beta * ug;
       NT gas[NG];
 #pragma unroll
-      for (int v = 0; v < NG; ++v) {
-        R net = (gfx[v * NFX + fxa + 1] * fxr - gfx[v * NFX + fxa] * fxl);
-        if (D == 3) net = net + (gfy[v * NFY + fya + TX] * fyr - gfy[v * NFY + fya] * fyl);
-        if (D >= 2) {
-          const R* gm_hi = gfm + ((k + 1) & 1) * (NG + 1) * TC;
-          const R* gm_lo = gfm + (k & 1) * (NG + 1) * TC;
-          net = net + (gm_hi[v * TC + tcell] * fmr - gm_lo[v * TC + tcell] * fml);
-        }
-        R u1 = S0[v * PC + sc] + dt * (-net);
-        if (A.base != nullptr && cell_ok) u1 = KR.alpha * A.base[v * ncell + cidx] + KR.beta * u1;
-        gas[v] = (NT)u1;
-      }
-      // radiation of this lane's group
+      for (int v = 0; v < NG; ++v) gas[v] = (NT)__shfl_sync(0xffffffffu, ug, v, GP);
       NT E = NT(0), F[3] = {NT(0), NT(0), NT(0)};
-      if (lane < G && cell_ok) {
+      if (has && cell_in) {
 #pragma unroll
         for (int v = 0; v < NRV; ++v) {
-          R net = (rfx[((int)v * NFX + fxa + 1) * G + lane] * fxr - rfx[((int)v * NFX + fxa) * G + lane] * fxl);
-          if (D == 3) net = net + (rfy[((int)v * NFY + fya + TX) * G + lane] * fyr - rfy[((int)v * NFY + fya) * G + lane] * fyl);
+          R net = rfx[(v * NFX + fxa + 1) * G + lane] * fxr - rfx[(v * NFX + fxa) * G + lane] * fxl;
+          if (D == 3) net = net + (rfy[(v * NFY + fya + TX) * G + lane] * fyr - rfy[(v * NFY + fya) * G + lane] * fyl);
           if (D >= 2) net = net + (rfm_new[v] * fmr - rfm_old[v] * fml);
-          R u1 = S0[NG * PC + ((int)v * PC + sc) * G + lane] + dt * (-net);
-          if (A.base != nullptr) {
-            R b = A.base[(int64_t)NG * ncell + ((int64_t)v * ncell + cidx) * G + lane];
-            u1 = KR.alpha * b + KR.beta * u1;
-          }
+          R u1 = Q0[v] + dt * (-net);
+          if (stage2) u1 = KR.alpha * b0[v] + KR.beta * u1;
           if (v == 0) E = (NT)u1; else F[v - 1] = (NT)u1;
         }
       }
@@ -719,36 +819,46 @@ stage_kernel(const StageArgs<R> A) {
         NT h[3] = {NT(1), NT(1), NT(1)};
         NT m[3] = {gas[1], D > 1 ? gas[2] : NT(0), D > 2 ? gas[3] : NT(0)};
         NT rho = gas[0], rhoe = gas[NG - 1];
-        stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.k(NT(0)), A.k(LT(0)), cell_ok, lane, h,
+        stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.ptab, A.k(NT(0)), A.k(LT(0)), cell_in, lane, h,
                                             rho, m, rhoe, E, F);
         gas[0] = rho;
 #pragma unroll
         for (int q = 0; q < D; ++q) gas[1 + q] = m[q];
         gas[NG - 1] = rhoe;
       }
-      if (cell_ok) {
-        bool bad = false;
+      if (cell_in) {
+        NT chk = NT(0);  // a NaN or inf anywhere in the cell's outputs makes this sum non-finite
         if (lane < NG) {
           NT val = gas[0];
 #pragma unroll
           for (int v = 1; v < NG; ++v) if (lane == v) val = gas[v];
-          A.out[(int64_t)lane * ncell + cidx] = R(val);
-          bad |= !isfinite(val);
+          A.out[lane * ncell + cidx] = R(val);
+          chk += val;
         }
-        if (lane < G) {
+        if (has) {
 #pragma unroll
           for (int v = 0; v < NRV; ++v) {
             NT val = v == 0 ? E : F[v - 1];
-            A.out[(int64_t)NG * ncell + ((int64_t)v * ncell + cidx) * G + lane] = R(val);
-            bad |= !isfinite(val);
+            A.out[NG * ncell + (v * ncell + cidx) * G + lane] = R(val);
+            chk += val * NT(0);
           }
         }
-        if (bad) stbits |= ST_NONFINITE;
+        if (!isfinite(chk)) stbits |= ST_NONFINITE;
         if (stbits) atomicOr(A.status, stbits);
       }
     }
+    // slide the march window
 #pragma unroll
-    for (int v = 0; v < NRV; ++v) rfm_old[v] = (D >= 2) ? rfm_new[v] : R(0);
+    for (int v = 0; v < NRV; ++v) {
+      Q0[v] = Q1[v];
+      Q1[v] = Q2[v];
+      bm0[v] = bm1[v];
+      rfm_old[v] = (D >= 2) ? rfm_new[v] : R(0);
+      b0[v] = b1[v];
+    }
+    g0 = g1;
+    g1 = g2;
+    bg0 = bg1;
   }
 }
 

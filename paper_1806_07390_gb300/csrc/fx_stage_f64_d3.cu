@@ -13,6 +13,15 @@ static cudaError_t launch_gp(const StageArgs<double>& a, cudaStream_t s) {
   e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
+  {
+    // gas faces first (same stream): fluxes and contact speeds of every face of every direction
+    int64_t nfmax = 0;
+    for (int d = 0; d < 3; ++d) nfmax = nfmax > faces_along(a.g.n, d) ? nfmax : faces_along(a.g.n, d);
+    dim3 gg((unsigned)((nfmax + 255) / 256), 3, 1);
+    gas_face_kernel<double, 3><<<gg, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   dim3 grid((a.g.n[0] + TS::TX - 1) / TS::TX, 1, 1);
   if (3 == 2) grid.y = (a.g.n[1] + a.chunk - 1) / a.chunk;
   if (3 == 3) {

@@ -48,7 +48,7 @@ def test_create_validates_parameters(L):
     st, h, ws = create(pb)
     assert st == 0 and ws > 0
     assert L.fx_state_elems(h) == pb.state_size()
-    assert L.fx_launches_per_step(h) == 2
+    assert L.fx_launches_per_step(h) == 4
     # workspace size covers two FP64 states
     assert ws >= 2 * pb.state_size() * 8
     L.fx_grid_destroy(h)
@@ -138,3 +138,35 @@ def test_host_tables_reproduce_oracle_reconstruction(L, maker):
                 ra, rb = oracle.recon_cell(pb, d, i, pm, p0, pp, kind=kind)
                 assert abs(a - ra) < 1e-13 and abs(b - rb) < 1e-13, (d, i, kind, a, ra, b, rb)
     L.fx_grid_destroy(h)
+
+
+def test_fp32_planck_tables_interpolate_the_band_integrals(L):
+    # the host-built FP32 band tables, interpolated with the device's cubic Hermite formula,
+    # reproduce the oracle's Planck band integrals to FP32 precision over the table's range
+    pb, _ = W.kh_2d(nx=16, ny=16, ngroups=16)
+    st, h, _ = create(pb)
+    assert st == 0
+    nu, u0 = ctypes.c_int(), ctypes.c_float()
+    n = L.fx_debug_planck_table(h, None, 0, ctypes.byref(nu), ctypes.byref(u0))
+    buf = np.zeros(n, dtype=np.float32)
+    L.fx_debug_planck_table(h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n,
+                            ctypes.byref(nu), ctypes.byref(u0))
+    tab = buf.reshape(pb.ngroups, nu.value, 4).astype(np.float64)
+    edges = pb.eps_min * (pb.eps_max / pb.eps_min) ** (np.arange(pb.ngroups + 1) / pb.ngroups)
+    rng = np.random.default_rng(3)
+    worst = 0.0
+    for T in np.exp(rng.uniform(np.log(0.02), np.log(50.0), 60)):
+        s = (np.log2(T) - u0.value) * 32.0
+        i = int(s)
+        t = s - i
+        for g in range(pb.ngroups):
+            p0, p1 = tab[g, i], tab[g, i + 1]
+            d1 = (p1[2] - p0[2]) + p1[0]
+            Lg = p0[2] + ((2 * t ** 3 - 3 * t ** 2 + 1) * p0[0] + (t ** 3 - 2 * t ** 2 + t) * p0[1] +
+                          (3 * t ** 2 - 2 * t ** 3) * d1 + (t ** 3 - t ** 2) * p1[1])
+            ref = oracle.lib().orc_planck_band(edges[g] / T, edges[g + 1] / T)
+            if ref < 1e-30:
+                continue
+            worst = max(worst, abs(2.0 ** Lg / ref - 1.0))
+    L.fx_grid_destroy(h)
+    assert worst < 3e-7, worst
