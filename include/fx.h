@@ -160,6 +160,28 @@ int fx_debug_ntab(void);
  * the number of floats (copied only when cap is large enough), or -1 for a null handle. */
 int fx_debug_planck_table(const fx_grid* h, float* out, size_t cap, int* nu, float* u0);
 
+/* Equilibrium initialisation for callers that cannot allocate device memory: code running inside
+ * a host that owns the allocator (a plugin, or a process under a memory pool that forbids
+ * cudaMalloc) may have no workspace to stage host data in.  This call allocates nothing: it
+ * stages the host primitives in a fixed device array that the library defines at file scope,
+ * of FX_NOALLOC_STAGE_BYTES bytes (64 MiB, held by every GPU that loads the library until the
+ * process exits; 1 KiB of it holds the group constants), then builds the state exactly as
+ * fx_state_init_equilibrium does, but into the caller's device buffer `state` (fx_state_elems()
+ * elements of state_precision, FX_FP64 or FX_FP32) on the given CUDA stream (NULL for the
+ * default stream).  The paper has no counterpart; this is an interface convenience.
+ *   - h may be unbound (no workspace): only its parameters and host tables are used.
+ *   - prim: host array [3+dims][ncell] as for fx_state_init_equilibrium; at most
+ *     FX_NOALLOC_STAGE_BYTES - 1024 bytes, otherwise FX_ERR_UNSUPPORTED with a message.
+ *   - The first call on a device resolves the array's device address on the current device;
+ *     make that first call before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind; calls that overlap on the
+ *     GPU (other streams, other host threads) race on it.  Order them on one stream.
+ *   - Asynchronous: the copies are enqueued on the stream; the host array may be reused when
+ *     the call returns (pageable source memory makes the staging copy synchronous). */
+#define FX_NOALLOC_STAGE_BYTES (64u << 20)
+fx_status fx_state_init_equilibrium_noalloc(fx_grid* h, const double* prim, void* state,
+                                            int state_precision, void* cuda_stream);
+
 const char* fx_last_error(const fx_grid* h);
 void fx_clear_error(fx_grid* h);
 void fx_grid_destroy(fx_grid* h);

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -858,4 +859,73 @@ int fx_debug_planck_table(const fx_grid* h, float* out, size_t cap, int* nu, flo
   return (int)n;
 }
 
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Initialisation without allocation.  fx_state_init_equilibrium stages host primitives in the
+// workspace's second state buffer; this variant stages them, together with the group constants,
+// in a file-scope device array of fixed size that every GPU loading the library holds until the
+// process exits.  Host code must not use the array's name as a device address, so each device
+// resolves it once with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // FX_NOALLOC_STAGE_BYTES in fx.h
+static __device__ __align__(256) unsigned char g_noalloc_stage[kNoAllocBytes];
+constexpr size_t kNoAllocGcBytes = 1024;  // GroupConst slot at the start of the array
+static_assert(sizeof(GroupConst) <= kNoAllocGcBytes, "group constants do not fit their slot");
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" fx_status fx_state_init_equilibrium_noalloc(fx_grid* h, const double* prim, void* state,
+                                                      int state_precision, void* cuda_stream) {
+  if (!h || !prim || !state) return FX_ERR_ARG;
+  if (state_precision != FX_FP64 && state_precision != FX_FP32) return fail(h, FX_ERR_ARG, "state precision must be FX_FP64 or FX_FP32");
+  const size_t pbytes = (size_t)(3 + h->D) * h->ncell * sizeof(double);
+  if (pbytes > kNoAllocBytes - kNoAllocGcBytes)
+    return fail(h, FX_ERR_UNSUPPORTED,
+                "fx_state_init_equilibrium_noalloc: the primitives (" + std::to_string(pbytes) +
+                    " bytes) exceed its fixed device staging array (" +
+                    std::to_string(kNoAllocBytes - kNoAllocGcBytes) + " bytes)");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(h, FX_ERR_UNSUPPORTED, "device ordinal beyond the supported range");
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // once per device, with that device current
+      e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_stage);
+      if (e != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        return cuda_fail(h, e, "cudaGetSymbolAddress of the staging array");
+      }
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  unsigned char* stage = static_cast<unsigned char*>(base);
+  e = cudaMemcpyAsync(stage, &h->gc, sizeof(GroupConst), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(stage + kNoAllocGcBytes, prim, pbytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "staging copy");
+  const int64_t nt = h->ncell * (h->G + 1);
+  const int nb = (int)((nt + 255) / 256);
+  const GroupConst* gc = reinterpret_cast<const GroupConst*>(stage);
+  const double* dprim = reinterpret_cast<const double*>(stage + kNoAllocGcBytes);
+  if (state_precision == FX_FP64)
+    k_init_equilibrium<double><<<nb, 256, 0, s>>>(dprim, static_cast<double*>(state), h->dg, gc,
+                                                  nullptr, nullptr, h->pk, h->P.geom);
+  else
+    k_init_equilibrium<float><<<nb, 256, 0, s>>>(dprim, static_cast<float*>(state), h->dg, gc,
+                                                 nullptr, nullptr, h->pk, h->P.geom);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "equilibrium initialisation (no-alloc)");
+  return FX_OK;
+}
+
+extern "C" {
 }  // extern "C"

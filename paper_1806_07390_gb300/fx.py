@@ -28,7 +28,7 @@ NTOTALS = 6
 EXPORTS = ["fx_grid_create", "fx_bind_workspace", "fx_state_elems", "fx_state_upload",
            "fx_state_init_equilibrium", "fx_step", "fx_sync", "fx_conserved_totals",
            "fx_state_download", "fx_launches_per_step", "fx_debug_table", "fx_debug_ntab",
-           "fx_debug_planck_table",
+           "fx_debug_planck_table", "fx_state_init_equilibrium_noalloc",
            "fx_last_error", "fx_clear_error", "fx_grid_destroy"]
 
 
@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
         L.fx_debug_ntab.argtypes = []
         L.fx_debug_planck_table.argtypes = [vp, ctypes.POINTER(ctypes.c_float), sz,
                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+        L.fx_state_init_equilibrium_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.fx_state_init_equilibrium_noalloc.restype = ctypes.c_int
         L.fx_last_error.argtypes = [vp]
         L.fx_last_error.restype = ctypes.c_char_p
         L.fx_clear_error.argtypes = [vp]
