@@ -5,7 +5,7 @@ the grid once), for the FP32 form (headline `value`) and the plain FP64 path (`f
 the 2-d periodic Kelvin-Helmholtz workload, 1024 x 1024 cells x 16 groups (synthetic seeded
 input; inputs are larger than L2, so no flush is needed between timed steps).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 
 One JSON line on rank 0.  Under torchrun each rank runs an independent replica (weak scaling);
 the stage update is not decomposed across GPUs in this build.
@@ -31,7 +31,7 @@ METRIC = "zone-group updates/s per RK stage"
 UNIT = "zone-group-stages/s"
 # DRAM bytes per stage launch from the committed ncu captures (profiles/); None until captured
 # for the current kernel.
-TRAFFIC_PER_LAUNCH = {"fp32": None, "fp32n64": None, "fp64": None}
+TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32": None, "fp32n64": None, "fp64": None}}
 
 
 def load_peaks():
@@ -116,6 +116,7 @@ def time_form(pb, prim, steps, warmup, dist):
         torch.distributed.barrier()
     s = g.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.kernel_timing(True)  # per-kernel CUDA events on the launching stream, inside the timed region
     e0.record(s)
     for _ in range(steps):
         g.step(pb.dt, 1)
@@ -123,13 +124,15 @@ def time_form(pb, prim, steps, warmup, dist):
     e1.synchronize()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    kt = g.kernel_times()
+    g.kernel_timing(False)
     st = g.status()
     if dist:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     launches = g.launches_per_step() * steps
-    return g, ms, st, launches
+    return g, ms, st, launches, kt
 
 
 def time_e2e(g, pb, steps, warmup):
@@ -163,14 +166,44 @@ def time_e2e(g, pb, steps, warmup):
     return sec, n * h_in.element_size(), n * h_out.element_size()
 
 
-def cpu_baseline(pb_full, prim_full, budget_s=15.0):
-    """The FP64 oracle, as it stands, on the host cores: a 256 x 256-cell window of the same
-    workload (same spacing, c and dt, outflow window edges), stepped until ~budget_s."""
-    import oracle
+# Workloads: generator, default headline precision form, description, and the oracle sample used
+# for the CPU baseline (window start, interior size, halo) or None for the whole grid.
+WORKLOADS = {
+    "kh2d": (W.kh_2d, "fp32", "2-d periodic Kelvin-Helmholtz, 1024x1024 cells x 16 groups",
+             ((384, 384), (248, 248), 4)),
+    "lognormal3d": (W.lognormal_3d, "fp32n64",
+                    "3-d periodic lognormal density, 256^3 cells x 12 groups",
+                    ((100, 100, 100), (40, 40, 40), 4)),
+    "sph2d": (W.spherical_2d, "fp32",
+              "2-d spherical (r, theta) log-r atmosphere, 640x128 cells x 20 groups", None),
+    "blobs2d": (W.blobs_2d, "fp32", "2-d density blobs, 512x512 cells x 8 groups",
+                ((128, 128), (248, 248), 4)),
+    "sod1d": (W.sod_1d, "fp64", "1-d radiating Sod tube, 512 cells x 12 groups", None),
+}
+FORM_DTYPE = {"fp32": "f32", "fp32n64": "f32+f64-newton", "fp64": "f64"}
+FORM_NOTE = {"fp32": "FP32 state, fluxes and coupling (anchored FP32 Newton), FP64 totals",
+             "fp32n64": "FP32 state and fluxes, FP64 Newton and energy bookkeeping, FP64 totals",
+             "fp64": "FP64 throughout"}
+
+
+def oracle_sample(pb64, prim, spec):
     from tests import helpers as H
 
+    if spec is None:
+        return pb64, prim, f"whole {'x'.join(str(n) for n in pb64.n[:pb64.dims])} grid"
+    start, size, halo = spec
+    sub, sprim = H.window(pb64, prim, start, size, halo)
+    return sub, sprim, (f"{'x'.join(str(n) for n in sub.n[:sub.dims])}-cell window "
+                        f"({halo}-cell halo, outflow edges) of the full grid")
+
+
+def cpu_baseline(pb64, prim, spec, budget_s=15.0):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the same workload
+    (same spacing, c and dt), stepped until ~budget_s."""
+    import oracle
+
     cores = os.cpu_count() or 1
-    sub, sprim = H.window(pb_full, prim_full, (384, 384), (256 - 8, 256 - 8), 4)
+    sub, sprim, what = oracle_sample(pb64, prim, spec)
     s = oracle.init_equilibrium(sub, sprim)
     t0 = time.perf_counter()
     nst = 0
@@ -182,21 +215,24 @@ def cpu_baseline(pb_full, prim_full, budget_s=15.0):
     sec = time.perf_counter() - t0
     zgs = sub.ncell * sub.ngroups * 2 * nst
     return {"value": zgs / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{sub.n[0]}x{sub.n[1]} cells x {sub.ngroups} groups window of the "
-                      f"1024^2 workload, {nst} FP64 steps, OpenMP over cells"}
+            "sample": f"{what} x {sub.ngroups} groups, {nst} FP64 steps, OpenMP over cells"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    pb, prim = W.kh_2d(precision="fp64")
+    gen, form, desc, spec = WORKLOADS[args.workload]
+    pb, prim = gen(precision="fp64")
+    if spec is not None and args.workload == "kh2d":
+        spec = ((384, 384), (120, 120), 4)  # smaller sample: each timed step stays ~1 s
+    elif spec is not None and args.workload == "lognormal3d":
+        spec = ((100, 100, 100), (24, 24, 24), 4)
     steps, warmup = args.steps, args.warmup
     import oracle
 
-    from tests import helpers as H
     cores = os.cpu_count() or 1
-    sub, sprim = H.window(pb, prim, (384, 384), (120, 120), 4)
+    sub, sprim, what = oracle_sample(pb, prim, spec)
     s = oracle.init_equilibrium(sub, sprim)
     for _ in range(warmup):
         s, _ = oracle.run(sub, s, sub.dt, 1, nthreads=cores)
@@ -210,11 +246,10 @@ def run_reference(args):
             "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * sec / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "kh2d 1024x1024 cells x 16 groups, periodic (oracle sample "
-                                   f"{sub.n[0]}x{sub.n[1]} window)", "precision": "fp64"},
+            "config": {"workload": f"{args.workload}: {desc} (oracle sample: {what})",
+                       "precision": "fp64"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{sub.n[0]}x{sub.n[1]} cells x 16 groups window, "
-                                       f"{steps} steps"},
+                             "sample": f"{what} x {sub.ngroups} groups, {steps} FP64 steps"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -225,8 +260,14 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="kh2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--form", default=None, choices=["fp32", "fp32n64", "fp64"],
+                    help="precision form of the headline value (default: the workload's)")
+    ap.add_argument("--forms", default="fp32,fp32n64,fp64",
+                    help="extra precision forms timed beside the headline (comma list)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -243,60 +284,76 @@ def main():
         torch.distributed.init_process_group("nccl")
     dev = torch.cuda.current_device()
 
-    pb32, prim = W.kh_2d(precision="fp32")
-    forms = {"fp32n64": W.kh_2d(precision="fp32n64")[0]}
-    if not args.no_fp64:
-        forms["fp64"] = W.kh_2d(precision="fp64")[0]
-    pb64 = W.kh_2d(precision="fp64")[0]
-    zg = pb32.ncell * pb32.ngroups
+    gen, form0, desc, spec = WORKLOADS[args.workload]
+    head = args.form or form0
+    pbh, prim = gen(precision=head)
+    forms = {}
+    for name in [f for f in args.forms.split(",") if f and f != head]:
+        if name == "fp64" and args.no_fp64:
+            continue
+        forms[name] = gen(precision=name)[0]
+    zg = pbh.ncell * pbh.ngroups
     peak, peak_kind = load_peaks()
 
     results = {}
     with ClockSampler(dev) as clk:
-        g32, ms32, st32, launches32 = time_form(pb32, prim, args.steps, args.warmup, dist)
+        gh, msh, sth, launchesh, kth = time_form(pbh, prim, args.steps, args.warmup, dist)
         for name, pbf in forms.items():
-            gf, msf, stf, lf = time_form(pbf, prim, args.steps, args.warmup, dist)
-            results[name] = (msf, stf, lf)
+            gf, msf, stf, lf, ktf = time_form(pbf, prim, args.steps, args.warmup, dist)
+            results[name] = (msf, stf, lf, ktf)
             gf.close()
     clocks = clk.summary()
 
-    sec32 = ms32 / 1e3
-    value = world * zg * 2 * args.steps / sec32
-    nv = pb32.nvar
+    sech = msh / 1e3
+    value = world * zg * 2 * args.steps / sech
+    nv = pbh.nvar
 
-    def roofline(kind, sec, steps):
+    def roofline(kind, kt):
+        """Radiation/update kernel (the dominant one): algorithmic bytes per launch over its
+        average CUDA-event launch duration in the timed region."""
         b = 8 if kind == "fp64" else 4
-        per_launch = 2.5 * b * nv * pb32.ncell  # algorithmic bytes per stage launch (2.5 N_v words)
-        achieved = per_launch / (sec / (2 * steps)) / 1e9
+        per_launch = 2.5 * b * nv * pbh.ncell  # 2.5 N_v words per cell per stage
+        avg_s = kt["stage_ms"] / max(kt["stage_launches"], 1) / 1e3
+        achieved = per_launch / avg_s / 1e9
+        trafficd = TRAFFIC_PER_LAUNCH.get(args.workload, {})
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(kind),
-                "peak_kind": peak_kind, "bytes_per_launch": per_launch}
+                "frac": achieved / peak, "traffic": trafficd.get(kind),
+                "peak_kind": peak_kind, "kernel": "stage_kernel (radiation/update)",
+                "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3,
+                "face_kernel_avg_ms": kt["face_ms"] / max(kt["face_launches"], 1),
+                "stage_share_of_step": kt["stage_ms"] / max(kt["stage_ms"] + kt["face_ms"], 1e-30)}
 
     e2e_steps = max(5, args.steps // 4)
-    e2e_sec, h2d, d2h = time_e2e(g32, pb32, e2e_steps, 2)
-    g32.close()
+    if args.no_e2e:
+        e2e_sec, h2d, d2h = float("nan"), 0, 0
+    else:
+        e2e_sec, h2d, d2h = time_e2e(gh, pbh, e2e_steps, 2)
+    gh.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "warmup": args.warmup, "ms_per_step": msh / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPE[head],
             "data": "synthetic",
-            "config": {"workload": "kh2d: 2-d periodic Kelvin-Helmholtz, 1024x1024 cells x 16 "
-                                   "groups, FP32 form", "cells": pb32.ncell, "groups": pb32.ngroups,
-                       "l2": "inputs larger than L2 (no flush)", "precision": "fp32",
-                       "parallelism": f"replicas{world}"},
-            "roofline": roofline("fp32", sec32, args.steps),
+            "config": {"workload": f"{args.workload}: {desc}, {head} form", "cells": pbh.ncell,
+                       "groups": pbh.ngroups, "form": FORM_NOTE[head],
+                       "l2": ("inputs larger than L2 (no flush)"
+                              if pbh.state_size() * (8 if head == "fp64" else 4) * 2 > 129e6
+                              else "state fits in L2 (no flush): L2-resident figure"),
+                       "precision": head, "parallelism": f"replicas{world}"},
+            "roofline": roofline(head, kth),
             "e2e": {"value": world * zg * 2 * e2e_steps / e2e_sec, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches32 + sum(r[2] for r in results.values()),
-            "clocks": clocks, "status": int(st32), "forms": {}}
-    for name, (msf, stf, lf) in results.items():
+            "gpu_launches": launchesh + sum(r[2] for r in results.values()),
+            "clocks": clocks, "status": int(sth), "forms": {}}
+    for name, (msf, stf, lf, ktf) in results.items():
         secf = msf / 1e3
         line["forms"][name] = {"value": world * zg * 2 * args.steps / secf, "unit": UNIT,
-                               "ms_per_step": msf / args.steps,
-                               "roofline": roofline(name, secf, args.steps), "status": int(stf),
-                               "fp32_speedup": msf / ms32}
+                               "ms_per_step": msf / args.steps, "note": FORM_NOTE[name],
+                               "roofline": roofline(name, ktf), "status": int(stf),
+                               "speedup_of_headline": msf / msh}
     if rank == 0 and not args.no_cpu and not dist:
-        line["cpu_baseline"] = cpu_baseline(pb64, prim)
+        pb64 = gen(precision="fp64")[0]
+        line["cpu_baseline"] = cpu_baseline(pb64, prim, spec)
     elif rank == 0 and not args.no_cpu and dist:
         line["cpu_baseline"] = None
     if rank == 0:

@@ -148,6 +148,19 @@ fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is
  * kernel and the radiation/update kernel). */
 int fx_launches_per_step(const fx_grid* h);
 
+/* Per-kernel device timing (instrumentation, not part of the method).  While enabled, every
+ * stage that fx_step enqueues records three CUDA events on the bound stream: before the gas face
+ * kernel, between it and the radiation/update kernel, and after the latter.
+ * fx_kernel_timing_enable(h, on) switches this on or off and discards what was recorded.
+ * fx_kernel_timing_read(h, out) waits for the last recorded event and writes
+ * out[0] = total milliseconds of the radiation/update kernel, out[1] = its launches,
+ * out[2] = total milliseconds of the gas face kernel, out[3] = its launches, summed over the
+ * stages recorded since enable or the previous read; it then starts a new record.  Each duration
+ * includes the launch gap between the bracketing events (~1 us).  Both return FX_ERR_ARG for a
+ * null handle or output and FX_ERR_CUDA when an event call fails. */
+fx_status fx_kernel_timing_enable(fx_grid* h, int on);
+fx_status fx_kernel_timing_read(fx_grid* h, double out[4]);
+
 /* Host-side inspection (no GPU needed): the FP64 reconstruction/divergence table of direction d,
  * fx_debug_ntab() entries of n[d] + 4 rows each (padded cells -2 .. n+1), entry-major.  Returns
  * the number of doubles (copied only when cap is large enough), or -1 for a bad argument. */

@@ -124,6 +124,11 @@ struct fx_grid {
   size_t off_faces = 0;           // gas face buffer [dir][NG+1][faces of dir]
   int64_t face_off[3] = {0, 0, 0};
   bool uniform[3] = {false, false, false};
+  // per-kernel timing: one event triple (before the face kernel, between, after the stage
+  // kernel) per stage launch since timing was enabled; events are pooled across reads
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  size_t nev = 0;
 };
 
 namespace {
@@ -212,11 +217,65 @@ void build_table(const fx_params& P, int d, std::vector<double>& T) {
     put(T_IC, ip, 1.0 / (h * (mu1[2] - mu1[0])));
     put(T_DL, ip, h * (xl - mu1[1]));
     put(T_DR, ip, h * (xr - mu1[1]));
-    // divergence factors and the optical-depth length of the lower face (Cartesian)
-    put(T_FL, ip, 1.0 / h);
-    put(T_FR, ip, 1.0 / h);
-    put(T_ELL, ip, h * (mu1[1] - mu1[0]));
+    // divergence factors, optical-depth length, scale factors, connection coefficients
     put(T_VOL, ip, mo[ip + 1].w0);
+    const double xl_abs = xc[ip + 1] - 0.5 * h, xr_abs = xc[ip + 1] + 0.5 * h;
+    const double ell = h * (mu1[1] - mu1[0]);  // centroid gap of the lower face
+    for (int e : {T_XS, T_X1, T_X2, T_XH, T_HA, T_HB}) put(e, ip, 1.0);
+    for (int e : {T_GA, T_GB, T_GC}) put(e, ip, 0.0);
+    if (P.geom == FX_CART || d >= 2) {
+      for (int e : {T_FL, T_FR, T_FL1, T_FR1, T_FL2, T_FR2}) put(e, ip, 1.0 / h);
+      put(T_ELL, ip, ell);
+      continue;
+    }
+    if (d == 0) {  // radius r(x1): faces carry r^2 (scalar), r^2 dr/dx1 (r comp.), r^3 (theta comp.)
+      const double Vr = mo[ip + 1].w0;
+      const double rl = rmap(P.map1, xl_abs), rr = rmap(P.map1, xr_abs);
+      const double ql = drmap(P.map1, xl_abs), qr = drmap(P.map1, xr_abs);
+      put(T_FL, ip, rl * rl / Vr);
+      put(T_FR, ip, rr * rr / Vr);
+      put(T_FL1, ip, rl * rl * ql / Vr);
+      put(T_FR1, ip, rr * rr * qr / Vr);
+      put(T_FL2, ip, rl * rl * rl / Vr);
+      put(T_FR2, ip, rr * rr * rr / Vr);
+      put(T_ELL, ip, ell * ql);
+      // theta faces of this radial cell: Int r dr/dx1, Int r (dr/dx1)^2, Int r^2 dr/dx1 over it
+      auto gl = [&](auto f) {  // 8-point Gauss-Legendre on the cell
+        static const double xg[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+        static const double wg[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+        double sum = 0.0, c = 0.5 * (xl_abs + xr_abs), hw = 0.5 * h;
+        for (int k = 0; k < 4; ++k) sum += wg[k] * (f(c + hw * xg[k]) + f(c - hw * xg[k]));
+        return sum * hw;
+      };
+      const double ra = gl([&](double x) { return std::fabs(rmap(P.map1, x)) * drmap(P.map1, x); });
+      const double rb = gl([&](double x) { double q = drmap(P.map1, x); return std::fabs(rmap(P.map1, x)) * q * q; });
+      const double rc = gl([&](double x) { double r = rmap(P.map1, x); return r * r * drmap(P.map1, x); });
+      put(T_XS, ip, ra / Vr);
+      put(T_X1, ip, rb / Vr);
+      put(T_X2, ip, rc / Vr);
+      put(T_XH, ip, rc / ra);
+      // cell scale factors sqrt<g_11>, sqrt<g_22> (identity theta map: g_22 = r^2)
+      put(T_HA, ip, std::sqrt(gl([&](double x) { double q = drmap(P.map1, x), r = rmap(P.map1, x); return q * q * std::fabs(r * r * q); }) / Vr));
+      put(T_HB, ip, std::sqrt(gl([&](double x) { double q = drmap(P.map1, x), r = rmap(P.map1, x); return r * r * std::fabs(r * r * q); }) / Vr));
+      const double g221 = gl([&](double x) { double q = drmap(P.map1, x), r = rmap(P.map1, x); return q / r * std::fabs(r * r * q); }) / Vr;
+      const double g122 = -gl([&](double x) { double q = drmap(P.map1, x), r = rmap(P.map1, x); return r / q * std::fabs(r * r * q); }) / Vr;
+      // pressure balance in r: <Gamma^1_11> = dA_1/dV - <Gamma^2_21> - <Gamma^3_31>
+      const double g111 = (rr * rr * qr - rl * rl * ql) / Vr - 2.0 * g221;
+      put(T_GA, ip, g111);
+      put(T_GB, ip, g221);
+      put(T_GC, ip, g122);
+    } else {  // polar angle theta = x2 (identity map), weight |sin theta|
+      const double Th = mo[ip + 1].w0;
+      const double sl = std::fabs(std::sin(xl_abs)), sr = std::fabs(std::sin(xr_abs));
+      for (int e : {T_FL, T_FL1, T_FL2}) put(e, ip, sl / Th);
+      for (int e : {T_FR, T_FR1, T_FR2}) put(e, ip, sr / Th);
+      put(T_ELL, ip, ell);
+      // Eq. 79f: <cot theta>, Int cos over the cell with the weight's sign (mirror cells flip it)
+      const double sgn = std::sin(xc[ip + 1]) >= 0.0 ? 1.0 : -1.0;
+      const double g332 = sgn * (std::sin(xr_abs) - std::sin(xl_abs)) / Th;
+      put(T_GA, ip, (sr - sl) / Th - g332);  // Eq. 85: <Gamma^2_22> = dA_2/dV - <Gamma^3_32>
+      put(T_GB, ip, g332);
+    }
   }
 }
 
@@ -469,24 +528,39 @@ fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
   const Consts<float> kf1 = make_consts<float>(h, dt, dt, 0.0, f32n);
   const Consts<double> kd2 = make_consts<double>(h, dt, 0.5 * dt, 0.5, f32n);
   const Consts<float> kf2 = make_consts<float>(h, dt, 0.5 * dt, 0.5, f32n);
+  auto stage = [&](const char* what) -> fx_status {
+    cudaEvent_t e3[3] = {nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    if (h->timing) {
+      while (h->ev.size() < h->nev + 3) {
+        cudaEvent_t x;
+        e = cudaEventCreate(&x);
+        if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
+        h->ev.push_back(x);
+      }
+      for (int q = 0; q < 3; ++q) e3[q] = h->ev[h->nev + q];
+      h->nev += 3;
+      e = cudaEventRecord(e3[0], h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
+    }
+    switch (h->D) {
+      case 1: e = launch_stage<R, 1, NT>(a, h->GP, h->stream, e3[1]); break;
+      case 2: e = launch_stage<R, 2, NT>(a, h->GP, h->stream, e3[1]); break;
+      default: e = launch_stage<R, 3, NT>(a, h->GP, h->stream, e3[1]); break;
+    }
+    if (e == cudaSuccess && e3[2]) e = cudaEventRecord(e3[2], h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    return FX_OK;
+  };
   for (int s = 0; s < nsteps; ++s) {
     // stage 1: U1 = U0 + dt L(U0), then the interaction with dt
     a.in = A; a.base = nullptr; a.out = B; a.dts = dt; a.alpha = 0.0; a.kd = kd1; a.kf = kf1;
-    cudaError_t e;
-    switch (h->D) {
-      case 1: e = launch_stage<R, 1, NT>(a, h->GP, h->stream); break;
-      case 2: e = launch_stage<R, 2, NT>(a, h->GP, h->stream); break;
-      default: e = launch_stage<R, 3, NT>(a, h->GP, h->stream); break;
-    }
-    if (e != cudaSuccess) return cuda_fail(h, e, "stage 1 launch");
+    fx_status st = stage("stage 1 launch");
+    if (st != FX_OK) return st;
     // stage 2: U = U0/2 + (U1 + dt L(U1))/2, then the interaction with dt/2 (reading R10)
     a.in = B; a.base = A; a.out = A; a.dts = 0.5 * dt; a.alpha = 0.5; a.kd = kd2; a.kf = kf2;
-    switch (h->D) {
-      case 1: e = launch_stage<R, 1, NT>(a, h->GP, h->stream); break;
-      case 2: e = launch_stage<R, 2, NT>(a, h->GP, h->stream); break;
-      default: e = launch_stage<R, 3, NT>(a, h->GP, h->stream); break;
-    }
-    if (e != cudaSuccess) return cuda_fail(h, e, "stage 2 launch");
+    st = stage("stage 2 launch");
+    if (st != FX_OK) return st;
   }
   return FX_OK;
 }
@@ -510,7 +584,13 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
     }
     if ((P.bc_lo[d] == FX_PERIODIC) != (P.bc_hi[d] == FX_PERIODIC)) return FX_ERR_ARG;
   }
-  if (P.geom != FX_CART) return FX_ERR_UNSUPPORTED;  // spherical geometry: not in this build yet
+  if (P.geom != FX_CART && P.geom != FX_SPH) return FX_ERR_ARG;
+  if (P.geom == FX_SPH) {
+    // spherical (r, theta) grids: 2-d, radial map identity or exponential, theta in [0, pi]
+    if (P.dims != 2 || (P.map1 != FX_MAP_ID && P.map1 != FX_MAP_EXP)) return FX_ERR_UNSUPPORTED;
+    if (P.x_lo[1] < 0.0 || P.x_hi[1] > M_PI + 1e-12) return FX_ERR_ARG;
+    if (P.map1 == FX_MAP_ID && !(P.x_lo[0] > 0.0)) return FX_ERR_UNSUPPORTED;
+  }
   if (P.precision != FX_FP64 && P.precision != FX_FP32 && P.precision != FX_FP32_F64NEWTON)
     return FX_ERR_ARG;
   if (P.rad_recon_order != 1) return FX_ERR_UNSUPPORTED;
@@ -588,9 +668,17 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   }
 
   // chunk length along the march axis
+  // (32 planes; halved down to 8 while the grid would give fewer than two waves of blocks at
+  // three resident blocks on each of 152 SMs: short chunks re-read more halo planes)
   if (P.dims >= 2) {
-    int nm = (int)P.n[P.dims - 1];
-    h->chunk = std::min(nm, 32);
+    const int nm = (int)P.n[P.dims - 1];
+    const int TC = 256 / h->GP;
+    const int TX = P.dims == 3 ? (TC >= 16 ? TC / 4 : TC / 2) : TC, TY = TC / TX;
+    int64_t tiles = (P.n[0] + TX - 1) / TX;
+    if (P.dims == 3) tiles *= (P.n[1] + TY - 1) / TY;
+    int chunk = 32;
+    while (chunk > 8 && tiles * ((nm + chunk - 1) / chunk) < 2 * 3 * 152) chunk /= 2;
+    h->chunk = std::min(nm, chunk);
   }
   // workspace layout
   size_t off = 0;
@@ -833,8 +921,36 @@ void fx_clear_error(fx_grid* h) {
   }
 }
 
+fx_status fx_kernel_timing_enable(fx_grid* h, int on) {
+  if (!h) return FX_ERR_ARG;
+  h->timing = on != 0;
+  h->nev = 0;
+  return FX_OK;
+}
+
+fx_status fx_kernel_timing_read(fx_grid* h, double out[4]) {
+  if (!h || !out) return FX_ERR_ARG;
+  for (int q = 0; q < 4; ++q) out[q] = 0.0;
+  if (h->nev == 0) return FX_OK;
+  cudaError_t e = cudaEventSynchronize(h->ev[h->nev - 1]);
+  if (e != cudaSuccess) return cuda_fail(h, e, "timing read");
+  for (size_t i = 0; i < h->nev; i += 3) {
+    float face = 0.f, stage = 0.f;
+    e = cudaEventElapsedTime(&face, h->ev[i], h->ev[i + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&stage, h->ev[i + 1], h->ev[i + 2]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "timing read");
+    out[0] += stage;
+    out[1] += 1.0;
+    out[2] += face;
+    out[3] += 1.0;
+  }
+  h->nev = 0;
+  return FX_OK;
+}
+
 void fx_grid_destroy(fx_grid* h) {
   if (!h) return;
+  for (cudaEvent_t x : h->ev) cudaEventDestroy(x);
   if (h->h_status) cudaFreeHost(h->h_status);
   delete h;
 }

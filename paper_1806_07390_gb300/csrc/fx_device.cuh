@@ -28,6 +28,18 @@ enum TabEntry {
   T_FL, T_FR,           // divergence factor of the lower / upper face (area / volume)
   T_ELL,                // optical-depth length of the lower face (R9)
   T_VOL,                // 1-d volume factor of the cell
+  // Separable finite-volume geometry (Sec. 4, Eq. 8; Appendix A).  For the faces of this
+  // direction: area/volume factor of the lower/upper face for scalar fluxes (T_FL/T_FR above),
+  // for the flux of covariant component 0 (T_FL1/T_FR1) and of component 1 (T_FL2/T_FR2).
+  T_FL1, T_FR1, T_FL2, T_FR2,
+  // Factors this direction contributes to the faces of the other direction (scalar, component
+  // 0, component 1) and to their optical-depth length.
+  T_XS, T_X1, T_X2, T_XH,
+  // Scale factors h of components 0 and 1 (their product over directions gives the cell's).
+  T_HA, T_HB,
+  // Volume-averaged connection coefficients carried by this direction (Appendix D): radial
+  // <Gamma^1_11>, <Gamma^2_21> = <Gamma^3_31>, <Gamma^1_22>; polar <Gamma^2_22>, <Gamma^3_32>.
+  T_GA, T_GB, T_GC,
   NTAB
 };
 

@@ -27,6 +27,11 @@ __device__ __forceinline__ void gas_face_dir(const StageArgs<R>& A, int64_t f) {
   const int id = DIR == 0 ? i0 : (DIR == 1 ? i1 : i2);
   const int64_t ncell = g.ncell;
   const auto& KR = A.k(R(0));
+  // curvilinear grids: the cell scale factors turn covariant momentum into physical velocity
+  const bool sph = g.geom != 0;
+  const Tab<R> t0{A.tab[0], n0 + 4, A.uniform[0] ? A.urow[0] : nullptr};
+  const Tab<R> t1{A.tab[D >= 2 ? 1 : 0], (D >= 2 ? n1 : n0) + 4,
+                  A.uniform[D >= 2 ? 1 : 0] ? A.urow[D >= 2 ? 1 : 0] : nullptr};
   // primitives of the cells id-2 .. id+1 along DIR (ghosts from the boundary rules)
   R W[4][NW];
 #pragma unroll
@@ -39,6 +44,11 @@ __device__ __forceinline__ void gas_face_dir(const StageArgs<R>& A, int64_t f) {
 #pragma unroll
     for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + ci];
     if (flip) u[1 + DIR] = -u[1 + DIR];
+    if (sph) {  // physical components m_q / h_q (the 2-d spherical grid is r x theta)
+      const int cr = DIR == 0 ? id - 2 + m : i0, ct = DIR == 1 ? id - 2 + m : i1;
+      u[1] *= frcp(t0(T_HA, bc_pad(cr)) * t1(T_HA, bc_pad(ct)));
+      if (D >= 2) u[2] *= frcp(t0(T_HB, bc_pad(cr)) * t1(T_HB, bc_pad(ct)));
+    }
     const R rho = u[0], irho = frcp(rho);
     R ke = R(0);
 #pragma unroll

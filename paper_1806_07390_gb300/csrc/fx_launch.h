@@ -14,10 +14,11 @@ template <int D, int GP> struct TileShape {
   static constexpr int TY = TC / TX;
 };
 
-// Enqueue one stage (state type R, D dimensions, Newton/bookkeeping type NT); returns the CUDA
-// error of the launch.
+// Enqueue one stage (state type R, D dimensions, Newton/bookkeeping type NT): the gas face
+// kernel, then the radiation/update kernel, both on stream s.  When `mid` is non-null it is
+// recorded between the two launches (per-kernel timing).  Returns the CUDA error of the launch.
 template <class R, int D, class NT>
-cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s);
+cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid);
 
 // Dynamic shared memory of the stage kernel (tile shape from D and GP).
 template <class R, int D>
@@ -29,5 +30,51 @@ inline size_t stage_smem(int GP, int G) {
     default: return 0;
   }
 }
+
+#ifdef FX_LAUNCH_DEFINE
+// Definition, included only by the per-instantiation translation units.  The group arithmetic
+// type of the stage kernel is the state type R.
+template <class R, int D, int GP, class NT>
+static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t mid) {
+  using TS = TileShape<D, GP>;
+  auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT>;
+  const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(a.g.G);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  // gas faces first (same stream): fluxes and contact speeds of every face of every direction
+  int64_t nfmax = 0;
+  for (int d = 0; d < D; ++d) nfmax = nfmax > faces_along(a.g.n, d) ? nfmax : faces_along(a.g.n, d);
+  dim3 gg((unsigned)((nfmax + 255) / 256), D, 1);
+  gas_face_kernel<R, D><<<gg, 256, 0, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (mid) {
+    e = cudaEventRecord(mid, s);
+    if (e != cudaSuccess) return e;
+  }
+  // radiation and update: tiles across the fast axes, chunks of the slowest axis
+  dim3 grid((a.g.n[0] + TS::TX - 1) / TS::TX, 1, 1);
+  if (D == 2) grid.y = (a.g.n[1] + a.chunk - 1) / a.chunk;
+  if (D == 3) {
+    grid.y = (a.g.n[1] + TS::TY - 1) / TS::TY;
+    grid.z = (a.g.n[2] + a.chunk - 1) / a.chunk;
+  }
+  kern<<<grid, TS::TX * TS::TY * GP, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class R, int D, class NT>
+cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid) {
+  switch (GP) {
+    case 8: return launch_gp<R, D, 8, NT>(a, s, mid);
+    case 16: return launch_gp<R, D, 16, NT>(a, s, mid);
+    case 32: return launch_gp<R, D, 32, NT>(a, s, mid);
+    default: return cudaErrorInvalidValue;
+  }
+}
+#endif
 
 }  // namespace fx

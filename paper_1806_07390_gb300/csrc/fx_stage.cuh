@@ -213,7 +213,7 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
   const NT irho = frcp(rho);
   NT ke = NT(0);
 #pragma unroll
-  for (int q = 0; q < D; ++q) { NT mh = m[q] * frcp(h[q]); ke += NT(0.5) * mh * mh * irho; }
+  for (int q = 0; q < D; ++q) { NT mh = h ? m[q] * frcp(h[q]) : m[q]; ke += NT(0.5) * mh * mh * irho; }
   NT u_m = rhoe - ke;
   if (u_m < kn.u_floor) { u_m = kn.u_floor; rhoe = ke + u_m; st |= ST_FLOOR; }
   const bool has = lane < G;
@@ -322,7 +322,7 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
       dF[q] = (NT)(Fn - Fq);
       F[q] = (NT)Fn;
     }
-    dwork += m[q] * irho * frcp(h[q] * h[q]) * dF[q];
+    dwork += (h ? m[q] * frcp(h[q] * h[q]) : m[q]) * irho * dF[q];
   }
   const NT ic2 = kn.ic2;
 #pragma unroll
@@ -442,7 +442,18 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     return st[((slot * NRV + v) * PC + sc) * G + gg];
   };
   // opacity factors K = kappa0 rho^a T^b and S = sigma0 rho of one cell from its gas variables
-  auto opac = [&](const R* u, int slot, int sc) {
+  const bool sph = (D == 2) && g.geom != 0;  // spherical (r, theta): x = r, march = theta
+  // scale factor of component q of the cell with x index ix on plane k
+  auto hfac = [&](int q, int ix, int k) -> R {
+    if (!sph) return R(1);
+    const int e = q == 0 ? T_HA : T_HB;
+    return tx(e, bc_pad(ix)) * tm(e, bc_pad(k));
+  };
+  auto opac = [&](const R* uc, int slot, int sc, int ix, int k) {
+    R u[NG];
+#pragma unroll
+    for (int v = 0; v < NG; ++v) u[v] = uc[v];
+    if (sph) { u[1] *= frcp(hfac(0, ix, k)); u[2] *= frcp(hfac(1, ix, k)); }
     R rho = u[0], irho = frcp(rho), ke = R(0);
 #pragma unroll
     for (int q = 0; q < D; ++q) ke += u[1 + q] * u[1 + q];
@@ -462,7 +473,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       R u[NG];
 #pragma unroll
       for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + gc_];
-      opac(u, slot, scell(sx, sy));
+      opac(u, slot, scell(sx, sy), x0 + sx, k);
     }
     for (int t = tid; t < ncl * GP; t += NTH) {
       const int i = t / GP, gg = t % GP;
@@ -476,6 +487,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       for (int v = 0; v < NRV; ++v) {
         R val = A.in[NG * ncell + (v * ncell + gc_) * G + gg];
         if (v >= 1 && fl[v - 1]) val = -val;
+        if (sph && v >= 1) val *= frcp(hfac(v - 1, x0 + sx, k));  // physical component
         rad_at(slot, v, sc, gg) = val;
       }
     }
@@ -519,6 +531,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     for (int v = 0; v < NRV; ++v) {
       R val = A.in[NG * ncell + (v * ncell + gc_) * G + gsel];
       Q[v] = (v >= 1 && fl[v - 1]) ? -val : val;
+      if (sph && v >= 1) Q[v] *= frcp(hfac(v - 1, gx, k));  // physical component
     }
   };
   const int gvar = lane < NG ? lane : 0;
@@ -530,7 +543,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   };
   // store prefetched own values of plane k into slot `slot`; the cell's lane 0 gathers the gas
   // variables from lanes 0..NG-1 and forms the opacity factors
-  auto store_own = [&](int slot, const R* Q, R gv) {
+  auto store_own = [&](int slot, const R* Q, R gv, int k) {
     if (has) {
 #pragma unroll
       for (int v = 0; v < NRV; ++v) rad_at(slot, v, sc_own, lane) = Q[v];
@@ -538,7 +551,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     R u[NG];
 #pragma unroll
     for (int v = 0; v < NG; ++v) u[v] = __shfl_sync(0xffffffffu, gv, v, GP);
-    if (lane == 0) opac(u, slot, sc_own);
+    if (lane == 0) opac(u, slot, sc_own, gx, k);
   };
 
   // radiation flux through a face along d: QL = left cell's upper-face state, QR = right cell's
@@ -615,7 +628,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     recon_rad(mc_coef(tm, bc_pad(kbeg)), Qm1, Q0, Q1, a_, bm0);
     const R vs = gface(MD, NG, face_m(kbeg));
     rad_face(MD, bprev, a_, chi_of((kbeg - 1) & 3, sc_own), chi_of(kbeg & 3, sc_own),
-             tm(T_ELL, bc_pad(kbeg)), vs, rfm_old);
+             sph ? tm(T_ELL, bc_pad(kbeg)) * tx(T_XH, bc_pad(gx)) : tm(T_ELL, bc_pad(kbeg)), vs, rfm_old);
   }
   if (A.base != nullptr && cell_in) {
     const uint32_t c0 = D == 1 ? gx : D == 2 ? (uint32_t)kbeg * nx + gx : ((uint32_t)kbeg * ny + gy) * nx + gx;
@@ -635,7 +648,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     // held plane k-2, last read in step k-1 before its barrier C; halo positions of slot k are
     // read only in this step.
     if (D >= 2) {
-      store_own((k + 2) & 3, Qn, gn);
+      store_own((k + 2) & 3, Qn, gn, k + 2);
       load_cells(s0, k, NHALO, halo_of);
     }
     // gas face data of this plane: the cell's lower faces and the march face k+1/2
@@ -647,16 +660,40 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       vsy = gface(1, NG, face_y3(k));
       vsy1 = (ly == TY - 1 && gy < ny) ? gface(1, NG, face_y3(k) + nx) : R(0);
     }
+    // Face area/volume factors of this cell for the three flux classes (scalar, covariant
+    // component 0, component 1).  Curvilinear: x faces carry the march direction's cross factor
+    // and march faces the x direction's (Eq. 8 with separable sqrt(g)); Cartesian: 1/dx.
+    R fx_l[3], fx_r[3], fm_l[3], fm_r[3];
+    {
+      const int ipm = bc_pad(k);
+      const int eL[3] = {T_FL, T_FL1, T_FL2}, eR[3] = {T_FR, T_FR1, T_FR2}, eX[3] = {T_XS, T_X1, T_X2};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (sph) {
+          fx_l[c] = tx(eL[c], ipx) * tm(eX[c], ipm);
+          fx_r[c] = tx(eR[c], ipx) * tm(eX[c], ipm);
+          fm_l[c] = tm(eL[c], ipm) * tx(eX[c], ipx);
+          fm_r[c] = tm(eR[c], ipm) * tx(eX[c], ipx);
+        } else {
+          fx_l[c] = fxl;
+          fx_r[c] = fxr;
+          fm_l[c] = D >= 2 ? tm(T_FL, ipm) : R(0);
+          fm_r[c] = D >= 2 ? tm(T_FR, ipm) : R(0);
+        }
+      }
+    }
+    // flux class of the gas variable of this lane and of each radiation variable
+    const int gcls = (gvar >= 1 && gvar <= 2 && gvar <= D) ? gvar : 0;
     R gnet = R(0);
     if (cell_in) {  // (an overhanging cell's upper face would lie past the last face)
       const uint32_t fxk = face_x(k);
-      gnet = gface(0, gvar, fxk + 1) * fxr - gface(0, gvar, fxk) * fxl;
+      gnet = gface(0, gvar, fxk + 1) * fx_r[gcls] - gface(0, gvar, fxk) * fx_l[gcls];
       if (D == 3) {
         const uint32_t fyk = face_y3(k);
         gnet = gnet + (gface(1, gvar, fyk + nx) * ty(T_FR, bc_pad(gy)) - gface(1, gvar, fyk) * ty(T_FL, bc_pad(gy)));
       }
       if (D >= 2)
-        gnet = gnet + (gface(MD, gvar, face_m(k + 1)) * tm(T_FR, bc_pad(k)) - gface(MD, gvar, face_m(k)) * tm(T_FL, bc_pad(k)));
+        gnet = gnet + (gface(MD, gvar, face_m(k + 1)) * fm_r[gcls] - gface(MD, gvar, face_m(k)) * fm_l[gcls]);
     }
     __syncthreads();
     R Q2[NRV];
@@ -768,8 +805,8 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       }
     }
     if (D >= 2)
-      rad_face(MD, bm0, am1, chi_of(s0, sc_own), chi_of((k + 1) & 3, sc_own), tm(T_ELL, bc_pad(k + 1)),
-               vsm, rfm_new);
+      rad_face(MD, bm0, am1, chi_of(s0, sc_own), chi_of((k + 1) & 3, sc_own),
+               sph ? tm(T_ELL, bc_pad(k + 1)) * tx(T_XH, ipx) : tm(T_ELL, bc_pad(k + 1)), vsm, rfm_new);
     __syncthreads();
     // prefetch: own values of plane k+3 and the stage-2 base of plane k+1
     R b1[NRV] = {}, bg1 = R(0);
@@ -785,10 +822,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     }
     // ---- D: update: divergence, RK combine, coupling, store
     {
-      const int ipy = gy + 2, ipm = k + 2;
-      R fyl = R(0), fyr = R(0), fml = R(0), fmr = R(0);
+      const int ipy = gy + 2;
+      R fyl = R(0), fyr = R(0);
       if (D == 3) { fyl = ty(T_FL, ipy); fyr = ty(T_FR, ipy); }
-      if (D >= 2) { fml = tm(T_FL, ipm); fmr = tm(T_FR, ipm); }
       const int fxa = ly * (TX + 1) + lx;
       const int fya = ly * TX + lx;
       const uint32_t cidx = (D == 1) ? (uint32_t)gx
@@ -796,8 +832,34 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
                                      : ((uint32_t)k * ny + gy) * nx + gx;
       const R dt = KR.dt;
       const bool stage2 = A.base != nullptr;
+      // geometric sources <Gamma^l_jk> T^k_l of the stage's input state (Eq. 9; Appendix D)
+      R hq[3] = {R(1), R(1), R(1)}, gsrc = R(0), rsrc[NRV] = {};
+      if (sph) {
+        const int ipm = bc_pad(k);
+        hq[0] = hfac(0, gx, k);
+        hq[1] = hfac(1, gx, k);
+        const R g111 = tx(T_GA, ipx), g221 = tx(T_GB, ipx), g122 = tx(T_GC, ipx);
+        const R g222 = tm(T_GA, ipm), g332 = tm(T_GB, ipm);
+        R gc[NG];
+#pragma unroll
+        for (int v = 0; v < NG; ++v) gc[v] = __shfl_sync(0xffffffffu, g0, v, GP);
+        const R rho = gc[0], irho = frcp(rho);
+        const R v1 = gc[1] * irho * frcp(hq[0]), v2 = gc[2] * irho * frcp(hq[1]);
+        const R p = KR.gm1 * (gc[NG - 1] - R(0.5) * rho * (v1 * v1 + v2 * v2));
+        const R r12 = hq[0] * frcp(hq[1]), r21 = hq[1] * frcp(hq[0]);
+        if (gvar == 1) gsrc = g111 * (rho * v1 * v1 + p) + g221 * (rho * v2 * v2 + p) + g221 * p;
+        if (gvar == 2)
+          gsrc = g122 * (rho * v1 * v2 * r12) + g221 * (rho * v1 * v2 * r21) + g222 * (rho * v2 * v2 + p) + g332 * p;
+        R Pd[3], P01;
+        m1_full<R, D>(KR.c, Q0[0], Q0 + 1, Pd, P01);
+        const R c2 = KR.c * KR.c;
+        const R R11 = c2 * Pd[0] + v1 * Q0[1], R22 = c2 * Pd[1] + v2 * Q0[2], R33 = c2 * Pd[2];
+        const R R21 = (c2 * P01 + v2 * Q0[1]) * r12, R12 = (c2 * P01 + v1 * Q0[2]) * r21;
+        rsrc[1] = g111 * R11 + g221 * R22 + g221 * R33;
+        rsrc[2] = g122 * R21 + g221 * R12 + g222 * R22 + g332 * R33;
+      }
       // gas: lane v < NG updates variable v, then the segment shares the cell's gas state
-      R ug = g0 + dt * (-gnet);
+      R ug = g0 + dt * (gsrc - gnet);
       if (stage2) ug = KR.alpha * bg0 + KR.beta * ug;
       NT gas[NG];
 #pragma unroll
@@ -806,20 +868,24 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       if (has && cell_in) {
 #pragma unroll
         for (int v = 0; v < NRV; ++v) {
-          R net = rfx[(v * NFX + fxa + 1) * G + lane] * fxr - rfx[(v * NFX + fxa) * G + lane] * fxl;
+          const int c = v <= 2 ? v : 0;
+          R net = rfx[(v * NFX + fxa + 1) * G + lane] * fx_r[c] - rfx[(v * NFX + fxa) * G + lane] * fx_l[c];
           if (D == 3) net = net + (rfy[(v * NFY + fya + TX) * G + lane] * fyr - rfy[(v * NFY + fya) * G + lane] * fyl);
-          if (D >= 2) net = net + (rfm_new[v] * fmr - rfm_old[v] * fml);
-          R u1 = Q0[v] + dt * (-net);
+          if (D >= 2) net = net + (rfm_new[v] * fm_r[c] - rfm_old[v] * fm_l[c]);
+          const R cov = (sph && v >= 1) ? Q0[v] * hq[v - 1] : Q0[v];  // covariant F
+          R u1 = cov + dt * (rsrc[v] - net);
           if (stage2) u1 = KR.alpha * b0[v] + KR.beta * u1;
           if (v == 0) E = (NT)u1; else F[v - 1] = (NT)u1;
         }
       }
       unsigned stbits = 0;
       if (g.couple) {
-        NT h[3] = {NT(1), NT(1), NT(1)};
+        // covariant components: physical = m_q / h_q on curvilinear grids (Cartesian: no scaling)
+        NT h[3] = {(NT)hq[0], (NT)hq[1], NT(1)};
         NT m[3] = {gas[1], D > 1 ? gas[2] : NT(0), D > 2 ? gas[3] : NT(0)};
         NT rho = gas[0], rhoe = gas[NG - 1];
-        stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.ptab, A.k(NT(0)), A.k(LT(0)), cell_in, lane, h,
+        stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.ptab, A.k(NT(0)), A.k(LT(0)), cell_in, lane,
+                                            sph ? h : nullptr,
                                             rho, m, rhoe, E, F);
         gas[0] = rho;
 #pragma unroll

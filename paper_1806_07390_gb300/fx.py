@@ -29,6 +29,7 @@ EXPORTS = ["fx_grid_create", "fx_bind_workspace", "fx_state_elems", "fx_state_up
            "fx_state_init_equilibrium", "fx_step", "fx_sync", "fx_conserved_totals",
            "fx_state_download", "fx_launches_per_step", "fx_debug_table", "fx_debug_ntab",
            "fx_debug_planck_table", "fx_state_init_equilibrium_noalloc",
+           "fx_kernel_timing_enable", "fx_kernel_timing_read",
            "fx_last_error", "fx_clear_error", "fx_grid_destroy"]
 
 
@@ -83,13 +84,15 @@ def lib() -> ctypes.CDLL:
                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
         L.fx_state_init_equilibrium_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.fx_state_init_equilibrium_noalloc.restype = ctypes.c_int
+        L.fx_kernel_timing_enable.argtypes = [vp, ctypes.c_int]
+        L.fx_kernel_timing_read.argtypes = [vp, dp]
         L.fx_last_error.argtypes = [vp]
         L.fx_last_error.restype = ctypes.c_char_p
         L.fx_clear_error.argtypes = [vp]
         L.fx_grid_destroy.argtypes = [vp]
         for f in ("fx_grid_create", "fx_bind_workspace", "fx_state_upload",
                   "fx_state_init_equilibrium", "fx_step", "fx_sync", "fx_conserved_totals",
-                  "fx_state_download"):
+                  "fx_state_download", "fx_kernel_timing_enable", "fx_kernel_timing_read"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -210,6 +213,17 @@ class Grid:
 
     def launches_per_step(self) -> int:
         return int(self.L.fx_launches_per_step(self.h))
+
+    def kernel_timing(self, on: bool) -> None:
+        """Start (or stop) recording per-kernel CUDA-event durations of the stages fx_step enqueues."""
+        self._check(self.L.fx_kernel_timing_enable(self.h, int(bool(on))))
+
+    def kernel_times(self) -> dict:
+        """Synchronising read of the recorded durations: total ms and launch counts per kernel."""
+        out = np.zeros(4)
+        self._check(self.L.fx_kernel_timing_read(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return {"stage_ms": float(out[0]), "stage_launches": int(out[1]),
+                "face_ms": float(out[2]), "face_launches": int(out[3])}
 
     def clear_error(self) -> None:
         self.L.fx_clear_error(self.h)

@@ -120,7 +120,6 @@ def test_host_tables_reproduce_oracle_reconstruction(L, maker):
         pb, _ = W.kh_2d(nx=24, ny=20, ngroups=2)
     else:
         pb, _ = W.spherical_2d(nr=24, nth=20, ngroups=2)
-        pb.geom = "cart"  # tables of the 1-d moments only; geometry handled per direction
     st, h, _ = create(pb)
     assert st == 0
     ntab = L.fx_debug_ntab()
@@ -170,3 +169,39 @@ def test_fp32_planck_tables_interpolate_the_band_integrals(L):
             worst = max(worst, abs(2.0 ** Lg / ref - 1.0))
     L.fx_grid_destroy(h)
     assert worst < 3e-7, worst
+
+
+def test_spherical_tables_match_oracle_geometry(L):
+    # volumes, connection coefficients and face factors of the library's host tables against
+    # the oracle's independently integrated geometry (Appendices A-D)
+    pb, _ = W.spherical_2d(nr=20, nth=12, ngroups=2)
+    st, h, _ = create(pb)
+    assert st == 0
+    ntab = L.fx_debug_ntab()
+    T = []
+    for d in range(2):
+        n = pb.n[d] + 4
+        buf = np.zeros(ntab * n)
+        L.fx_debug_table(h, d, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), buf.size)
+        T.append(buf.reshape(ntab, n)[:, 2:-2])
+    names = ["WA0", "WA1", "WA2", "WB0", "WB1", "WB2", "SL2", "TL2", "SR2", "TR2", "AL0", "AL1",
+             "AL2", "AR0", "AR1", "AR2", "RHL", "RHR", "IL", "IR", "IC", "DL", "DR", "FL", "FR",
+             "ELL", "VOL", "FL1", "FR1", "FL2", "FR2", "XS", "X1", "X2", "XH", "HA", "HB", "GA",
+             "GB", "GC"]
+    e = {nm: i for i, nm in enumerate(names)}
+    assert ntab == len(names)
+    vol_r, _, _ = oracle.geometry(pb, 0)
+    vol_t, _, _ = oracle.geometry(pb, 1)
+    np.testing.assert_allclose(T[0][e["VOL"]], vol_r, rtol=1e-13)
+    np.testing.assert_allclose(T[1][e["VOL"]], vol_t, rtol=1e-13)
+    G = oracle.christoffel(pb)
+    np.testing.assert_allclose(T[0][e["GA"]], G["G111"], rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(T[0][e["GB"]], G["G221"], rtol=1e-12)
+    np.testing.assert_allclose(T[0][e["GC"]], G["G122"], rtol=1e-12)
+    np.testing.assert_allclose(T[1][e["GA"]], G["G222"], rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(T[1][e["GB"]], G["G332"], rtol=1e-12, atol=1e-14)
+    # radial faces: r^2 / V_r from the exponential map
+    xf = np.linspace(pb.x_lo[0], pb.x_hi[0], pb.n[0] + 1)
+    np.testing.assert_allclose(T[0][e["FL"]], np.exp(2 * xf[:-1]) / vol_r, rtol=1e-13)
+    np.testing.assert_allclose(T[0][e["FR2"]], np.exp(3 * xf[1:]) / vol_r, rtol=1e-13)
+    L.fx_grid_destroy(h)

@@ -177,3 +177,31 @@ def test_newton_failure_is_reported(fxmod):
     pb2, prim2 = W.kh_2d(nx=16, ny=16, ngroups=4, nsteps=1)
     out, st, _ = run_gpu(fxmod, pb2, prim2)
     assert st == 0
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32", 1e-5)])
+def test_spherical_2d_small(fxmod, precision, tol):
+    # log-r x theta grid with reflecting inner radius, outflow outer radius, polar-axis parity;
+    # coordinate moments, curvilinear face factors and geometric sources all active
+    pb, prim = W.spherical_2d(nr=36, nth=20, ngroups=20, nsteps=3, precision=precision)
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    if precision == "fp64":
+        H.assert_parity(pb, got, ref, tol, FP64_MAX)
+    else:
+        H.assert_parity(pb, got, ref, tol, natural=True)
+
+
+def test_spherical_static_atmosphere_gpu(fxmod):
+    # uniform p and E, v = F = 0: flux divergence and geometric sources cancel (Eqs. 84-85)
+    pb, _ = W.spherical_2d(nr=24, nth=16, ngroups=3, nsteps=1, precision="fp64")
+    pb.couple = 0
+    N = pb.ncell
+    s = np.zeros(pb.state_size())
+    s[:N] = np.linspace(0.5, 2.0, N)
+    s[3 * N: 4 * N] = 0.7 / (pb.gamma - 1)
+    s[4 * N: 4 * N + N * 3] = 0.3
+    got, st, _ = run_gpu(fxmod, pb, state=s, nsteps=2)
+    assert st == 0
+    assert np.max(np.abs(got - s)) < 1e-12
