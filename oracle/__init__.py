@@ -57,6 +57,8 @@ def lib():
         P = ctypes.POINTER(OrcParams)
         L.orc_run.argtypes = [P, _DP, ctypes.c_double, ctypes.c_int]
         L.orc_run_tangent.argtypes = [P, _DP, _DP, ctypes.c_double, ctypes.c_int]
+        L.orc_run_objective.argtypes = [P, _DP, _DP, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, _DP]
         L.orc_rhs.argtypes = [P, _DP, _DP]
         L.orc_couple.argtypes = [P, _DP, ctypes.c_double]
         L.orc_totals.argtypes = [P, _DP, _DP]
@@ -131,6 +133,25 @@ def run_tangent(pb: Problem, state: np.ndarray, tangent: np.ndarray, dt: float, 
     tan = np.array(tangent, dtype=np.float64, copy=True)
     st = lib().orc_run_tangent(ctypes.byref(P), _ptr(out), _ptr(tan), dt, nsteps)
     return out, tan, st
+
+
+def run_objective(pb: Problem, state: np.ndarray, dt: float, nsteps: int, tangent=None,
+                  dkappa0: float = 0.0, signature: bool = False, nthreads: int = 1, **kw):
+    """Advance nsteps steps accumulating the boundary outflow objective J (R19).
+
+    Returns (final state, J, dJ, signature, status): dJ is the tangent of J along the initial-state
+    tangent `tangent` and the kappa0 tangent `dkappa0` (0 when `tangent` is None); the signature
+    (a Python int, or None) hashes every branch decision of the run in order."""
+    P = params(pb, nthreads=nthreads, **kw)
+    out = np.array(state, dtype=np.float64, copy=True)
+    res = np.zeros(3)
+    tan = None
+    if tangent is not None:
+        tan = np.array(tangent, dtype=np.float64, copy=True)
+    st = lib().orc_run_objective(ctypes.byref(P), _ptr(out), _ptr(tan) if tan is not None else None,
+                                 float(dkappa0), dt, nsteps, int(signature), _ptr(res))
+    sig = int(res[2:3].view(np.uint64)[0]) if signature else None
+    return out, float(res[0]), float(res[1]), sig, st
 
 
 def rhs(pb: Problem, state: np.ndarray) -> np.ndarray:

@@ -18,6 +18,8 @@
 //   * energy coupling (BE + Newton on T)  -- Sec. 5.3, Eqs. 24-27
 //   * momentum coupling (BE flux update)  -- Sec. 5.3, Eqs. 28, 31-32
 //   * conserved totals (compensated sums)
+//   * the objective J: RK-weighted radiation energy leaving through the upper x boundary (R19),
+//     with its tangent (initial-state and kappa0 directions) through the dual-number instantiation
 //
 // Readings where the paper is silent or ambiguous (numbered as in the design notes):
 //   R1 radiation reconstructed linearly with an MC slope limiter in moment form (Sec. 2 says linear).
@@ -38,6 +40,8 @@
 //   R15 volume-averaged Christoffel symbols with the pressure-balance corrections in r and theta.
 //   R16 D momentum components; T^3_3 = p enters the sources.
 //   R18 floors on rho and p (reported) and a silent positivity floor on E_g.
+//   R19 J = sum_steps dt (Phi(U^n) + Phi(U^(1)))/2, Phi = sum over groups and upper-x faces of
+//      face area x (corrected HLL energy flux + v* E upwind): the outflow the update itself uses.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -93,6 +97,27 @@ using std::pow;
 using std::sqrt;
 template <class S> static inline S smin(S a, S b) { return val(a) <= val(b) ? a : b; }
 template <class S> static inline S smax(S a, S b) { return val(a) >= val(b) ? a : b; }
+
+// ---------------------------------------------------------------------------------------------
+// Branch signature (used by the finite-difference tests only).  While enabled, each branch
+// decision of the limiters, HLLC, the opacity guard, the optical-depth correction, the upwind
+// choice, the floors and the interaction's fallback is folded, in evaluation order, into a
+// 64-bit hash.  Two single-threaded runs end with the same signature exactly when they took the
+// same branches in the same order (up to hash collisions): a central difference between them
+// then crosses no kink of the discrete map.
+// ---------------------------------------------------------------------------------------------
+static bool g_sig_on = false;
+static uint64_t g_sig = 0;
+static inline void branch(unsigned site, unsigned outcome) {
+  if (!g_sig_on) return;
+  uint64_t x = g_sig ^ (((uint64_t)site << 32) | outcome);
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdULL;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ULL;
+  x ^= x >> 33;
+  g_sig = x + 0x9e3779b97f4a7c15ULL;
+}
 
 // ---------------------------------------------------------------------------------------------
 // Parameters (C layout, filled from Python).
@@ -475,8 +500,9 @@ template <class S> static S face_interval_reset(S f, S pa, S pb, double xa, doub
   S lo = pa + dlt * (s * s);                  // zero slope at xa
   S hi = pb - dlt * ((1.0 - s) * (1.0 - s));  // zero slope at xb
   if (val(dlt) < 0.0) std::swap(lo, hi);
-  if (val(f) < val(lo)) return lo;
-  if (val(f) > val(hi)) return hi;
+  if (val(f) < val(lo)) { branch(2, 1 + 4 * (val(dlt) < 0.0)); return lo; }
+  if (val(f) > val(hi)) { branch(2, 2 + 4 * (val(dlt) < 0.0)); return hi; }
+  branch(2, 4 * (val(dlt) < 0.0));
   return f;
 }
 
@@ -484,7 +510,8 @@ template <class S> static S face_interval_reset(S f, S pa, S pb, double xa, doub
 template <class S>
 static void recon_parabolic(const orc_params& P, const StencilGeo& g, S pm, S p0, S pp, S& a, S& b) {
   // extremum of the data -> piecewise constant (R4)
-  if (val((pp - p0) * (p0 - pm)) <= 0.0) { a = p0; b = p0; return; }
+  if (val((pp - p0) * (p0 - pm)) <= 0.0) { branch(1, 1); a = p0; b = p0; return; }
+  branch(1, 0);
   // system 1 (Eq. 15): parabola matching the three cell averages
   double A1[3][3];
   for (int k = 0; k < 3; ++k) { A1[k][0] = 1.0; A1[k][1] = g.M1[k]; A1[k][2] = g.M2[k]; }
@@ -501,15 +528,16 @@ static void recon_parabolic(const orc_params& P, const StencilGeo& g, S pm, S p0
   solve3(A2, r2, c);
   // in-cell extremum: slopes at the two faces of opposite sign (R3)
   S sl = dpoly(c, g.xl), sr = dpoly(c, g.xr);
-  if (val(sl * sr) >= 0.0) return;
+  if (val(sl * sr) >= 0.0) { branch(3, 0); return; }
   double w = g.xr - g.xl;
   double hl = -g.xl;  // xc - x_L
   double M2L = g.M2[1] + 2.0 * hl * g.M1[1] + hl * hl;  // <(x - x_L)^2>_i
   double hr = -g.xr;
   double M2R = g.M2[1] + 2.0 * hr * g.M1[1] + hr * hr;  // <(x - x_R)^2>_i
   double asl = std::fabs(val(sl)), asr = std::fabs(val(sr));
-  if (asl == asr) { a = p0; b = p0; return; }  // vertex at the centre
+  if (asl == asr) { branch(3, 1); a = p0; b = p0; return; }  // vertex at the centre
   bool near_lower = asl < asr;
+  branch(3, near_lower ? 2 : 3);
   if (!P.r3_literal) {
     if (near_lower) b = a + (p0 - a) * (w * w / M2L);  // zero slope at the lower face
     else a = b + (p0 - b) * (w * w / M2R);            // zero slope at the upper face
@@ -536,6 +564,11 @@ static void recon_linear_mc(const StencilGeo& g, S pm, S p0, S pp, S& a, S& b) {
   if (val(sL * sR) > 0.0) {
     S m = smin(smin(2.0 * fabs(sL), 2.0 * fabs(sR)), fabs(sC));
     sl = val(sC) > 0.0 ? m : -m;
+    const double aL = 2.0 * std::fabs(val(sL)), aR = 2.0 * std::fabs(val(sR)), aC = std::fabs(val(sC));
+    const unsigned arg = (aL <= aR) ? (aL <= aC ? 1 : 3) : (aR <= aC ? 2 : 3);
+    branch(4, arg + 4 * (val(sC) > 0.0) + 8 * (val(sL) > 0.0));
+  } else {
+    branch(4, 0);
   }
   a = p0 + sl * (g.xl - g.M1[1]);
   b = p0 + sl * (g.xr - g.M1[1]);
@@ -570,6 +603,10 @@ static void hllc(int D, double gam, const S WL[5], const S WR[5], S flux[5], S& 
   S at = sqrt(smax(at2, S(0.0)));
   S SL = smin(ul - al, ut - at);
   S SR = smax(ur + ar, ut + at);
+  // (the choice between the two speed estimates is not part of the branch signature: they tie
+  // wherever the reconstructed states coincide, which the face-interval reset produces exactly,
+  // and there the flux does not depend on S_L, S_R to first order)
+  branch(5, val(at2) >= 0.0);
   S dl = rl * (SL - ul), dr = rr * (SR - ur);
   S Ss = (pr - pl + ul * dl - ur * dr) / (dl - dr);
   vstar = Ss;
@@ -582,9 +619,10 @@ static void hllc(int D, double gam, const S WL[5], const S WR[5], S flux[5], S& 
   for (int q = 0; q < D; ++q) { FL[1 + q] = rl * ul * WL[2 + q]; FR[1 + q] = rr * ur * WR[2 + q]; }
   FL[1] = FL[1] + pl; FR[1] = FR[1] + pr;
   FL[1 + D] = (El + pl) * ul; FR[1 + D] = (Er + pr) * ur;
-  if (val(SL) >= 0.0) { for (int v = 0; v < nv; ++v) flux[v] = FL[v]; return; }
-  if (val(SR) < 0.0) { for (int v = 0; v < nv; ++v) flux[v] = FR[v]; return; }
+  if (val(SL) >= 0.0) { branch(6, 0); for (int v = 0; v < nv; ++v) flux[v] = FL[v]; return; }
+  if (val(SR) < 0.0) { branch(6, 1); for (int v = 0; v < nv; ++v) flux[v] = FR[v]; return; }
   bool left = val(Ss) >= 0.0;
+  branch(6, left ? 2 : 3);
   const S* W = left ? WL : WR;
   const S* Uk = left ? UL : UR;
   const S* Fk = left ? FL : FR;
@@ -609,10 +647,12 @@ template <class S> static void m1_pressure_row(int D, double c, S E, const S* F,
   for (int q = 0; q < D; ++q) F2 += F[q] * F[q];
   S Fm = sqrt(F2);
   if (val(Fm) <= 0.0 || val(E) <= 0.0) {
+    branch(7, 0);
     for (int q = 0; q < D; ++q) Prow[q] = (q == n) ? E / 3.0 : S(0.0);
     return;
   }
   S f = Fm / (c * E);
+  branch(7, 1 + (val(f) > 1.0));
   if (val(f) > 1.0) f = 1.0;
   S chi = m1_chi(f);
   S a = 0.5 * (1.0 - chi), b = 0.5 * (3.0 * chi - 1.0);
@@ -642,6 +682,7 @@ template <class S> static void m1_pressure_full(int D, double c, S E, const S* F
 struct Groups {
   int G;
   std::vector<double> edge, centre;
+  double dkappa0 = 0.0;  // tangent of kappa0 (the dual-number instantiation only)
 };
 static Groups make_groups(const orc_params& P) {
   Groups g;
@@ -652,8 +693,10 @@ static Groups make_groups(const orc_params& P) {
   for (int k = 0; k < g.G; ++k) g.centre[k] = std::sqrt(g.edge[k] * g.edge[k + 1]);
   return g;
 }
+static inline double kappa0_of(const orc_params& P, const Groups&, double) { return P.kappa0; }
+static inline Dual kappa0_of(const orc_params& P, const Groups& gr, const Dual&) { return Dual(P.kappa0, gr.dkappa0); }
 template <class S> static S kappa_of(const orc_params& P, const Groups& gr, int g, S rho, S T) {
-  return P.kappa0 * pow(rho, P.kap_rho_exp) * pow(T, P.kap_T_exp) * std::pow(gr.centre[g], P.kap_eps_exp);
+  return kappa0_of(P, gr, rho) * pow(rho, P.kap_rho_exp) * pow(T, P.kap_T_exp) * std::pow(gr.centre[g], P.kap_eps_exp);
 }
 template <class S> static S sigma_of(const orc_params& P, S rho) { return P.sigma0 * rho; }
 
@@ -679,11 +722,13 @@ static int couple_cell(const orc_params& P, const Groups& gr, int D, const doubl
   const double c = P.c_light, cv = 1.0 / (P.gamma - 1.0);
   int status = 0;
   S rho = U[0];
+  branch(10, val(rho) < P.rho_floor);
   if (val(rho) < P.rho_floor) { rho = P.rho_floor; U[0] = rho; status |= 2; }
   S ke = 0.0;
   for (int q = 0; q < D; ++q) { S vh = U[1 + q] / (rho * h[q]); ke += 0.5 * rho * vh * vh; }
   S u_m = U[NG - 1] - ke;
   double u_floor = P.p_floor / (P.gamma - 1.0);
+  branch(11, val(u_m) < u_floor);
   if (val(u_m) < u_floor) { u_m = u_floor; U[NG - 1] = ke + u_m; status |= 2; }
   std::vector<S> Em(G), En(G);
   S Esum = 0.0;
@@ -738,6 +783,7 @@ static int couple_cell(const orc_params& P, const Groups& gr, int D, const doubl
     }
     if (!acc) break;
   }
+  branch(12, ok);
   if (!ok) {
     // bisection fallback on a bracket around [T^-, T_rad]
     S Tr = pow(Esum / P.a_rad, 0.25);
@@ -794,9 +840,12 @@ static int couple_cell(const orc_params& P, const Groups& gr, int D, const doubl
 // Explicit operator L(U): flux divergence + geometric sources (Sec. 4, Eq. 8, Eq. 9).
 // U must have its ghosts filled.  dU gets -(1/V) sum_faces A.F + <S> for all interior cells.
 // ---------------------------------------------------------------------------------------------
+// When phi is non-null it receives Phi(U) of R19: the radiation energy flux (corrected HLL + v* E
+// upwind, Eqs. 17, 19) times the face area, summed over the groups and the faces of the upper x
+// boundary, rows added in a fixed order.
 template <class S>
 static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout& L, const Groups& gr,
-                         const std::vector<S>& U, std::vector<S>& dU) {
+                         const std::vector<S>& U, std::vector<S>& dU, S* phi = nullptr) {
   const int D = L.D, G = L.G, NG = L.NG, NRV = L.NRV, NV = L.NV;
   const double c = P.c_light, gam = P.gamma;
   std::fill(dU.begin(), dU.end(), S(0.0));
@@ -830,8 +879,11 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
           for (int q = 0; q < D; ++q) rr[1 + q] = u[NG + g * NRV + 1 + q] / h[q];
           if (val(T) > 0.0) chi[id * G + g] = kappa_of(P, gr, g, rho, T) + sigma_of(P, rho);
           else chi[id * G + g] = 0.0;
+          branch(8, val(T) > 0.0);
         }
       }
+  // boundary outflow per row of the upper x boundary (R19)
+  std::vector<S> phi_row((size_t)L.n[1] * L.n[2], S(0.0));
   // flux divergence, one direction at a time
   for (int d = 0; d < D; ++d) {
     const Dir& ad = geo.dir[d];
@@ -908,6 +960,7 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
             S tau = 0.5 * (chi[il * G + g] + chi[ir * G + g]) * (ell * hn);
             S eps = val(tau) > 1.0 ? 1.0 / tau : S(1.0);
             bool up_left = val(vstar) >= 0.0;
+            branch(9, (val(tau) > 1.0) + 2 * up_left);
             const S* Qu = up_left ? QL : QR;
             // energy: corrected HLL (Eq. 17) with S_L = -c, S_R = c, plus v* E upwind (Eq. 19)
             S FE = 0.5 * (QL[1 + d] + QR[1 + d]) - 0.5 * eps * c * (QR[0] - QL[0]) + vstar * Qu[0];
@@ -915,6 +968,8 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
             S fE = FE * Aph;
             acc[il * NV + o] += fE;
             acc[ir * NV + o] -= fE;
+            if (d == 0 && f == L.ng[0] + L.n[0])
+              phi_row[(size_t)(b - L.ng[2]) * L.n[1] + (a - L.ng[1])] += fE;
             for (int q = 0; q < D; ++q) {
               S FF = 0.5 * c * c * (PL[q] + PR[q]) - 0.5 * c * (QR[1 + q] - QL[1 + q]) + vstar * Qu[1 + q];
               S fF = FF * Ah[q];
@@ -924,6 +979,11 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
           }
         }
       }
+  }
+  if (phi) {
+    S sum = 0.0;
+    for (size_t r = 0; r < phi_row.size(); ++r) sum += phi_row[r];
+    *phi = sum;
   }
   // divide by the cell volume; add geometric sources (spherical only)
   for (int k = L.ng[2]; k < L.ng[2] + L.n[2]; ++k)
@@ -995,20 +1055,24 @@ static int couple_all(const Oracle& O, std::vector<S>& U, double dt) {
   return status;
 }
 
+// One SSP-RK2 step.  When J is non-null the step's share of the objective (R19) is added:
+// dt (Phi(U^n) + Phi(U^(1)))/2, the same weights the update gives the boundary fluxes.
 template <class S>
-static int rk2_step(const Oracle& O, std::vector<S>& U, double dt) {
+static int rk2_step(const Oracle& O, std::vector<S>& U, double dt, S* J = nullptr) {
   const Layout& L = O.L;
   const size_t N = L.ncell_p * L.NV;
   std::vector<S> U0 = U, dU(N), U1(N);
   int status = 0;
+  S phi0 = 0.0, phi1 = 0.0;
   fill_ghosts(O.P, L, U0);
-  explicit_rhs(O.P, O.geo, L, O.gr, U0, dU);
+  explicit_rhs(O.P, O.geo, L, O.gr, U0, dU, J ? &phi0 : nullptr);
   for (size_t q = 0; q < N; ++q) U1[q] = U0[q] + dt * dU[q];
   if (O.P.couple) status |= couple_all(O, U1, dt);
   fill_ghosts(O.P, L, U1);
-  explicit_rhs(O.P, O.geo, L, O.gr, U1, dU);
+  explicit_rhs(O.P, O.geo, L, O.gr, U1, dU, J ? &phi1 : nullptr);
   for (size_t q = 0; q < N; ++q) U[q] = 0.5 * U0[q] + 0.5 * (U1[q] + dt * dU[q]);
   if (O.P.couple) status |= couple_all(O, U, 0.5 * dt);
+  if (J) *J += dt * (0.5 * phi0 + 0.5 * phi1);
   return status;
 }
 
@@ -1110,6 +1174,43 @@ int orc_run_tangent(const orc_params* P, double* state, double* tangent, double 
   int status = 0;
   for (int s = 0; s < nsteps; ++s) status |= rk2_step(O, U, dt);
   pack(O, U, state, tangent);
+  return status;
+}
+
+// Objective run (R19): advance `state` by nsteps steps, returning J in out[0].  With `tangent`
+// non-null the run is tangent-linear: the state tangent advances too and out[1] receives dJ for
+// the initial-state tangent `tangent` and the kappa0 tangent `dkappa0`.  With `want_sig` the run
+// is single-threaded and out[2] receives the branch signature (its 64 bits as a double's bytes).
+int orc_run_objective(const orc_params* P, double* state, double* tangent, double dkappa0, double dt,
+                      int nsteps, int want_sig, double* out) {
+  Oracle O;
+  orc_params Q = *P;
+  if (want_sig) Q.nthreads = 1;
+  setup(O, &Q);
+  O.gr.dkappa0 = dkappa0;
+  int status = 0;
+  g_sig = 0;
+  g_sig_on = want_sig != 0;
+  if (tangent) {
+    std::vector<Dual> U;
+    unpack(O, state, U, tangent);
+    Dual J = 0.0;
+    for (int s = 0; s < nsteps; ++s) status |= rk2_step(O, U, dt, &J);
+    pack(O, U, state, tangent);
+    out[0] = J.v;
+    out[1] = J.d;
+  } else {
+    std::vector<double> U;
+    unpack(O, state, U, (const double*)nullptr);
+    double J = 0.0;
+    for (int s = 0; s < nsteps; ++s) status |= rk2_step(O, U, dt, &J);
+    pack(O, U, state, (double*)nullptr);
+    out[0] = J;
+    out[1] = 0.0;
+  }
+  g_sig_on = false;
+  uint64_t sig = g_sig;
+  std::memcpy(&out[2], &sig, sizeof(sig));
   return status;
 }
 

@@ -118,3 +118,37 @@ def gather_cells(pb: Problem, state: np.ndarray, cells: np.ndarray) -> np.ndarra
     gas = state[: NG * N].reshape(NG, N)[:, cells]
     rad = state[NG * N:].reshape(1 + D, N, G)[:, cells, :]
     return np.concatenate([gas.reshape(-1), rad.reshape(-1)])
+
+
+def rho_tangent(pb: Problem, state: np.ndarray, drho: np.ndarray) -> np.ndarray:
+    """State tangent of a density perturbation drho (per cell) that holds the pressure, the
+    velocity and the radiation variables fixed (Cartesian): d rho = drho, d m = v drho,
+    d(rho e) = |v|^2/2 drho, zero elsewhere."""
+    D, N = pb.dims, pb.ncell
+    rho = state[:N]
+    out = np.zeros_like(state)
+    out[:N] = drho
+    ke = np.zeros(N)
+    for q in range(D):
+        v = state[(1 + q) * N:(2 + q) * N] / rho
+        out[(1 + q) * N:(2 + q) * N] = v * drho
+        ke += 0.5 * v * v
+    out[(1 + D) * N:(2 + D) * N] = ke * drho
+    return out
+
+
+def with_rho(pb: Problem, state: np.ndarray, rho_new: np.ndarray) -> np.ndarray:
+    """The state with density rho_new and the same pressure, velocity and radiation (Cartesian)."""
+    D, N = pb.dims, pb.ncell
+    out = np.array(state, copy=True)
+    rho = state[:N]
+    ke_old = np.zeros(N)
+    ke_new = np.zeros(N)
+    for q in range(D):
+        v = state[(1 + q) * N:(2 + q) * N] / rho
+        out[(1 + q) * N:(2 + q) * N] = rho_new * v
+        ke_old += 0.5 * rho * v * v
+        ke_new += 0.5 * rho_new * v * v
+    out[:N] = rho_new
+    out[(1 + D) * N:(2 + D) * N] = state[(1 + D) * N:(2 + D) * N] - ke_old + ke_new
+    return out
