@@ -186,6 +186,68 @@ FORM_NOTE = {"fp32": "FP32 state, fluxes and coupling (anchored FP32 Newton), FP
              "fp64": "FP64 throughout"}
 
 
+def time_adjoint(steps_rep: int = 3):
+    """The differentiation form on its own workload (blobs2d: 512 x 512 cells x 8 groups, FP32,
+    a beam along +x through density blobs): J = radiation energy leaving through +x over 50
+    steps, gradients with respect to rho(x, 0) and kappa0 with a checkpoint every 10 steps.
+    Times (CUDA events on the handle's stream) the plain forward with the objective, the
+    adjoint's forward pass (objective + checkpoints) and its backward pass (recomputation +
+    stage adjoints); the median of steps_rep repetitions after one warm-up."""
+    import torch
+
+    from paper_1806_07390_gb300 import fx
+
+    nsteps, k = 50, 10
+    pb, prim = W.blobs_2d(precision="fp32")
+    g = fx.Grid(pb)
+    g.init_equilibrium(prim)
+    s0 = W.streaming_flux(pb, g.download().astype(np.float64), 0.5)
+    g.upload(s0.astype(np.float32))
+    ws = g.adjoint_workspace(nsteps, k)
+    st = g.stream
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def fwd_plain():
+        g.upload(s0.astype(np.float32))
+        g.objective(True)
+        g.step(pb.dt, nsteps)
+        g.sync()
+
+    res = {"fwd": [], "adj_fwd": [], "adj_bwd": []}
+    out = {}
+    for rep in range(steps_rep + 1):
+        tf = timed(fwd_plain)
+        J_plain = g.boundary_energy_out()
+        g.objective(False)
+        g.upload(s0.astype(np.float32))
+        ta = timed(lambda: out.__setitem__("J", g.adjoint_forward(ws, pb.dt, nsteps, k)))
+        tb = timed(lambda: out.__setitem__("g", g.adjoint_backward(ws, pb.dt, nsteps, k)))
+        if rep > 0:
+            res["fwd"].append(tf)
+            res["adj_fwd"].append(ta)
+            res["adj_bwd"].append(tb)
+    med = {kk: statistics.median(v) for kk, v in res.items()}
+    gs, gr, dk = out["g"]
+    g.close()
+    return {"workload": "blobs2d: 512x512 cells x 8 groups, FP32 form, beam along +x, 50 steps, "
+                        "checkpoint every 10 steps",
+            "J": out["J"], "J_plain_forward": J_plain, "dJ_dkappa0": dk,
+            "grad_rho_norm": float(gr.double().norm()),
+            "forward_ms": med["fwd"], "adjoint_forward_ms": med["adj_fwd"],
+            "adjoint_backward_ms": med["adj_bwd"],
+            "adjoint_step_over_forward_step": med["adj_bwd"] / med["fwd"],
+            "gradient_over_forward": (med["adj_fwd"] + med["adj_bwd"]) / med["fwd"],
+            "note": "adjoint step = recomputation of its checkpoint segment + the two stage adjoints"}
+
+
 def oracle_sample(pb64, prim, spec):
     from tests import helpers as H
 
@@ -268,6 +330,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -351,6 +414,8 @@ def main():
                                "ms_per_step": msf / args.steps, "note": FORM_NOTE[name],
                                "roofline": roofline(name, ktf), "status": int(stf),
                                "speedup_of_headline": msf / msh}
+    if not args.no_adjoint and args.workload == "kh2d":
+        line["adjoint"] = time_adjoint()
     if rank == 0 and not args.no_cpu and not dist:
         pb64 = gen(precision="fp64")[0]
         line["cpu_baseline"] = cpu_baseline(pb64, prim, spec)

@@ -145,7 +145,7 @@ fx_status fx_conserved_totals(fx_grid* h, double out[FX_NTOTALS]);
 fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is_device);
 
 /* Number of kernel launches enqueued by one fx_step(dt, 1) call (per RK stage: the gas face
- * kernel and the radiation/update kernel). */
+ * kernel and the radiation/update kernel, plus the objective's reduction while it is enabled). */
 int fx_launches_per_step(const fx_grid* h);
 
 /* Per-kernel device timing (instrumentation, not part of the method).  While enabled, every
@@ -194,6 +194,49 @@ int fx_debug_planck_table(const fx_grid* h, float* out, size_t cap, int* nu, flo
 #define FX_NOALLOC_STAGE_BYTES (64u << 20)
 fx_status fx_state_init_equilibrium_noalloc(fx_grid* h, const double* prim, void* state,
                                             int state_precision, void* cuda_stream);
+
+/* ---- Objective and adjoint (Cartesian grids) --------------------------------------------
+ *
+ * Objective J (reading R19 of the design notes): the radiation energy that the update itself
+ * moves out through the upper x boundary, J = sum over steps of dt (Phi(U^n) + Phi(U^(1)))/2,
+ * Phi = sum over groups and upper-x faces of face area x (corrected HLL energy flux + v* E
+ * upwind term), Sec. 4 and Eqs. 17-19 of the paper.  Its gradient with respect to the initial
+ * state and to the opacity normalisation kappa0 comes from a hand-written adjoint of the stage
+ * (interaction: implicit-function derivative of the Newton system, Eqs. 25-28), run backwards
+ * over checkpoints taken every k steps and recomputed segment by segment. */
+
+/* Accumulate J during subsequent fx_step calls (on != 0; resets J to 0) or stop (on == 0).
+ * While on, each stage enqueues one more small reduction kernel.  FX_ERR_UNSUPPORTED on
+ * curvilinear grids. */
+fx_status fx_objective_enable(fx_grid* h, int on);
+/* J accumulated since fx_objective_enable (synchronises). */
+fx_status fx_boundary_energy_out(fx_grid* h, double* J);
+/* Set the opacity normalisation kappa0 (>= 0) used by subsequent steps. */
+fx_status fx_set_kappa0(fx_grid* h, double kappa0);
+/* Replace the density of the current state by rho (ncell values in the state's precision, host
+ * or device), holding pressure, velocity, E_g and F_g fixed: m = rho v, rho e adjusted by the
+ * kinetic energy change.  Host sources synchronise; device sources are stream-ordered. */
+fx_status fx_state_set_density(fx_grid* h, const void* rho, int rho_precision, int rho_is_device);
+
+/* Bytes of the caller-owned adjoint workspace for nsteps steps with a checkpoint every k steps:
+ * ceil(nsteps/k) checkpoints, k + 1 segment states, 3k stage records, adjoint buffers. */
+fx_status fx_adjoint_workspace_bytes(const fx_grid* h, int nsteps, int k, size_t* bytes);
+/* Forward pass: from the current state, nsteps steps of size dt accumulating J (written to *J)
+ * and storing the checkpoints in adj_ws (device memory, 256-byte aligned, at least the size
+ * fx_adjoint_workspace_bytes gives).  The handle's state is left unchanged.  Synchronises. */
+fx_status fx_adjoint_forward(fx_grid* h, double dt, int nsteps, int k, void* adj_ws, size_t adj_bytes,
+                             double* J);
+/* Backward pass over the checkpoints a preceding fx_adjoint_forward (same dt, nsteps, k, adj_ws
+ * and kappa0) stored: gradients of seed * J.  grad_state (device, fx_state_elems() values of the
+ * state's precision, state layout) receives dJ/dU^0 in conserved variables; grad_rho (device,
+ * ncell values) receives dJ/drho(x, 0) at fixed pressure, velocity, E_g and F_g; *dJ_dkappa0 the
+ * kappa0 derivative.  Any output may be NULL.  Synchronises; returns the sticky status of the
+ * recomputed steps (FX_ERR_NEWTON etc.) like fx_sync. */
+fx_status fx_adjoint_backward(fx_grid* h, double dt, int nsteps, int k, void* adj_ws, size_t adj_bytes,
+                              double seed, void* grad_state, void* grad_rho, double* dJ_dkappa0);
+/* Both passes (seed 1). */
+fx_status fx_adjoint(fx_grid* h, double dt, int nsteps, int k, void* adj_ws, size_t adj_bytes,
+                     void* grad_state, void* grad_rho, double* J, double* dJ_dkappa0);
 
 const char* fx_last_error(const fx_grid* h);
 void fx_clear_error(fx_grid* h);

@@ -27,7 +27,7 @@ FP32_FLAGS = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
 
 
 def _compile(src: str, extra: list[str]) -> str:
-    fp32 = os.path.basename(src).startswith("fx_stage_f32")
+    fp32 = os.path.basename(src).startswith(("fx_stage_f32", "fx_adjoint_f32"))
     cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *(FP32_FLAGS if fp32 else []), *extra, "-c", src]
     tag = hashlib.sha1(" ".join(cmd[1:]).encode()).hexdigest()[:10]
     obj = os.path.join(BUILD, f"{os.path.basename(src)}.{tag}.o")

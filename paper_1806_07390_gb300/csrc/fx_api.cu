@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/fx.h"
+#include "fx_adjoint.cuh"
 #include "fx_launch.h"
 
 using namespace fx;
@@ -129,6 +130,12 @@ struct fx_grid {
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   size_t nev = 0;
+  // objective (boundary radiation energy outflow, reading R19): per-row face fluxes of one stage
+  // [rows][G] and FP64 accumulators obj[0] = J, obj[1] = dJ/dkappa0 (adjoint)
+  bool objective = false;
+  size_t off_phi = 0, off_obj = 0;
+  int64_t phi_rows = 0;
+  double phi_area = 0.0;
 };
 
 namespace {
@@ -470,6 +477,54 @@ __global__ void k_totals_final(const double* part, int nblocks, double* out) {
   out[q] = a.s + a.c;
 }
 
+// acc[0] += w * sum(x[0..n)), deterministic (one block, Neumaier per thread, fixed tree).
+template <class T>
+__global__ void __launch_bounds__(256) k_sum_into(const T* x, int64_t n, double w, double* acc) {
+  KS a = {0.0, 0.0};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) ks_add(a, (double)x[i]);
+  __shared__ KS sh[256];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) ks_merge(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) acc[0] += w * (sh[0].s + sh[0].c);
+}
+
+// dJ/drho(x, 0) at fixed pressure, velocity and radiation (reading R20): with U = (rho, rho v,
+// p/(gamma-1) + rho |v|^2/2, E, F), dU/drho = (1, v, |v|^2/2, 0, 0).
+template <class R>
+__global__ void k_grad_rho(const R* U, const R* lam, DevGrid g, R* out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int64_t n = g.ncell;
+  const R rho = U[c];
+  R s = lam[c], v2 = R(0);
+  for (int q = 0; q < g.D; ++q) {
+    const R v = U[(1 + q) * n + c] / rho;
+    s += lam[(1 + q) * n + c] * v;
+    v2 += v * v;
+  }
+  out[c] = s + lam[(1 + g.D) * n + c] * R(0.5) * v2;
+}
+
+template <class R>
+__global__ void k_set_density(R* U, const R* rho_new, DevGrid g) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int64_t n = g.ncell;
+  const R rho = U[c], rn = rho_new[c];
+  R v2 = R(0);
+  for (int q = 0; q < g.D; ++q) {
+    const R v = U[(1 + q) * n + c] / rho;
+    U[(1 + q) * n + c] = rn * v;
+    v2 += v * v;
+  }
+  U[(1 + g.D) * n + c] += R(0.5) * (rn - rho) * v2;
+  U[c] = rn;
+}
+
 bool has_ws(fx_grid* h) { return h && h->ws; }
 
 // Per-launch scalar constants, computed once in FP64 and rounded to the kernel types.
@@ -500,8 +555,9 @@ Consts<T> make_consts(const fx_grid* h, double dt, double dts, double alpha, boo
   return k;
 }
 
-template <class R, class NT>
-fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
+// Stage arguments common to every stage of a handle (tables, constants, buffers).
+template <class R>
+StageArgs<R> stage_args(fx_grid* h) {
   StageArgs<R> a{};
   a.g = h->dg;
   for (int d = 0; d < 3; ++d) a.tab[d] = dev_tab<R>(h, d < h->D ? d : 0);
@@ -520,48 +576,261 @@ fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
   a.pk = h->pk;
   a.status = reinterpret_cast<unsigned*>(h->ws + h->off_status);
   a.chunk = h->chunk;
+  a.phi_area = (R)h->phi_area;
+  return a;
+}
+
+// Set the stage-dependent fields: stage 1 (U1 = U0 + dt L(U0), interaction with dt) or stage 2
+// (U = U0/2 + (U1 + dt L(U1))/2, interaction with dt/2; reading R10).
+template <class R>
+void set_stage(fx_grid* h, StageArgs<R>& a, int stage, double dt) {
+  const bool f32n = sizeof(R) == 4;  // FP32 group sums bound the attainable residual
   a.dt = dt;
+  if (stage == 1) {
+    a.dts = dt;
+    a.alpha = 0.0;
+    a.kd = make_consts<double>(h, dt, dt, 0.0, f32n);
+    a.kf = make_consts<float>(h, dt, dt, 0.0, f32n);
+  } else {
+    a.dts = 0.5 * dt;
+    a.alpha = 0.5;
+    a.kd = make_consts<double>(h, dt, 0.5 * dt, 0.5, f32n);
+    a.kf = make_consts<float>(h, dt, 0.5 * dt, 0.5, f32n);
+  }
+}
+
+// Enqueue one stage (both kernels), with the per-kernel timing events when enabled and the
+// objective's reduction when a.phi_out is set.
+template <class R, class NT>
+fx_status launch_one_stage(fx_grid* h, const StageArgs<R>& a, const char* what) {
+  cudaEvent_t e3[3] = {nullptr, nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  if (h->timing) {
+    while (h->ev.size() < h->nev + 3) {
+      cudaEvent_t x;
+      e = cudaEventCreate(&x);
+      if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
+      h->ev.push_back(x);
+    }
+    for (int q = 0; q < 3; ++q) e3[q] = h->ev[h->nev + q];
+    h->nev += 3;
+    e = cudaEventRecord(e3[0], h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
+  }
+  switch (h->D) {
+    case 1: e = launch_stage<R, 1, NT>(a, h->GP, h->stream, e3[1]); break;
+    case 2: e = launch_stage<R, 2, NT>(a, h->GP, h->stream, e3[1]); break;
+    default: e = launch_stage<R, 3, NT>(a, h->GP, h->stream, e3[1]); break;
+  }
+  if (e == cudaSuccess && e3[2]) e = cudaEventRecord(e3[2], h->stream);
+  if (e == cudaSuccess && a.phi_out) {
+    // J += dt/2 Phi(U_in): this stage's share of the RK-weighted boundary outflow
+    k_sum_into<R><<<1, 256, 0, h->stream>>>(a.phi_out, h->phi_rows * h->G, 0.5 * a.dt,
+                                             reinterpret_cast<double*>(h->ws + h->off_obj));
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, what);
+  return FX_OK;
+}
+
+template <class R, class NT>
+fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
+  StageArgs<R> a = stage_args<R>(h);
   R* A = reinterpret_cast<R*>(h->ws + h->off_A);
   R* B = reinterpret_cast<R*>(h->ws + h->off_B);
-  const bool f32n = sizeof(R) == 4;  // FP32 group sums bound the attainable residual
-  const Consts<double> kd1 = make_consts<double>(h, dt, dt, 0.0, f32n);
-  const Consts<float> kf1 = make_consts<float>(h, dt, dt, 0.0, f32n);
-  const Consts<double> kd2 = make_consts<double>(h, dt, 0.5 * dt, 0.5, f32n);
-  const Consts<float> kf2 = make_consts<float>(h, dt, 0.5 * dt, 0.5, f32n);
-  auto stage = [&](const char* what) -> fx_status {
-    cudaEvent_t e3[3] = {nullptr, nullptr, nullptr};
-    cudaError_t e = cudaSuccess;
-    if (h->timing) {
-      while (h->ev.size() < h->nev + 3) {
-        cudaEvent_t x;
-        e = cudaEventCreate(&x);
-        if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
-        h->ev.push_back(x);
-      }
-      for (int q = 0; q < 3; ++q) e3[q] = h->ev[h->nev + q];
-      h->nev += 3;
-      e = cudaEventRecord(e3[0], h->stream);
-      if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
-    }
-    switch (h->D) {
-      case 1: e = launch_stage<R, 1, NT>(a, h->GP, h->stream, e3[1]); break;
-      case 2: e = launch_stage<R, 2, NT>(a, h->GP, h->stream, e3[1]); break;
-      default: e = launch_stage<R, 3, NT>(a, h->GP, h->stream, e3[1]); break;
-    }
-    if (e == cudaSuccess && e3[2]) e = cudaEventRecord(e3[2], h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, what);
-    return FX_OK;
-  };
+  if (h->objective) a.phi_out = reinterpret_cast<R*>(h->ws + h->off_phi);
+  StageArgs<R> a1 = a, a2 = a;
+  set_stage(h, a1, 1, dt);
+  set_stage(h, a2, 2, dt);
+  a1.in = A; a1.base = nullptr; a1.out = B;
+  a2.in = B; a2.base = A; a2.out = A;
   for (int s = 0; s < nsteps; ++s) {
-    // stage 1: U1 = U0 + dt L(U0), then the interaction with dt
-    a.in = A; a.base = nullptr; a.out = B; a.dts = dt; a.alpha = 0.0; a.kd = kd1; a.kf = kf1;
-    fx_status st = stage("stage 1 launch");
+    fx_status st = launch_one_stage<R, NT>(h, a1, "stage 1 launch");
     if (st != FX_OK) return st;
-    // stage 2: U = U0/2 + (U1 + dt L(U1))/2, then the interaction with dt/2 (reading R10)
-    a.in = B; a.base = A; a.out = A; a.dts = 0.5 * dt; a.alpha = 0.5; a.kd = kd2; a.kf = kf2;
-    st = stage("stage 2 launch");
+    st = launch_one_stage<R, NT>(h, a2, "stage 2 launch");
     if (st != FX_OK) return st;
   }
+  return FX_OK;
+}
+
+// ---- adjoint (config of the boundary-outflow objective; Cartesian grids)
+
+// Adjoint workspace layout for nsteps steps with a checkpoint every k steps.
+struct AdjLayout {
+  size_t S = 0, Tn = 0, LWn = 0;
+  int nseg = 0, k = 0;
+  size_t off_ckpt = 0, off_U = 0, off_U1 = 0, off_pre1 = 0, off_pre2 = 0, off_t1 = 0, off_t2 = 0,
+         off_LA = 0, off_LB = 0, off_LP = 0, off_LW = 0, off_kpart = 0, bytes = 0;
+  unsigned nblk = 0;
+};
+AdjLayout adj_layout(const fx_grid* h, int nsteps, int k) {
+  AdjLayout L;
+  L.k = k;
+  L.nseg = nsteps > 0 ? (nsteps + k - 1) / k : 1;
+  L.S = align_up(h->state_bytes);
+  L.Tn = align_up((size_t)h->ncell * h->elem);
+  L.LWn = align_up((size_t)h->ncell * (2 + h->D + h->G * (1 + h->D) + h->G) * h->elem);
+  L.nblk = adj_cell_blocks(h->ncell, h->GP);
+  size_t off = 0;
+  L.off_ckpt = off; off += (size_t)L.nseg * L.S;
+  L.off_U = off; off += (size_t)(k + 1) * L.S;   // U[0] unused (the checkpoint), U[1..k]
+  L.off_U1 = off; off += (size_t)k * L.S;
+  L.off_pre1 = off; off += (size_t)k * L.S;
+  L.off_pre2 = off; off += (size_t)k * L.S;
+  L.off_t1 = off; off += (size_t)k * L.Tn;
+  L.off_t2 = off; off += (size_t)k * L.Tn;
+  L.off_LA = off; off += L.S;
+  L.off_LB = off; off += L.S;
+  L.off_LP = off; off += L.S;
+  L.off_LW = off; off += L.LWn;
+  L.off_kpart = off; off += align_up((size_t)L.nblk * sizeof(double));
+  L.bytes = off;
+  return L;
+}
+
+// Pass 1 (forward): from the current state, nsteps steps with the objective, a checkpoint of
+// the state every k steps (checkpoint 0 = the current state); the handle's state is unchanged.
+// Pass 2 (backward): segment by segment from the last checkpoint, recompute the segment's
+// steps recording each stage's pre-interaction state and temperature, then run the stage
+// adjoints backwards through it.  seed scales the objective (the adjoint of J).
+template <class R, class NT>
+fx_status adjoint_impl(fx_grid* h, double dt, int nsteps, int k, unsigned char* ws, bool fwd, bool bwd,
+                       double seed, void* grad_state, void* grad_rho, double* J, double* dJ_dkappa0) {
+  const AdjLayout L = adj_layout(h, nsteps, k);
+  cudaStream_t st = h->stream;
+  auto P = [&](size_t off) { return reinterpret_cast<R*>(ws + off); };
+  auto ckpt = [&](int j) { return P(L.off_ckpt + (size_t)j * L.S); };
+  auto Ub = [&](int m) { return P(L.off_U + (size_t)m * L.S); };
+  auto U1b = [&](int m) { return P(L.off_U1 + (size_t)m * L.S); };
+  auto pre1 = [&](int m) { return P(L.off_pre1 + (size_t)m * L.S); };
+  auto pre2 = [&](int m) { return P(L.off_pre2 + (size_t)m * L.S); };
+  auto t1 = [&](int m) { return P(L.off_t1 + (size_t)m * L.Tn); };
+  auto t2 = [&](int m) { return P(L.off_t2 + (size_t)m * L.Tn); };
+  R* LA = P(L.off_LA);
+  R* LB = P(L.off_LB);
+  R* LP = P(L.off_LP);
+  R* LW = P(L.off_LW);
+  double* kpart = reinterpret_cast<double*>(ws + L.off_kpart);
+  double* obj = reinterpret_cast<double*>(h->ws + h->off_obj);
+  cudaError_t e;
+  StageArgs<R> a = stage_args<R>(h);
+  StageArgs<R> a1 = a, a2 = a;
+  set_stage(h, a1, 1, dt);
+  set_stage(h, a2, 2, dt);
+  const bool tim = h->timing;
+  h->timing = false;
+  if (fwd) {
+    e = cudaMemsetAsync(obj, 0, sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ckpt(0), h->ws + h->off_A, h->state_bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) { h->timing = tim; return cuda_fail(h, e, "adjoint setup"); }
+    a1.phi_out = a2.phi_out = reinterpret_cast<R*>(h->ws + h->off_phi);
+    R* cur = ckpt(0);
+    for (int n = 0; n < nsteps; ++n) {
+      R* nxt = ((n + 1) % k == 0 && n + 1 < nsteps) ? ckpt((n + 1) / k) : Ub(n & 1);
+      a1.in = cur; a1.base = nullptr; a1.out = U1b(0);
+      a2.in = U1b(0); a2.base = cur; a2.out = nxt;
+      fx_status s1 = launch_one_stage<R, NT>(h, a1, "adjoint forward pass");
+      if (s1 == FX_OK) s1 = launch_one_stage<R, NT>(h, a2, "adjoint forward pass");
+      if (s1 != FX_OK) { h->timing = tim; return s1; }
+      cur = nxt;
+    }
+    a1.phi_out = a2.phi_out = nullptr;
+    if (J) {
+      e = cudaMemcpyAsync(J, obj, sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) { h->timing = tim; return cuda_fail(h, e, "objective read"); }
+    }
+  }
+  if (!bwd) { h->timing = tim; return FX_OK; }
+
+  // reverse sweep, one checkpoint segment at a time
+  AdjArgs<R> b{};
+  b.g = h->dg;
+  for (int d = 0; d < 3; ++d) {
+    b.tab[d] = a.tab[d];
+    b.uniform[d] = a.uniform[d];
+    for (int q = 0; q < NTAB; ++q) b.urow[d][q] = a.urow[d][q];
+  }
+  b.gc = a.gc;
+  b.pk = a.pk;
+  b.ptab = a.ptab;
+  b.lam_w = LW;
+  b.kpart = kpart;
+  b.phi_area = (R)h->phi_area;
+  b.dt = dt;
+  b.wJ = (R)(0.5 * dt * seed);
+  AdjArgs<R> b1 = b, b2 = b;
+  b1.alpha = 0.0; b1.kd = a1.kd; b1.kf = a1.kf;
+  b2.alpha = 0.5; b2.kd = a2.kd; b2.kf = a2.kf;
+  e = cudaMemsetAsync(LA, 0, h->state_bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(obj + 1, 0, sizeof(double), st);
+  if (e != cudaSuccess) { h->timing = tim; return cuda_fail(h, e, "adjoint setup"); }
+  auto run = [&](AdjArgs<R>& bb) -> cudaError_t {
+    cudaError_t x;
+    switch (h->D) {
+      case 1: x = adj_launch_couple<R, 1>(bb, h->GP, st); break;
+      case 2: x = adj_launch_couple<R, 2>(bb, h->GP, st); break;
+      default: x = adj_launch_couple<R, 3>(bb, h->GP, st); break;
+    }
+    if (x != cudaSuccess) return x;
+    k_sum_into<double><<<1, 256, 0, st>>>(kpart, L.nblk, 1.0, obj + 1);
+    x = cudaMemsetAsync(LW, 0, L.LWn, st);
+    if (x != cudaSuccess) return x;
+    switch (h->D) {
+      case 1: x = adj_launch_face<R, 1>(bb, st); break;
+      case 2: x = adj_launch_face<R, 2>(bb, st); break;
+      default: x = adj_launch_face<R, 3>(bb, st); break;
+    }
+    if (x != cudaSuccess) return x;
+    switch (h->D) {
+      case 1: x = adj_launch_cell<R, 1>(bb, h->GP, st); break;
+      case 2: x = adj_launch_cell<R, 2>(bb, h->GP, st); break;
+      default: x = adj_launch_cell<R, 3>(bb, h->GP, st); break;
+    }
+    if (x != cudaSuccess) return x;
+    k_sum_into<double><<<1, 256, 0, st>>>(kpart, L.nblk, 1.0, obj + 1);
+    return cudaGetLastError();
+  };
+  for (int j = L.nseg - 1; j >= 0 && nsteps > 0; --j) {
+    const int s0 = j * k, s1 = std::min(s0 + k, nsteps), ns = s1 - s0;
+    // recompute the segment, recording each stage's pre-interaction state and temperature
+    for (int m = 0; m < ns; ++m) {
+      R* Um = m == 0 ? ckpt(j) : Ub(m);
+      a1.in = Um; a1.base = nullptr; a1.out = U1b(m); a1.pre_out = pre1(m); a1.tstar_out = t1(m);
+      a2.in = U1b(m); a2.base = Um; a2.out = Ub(m + 1); a2.pre_out = pre2(m); a2.tstar_out = t2(m);
+      fx_status s2 = launch_one_stage<R, NT>(h, a1, "adjoint recomputation");
+      if (s2 == FX_OK) s2 = launch_one_stage<R, NT>(h, a2, "adjoint recomputation");
+      if (s2 != FX_OK) { h->timing = tim; return s2; }
+    }
+    for (int m = ns - 1; m >= 0; --m) {
+      R* Um = m == 0 ? ckpt(j) : Ub(m);
+      // stage 2: lam(U^(n+1)) = LA -> lam(U^(1)) = LB, lam(U^n) partial = LA
+      b2.in = U1b(m); b2.pre = pre2(m); b2.tstar = t2(m); b2.lam_out = LA; b2.lam_pre = LP;
+      b2.lam_in = LB; b2.lam_base = LA; b2.accumulate_in = 0;
+      e = run(b2);
+      if (e != cudaSuccess) { h->timing = tim; return cuda_fail(h, e, "adjoint stage 2"); }
+      // stage 1: lam(U^(1)) = LB -> lam(U^n) += ...
+      b1.in = Um; b1.pre = pre1(m); b1.tstar = t1(m); b1.lam_out = LB; b1.lam_pre = LP;
+      b1.lam_in = LA; b1.lam_base = nullptr; b1.accumulate_in = 1;
+      e = run(b1);
+      if (e != cudaSuccess) { h->timing = tim; return cuda_fail(h, e, "adjoint stage 1"); }
+    }
+  }
+  h->timing = tim;
+  if (grad_state) {
+    e = cudaMemcpyAsync(grad_state, LA, h->state_bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "gradient copy");
+  }
+  if (grad_rho) {
+    k_grad_rho<R><<<(unsigned)((h->ncell + 255) / 256), 256, 0, st>>>(ckpt(0), LA, h->dg, (R*)grad_rho);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "density gradient");
+  }
+  double res = 0.0;
+  e = cudaMemcpyAsync(&res, obj + 1, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint result");
+  if (dJ_dkappa0) *dJ_dkappa0 = res;
   return FX_OK;
 }
 
@@ -710,6 +979,12 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   size_t vol_bytes = 0;
   for (int d = 0; d < P.dims; ++d) vol_bytes += align_up((size_t)(P.n[d] + 4) * sizeof(double));
   off += vol_bytes;
+  // objective: one row of upper-x boundary faces per (y, z) line; Cartesian face area
+  h->phi_rows = (P.dims > 1 ? P.n[1] : 1) * (P.dims > 2 ? P.n[2] : 1);
+  h->phi_area = 1.0;
+  for (int d = 1; d < P.dims; ++d) h->phi_area *= (P.x_hi[d] - P.x_lo[d]) / (double)P.n[d];
+  h->off_phi = off; off = align_up(off + (size_t)h->phi_rows * h->G * h->elem);
+  h->off_obj = off; off = align_up(off + 8 * sizeof(double));
   h->ws_bytes = off;
   *workspace_bytes = off;
   *out = h;
@@ -718,7 +993,101 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
 
 size_t fx_state_elems(const fx_grid* h) { return h ? (size_t)h->ncell * h->NV : 0; }
 
-int fx_launches_per_step(const fx_grid* h) { return h ? 4 : 0; }
+int fx_launches_per_step(const fx_grid* h) { return h ? (h->objective ? 6 : 4) : 0; }
+
+fx_status fx_objective_enable(fx_grid* h, int on) {
+  if (!h) return FX_ERR_ARG;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  if (on && h->P.geom != FX_CART) return fail(h, FX_ERR_UNSUPPORTED, "the outflow objective needs a Cartesian grid");
+  h->objective = on != 0;
+  cudaError_t e = cudaMemsetAsync(h->ws + h->off_obj, 0, sizeof(double), h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "objective reset");
+  return FX_OK;
+}
+
+fx_status fx_boundary_energy_out(fx_grid* h, double* J) {
+  if (!h || !J) return FX_ERR_ARG;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  cudaError_t e = cudaMemcpyAsync(J, h->ws + h->off_obj, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "objective read");
+  return FX_OK;
+}
+
+fx_status fx_set_kappa0(fx_grid* h, double kappa0) {
+  if (!h || !(kappa0 >= 0.0)) return FX_ERR_ARG;
+  h->P.kappa0 = kappa0;
+  h->dg.kappa0 = kappa0;
+  return FX_OK;
+}
+
+fx_status fx_adjoint_workspace_bytes(const fx_grid* h, int nsteps, int k, size_t* bytes) {
+  if (!h || !bytes || nsteps < 0 || k < 1) return FX_ERR_ARG;
+  *bytes = adj_layout(h, nsteps, k).bytes;
+  return FX_OK;
+}
+
+static fx_status adjoint_entry(fx_grid* h, double dt, int nsteps, int k, void* adj_ws, size_t adj_bytes,
+                               bool fwd, bool bwd, double seed, void* grad_state, void* grad_rho,
+                               double* J, double* dJ_dkappa0) {
+  if (!h) return FX_ERR_ARG;
+  if (h->sticky != FX_OK) return h->sticky;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  if (!(dt > 0.0) || nsteps < 0 || k < 1) return fail(h, FX_ERR_ARG, "dt must be > 0, nsteps >= 0, k >= 1");
+  if (h->P.geom != FX_CART) return fail(h, FX_ERR_UNSUPPORTED, "the adjoint supports Cartesian grids");
+  if (!adj_ws || adj_bytes < adj_layout(h, nsteps, k).bytes || (reinterpret_cast<uintptr_t>(adj_ws) % kAlign) != 0)
+    return fail(h, FX_ERR_WORKSPACE, "adjoint workspace missing, too small or not 256-byte aligned");
+  unsigned char* ws = static_cast<unsigned char*>(adj_ws);
+  fx_status st;
+  if (h->elem == 8)
+    st = adjoint_impl<double, double>(h, dt, nsteps, k, ws, fwd, bwd, seed, grad_state, grad_rho, J, dJ_dkappa0);
+  else if (h->P.precision == FX_FP32_F64NEWTON)
+    st = adjoint_impl<float, double>(h, dt, nsteps, k, ws, fwd, bwd, seed, grad_state, grad_rho, J, dJ_dkappa0);
+  else
+    st = adjoint_impl<float, float>(h, dt, nsteps, k, ws, fwd, bwd, seed, grad_state, grad_rho, J, dJ_dkappa0);
+  if (st != FX_OK) return st;
+  return fx_sync(h);
+}
+
+fx_status fx_adjoint_forward(fx_grid* h, double dt, int nsteps, int k, void* adj_ws, size_t adj_bytes,
+                             double* J) {
+  return adjoint_entry(h, dt, nsteps, k, adj_ws, adj_bytes, true, false, 1.0, nullptr, nullptr, J, nullptr);
+}
+
+fx_status fx_adjoint_backward(fx_grid* h, double dt, int nsteps, int k, void* adj_ws, size_t adj_bytes,
+                              double seed, void* grad_state, void* grad_rho, double* dJ_dkappa0) {
+  return adjoint_entry(h, dt, nsteps, k, adj_ws, adj_bytes, false, true, seed, grad_state, grad_rho,
+                       nullptr, dJ_dkappa0);
+}
+
+fx_status fx_adjoint(fx_grid* h, double dt, int nsteps, int k, void* adj_ws, size_t adj_bytes,
+                     void* grad_state, void* grad_rho, double* J, double* dJ_dkappa0) {
+  return adjoint_entry(h, dt, nsteps, k, adj_ws, adj_bytes, true, true, 1.0, grad_state, grad_rho, J,
+                       dJ_dkappa0);
+}
+
+// Replace the density of the current state, holding pressure, velocity and radiation fixed
+// (reading R20): m = rho_new v, rho e = rho e - rho |v|^2/2 + rho_new |v|^2/2.
+fx_status fx_state_set_density(fx_grid* h, const void* rho, int rho_precision, int rho_is_device) {
+  if (!h || !rho) return FX_ERR_ARG;
+  if (h->sticky != FX_OK) return h->sticky;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  const int my = h->elem == 8 ? FX_FP64 : FX_FP32;
+  if (rho_precision != my) return fail(h, FX_ERR_ARG, "density precision must match the state");
+  const size_t nb = (size_t)h->ncell * h->elem;
+  // stage the new density in the second state buffer (free between steps)
+  cudaError_t e = cudaMemcpyAsync(h->ws + h->off_B, rho, nb, rho_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "density upload");
+  const unsigned blocks = (unsigned)((h->ncell + 255) / 256);
+  if (h->elem == 8)
+    k_set_density<double><<<blocks, 256, 0, h->stream>>>((double*)(h->ws + h->off_A), (const double*)(h->ws + h->off_B), h->dg);
+  else
+    k_set_density<float><<<blocks, 256, 0, h->stream>>>((float*)(h->ws + h->off_A), (const float*)(h->ws + h->off_B), h->dg);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && !rho_is_device) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "density update");
+  return FX_OK;
+}
 
 fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_stream) {
   if (!h) return FX_ERR_ARG;

@@ -58,30 +58,31 @@ template <class R> struct Tab {
 
 // ---------------------------------------------------------------------------------------------
 // Parabolic (n = 2) reconstruction of one variable in one cell (Sec. 5.1; readings R2-R4).
-// ip: padded index of the cell (cell i -> i + 2).
+// ip: padded index of the cell (cell i -> i + 2).  R: table type; V: value type (R itself, or a
+// forward-mode dual number when the adjoint forms local Jacobians).
 // ---------------------------------------------------------------------------------------------
-template <class R>
-__device__ __forceinline__ void recon_parabolic(const Tab<R>& t, int ip, R pm, R p0, R pp, R& a, R& b) {
-  R dl = p0 - pm, dr = pp - p0;
+template <class R, class V>
+__device__ __forceinline__ void recon_parabolic(const Tab<R>& t, int ip, V pm, V p0, V pp, V& a, V& b) {
+  V dl = p0 - pm, dr = pp - p0;
   if (dl * dr <= R(0)) { a = p0; b = p0; return; }  // extremum of the data (R4)
   a = t(T_WA0, ip) * pm + t(T_WA1, ip) * p0 + t(T_WA2, ip) * pp;
   b = t(T_WB0, ip) * pm + t(T_WB1, ip) * p0 + t(T_WB2, ip) * pp;
   // face-interval monotonicity (R2): clamp between the zero-slope values at the two centroids
   {
-    R lo = pm + dl * t(T_SL2, ip), hi = p0 - dl * t(T_TL2, ip);
-    if (dl < R(0)) { R s = lo; lo = hi; hi = s; }
+    V lo = pm + dl * t(T_SL2, ip), hi = p0 - dl * t(T_TL2, ip);
+    if (dl < R(0)) { V s = lo; lo = hi; hi = s; }
     a = a < lo ? lo : (a > hi ? hi : a);
   }
   {
-    R lo = p0 + dr * t(T_SR2, ip), hi = pp - dr * t(T_TR2, ip);
-    if (dr < R(0)) { R s = lo; lo = hi; hi = s; }
+    V lo = p0 + dr * t(T_SR2, ip), hi = pp - dr * t(T_TR2, ip);
+    if (dr < R(0)) { V s = lo; lo = hi; hi = s; }
     b = b < lo ? lo : (b > hi ? hi : b);
   }
   // system 2 end slopes; opposite signs mean an extremum inside the cell (R3)
-  R sl = t(T_AL0, ip) * a + t(T_AL1, ip) * p0 + t(T_AL2, ip) * b;
-  R sr = t(T_AR0, ip) * a + t(T_AR1, ip) * p0 + t(T_AR2, ip) * b;
+  V sl = t(T_AL0, ip) * a + t(T_AL1, ip) * p0 + t(T_AL2, ip) * b;
+  V sr = t(T_AR0, ip) * a + t(T_AR1, ip) * p0 + t(T_AR2, ip) * b;
   if (sl * sr >= R(0)) return;
-  R asl = fabs(sl), asr = fabs(sr);
+  V asl = fabs(sl), asr = fabs(sr);
   if (asl == asr) { a = p0; b = p0; return; }
   if (asl < asr) b = a + (p0 - a) * t(T_RHL, ip);  // zero slope at the lower face
   else a = b + (p0 - b) * t(T_RHR, ip);            // zero slope at the upper face
@@ -93,14 +94,14 @@ template <class R> struct MCCoef { R il, ir, ic, dl, dr; };
 template <class R> __device__ __forceinline__ MCCoef<R> mc_coef(const Tab<R>& t, int ip) {
   return {t(T_IL, ip), t(T_IR, ip), t(T_IC, ip), t(T_DL, ip), t(T_DR, ip)};
 }
-template <class R>
-__device__ __forceinline__ void recon_linear_c(const MCCoef<R>& c, R pm, R p0, R pp, R& a, R& b) {
-  R sL = (p0 - pm) * c.il;
-  R sR = (pp - p0) * c.ir;
-  R s = R(0);
+template <class R, class V>
+__device__ __forceinline__ void recon_linear_c(const MCCoef<R>& c, V pm, V p0, V pp, V& a, V& b) {
+  V sL = (p0 - pm) * c.il;
+  V sR = (pp - p0) * c.ir;
+  V s = V(R(0));
   if (sL * sR > R(0)) {
-    R sC = (pp - pm) * c.ic;
-    R m = fmin(fmin(R(2) * fabs(sL), R(2) * fabs(sR)), fabs(sC));
+    V sC = (pp - pm) * c.ic;
+    V m = fmin(fmin(R(2) * fabs(sL), R(2) * fabs(sR)), fabs(sC));
     s = sC > R(0) ? m : -m;
   }
   a = p0 + s * c.dl;
@@ -128,30 +129,30 @@ __device__ __forceinline__ void recon_linear(const Tab<R>& t, int ip, R pm, R p0
 // Output: fluxes of (rho, rho u_n, rho u_t1, rho u_t2, rho e) per unit physical area and the
 // contact speed (the particle velocity used to upwind radiation advection, Eq. 19).
 // ---------------------------------------------------------------------------------------------
-template <class R, int D>
-__device__ __forceinline__ void hllc(R gam, const R* L, const R* Rs, R* f, R& vstar) {
+template <class R, int D, class V = R>
+__device__ __forceinline__ void hllc(R gam, const V* L, const V* Rs, V* f, V& vstar) {
   const R gm1 = gam - R(1);
-  R rl = L[0], pl = L[1], ul = L[2];
-  R rr = Rs[0], pr = Rs[1], ur = Rs[2];
-  R kl = ul * ul, kr = ur * ur;
+  V rl = L[0], pl = L[1], ul = L[2];
+  V rr = Rs[0], pr = Rs[1], ur = Rs[2];
+  V kl = ul * ul, kr = ur * ur;
 #pragma unroll
   for (int q = 1; q < D; ++q) { kl += L[2 + q] * L[2 + q]; kr += Rs[2 + q] * Rs[2 + q]; }
-  R El = pl / gm1 + R(0.5) * rl * kl;
-  R Er = pr / gm1 + R(0.5) * rr * kr;
-  R al = sqrt(gam * pl / rl), ar = sqrt(gam * pr / rr);
-  R sl = sqrt(rl), sr = sqrt(rr);
-  R iw = R(1) / (sl + sr);
-  R Ht = (sl * ((El + pl) / rl) + sr * ((Er + pr) / rr)) * iw;
-  R ut = (sl * ul + sr * ur) * iw;
-  R v2 = ut * ut;
+  V El = pl / gm1 + R(0.5) * rl * kl;
+  V Er = pr / gm1 + R(0.5) * rr * kr;
+  V al = sqrt(gam * pl / rl), ar = sqrt(gam * pr / rr);
+  V sl = sqrt(rl), sr = sqrt(rr);
+  V iw = R(1) / (sl + sr);
+  V Ht = (sl * ((El + pl) / rl) + sr * ((Er + pr) / rr)) * iw;
+  V ut = (sl * ul + sr * ur) * iw;
+  V v2 = ut * ut;
 #pragma unroll
-  for (int q = 1; q < D; ++q) { R vq = (sl * L[2 + q] + sr * Rs[2 + q]) * iw; v2 += vq * vq; }
-  R at2 = gm1 * (Ht - R(0.5) * v2);
-  R at = sqrt(at2 > R(0) ? at2 : R(0));
-  R SL = fmin(ul - al, ut - at);
-  R SR = fmax(ur + ar, ut + at);
-  R dl = rl * (SL - ul), dr = rr * (SR - ur);
-  R Ss = (pr - pl + ul * dl - ur * dr) / (dl - dr);
+  for (int q = 1; q < D; ++q) { V vq = (sl * L[2 + q] + sr * Rs[2 + q]) * iw; v2 += vq * vq; }
+  V at2 = gm1 * (Ht - R(0.5) * v2);
+  V at = sqrt(at2 > R(0) ? at2 : V(R(0)));
+  V SL = fmin(ul - al, ut - at);
+  V SR = fmax(ur + ar, ut + at);
+  V dl = rl * (SL - ul), dr = rr * (SR - ur);
+  V Ss = (pr - pl + ul * dl - ur * dr) / (dl - dr);
   vstar = Ss;
   if (SL >= R(0)) {
     f[0] = rl * ul;
@@ -170,16 +171,16 @@ __device__ __forceinline__ void hllc(R gam, const R* L, const R* Rs, R* f, R& vs
     return;
   }
   const bool left = Ss >= R(0);
-  const R* W = left ? L : Rs;
-  R rk = W[0], pk = W[1], uk = W[2], Ek = left ? El : Er, Sk = left ? SL : SR;
-  R sku = Sk - uk;
-  R fac = rk * sku / (Sk - Ss);
+  const V* W = left ? L : Rs;
+  V rk = W[0], pk = W[1], uk = W[2], Ek = left ? El : Er, Sk = left ? SL : SR;
+  V sku = Sk - uk;
+  V fac = rk * sku / (Sk - Ss);
   // F* = F_k + S_k (U*_k - U_k)
   f[0] = rk * uk + Sk * (fac - rk);
   f[1] = rk * uk * uk + pk + Sk * (fac * Ss - rk * uk);
 #pragma unroll
   for (int q = 1; q < D; ++q) f[1 + q] = rk * uk * W[2 + q] + Sk * (fac * W[2 + q] - rk * W[2 + q]);
-  R Es = fac * (Ek / rk + (Ss - uk) * (Ss + pk / (rk * sku)));
+  V Es = fac * (Ek / rk + (Ss - uk) * (Ss + pk / (rk * sku)));
   f[1 + D] = (Ek + pk) * uk + Sk * (Es - Ek);
 }
 
@@ -195,25 +196,25 @@ __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 // so P_{nq} = E [1/3 - f^2/(2+s)] delta_{nq} + 3 F_n F_q / ((2+s) c^2 E): one reciprocal of E, one
 // square root and one reciprocal per state, and F = 0 needs no special case.
 // ---------------------------------------------------------------------------------------------
-template <class R, int D>
-__device__ __forceinline__ void m1_row(R ic2, R E, const R* F, int n, R* P) {
+template <class R, int D, class V = R>
+__device__ __forceinline__ void m1_row(R ic2, V E, const V* F, int n, V* P) {
   if (!(E > R(0))) {
 #pragma unroll
-    for (int q = 0; q < D; ++q) P[q] = q == n ? E * R(1.0 / 3.0) : R(0);
+    for (int q = 0; q < D; ++q) P[q] = q == n ? E * R(1.0 / 3.0) : V(R(0));
     return;
   }
-  R F2 = F[0] * F[0];
+  V F2 = F[0] * F[0];
 #pragma unroll
   for (int q = 1; q < D; ++q) F2 += F[q] * F[q];
-  const R iE = frcp(E);
-  R f2 = F2 * iE * iE * ic2;
-  R scale = R(1);
-  if (f2 > R(1)) { scale = frcp(f2); f2 = R(1); }  // |F| > cE: keep the direction, clamp f to 1
-  const R qd = frcp(R(2) + sqrt(R(4) - R(3) * f2));
-  const R diag = E * (R(1.0 / 3.0) - f2 * qd);
-  const R w = R(3) * qd * iE * ic2 * scale * F[n];
+  const V iE = frcp(E);
+  V f2 = F2 * iE * iE * ic2;
+  V scale = V(R(1));
+  if (f2 > R(1)) { scale = frcp(f2); f2 = V(R(1)); }  // |F| > cE: keep the direction, clamp f to 1
+  const V qd = frcp(R(2) + sqrt(R(4) - R(3) * f2));
+  const V diag = E * (R(1.0 / 3.0) - f2 * qd);
+  const V w = R(3) * qd * iE * ic2 * scale * F[n];
 #pragma unroll
-  for (int q = 0; q < D; ++q) P[q] = w * F[q] + (q == n ? diag : R(0));
+  for (int q = 0; q < D; ++q) P[q] = w * F[q] + (q == n ? diag : V(R(0)));
 }
 
 // Full diagonal and the (0,1) entry of P, for the geometric sources of curvilinear grids.

@@ -71,6 +71,14 @@ template <class R> struct StageArgs {
   double dts;          // coupling step (dt after stage 1, dt/2 after stage 2; reading R10)
   double alpha;        // 0 (stage 1) or 1/2 (stage 2)
   int chunk;           // planes per block along the march axis
+  // Optional outputs (null when unused).  pre_out: the state after the explicit update and RK
+  // combination, before the interaction (state layout); tstar_out: the interaction's converged
+  // temperature per cell; phi_out: per row of upper-x boundary faces and group, the radiation
+  // energy flux through the face times phi_area, the area of one such face (Cartesian).
+  R* pre_out;
+  R* tstar_out;
+  R* phi_out;
+  R phi_area;
   Consts<double> kd;
   Consts<float> kf;
   __device__ __forceinline__ const Consts<double>& k(double) const { return kd; }
@@ -163,11 +171,9 @@ struct Coupler {
     dB = (float)aN * T3 * I * (4.0f + dLdu);  // d/dT (T^4 I) = T^3 I (4 + d ln I / d ln T)
   }
 
-  // residual and derivative at T = Tm + dl; this lane's E_g(T) and dE_g/dT
-  __device__ __forceinline__ void eval(NT dl, NT& r, NT& dr, LT& Eg, LT& dEg) const {
-    LT Tl = (LT)(Tm + dl);
-    LT invT = frcp(Tl);
-    LT Bq, dBq;
+  // this lane's group energy B_g(T) and dB_g/dT (all lanes of the segment take part: the FP64
+  // form shares edge integrals between neighbouring lanes)
+  __device__ __forceinline__ void planck(LT Tl, LT invT, LT& Bq, LT& dBq) const {
     if (sizeof(LT) == 4) {
       float B_, dB_;
       if (has) planck_tab((float)Tl, (float)invT, B_, dB_);
@@ -186,6 +192,14 @@ struct Coupler {
       Bq = aN * T3 * Tl * I;
       dBq = aN * T3 * (LT(4) * I + (LT)(lo.w - hi.w));
     }
+  }
+
+  // residual and derivative at T = Tm + dl; this lane's E_g(T) and dE_g/dT
+  __device__ __forceinline__ void eval(NT dl, NT& r, NT& dr, LT& Eg, LT& dEg) const {
+    LT Tl = (LT)(Tm + dl);
+    LT invT = frcp(Tl);
+    LT Bq, dBq;
+    planck(Tl, invT, Bq, dBq);
     LT kap = K * hpow(Tl, g.kap_T_h) * efac;
     LT tau = cdts * kap;
     LT dtau = tau * (LT(0.5) * (LT)g.kap_T_h) * invT;
@@ -205,7 +219,7 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
                                                 const Consts<NT>& kn,
                                                 const Consts<LT>& kl, bool active,
                                                 int lane, const NT* h, NT& rho, NT* m,
-                                                NT& rhoe, NT& E, NT* F) {
+                                                NT& rhoe, NT& E, NT* F, NT* Tout = nullptr) {
   const int G = g.G;
   unsigned st = 0;
   const NT cv = kn.cv;
@@ -305,6 +319,7 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
     if (need) Eg = e2;
   }
   if (active && !ok) st |= ST_NEWTON;
+  if (Tout) *Tout = cp.Tm + dl;
   // energy update by conservation (R12)
   NT dEsum = seg_sum<GP>(has ? (NT)Eg - Em : NT(0));
   rhoe = ke + (u_m - dEsum);
@@ -878,7 +893,21 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           if (v == 0) E = (NT)u1; else F[v - 1] = (NT)u1;
         }
       }
+      // recording for the adjoint: the pre-interaction state
+      if (A.pre_out != nullptr && cell_in) {
+        if (lane < NG) A.pre_out[lane * ncell + cidx] = ug;
+        if (has) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) A.pre_out[NG * ncell + (v * ncell + cidx) * G + lane] = R(v == 0 ? E : F[v - 1]);
+        }
+      }
+      // objective: energy flux through the upper x boundary face of the row, times its area
+      if (A.phi_out != nullptr && cell_in && has && gx == nx - 1) {
+        const uint32_t row = D == 1 ? 0u : D == 2 ? (uint32_t)k : (uint32_t)k * ny + gy;
+        A.phi_out[row * G + lane] = rfx[(0 * NFX + fxa + 1) * G + lane] * A.phi_area;
+      }
       unsigned stbits = 0;
+      NT Tst = NT(0);
       if (g.couple) {
         // covariant components: physical = m_q / h_q on curvilinear grids (Cartesian: no scaling)
         NT h[3] = {(NT)hq[0], (NT)hq[1], NT(1)};
@@ -886,11 +915,12 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         NT rho = gas[0], rhoe = gas[NG - 1];
         stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.ptab, A.k(NT(0)), A.k(LT(0)), cell_in, lane,
                                             sph ? h : nullptr,
-                                            rho, m, rhoe, E, F);
+                                            rho, m, rhoe, E, F, &Tst);
         gas[0] = rho;
 #pragma unroll
         for (int q = 0; q < D; ++q) gas[1 + q] = m[q];
         gas[NG - 1] = rhoe;
+        if (A.tstar_out != nullptr && cell_in && lane == 0) A.tstar_out[cidx] = R(Tst);
       }
       if (cell_in) {
         NT chk = NT(0);  // a NaN or inf anywhere in the cell's outputs makes this sum non-finite

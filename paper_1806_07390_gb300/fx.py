@@ -29,7 +29,9 @@ EXPORTS = ["fx_grid_create", "fx_bind_workspace", "fx_state_elems", "fx_state_up
            "fx_state_init_equilibrium", "fx_step", "fx_sync", "fx_conserved_totals",
            "fx_state_download", "fx_launches_per_step", "fx_debug_table", "fx_debug_ntab",
            "fx_debug_planck_table", "fx_state_init_equilibrium_noalloc",
-           "fx_kernel_timing_enable", "fx_kernel_timing_read",
+           "fx_kernel_timing_enable", "fx_kernel_timing_read", "fx_objective_enable",
+           "fx_boundary_energy_out", "fx_set_kappa0", "fx_state_set_density",
+           "fx_adjoint_workspace_bytes", "fx_adjoint_forward", "fx_adjoint_backward", "fx_adjoint",
            "fx_last_error", "fx_clear_error", "fx_grid_destroy"]
 
 
@@ -86,13 +88,25 @@ def lib() -> ctypes.CDLL:
         L.fx_state_init_equilibrium_noalloc.restype = ctypes.c_int
         L.fx_kernel_timing_enable.argtypes = [vp, ctypes.c_int]
         L.fx_kernel_timing_read.argtypes = [vp, dp]
+        L.fx_objective_enable.argtypes = [vp, ctypes.c_int]
+        L.fx_boundary_energy_out.argtypes = [vp, dp]
+        L.fx_set_kappa0.argtypes = [vp, ctypes.c_double]
+        L.fx_state_set_density.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
+        L.fx_adjoint_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(sz)]
+        L.fx_adjoint_forward.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, sz, dp]
+        L.fx_adjoint_backward.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, sz,
+                                          ctypes.c_double, vp, vp, dp]
+        L.fx_adjoint.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, sz, vp, vp, dp, dp]
         L.fx_last_error.argtypes = [vp]
         L.fx_last_error.restype = ctypes.c_char_p
         L.fx_clear_error.argtypes = [vp]
         L.fx_grid_destroy.argtypes = [vp]
         for f in ("fx_grid_create", "fx_bind_workspace", "fx_state_upload",
                   "fx_state_init_equilibrium", "fx_step", "fx_sync", "fx_conserved_totals",
-                  "fx_state_download", "fx_kernel_timing_enable", "fx_kernel_timing_read"):
+                  "fx_state_download", "fx_kernel_timing_enable", "fx_kernel_timing_read",
+                  "fx_objective_enable", "fx_boundary_energy_out", "fx_set_kappa0",
+                  "fx_state_set_density", "fx_adjoint_workspace_bytes", "fx_adjoint_forward",
+                  "fx_adjoint_backward", "fx_adjoint"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -224,6 +238,76 @@ class Grid:
         self._check(self.L.fx_kernel_timing_read(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return {"stage_ms": float(out[0]), "stage_launches": int(out[1]),
                 "face_ms": float(out[2]), "face_launches": int(out[3])}
+
+    # -- objective and adjoint
+    def objective(self, on: bool = True) -> None:
+        """Accumulate the boundary outflow J during subsequent steps (resets it to 0)."""
+        self._check(self.L.fx_objective_enable(self.h, int(bool(on))))
+
+    def boundary_energy_out(self) -> float:
+        out = ctypes.c_double()
+        self._check(self.L.fx_boundary_energy_out(self.h, ctypes.byref(out)))
+        return out.value
+
+    def set_kappa0(self, kappa0: float) -> None:
+        self._check(self.L.fx_set_kappa0(self.h, float(kappa0)))
+        self.pb.kappa0 = float(kappa0)
+
+    def set_density(self, rho) -> None:
+        """Replace the density at fixed pressure, velocity and radiation (torch CUDA tensor or
+        host array of the state's precision)."""
+        import torch
+
+        prec = FX_FP64 if self.pb.precision == "fp64" else FX_FP32
+        if isinstance(rho, torch.Tensor):
+            assert rho.is_cuda and rho.is_contiguous() and rho.numel() == self.pb.ncell
+            assert rho.dtype == (torch.float64 if prec == FX_FP64 else torch.float32)
+            self._check(self.L.fx_state_set_density(self.h, ctypes.c_void_p(rho.data_ptr()), prec, 1))
+        else:
+            r = np.ascontiguousarray(rho, dtype=self.np_dtype)
+            assert r.size == self.pb.ncell
+            self._check(self.L.fx_state_set_density(self.h, r.ctypes.data_as(ctypes.c_void_p), prec, 0))
+
+    def adjoint_workspace(self, nsteps: int, k: int):
+        import torch
+
+        nb = ctypes.c_size_t()
+        self._check(self.L.fx_adjoint_workspace_bytes(self.h, int(nsteps), int(k), ctypes.byref(nb)))
+        return torch.empty(max(nb.value, 1), dtype=torch.uint8, device=self.workspace.device)
+
+    def adjoint_forward(self, ws, dt: float, nsteps: int, k: int) -> float:
+        J = ctypes.c_double()
+        self._check(self.L.fx_adjoint_forward(self.h, float(dt), int(nsteps), int(k),
+                                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(J)))
+        return J.value
+
+    def adjoint_backward(self, ws, dt: float, nsteps: int, k: int, seed: float = 1.0):
+        """Returns (dJ/dU^0 as a device tensor in the state layout, dJ/drho(x,0), dJ/dkappa0)."""
+        import torch
+
+        tdt = torch.float64 if self.pb.precision == "fp64" else torch.float32
+        gs = torch.empty(self.nelem, dtype=tdt, device=self.workspace.device)
+        gr = torch.empty(self.pb.ncell, dtype=tdt, device=self.workspace.device)
+        dk = ctypes.c_double()
+        self._check(self.L.fx_adjoint_backward(self.h, float(dt), int(nsteps), int(k),
+                                               ctypes.c_void_p(ws.data_ptr()), ws.numel(), float(seed),
+                                               ctypes.c_void_p(gs.data_ptr()), ctypes.c_void_p(gr.data_ptr()),
+                                               ctypes.byref(dk)))
+        return gs, gr, dk.value
+
+    def adjoint(self, dt: float, nsteps: int, k: int):
+        """Both passes: (J, dJ/dU^0, dJ/drho(x,0), dJ/dkappa0)."""
+        import torch
+
+        ws = self.adjoint_workspace(nsteps, k)
+        tdt = torch.float64 if self.pb.precision == "fp64" else torch.float32
+        gs = torch.empty(self.nelem, dtype=tdt, device=self.workspace.device)
+        gr = torch.empty(self.pb.ncell, dtype=tdt, device=self.workspace.device)
+        J, dk = ctypes.c_double(), ctypes.c_double()
+        self._check(self.L.fx_adjoint(self.h, float(dt), int(nsteps), int(k), ctypes.c_void_p(ws.data_ptr()),
+                                      ws.numel(), ctypes.c_void_p(gs.data_ptr()), ctypes.c_void_p(gr.data_ptr()),
+                                      ctypes.byref(J), ctypes.byref(dk)))
+        return J.value, gs, gr, dk.value
 
     def clear_error(self) -> None:
         self.L.fx_clear_error(self.h)

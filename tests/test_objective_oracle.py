@@ -126,6 +126,27 @@ def test_objective_tangent_on_the_blob_screen():
     assert abs(dJ - fd) <= 1e-6 * abs(dJ)
 
 
+@pytest.mark.parametrize("part", ["rho", "m", "rhoe", "E", "F"])
+def test_objective_tangent_of_each_state_component(part):
+    # the tangent along random perturbations of one block of conserved variables at a time
+    pb, _ = _beam_problem(16, 12, 3)
+    s = W.random_state(pb, seed=5, flux_frac=0.5)
+    N, D, G = pb.ncell, pb.dims, pb.ngroups
+    NG = 2 + D
+    sl = {"rho": slice(0, N), "m": slice(N, (1 + D) * N), "rhoe": slice((1 + D) * N, NG * N),
+          "E": slice(NG * N, NG * N + N * G), "F": slice(NG * N + N * G, None)}[part]
+    t = np.zeros_like(s)
+    rng = np.random.default_rng(1)
+    t[sl] = rng.uniform(-1, 1, t[sl].size) * np.abs(s[sl]).mean()
+    dJ = oracle.run_objective(pb, s, pb.dt, 3, tangent=t)[2]
+    h = 1e-6
+    Jp = oracle.run_objective(pb, s + h * t, pb.dt, 3, signature=True)
+    Jm = oracle.run_objective(pb, s - h * t, pb.dt, 3, signature=True)
+    assert Jp[3] == Jm[3]
+    fd = (Jp[1] - Jm[1]) / (2 * h)
+    assert abs(dJ - fd) <= 1e-7 * abs(fd)
+
+
 def test_branch_signature_is_deterministic_and_sees_a_kink():
     pb, prim = _beam_problem(12, 10, 3)
     s = W.streaming_flux(pb, oracle.init_equilibrium(pb, prim), 0.5)
