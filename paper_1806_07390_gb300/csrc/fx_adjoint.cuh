@@ -212,6 +212,64 @@ __global__ void __launch_bounds__(256) adj_couple_kernel(const __grid_constant__
   block_partial((active && lane == 0) ? (double)lk0 : 0.0, A.kpart);
 }
 
+// Jacobian of the M1 pressure row n at the state Q = (E, F) (derivative parts of P; the value
+// parts are unused).  P is homogeneous of degree one in (E, F), so below the free-streaming
+// limit the derivatives are formed at the normalised state (1, F/E): dP/dF_j = dP'/dF'_j and
+// dP/dE = P' - sum_j F'_j dP'/dF'_j, which keeps FP32 Jacobians finite for the tiny E_g of cold
+// groups (1/E^2 would overflow).  Where |F| > cE the closure clamps f to 1 and P = E n n with
+// n = F/|F|; that branch's Jacobian is written out.
+template <class R, int D>
+__device__ __forceinline__ void m1_jacobian(R ic2, R c, const R* Q, int n, Dn<R, 1 + D>* P) {
+  constexpr int NRV = 1 + D;
+  R smax = R(0);
+#pragma unroll
+  for (int q = 0; q < D; ++q) smax = fmax(smax, fabs(Q[1 + q]));
+  if (!(Q[0] > R(0)) || smax == R(0)) {
+    // E <= 0 (isotropic branch) or F = 0: P = E/3 delta, and P is quadratic in F
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      P[q] = Dn<R, NRV>(R(0));
+      P[q].d[0] = q == n ? R(1.0 / 3.0) : R(0);
+    }
+    return;
+  }
+  R u[D], un2 = R(0);
+#pragma unroll
+  for (int q = 0; q < D; ++q) { u[q] = Q[1 + q] / smax; un2 += u[q] * u[q]; }
+  const R un = sqrt(un2);
+  // f = |F| / (cE) = (smax un / E) / c, compared with 1 without forming |F|^2 / E^2
+  const bool clamped = smax * un > c * Q[0];
+  if (clamped) {
+    const R EoF = Q[0] / (smax * un);
+    R nv[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) nv[q] = u[q] / un;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      P[q] = Dn<R, NRV>(R(0));
+      P[q].d[0] = nv[n] * nv[q];
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+        P[q].d[1 + j] = EoF * ((j == n ? nv[q] : R(0)) + (j == q ? nv[n] : R(0)) - R(2) * nv[n] * nv[q] * nv[j]);
+    }
+    return;
+  }
+  const R iE = R(1) / Q[0];
+  Dn<R, NRV> E1 = Dn<R, NRV>::seed(R(1), 0), F1[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) F1[q] = Dn<R, NRV>::seed(Q[1 + q] * iE, 1 + q);
+  Dn<R, NRV> P1[D];
+  m1_row<R, D, Dn<R, NRV>>(ic2, E1, F1, n, P1);
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    R dE = P1[q].v;
+#pragma unroll
+    for (int j = 0; j < D; ++j) dE -= F1[j].v * P1[q].d[1 + j];
+    P[q] = P1[q];
+    P[q].d[0] = dE;
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Adjoint of the face fluxes of direction DIR: one thread per face.  Recomputes the
 // reconstructed states and fluxes of the face from the stage input, takes the flux adjoints
@@ -347,13 +405,8 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<R>& A, int64_t f) {
     const bool upL = vstar >= R(0);
     // M1 pressure rows of the two states with their Jacobians in (E, F)
     Dn<R, NRV> PL[D], PR[D];
-    {
-      Dn<R, NRV> EL = Dn<R, NRV>::seed(QL[0], 0), ER = Dn<R, NRV>::seed(QR[0], 0), FL[D], FR[D];
-#pragma unroll
-      for (int q = 0; q < D; ++q) { FL[q] = Dn<R, NRV>::seed(QL[1 + q], 1 + q); FR[q] = Dn<R, NRV>::seed(QR[1 + q], 1 + q); }
-      m1_row<R, D, Dn<R, NRV>>(KR.ic2, EL, FL, DIR, PL);
-      m1_row<R, D, Dn<R, NRV>>(KR.ic2, ER, FR, DIR, PR);
-    }
+    m1_jacobian<R, D>(KR.ic2, KR.c, QL, DIR, PL);
+    m1_jacobian<R, D>(KR.ic2, KR.c, QR, DIR, PR);
     // transpose of the face formula (Eqs. 17-19; R8, R9)
     R lQL[NRV], lQR[NRV];
 #pragma unroll

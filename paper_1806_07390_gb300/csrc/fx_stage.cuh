@@ -346,6 +346,305 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
   return st;
 }
 
+// ---------------------------------------------------------------------------------------------
+// The same interaction for the FP32 form with the FP64 Newton (group arithmetic in FP32, the
+// temperature iterate, residual and the energy/momentum bookkeeping in FP64), organised for
+// GB300's FP64 pipe, whose cost is per warp instruction whatever the number of active lanes:
+// the scalar FP64 work of all TC cells of the block runs in one warp (lane c = cell c) instead of
+// redundantly in every lane of every cell.  The cells' GP-lane segments evaluate the FP32 group
+// terms at the temperature the scalar warp proposes and return the two group sums through shared
+// memory; Newton, line search, bisection and the bookkeeping sums are the scalar warp's, in the
+// same order of decisions as couple_cell.  Called by all threads of the block (two barriers per
+// evaluation); the iteration counts are bounded as in couple_cell.
+// ---------------------------------------------------------------------------------------------
+template <int D, int GP, int TC>
+__device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupConst& gc,
+                                                 const PlanckParams& pk, const PlanckTable& ptab,
+                                                 const Consts<double>& kn, const Consts<float>& kl,
+                                                 bool active, int lane, int tcell, const float* h,
+                                                 float& rho, float* m, float& rhoe, float& E,
+                                                 float* F, float* Tout) {
+  using LT = float;
+  using NT = double;
+  static_assert(TC * GP == 256 && TC <= 32, "one scalar lane per cell of a 256-thread block");
+  __shared__ double s_rho[TC], s_m[3][TC], s_rhoe[TC], s_h[2][TC], s_T[TC];
+  __shared__ float s_Esum[TC], s_s1[TC], s_s2[TC], s_Tt[TC], s_lin[TC], s_Es0[TC];
+  __shared__ int s_flag[TC], s_more;
+  __shared__ float s_Eg[TC * GP], s_Em[TC * GP], s_dF[3][TC * GP];
+  enum { F_ACC = 1, F_DONE = 2, F_NEWTON = 4, F_FLOOR = 8, F_BIS = 16 };
+  const int G = g.G;
+  const bool has = lane < G;
+  const int w = tcell * GP + lane;  // this thread's slot in the per-group arrays
+  const bool scalar = threadIdx.x < TC;  // the scalar warp's lanes, one per cell
+  const int c = threadIdx.x;
+
+  // ---- segments: the cell's inputs for the scalar warp (FP32 values, exact in FP64); E^- with
+  // its silent positivity floor.  Every per-lane value stays FP32: FP64 is the scalar warp's.
+  LT Em = has ? E : LT(0);
+  if (has && Em < kl.E_floor) Em = kl.E_floor;
+  const LT Esum = seg_sum<GP>(Em);
+  if (lane == 0) {
+    s_rho[tcell] = (double)rho;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s_m[q][tcell] = q < D ? (double)m[q] : 0.0;
+    s_rhoe[tcell] = (double)rhoe;
+    s_h[0][tcell] = h ? (double)h[0] : 1.0;
+    s_h[1][tcell] = h ? (double)h[1] : 1.0;
+    s_Esum[tcell] = Esum;
+    s_flag[tcell] = active ? 0 : F_DONE;
+  }
+  __syncthreads();
+
+  // ---- scalar warp: floors, T^- = u^-/(rho c_v), the Newton state of its cell
+  NT rcv = 0.0, Tm = 0.0, ke = 0.0, um = 0.0, scale = 0.0, dl = 0.0, r = 0.0, dr = 0.0, dT = 0.0,
+     lam = 1.0, dtt = 0.0;
+  int it = 0, ls = 0, fl = 0;
+  bool need_dir = true, valid = true;
+  if (scalar) {
+    fl = s_flag[c];
+    NT rr = s_rho[c];
+    if (rr < kn.rho_floor) { rr = kn.rho_floor; fl |= F_FLOOR; }
+    const NT ir = 1.0 / rr;
+    for (int q = 0; q < D; ++q) {
+      const NT mh = s_m[q][c] / (q < 2 ? s_h[q][c] : 1.0);
+      ke += 0.5 * mh * mh * ir;
+    }
+    um = s_rhoe[c] - ke;
+    if (um < kn.u_floor) { um = kn.u_floor; fl |= F_FLOOR; }
+    rcv = rr * kn.cv;
+    Tm = um / rcv;
+    scale = um + (NT)s_Esum[c];
+    s_Es0[c] = s_Esum[c];
+    s_rho[c] = rr;
+    s_Tt[c] = (float)Tm;
+  }
+  if (scalar) {
+    // the opacity factors K = kappa0 rho^a and S = sigma0 rho of the (floored) density
+    s_Esum[c] = (float)(kn.kappa0 * hpow(s_rho[c], g.kap_rho_h));
+    s_s1[c] = (float)(kn.sigma0 * s_rho[c]);
+  }
+  __syncthreads();
+  // the segment's group state: accepted (Eg, dEg) and the latest evaluation (Et, dEt)
+  Coupler<GP, LT, NT> cp{g, pk, ptab, lane, has, (G == GP) && (lane == G - 1), 0.0, 0.0,
+                         s_Esum[tcell], s_s1[tcell],
+                         kl.cdts, Em, kl.aN, gc.efac_of(has ? lane : 0, LT(0)),
+                         gc.edge_of(lane <= G ? lane : G, LT(0)), gc.edge_of(G, LT(0))};
+  LT Eg = Em, dEg = LT(0), Et = Em, dEt = LT(0);
+  // one evaluation at the proposed temperature: E_g(T) (Eq. 25) and dE_g/dT; the two group sums
+  // go to the scalar warp
+  auto seg_eval = [&]() {
+    const LT Tl = s_Tt[tcell];
+    const LT invT = frcp(Tl);
+    LT Bq, dBq;
+    cp.planck(Tl, invT, Bq, dBq);
+    const LT kap = cp.K * hpow(Tl, g.kap_T_h) * cp.efac;
+    const LT tau = cp.cdts * kap;
+    const LT dtau = tau * (LT(0.5) * (LT)g.kap_T_h) * invT;
+    const LT inv = frcp(LT(1) + tau);
+    Et = (Em + tau * Bq) * inv;
+    dEt = (tau * dBq + dtau * (Bq - Et)) * inv;
+    const LT a = seg_sum<GP>(has ? Et - Em : LT(0));
+    const LT b = seg_sum<GP>(has ? dEt : LT(0));
+    if (lane == 0) { s_s1[tcell] = a; s_s2[tcell] = b; }
+  };
+  // the scalar warp's Newton decision for its cell (as in couple_cell): from the accepted point
+  // either stop or propose the trial dl + lam dT
+  auto newton_dir = [&]() {
+    if (it >= g.newton_maxit) { fl |= F_DONE | F_NEWTON; return; }
+    if (fabs(r) <= kn.atol * scale) { fl |= F_DONE; return; }
+    dT = -r / dr;
+    ++it;
+    if (fabs(dT) <= kn.rtol * (Tm + dl)) {
+      // converged: the group energies at T + dT follow from the linearisation
+      dl += dT;
+      s_lin[c] = (float)dT;
+      fl |= F_DONE;
+      return;
+    }
+    lam = 1.0;
+    ls = 0;
+    need_dir = false;
+  };
+  auto propose = [&]() {
+    dtt = dl + lam * dT;
+    valid = (Tm + dtt) > 0.0;
+    s_Tt[c] = (float)(Tm + (valid ? dtt : dl));
+  };
+
+  // ---- Newton with backtracking (Eqs. 26-27; reading R11)
+  seg_eval();
+  __syncthreads();
+  if (scalar) {
+    s_lin[c] = 0.0f;
+    if (!(fl & F_DONE)) {
+      r = rcv * dl + (NT)s_s1[c];
+      dr = rcv + (NT)s_s2[c];
+      fl |= F_ACC;
+      newton_dir();
+      if (!(fl & F_DONE)) propose();
+    } else {
+      fl |= F_ACC;
+    }
+    s_flag[c] = fl;
+    const bool more = __any_sync(0xffffffffu >> (32 - TC), !(fl & F_DONE));
+    if (c == 0) s_more = more;
+  }
+  __syncthreads();
+  const int guard = g.newton_maxit * 41 + 2;
+  for (int kk = 0; kk < guard; ++kk) {
+    {
+      const int f = s_flag[tcell];
+      if (f & F_ACC) { Eg = Et; dEg = dEt; }
+      const float lin = s_lin[tcell];
+      if (lin != 0.0f) Eg += dEg * lin;
+    }
+    const bool more = s_more;
+    __syncthreads();  // every thread has read the flags before the scalar warp rewrites them
+    if (!more) break;
+    seg_eval();
+    __syncthreads();
+    if (scalar) {
+      fl &= ~F_ACC;
+      s_lin[c] = 0.0f;
+      if (!(fl & F_DONE)) {
+        const NT rt = rcv * dtt + (NT)s_s1[c];
+        const NT drt = rcv + (NT)s_s2[c];
+        if (valid && fabs(rt) < fabs(r)) {
+          dl = dtt; r = rt; dr = drt; fl |= F_ACC; need_dir = true;
+        } else {
+          lam *= 0.5;
+          if (++ls >= 40) fl |= F_DONE | F_NEWTON;
+        }
+        if (!(fl & F_DONE) && need_dir) newton_dir();
+        if (!(fl & F_DONE)) propose();
+      }
+      s_flag[c] = fl;
+      const bool m2 = __any_sync(0xffffffffu >> (32 - TC), !(fl & F_DONE));
+      if (c == 0) s_more = m2;
+    }
+    __syncthreads();
+  }
+  if (scalar && !(s_flag[c] & F_DONE)) fl |= F_NEWTON;  // guard exhausted
+
+  // ---- bisection fallback on a bracket around [T^-, T_rad] (reading R11), in T - T^-
+  if (scalar) {
+    s_flag[c] = (fl & F_NEWTON) ? (fl | F_BIS) : (fl & ~F_BIS);
+    const bool any_bis = __any_sync(0xffffffffu >> (32 - TC), (fl & F_NEWTON) != 0);
+    if (c == 0) s_more = any_bis;
+  }
+  __syncthreads();
+  if (s_more) {
+    NT lo = 0.0, hi = 0.0, Te = 0.0;
+    int phase = 3, cnt = 0;
+    bool brk = false;
+    if (scalar && (fl & F_NEWTON)) {
+      const NT Tr = sqrt(sqrt((NT)s_Es0[c] / (kn.aN * 6.4939394022668291491)));  // (sum E / a_R)^(1/4)
+      const NT T = Tm + dl;
+      lo = fmin(fmin(T, Tr), Tm) - Tm;
+      hi = fmax(fmax(T, Tr), Tm) - Tm;
+      phase = 0;
+      Te = lo;
+      s_Tt[c] = (float)(Tm + Te);
+    }
+    __syncthreads();
+    for (int kk = 0; kk < 400 + g.bisect_maxit + 4; ++kk) {
+      seg_eval();
+      __syncthreads();
+      if (scalar) {
+        if (phase < 3) {
+          const NT rr = rcv * Te + (NT)s_s1[c];
+          if (phase == 0) {
+            if (rr > 0.0 && cnt < 200) { lo = 0.5 * (lo + Tm) - Tm; ++cnt; }  // T_lo /= 2
+            else { phase = 1; cnt = 0; brk = rr <= 0.0; }
+          } else if (phase == 1) {
+            if (rr < 0.0 && cnt < 200) { hi = 2.0 * (hi + Tm) - Tm; ++cnt; }  // T_hi *= 2
+            else { brk = brk && rr >= 0.0; cnt = 0; phase = brk ? (g.bisect_maxit > 0 ? 2 : 3) : 3; }
+          } else {
+            if (rr > 0.0) hi = Te; else lo = Te;
+            ++cnt;
+            if (hi - lo <= kn.rtol * (hi + Tm)) { fl &= ~F_NEWTON; phase = 3; }
+            else if (cnt >= g.bisect_maxit) phase = 3;
+          }
+          Te = phase == 0 ? lo : (phase == 1 ? hi : (phase == 2 ? 0.5 * (lo + hi) : Te));
+          s_Tt[c] = (float)(Tm + Te);
+        }
+        const bool m3 = __any_sync(0xffffffffu >> (32 - TC), phase < 3);
+        if (c == 0) s_more = m3;
+      }
+      __syncthreads();
+      const bool more = s_more;
+      __syncthreads();
+      if (!more) break;
+    }
+    // the group energies at the bracket's midpoint
+    if (scalar && (s_flag[c] & F_BIS)) {
+      if (brk) dl = 0.5 * (lo + hi);
+      s_Tt[c] = (float)(Tm + dl);
+    }
+    __syncthreads();
+    seg_eval();
+    if (s_flag[tcell] & F_BIS) Eg = Et;
+    __syncthreads();
+  }
+
+  // ---- bookkeeping in the scalar warp (FP64): energy by conservation (R12), then the flux
+  // absorption update at the converged temperature (Eq. 28) and its feedback (Eqs. 31-32)
+  if (scalar) {
+    s_T[c] = Tm + dl;
+    s_Tt[c] = (float)(Tm + dl);
+  }
+  __syncthreads();
+  const LT Tst = s_Tt[tcell];
+  const LT kap = cp.K * hpow(Tst, g.kap_T_h) * cp.efac;
+  const LT fac = frcp(LT(1) + cp.cdts * (kap + cp.Sg));
+  s_Eg[w] = has ? Eg : 0.0f;
+  s_Em[w] = has ? Em : 0.0f;
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    const LT Fq = has ? F[q] : LT(0);
+    const LT Fn = Fq * fac;
+    s_dF[q][w] = Fn - Fq;
+    if (has) F[q] = Fn;
+  }
+  if (has) E = Eg;
+  __syncthreads();
+  if (scalar) {
+    NT dEsum = 0.0, SdF[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < G; ++j) {
+      dEsum += (NT)s_Eg[c * GP + j] - (NT)s_Em[c * GP + j];
+      for (int q = 0; q < D; ++q) SdF[q] += (NT)s_dF[q][c * GP + j];
+    }
+    const NT rr = s_rho[c], ir = 1.0 / rr;
+    NT re = ke + (um - dEsum);
+    NT work = 0.0;
+    for (int q = 0; q < D; ++q) {
+      const NT mq = s_m[q][c];
+      const NT hq = q < 2 ? s_h[q][c] : 1.0;
+      work += mq / (hq * hq) * ir * SdF[q];
+      s_m[q][c] = mq - SdF[q] * kn.ic2;
+    }
+    s_rhoe[c] = re - work * kn.ic2;
+    if (fl & F_NEWTON) s_flag[c] |= F_NEWTON;
+    if (fl & F_FLOOR) s_flag[c] |= F_FLOOR;
+    s_Tt[c] = (float)s_rho[c];
+    s_s1[c] = (float)s_rhoe[c];
+#pragma unroll
+    for (int q = 0; q < D; ++q) s_dF[q][c * GP] = (float)s_m[q][c];
+  }
+  __syncthreads();
+  rho = s_Tt[tcell];
+#pragma unroll
+  for (int q = 0; q < D; ++q) m[q] = s_dF[q][tcell * GP];
+  rhoe = s_s1[tcell];
+  if (Tout) *Tout = Tst;
+  const int f = s_flag[tcell];
+  unsigned st = 0;
+  if (active && (f & F_NEWTON)) st |= ST_NEWTON;
+  if (active && (f & F_FLOOR)) st |= ST_FLOOR;
+  __syncthreads();  // the shared arrays are reused by the next plane's call
+  return st;
+}
+
 // Shared-memory layout of stage_kernel (offsets in elements of R; used by the kernel and by the
 // host to size the launch).
 template <int D, int TX, int TY>
@@ -876,10 +1175,14 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       // gas: lane v < NG updates variable v, then the segment shares the cell's gas state
       R ug = g0 + dt * (gsrc - gnet);
       if (stage2) ug = KR.alpha * bg0 + KR.beta * ug;
-      NT gas[NG];
+      // per-lane carrier type of the interaction's inputs and outputs: NT, except in the FP32 form
+      // with the FP64 Newton, whose FP64 work is confined to one warp per block (couple_block)
+      constexpr bool coop = std::is_same<LT, float>::value && std::is_same<NT, double>::value;
+      using CT = typename std::conditional<coop, R, NT>::type;
+      CT gas[NG];
 #pragma unroll
-      for (int v = 0; v < NG; ++v) gas[v] = (NT)__shfl_sync(0xffffffffu, ug, v, GP);
-      NT E = NT(0), F[3] = {NT(0), NT(0), NT(0)};
+      for (int v = 0; v < NG; ++v) gas[v] = (CT)__shfl_sync(0xffffffffu, ug, v, GP);
+      CT E = CT(0), F[3] = {CT(0), CT(0), CT(0)};
       if (has && cell_in) {
 #pragma unroll
         for (int v = 0; v < NRV; ++v) {
@@ -890,7 +1193,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           const R cov = (sph && v >= 1) ? Q0[v] * hq[v - 1] : Q0[v];  // covariant F
           R u1 = cov + dt * (rsrc[v] - net);
           if (stage2) u1 = KR.alpha * b0[v] + KR.beta * u1;
-          if (v == 0) E = (NT)u1; else F[v - 1] = (NT)u1;
+          if (v == 0) E = (CT)u1; else F[v - 1] = (CT)u1;
         }
       }
       // recording for the adjoint: the pre-interaction state
@@ -907,15 +1210,20 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         A.phi_out[row * G + lane] = rfx[(0 * NFX + fxa + 1) * G + lane] * A.phi_area;
       }
       unsigned stbits = 0;
-      NT Tst = NT(0);
+      CT Tst = CT(0);
       if (g.couple) {
         // covariant components: physical = m_q / h_q on curvilinear grids (Cartesian: no scaling)
-        NT h[3] = {(NT)hq[0], (NT)hq[1], NT(1)};
-        NT m[3] = {gas[1], D > 1 ? gas[2] : NT(0), D > 2 ? gas[3] : NT(0)};
-        NT rho = gas[0], rhoe = gas[NG - 1];
-        stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.ptab, A.k(NT(0)), A.k(LT(0)), cell_in, lane,
-                                            sph ? h : nullptr,
-                                            rho, m, rhoe, E, F, &Tst);
+        CT h[3] = {(CT)hq[0], (CT)hq[1], CT(1)};
+        CT m[3] = {gas[1], D > 1 ? gas[2] : CT(0), D > 2 ? gas[3] : CT(0)};
+        CT rho = gas[0], rhoe = gas[NG - 1];
+        if constexpr (coop) {
+          stbits = couple_block<D, GP, TX * TY>(g, *sgc, A.pk, A.ptab, A.kd, A.kf, cell_in, lane, tcell,
+                                                sph ? h : nullptr, rho, m, rhoe, E, F, &Tst);
+        } else {
+          stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.ptab, A.k(NT(0)), A.k(LT(0)), cell_in, lane,
+                                              sph ? h : nullptr,
+                                              rho, m, rhoe, E, F, &Tst);
+        }
         gas[0] = rho;
 #pragma unroll
         for (int q = 0; q < D; ++q) gas[1 + q] = m[q];
@@ -923,9 +1231,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         if (A.tstar_out != nullptr && cell_in && lane == 0) A.tstar_out[cidx] = R(Tst);
       }
       if (cell_in) {
-        NT chk = NT(0);  // a NaN or inf anywhere in the cell's outputs makes this sum non-finite
+        CT chk = CT(0);  // a NaN or inf anywhere in the cell's outputs makes this sum non-finite
         if (lane < NG) {
-          NT val = gas[0];
+          CT val = gas[0];
 #pragma unroll
           for (int v = 1; v < NG; ++v) if (lane == v) val = gas[v];
           A.out[lane * ncell + cidx] = R(val);
@@ -934,9 +1242,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         if (has) {
 #pragma unroll
           for (int v = 0; v < NRV; ++v) {
-            NT val = v == 0 ? E : F[v - 1];
+            CT val = v == 0 ? E : F[v - 1];
             A.out[NG * ncell + (v * ncell + cidx) * G + lane] = R(val);
-            chk += val * NT(0);
+            chk += val * CT(0);
           }
         }
         if (!isfinite(chk)) stbits |= ST_NONFINITE;
