@@ -99,6 +99,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float) -> float:
+    """Maximum of x over the ranks of the default process group (x itself without one): the
+    timed region of a multi-GPU run ends when its slowest rank ends."""
+    import torch
+    import torch.distributed as tdist
+
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return x
+    dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units all ranks processed (each rank runs its own replica) per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def time_form(pb, prim, steps, warmup, dist):
     """Device-timed K steps of one precision form with inputs resident in HBM."""
     import torch
@@ -128,9 +147,7 @@ def time_form(pb, prim, steps, warmup, dist):
     g.kernel_timing(False)
     st = g.status()
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms)
     launches = g.launches_per_step() * steps
     return g, ms, st, launches, kt
 
@@ -368,7 +385,7 @@ def main():
     clocks = clk.summary()
 
     sech = msh / 1e3
-    value = world * zg * 2 * args.steps / sech
+    value = whole_job_rate(zg * 2 * args.steps, world, sech)
     nv = pbh.nvar
 
     def roofline(kind, kt):
@@ -410,7 +427,7 @@ def main():
             "clocks": clocks, "status": int(sth), "forms": {}}
     for name, (msf, stf, lf, ktf) in results.items():
         secf = msf / 1e3
-        line["forms"][name] = {"value": world * zg * 2 * args.steps / secf, "unit": UNIT,
+        line["forms"][name] = {"value": whole_job_rate(zg * 2 * args.steps, world, secf), "unit": UNIT,
                                "ms_per_step": msf / args.steps, "note": FORM_NOTE[name],
                                "roofline": roofline(name, ktf), "status": int(stf),
                                "speedup_of_headline": msf / msh}

@@ -367,7 +367,7 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
   using LT = float;
   using NT = double;
   static_assert(TC * GP == 256 && TC <= 32, "one scalar lane per cell of a 256-thread block");
-  __shared__ double s_rho[TC], s_m[3][TC], s_rhoe[TC], s_h[2][TC], s_T[TC];
+  __shared__ double s_rho[TC], s_m[3][TC], s_rhoe[TC], s_h[2][TC];
   __shared__ float s_Esum[TC], s_s1[TC], s_s2[TC], s_Tt[TC], s_lin[TC], s_Es0[TC];
   __shared__ int s_flag[TC], s_more;
   __shared__ float s_Eg[TC * GP], s_Em[TC * GP], s_dF[3][TC * GP];
@@ -451,13 +451,18 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
   // either stop or propose the trial dl + lam dT
   auto newton_dir = [&]() {
     if (it >= g.newton_maxit) { fl |= F_DONE | F_NEWTON; return; }
-    if (fabs(r) <= kn.atol * scale) { fl |= F_DONE; return; }
-    dT = -r / dr;
+    if (fabs(r) <= kn.atol * scale) { fl |= F_DONE; s_Tt[c] = (float)(Tm + dl); return; }
+    // 1/dr: FP32 seed refined by one Newton-Raphson step y <- y + y (1 - dr y) (relative error
+    // ~1e-14, far below the step tolerance), shorter in latency than an FP64 division
+    NT y = (NT)(1.0f / (float)dr);
+    y = fma(y, fma(-dr, y, 1.0), y);
+    dT = -r * y;
     ++it;
     if (fabs(dT) <= kn.rtol * (Tm + dl)) {
       // converged: the group energies at T + dT follow from the linearisation
       dl += dT;
       s_lin[c] = (float)dT;
+      s_Tt[c] = (float)(Tm + dl);
       fl |= F_DONE;
       return;
     }
@@ -498,8 +503,9 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
       const float lin = s_lin[tcell];
       if (lin != 0.0f) Eg += dEg * lin;
     }
+    // (the scalar warp rewrites the flags and s_more only after the barrier that follows the
+    // next evaluation, which every thread reaches after reading them)
     const bool more = s_more;
-    __syncthreads();  // every thread has read the flags before the scalar warp rewrites them
     if (!more) break;
     seg_eval();
     __syncthreads();
@@ -524,6 +530,7 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
     }
     __syncthreads();
   }
+  __syncthreads();  // all threads have read the last flags and s_more before they are rewritten
   if (scalar && !(s_flag[c] & F_DONE)) fl |= F_NEWTON;  // guard exhausted
 
   // ---- bisection fallback on a bracket around [T^-, T_rad] (reading R11), in T - T^-
@@ -573,7 +580,6 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
       }
       __syncthreads();
       const bool more = s_more;
-      __syncthreads();
       if (!more) break;
     }
     // the group energies at the bracket's midpoint
@@ -589,11 +595,7 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
 
   // ---- bookkeeping in the scalar warp (FP64): energy by conservation (R12), then the flux
   // absorption update at the converged temperature (Eq. 28) and its feedback (Eqs. 31-32)
-  if (scalar) {
-    s_T[c] = Tm + dl;
-    s_Tt[c] = (float)(Tm + dl);
-  }
-  __syncthreads();
+  // (s_Tt holds T* = T^- + dl of every cell: written when Newton stopped, or by the bisection)
   const LT Tst = s_Tt[tcell];
   const LT kap = cp.K * hpow(Tst, g.kap_T_h) * cp.efac;
   const LT fac = frcp(LT(1) + cp.cdts * (kap + cp.Sg));
@@ -609,11 +611,22 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
   if (has) E = Eg;
   __syncthreads();
   if (scalar) {
-    NT dEsum = 0.0, SdF[3] = {0.0, 0.0, 0.0};
-    for (int j = 0; j < G; ++j) {
-      dEsum += (NT)s_Eg[c * GP + j] - (NT)s_Em[c * GP + j];
-      for (int q = 0; q < D; ++q) SdF[q] += (NT)s_dF[q][c * GP + j];
+    // FP64 group sums, four independent partial sums each (the slots beyond G hold zeros)
+    NT pe[4] = {0.0, 0.0, 0.0, 0.0}, pf[3][4] = {};
+    for (int j = 0; j < G; j += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jj = c * GP + j + u;
+        const bool in = j + u < GP;
+        pe[u] += in ? (NT)s_Eg[jj] - (NT)s_Em[jj] : 0.0;
+#pragma unroll
+        for (int q = 0; q < D; ++q) pf[q][u] += in ? (NT)s_dF[q][jj] : 0.0;
+      }
     }
+    const NT dEsum = (pe[0] + pe[1]) + (pe[2] + pe[3]);
+    NT SdF[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < D; ++q) SdF[q] = (pf[q][0] + pf[q][1]) + (pf[q][2] + pf[q][3]);
     const NT rr = s_rho[c], ir = 1.0 / rr;
     NT re = ke + (um - dEsum);
     NT work = 0.0;
@@ -641,7 +654,8 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
   unsigned st = 0;
   if (active && (f & F_NEWTON)) st |= ST_NEWTON;
   if (active && (f & F_FLOOR)) st |= ST_FLOOR;
-  __syncthreads();  // the shared arrays are reused by the next plane's call
+  // (the next call writes the shared arrays only after the stage kernel's next plane has passed
+  // its own barriers)
   return st;
 }
 
