@@ -132,6 +132,7 @@ struct fx_grid {
   size_t nev = 0;
   // objective (boundary radiation energy outflow, reading R19): per-row face fluxes of one stage
   // [rows][G] and FP64 accumulators obj[0] = J, obj[1] = dJ/dkappa0 (adjoint)
+  int nsm = 0;  // multiprocessors of the bound device
   bool objective = false;
   size_t off_phi = 0, off_obj = 0;
   int64_t phi_rows = 0;
@@ -577,6 +578,7 @@ StageArgs<R> stage_args(fx_grid* h) {
   a.status = reinterpret_cast<unsigned*>(h->ws + h->off_status);
   a.chunk = h->chunk;
   a.phi_area = (R)h->phi_area;
+  a.nsm = h->nsm;
   return a;
 }
 
@@ -1096,6 +1098,12 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
   h->ws = static_cast<unsigned char*>(dev_ptr);
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e;
+  {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "device query");
+  }
   if (!h->h_status) {
     e = cudaMallocHost(&h->h_status, sizeof(unsigned));
     if (e != cudaSuccess) return cuda_fail(h, e, "pinned status word");

@@ -79,6 +79,7 @@ template <class R> struct StageArgs {
   R* tstar_out;
   R* phi_out;
   R phi_area;
+  int nsm;             // multiprocessors of the device (spreads couple_block's scalar warps)
   Consts<double> kd;
   Consts<float> kf;
   __device__ __forceinline__ const Consts<double>& k(double) const { return kd; }
@@ -361,7 +362,7 @@ template <int D, int GP, int TC>
 __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupConst& gc,
                                                  const PlanckParams& pk, const PlanckTable& ptab,
                                                  const Consts<double>& kn, const Consts<float>& kl,
-                                                 bool active, int lane, int tcell, const float* h,
+                                                 int nsm, bool active, int lane, int tcell, const float* h,
                                                  float& rho, float* m, float& rhoe, float& E,
                                                  float* F, float* Tout) {
   using LT = float;
@@ -370,13 +371,17 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
   __shared__ double s_rho[TC], s_m[3][TC], s_rhoe[TC], s_h[2][TC];
   __shared__ float s_Esum[TC], s_s1[TC], s_s2[TC], s_Tt[TC], s_lin[TC], s_Es0[TC];
   __shared__ int s_flag[TC], s_more;
-  __shared__ float s_Eg[TC * GP], s_Em[TC * GP], s_dF[3][TC * GP];
+  __shared__ double s_sum[4][TC];  // FP64 group sums of dE and dF_q per cell
   enum { F_ACC = 1, F_DONE = 2, F_NEWTON = 4, F_FLOOR = 8, F_BIS = 16 };
   const int G = g.G;
   const bool has = lane < G;
-  const int w = tcell * GP + lane;  // this thread's slot in the per-group arrays
-  const bool scalar = threadIdx.x < TC;  // the scalar warp's lanes, one per cell
-  const int c = threadIdx.x;
+  // The scalar warp: blocks resident on one multiprocessor at the same time (linear indices that
+  // differ by multiples of the multiprocessor count, in the first wave) take different warps, so
+  // that their FP64 work lands in different sub-partitions of the multiprocessor.
+  const unsigned blin = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const int sw = (int)((blin / (unsigned)(nsm > 0 ? nsm : 1)) & 3u);
+  const int c = threadIdx.x & 31;
+  const bool scalar = (int)(threadIdx.x >> 5) == sw && c < TC;  // one lane per cell
 
   // ---- segments: the cell's inputs for the scalar warp (FP32 values, exact in FP64); E^- with
   // its silent positivity floor.  Every per-lane value stays FP32: FP64 is the scalar warp's.
@@ -406,13 +411,13 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
     if (rr < kn.rho_floor) { rr = kn.rho_floor; fl |= F_FLOOR; }
     const NT ir = 1.0 / rr;
     for (int q = 0; q < D; ++q) {
-      const NT mh = s_m[q][c] / (q < 2 ? s_h[q][c] : 1.0);
+      const NT mh = h ? s_m[q][c] / (q < 2 ? s_h[q][c] : 1.0) : s_m[q][c];
       ke += 0.5 * mh * mh * ir;
     }
     um = s_rhoe[c] - ke;
     if (um < kn.u_floor) { um = kn.u_floor; fl |= F_FLOOR; }
     rcv = rr * kn.cv;
-    Tm = um / rcv;
+    Tm = um * ir * kn.gm1;  // u / (rho c_v), c_v = 1/(gamma - 1)
     scale = um + (NT)s_Esum[c];
     s_Es0[c] = s_Esum[c];
     s_rho[c] = rr;
@@ -599,41 +604,34 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
   const LT Tst = s_Tt[tcell];
   const LT kap = cp.K * hpow(Tst, g.kap_T_h) * cp.efac;
   const LT fac = frcp(LT(1) + cp.cdts * (kap + cp.Sg));
-  s_Eg[w] = has ? Eg : 0.0f;
-  s_Em[w] = has ? Em : 0.0f;
+  // FP64 group sums of the energy change and of the flux changes, in the cells' segments (the
+  // FP64 pipe cost is per warp instruction: spread over all warps, not serialised in one)
+  {
+    const NT sE = seg_sum<GP>(has ? (NT)Eg - (NT)Em : 0.0);
+    if (lane == 0) s_sum[0][tcell] = sE;
+  }
 #pragma unroll
   for (int q = 0; q < D; ++q) {
     const LT Fq = has ? F[q] : LT(0);
     const LT Fn = Fq * fac;
-    s_dF[q][w] = Fn - Fq;
+    const NT sF = seg_sum<GP>((NT)(Fn - Fq));
+    if (lane == 0) s_sum[1 + q][tcell] = sF;
     if (has) F[q] = Fn;
   }
   if (has) E = Eg;
   __syncthreads();
   if (scalar) {
-    // FP64 group sums, four independent partial sums each (the slots beyond G hold zeros)
-    NT pe[4] = {0.0, 0.0, 0.0, 0.0}, pf[3][4] = {};
-    for (int j = 0; j < G; j += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int jj = c * GP + j + u;
-        const bool in = j + u < GP;
-        pe[u] += in ? (NT)s_Eg[jj] - (NT)s_Em[jj] : 0.0;
-#pragma unroll
-        for (int q = 0; q < D; ++q) pf[q][u] += in ? (NT)s_dF[q][jj] : 0.0;
-      }
-    }
-    const NT dEsum = (pe[0] + pe[1]) + (pe[2] + pe[3]);
+    const NT dEsum = s_sum[0][c];
     NT SdF[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-    for (int q = 0; q < D; ++q) SdF[q] = (pf[q][0] + pf[q][1]) + (pf[q][2] + pf[q][3]);
+    for (int q = 0; q < D; ++q) SdF[q] = s_sum[1 + q][c];
     const NT rr = s_rho[c], ir = 1.0 / rr;
     NT re = ke + (um - dEsum);
     NT work = 0.0;
     for (int q = 0; q < D; ++q) {
       const NT mq = s_m[q][c];
       const NT hq = q < 2 ? s_h[q][c] : 1.0;
-      work += mq / (hq * hq) * ir * SdF[q];
+      work += (h ? mq / (hq * hq) : mq) * ir * SdF[q];
       s_m[q][c] = mq - SdF[q] * kn.ic2;
     }
     s_rhoe[c] = re - work * kn.ic2;
@@ -642,12 +640,12 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
     s_Tt[c] = (float)s_rho[c];
     s_s1[c] = (float)s_rhoe[c];
 #pragma unroll
-    for (int q = 0; q < D; ++q) s_dF[q][c * GP] = (float)s_m[q][c];
+    for (int q = 0; q < D; ++q) s_sum[1 + q][c] = s_m[q][c];
   }
   __syncthreads();
   rho = s_Tt[tcell];
 #pragma unroll
-  for (int q = 0; q < D; ++q) m[q] = s_dF[q][tcell * GP];
+  for (int q = 0; q < D; ++q) m[q] = (float)s_sum[1 + q][tcell];
   rhoe = s_s1[tcell];
   if (Tout) *Tout = Tst;
   const int f = s_flag[tcell];
@@ -1231,7 +1229,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         CT m[3] = {gas[1], D > 1 ? gas[2] : CT(0), D > 2 ? gas[3] : CT(0)};
         CT rho = gas[0], rhoe = gas[NG - 1];
         if constexpr (coop) {
-          stbits = couple_block<D, GP, TX * TY>(g, *sgc, A.pk, A.ptab, A.kd, A.kf, cell_in, lane, tcell,
+          stbits = couple_block<D, GP, TX * TY>(g, *sgc, A.pk, A.ptab, A.kd, A.kf, A.nsm, cell_in, lane, tcell,
                                                 sph ? h : nullptr, rho, m, rhoe, E, F, &Tst);
         } else {
           stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.ptab, A.k(NT(0)), A.k(LT(0)), cell_in, lane,
