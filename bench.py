@@ -1,9 +1,12 @@
 """Benchmark of the multigroup M1 radiation-hydrodynamics stage update on GB300.
 
 Metric: zone-group updates per second per RK stage (each RK stage updates every zone-group of
-the grid once), for the FP32 form (headline `value`) and the plain FP64 path (`fp64` object), on
-the 2-d periodic Kelvin-Helmholtz workload, 1024 x 1024 cells x 16 groups (synthetic seeded
-input; inputs are larger than L2, so no flush is needed between timed steps).
+the grid once).  Headline `value`: the FP32 form with the FP64 Newton (FP32 state, reconstruction
+and fluxes; FP64 temperature iterate, residual and energy/momentum bookkeeping); the `forms`
+object reports the all-FP32 variant and the plain FP64 path.  Workload: 2-d periodic
+Kelvin-Helmholtz, 1024 x 1024 cells x 16 groups (synthetic seeded input; inputs are larger than
+L2, so no flush is needed between timed steps).  The `adjoint` object times the differentiation
+form (forward + hand-written adjoint) on the 512 x 512 x 8 blob-screen workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 
@@ -186,7 +189,7 @@ def time_e2e(g, pb, steps, warmup):
 # Workloads: generator, default headline precision form, description, and the oracle sample used
 # for the CPU baseline (window start, interior size, halo) or None for the whole grid.
 WORKLOADS = {
-    "kh2d": (W.kh_2d, "fp32", "2-d periodic Kelvin-Helmholtz, 1024x1024 cells x 16 groups",
+    "kh2d": (W.kh_2d, "fp32n64", "2-d periodic Kelvin-Helmholtz, 1024x1024 cells x 16 groups",
              ((384, 384), (248, 248), 4)),
     "lognormal3d": (W.lognormal_3d, "fp32n64",
                     "3-d periodic lognormal density, 256^3 cells x 12 groups",
