@@ -32,9 +32,10 @@ from paper_1806_07390_gb300 import workloads as W  # noqa: E402
 
 METRIC = "zone-group updates/s per RK stage"
 UNIT = "zone-group-stages/s"
-# DRAM bytes per stage launch from the committed ncu captures (profiles/); None until captured
-# for the current kernel.
-TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32": None, "fp32n64": None, "fp64": None}}
+# DRAM bytes per radiation/update kernel launch (mean of the two RK stages) from the committed
+# ncu capture profiles/traffic_stage_kernel_kh2d_1024x1024x16.txt; None where not captured for
+# the current kernels.
+TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": 615.7e6, "fp32": 594.3e6, "fp64": 1353.5e6}}
 
 
 def load_peaks():
