@@ -478,19 +478,23 @@ __global__ void k_totals_final(const double* part, int nblocks, double* out) {
   out[q] = a.s + a.c;
 }
 
-// acc[0] += w * sum(x[0..n)), deterministic (one block, Neumaier per thread, fixed tree).
+// acc[0] += w * sum(x[0..n)) in FP64, deterministic: one block of 1024 threads, strided partial
+// sums, then a fixed shuffle and shared-memory tree.
 template <class T>
-__global__ void __launch_bounds__(256) k_sum_into(const T* x, int64_t n, double w, double* acc) {
-  KS a = {0.0, 0.0};
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) ks_add(a, (double)x[i]);
-  __shared__ KS sh[256];
-  sh[threadIdx.x] = a;
+__global__ void __launch_bounds__(1024) k_sum_into(const T* x, int64_t n, double w, double* acc) {
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += (double)x[i];
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) ks_merge(sh[threadIdx.x], sh[threadIdx.x + s]);
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    double b = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if (threadIdx.x == 0) acc[0] += w * b;
   }
-  if (threadIdx.x == 0) acc[0] += w * (sh[0].s + sh[0].c);
 }
 
 // dJ/drho(x, 0) at fixed pressure, velocity and radiation (reading R20): with U = (rho, rho v,
@@ -627,7 +631,7 @@ fx_status launch_one_stage(fx_grid* h, const StageArgs<R>& a, const char* what) 
   if (e == cudaSuccess && e3[2]) e = cudaEventRecord(e3[2], h->stream);
   if (e == cudaSuccess && a.phi_out) {
     // J += dt/2 Phi(U_in): this stage's share of the RK-weighted boundary outflow
-    k_sum_into<R><<<1, 256, 0, h->stream>>>(a.phi_out, h->phi_rows * h->G, 0.5 * a.dt,
+    k_sum_into<R><<<1, 1024, 0, h->stream>>>(a.phi_out, h->phi_rows * h->G, 0.5 * a.dt,
                                              reinterpret_cast<double*>(h->ws + h->off_obj));
     e = cudaGetLastError();
   }
@@ -775,7 +779,7 @@ fx_status adjoint_impl(fx_grid* h, double dt, int nsteps, int k, unsigned char* 
       default: x = adj_launch_couple<R, 3>(bb, h->GP, st); break;
     }
     if (x != cudaSuccess) return x;
-    k_sum_into<double><<<1, 256, 0, st>>>(kpart, L.nblk, 1.0, obj + 1);
+    k_sum_into<double><<<1, 1024, 0, st>>>(kpart, L.nblk, 1.0, obj + 1);
     x = cudaMemsetAsync(LW, 0, L.LWn, st);
     if (x != cudaSuccess) return x;
     switch (h->D) {
@@ -790,7 +794,7 @@ fx_status adjoint_impl(fx_grid* h, double dt, int nsteps, int k, unsigned char* 
       default: x = adj_launch_cell<R, 3>(bb, h->GP, st); break;
     }
     if (x != cudaSuccess) return x;
-    k_sum_into<double><<<1, 256, 0, st>>>(kpart, L.nblk, 1.0, obj + 1);
+    k_sum_into<double><<<1, 1024, 0, st>>>(kpart, L.nblk, 1.0, obj + 1);
     return cudaGetLastError();
   };
   for (int j = L.nseg - 1; j >= 0 && nsteps > 0; --j) {
@@ -943,7 +947,7 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   // three resident blocks on each of 152 SMs: short chunks re-read more halo planes)
   if (P.dims >= 2) {
     const int nm = (int)P.n[P.dims - 1];
-    const int TC = 256 / h->GP;
+    const int TC = 256 / (h->GP / groups_per_lane(h->elem == 4, h->GP));  // cells per tile
     const int TX = P.dims == 3 ? (TC >= 16 ? TC / 4 : TC / 2) : TC, TY = TC / TX;
     int64_t tiles = (P.n[0] + TX - 1) / TX;
     if (P.dims == 3) tiles *= (P.n[1] + TY - 1) / TY;

@@ -7,9 +7,13 @@
 
 namespace fx {
 
-// Tile shape of the stage kernel for D dimensions and GP lanes per cell (256 threads per block).
-template <int D, int GP> struct TileShape {
-  static constexpr int TC = 256 / GP;                       // cells per tile
+// Groups per lane of the stage kernel: two in the FP32 forms when a cell has more than 8
+// groups (GP >= 16), else one.  GP = next power of two >= G is the cell's padded group count.
+constexpr int groups_per_lane(bool fp32, int GP) { return (fp32 && GP >= 16) ? 2 : 1; }
+
+// Tile shape of the stage kernel for D dimensions and GL lanes per cell (256 threads per block).
+template <int D, int GL> struct TileShape {
+  static constexpr int TC = 256 / GL;                       // cells per tile
   static constexpr int TX = (D == 3) ? (TC >= 16 ? TC / 4 : TC / 2) : TC;
   static constexpr int TY = TC / TX;
 };
@@ -21,12 +25,17 @@ template <class R, int D, class NT>
 cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid);
 
 // Dynamic shared memory of the stage kernel (tile shape from D and GP).
+template <class R, int D, int GP>
+inline size_t stage_smem_gp(int G) {
+  constexpr int GL = GP / groups_per_lane(sizeof(R) == 4, GP);
+  return stage_smem_bytes<R, D, TileShape<D, GL>::TX, TileShape<D, GL>::TY>(G);
+}
 template <class R, int D>
 inline size_t stage_smem(int GP, int G) {
   switch (GP) {
-    case 8: return stage_smem_bytes<R, D, TileShape<D, 8>::TX, TileShape<D, 8>::TY>(G);
-    case 16: return stage_smem_bytes<R, D, TileShape<D, 16>::TX, TileShape<D, 16>::TY>(G);
-    case 32: return stage_smem_bytes<R, D, TileShape<D, 32>::TX, TileShape<D, 32>::TY>(G);
+    case 8: return stage_smem_gp<R, D, 8>(G);
+    case 16: return stage_smem_gp<R, D, 16>(G);
+    case 32: return stage_smem_gp<R, D, 32>(G);
     default: return 0;
   }
 }
@@ -36,8 +45,10 @@ inline size_t stage_smem(int GP, int G) {
 // type of the stage kernel is the state type R.
 template <class R, int D, int GP, class NT>
 static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t mid) {
-  using TS = TileShape<D, GP>;
-  auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT>;
+  constexpr int NGL = groups_per_lane(sizeof(R) == 4, GP);
+  constexpr int GL = GP / NGL;
+  using TS = TileShape<D, GL>;
+  auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL>;
   const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(a.g.G);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -62,7 +73,7 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
     grid.y = (a.g.n[1] + TS::TY - 1) / TS::TY;
     grid.z = (a.g.n[2] + a.chunk - 1) / a.chunk;
   }
-  kern<<<grid, TS::TX * TS::TY * GP, smem, s>>>(a);
+  kern<<<grid, TS::TX * TS::TY * GL, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -348,6 +348,182 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
 }
 
 // ---------------------------------------------------------------------------------------------
+// couple_cell for the all-FP32 form with NGL groups per lane (GL = GP/NGL lanes per cell): the
+// same iteration, stopping tests and bookkeeping; the group sums add the lane's own groups before
+// the segment shuffle, and the temperature power of the opacity is shared by a lane's groups.
+// ---------------------------------------------------------------------------------------------
+template <int D, int GL, int NGL>
+__device__ __forceinline__ unsigned couple_cell_n(const DevGrid& g, const GroupConst& gc,
+                                                  const PlanckParams& pk, const PlanckTable& ptab,
+                                                  const Consts<float>& kn, bool active, int lane,
+                                                  const float* h, float& rho, float* m, float& rhoe,
+                                                  float* E, float (*F)[3], float* Tout) {
+  using T = float;
+  const int G = g.G;
+  unsigned st = 0;
+  bool hasj[NGL];
+  int gidx[NGL];
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) {
+    hasj[j] = lane * NGL + j < G;
+    gidx[j] = hasj[j] ? lane * NGL + j : 0;
+  }
+  if (rho < kn.rho_floor) { rho = kn.rho_floor; st |= ST_FLOOR; }
+  const T irho = frcp(rho);
+  T ke = T(0);
+#pragma unroll
+  for (int q = 0; q < D; ++q) { T mh = h ? m[q] * frcp(h[q]) : m[q]; ke += T(0.5) * mh * mh * irho; }
+  T u_m = rhoe - ke;
+  if (u_m < kn.u_floor) { u_m = kn.u_floor; rhoe = ke + u_m; st |= ST_FLOOR; }
+  T Em[NGL], efj[NGL], Esl = T(0);
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) {
+    Em[j] = hasj[j] ? E[j] : T(0);
+    if (hasj[j] && Em[j] < kn.E_floor) Em[j] = kn.E_floor;  // silent positivity floor
+    Esl += Em[j];
+    efj[j] = gc.efac_of(gidx[j], T(0));
+  }
+  const T Esum = seg_sum<GL>(Esl);
+  const T rcv = rho * kn.cv;
+  const T Tm = u_m * frcp(rcv);
+  const T K = kn.kappa0 * hpow(rho, g.kap_rho_h), Sg = kn.sigma0 * rho;
+  // residual r = rho c_v dl + sum_g (E_g(T) - E_g^-) and dr/dT at T = T^- + dl, with each of the
+  // lane's group energies and their T derivatives
+  auto evaln = [&](T dl, T& r, T& dr, T* Eg, T* dEg) {
+    const T Tl = Tm + dl;
+    const T invT = frcp(Tl);
+    const T kT = K * hpow(Tl, g.kap_T_h);
+    T a = T(0), b = T(0);
+#pragma unroll
+    for (int j = 0; j < NGL; ++j) {
+      T Bq, dBq;
+      const Coupler<2 * GL, T, T> cpj{g, pk, ptab, gidx[j], hasj[j], false, rcv, Tm, K, Sg, kn.cdts, Em[j],
+                                      kn.aN, efj[j], gc.edge_of(gidx[j], T(0)), gc.edge_of(G, T(0))};
+      cpj.planck(Tl, invT, Bq, dBq);
+      const T tau = kn.cdts * kT * efj[j];
+      const T dtau = tau * (T(0.5) * (T)g.kap_T_h) * invT;
+      const T inv = frcp(T(1) + tau);
+      Eg[j] = (Em[j] + tau * Bq) * inv;
+      dEg[j] = (tau * dBq + dtau * (Bq - Eg[j])) * inv;
+      a += hasj[j] ? Eg[j] - Em[j] : T(0);
+      b += hasj[j] ? dEg[j] : T(0);
+    }
+    r = rcv * dl + seg_sum<GL>(a);
+    dr = rcv + seg_sum<GL>(b);
+  };
+  T dl = T(0), r, dr;
+  T Eg[NGL], dEg[NGL];
+  evaln(dl, r, dr, Eg, dEg);
+  const T scale = u_m + Esum;
+  const T rtol = kn.rtol, atol = kn.atol;
+  bool done = !active, ok = !active, need_dir = true;
+  int it = 0, ls = 0;
+  T dT = T(0), lam = T(1);
+  const int guard = g.newton_maxit * 41 + 2;
+  for (int k = 0; k < guard; ++k) {
+    if (!done && need_dir) {
+      if (it >= g.newton_maxit) { done = true; }
+      else if (fabsf(r) <= atol * scale) { done = true; ok = true; }
+      else {
+        dT = -r / dr;
+        ++it;
+        if (fabsf(dT) <= rtol * (Tm + dl)) {
+          // converged: the group energies at T + dT follow from the linearisation
+          dl += dT;
+#pragma unroll
+          for (int j = 0; j < NGL; ++j) Eg[j] += dEg[j] * dT;
+          done = true;
+          ok = true;
+        } else { lam = T(1); ls = 0; need_dir = false; }
+      }
+    }
+    if (__all_sync(0xffffffffu, done)) break;
+    const T dt_ = dl + lam * dT;
+    const bool valid = !done && (Tm + dt_) > T(0);
+    T rt, drt, Et[NGL], dEt[NGL];
+    evaln(valid ? dt_ : dl, rt, drt, Et, dEt);
+    if (!done) {
+      if (valid && fabsf(rt) < fabsf(r)) {
+        dl = dt_; r = rt; dr = drt; need_dir = true;
+#pragma unroll
+        for (int j = 0; j < NGL; ++j) { Eg[j] = Et[j]; dEg[j] = dEt[j]; }
+      } else { lam *= T(0.5); if (++ls >= 40) done = true; }
+    }
+  }
+  // bisection fallback on a bracket around [T^-, T_rad] (reading R11), in T - T^-
+  if (__any_sync(0xffffffffu, active && !ok)) {
+    const bool need = active && !ok;
+    const T Tr = sqrtf(sqrtf(Esum * frcp(kn.aN * T(6.4939394022668291491))));  // (sum E / a_R)^(1/4)
+    const T Tc = Tm + dl;
+    T lo = fminf(fminf(Tc, Tr), Tm) - Tm, hi = fmaxf(fmaxf(Tc, Tr), Tm) - Tm;
+    int phase = need ? 0 : 3, cnt = 0;
+    bool brk = false;
+    T rr, dd, ee[NGL], de[NGL];
+    for (int k = 0; k < 400 + g.bisect_maxit + 4; ++k) {
+      if (__all_sync(0xffffffffu, phase == 3)) break;
+      const T Te = phase == 0 ? lo : (phase == 1 ? hi : (phase == 2 ? T(0.5) * (lo + hi) : dl));
+      evaln(Te, rr, dd, ee, de);
+      if (phase == 0) {
+        if (rr > T(0) && cnt < 200) { lo = T(0.5) * (lo + Tm) - Tm; ++cnt; }  // T_lo /= 2
+        else { phase = 1; cnt = 0; brk = rr <= T(0); }
+      } else if (phase == 1) {
+        if (rr < T(0) && cnt < 200) { hi = T(2) * (hi + Tm) - Tm; ++cnt; }   // T_hi *= 2
+        else {
+          brk = brk && rr >= T(0);
+          cnt = 0;
+          phase = brk ? (g.bisect_maxit > 0 ? 2 : 3) : 3;
+        }
+      } else if (phase == 2) {
+        if (rr > T(0)) hi = Te; else lo = Te;
+        ++cnt;
+        if (hi - lo <= rtol * (hi + Tm)) { ok = true; phase = 3; }
+        else if (cnt >= g.bisect_maxit) phase = 3;
+      }
+    }
+    if (need && brk) dl = T(0.5) * (lo + hi);
+    T r2, d2, e2[NGL], de2[NGL];
+    evaln(dl, r2, d2, e2, de2);
+    if (need) {
+#pragma unroll
+      for (int j = 0; j < NGL; ++j) Eg[j] = e2[j];
+    }
+  }
+  if (active && !ok) st |= ST_NEWTON;
+  if (Tout) *Tout = Tm + dl;
+  // energy update by conservation (R12)
+  T dEl = T(0);
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) dEl += hasj[j] ? Eg[j] - Em[j] : T(0);
+  rhoe = ke + (u_m - seg_sum<GL>(dEl));
+#pragma unroll
+  for (int j = 0; j < NGL; ++j)
+    if (hasj[j]) E[j] = Eg[j];
+  // momentum coupling at the converged temperature (Eq. 28; Eqs. 31-32)
+  const T kT = K * hpow(Tm + dl, g.kap_T_h);
+  T dF[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) {
+    const T fac = frcp(T(1) + kn.cdts * (kT * efj[j] + Sg));
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      if (hasj[j]) {
+        const T Fq = F[j][q];
+        const T Fn = Fq * fac;
+        dF[q] += Fn - Fq;
+        F[j][q] = Fn;
+      }
+    }
+  }
+  T dwork = T(0);
+#pragma unroll
+  for (int q = 0; q < D; ++q) dwork += (h ? m[q] * frcp(h[q] * h[q]) : m[q]) * irho * dF[q];
+#pragma unroll
+  for (int q = 0; q < D; ++q) m[q] -= seg_sum<GL>(dF[q]) * kn.ic2;
+  rhoe -= seg_sum<GL>(dwork) * kn.ic2;
+  return st;
+}
+
+// ---------------------------------------------------------------------------------------------
 // The same interaction for the FP32 form with the FP64 Newton (group arithmetic in FP32, the
 // temperature iterate, residual and the energy/momentum bookkeeping in FP64), organised for
 // GB300's FP64 pipe, whose cost is per warp instruction whatever the number of active lanes:
@@ -358,23 +534,30 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
 // same order of decisions as couple_cell.  Called by all threads of the block (two barriers per
 // evaluation); the iteration counts are bounded as in couple_cell.
 // ---------------------------------------------------------------------------------------------
-template <int D, int GP, int TC>
+template <int D, int GP, int NGL, int TC>
 __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupConst& gc,
                                                  const PlanckParams& pk, const PlanckTable& ptab,
                                                  const Consts<double>& kn, const Consts<float>& kl,
                                                  int nsm, bool active, int lane, int tcell, const float* h,
-                                                 float& rho, float* m, float& rhoe, float& E,
-                                                 float* F, float* Tout) {
+                                                 float& rho, float* m, float& rhoe, float* E,
+                                                 float (*F)[3], float* Tout) {
   using LT = float;
   using NT = double;
-  static_assert(TC * GP == 256 && TC <= 32, "one scalar lane per cell of a 256-thread block");
+  constexpr int GL = GP / NGL;  // lanes per cell; lane l owns groups l*NGL .. l*NGL + NGL-1
+  static_assert(TC * GL == 256 && TC <= 32, "one scalar lane per cell of a 256-thread block");
   __shared__ double s_rho[TC], s_m[3][TC], s_rhoe[TC], s_h[2][TC];
   __shared__ float s_Esum[TC], s_s1[TC], s_s2[TC], s_Tt[TC], s_lin[TC], s_Es0[TC];
   __shared__ int s_flag[TC], s_more;
   __shared__ double s_sum[4][TC];  // FP64 group sums of dE and dF_q per cell
   enum { F_ACC = 1, F_DONE = 2, F_NEWTON = 4, F_FLOOR = 8, F_BIS = 16 };
   const int G = g.G;
-  const bool has = lane < G;
+  bool hasj[NGL];
+  int gidx[NGL];
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) {
+    hasj[j] = lane * NGL + j < G;
+    gidx[j] = hasj[j] ? lane * NGL + j : 0;
+  }
   // The scalar warp: blocks resident on one multiprocessor at the same time (linear indices that
   // differ by multiples of the multiprocessor count, in the first wave) take different warps, so
   // that their FP64 work lands in different sub-partitions of the multiprocessor.
@@ -385,9 +568,14 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
 
   // ---- segments: the cell's inputs for the scalar warp (FP32 values, exact in FP64); E^- with
   // its silent positivity floor.  Every per-lane value stays FP32: FP64 is the scalar warp's.
-  LT Em = has ? E : LT(0);
-  if (has && Em < kl.E_floor) Em = kl.E_floor;
-  const LT Esum = seg_sum<GP>(Em);
+  LT Em[NGL], Esl = LT(0);
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) {
+    Em[j] = hasj[j] ? E[j] : LT(0);
+    if (hasj[j] && Em[j] < kl.E_floor) Em[j] = kl.E_floor;
+    Esl += Em[j];
+  }
+  const LT Esum = seg_sum<GL>(Esl);
   if (lane == 0) {
     s_rho[tcell] = (double)rho;
 #pragma unroll
@@ -429,27 +617,39 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
     s_s1[c] = (float)(kn.sigma0 * s_rho[c]);
   }
   __syncthreads();
-  // the segment's group state: accepted (Eg, dEg) and the latest evaluation (Et, dEt)
-  Coupler<GP, LT, NT> cp{g, pk, ptab, lane, has, (G == GP) && (lane == G - 1), 0.0, 0.0,
-                         s_Esum[tcell], s_s1[tcell],
-                         kl.cdts, Em, kl.aN, gc.efac_of(has ? lane : 0, LT(0)),
-                         gc.edge_of(lane <= G ? lane : G, LT(0)), gc.edge_of(G, LT(0))};
-  LT Eg = Em, dEg = LT(0), Et = Em, dEt = LT(0);
+  // the segment's group state: accepted (Eg, dEg) and the latest evaluation (Et, dEt); one
+  // Coupler per owned group serves the FP32 Planck tables (its lane field is the group index)
+  const LT Kc = s_Esum[tcell], Sc = s_s1[tcell];
+  LT efj[NGL];
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) efj[j] = gc.efac_of(gidx[j], LT(0));
+  LT Eg[NGL], dEg[NGL], Et[NGL], dEt[NGL];
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) { Eg[j] = Em[j]; dEg[j] = LT(0); Et[j] = Em[j]; dEt[j] = LT(0); }
   // one evaluation at the proposed temperature: E_g(T) (Eq. 25) and dE_g/dT; the two group sums
   // go to the scalar warp
   auto seg_eval = [&]() {
     const LT Tl = s_Tt[tcell];
     const LT invT = frcp(Tl);
-    LT Bq, dBq;
-    cp.planck(Tl, invT, Bq, dBq);
-    const LT kap = cp.K * hpow(Tl, g.kap_T_h) * cp.efac;
-    const LT tau = cp.cdts * kap;
-    const LT dtau = tau * (LT(0.5) * (LT)g.kap_T_h) * invT;
-    const LT inv = frcp(LT(1) + tau);
-    Et = (Em + tau * Bq) * inv;
-    dEt = (tau * dBq + dtau * (Bq - Et)) * inv;
-    const LT a = seg_sum<GP>(has ? Et - Em : LT(0));
-    const LT b = seg_sum<GP>(has ? dEt : LT(0));
+    const LT kT = Kc * hpow(Tl, g.kap_T_h);
+    LT a = LT(0), b = LT(0);
+#pragma unroll
+    for (int j = 0; j < NGL; ++j) {
+      LT Bq, dBq;
+      const Coupler<GP, LT, NT> cpj{g, pk, ptab, gidx[j], hasj[j], false, 0.0, 0.0, Kc, Sc, kl.cdts, Em[j],
+                                    kl.aN, efj[j], gc.edge_of(gidx[j], LT(0)), gc.edge_of(G, LT(0))};
+      cpj.planck(Tl, invT, Bq, dBq);
+      const LT kap = kT * efj[j];
+      const LT tau = kl.cdts * kap;
+      const LT dtau = tau * (LT(0.5) * (LT)g.kap_T_h) * invT;
+      const LT inv = frcp(LT(1) + tau);
+      Et[j] = (Em[j] + tau * Bq) * inv;
+      dEt[j] = (tau * dBq + dtau * (Bq - Et[j])) * inv;
+      a += hasj[j] ? Et[j] - Em[j] : LT(0);
+      b += hasj[j] ? dEt[j] : LT(0);
+    }
+    a = seg_sum<GL>(a);
+    b = seg_sum<GL>(b);
     if (lane == 0) { s_s1[tcell] = a; s_s2[tcell] = b; }
   };
   // the scalar warp's Newton decision for its cell (as in couple_cell): from the accepted point
@@ -504,9 +704,12 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
   for (int kk = 0; kk < guard; ++kk) {
     {
       const int f = s_flag[tcell];
-      if (f & F_ACC) { Eg = Et; dEg = dEt; }
       const float lin = s_lin[tcell];
-      if (lin != 0.0f) Eg += dEg * lin;
+#pragma unroll
+      for (int j = 0; j < NGL; ++j) {
+        if (f & F_ACC) { Eg[j] = Et[j]; dEg[j] = dEt[j]; }
+        if (lin != 0.0f) Eg[j] += dEg[j] * lin;
+      }
     }
     // (the scalar warp rewrites the flags and s_more only after the barrier that follows the
     // next evaluation, which every thread reaches after reading them)
@@ -594,7 +797,10 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
     }
     __syncthreads();
     seg_eval();
-    if (s_flag[tcell] & F_BIS) Eg = Et;
+    if (s_flag[tcell] & F_BIS) {
+#pragma unroll
+      for (int j = 0; j < NGL; ++j) Eg[j] = Et[j];
+    }
     __syncthreads();
   }
 
@@ -602,23 +808,35 @@ __device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupCo
   // absorption update at the converged temperature (Eq. 28) and its feedback (Eqs. 31-32)
   // (s_Tt holds T* = T^- + dl of every cell: written when Newton stopped, or by the bisection)
   const LT Tst = s_Tt[tcell];
-  const LT kap = cp.K * hpow(Tst, g.kap_T_h) * cp.efac;
-  const LT fac = frcp(LT(1) + cp.cdts * (kap + cp.Sg));
+  const LT kT = Kc * hpow(Tst, g.kap_T_h);
   // FP64 group sums of the energy change and of the flux changes, in the cells' segments (the
   // FP64 pipe cost is per warp instruction: spread over all warps, not serialised in one)
   {
-    const NT sE = seg_sum<GP>(has ? (NT)Eg - (NT)Em : 0.0);
+    NT dE = 0.0;
+#pragma unroll
+    for (int j = 0; j < NGL; ++j) dE += hasj[j] ? (NT)Eg[j] - (NT)Em[j] : 0.0;
+    const NT sE = seg_sum<GL>(dE);
     if (lane == 0) s_sum[0][tcell] = sE;
   }
+  LT fac[NGL];
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) fac[j] = frcp(LT(1) + kl.cdts * (kT * efj[j] + Sc));
 #pragma unroll
   for (int q = 0; q < D; ++q) {
-    const LT Fq = has ? F[q] : LT(0);
-    const LT Fn = Fq * fac;
-    const NT sF = seg_sum<GP>((NT)(Fn - Fq));
+    NT dF = 0.0;
+#pragma unroll
+    for (int j = 0; j < NGL; ++j) {
+      const LT Fq = hasj[j] ? F[j][q] : LT(0);
+      const LT Fn = Fq * fac[j];
+      dF += (NT)(Fn - Fq);
+      if (hasj[j]) F[j][q] = Fn;
+    }
+    const NT sF = seg_sum<GL>(dF);
     if (lane == 0) s_sum[1 + q][tcell] = sF;
-    if (has) F[q] = Fn;
   }
-  if (has) E = Eg;
+#pragma unroll
+  for (int j = 0; j < NGL; ++j)
+    if (hasj[j]) E[j] = Eg[j];
   __syncthreads();
   if (scalar) {
     const NT dEsum = s_sum[0][c];
@@ -687,8 +905,10 @@ inline size_t stage_smem_bytes(int G) {
 
 // ---------------------------------------------------------------------------------------------
 // The radiation/update kernel (one launch per RK stage, after gas_face_kernel).  A block owns a
-// tile of TX x TY cells and marches along the slowest axis; a thread serves one (cell, group).
-// Per plane k, between three barriers:
+// tile of TX x TY cells and marches along the slowest axis.  Each cell is served by a segment of
+// GL = GP/NGL lanes, and a thread owns NGL consecutive groups of its cell (NGL = 2 in the FP32
+// forms with G > 8: the per-cell work of a thread is shared by two groups and the two groups'
+// arithmetic interleaves).  Per plane k, between three barriers:
 //   A  its own radiation values of plane k+2 (prefetched into registers one step ahead) and the
 //      in-plane halo of plane k go to a four-plane shared ring; the cell's opacity factors are
 //      formed from its gas variables (held by lanes 0..NG-1);
@@ -698,21 +918,23 @@ inline size_t stage_smem_bytes(int G) {
 //      the contact speeds of the gas faces (Eq. 19);
 //   D  divergence (gas fluxes from the face buffer), RK combine, coupling, store of plane k.
 // ---------------------------------------------------------------------------------------------
-template <class R, int D, int GP, int TX, int TY, class LT, class NT>
-__global__ void __launch_bounds__(TX * TY * GP, sizeof(R) == 4 ? 3 : 2)
+template <class R, int D, int GP, int TX, int TY, class LT, class NT, int NGL>
+__global__ void __launch_bounds__(TX * TY * (GP / NGL), (sizeof(R) == 4 && NGL == 1) ? 3 : 2)
 stage_kernel(const __grid_constant__ StageArgs<R> A) {
   using LY = StageLayout<D, TX, TY>;
-  constexpr int NTH = TX * TY * GP;  // threads per block
+  constexpr int GL = GP / NGL;       // lanes per cell
+  constexpr int NTH = TX * TY * GL;  // threads per block
   constexpr int NG = LY::NG, NRV = LY::NRV;
   constexpr int PX = LY::PX, PC = LY::PC, TC = LY::TC, NFX = LY::NFX, NFY = LY::NFY;
   constexpr int MD = D - 1;  // march direction (D >= 2)
+  static_assert(NGL == 1 || (sizeof(LT) == 4 && GL >= 2 + D), "two groups per lane: FP32 groups, gas in lanes < 2+D");
 
   const DevGrid& g = A.g;
   const Consts<R>& KR = A.k(R(0));
   const int G = g.G;
   const int tid = threadIdx.x;
-  const int lane = tid % GP;
-  const int tcell = tid / GP;  // tile cell of this thread
+  const int lane = tid % GL;
+  const int tcell = tid / GL;  // tile cell of this thread
   const int lx = tcell % TX, ly = tcell / TX;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int x0 = blockIdx.x * TX;
@@ -721,8 +943,14 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   const int kbeg = (D == 1) ? 0 : ((D == 2) ? blockIdx.y : blockIdx.z) * A.chunk;
   const int kend = (D == 1) ? 1 : min(kbeg + A.chunk, nmarch);
   const uint32_t ncell = (uint32_t)g.ncell;  // the host keeps every state offset below 2^32
-  const bool has = lane < G;
-  const int gsel = has ? lane : 0;
+  // this thread's groups: lane * NGL + j
+  bool hasj[NGL];
+  int gj[NGL];
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) {
+    hasj[j] = lane * NGL + j < G;
+    gj[j] = hasj[j] ? lane * NGL + j : 0;
+  }
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* const sm = reinterpret_cast<R*>(smem_raw);
@@ -789,7 +1017,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   };
 
   // Load `ncl` cells of plane k (enumerated by cell_of) into ring slot `slot`: gas (one thread
-  // per cell, for the opacity factors), radiation with GP lanes per cell, lane = group.
+  // per cell, for the opacity factors), radiation with one thread per (cell, group).
   auto load_cells = [&](int slot, int k, int ncl, auto cell_of) {
     for (int i = tid; i < ncl; i += NTH) {
       int sx, sy;
@@ -829,7 +1057,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   const bool cell_in = (x0 + lx < nx) && (D < 3 || y0 + ly < ny);
   const int gx = x0 + lx, gy = y0 + ly;
   const int sc_own = scell(lx, ly);
-  // own radiation values (this thread's cell and group) and own gas variable (lanes 0..NG-1)
+  // own radiation values (this thread's cell and groups) and own gas variable (lanes 0..NG-1)
   // of plane k, from global memory (mirror ghosts negate the normal components)
   // the in-plane part of this thread's cell index and its mirror flips are fixed along the march
   bool own_fl[3] = {false, false, false};
@@ -850,14 +1078,17 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     fl[MD] = fm;
     return own_xy + (uint32_t)km * (D == 2 ? (uint32_t)nx : (uint32_t)nx * ny);
   };
-  auto own_rad = [&](int k, R* Q) {
+  auto own_rad = [&](int k, R (*Q)[NRV]) {
     bool fl[3];
     const uint32_t gc_ = own_idx(k, fl);
 #pragma unroll
     for (int v = 0; v < NRV; ++v) {
-      R val = A.in[NG * ncell + (v * ncell + gc_) * G + gsel];
-      Q[v] = (v >= 1 && fl[v - 1]) ? -val : val;
-      if (sph && v >= 1) Q[v] *= frcp(hfac(v - 1, gx, k));  // physical component
+#pragma unroll
+      for (int j = 0; j < NGL; ++j) {
+        R val = A.in[NG * ncell + (v * ncell + gc_) * G + gj[j]];
+        Q[j][v] = (v >= 1 && fl[v - 1]) ? -val : val;
+        if (sph && v >= 1) Q[j][v] *= frcp(hfac(v - 1, gx, k));  // physical component
+      }
     }
   };
   const int gvar = lane < NG ? lane : 0;
@@ -869,14 +1100,17 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   };
   // store prefetched own values of plane k into slot `slot`; the cell's lane 0 gathers the gas
   // variables from lanes 0..NG-1 and forms the opacity factors
-  auto store_own = [&](int slot, const R* Q, R gv, int k) {
-    if (has) {
+  auto store_own = [&](int slot, R (*Q)[NRV], R gv, int k) {
 #pragma unroll
-      for (int v = 0; v < NRV; ++v) rad_at(slot, v, sc_own, lane) = Q[v];
+    for (int j = 0; j < NGL; ++j) {
+      if (hasj[j]) {
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rad_at(slot, v, sc_own, gj[j]) = Q[j][v];
+      }
     }
     R u[NG];
 #pragma unroll
-    for (int v = 0; v < NG; ++v) u[v] = __shfl_sync(0xffffffffu, gv, v, GP);
+    for (int v = 0; v < NG; ++v) u[v] = __shfl_sync(0xffffffffu, gv, v, GL);
     if (lane == 0) opac(u, slot, sc_own, gx, k);
   };
 
@@ -894,15 +1128,19 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     for (int q = 0; q < D; ++q)
       out[1 + q] = KR.hc2 * (PL[q] + PR[q]) - KR.hc * (QR[1 + q] - QL[1 + q]) + vstar * Qu[1 + q];
   };
-  const R ef = R(sgc->efac_of(gsel, R(0)));
-  auto chi_of = [&](int slot, int sc) { return pk[(slot * 2) * PC + sc] * ef + pk[(slot * 2 + 1) * PC + sc]; };
+  R ef[NGL];
+#pragma unroll
+  for (int j = 0; j < NGL; ++j) ef[j] = R(sgc->efac_of(gj[j], R(0)));
+  auto chi_of = [&](int slot, int sc, int j) {
+    return pk[(slot * 2) * PC + sc] * ef[j] + pk[(slot * 2 + 1) * PC + sc];
+  };
   auto recon_rad = [&](const MCCoef<R>& c, const R* Qm, const R* Q0, const R* Qp, R* a, R* b) {
 #pragma unroll
     for (int v = 0; v < NRV; ++v) recon_linear_c(c, Qm[v], Q0[v], Qp[v], a[v], b[v]);
   };
-  auto rad_cell = [&](int slot, int sc, R* Q) {
+  auto rad_cell = [&](int slot, int sc, int gg, R* Q) {
 #pragma unroll
-    for (int v = 0; v < NRV; ++v) Q[v] = rad_at(slot, v, sc, gsel);
+    for (int v = 0; v < NRV; ++v) Q[v] = rad_at(slot, v, sc, gg);
   };
 
   // gas face buffer: lower-face index of cell (gx, gy, k) along direction d
@@ -924,11 +1162,11 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     return __ldg(A.faces + (uint32_t)A.face_off[d] + v * nfd[d] + f);
   };
 
-  R Q0[NRV] = {}, Q1[NRV] = {}, Qn[NRV] = {};  // own radiation values: plane k, k+1, prefetch
-  R bm0[NRV] = {};                             // own march-direction upper-face state, plane k
-  R rfm_old[NRV] = {};                         // radiation flux through the lower march face
-  R g0 = R(0), g1 = R(0), gn = R(0);           // own gas variable (lanes < NG): k, k+1, prefetch
-  R b0[NRV] = {}, bg0 = R(0);                  // stage-2 base values of plane k
+  R Q0[NGL][NRV] = {}, Q1[NGL][NRV] = {}, Qn[NGL][NRV] = {};  // own values: plane k, k+1, prefetch
+  R bm0[NGL][NRV] = {};                     // own march-direction upper-face states, plane k
+  R rfm_old[NGL][NRV] = {};                 // radiation fluxes through the lower march face
+  R g0 = R(0), g1 = R(0), gn = R(0);        // own gas variable (lanes < NG): k, k+1, prefetch
+  R b0[NGL][NRV] = {}, bg0 = R(0);          // stage-2 base values of plane k
 
   // ---------------------------------------------------------------- prologue
   if (D == 1) {
@@ -938,7 +1176,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     __syncthreads();
   } else {
     for (int k = kbeg - 1; k <= kbeg + 1; ++k) load_cells(k & 3, k, TC, interior_of);
-    R Qm1[NRV], Qm2[NRV];
+    R Qm1[NGL][NRV], Qm2[NGL][NRV];
     own_rad(kbeg - 2, Qm2);
     own_rad(kbeg - 1, Qm1);
     own_rad(kbeg, Q0);
@@ -949,17 +1187,24 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     gn = own_gas(kbeg + 2);
     __syncthreads();
     // march reconstruction of planes kbeg-1 (upper face) and kbeg, and the face kbeg-1/2
-    R a_[NRV], bprev[NRV];
-    recon_rad(mc_coef(tm, bc_pad(kbeg - 1)), Qm2, Qm1, Q0, a_, bprev);
-    recon_rad(mc_coef(tm, bc_pad(kbeg)), Qm1, Q0, Q1, a_, bm0);
+    const MCCoef<R> mp = mc_coef(tm, bc_pad(kbeg - 1)), m0 = mc_coef(tm, bc_pad(kbeg));
     const R vs = gface(MD, NG, face_m(kbeg));
-    rad_face(MD, bprev, a_, chi_of((kbeg - 1) & 3, sc_own), chi_of(kbeg & 3, sc_own),
-             sph ? tm(T_ELL, bc_pad(kbeg)) * tx(T_XH, bc_pad(gx)) : tm(T_ELL, bc_pad(kbeg)), vs, rfm_old);
+    const R ell = sph ? tm(T_ELL, bc_pad(kbeg)) * tx(T_XH, bc_pad(gx)) : tm(T_ELL, bc_pad(kbeg));
+#pragma unroll
+    for (int j = 0; j < NGL; ++j) {
+      R a_[NRV], bprev[NRV];
+      recon_rad(mp, Qm2[j], Qm1[j], Q0[j], a_, bprev);
+      recon_rad(m0, Qm1[j], Q0[j], Q1[j], a_, bm0[j]);
+      rad_face(MD, bprev, a_, chi_of((kbeg - 1) & 3, sc_own, j), chi_of(kbeg & 3, sc_own, j), ell, vs,
+               rfm_old[j]);
+    }
   }
   if (A.base != nullptr && cell_in) {
     const uint32_t c0 = D == 1 ? gx : D == 2 ? (uint32_t)kbeg * nx + gx : ((uint32_t)kbeg * ny + gy) * nx + gx;
 #pragma unroll
-    for (int v = 0; v < NRV; ++v) b0[v] = A.base[NG * ncell + (v * ncell + c0) * G + gsel];
+    for (int v = 0; v < NRV; ++v)
+#pragma unroll
+      for (int j = 0; j < NGL; ++j) b0[j][v] = A.base[NG * ncell + (v * ncell + c0) * G + gj[j]];
     bg0 = A.base[gvar * ncell + c0];
   }
   const int ipx = bc_pad(gx);  // the x-direction table row of this cell
@@ -1022,127 +1267,137 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         gnet = gnet + (gface(MD, gvar, face_m(k + 1)) * fm_r[gcls] - gface(MD, gvar, face_m(k)) * fm_l[gcls]);
     }
     __syncthreads();
-    R Q2[NRV];
+    R Q2[NGL][NRV];
 #pragma unroll
-    for (int v = 0; v < NRV; ++v) Q2[v] = Qn[v];
+    for (int j = 0; j < NGL; ++j)
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) Q2[j][v] = Qn[j][v];
     const R g2 = gn;  // own gas variable of plane k+2 (gn is refilled with plane k+3 below)
     // ---- B: reconstructions
-    R ax[NRV], bx[NRV], am1[NRV], bm1[NRV], ay[NRV], by[NRV];
-    {
-      R Qa[NRV], Qb[NRV];
-      rad_cell(s0, sc_own - 1, Qa);
-      rad_cell(s0, sc_own + 1, Qb);
-      recon_rad(mcx, Qa, Q0, Qb, ax, bx);
-      if (has) {
+    R ax[NGL][NRV], bx[NGL][NRV], am1[NGL][NRV], bm1[NGL][NRV], ay[NGL][NRV], by[NGL][NRV];
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1) + lx + 1) * G + lane] = bx[v];
+    for (int j = 0; j < NGL; ++j) {
+      const int gg = gj[j];
+      R Qa[NRV], Qb[NRV];
+      rad_cell(s0, sc_own - 1, gg, Qa);
+      rad_cell(s0, sc_own + 1, gg, Qb);
+      recon_rad(mcx, Qa, Q0[j], Qb, ax[j], bx[j]);
+      if (hasj[j]) {
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1) + lx + 1) * G + gg] = bx[j][v];
       }
       if (lx == 0) {  // halo cell -1: its upper-face state is the left state of face 0
         R Qc[NRV], ta[NRV], tb[NRV];
-        rad_cell(s0, sc_own - 2, Qc);
-        recon_rad(mc_coef(tx, bc_pad(gx - 1)), Qc, Qa, Q0, ta, tb);
-        if (has) {
+        rad_cell(s0, sc_own - 2, gg, Qc);
+        recon_rad(mc_coef(tx, bc_pad(gx - 1)), Qc, Qa, Q0[j], ta, tb);
+        if (hasj[j]) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * G + lane] = tb[v];
+          for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * G + gg] = tb[v];
         }
       }
       if (lx == TX - 1) {  // halo cell TX: its lower-face state is the right state of face TX
         R Qc[NRV], ta[NRV], tb[NRV];
-        rad_cell(s0, sc_own + 2, Qc);
-        recon_rad(mc_coef(tx, bc_pad(gx + 1)), Q0, Qb, Qc, ta, tb);
-        if (has) {
+        rad_cell(s0, sc_own + 2, gg, Qc);
+        recon_rad(mc_coef(tx, bc_pad(gx + 1)), Q0[j], Qb, Qc, ta, tb);
+        if (hasj[j]) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * G + lane] = ta[v];
+          for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * G + gg] = ta[v];
         }
       }
+      if (D == 3) {
+        R Qa3[NRV], Qb3[NRV];
+        rad_cell(s0, sc_own - PX, gg, Qa3);
+        rad_cell(s0, sc_own + PX, gg, Qb3);
+        recon_rad(mc_coef(ty, bc_pad(gy)), Qa3, Q0[j], Qb3, ay[j], by[j]);
+        if (hasj[j]) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) rby[(v * NFY + (ly + 1) * TX + lx) * G + gg] = by[j][v];
+        }
+        if (ly == 0) {
+          R Qc[NRV], ta[NRV], tb[NRV];
+          rad_cell(s0, sc_own - 2 * PX, gg, Qc);
+          recon_rad(mc_coef(ty, bc_pad(gy - 1)), Qc, Qa3, Q0[j], ta, tb);
+          if (hasj[j]) {
+#pragma unroll
+            for (int v = 0; v < NRV; ++v) rby[(v * NFY + lx) * G + gg] = tb[v];
+          }
+        }
+        if (ly == TY - 1) {
+          R Qc[NRV], ta[NRV], tb[NRV];
+          rad_cell(s0, sc_own + 2 * PX, gg, Qc);
+          recon_rad(mc_coef(ty, bc_pad(gy + 1)), Q0[j], Qb3, Qc, ta, tb);
+          if (hasj[j]) {
+#pragma unroll
+            for (int v = 0; v < NRV; ++v) ray[(v * TX + lx) * G + gg] = ta[v];
+          }
+        }
+      }
+      if (D >= 2) recon_rad(mc_coef(tm, bc_pad(k + 1)), Q0[j], Q1[j], Q2[j], am1[j], bm1[j]);
     }
-    if (D == 3) {
-      R Qa[NRV], Qb[NRV];
-      rad_cell(s0, sc_own - PX, Qa);
-      rad_cell(s0, sc_own + PX, Qb);
-      recon_rad(mc_coef(ty, bc_pad(gy)), Qa, Q0, Qb, ay, by);
-      if (has) {
-#pragma unroll
-        for (int v = 0; v < NRV; ++v) rby[(v * NFY + (ly + 1) * TX + lx) * G + lane] = by[v];
-      }
-      if (ly == 0) {
-        R Qc[NRV], ta[NRV], tb[NRV];
-        rad_cell(s0, sc_own - 2 * PX, Qc);
-        recon_rad(mc_coef(ty, bc_pad(gy - 1)), Qc, Qa, Q0, ta, tb);
-        if (has) {
-#pragma unroll
-          for (int v = 0; v < NRV; ++v) rby[(v * NFY + lx) * G + lane] = tb[v];
-        }
-      }
-      if (ly == TY - 1) {
-        R Qc[NRV], ta[NRV], tb[NRV];
-        rad_cell(s0, sc_own + 2 * PX, Qc);
-        recon_rad(mc_coef(ty, bc_pad(gy + 1)), Q0, Qb, Qc, ta, tb);
-        if (has) {
-#pragma unroll
-          for (int v = 0; v < NRV; ++v) ray[(v * TX + lx) * G + lane] = ta[v];
-        }
-      }
-    }
-    if (D >= 2) recon_rad(mc_coef(tm, bc_pad(k + 1)), Q0, Q1, Q2, am1, bm1);
     __syncthreads();
     // ---- C: radiation face fluxes
-    R rfm_new[NRV] = {};
-    {
-      const int fx = ly * (TX + 1) + lx;
-      R QL[NRV], out[NRV];
+    R rfm_new[NGL][NRV] = {};
+    const R ell_m = sph ? tm(T_ELL, bc_pad(k + 1)) * tx(T_XH, ipx) : tm(T_ELL, bc_pad(k + 1));
 #pragma unroll
-      for (int v = 0; v < NRV; ++v) QL[v] = rbx[(v * NFX + fx) * G + gsel];
-      rad_face(0, QL, ax, chi_of(s0, sc_own - 1), chi_of(s0, sc_own), ellx, vsx, out);
-      if (has) {
+    for (int j = 0; j < NGL; ++j) {
+      const int gg = gj[j];
+      {
+        const int fx = ly * (TX + 1) + lx;
+        R QL[NRV], out[NRV];
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx) * G + lane] = out[v];
-      }
-      if (lx == TX - 1) {
-        R QR[NRV];
+        for (int v = 0; v < NRV; ++v) QL[v] = rbx[(v * NFX + fx) * G + gg];
+        rad_face(0, QL, ax[j], chi_of(s0, sc_own - 1, j), chi_of(s0, sc_own, j), ellx, vsx, out);
+        if (hasj[j]) {
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) QR[v] = rax[(v * TY + ly) * G + gsel];
-        rad_face(0, bx, QR, chi_of(s0, sc_own), chi_of(s0, sc_own + 1), tx(T_ELL, ipx + 1), vsx1, out);
-        if (has) {
+          for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx) * G + gg] = out[v];
+        }
+        if (lx == TX - 1) {
+          R QR[NRV];
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx + 1) * G + lane] = out[v];
+          for (int v = 0; v < NRV; ++v) QR[v] = rax[(v * TY + ly) * G + gg];
+          rad_face(0, bx[j], QR, chi_of(s0, sc_own, j), chi_of(s0, sc_own + 1, j), tx(T_ELL, ipx + 1), vsx1, out);
+          if (hasj[j]) {
+#pragma unroll
+            for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx + 1) * G + gg] = out[v];
+          }
         }
       }
-    }
-    if (D == 3) {
-      const int fy = ly * TX + lx;
-      R QL[NRV], out[NRV];
+      if (D == 3) {
+        const int fy = ly * TX + lx;
+        R QL[NRV], out[NRV];
 #pragma unroll
-      for (int v = 0; v < NRV; ++v) QL[v] = rby[(v * NFY + fy) * G + gsel];
-      rad_face(1, QL, ay, chi_of(s0, sc_own - PX), chi_of(s0, sc_own), ty(T_ELL, bc_pad(gy)), vsy, out);
-      if (has) {
+        for (int v = 0; v < NRV; ++v) QL[v] = rby[(v * NFY + fy) * G + gg];
+        rad_face(1, QL, ay[j], chi_of(s0, sc_own - PX, j), chi_of(s0, sc_own, j), ty(T_ELL, bc_pad(gy)), vsy, out);
+        if (hasj[j]) {
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy) * G + lane] = out[v];
-      }
-      if (ly == TY - 1) {
-        R QR[NRV];
+          for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy) * G + gg] = out[v];
+        }
+        if (ly == TY - 1) {
+          R QR[NRV];
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) QR[v] = ray[(v * TX + lx) * G + gsel];
-        rad_face(1, by, QR, chi_of(s0, sc_own), chi_of(s0, sc_own + PX), ty(T_ELL, bc_pad(gy + 1)), vsy1, out);
-        if (has) {
+          for (int v = 0; v < NRV; ++v) QR[v] = ray[(v * TX + lx) * G + gg];
+          rad_face(1, by[j], QR, chi_of(s0, sc_own, j), chi_of(s0, sc_own + PX, j), ty(T_ELL, bc_pad(gy + 1)), vsy1, out);
+          if (hasj[j]) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy + TX) * G + lane] = out[v];
+            for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy + TX) * G + gg] = out[v];
+          }
         }
       }
+      if (D >= 2)
+        rad_face(MD, bm0[j], am1[j], chi_of(s0, sc_own, j), chi_of((k + 1) & 3, sc_own, j), ell_m, vsm, rfm_new[j]);
     }
-    if (D >= 2)
-      rad_face(MD, bm0, am1, chi_of(s0, sc_own), chi_of((k + 1) & 3, sc_own),
-               sph ? tm(T_ELL, bc_pad(k + 1)) * tx(T_XH, ipx) : tm(T_ELL, bc_pad(k + 1)), vsm, rfm_new);
     __syncthreads();
     // prefetch: own values of plane k+3 and the stage-2 base of plane k+1
-    R b1[NRV] = {}, bg1 = R(0);
+    R b1[NGL][NRV] = {}, bg1 = R(0);
     if (D >= 2 && k + 1 < kend) {
       own_rad(k + 3, Qn);
       gn = own_gas(k + 3);
       if (A.base != nullptr && cell_in) {
         const uint32_t c1 = D == 2 ? (uint32_t)(k + 1) * nx + gx : ((uint32_t)(k + 1) * ny + gy) * nx + gx;
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) b1[v] = A.base[NG * ncell + (v * ncell + c1) * G + gsel];
+        for (int v = 0; v < NRV; ++v)
+#pragma unroll
+          for (int j = 0; j < NGL; ++j) b1[j][v] = A.base[NG * ncell + (v * ncell + c1) * G + gj[j]];
         bg1 = A.base[gvar * ncell + c1];
       }
     }
@@ -1159,7 +1414,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       const R dt = KR.dt;
       const bool stage2 = A.base != nullptr;
       // geometric sources <Gamma^l_jk> T^k_l of the stage's input state (Eq. 9; Appendix D)
-      R hq[3] = {R(1), R(1), R(1)}, gsrc = R(0), rsrc[NRV] = {};
+      R hq[3] = {R(1), R(1), R(1)}, gsrc = R(0), rsrc[NGL][NRV] = {};
       if (sph) {
         const int ipm = bc_pad(k);
         hq[0] = hfac(0, gx, k);
@@ -1168,7 +1423,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         const R g222 = tm(T_GA, ipm), g332 = tm(T_GB, ipm);
         R gc[NG];
 #pragma unroll
-        for (int v = 0; v < NG; ++v) gc[v] = __shfl_sync(0xffffffffu, g0, v, GP);
+        for (int v = 0; v < NG; ++v) gc[v] = __shfl_sync(0xffffffffu, g0, v, GL);
         const R rho = gc[0], irho = frcp(rho);
         const R v1 = gc[1] * irho * frcp(hq[0]), v2 = gc[2] * irho * frcp(hq[1]);
         const R p = KR.gm1 * (gc[NG - 1] - R(0.5) * rho * (v1 * v1 + v2 * v2));
@@ -1176,13 +1431,16 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         if (gvar == 1) gsrc = g111 * (rho * v1 * v1 + p) + g221 * (rho * v2 * v2 + p) + g221 * p;
         if (gvar == 2)
           gsrc = g122 * (rho * v1 * v2 * r12) + g221 * (rho * v1 * v2 * r21) + g222 * (rho * v2 * v2 + p) + g332 * p;
-        R Pd[3], P01;
-        m1_full<R, D>(KR.c, Q0[0], Q0 + 1, Pd, P01);
         const R c2 = KR.c * KR.c;
-        const R R11 = c2 * Pd[0] + v1 * Q0[1], R22 = c2 * Pd[1] + v2 * Q0[2], R33 = c2 * Pd[2];
-        const R R21 = (c2 * P01 + v2 * Q0[1]) * r12, R12 = (c2 * P01 + v1 * Q0[2]) * r21;
-        rsrc[1] = g111 * R11 + g221 * R22 + g221 * R33;
-        rsrc[2] = g122 * R21 + g221 * R12 + g222 * R22 + g332 * R33;
+#pragma unroll
+        for (int j = 0; j < NGL; ++j) {
+          R Pd[3], P01;
+          m1_full<R, D>(KR.c, Q0[j][0], Q0[j] + 1, Pd, P01);
+          const R R11 = c2 * Pd[0] + v1 * Q0[j][1], R22 = c2 * Pd[1] + v2 * Q0[j][2], R33 = c2 * Pd[2];
+          const R R21 = (c2 * P01 + v2 * Q0[j][1]) * r12, R12 = (c2 * P01 + v1 * Q0[j][2]) * r21;
+          rsrc[j][1] = g111 * R11 + g221 * R22 + g221 * R33;
+          rsrc[j][2] = g122 * R21 + g221 * R12 + g222 * R22 + g332 * R33;
+        }
       }
       // gas: lane v < NG updates variable v, then the segment shares the cell's gas state
       R ug = g0 + dt * (gsrc - gnet);
@@ -1193,33 +1451,45 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       using CT = typename std::conditional<coop, R, NT>::type;
       CT gas[NG];
 #pragma unroll
-      for (int v = 0; v < NG; ++v) gas[v] = (CT)__shfl_sync(0xffffffffu, ug, v, GP);
-      CT E = CT(0), F[3] = {CT(0), CT(0), CT(0)};
-      if (has && cell_in) {
+      for (int v = 0; v < NG; ++v) gas[v] = (CT)__shfl_sync(0xffffffffu, ug, v, GL);
+      CT E[NGL], F[NGL][3];
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) {
-          const int c = v <= 2 ? v : 0;
-          R net = rfx[(v * NFX + fxa + 1) * G + lane] * fx_r[c] - rfx[(v * NFX + fxa) * G + lane] * fx_l[c];
-          if (D == 3) net = net + (rfy[(v * NFY + fya + TX) * G + lane] * fyr - rfy[(v * NFY + fya) * G + lane] * fyl);
-          if (D >= 2) net = net + (rfm_new[v] * fm_r[c] - rfm_old[v] * fm_l[c]);
-          const R cov = (sph && v >= 1) ? Q0[v] * hq[v - 1] : Q0[v];  // covariant F
-          R u1 = cov + dt * (rsrc[v] - net);
-          if (stage2) u1 = KR.alpha * b0[v] + KR.beta * u1;
-          if (v == 0) E = (CT)u1; else F[v - 1] = (CT)u1;
+      for (int j = 0; j < NGL; ++j) {
+        E[j] = CT(0);
+        F[j][0] = F[j][1] = F[j][2] = CT(0);
+        if (hasj[j] && cell_in) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) {
+            const int c = v <= 2 ? v : 0;
+            const int gg = gj[j];
+            R net = rfx[(v * NFX + fxa + 1) * G + gg] * fx_r[c] - rfx[(v * NFX + fxa) * G + gg] * fx_l[c];
+            if (D == 3) net = net + (rfy[(v * NFY + fya + TX) * G + gg] * fyr - rfy[(v * NFY + fya) * G + gg] * fyl);
+            if (D >= 2) net = net + (rfm_new[j][v] * fm_r[c] - rfm_old[j][v] * fm_l[c]);
+            const R cov = (sph && v >= 1) ? Q0[j][v] * hq[v - 1] : Q0[j][v];  // covariant F
+            R u1 = cov + dt * (rsrc[j][v] - net);
+            if (stage2) u1 = KR.alpha * b0[j][v] + KR.beta * u1;
+            if (v == 0) E[j] = (CT)u1; else F[j][v - 1] = (CT)u1;
+          }
         }
       }
       // recording for the adjoint: the pre-interaction state
       if (A.pre_out != nullptr && cell_in) {
         if (lane < NG) A.pre_out[lane * ncell + cidx] = ug;
-        if (has) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) A.pre_out[NG * ncell + (v * ncell + cidx) * G + lane] = R(v == 0 ? E : F[v - 1]);
+        for (int j = 0; j < NGL; ++j) {
+          if (hasj[j]) {
+#pragma unroll
+            for (int v = 0; v < NRV; ++v)
+              A.pre_out[NG * ncell + (v * ncell + cidx) * G + gj[j]] = R(v == 0 ? E[j] : F[j][v - 1]);
+          }
         }
       }
       // objective: energy flux through the upper x boundary face of the row, times its area
-      if (A.phi_out != nullptr && cell_in && has && gx == nx - 1) {
+      if (A.phi_out != nullptr && cell_in && gx == nx - 1) {
         const uint32_t row = D == 1 ? 0u : D == 2 ? (uint32_t)k : (uint32_t)k * ny + gy;
-        A.phi_out[row * G + lane] = rfx[(0 * NFX + fxa + 1) * G + lane] * A.phi_area;
+#pragma unroll
+        for (int j = 0; j < NGL; ++j)
+          if (hasj[j]) A.phi_out[row * G + gj[j]] = rfx[(0 * NFX + fxa + 1) * G + gj[j]] * A.phi_area;
       }
       unsigned stbits = 0;
       CT Tst = CT(0);
@@ -1229,12 +1499,14 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         CT m[3] = {gas[1], D > 1 ? gas[2] : CT(0), D > 2 ? gas[3] : CT(0)};
         CT rho = gas[0], rhoe = gas[NG - 1];
         if constexpr (coop) {
-          stbits = couple_block<D, GP, TX * TY>(g, *sgc, A.pk, A.ptab, A.kd, A.kf, A.nsm, cell_in, lane, tcell,
-                                                sph ? h : nullptr, rho, m, rhoe, E, F, &Tst);
+          stbits = couple_block<D, GP, NGL, TX * TY>(g, *sgc, A.pk, A.ptab, A.kd, A.kf, A.nsm, cell_in, lane,
+                                                     tcell, sph ? h : nullptr, rho, m, rhoe, E, F, &Tst);
+        } else if constexpr (NGL == 2) {
+          stbits = couple_cell_n<D, GL, NGL>(g, *sgc, A.pk, A.ptab, A.kf, cell_in, lane, sph ? h : nullptr,
+                                             rho, m, rhoe, E, F, &Tst);
         } else {
           stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.ptab, A.k(NT(0)), A.k(LT(0)), cell_in, lane,
-                                              sph ? h : nullptr,
-                                              rho, m, rhoe, E, F, &Tst);
+                                              sph ? h : nullptr, rho, m, rhoe, E[0], F[0], &Tst);
         }
         gas[0] = rho;
 #pragma unroll
@@ -1251,12 +1523,15 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           A.out[lane * ncell + cidx] = R(val);
           chk += val;
         }
-        if (has) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) {
-            CT val = v == 0 ? E : F[v - 1];
-            A.out[NG * ncell + (v * ncell + cidx) * G + lane] = R(val);
-            chk += val * CT(0);
+        for (int j = 0; j < NGL; ++j) {
+          if (hasj[j]) {
+#pragma unroll
+            for (int v = 0; v < NRV; ++v) {
+              CT val = v == 0 ? E[j] : F[j][v - 1];
+              A.out[NG * ncell + (v * ncell + cidx) * G + gj[j]] = R(val);
+              chk += val * CT(0);
+            }
           }
         }
         if (!isfinite(chk)) stbits |= ST_NONFINITE;
@@ -1265,12 +1540,15 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     }
     // slide the march window
 #pragma unroll
-    for (int v = 0; v < NRV; ++v) {
-      Q0[v] = Q1[v];
-      Q1[v] = Q2[v];
-      bm0[v] = bm1[v];
-      rfm_old[v] = (D >= 2) ? rfm_new[v] : R(0);
-      b0[v] = b1[v];
+    for (int j = 0; j < NGL; ++j) {
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) {
+        Q0[j][v] = Q1[j][v];
+        Q1[j][v] = Q2[j][v];
+        bm0[j][v] = bm1[j][v];
+        rfm_old[j][v] = (D >= 2) ? rfm_new[j][v] : R(0);
+        b0[j][v] = b1[j][v];
+      }
     }
     g0 = g1;
     g1 = g2;
