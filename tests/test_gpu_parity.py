@@ -124,7 +124,18 @@ def test_fp32_form_small(fxmod, maker, tol, form):
     H.assert_parity(pb, got, ref, tol, natural=True)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32", 1e-4)])
+@pytest.mark.parametrize("form", ["fp32", "fp32n64"])
+@pytest.mark.parametrize("G", [9, 13])
+def test_fp32_forms_odd_group_counts(fxmod, form, G):
+    # two groups per lane with an odd group count: the last lane of each cell owns one group
+    pb, prim = W.kh_2d(nx=44, ny=38, ngroups=G, nsteps=3, precision=form)
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, 1e-4, natural=True)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32", 1e-4), ("fp32n64", 1e-4)])
 def test_kh2d_full_size_sampled_windows(fxmod, precision, tol):
     # 1024^2 x 16 groups, one step in the benchmark's launch configuration; windows of 8x8 cells
     # (+4 halo: the two-stage dependency radius) recomputed by the oracle
@@ -179,7 +190,7 @@ def test_newton_failure_is_reported(fxmod):
     assert st == 0
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32", 1e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32", 1e-5), ("fp32n64", 1e-5)])
 def test_spherical_2d_small(fxmod, precision, tol):
     # log-r x theta grid with reflecting inner radius, outflow outer radius, polar-axis parity;
     # coordinate moments, curvilinear face factors and geometric sources all active
