@@ -35,7 +35,7 @@ UNIT = "zone-group-stages/s"
 # DRAM bytes per radiation/update kernel launch (mean of the two RK stages) from the committed
 # ncu capture profiles/traffic_stage_kernel_kh2d_1024x1024x16.txt; None where not captured for
 # the current kernels.
-TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": None, "fp32": None, "fp64": 1353.5e6}}
+TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": 575.4e6, "fp32": 572.3e6, "fp64": 1353.2e6}}
 
 
 def load_peaks():
