@@ -35,7 +35,7 @@ UNIT = "zone-group-stages/s"
 # DRAM bytes per radiation/update kernel launch (mean of the two RK stages) from the committed
 # ncu capture profiles/traffic_stage_kernel_kh2d_1024x1024x16.txt; None where not captured for
 # the current kernels.
-TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": 575.4e6, "fp32": 572.3e6, "fp64": 1353.2e6}}
+TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": None, "fp32": None, "fp64": None}}
 
 
 def load_peaks():
@@ -400,12 +400,23 @@ def main():
         avg_s = kt["stage_ms"] / max(kt["stage_launches"], 1) / 1e3
         achieved = per_launch / avg_s / 1e9
         trafficd = TRAFFIC_PER_LAUNCH.get(args.workload, {})
-        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": trafficd.get(kind),
-                "peak_kind": peak_kind, "kernel": "stage_kernel (radiation/update)",
-                "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3,
-                "face_kernel_avg_ms": kt["face_ms"] / max(kt["face_launches"], 1),
-                "stage_share_of_step": kt["stage_ms"] / max(kt["stage_ms"] + kt["face_ms"], 1e-30)}
+        total = max(kt["stage_ms"] + kt["face_ms"] + kt["couple_ms"], 1e-30)
+        out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+               "frac": achieved / peak, "traffic": trafficd.get(kind),
+               "peak_kind": peak_kind, "kernel": "stage_kernel (radiation/update)",
+               "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3,
+               "face_kernel_avg_ms": kt["face_ms"] / max(kt["face_launches"], 1),
+               "stage_share_of_step": kt["stage_ms"] / total}
+        if kt["couple_launches"]:
+            # the interaction kernel of the FP32 form with the FP64 Newton reads and writes the
+            # state once per stage
+            cb = 2.0 * b * nv * pbh.ncell
+            cs = kt["couple_ms"] / kt["couple_launches"] / 1e3
+            out["interaction_kernel"] = {
+                "kernel": "couple_kernel (interaction, one thread per cell)",
+                "bytes_per_launch": cb, "avg_launch_ms": cs * 1e3, "achieved": cb / cs / 1e9,
+                "frac": cb / cs / 1e9 / peak, "share_of_step": kt["couple_ms"] / total}
+        return out
 
     e2e_steps = max(5, args.steps // 4)
     if args.no_e2e:

@@ -145,21 +145,25 @@ fx_status fx_conserved_totals(fx_grid* h, double out[FX_NTOTALS]);
 fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is_device);
 
 /* Number of kernel launches enqueued by one fx_step(dt, 1) call (per RK stage: the gas face
- * kernel and the radiation/update kernel, plus the objective's reduction while it is enabled). */
+ * kernel and the radiation/update kernel; in FX_FP32_F64NEWTON with the interaction on, the
+ * interaction kernel; and the objective's reduction while it is enabled). */
 int fx_launches_per_step(const fx_grid* h);
 
 /* Per-kernel device timing (instrumentation, not part of the method).  While enabled, every
- * stage that fx_step enqueues records three CUDA events on the bound stream: before the gas face
- * kernel, between it and the radiation/update kernel, and after the latter.
+ * stage that fx_step enqueues records four CUDA events on the bound stream: before the gas face
+ * kernel, after it, after the radiation/update kernel, and after the interaction kernel (which
+ * runs as a kernel of its own in FX_FP32_F64NEWTON; elsewhere the last two events coincide).
  * fx_kernel_timing_enable(h, on) switches this on or off and discards what was recorded.
  * fx_kernel_timing_read(h, out) waits for the last recorded event and writes
  * out[0] = total milliseconds of the radiation/update kernel, out[1] = its launches,
- * out[2] = total milliseconds of the gas face kernel, out[3] = its launches, summed over the
- * stages recorded since enable or the previous read; it then starts a new record.  Each duration
- * includes the launch gap between the bracketing events (~1 us).  Both return FX_ERR_ARG for a
- * null handle or output and FX_ERR_CUDA when an event call fails. */
+ * out[2] = total milliseconds of the gas face kernel, out[3] = its launches,
+ * out[4] = total milliseconds of the interaction kernel, out[5] = its launches (0 when the
+ * interaction runs inside the radiation/update kernel), summed over the stages recorded since
+ * enable or the previous read; it then starts a new record.  Each duration includes the launch
+ * gap between the bracketing events (~1 us).  Both return FX_ERR_ARG for a null handle or output
+ * and FX_ERR_CUDA when an event call fails. */
 fx_status fx_kernel_timing_enable(fx_grid* h, int on);
-fx_status fx_kernel_timing_read(fx_grid* h, double out[4]);
+fx_status fx_kernel_timing_read(fx_grid* h, double out[6]);
 
 /* Host-side inspection (no GPU needed): the FP64 reconstruction/divergence table of direction d,
  * fx_debug_ntab() entries of n[d] + 4 rows each (padded cells -2 .. n+1), entry-major.  Returns

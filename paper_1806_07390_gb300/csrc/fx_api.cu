@@ -132,7 +132,6 @@ struct fx_grid {
   size_t nev = 0;
   // objective (boundary radiation energy outflow, reading R19): per-row face fluxes of one stage
   // [rows][G] and FP64 accumulators obj[0] = J, obj[1] = dJ/dkappa0 (adjoint)
-  int nsm = 0;  // multiprocessors of the bound device
   bool objective = false;
   size_t off_phi = 0, off_obj = 0;
   int64_t phi_rows = 0;
@@ -582,7 +581,6 @@ StageArgs<R> stage_args(fx_grid* h) {
   a.status = reinterpret_cast<unsigned*>(h->ws + h->off_status);
   a.chunk = h->chunk;
   a.phi_area = (R)h->phi_area;
-  a.nsm = h->nsm;
   return a;
 }
 
@@ -609,26 +607,26 @@ void set_stage(fx_grid* h, StageArgs<R>& a, int stage, double dt) {
 // objective's reduction when a.phi_out is set.
 template <class R, class NT>
 fx_status launch_one_stage(fx_grid* h, const StageArgs<R>& a, const char* what) {
-  cudaEvent_t e3[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t e4[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaError_t e = cudaSuccess;
   if (h->timing) {
-    while (h->ev.size() < h->nev + 3) {
+    while (h->ev.size() < h->nev + 4) {
       cudaEvent_t x;
       e = cudaEventCreate(&x);
       if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
       h->ev.push_back(x);
     }
-    for (int q = 0; q < 3; ++q) e3[q] = h->ev[h->nev + q];
-    h->nev += 3;
-    e = cudaEventRecord(e3[0], h->stream);
+    for (int q = 0; q < 4; ++q) e4[q] = h->ev[h->nev + q];
+    h->nev += 4;
+    e = cudaEventRecord(e4[0], h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
   }
   switch (h->D) {
-    case 1: e = launch_stage<R, 1, NT>(a, h->GP, h->stream, e3[1]); break;
-    case 2: e = launch_stage<R, 2, NT>(a, h->GP, h->stream, e3[1]); break;
-    default: e = launch_stage<R, 3, NT>(a, h->GP, h->stream, e3[1]); break;
+    case 1: e = launch_stage<R, 1, NT>(a, h->GP, h->stream, e4[1], e4[2]); break;
+    case 2: e = launch_stage<R, 2, NT>(a, h->GP, h->stream, e4[1], e4[2]); break;
+    default: e = launch_stage<R, 3, NT>(a, h->GP, h->stream, e4[1], e4[2]); break;
   }
-  if (e == cudaSuccess && e3[2]) e = cudaEventRecord(e3[2], h->stream);
+  if (e == cudaSuccess && e4[3]) e = cudaEventRecord(e4[3], h->stream);
   if (e == cudaSuccess && a.phi_out) {
     // J += dt/2 Phi(U_in): this stage's share of the RK-weighted boundary outflow
     k_sum_into<R><<<1, 1024, 0, h->stream>>>(a.phi_out, h->phi_rows * h->G, 0.5 * a.dt,
@@ -999,7 +997,11 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
 
 size_t fx_state_elems(const fx_grid* h) { return h ? (size_t)h->ncell * h->NV : 0; }
 
-int fx_launches_per_step(const fx_grid* h) { return h ? (h->objective ? 6 : 4) : 0; }
+int fx_launches_per_step(const fx_grid* h) {
+  if (!h) return 0;
+  const bool split = h->P.precision == FX_FP32_F64NEWTON && h->P.couple;
+  return 2 * (2 + (split ? 1 : 0) + (h->objective ? 1 : 0));
+}
 
 fx_status fx_objective_enable(fx_grid* h, int on) {
   if (!h) return FX_ERR_ARG;
@@ -1102,12 +1104,6 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
   h->ws = static_cast<unsigned char*>(dev_ptr);
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e;
-  {
-    int dev = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(h, e, "device query");
-  }
   if (!h->h_status) {
     e = cudaMallocHost(&h->h_status, sizeof(unsigned));
     if (e != cudaSuccess) return cuda_fail(h, e, "pinned status word");
@@ -1309,21 +1305,27 @@ fx_status fx_kernel_timing_enable(fx_grid* h, int on) {
   return FX_OK;
 }
 
-fx_status fx_kernel_timing_read(fx_grid* h, double out[4]) {
+fx_status fx_kernel_timing_read(fx_grid* h, double out[6]) {
   if (!h || !out) return FX_ERR_ARG;
-  for (int q = 0; q < 4; ++q) out[q] = 0.0;
+  for (int q = 0; q < 6; ++q) out[q] = 0.0;
   if (h->nev == 0) return FX_OK;
   cudaError_t e = cudaEventSynchronize(h->ev[h->nev - 1]);
   if (e != cudaSuccess) return cuda_fail(h, e, "timing read");
-  for (size_t i = 0; i < h->nev; i += 3) {
-    float face = 0.f, stage = 0.f;
+  const bool split = h->P.precision == FX_FP32_F64NEWTON && h->P.couple;
+  for (size_t i = 0; i < h->nev; i += 4) {
+    float face = 0.f, stage = 0.f, inter = 0.f;
     e = cudaEventElapsedTime(&face, h->ev[i], h->ev[i + 1]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&stage, h->ev[i + 1], h->ev[i + 2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&inter, h->ev[i + 2], h->ev[i + 3]);
     if (e != cudaSuccess) return cuda_fail(h, e, "timing read");
     out[0] += stage;
     out[1] += 1.0;
     out[2] += face;
     out[3] += 1.0;
+    if (split) {
+      out[4] += inter;
+      out[5] += 1.0;
+    }
   }
   h->nev = 0;
   return FX_OK;

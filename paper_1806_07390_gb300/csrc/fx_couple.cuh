@@ -1,0 +1,373 @@
+// Cell-local implicit matter-radiation interaction of the FP32 state as a kernel of its own, one
+// thread per cell (Sec. 5.3: the backward-Euler group update of Eq. 25 inside the Newton iteration
+// on T of Eqs. 26-27, the gas energy by conservation, then the flux absorption of Eq. 28 and its
+// momentum and energy feedback, Eqs. 31-32; readings R10-R12).
+//
+// Inside the stage kernel a cell's groups are spread over the lanes of a segment, so the scalar
+// part of the interaction (the iteration on T, its stopping tests, the gas update) is repeated by
+// every lane or confined to one warp that the others wait for at block barriers.  GB300 executes
+// two FP64 lane-operations per cycle per multiprocessor, so an FP64 warp instruction costs the same
+// with one active lane as with 32.  Here a thread owns a cell: each FP64 instruction serves 32
+// cells, the group loop runs in FP32 with the temperature-dependent parts of the Planck table
+// interpolation and of the opacity computed once per evaluation, and no warp waits at a barrier.
+// The stage kernel leaves the state after the explicit update and RK combination in its output;
+// this kernel updates that state in place.
+//
+// NT is the type of the iterate T, the residual and the gas update: double for the FP32 form with
+// the FP64 Newton, float for the all-FP32 form.  Group arithmetic is FP32 in both.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fx_stage.cuh"
+
+namespace fx {
+
+constexpr int CPL_THREADS = 128;  // cells (threads) per block of couple_kernel
+
+// Dynamic shared memory of couple_kernel: the block's rows of E and F_q, G + 1 floats per row
+// (the pad spreads the threads' row reads over all banks).
+template <int D> inline size_t couple_smem_bytes(int G) {
+  return (size_t)(1 + D) * CPL_THREADS * (size_t)(G + 1) * sizeof(float);
+}
+
+// Temperature-dependent part of one evaluation of the group energies: the position in the FP32
+// Planck band tables (shared by all groups: the tables have common nodes in log2 T), the cubic
+// Hermite weights there, and the powers of T.
+struct PlanckAt {
+  int mode;          // 0: every band in the Wien tail (B = 0); 1: table; 2: hot-limit series
+  int i;             // left node (mode 1)
+  float w0, w1, w2, w3;  // Hermite weights of L_i, h L'_i, L_{i+1}, h L'_{i+1}
+  float v0, v1, v2;      // weights of the derivative dL/dt: (L_i - L_{i+1}), h L'_i, h L'_{i+1}
+  float invT, aT3, aT4;  // 1/T, a_N T^3, a_N T^4
+};
+
+__device__ __forceinline__ PlanckAt planck_at(const PlanckTable& ptab, float aN, float T) {
+  PlanckAt p;
+  p.invT = frcp(T);
+  const float T3 = T * T * T;
+  p.aT3 = aN * T3;
+  p.aT4 = p.aT3 * T;
+  const float s = (__log2f(T) - ptab.u0) * float(PTAB_PER_OCT);
+  p.mode = s < 0.0f ? 0 : (s >= float(ptab.nu - 1) ? 2 : 1);
+  p.i = p.mode == 1 ? (int)s : 0;
+  const float t = p.mode == 1 ? s - (float)p.i : 0.0f;
+  const float t2 = t * t, t3 = t2 * t;
+  p.w0 = 2.0f * t3 - 3.0f * t2 + 1.0f;
+  p.w1 = t3 - 2.0f * t2 + t;
+  p.w2 = 3.0f * t2 - 2.0f * t3;
+  p.w3 = t3 - t2;
+  p.v0 = 6.0f * t2 - 6.0f * t;
+  p.v1 = 3.0f * t2 - 4.0f * t + 1.0f;
+  p.v2 = 3.0f * t2 - 2.0f * t;
+  return p;
+}
+
+// B_g(T) and dB_g/dT of group g (band edges elo, ehi) at the evaluation point p.
+__device__ __forceinline__ void planck_group(const PlanckTable& ptab, const PlanckAt& p, int g,
+                                             float elo, float ehi, float& B, float& dB) {
+  float I, dLdu;
+  if (p.mode == 1) {
+    const float4 p0 = __ldg(ptab.tab + g * ptab.nu + p.i);
+    const float4 p1 = __ldg(ptab.tab + g * ptab.nu + p.i + 1);
+    // node values relative to floor(L) of the left node (small numbers, full FP32 precision)
+    const float d1 = (p1.z - p0.z) + p1.x;
+    const float Lr = p.w0 * p0.x + p.w1 * p0.y + p.w2 * d1 + p.w3 * p1.y;
+    const float dLdt = p.v0 * (p0.x - d1) + p.v1 * p0.y + p.v2 * p1.y;
+    I = ldexpf(exp2f(Lr), (int)p0.z);
+    dLdu = dLdt * float(PTAB_PER_OCT);
+  } else if (p.mode == 0) {
+    I = 0.0f;  // deep in the Wien tail
+    dLdu = 0.0f;
+  } else {
+    // very hot: x = eps/T < 2^-14 at both edges, Int t^3/(e^t-1) = x^3/3 - x^4/8 + O(x^5)
+    const float a = elo * p.invT, b = ehi * p.invT;
+    const float a3 = a * a * a, b3 = b * b * b;
+    I = (b3 - a3) * (1.0f / 3.0f) - (b3 * b - a3 * a) * 0.125f;
+    dLdu = ((a3 * a * (1.0f - 0.5f * a)) - (b3 * b * (1.0f - 0.5f * b))) * frcp(I);
+  }
+  B = p.aT4 * I;
+  dB = p.aT3 * I * (4.0f + dLdu);  // d/dT (T^4 I) = T^3 I (4 + d ln I / d ln T)
+}
+
+template <int D, class NT>
+__global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A) {
+  using LT = float;
+  constexpr int NG = 2 + D, NRV = 1 + D;
+  const DevGrid& g = A.g;
+  const int G = g.G;
+  const uint32_t ncell = (uint32_t)g.ncell;
+  const Consts<NT>& kn = A.k(NT(0));
+  const Consts<float>& kl = A.kf;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* const srow = reinterpret_cast<float*>(smem_raw);  // [NRV][CPL_THREADS][G + 1]
+  __shared__ float s_ef[MAXG], s_ed[MAXG + 1];
+  const int RS = G + 1;
+  const int t = threadIdx.x;
+  const uint32_t c0 = blockIdx.x * (uint32_t)CPL_THREADS;
+  const int nc = (int)min((uint32_t)CPL_THREADS, ncell - c0);
+  const bool act = t < nc;
+  const uint32_t cid = c0 + (uint32_t)t;
+
+  for (int j = t; j <= G; j += CPL_THREADS) {
+    if (j < G) s_ef[j] = A.gc->efac32[j];
+    s_ed[j] = A.gc->edge32[j];
+  }
+  // the block's radiation rows: coalesced reads of the contiguous range [c0 G, (c0 + nc) G) of
+  // each moment, scattered into per-cell rows
+  {
+    const int tot = nc * G;
+    const int q0 = CPL_THREADS / G, r0 = CPL_THREADS - q0 * G;
+    for (int v = 0; v < NRV; ++v) {
+      const float* src = A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G;
+      float* dst = srow + v * CPL_THREADS * RS;
+      int row = t / G, gg = t - row * G;
+      for (int e = t; e < tot; e += CPL_THREADS) {
+        dst[row * RS + gg] = src[e];
+        row += q0;
+        gg += r0;
+        if (gg >= G) { gg -= G; ++row; }
+      }
+    }
+  }
+  float rho_f = 1.0f, m_f[3] = {0.0f, 0.0f, 0.0f}, rhoe_f = 1.0f;
+  if (act) {
+    rho_f = A.out[cid];
+#pragma unroll
+    for (int q = 0; q < D; ++q) m_f[q] = A.out[(1 + q) * ncell + cid];
+    rhoe_f = A.out[(NG - 1) * ncell + cid];
+  }
+  // covariant components: physical = m_q / h_q on the spherical (r, theta) grid
+  const bool sph = (D == 2) && g.geom != 0;
+  NT h[2] = {NT(1), NT(1)};
+  if (sph && act) {
+    const int nx = g.n[0], ny = g.n[1];
+    const int gx = (int)(cid % (uint32_t)nx), gy = (int)(cid / (uint32_t)nx);
+    const Tab<float> tx{A.tab[0], nx + 4, A.uniform[0] ? A.urow[0] : nullptr};
+    const Tab<float> ty{A.tab[1], ny + 4, A.uniform[1] ? A.urow[1] : nullptr};
+    h[0] = (NT)(tx(T_HA, bc_pad(gx)) * ty(T_HA, bc_pad(gy)));
+    h[1] = (NT)(tx(T_HB, bc_pad(gx)) * ty(T_HB, bc_pad(gy)));
+  }
+  __syncthreads();
+
+  float* const rE = srow + t * RS;
+  unsigned st = 0;
+  if (act && g.couple) {
+    // ---- floors, T^- = u^-/(rho c_v), the opacity factors of the (floored) density
+    NT rr = (NT)rho_f;
+    if (rr < kn.rho_floor) { rr = kn.rho_floor; st |= ST_FLOOR; }
+    const NT ir = NT(1) / rr;
+    NT ke = NT(0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      const NT mh = sph ? (NT)m_f[q] / h[q] : (NT)m_f[q];
+      ke += NT(0.5) * mh * mh * ir;
+    }
+    NT um = (NT)rhoe_f - ke;
+    if (um < kn.u_floor) { um = kn.u_floor; st |= ST_FLOOR; }
+    const NT rcv = rr * kn.cv;
+    const NT Tm = um * ir * kn.gm1;  // c_v = 1/(gamma - 1)
+    const LT Kc = (LT)(kn.kappa0 * hpow(rr, g.kap_rho_h)), Sc = (LT)(kn.sigma0 * rr);
+    // E^- with its silent positivity floor (Wien tails), and its group sum
+    LT Esum = LT(0);
+    for (int j = 0; j < G; ++j) {
+      LT e = rE[j];
+      if (e < kl.E_floor) { e = kl.E_floor; rE[j] = e; }
+      Esum += e;
+    }
+    const NT scale = um + (NT)Esum;
+    const LT hh = LT(0.5) * (LT)g.kap_T_h;
+    // one evaluation at T: the group sums of E_g(T) - E_g^- (Eq. 25) and of dE_g/dT
+    auto eval = [&](LT Tl, LT& sa, LT& sb) {
+      const PlanckAt p = planck_at(A.ptab, kl.aN, Tl);
+      const LT kT = Kc * hpow(Tl, g.kap_T_h);
+      LT a = LT(0), b = LT(0);
+      for (int j = 0; j < G; ++j) {
+        LT Bq, dBq;
+        planck_group(A.ptab, p, j, s_ed[j], s_ed[j + 1], Bq, dBq);
+        const LT Em = rE[j];
+        const LT tau = kl.cdts * (kT * s_ef[j]);
+        const LT dtau = tau * hh * p.invT;
+        const LT inv = frcp(LT(1) + tau);
+        const LT Eg = (Em + tau * Bq) * inv;
+        const LT dEg = (tau * dBq + dtau * (Bq - Eg)) * inv;
+        a += Eg - Em;
+        b += dEg;
+      }
+      sa = a;
+      sb = b;
+    };
+    // 1/dr: for FP64, an FP32 seed refined by one Newton-Raphson step (relative error ~1e-14, far
+    // below the step tolerance), shorter in latency than an FP64 division
+    auto recip = [](NT x) -> NT {
+      NT y = (NT)(1.0f / (float)x);
+      if (sizeof(NT) == 8) y = fma(y, fma(-x, y, NT(1)), y);
+      return y;
+    };
+
+    // ---- Newton with backtracking (Eqs. 26-27; reading R11)
+    NT dl = NT(0), dacc = NT(0), r, dr, dT = NT(0), lam = NT(1);
+    LT lin = LT(0);  // linearised step added to the accepted group energies at convergence
+    int it = 0, ls = 0;
+    bool ok = false, done = false, need_dir = true;
+    {
+      LT a, b;
+      eval((LT)Tm, a, b);
+      r = (NT)a;
+      dr = rcv + (NT)b;
+    }
+    const int guard = g.newton_maxit * 41 + 2;
+    for (int kk = 0; kk < guard; ++kk) {
+      if (need_dir) {
+        if (it >= g.newton_maxit) { done = true; }
+        else if (fabs(r) <= kn.atol * scale) { done = true; ok = true; }
+        else {
+          dT = -r * recip(dr);
+          ++it;
+          if (fabs(dT) <= kn.rtol * (Tm + dl)) {
+            // converged: the group energies at T + dT follow from the linearisation
+            dl += dT;
+            lin = (LT)dT;
+            done = true;
+            ok = true;
+          } else { lam = NT(1); ls = 0; need_dir = false; }
+        }
+      }
+      if (done) break;
+      const NT dtt = dl + lam * dT;
+      const bool valid = (Tm + dtt) > NT(0);
+      LT a, b;
+      eval((LT)(Tm + (valid ? dtt : dl)), a, b);
+      const NT rt = rcv * dtt + (NT)a;
+      if (valid && fabs(rt) < fabs(r)) {
+        dl = dtt;
+        dacc = dtt;
+        r = rt;
+        dr = rcv + (NT)b;
+        need_dir = true;
+      } else {
+        lam *= NT(0.5);
+        if (++ls >= 40) done = true;
+      }
+    }
+    // ---- bisection fallback on a bracket around [T^-, T_rad] (reading R11), in T - T^-
+    if (!ok) {
+      const NT Tr = sqrt(sqrt((NT)Esum / (kn.aN * NT(6.4939394022668291491))));  // (sum E / a_R)^(1/4)
+      const NT Tc = Tm + dl;
+      NT lo = fmin(fmin(Tc, Tr), Tm) - Tm, hi = fmax(fmax(Tc, Tr), Tm) - Tm;
+      int phase = 0, cnt = 0;
+      bool brk = false;
+      NT Te = lo;
+      for (int kk = 0; kk < 400 + g.bisect_maxit + 4 && phase < 3; ++kk) {
+        LT a, b;
+        eval((LT)(Tm + Te), a, b);
+        const NT rq = rcv * Te + (NT)a;
+        if (phase == 0) {
+          if (rq > NT(0) && cnt < 200) { lo = NT(0.5) * (lo + Tm) - Tm; ++cnt; }  // T_lo /= 2
+          else { phase = 1; cnt = 0; brk = rq <= NT(0); }
+        } else if (phase == 1) {
+          if (rq < NT(0) && cnt < 200) { hi = NT(2) * (hi + Tm) - Tm; ++cnt; }  // T_hi *= 2
+          else { brk = brk && rq >= NT(0); cnt = 0; phase = brk ? (g.bisect_maxit > 0 ? 2 : 3) : 3; }
+        } else {
+          if (rq > NT(0)) hi = Te; else lo = Te;
+          ++cnt;
+          if (hi - lo <= kn.rtol * (hi + Tm)) { ok = true; phase = 3; }
+          else if (cnt >= g.bisect_maxit) phase = 3;
+        }
+        Te = phase == 0 ? lo : (phase == 1 ? hi : (phase == 2 ? NT(0.5) * (lo + hi) : Te));
+      }
+      if (brk) dl = NT(0.5) * (lo + hi);
+      dacc = dl;
+      lin = LT(0);
+    }
+    if (!ok) st |= ST_NEWTON;
+    const LT Tst = (LT)(Tm + dl);
+    if (A.tstar_out != nullptr) A.tstar_out[cid] = Tst;
+
+    // ---- the accepted group energies, and the group sum of their changes as a float pair
+    // (each change split exactly by TwoSum, the sum keeping its rounding errors)
+    float eh = 0.0f, el = 0.0f;
+    {
+      const LT Ta = (LT)(Tm + dacc);
+      const PlanckAt p = planck_at(A.ptab, kl.aN, Ta);
+      const LT kT = Kc * hpow(Ta, g.kap_T_h);
+      for (int j = 0; j < G; ++j) {
+        LT Bq, dBq;
+        planck_group(A.ptab, p, j, s_ed[j], s_ed[j + 1], Bq, dBq);
+        const LT Em = rE[j];
+        const LT tau = kl.cdts * (kT * s_ef[j]);
+        const LT dtau = tau * hh * p.invT;
+        const LT inv = frcp(LT(1) + tau);
+        LT Eg = (Em + tau * Bq) * inv;
+        if (lin != LT(0)) Eg += (tau * dBq + dtau * (Bq - Eg)) * inv * lin;
+        float d, e;
+        two_sum(Eg, -Em, d, e);
+        pair_add(eh, el, d, e);
+        rE[j] = Eg;
+      }
+    }
+    // ---- flux absorption at the converged temperature (Eq. 28) and the group sums of the flux
+    // changes
+    float fh[3] = {0.0f, 0.0f, 0.0f}, fl[3] = {0.0f, 0.0f, 0.0f};
+    {
+      const LT kT = Kc * hpow(Tst, g.kap_T_h);
+      for (int j = 0; j < G; ++j) {
+        const LT fac = frcp(LT(1) + kl.cdts * (kT * s_ef[j] + Sc));
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          float* rF = srow + ((1 + q) * CPL_THREADS + t) * RS;
+          const LT Fq = rF[j];
+          const LT Fn = Fq * fac;
+          float d, e;
+          two_sum(Fn, -Fq, d, e);
+          pair_add(fh[q], fl[q], d, e);
+          rF[j] = Fn;
+        }
+      }
+    }
+    // ---- gas energy by conservation (R12) and the momentum/energy feedback (Eqs. 31-32)
+    const NT dEsum = (NT)eh + (NT)el;
+    NT re = ke + (um - dEsum);
+    NT work = NT(0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      const NT SdF = (NT)fh[q] + (NT)fl[q];
+      const NT mq = (NT)m_f[q];
+      work += (sph ? mq / (h[q] * h[q]) : mq) * ir * SdF;
+      m_f[q] = (float)(mq - SdF * kn.ic2);
+    }
+    rhoe_f = (float)(re - work * kn.ic2);
+    rho_f = (float)rr;
+  }
+  if (act) {
+    float chk = rho_f + rhoe_f;  // a NaN or inf anywhere in the cell's outputs makes this non-finite
+    A.out[cid] = rho_f;
+#pragma unroll
+    for (int q = 0; q < D; ++q) { A.out[(1 + q) * ncell + cid] = m_f[q]; chk += m_f[q]; }
+    A.out[(NG - 1) * ncell + cid] = rhoe_f;
+    for (int v = 0; v < NRV; ++v) {
+      const float* rv = srow + (v * CPL_THREADS + t) * RS;
+      for (int j = 0; j < G; ++j) chk += rv[j] * 0.0f;
+    }
+    if (!isfinite(chk)) st |= ST_NONFINITE;
+    if (st) atomicOr(A.status, st);
+  }
+  __syncthreads();
+  // write the rows back: coalesced stores of each moment's contiguous range
+  {
+    const int tot = nc * G;
+    const int q0 = CPL_THREADS / G, r0 = CPL_THREADS - q0 * G;
+    for (int v = 0; v < NRV; ++v) {
+      float* dst = A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G;
+      const float* src = srow + v * CPL_THREADS * RS;
+      int row = t / G, gg = t - row * G;
+      for (int e = t; e < tot; e += CPL_THREADS) {
+        dst[e] = src[row * RS + gg];
+        row += q0;
+        gg += r0;
+        if (gg >= G) { gg -= G; ++row; }
+      }
+    }
+  }
+}
+
+}  // namespace fx

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "fx_couple.cuh"
 #include "fx_stage.cuh"
 
 namespace fx {
@@ -18,11 +19,19 @@ template <int D, int GL> struct TileShape {
   static constexpr int TY = TC / TX;
 };
 
-// Enqueue one stage (state type R, D dimensions, Newton/bookkeeping type NT): the gas face
-// kernel, then the radiation/update kernel, both on stream s.  When `mid` is non-null it is
-// recorded between the two launches (per-kernel timing).  Returns the CUDA error of the launch.
+// Enqueue one stage (state type R, D dimensions, Newton/bookkeeping type NT) on stream s: the gas
+// face kernel, the radiation/update kernel and, in the FP32 form with the FP64 Newton, the
+// interaction kernel (one thread per cell).  When non-null, `mid` is recorded after the face
+// kernel and `mid2` after the radiation/update kernel (per-kernel timing).  Returns the CUDA
+// error of the launches.
 template <class R, int D, class NT>
-cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid);
+cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid,
+                         cudaEvent_t mid2);
+
+// Whether the interaction runs in couple_kernel rather than inside the stage kernel.
+template <class R, class NT> constexpr bool split_interaction() {
+  return std::is_same<R, float>::value && std::is_same<NT, double>::value;
+}
 
 // Dynamic shared memory of the stage kernel (tile shape from D and GP).
 template <class R, int D, int GP>
@@ -44,7 +53,7 @@ inline size_t stage_smem(int GP, int G) {
 // Definition, included only by the per-instantiation translation units.  The group arithmetic
 // type of the stage kernel is the state type R.
 template <class R, int D, int GP, class NT>
-static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t mid) {
+static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t mid, cudaEvent_t mid2) {
   constexpr int NGL = groups_per_lane(sizeof(R) == 4, GP);
   constexpr int GL = GP / NGL;
   using TS = TileShape<D, GL>;
@@ -74,15 +83,33 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
     grid.z = (a.g.n[2] + a.chunk - 1) / a.chunk;
   }
   kern<<<grid, TS::TX * TS::TY * GL, smem, s>>>(a);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (mid2) {
+    e = cudaEventRecord(mid2, s);
+    if (e != cudaSuccess) return e;
+  }
+  if constexpr (split_interaction<R, NT>()) {
+    if (a.g.couple) {
+      auto ck = couple_kernel<D, double>;
+      const size_t cs = couple_smem_bytes<D>(a.g.G);
+      e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
+      if (e != cudaSuccess) return e;
+      const unsigned nb = (unsigned)((a.g.ncell + CPL_THREADS - 1) / CPL_THREADS);
+      ck<<<nb, CPL_THREADS, cs, s>>>(a);
+      e = cudaGetLastError();
+    }
+  }
+  return e;
 }
 
 template <class R, int D, class NT>
-cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid) {
+cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid,
+                         cudaEvent_t mid2) {
   switch (GP) {
-    case 8: return launch_gp<R, D, 8, NT>(a, s, mid);
-    case 16: return launch_gp<R, D, 16, NT>(a, s, mid);
-    case 32: return launch_gp<R, D, 32, NT>(a, s, mid);
+    case 8: return launch_gp<R, D, 8, NT>(a, s, mid, mid2);
+    case 16: return launch_gp<R, D, 16, NT>(a, s, mid, mid2);
+    case 32: return launch_gp<R, D, 32, NT>(a, s, mid, mid2);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -79,7 +79,6 @@ template <class R> struct StageArgs {
   R* tstar_out;
   R* phi_out;
   R phi_area;
-  int nsm;             // multiprocessors of the device (spreads couple_block's scalar warps)
   Consts<double> kd;
   Consts<float> kf;
   __device__ __forceinline__ const Consts<double>& k(double) const { return kd; }
@@ -115,6 +114,32 @@ template <int GP, class V> __device__ __forceinline__ V seg_sum(V v) {
   return v;
 }
 
+// Error-free float addition (Knuth's TwoSum): s = fl(a + b) and s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bv = s - a;
+  e = (a - (s - bv)) + (b - bv);
+}
+// Adds a + b into the unevaluated pair (hi, lo), keeping the rounding error of the leading part.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float a, float b) {
+  float s, e;
+  two_sum(hi, a, s, e);
+  hi = s;
+  lo = (lo + b) + e;
+}
+// Segment sum of unevaluated float pairs hi + lo by cascaded TwoSum (the summation of Ogita, Rump
+// and Oishi, 2005): the result is as accurate as a sum carried in twice FP32's precision, at FP32
+// cost.  TwoSum's error term is exact, hence symmetric in its operands, so every lane of the
+// segment ends with the same pair.
+template <int GP> __device__ __forceinline__ void seg_sum2(float& hi, float& lo) {
+#pragma unroll
+  for (int o = GP / 2; o >= 1; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o, GP);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo, o, GP);
+    pair_add(hi, lo, oh, ol);
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Cell-local implicit interaction (Sec. 5.3): inner backward-Euler group update (Eq. 25) inside
 // an outer Newton iteration on T (Eqs. 26-27; reading R11), energy update by conservation (R12),
@@ -137,7 +162,8 @@ struct Coupler {
   bool has;       // lane < G
   bool top2;      // this lane also evaluates the top edge (G == GP)
   NT rcv, Tm;
-  LT K, Sg, cdts, Em, aN, efac, elo, etop;
+  LT K, Sg, cdts, Em, aN, efac;
+  LT elo, etop;   // lower and upper edge of this lane's group
 
   // FP32 group energy B_g(T) and T dB_g/dT from the band table of this lane's group
   __device__ __forceinline__ void planck_tab(float T, float invT, float& B, float& dB) const {
@@ -241,7 +267,7 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
                          (LT)(kn.kappa0 * hpow(rho, g.kap_rho_h)), (LT)(kn.sigma0 * rho),
                          kl.cdts, (LT)Em, kl.aN,
                          gc.efac_of(has ? lane : 0, LT(0)), gc.edge_of(lane <= G ? lane : G, LT(0)),
-                         gc.edge_of(G, LT(0))};
+                         gc.edge_of(lane < G ? lane + 1 : G, LT(0))};
   NT dl = NT(0);
   NT r, dr;
   LT Eg, dEg;
@@ -398,7 +424,7 @@ __device__ __forceinline__ unsigned couple_cell_n(const DevGrid& g, const GroupC
     for (int j = 0; j < NGL; ++j) {
       T Bq, dBq;
       const Coupler<2 * GL, T, T> cpj{g, pk, ptab, gidx[j], hasj[j], false, rcv, Tm, K, Sg, kn.cdts, Em[j],
-                                      kn.aN, efj[j], gc.edge_of(gidx[j], T(0)), gc.edge_of(G, T(0))};
+                                      kn.aN, efj[j], gc.edge_of(gidx[j], T(0)), gc.edge_of(gidx[j] + 1, T(0))};
       cpj.planck(Tl, invT, Bq, dBq);
       const T tau = kn.cdts * kT * efj[j];
       const T dtau = tau * (T(0.5) * (T)g.kap_T_h) * invT;
@@ -520,358 +546,6 @@ __device__ __forceinline__ unsigned couple_cell_n(const DevGrid& g, const GroupC
 #pragma unroll
   for (int q = 0; q < D; ++q) m[q] -= seg_sum<GL>(dF[q]) * kn.ic2;
   rhoe -= seg_sum<GL>(dwork) * kn.ic2;
-  return st;
-}
-
-// ---------------------------------------------------------------------------------------------
-// The same interaction for the FP32 form with the FP64 Newton (group arithmetic in FP32, the
-// temperature iterate, residual and the energy/momentum bookkeeping in FP64), organised for
-// GB300's FP64 pipe, whose cost is per warp instruction whatever the number of active lanes:
-// the scalar FP64 work of all TC cells of the block runs in one warp (lane c = cell c) instead of
-// redundantly in every lane of every cell.  The cells' GP-lane segments evaluate the FP32 group
-// terms at the temperature the scalar warp proposes and return the two group sums through shared
-// memory; Newton, line search, bisection and the bookkeeping sums are the scalar warp's, in the
-// same order of decisions as couple_cell.  Called by all threads of the block (two barriers per
-// evaluation); the iteration counts are bounded as in couple_cell.
-// ---------------------------------------------------------------------------------------------
-template <int D, int GP, int NGL, int TC>
-__device__ __forceinline__ unsigned couple_block(const DevGrid& g, const GroupConst& gc,
-                                                 const PlanckParams& pk, const PlanckTable& ptab,
-                                                 const Consts<double>& kn, const Consts<float>& kl,
-                                                 int nsm, bool active, int lane, int tcell, const float* h,
-                                                 float& rho, float* m, float& rhoe, float* E,
-                                                 float (*F)[3], float* Tout) {
-  using LT = float;
-  using NT = double;
-  constexpr int GL = GP / NGL;  // lanes per cell; lane l owns groups l*NGL .. l*NGL + NGL-1
-  static_assert(TC * GL == 256 && TC <= 32, "one scalar lane per cell of a 256-thread block");
-  __shared__ double s_rho[TC], s_m[3][TC], s_rhoe[TC], s_h[2][TC];
-  __shared__ float s_Esum[TC], s_s1[TC], s_s2[TC], s_Tt[TC], s_lin[TC], s_Es0[TC];
-  __shared__ int s_flag[TC], s_more;
-  __shared__ double s_sum[4][TC];  // FP64 group sums of dE and dF_q per cell
-  enum { F_ACC = 1, F_DONE = 2, F_NEWTON = 4, F_FLOOR = 8, F_BIS = 16 };
-  const int G = g.G;
-  bool hasj[NGL];
-  int gidx[NGL];
-#pragma unroll
-  for (int j = 0; j < NGL; ++j) {
-    hasj[j] = lane * NGL + j < G;
-    gidx[j] = hasj[j] ? lane * NGL + j : 0;
-  }
-  // The scalar warp: blocks resident on one multiprocessor at the same time (linear indices that
-  // differ by multiples of the multiprocessor count, in the first wave) take different warps, so
-  // that their FP64 work lands in different sub-partitions of the multiprocessor.
-  const unsigned blin = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  const int sw = (int)((blin / (unsigned)(nsm > 0 ? nsm : 1)) & 3u);
-  const int c = threadIdx.x & 31;
-  const bool scalar = (int)(threadIdx.x >> 5) == sw && c < TC;  // one lane per cell
-
-  // ---- segments: the cell's inputs for the scalar warp (FP32 values, exact in FP64); E^- with
-  // its silent positivity floor.  Every per-lane value stays FP32: FP64 is the scalar warp's.
-  LT Em[NGL], Esl = LT(0);
-#pragma unroll
-  for (int j = 0; j < NGL; ++j) {
-    Em[j] = hasj[j] ? E[j] : LT(0);
-    if (hasj[j] && Em[j] < kl.E_floor) Em[j] = kl.E_floor;
-    Esl += Em[j];
-  }
-  const LT Esum = seg_sum<GL>(Esl);
-  if (lane == 0) {
-    s_rho[tcell] = (double)rho;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) s_m[q][tcell] = q < D ? (double)m[q] : 0.0;
-    s_rhoe[tcell] = (double)rhoe;
-    s_h[0][tcell] = h ? (double)h[0] : 1.0;
-    s_h[1][tcell] = h ? (double)h[1] : 1.0;
-    s_Esum[tcell] = Esum;
-    s_flag[tcell] = active ? 0 : F_DONE;
-  }
-  __syncthreads();
-
-  // ---- scalar warp: floors, T^- = u^-/(rho c_v), the Newton state of its cell
-  NT rcv = 0.0, Tm = 0.0, ke = 0.0, um = 0.0, scale = 0.0, dl = 0.0, r = 0.0, dr = 0.0, dT = 0.0,
-     lam = 1.0, dtt = 0.0;
-  int it = 0, ls = 0, fl = 0;
-  bool need_dir = true, valid = true;
-  if (scalar) {
-    fl = s_flag[c];
-    NT rr = s_rho[c];
-    if (rr < kn.rho_floor) { rr = kn.rho_floor; fl |= F_FLOOR; }
-    const NT ir = 1.0 / rr;
-    for (int q = 0; q < D; ++q) {
-      const NT mh = h ? s_m[q][c] / (q < 2 ? s_h[q][c] : 1.0) : s_m[q][c];
-      ke += 0.5 * mh * mh * ir;
-    }
-    um = s_rhoe[c] - ke;
-    if (um < kn.u_floor) { um = kn.u_floor; fl |= F_FLOOR; }
-    rcv = rr * kn.cv;
-    Tm = um * ir * kn.gm1;  // u / (rho c_v), c_v = 1/(gamma - 1)
-    scale = um + (NT)s_Esum[c];
-    s_Es0[c] = s_Esum[c];
-    s_rho[c] = rr;
-    s_Tt[c] = (float)Tm;
-  }
-  if (scalar) {
-    // the opacity factors K = kappa0 rho^a and S = sigma0 rho of the (floored) density
-    s_Esum[c] = (float)(kn.kappa0 * hpow(s_rho[c], g.kap_rho_h));
-    s_s1[c] = (float)(kn.sigma0 * s_rho[c]);
-  }
-  __syncthreads();
-  // the segment's group state: accepted (Eg, dEg) and the latest evaluation (Et, dEt); one
-  // Coupler per owned group serves the FP32 Planck tables (its lane field is the group index)
-  const LT Kc = s_Esum[tcell], Sc = s_s1[tcell];
-  LT efj[NGL];
-#pragma unroll
-  for (int j = 0; j < NGL; ++j) efj[j] = gc.efac_of(gidx[j], LT(0));
-  LT Eg[NGL], dEg[NGL], Et[NGL], dEt[NGL];
-#pragma unroll
-  for (int j = 0; j < NGL; ++j) { Eg[j] = Em[j]; dEg[j] = LT(0); Et[j] = Em[j]; dEt[j] = LT(0); }
-  // one evaluation at the proposed temperature: E_g(T) (Eq. 25) and dE_g/dT; the two group sums
-  // go to the scalar warp
-  auto seg_eval = [&]() {
-    const LT Tl = s_Tt[tcell];
-    const LT invT = frcp(Tl);
-    const LT kT = Kc * hpow(Tl, g.kap_T_h);
-    LT a = LT(0), b = LT(0);
-#pragma unroll
-    for (int j = 0; j < NGL; ++j) {
-      LT Bq, dBq;
-      const Coupler<GP, LT, NT> cpj{g, pk, ptab, gidx[j], hasj[j], false, 0.0, 0.0, Kc, Sc, kl.cdts, Em[j],
-                                    kl.aN, efj[j], gc.edge_of(gidx[j], LT(0)), gc.edge_of(G, LT(0))};
-      cpj.planck(Tl, invT, Bq, dBq);
-      const LT kap = kT * efj[j];
-      const LT tau = kl.cdts * kap;
-      const LT dtau = tau * (LT(0.5) * (LT)g.kap_T_h) * invT;
-      const LT inv = frcp(LT(1) + tau);
-      Et[j] = (Em[j] + tau * Bq) * inv;
-      dEt[j] = (tau * dBq + dtau * (Bq - Et[j])) * inv;
-      a += hasj[j] ? Et[j] - Em[j] : LT(0);
-      b += hasj[j] ? dEt[j] : LT(0);
-    }
-    a = seg_sum<GL>(a);
-    b = seg_sum<GL>(b);
-    if (lane == 0) { s_s1[tcell] = a; s_s2[tcell] = b; }
-  };
-  // the scalar warp's Newton decision for its cell (as in couple_cell): from the accepted point
-  // either stop or propose the trial dl + lam dT
-  auto newton_dir = [&]() {
-    if (it >= g.newton_maxit) { fl |= F_DONE | F_NEWTON; return; }
-    if (fabs(r) <= kn.atol * scale) { fl |= F_DONE; s_Tt[c] = (float)(Tm + dl); return; }
-    // 1/dr: FP32 seed refined by one Newton-Raphson step y <- y + y (1 - dr y) (relative error
-    // ~1e-14, far below the step tolerance), shorter in latency than an FP64 division
-    NT y = (NT)(1.0f / (float)dr);
-    y = fma(y, fma(-dr, y, 1.0), y);
-    dT = -r * y;
-    ++it;
-    if (fabs(dT) <= kn.rtol * (Tm + dl)) {
-      // converged: the group energies at T + dT follow from the linearisation
-      dl += dT;
-      s_lin[c] = (float)dT;
-      s_Tt[c] = (float)(Tm + dl);
-      fl |= F_DONE;
-      return;
-    }
-    lam = 1.0;
-    ls = 0;
-    need_dir = false;
-  };
-  auto propose = [&]() {
-    dtt = dl + lam * dT;
-    valid = (Tm + dtt) > 0.0;
-    s_Tt[c] = (float)(Tm + (valid ? dtt : dl));
-  };
-
-  // ---- Newton with backtracking (Eqs. 26-27; reading R11)
-  seg_eval();
-  __syncthreads();
-  if (scalar) {
-    s_lin[c] = 0.0f;
-    if (!(fl & F_DONE)) {
-      r = rcv * dl + (NT)s_s1[c];
-      dr = rcv + (NT)s_s2[c];
-      fl |= F_ACC;
-      newton_dir();
-      if (!(fl & F_DONE)) propose();
-    } else {
-      fl |= F_ACC;
-    }
-    s_flag[c] = fl;
-    const bool more = __any_sync(0xffffffffu >> (32 - TC), !(fl & F_DONE));
-    if (c == 0) s_more = more;
-  }
-  __syncthreads();
-  const int guard = g.newton_maxit * 41 + 2;
-  for (int kk = 0; kk < guard; ++kk) {
-    {
-      const int f = s_flag[tcell];
-      const float lin = s_lin[tcell];
-#pragma unroll
-      for (int j = 0; j < NGL; ++j) {
-        if (f & F_ACC) { Eg[j] = Et[j]; dEg[j] = dEt[j]; }
-        if (lin != 0.0f) Eg[j] += dEg[j] * lin;
-      }
-    }
-    // (the scalar warp rewrites the flags and s_more only after the barrier that follows the
-    // next evaluation, which every thread reaches after reading them)
-    const bool more = s_more;
-    if (!more) break;
-    seg_eval();
-    __syncthreads();
-    if (scalar) {
-      fl &= ~F_ACC;
-      s_lin[c] = 0.0f;
-      if (!(fl & F_DONE)) {
-        const NT rt = rcv * dtt + (NT)s_s1[c];
-        const NT drt = rcv + (NT)s_s2[c];
-        if (valid && fabs(rt) < fabs(r)) {
-          dl = dtt; r = rt; dr = drt; fl |= F_ACC; need_dir = true;
-        } else {
-          lam *= 0.5;
-          if (++ls >= 40) fl |= F_DONE | F_NEWTON;
-        }
-        if (!(fl & F_DONE) && need_dir) newton_dir();
-        if (!(fl & F_DONE)) propose();
-      }
-      s_flag[c] = fl;
-      const bool m2 = __any_sync(0xffffffffu >> (32 - TC), !(fl & F_DONE));
-      if (c == 0) s_more = m2;
-    }
-    __syncthreads();
-  }
-  __syncthreads();  // all threads have read the last flags and s_more before they are rewritten
-  if (scalar && !(s_flag[c] & F_DONE)) fl |= F_NEWTON;  // guard exhausted
-
-  // ---- bisection fallback on a bracket around [T^-, T_rad] (reading R11), in T - T^-
-  if (scalar) {
-    s_flag[c] = (fl & F_NEWTON) ? (fl | F_BIS) : (fl & ~F_BIS);
-    const bool any_bis = __any_sync(0xffffffffu >> (32 - TC), (fl & F_NEWTON) != 0);
-    if (c == 0) s_more = any_bis;
-  }
-  __syncthreads();
-  if (s_more) {
-    NT lo = 0.0, hi = 0.0, Te = 0.0;
-    int phase = 3, cnt = 0;
-    bool brk = false;
-    if (scalar && (fl & F_NEWTON)) {
-      const NT Tr = sqrt(sqrt((NT)s_Es0[c] / (kn.aN * 6.4939394022668291491)));  // (sum E / a_R)^(1/4)
-      const NT T = Tm + dl;
-      lo = fmin(fmin(T, Tr), Tm) - Tm;
-      hi = fmax(fmax(T, Tr), Tm) - Tm;
-      phase = 0;
-      Te = lo;
-      s_Tt[c] = (float)(Tm + Te);
-    }
-    __syncthreads();
-    for (int kk = 0; kk < 400 + g.bisect_maxit + 4; ++kk) {
-      seg_eval();
-      __syncthreads();
-      if (scalar) {
-        if (phase < 3) {
-          const NT rr = rcv * Te + (NT)s_s1[c];
-          if (phase == 0) {
-            if (rr > 0.0 && cnt < 200) { lo = 0.5 * (lo + Tm) - Tm; ++cnt; }  // T_lo /= 2
-            else { phase = 1; cnt = 0; brk = rr <= 0.0; }
-          } else if (phase == 1) {
-            if (rr < 0.0 && cnt < 200) { hi = 2.0 * (hi + Tm) - Tm; ++cnt; }  // T_hi *= 2
-            else { brk = brk && rr >= 0.0; cnt = 0; phase = brk ? (g.bisect_maxit > 0 ? 2 : 3) : 3; }
-          } else {
-            if (rr > 0.0) hi = Te; else lo = Te;
-            ++cnt;
-            if (hi - lo <= kn.rtol * (hi + Tm)) { fl &= ~F_NEWTON; phase = 3; }
-            else if (cnt >= g.bisect_maxit) phase = 3;
-          }
-          Te = phase == 0 ? lo : (phase == 1 ? hi : (phase == 2 ? 0.5 * (lo + hi) : Te));
-          s_Tt[c] = (float)(Tm + Te);
-        }
-        const bool m3 = __any_sync(0xffffffffu >> (32 - TC), phase < 3);
-        if (c == 0) s_more = m3;
-      }
-      __syncthreads();
-      const bool more = s_more;
-      if (!more) break;
-    }
-    // the group energies at the bracket's midpoint
-    if (scalar && (s_flag[c] & F_BIS)) {
-      if (brk) dl = 0.5 * (lo + hi);
-      s_Tt[c] = (float)(Tm + dl);
-    }
-    __syncthreads();
-    seg_eval();
-    if (s_flag[tcell] & F_BIS) {
-#pragma unroll
-      for (int j = 0; j < NGL; ++j) Eg[j] = Et[j];
-    }
-    __syncthreads();
-  }
-
-  // ---- bookkeeping in the scalar warp (FP64): energy by conservation (R12), then the flux
-  // absorption update at the converged temperature (Eq. 28) and its feedback (Eqs. 31-32)
-  // (s_Tt holds T* = T^- + dl of every cell: written when Newton stopped, or by the bisection)
-  const LT Tst = s_Tt[tcell];
-  const LT kT = Kc * hpow(Tst, g.kap_T_h);
-  // FP64 group sums of the energy change and of the flux changes, in the cells' segments (the
-  // FP64 pipe cost is per warp instruction: spread over all warps, not serialised in one)
-  {
-    NT dE = 0.0;
-#pragma unroll
-    for (int j = 0; j < NGL; ++j) dE += hasj[j] ? (NT)Eg[j] - (NT)Em[j] : 0.0;
-    const NT sE = seg_sum<GL>(dE);
-    if (lane == 0) s_sum[0][tcell] = sE;
-  }
-  LT fac[NGL];
-#pragma unroll
-  for (int j = 0; j < NGL; ++j) fac[j] = frcp(LT(1) + kl.cdts * (kT * efj[j] + Sc));
-#pragma unroll
-  for (int q = 0; q < D; ++q) {
-    NT dF = 0.0;
-#pragma unroll
-    for (int j = 0; j < NGL; ++j) {
-      const LT Fq = hasj[j] ? F[j][q] : LT(0);
-      const LT Fn = Fq * fac[j];
-      dF += (NT)(Fn - Fq);
-      if (hasj[j]) F[j][q] = Fn;
-    }
-    const NT sF = seg_sum<GL>(dF);
-    if (lane == 0) s_sum[1 + q][tcell] = sF;
-  }
-#pragma unroll
-  for (int j = 0; j < NGL; ++j)
-    if (hasj[j]) E[j] = Eg[j];
-  __syncthreads();
-  if (scalar) {
-    const NT dEsum = s_sum[0][c];
-    NT SdF[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int q = 0; q < D; ++q) SdF[q] = s_sum[1 + q][c];
-    const NT rr = s_rho[c], ir = 1.0 / rr;
-    NT re = ke + (um - dEsum);
-    NT work = 0.0;
-    for (int q = 0; q < D; ++q) {
-      const NT mq = s_m[q][c];
-      const NT hq = q < 2 ? s_h[q][c] : 1.0;
-      work += (h ? mq / (hq * hq) : mq) * ir * SdF[q];
-      s_m[q][c] = mq - SdF[q] * kn.ic2;
-    }
-    s_rhoe[c] = re - work * kn.ic2;
-    if (fl & F_NEWTON) s_flag[c] |= F_NEWTON;
-    if (fl & F_FLOOR) s_flag[c] |= F_FLOOR;
-    s_Tt[c] = (float)s_rho[c];
-    s_s1[c] = (float)s_rhoe[c];
-#pragma unroll
-    for (int q = 0; q < D; ++q) s_sum[1 + q][c] = s_m[q][c];
-  }
-  __syncthreads();
-  rho = s_Tt[tcell];
-#pragma unroll
-  for (int q = 0; q < D; ++q) m[q] = (float)s_sum[1 + q][tcell];
-  rhoe = s_s1[tcell];
-  if (Tout) *Tout = Tst;
-  const int f = s_flag[tcell];
-  unsigned st = 0;
-  if (active && (f & F_NEWTON)) st |= ST_NEWTON;
-  if (active && (f & F_FLOOR)) st |= ST_FLOOR;
-  // (the next call writes the shared arrays only after the stage kernel's next plane has passed
-  // its own barriers)
   return st;
 }
 
@@ -1445,8 +1119,8 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       // gas: lane v < NG updates variable v, then the segment shares the cell's gas state
       R ug = g0 + dt * (gsrc - gnet);
       if (stage2) ug = KR.alpha * bg0 + KR.beta * ug;
-      // per-lane carrier type of the interaction's inputs and outputs: NT, except in the FP32 form
-      // with the FP64 Newton, whose FP64 work is confined to one warp per block (couple_block)
+      // The FP32 form with the FP64 Newton leaves the interaction to couple_kernel (one thread per
+      // cell, so that each FP64 instruction serves 32 cells); its per-lane carrier type is R.
       constexpr bool coop = std::is_same<LT, float>::value && std::is_same<NT, double>::value;
       using CT = typename std::conditional<coop, R, NT>::type;
       CT gas[NG];
@@ -1493,14 +1167,13 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       }
       unsigned stbits = 0;
       CT Tst = CT(0);
-      if (g.couple) {
+      if (g.couple && !coop) {
         // covariant components: physical = m_q / h_q on curvilinear grids (Cartesian: no scaling)
         CT h[3] = {(CT)hq[0], (CT)hq[1], CT(1)};
         CT m[3] = {gas[1], D > 1 ? gas[2] : CT(0), D > 2 ? gas[3] : CT(0)};
         CT rho = gas[0], rhoe = gas[NG - 1];
         if constexpr (coop) {
-          stbits = couple_block<D, GP, NGL, TX * TY>(g, *sgc, A.pk, A.ptab, A.kd, A.kf, A.nsm, cell_in, lane,
-                                                     tcell, sph ? h : nullptr, rho, m, rhoe, E, F, &Tst);
+          // (not reached: couple_kernel)
         } else if constexpr (NGL == 2) {
           stbits = couple_cell_n<D, GL, NGL>(g, *sgc, A.pk, A.ptab, A.kf, cell_in, lane, sph ? h : nullptr,
                                              rho, m, rhoe, E, F, &Tst);

@@ -3,6 +3,6 @@
 #include "fx_launch.h"
 
 namespace fx {
-template cudaError_t launch_stage<float, 2, float>(const StageArgs<float>&, int, cudaStream_t,
+template cudaError_t launch_stage<float, 2, float>(const StageArgs<float>&, int, cudaStream_t, cudaEvent_t,
                                                   cudaEvent_t);
 }  // namespace fx

@@ -1,8 +1,9 @@
-// Stage kernel instantiations: state float, group arithmetic float, Newton/bookkeeping double, 1-d.
+// Stage kernel instantiations: state float, group arithmetic float, Newton/bookkeeping double
+// (interaction kernel of its own), 1-d.
 #define FX_LAUNCH_DEFINE
 #include "fx_launch.h"
 
 namespace fx {
-template cudaError_t launch_stage<float, 1, double>(const StageArgs<float>&, int, cudaStream_t,
+template cudaError_t launch_stage<float, 1, double>(const StageArgs<float>&, int, cudaStream_t, cudaEvent_t,
                                                   cudaEvent_t);
 }  // namespace fx

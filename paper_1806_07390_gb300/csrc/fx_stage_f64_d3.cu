@@ -3,6 +3,6 @@
 #include "fx_launch.h"
 
 namespace fx {
-template cudaError_t launch_stage<double, 3, double>(const StageArgs<double>&, int, cudaStream_t,
+template cudaError_t launch_stage<double, 3, double>(const StageArgs<double>&, int, cudaStream_t, cudaEvent_t,
                                                   cudaEvent_t);
 }  // namespace fx

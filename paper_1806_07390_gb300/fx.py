@@ -234,10 +234,11 @@ class Grid:
 
     def kernel_times(self) -> dict:
         """Synchronising read of the recorded durations: total ms and launch counts per kernel."""
-        out = np.zeros(4)
+        out = np.zeros(6)
         self._check(self.L.fx_kernel_timing_read(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return {"stage_ms": float(out[0]), "stage_launches": int(out[1]),
-                "face_ms": float(out[2]), "face_launches": int(out[3])}
+                "face_ms": float(out[2]), "face_launches": int(out[3]),
+                "couple_ms": float(out[4]), "couple_launches": int(out[5])}
 
     # -- objective and adjoint
     def objective(self, on: bool = True) -> None:
