@@ -999,7 +999,7 @@ size_t fx_state_elems(const fx_grid* h) { return h ? (size_t)h->ncell * h->NV : 
 
 int fx_launches_per_step(const fx_grid* h) {
   if (!h) return 0;
-  const bool split = h->P.precision == FX_FP32_F64NEWTON && h->P.couple;
+  const bool split = h->P.precision != FX_FP64 && h->P.couple;
   return 2 * (2 + (split ? 1 : 0) + (h->objective ? 1 : 0));
 }
 
@@ -1311,7 +1311,7 @@ fx_status fx_kernel_timing_read(fx_grid* h, double out[6]) {
   if (h->nev == 0) return FX_OK;
   cudaError_t e = cudaEventSynchronize(h->ev[h->nev - 1]);
   if (e != cudaSuccess) return cuda_fail(h, e, "timing read");
-  const bool split = h->P.precision == FX_FP32_F64NEWTON && h->P.couple;
+  const bool split = h->P.precision != FX_FP64 && h->P.couple;
   for (size_t i = 0; i < h->nev; i += 4) {
     float face = 0.f, stage = 0.f, inter = 0.f;
     e = cudaEventElapsedTime(&face, h->ev[i], h->ev[i + 1]);

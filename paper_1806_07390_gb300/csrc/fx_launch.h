@@ -28,9 +28,10 @@ template <class R, int D, class NT>
 cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid,
                          cudaEvent_t mid2);
 
-// Whether the interaction runs in couple_kernel rather than inside the stage kernel.
+// Whether the interaction runs in couple_kernel rather than inside the stage kernel: in both
+// forms with an FP32 state.
 template <class R, class NT> constexpr bool split_interaction() {
-  return std::is_same<R, float>::value && std::is_same<NT, double>::value;
+  return std::is_same<R, float>::value;
 }
 
 // Dynamic shared memory of the stage kernel (tile shape from D and GP).
@@ -91,7 +92,7 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
   }
   if constexpr (split_interaction<R, NT>()) {
     if (a.g.couple) {
-      auto ck = couple_kernel<D, double>;
+      auto ck = couple_kernel<D, NT>;
       const size_t cs = couple_smem_bytes<D>(a.g.G);
       e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
       if (e != cudaSuccess) return e;

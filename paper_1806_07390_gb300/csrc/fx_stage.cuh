@@ -1,9 +1,11 @@
 // Fused SSP-RK2 stage kernel: explicit transport (reconstruction, HLLC, M1/HLL radiation fluxes,
-// flux divergence) + RK combine + the cell-local implicit interaction, in one pass over HBM.
+// flux divergence) + RK combine, and in the FP64 form the cell-local implicit interaction, in one
+// pass over HBM (the FP32 forms run the interaction in couple_kernel, fx_couple.cuh).
 //
 // Work decomposition.  A thread block owns a tile of TX (x) by TY (y, 3-d only) cells and
 // marches along the slowest active axis (y in 2-d, z in 3-d) over `chunk` planes.  Each cell is
-// served by a segment of GP lanes (GP = power of two >= groups); lane g owns group g.  A shared
+// served by a segment of GP/NGL lanes (GP = power of two >= groups); a lane owns NGL consecutive
+// groups (two in the FP32 forms when GP >= 16, else one).  A shared
 // ring of four planes holds the conserved state (k-1 .. k+2) so that every face flux is computed
 // exactly once: in-plane faces per plane, and the march-direction face k+1/2 per step, carried
 // in registers to the next step.  Ghost cells are produced at load time from the boundary
@@ -370,182 +372,6 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
 #pragma unroll
   for (int q = 0; q < D; ++q) m[q] -= seg_sum<GP>(dF[q]) * ic2;
   rhoe -= seg_sum<GP>(dwork) * ic2;
-  return st;
-}
-
-// ---------------------------------------------------------------------------------------------
-// couple_cell for the all-FP32 form with NGL groups per lane (GL = GP/NGL lanes per cell): the
-// same iteration, stopping tests and bookkeeping; the group sums add the lane's own groups before
-// the segment shuffle, and the temperature power of the opacity is shared by a lane's groups.
-// ---------------------------------------------------------------------------------------------
-template <int D, int GL, int NGL>
-__device__ __forceinline__ unsigned couple_cell_n(const DevGrid& g, const GroupConst& gc,
-                                                  const PlanckParams& pk, const PlanckTable& ptab,
-                                                  const Consts<float>& kn, bool active, int lane,
-                                                  const float* h, float& rho, float* m, float& rhoe,
-                                                  float* E, float (*F)[3], float* Tout) {
-  using T = float;
-  const int G = g.G;
-  unsigned st = 0;
-  bool hasj[NGL];
-  int gidx[NGL];
-#pragma unroll
-  for (int j = 0; j < NGL; ++j) {
-    hasj[j] = lane * NGL + j < G;
-    gidx[j] = hasj[j] ? lane * NGL + j : 0;
-  }
-  if (rho < kn.rho_floor) { rho = kn.rho_floor; st |= ST_FLOOR; }
-  const T irho = frcp(rho);
-  T ke = T(0);
-#pragma unroll
-  for (int q = 0; q < D; ++q) { T mh = h ? m[q] * frcp(h[q]) : m[q]; ke += T(0.5) * mh * mh * irho; }
-  T u_m = rhoe - ke;
-  if (u_m < kn.u_floor) { u_m = kn.u_floor; rhoe = ke + u_m; st |= ST_FLOOR; }
-  T Em[NGL], efj[NGL], Esl = T(0);
-#pragma unroll
-  for (int j = 0; j < NGL; ++j) {
-    Em[j] = hasj[j] ? E[j] : T(0);
-    if (hasj[j] && Em[j] < kn.E_floor) Em[j] = kn.E_floor;  // silent positivity floor
-    Esl += Em[j];
-    efj[j] = gc.efac_of(gidx[j], T(0));
-  }
-  const T Esum = seg_sum<GL>(Esl);
-  const T rcv = rho * kn.cv;
-  const T Tm = u_m * frcp(rcv);
-  const T K = kn.kappa0 * hpow(rho, g.kap_rho_h), Sg = kn.sigma0 * rho;
-  // residual r = rho c_v dl + sum_g (E_g(T) - E_g^-) and dr/dT at T = T^- + dl, with each of the
-  // lane's group energies and their T derivatives
-  auto evaln = [&](T dl, T& r, T& dr, T* Eg, T* dEg) {
-    const T Tl = Tm + dl;
-    const T invT = frcp(Tl);
-    const T kT = K * hpow(Tl, g.kap_T_h);
-    T a = T(0), b = T(0);
-#pragma unroll
-    for (int j = 0; j < NGL; ++j) {
-      T Bq, dBq;
-      const Coupler<2 * GL, T, T> cpj{g, pk, ptab, gidx[j], hasj[j], false, rcv, Tm, K, Sg, kn.cdts, Em[j],
-                                      kn.aN, efj[j], gc.edge_of(gidx[j], T(0)), gc.edge_of(gidx[j] + 1, T(0))};
-      cpj.planck(Tl, invT, Bq, dBq);
-      const T tau = kn.cdts * kT * efj[j];
-      const T dtau = tau * (T(0.5) * (T)g.kap_T_h) * invT;
-      const T inv = frcp(T(1) + tau);
-      Eg[j] = (Em[j] + tau * Bq) * inv;
-      dEg[j] = (tau * dBq + dtau * (Bq - Eg[j])) * inv;
-      a += hasj[j] ? Eg[j] - Em[j] : T(0);
-      b += hasj[j] ? dEg[j] : T(0);
-    }
-    r = rcv * dl + seg_sum<GL>(a);
-    dr = rcv + seg_sum<GL>(b);
-  };
-  T dl = T(0), r, dr;
-  T Eg[NGL], dEg[NGL];
-  evaln(dl, r, dr, Eg, dEg);
-  const T scale = u_m + Esum;
-  const T rtol = kn.rtol, atol = kn.atol;
-  bool done = !active, ok = !active, need_dir = true;
-  int it = 0, ls = 0;
-  T dT = T(0), lam = T(1);
-  const int guard = g.newton_maxit * 41 + 2;
-  for (int k = 0; k < guard; ++k) {
-    if (!done && need_dir) {
-      if (it >= g.newton_maxit) { done = true; }
-      else if (fabsf(r) <= atol * scale) { done = true; ok = true; }
-      else {
-        dT = -r / dr;
-        ++it;
-        if (fabsf(dT) <= rtol * (Tm + dl)) {
-          // converged: the group energies at T + dT follow from the linearisation
-          dl += dT;
-#pragma unroll
-          for (int j = 0; j < NGL; ++j) Eg[j] += dEg[j] * dT;
-          done = true;
-          ok = true;
-        } else { lam = T(1); ls = 0; need_dir = false; }
-      }
-    }
-    if (__all_sync(0xffffffffu, done)) break;
-    const T dt_ = dl + lam * dT;
-    const bool valid = !done && (Tm + dt_) > T(0);
-    T rt, drt, Et[NGL], dEt[NGL];
-    evaln(valid ? dt_ : dl, rt, drt, Et, dEt);
-    if (!done) {
-      if (valid && fabsf(rt) < fabsf(r)) {
-        dl = dt_; r = rt; dr = drt; need_dir = true;
-#pragma unroll
-        for (int j = 0; j < NGL; ++j) { Eg[j] = Et[j]; dEg[j] = dEt[j]; }
-      } else { lam *= T(0.5); if (++ls >= 40) done = true; }
-    }
-  }
-  // bisection fallback on a bracket around [T^-, T_rad] (reading R11), in T - T^-
-  if (__any_sync(0xffffffffu, active && !ok)) {
-    const bool need = active && !ok;
-    const T Tr = sqrtf(sqrtf(Esum * frcp(kn.aN * T(6.4939394022668291491))));  // (sum E / a_R)^(1/4)
-    const T Tc = Tm + dl;
-    T lo = fminf(fminf(Tc, Tr), Tm) - Tm, hi = fmaxf(fmaxf(Tc, Tr), Tm) - Tm;
-    int phase = need ? 0 : 3, cnt = 0;
-    bool brk = false;
-    T rr, dd, ee[NGL], de[NGL];
-    for (int k = 0; k < 400 + g.bisect_maxit + 4; ++k) {
-      if (__all_sync(0xffffffffu, phase == 3)) break;
-      const T Te = phase == 0 ? lo : (phase == 1 ? hi : (phase == 2 ? T(0.5) * (lo + hi) : dl));
-      evaln(Te, rr, dd, ee, de);
-      if (phase == 0) {
-        if (rr > T(0) && cnt < 200) { lo = T(0.5) * (lo + Tm) - Tm; ++cnt; }  // T_lo /= 2
-        else { phase = 1; cnt = 0; brk = rr <= T(0); }
-      } else if (phase == 1) {
-        if (rr < T(0) && cnt < 200) { hi = T(2) * (hi + Tm) - Tm; ++cnt; }   // T_hi *= 2
-        else {
-          brk = brk && rr >= T(0);
-          cnt = 0;
-          phase = brk ? (g.bisect_maxit > 0 ? 2 : 3) : 3;
-        }
-      } else if (phase == 2) {
-        if (rr > T(0)) hi = Te; else lo = Te;
-        ++cnt;
-        if (hi - lo <= rtol * (hi + Tm)) { ok = true; phase = 3; }
-        else if (cnt >= g.bisect_maxit) phase = 3;
-      }
-    }
-    if (need && brk) dl = T(0.5) * (lo + hi);
-    T r2, d2, e2[NGL], de2[NGL];
-    evaln(dl, r2, d2, e2, de2);
-    if (need) {
-#pragma unroll
-      for (int j = 0; j < NGL; ++j) Eg[j] = e2[j];
-    }
-  }
-  if (active && !ok) st |= ST_NEWTON;
-  if (Tout) *Tout = Tm + dl;
-  // energy update by conservation (R12)
-  T dEl = T(0);
-#pragma unroll
-  for (int j = 0; j < NGL; ++j) dEl += hasj[j] ? Eg[j] - Em[j] : T(0);
-  rhoe = ke + (u_m - seg_sum<GL>(dEl));
-#pragma unroll
-  for (int j = 0; j < NGL; ++j)
-    if (hasj[j]) E[j] = Eg[j];
-  // momentum coupling at the converged temperature (Eq. 28; Eqs. 31-32)
-  const T kT = K * hpow(Tm + dl, g.kap_T_h);
-  T dF[3] = {T(0), T(0), T(0)};
-#pragma unroll
-  for (int j = 0; j < NGL; ++j) {
-    const T fac = frcp(T(1) + kn.cdts * (kT * efj[j] + Sg));
-#pragma unroll
-    for (int q = 0; q < D; ++q) {
-      if (hasj[j]) {
-        const T Fq = F[j][q];
-        const T Fn = Fq * fac;
-        dF[q] += Fn - Fq;
-        F[j][q] = Fn;
-      }
-    }
-  }
-  T dwork = T(0);
-#pragma unroll
-  for (int q = 0; q < D; ++q) dwork += (h ? m[q] * frcp(h[q] * h[q]) : m[q]) * irho * dF[q];
-#pragma unroll
-  for (int q = 0; q < D; ++q) m[q] -= seg_sum<GL>(dF[q]) * kn.ic2;
-  rhoe -= seg_sum<GL>(dwork) * kn.ic2;
   return st;
 }
 
@@ -1119,9 +945,10 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       // gas: lane v < NG updates variable v, then the segment shares the cell's gas state
       R ug = g0 + dt * (gsrc - gnet);
       if (stage2) ug = KR.alpha * bg0 + KR.beta * ug;
-      // The FP32 form with the FP64 Newton leaves the interaction to couple_kernel (one thread per
-      // cell, so that each FP64 instruction serves 32 cells); its per-lane carrier type is R.
-      constexpr bool coop = std::is_same<LT, float>::value && std::is_same<NT, double>::value;
+      // The FP32 forms leave the interaction to couple_kernel (one thread per cell: each FP64
+      // instruction of the FP64 Newton serves 32 cells, and the scalar steps are not repeated by
+      // the group lanes); their per-lane carrier type is R.
+      constexpr bool coop = std::is_same<LT, float>::value;
       using CT = typename std::conditional<coop, R, NT>::type;
       CT gas[NG];
 #pragma unroll
@@ -1174,9 +1001,6 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         CT rho = gas[0], rhoe = gas[NG - 1];
         if constexpr (coop) {
           // (not reached: couple_kernel)
-        } else if constexpr (NGL == 2) {
-          stbits = couple_cell_n<D, GL, NGL>(g, *sgc, A.pk, A.ptab, A.kf, cell_in, lane, sph ? h : nullptr,
-                                             rho, m, rhoe, E, F, &Tst);
         } else {
           stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.ptab, A.k(NT(0)), A.k(LT(0)), cell_in, lane,
                                               sph ? h : nullptr, rho, m, rhoe, E[0], F[0], &Tst);

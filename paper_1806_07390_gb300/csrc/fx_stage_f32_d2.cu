@@ -1,4 +1,5 @@
-// Stage kernel instantiations: state float, group arithmetic float, Newton/bookkeeping float, 2-d.
+// Stage kernel instantiations: state float, group arithmetic float, Newton/bookkeeping float
+// (interaction kernel of its own), 2-d.
 #define FX_LAUNCH_DEFINE
 #include "fx_launch.h"
 
