@@ -173,7 +173,8 @@ int fx_debug_ntab(void);
 
 /* Host-side inspection of the FP32 Planck band tables: for group g and node i (u = log2 T =
  * *u0 + i/32), with L = log2 of the band integral Int t^3/(e^t-1) dt over the group's edges
- * divided by T: out[4(g*nu + i) + {0,1,2,3}] = L - floor(L), (dL/du)/32, floor(L), 0.  Returns
+ * divided by T: out[4(g*nu + i) + {0,1,2,3}] = L - floor(L), (dL/du)/32, floor(L), and 2^floor(L)
+ * (0 where floor(L) < -126).  Returns
  * the number of floats (copied only when cap is large enough), or -1 for a null handle. */
 int fx_debug_planck_table(const fx_grid* h, float* out, size_t cap, int* nu, float* u0);
 

@@ -363,7 +363,10 @@ void build_planck_table(const fx_params& P, const GroupConst& gc, const PlanckPa
         m = -h * a;  // the band underflows in FP32 here; keep the table smooth and negative
       }
       const double k = std::floor(L);
-      T.tab[(size_t)g * T.nu + i] = make_float4((float)(L - k), (float)m, (float)k, 0.0f);
+      // 2^floor(L), exact in FP32 down to the smallest normal number (0 below, where the band
+      // integral flushes to zero in FP32 anyway)
+      const float sc = k >= -126.0 ? (float)std::ldexp(1.0, (int)k) : 0.0f;
+      T.tab[(size_t)g * T.nu + i] = make_float4((float)(L - k), (float)m, (float)k, sc);
     }
 }
 

@@ -30,14 +30,22 @@ template <int D> inline size_t couple_smem_bytes(int G) {
   return (size_t)(1 + D) * CPL_THREADS * (size_t)(G + 1) * sizeof(float);
 }
 
+// 2^x for the table's fractional part (|x| < 2): the PTX base-2 exponential (relative error
+// about 2^-22, far below the FP32 form's tolerances).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Temperature-dependent part of one evaluation of the group energies: the position in the FP32
 // Planck band tables (shared by all groups: the tables have common nodes in log2 T), the cubic
 // Hermite weights there, and the powers of T.
 struct PlanckAt {
-  int mode;          // 0: every band in the Wien tail (B = 0); 1: table; 2: hot-limit series
-  int i;             // left node (mode 1)
+  int mode;              // 0: every band in the Wien tail (B = 0); 1: table; 2: hot-limit series
+  int i;                 // left node (mode 1)
   float w0, w1, w2, w3;  // Hermite weights of L_i, h L'_i, L_{i+1}, h L'_{i+1}
-  float v0, v1, v2;      // weights of the derivative dL/dt: (L_i - L_{i+1}), h L'_i, h L'_{i+1}
+  float v0, v1, v2;      // weights of dL/du: (L_i - L_{i+1}), h L'_i, h L'_{i+1} (times 1/h)
   float invT, aT3, aT4;  // 1/T, a_N T^3, a_N T^4
 };
 
@@ -56,37 +64,38 @@ __device__ __forceinline__ PlanckAt planck_at(const PlanckTable& ptab, float aN,
   p.w1 = t3 - 2.0f * t2 + t;
   p.w2 = 3.0f * t2 - 2.0f * t3;
   p.w3 = t3 - t2;
-  p.v0 = 6.0f * t2 - 6.0f * t;
-  p.v1 = 3.0f * t2 - 4.0f * t + 1.0f;
-  p.v2 = 3.0f * t2 - 2.0f * t;
+  p.v0 = (6.0f * t2 - 6.0f * t) * float(PTAB_PER_OCT);
+  p.v1 = (3.0f * t2 - 4.0f * t + 1.0f) * float(PTAB_PER_OCT);
+  p.v2 = (3.0f * t2 - 2.0f * t) * float(PTAB_PER_OCT);
   return p;
 }
 
 // B_g(T) and dB_g/dT of group g (band edges elo, ehi) at the evaluation point p.
 __device__ __forceinline__ void planck_group(const PlanckTable& ptab, const PlanckAt& p, int g,
-                                             float elo, float ehi, float& B, float& dB) {
+                                             const float* edge, float& B, float& dB) {
   float I, dLdu;
   if (p.mode == 1) {
     const float4 p0 = __ldg(ptab.tab + g * ptab.nu + p.i);
     const float4 p1 = __ldg(ptab.tab + g * ptab.nu + p.i + 1);
-    // node values relative to floor(L) of the left node (small numbers, full FP32 precision)
+    // node values relative to floor(L) of the left node (small numbers, full FP32 precision);
+    // I = 2^(L - floor L) 2^floor(L), the second factor exact from the table
     const float d1 = (p1.z - p0.z) + p1.x;
     const float Lr = p.w0 * p0.x + p.w1 * p0.y + p.w2 * d1 + p.w3 * p1.y;
-    const float dLdt = p.v0 * (p0.x - d1) + p.v1 * p0.y + p.v2 * p1.y;
-    I = ldexpf(exp2f(Lr), (int)p0.z);
-    dLdu = dLdt * float(PTAB_PER_OCT);
+    dLdu = p.v0 * (p0.x - d1) + p.v1 * p0.y + p.v2 * p1.y;
+    I = ex2_approx(Lr) * p0.w;
   } else if (p.mode == 0) {
     I = 0.0f;  // deep in the Wien tail
     dLdu = 0.0f;
   } else {
     // very hot: x = eps/T < 2^-14 at both edges, Int t^3/(e^t-1) = x^3/3 - x^4/8 + O(x^5)
-    const float a = elo * p.invT, b = ehi * p.invT;
+    const float a = edge[g] * p.invT, b = edge[g + 1] * p.invT;
     const float a3 = a * a * a, b3 = b * b * b;
     I = (b3 - a3) * (1.0f / 3.0f) - (b3 * b - a3 * a) * 0.125f;
     dLdu = ((a3 * a * (1.0f - 0.5f * a)) - (b3 * b * (1.0f - 0.5f * b))) * frcp(I);
   }
   B = p.aT4 * I;
-  dB = p.aT3 * I * (4.0f + dLdu);  // d/dT (T^4 I) = T^3 I (4 + d ln I / d ln T)
+  const float t = p.aT3 * I;
+  dB = fmaf(t, dLdu, 4.0f * t);  // d/dT (T^4 I) = T^3 I (4 + d ln I / d ln T)
 }
 
 template <int D, class NT>
@@ -155,7 +164,9 @@ __global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A)
     // ---- floors, T^- = u^-/(rho c_v), the opacity factors of the (floored) density
     NT rr = (NT)rho_f;
     if (rr < kn.rho_floor) { rr = kn.rho_floor; st |= ST_FLOOR; }
-    const NT ir = NT(1) / rr;
+    // 1/rho: for FP64, an FP32 seed refined by one Newton-Raphson step (relative error ~1e-14)
+    NT ir = (NT)(1.0f / (float)rr);
+    if (sizeof(NT) == 8) ir = fma(ir, fma(-rr, ir, NT(1)), ir);
     NT ke = NT(0);
 #pragma unroll
     for (int q = 0; q < D; ++q) {
@@ -165,6 +176,7 @@ __global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A)
     NT um = (NT)rhoe_f - ke;
     if (um < kn.u_floor) { um = kn.u_floor; st |= ST_FLOOR; }
     const NT rcv = rr * kn.cv;
+    const LT rcv_f = (LT)rcv;
     const NT Tm = um * ir * kn.gm1;  // c_v = 1/(gamma - 1)
     const LT Kc = (LT)(kn.kappa0 * hpow(rr, g.kap_rho_h)), Sc = (LT)(kn.sigma0 * rr);
     // E^- with its silent positivity floor (Wien tails), and its group sum
@@ -174,78 +186,79 @@ __global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A)
       if (e < kl.E_floor) { e = kl.E_floor; rE[j] = e; }
       Esum += e;
     }
-    const NT scale = um + (NT)Esum;
+    const NT ats = kn.atol * (um + (NT)Esum);
     const LT hh = LT(0.5) * (LT)g.kap_T_h;
     // one evaluation at T: the group sums of E_g(T) - E_g^- (Eq. 25) and of dE_g/dT
     auto eval = [&](LT Tl, LT& sa, LT& sb) {
       const PlanckAt p = planck_at(A.ptab, kl.aN, Tl);
-      const LT kT = Kc * hpow(Tl, g.kap_T_h);
+      const LT ck = kl.cdts * (Kc * hpow(Tl, g.kap_T_h));
+      const LT hi = hh * p.invT;
       LT a = LT(0), b = LT(0);
+#pragma unroll 1
       for (int j = 0; j < G; ++j) {
         LT Bq, dBq;
-        planck_group(A.ptab, p, j, s_ed[j], s_ed[j + 1], Bq, dBq);
+        planck_group(A.ptab, p, j, s_ed, Bq, dBq);
         const LT Em = rE[j];
-        const LT tau = kl.cdts * (kT * s_ef[j]);
-        const LT dtau = tau * hh * p.invT;
+        const LT tau = ck * s_ef[j];
         const LT inv = frcp(LT(1) + tau);
         const LT Eg = (Em + tau * Bq) * inv;
-        const LT dEg = (tau * dBq + dtau * (Bq - Eg)) * inv;
+        const LT dEg = (tau * dBq + (tau * hi) * (Bq - Eg)) * inv;
         a += Eg - Em;
         b += dEg;
       }
       sa = a;
       sb = b;
     };
-    // 1/dr: for FP64, an FP32 seed refined by one Newton-Raphson step (relative error ~1e-14, far
-    // below the step tolerance), shorter in latency than an FP64 division
-    auto recip = [](NT x) -> NT {
-      NT y = (NT)(1.0f / (float)x);
-      if (sizeof(NT) == 8) y = fma(y, fma(-x, y, NT(1)), y);
-      return y;
-    };
 
-    // ---- Newton with backtracking (Eqs. 26-27; reading R11)
-    NT dl = NT(0), dacc = NT(0), r, dr, dT = NT(0), lam = NT(1);
-    LT lin = LT(0);  // linearised step added to the accepted group energies at convergence
+    // ---- Newton with backtracking (Eqs. 26-27; reading R11).  The iterate dl = T - T^- and the
+    // residual r are NT; the direction -r/(dr/dT) only needs FP32 (a Newton step is as good as
+    // its residual), so dr/dT, the step and the step test are FP32.
+    NT dl = NT(0), dacc = NT(0), r;
+    LT drf, dTf = LT(0), lam = LT(1);
+    LT Tacc = (LT)Tm;  // T at the accepted point, in FP32
+    LT lin = LT(0);    // linearised step added to the accepted group energies at convergence
     int it = 0, ls = 0;
     bool ok = false, done = false, need_dir = true;
     {
       LT a, b;
-      eval((LT)Tm, a, b);
+      eval(Tacc, a, b);
       r = (NT)a;
-      dr = rcv + (NT)b;
+      drf = rcv_f + b;
     }
     const int guard = g.newton_maxit * 41 + 2;
     for (int kk = 0; kk < guard; ++kk) {
       if (need_dir) {
         if (it >= g.newton_maxit) { done = true; }
-        else if (fabs(r) <= kn.atol * scale) { done = true; ok = true; }
+        else if (fabs(r) <= ats) { done = true; ok = true; }
         else {
-          dT = -r * recip(dr);
+          dTf = -(LT)r * frcp(drf);
           ++it;
-          if (fabs(dT) <= kn.rtol * (Tm + dl)) {
+          if (fabsf(dTf) <= kl.rtol * Tacc) {
             // converged: the group energies at T + dT follow from the linearisation
-            dl += dT;
-            lin = (LT)dT;
+            dl += (NT)dTf;
+            lin = dTf;
             done = true;
             ok = true;
-          } else { lam = NT(1); ls = 0; need_dir = false; }
+          } else { lam = LT(1); ls = 0; need_dir = false; }
         }
       }
       if (done) break;
-      const NT dtt = dl + lam * dT;
-      const bool valid = (Tm + dtt) > NT(0);
+      const NT dtt = dl + (NT)(lam * dTf);
+      const NT Ttr = Tm + dtt;
+      const bool valid = Ttr > NT(0);
+      const LT Tl = valid ? (LT)Ttr : Tacc;
       LT a, b;
-      eval((LT)(Tm + (valid ? dtt : dl)), a, b);
+      eval(Tl, a, b);
       const NT rt = rcv * dtt + (NT)a;
       if (valid && fabs(rt) < fabs(r)) {
         dl = dtt;
         dacc = dtt;
+        Tacc = Tl;
         r = rt;
-        dr = rcv + (NT)b;
+        drf = rcv_f + b;
         need_dir = true;
       } else {
-        lam *= NT(0.5);
+        lam *= LT(0.5);
         if (++ls >= 40) done = true;
       }
     }
@@ -289,16 +302,16 @@ __global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A)
     {
       const LT Ta = (LT)(Tm + dacc);
       const PlanckAt p = planck_at(A.ptab, kl.aN, Ta);
-      const LT kT = Kc * hpow(Ta, g.kap_T_h);
+      const LT ck = kl.cdts * (Kc * hpow(Ta, g.kap_T_h));
+      const LT hi = hh * p.invT;
       for (int j = 0; j < G; ++j) {
         LT Bq, dBq;
-        planck_group(A.ptab, p, j, s_ed[j], s_ed[j + 1], Bq, dBq);
+        planck_group(A.ptab, p, j, s_ed, Bq, dBq);
         const LT Em = rE[j];
-        const LT tau = kl.cdts * (kT * s_ef[j]);
-        const LT dtau = tau * hh * p.invT;
+        const LT tau = ck * s_ef[j];
         const LT inv = frcp(LT(1) + tau);
         LT Eg = (Em + tau * Bq) * inv;
-        if (lin != LT(0)) Eg += (tau * dBq + dtau * (Bq - Eg)) * inv * lin;
+        if (lin != LT(0)) Eg += (tau * dBq + (tau * hi) * (Bq - Eg)) * inv * lin;
         float d, e;
         two_sum(Eg, -Em, d, e);
         pair_add(eh, el, d, e);

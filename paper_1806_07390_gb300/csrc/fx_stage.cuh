@@ -49,7 +49,7 @@ struct PlanckParams {
 // (L, h dL/du) with L = log2 Int_{eps_g-1/2/T}^{eps_g+1/2/T} t^3/(e^t-1) dt, built on the host in
 // FP64 and interpolated with cubic Hermite polynomials.
 struct PlanckTable {
-  const float4* tab;  // [G][nu]: (L - floor(L), h dL/du, floor(L), 0)
+  const float4* tab;  // [G][nu]: (L - floor(L), h dL/du, floor(L), 2^floor(L) or 0 below 2^-126)
   int nu;
   float u0;
 };
@@ -192,7 +192,7 @@ struct Coupler {
                        (3.0f * t2 - 2.0f * t3) * d1 + (t3 - t2) * p1.y;
       const float dLdt = (6.0f * t2 - 6.0f * t) * (p0.x - d1) + (3.0f * t2 - 4.0f * t + 1.0f) * p0.y +
                          (3.0f * t2 - 2.0f * t) * p1.y;
-      I = ldexpf(exp2f(Lr), (int)p0.z);
+      I = exp2f(Lr) * p0.w;
       dLdu = dLdt * float(PTAB_PER_OCT);
     }
     const float T2 = T * T, T3 = T2 * T;
@@ -596,7 +596,8 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     bool fl[3];
     const uint32_t gc_ = own_idx(k, fl);
     R val = A.in[gvar * ncell + gc_];
-    return (gvar >= 1 && gvar <= D && fl[gvar - 1]) ? -val : val;
+    const bool flip = (gvar == 1 && fl[0]) || (D >= 2 && gvar == 2 && fl[1]) || (D >= 3 && gvar == 3 && fl[2]);
+    return flip ? -val : val;
   };
   // store prefetched own values of plane k into slot `slot`; the cell's lane 0 gathers the gas
   // variables from lanes 0..NG-1 and forms the opacity factors
@@ -753,18 +754,20 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         }
       }
     }
-    // flux class of the gas variable of this lane and of each radiation variable
+    // flux class of the gas variable of this lane and of each radiation variable (selected by
+    // value: a lane-dependent array index would place the factor arrays in local memory)
     const int gcls = (gvar >= 1 && gvar <= 2 && gvar <= D) ? gvar : 0;
+    auto cls = [&](const R* f) { return gcls == 0 ? f[0] : (gcls == 1 ? f[1] : f[2]); };
     R gnet = R(0);
     if (cell_in) {  // (an overhanging cell's upper face would lie past the last face)
       const uint32_t fxk = face_x(k);
-      gnet = gface(0, gvar, fxk + 1) * fx_r[gcls] - gface(0, gvar, fxk) * fx_l[gcls];
+      gnet = gface(0, gvar, fxk + 1) * cls(fx_r) - gface(0, gvar, fxk) * cls(fx_l);
       if (D == 3) {
         const uint32_t fyk = face_y3(k);
         gnet = gnet + (gface(1, gvar, fyk + nx) * ty(T_FR, bc_pad(gy)) - gface(1, gvar, fyk) * ty(T_FL, bc_pad(gy)));
       }
       if (D >= 2)
-        gnet = gnet + (gface(MD, gvar, face_m(k + 1)) * fm_r[gcls] - gface(MD, gvar, face_m(k)) * fm_l[gcls]);
+        gnet = gnet + (gface(MD, gvar, face_m(k + 1)) * cls(fm_r) - gface(MD, gvar, face_m(k)) * cls(fm_l));
     }
     __syncthreads();
     R Q2[NGL][NRV];

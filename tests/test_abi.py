@@ -151,6 +151,9 @@ def test_fp32_planck_tables_interpolate_the_band_integrals(L):
     L.fx_debug_planck_table(h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n,
                             ctypes.byref(nu), ctypes.byref(u0))
     tab = buf.reshape(pb.ngroups, nu.value, 4).astype(np.float64)
+    # the fourth entry is the exact FP32 power of two 2^floor(L), or 0 below the normal range
+    want = np.where(tab[..., 2] >= -126, 2.0 ** tab[..., 2], 0.0)
+    assert np.array_equal(tab[..., 3], want)
     edges = pb.eps_min * (pb.eps_max / pb.eps_min) ** (np.arange(pb.ngroups + 1) / pb.ngroups)
     rng = np.random.default_rng(3)
     worst = 0.0
