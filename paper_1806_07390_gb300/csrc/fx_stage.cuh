@@ -375,6 +375,20 @@ __device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupCon
   return st;
 }
 
+// Asynchronous global -> shared copies of single elements (cp.async, sm_80 and later): the
+// stage kernel stages each march plane into shared memory one step ahead, without passing the
+// values through registers.  A thread's copies are complete, and visible to that thread, after
+// its wait; other threads see them after the next barrier.
+template <class R> __device__ __forceinline__ void cp_async(R* smem, const R* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(R) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Shared-memory layout of stage_kernel (offsets in elements of R; used by the kernel and by the
 // host to size the launch).
 template <int D, int TX, int TY>
@@ -383,7 +397,9 @@ struct StageLayout {
   static constexpr int PX = TX + 4, PY = (D == 3) ? TY + 4 : 1, PC = PX * PY;
   static constexpr int NSLOT = (D >= 2) ? 4 : 1, TC = TX * TY;
   static constexpr int NFX = (TX + 1) * TY, NFY = (D == 3) ? TX * (TY + 1) : 0;
-  int st, pk, rbx, rax, rby, ray, rfx, rfy, end;
+  int st, pk, rbx, rax, rby, ray, rfx, rfy, sg, sbr, sbg, end;
+  // (the face fluxes of C overwrite the left face states of B: each face's left state is read,
+  // and its flux written, by the thread that owns the face, between the same two barriers)
   __host__ __device__ explicit StageLayout(int G) {
     st = 0;
     pk = st + NSLOT * NRV * PC * G;       // radiation ring [slot][NRV][PC][G]
@@ -391,9 +407,12 @@ struct StageLayout {
     rax = rbx + NRV * NFX * G;            // left state of every x face [NRV][NFX][G]
     rby = rax + NRV * TY * G;             // right state of the last x face of each row
     ray = rby + NRV * NFY * G;            // left state of every y face (3-d)
-    rfx = ray + (D == 3 ? NRV * TX * G : 0);  // right state of the last y face (3-d)
-    rfy = rfx + NRV * NFX * G;            // radiation x-face fluxes [NRV][NFX][G]
-    end = rfy + NRV * NFY * G;            // radiation y-face fluxes (3-d)
+    sg = ray + (D == 3 ? NRV * TX * G : 0);  // right state of the last y face (3-d)
+    rfx = rbx;                            // radiation x-face fluxes [NRV][NFX][G]
+    rfy = rby;                            // radiation y-face fluxes (3-d)
+    sbr = sg + NSLOT * NG * PC;           // gas variables ring [slot][NG][PC]
+    sbg = sbr + NRV * TC * G;             // stage-2 base, radiation [NRV][TC][G]
+    end = sbg + NG * TC;                  // stage-2 base, gas [NG][TC]
   }
 };
 
@@ -463,6 +482,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   R* const ray = sm + L.ray;
   R* const rfx = sm + L.rfx;
   R* const rfy = sm + L.rfy;
+  R* const sgr = sm + L.sg;   // gas variables of the ring's planes
+  R* const sbr = sm + L.sbr;  // stage-2 base of the tile's cells (radiation), by plane parity
+  R* const sbg = sm + L.sbg;  // stage-2 base (gas)
   GroupConst* sgc = reinterpret_cast<GroupConst*>(
       (reinterpret_cast<uintptr_t>(sm + L.end) + 15) & ~static_cast<uintptr_t>(15));
   for (int i = tid; i < (int)(sizeof(GroupConst) / sizeof(int)); i += NTH)
@@ -495,6 +517,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   auto rad_at = [&](int slot, int v, int sc, int gg) -> R& {
     return st[((slot * NRV + v) * PC + sc) * G + gg];
   };
+  auto gas_at = [&](int slot, int v, int sc) -> R& { return sgr[(slot * NG + v) * PC + sc]; };
   // opacity factors K = kappa0 rho^a T^b and S = sigma0 rho of one cell from its gas variables
   const bool sph = (D == 2) && g.geom != 0;  // spherical (r, theta): x = r, march = theta
   // scale factor of component q of the cell with x index ix on plane k
@@ -526,7 +549,10 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       const uint32_t gc_ = map_cell(sx, sy, k, fl);
       R u[NG];
 #pragma unroll
-      for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + gc_];
+      for (int v = 0; v < NG; ++v) {
+        u[v] = A.in[v * ncell + gc_];
+        gas_at(slot, v, scell(sx, sy)) = u[v];
+      }
       opac(u, slot, scell(sx, sy), x0 + sx, k);
     }
     for (int t = tid; t < ncl * GP; t += NTH) {
@@ -592,27 +618,116 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     }
   };
   const int gvar = lane < NG ? lane : 0;
-  auto own_gas = [&](int k) -> R {
+  // ---- staging of plane P into ring slot P & 3 with cp.async, issued one march step before the
+  // plane is first read: the own cell's groups by their threads (lane 0 also copies the cell's gas
+  // variables, from which it forms the opacity factors after its wait), the in-plane halo as
+  // (cell, group) items, and the halo cells' gas variables one thread per cell.  Each thread later
+  // finishes what it copied itself: mirror flips of ghost cells, physical flux components on the
+  // spherical grid, and the opacity factors.
+  auto issue_plane = [&](int P) {
+    const int slot = P & 3;
     bool fl[3];
-    const uint32_t gc_ = own_idx(k, fl);
-    R val = A.in[gvar * ncell + gc_];
-    const bool flip = (gvar == 1 && fl[0]) || (D >= 2 && gvar == 2 && fl[1]) || (D >= 3 && gvar == 3 && fl[2]);
-    return flip ? -val : val;
-  };
-  // store prefetched own values of plane k into slot `slot`; the cell's lane 0 gathers the gas
-  // variables from lanes 0..NG-1 and forms the opacity factors
-  auto store_own = [&](int slot, R (*Q)[NRV], R gv, int k) {
+    const uint32_t gc_ = own_idx(P, fl);
 #pragma unroll
     for (int j = 0; j < NGL; ++j) {
       if (hasj[j]) {
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rad_at(slot, v, sc_own, gj[j]) = Q[j][v];
+        for (int v = 0; v < NRV; ++v)
+          cp_async(&rad_at(slot, v, sc_own, gj[j]), A.in + NG * ncell + (v * ncell + gc_) * G + gj[j]);
       }
     }
-    R u[NG];
+    if (lane == 0) {
 #pragma unroll
-    for (int v = 0; v < NG; ++v) u[v] = __shfl_sync(0xffffffffu, gv, v, GL);
-    if (lane == 0) opac(u, slot, sc_own, gx, k);
+      for (int v = 0; v < NG; ++v) cp_async(&gas_at(slot, v, sc_own), A.in + v * ncell + gc_);
+    }
+    for (int t = tid; t < NHALO * GP; t += NTH) {
+      const int i = t / GP, gg = t % GP;
+      if (gg >= G) continue;
+      int sx, sy;
+      halo_of(i, sx, sy);
+      bool f[3];
+      const uint32_t c = map_cell(sx, sy, P, f);
+      const int sc = scell(sx, sy);
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) cp_async(&rad_at(slot, v, sc, gg), A.in + NG * ncell + (v * ncell + c) * G + gg);
+    }
+    for (int i = tid; i < NHALO; i += NTH) {
+      int sx, sy;
+      halo_of(i, sx, sy);
+      bool f[3];
+      const uint32_t c = map_cell(sx, sy, P, f);
+#pragma unroll
+      for (int v = 0; v < NG; ++v) cp_async(&gas_at(slot, v, scell(sx, sy)), A.in + v * ncell + c);
+    }
+  };
+  auto finish_plane = [&](int P) {
+    const int slot = P & 3;
+    {
+      bool fl[3];
+      own_idx(P, fl);
+      if (fl[0] || fl[1] || fl[2] || sph) {
+#pragma unroll
+        for (int j = 0; j < NGL; ++j) {
+          if (hasj[j]) {
+#pragma unroll
+            for (int v = 1; v < NRV; ++v) {
+              R x = rad_at(slot, v, sc_own, gj[j]);
+              if (fl[v - 1]) x = -x;
+              if (sph) x *= frcp(hfac(v - 1, gx, P));  // physical component
+              rad_at(slot, v, sc_own, gj[j]) = x;
+            }
+          }
+        }
+      }
+      if (lane == 0) {
+        R u[NG];
+#pragma unroll
+        for (int v = 0; v < NG; ++v) u[v] = gas_at(slot, v, sc_own);
+        opac(u, slot, sc_own, gx, P);
+      }
+    }
+    for (int t = tid; t < NHALO * GP; t += NTH) {
+      const int i = t / GP, gg = t % GP;
+      if (gg >= G) continue;
+      int sx, sy;
+      halo_of(i, sx, sy);
+      bool f[3];
+      map_cell(sx, sy, P, f);
+      if (f[0] || f[1] || f[2] || sph) {
+        const int sc = scell(sx, sy);
+#pragma unroll
+        for (int v = 1; v < NRV; ++v) {
+          R x = rad_at(slot, v, sc, gg);
+          if (f[v - 1]) x = -x;
+          if (sph) x *= frcp(hfac(v - 1, x0 + sx, P));
+          rad_at(slot, v, sc, gg) = x;
+        }
+      }
+    }
+    for (int i = tid; i < NHALO; i += NTH) {
+      int sx, sy;
+      halo_of(i, sx, sy);
+      R u[NG];
+#pragma unroll
+      for (int v = 0; v < NG; ++v) u[v] = gas_at(slot, v, scell(sx, sy));
+      opac(u, slot, scell(sx, sy), x0 + sx, P);
+    }
+  };
+  // stage-2 base of the thread's cell on plane P, staged at the end of the previous step and read
+  // back by the same thread in D
+  auto base_r = [&](int v, int j) -> R& { return sbr[(v * TC + tcell) * G + gj[j]]; };
+  auto base_g = [&]() -> R& { return sbg[gvar * TC + tcell]; };
+  auto issue_base = [&](int P) {
+    if (A.base == nullptr || !cell_in) return;
+    const uint32_t c = D == 1 ? (uint32_t)gx : D == 2 ? (uint32_t)P * nx + gx : ((uint32_t)P * ny + gy) * nx + gx;
+#pragma unroll
+    for (int j = 0; j < NGL; ++j) {
+      if (hasj[j]) {
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) cp_async(&base_r(v, j), A.base + NG * ncell + (v * ncell + c) * G + gj[j]);
+      }
+    }
+    if (lane < NG) cp_async(&base_g(), A.base + gvar * ncell + c);
   };
 
   // radiation flux through a face along d: QL = left cell's upper-face state, QR = right cell's
@@ -663,29 +778,27 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     return __ldg(A.faces + (uint32_t)A.face_off[d] + v * nfd[d] + f);
   };
 
-  R Q0[NGL][NRV] = {}, Q1[NGL][NRV] = {}, Qn[NGL][NRV] = {};  // own values: plane k, k+1, prefetch
   R bm0[NGL][NRV] = {};                     // own march-direction upper-face states, plane k
   R rfm_old[NGL][NRV] = {};                 // radiation fluxes through the lower march face
-  R g0 = R(0), g1 = R(0), gn = R(0);        // own gas variable (lanes < NG): k, k+1, prefetch
-  R b0[NGL][NRV] = {}, bg0 = R(0);          // stage-2 base values of plane k
 
   // ---------------------------------------------------------------- prologue
   if (D == 1) {
     load_cells(0, 0, TX + 4, all_of);
-    own_rad(0, Q0);
-    g0 = own_gas(0);
+    issue_base(0);
+    cp_async_commit();
     __syncthreads();
   } else {
+    // planes kbeg-1 .. kbeg+1 directly; plane kbeg+2 and the stage-2 base of plane kbeg staged
     for (int k = kbeg - 1; k <= kbeg + 1; ++k) load_cells(k & 3, k, TC, interior_of);
-    R Qm1[NGL][NRV], Qm2[NGL][NRV];
+    for (int k = kbeg; k <= kbeg + 1; ++k) load_cells(k & 3, k, NHALO, halo_of);
+    issue_plane(kbeg + 2);
+    issue_base(kbeg);
+    cp_async_commit();
+    R Qm1[NGL][NRV], Qm2[NGL][NRV], Q0[NGL][NRV], Q1[NGL][NRV];
     own_rad(kbeg - 2, Qm2);
     own_rad(kbeg - 1, Qm1);
     own_rad(kbeg, Q0);
     own_rad(kbeg + 1, Q1);
-    own_rad(kbeg + 2, Qn);
-    g0 = own_gas(kbeg);
-    g1 = own_gas(kbeg + 1);
-    gn = own_gas(kbeg + 2);
     __syncthreads();
     // march reconstruction of planes kbeg-1 (upper face) and kbeg, and the face kbeg-1/2
     const MCCoef<R> mp = mc_coef(tm, bc_pad(kbeg - 1)), m0 = mc_coef(tm, bc_pad(kbeg));
@@ -700,14 +813,6 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
                rfm_old[j]);
     }
   }
-  if (A.base != nullptr && cell_in) {
-    const uint32_t c0 = D == 1 ? gx : D == 2 ? (uint32_t)kbeg * nx + gx : ((uint32_t)kbeg * ny + gy) * nx + gx;
-#pragma unroll
-    for (int v = 0; v < NRV; ++v)
-#pragma unroll
-      for (int j = 0; j < NGL; ++j) b0[j][v] = A.base[NG * ncell + (v * ncell + c0) * G + gj[j]];
-    bg0 = A.base[gvar * ncell + c0];
-  }
   const int ipx = bc_pad(gx);  // the x-direction table row of this cell
   // x-direction coefficients of this cell do not change along the march
   const MCCoef<R> mcx = mc_coef(tx, ipx);
@@ -716,13 +821,15 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   // ---------------------------------------------------------------- march
   for (int k = kbeg; k < kend; ++k) {
     const int s0 = k & 3;
-    // ---- A: plane k+2 (prefetched last step) and the in-plane halo of plane k.  Slot (k+2)&3
-    // held plane k-2, last read in step k-1 before its barrier C; halo positions of slot k are
-    // read only in this step.
-    if (D >= 2) {
-      store_own((k + 2) & 3, Qn, gn, k + 2);
-      load_cells(s0, k, NHALO, halo_of);
-    }
+    // ---- A: finish plane k+2 (staged during step k-1) and stage plane k+3.  Slot (k+3)&3 held
+    // plane k-1, last read in step k-1 before its barrier C; the warp barrier keeps the cell's
+    // lanes out of step k-1's D (which reads the cell's gas variables of plane k-1) before lane 0
+    // restages them.
+    cp_async_wait_all();
+    __syncwarp();
+    if (D >= 2) finish_plane(k + 2);
+    if (D >= 2 && k + 1 < kend) issue_plane(k + 3);
+    cp_async_commit();
     // gas face data of this plane: the cell's lower faces and the march face k+1/2
     const R vsx = gface(0, NG, face_x(k));
     const R vsx1 = (lx == TX - 1 && gx < nx) ? gface(0, NG, face_x(k) + 1) : R(0);
@@ -770,12 +877,16 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         gnet = gnet + (gface(MD, gvar, face_m(k + 1)) * cls(fm_r) - gface(MD, gvar, face_m(k)) * cls(fm_l));
     }
     __syncthreads();
-    R Q2[NGL][NRV];
+    // the own column of planes k, k+1, k+2 from the ring
+    R Q0[NGL][NRV], Q1[NGL][NRV], Q2[NGL][NRV];
 #pragma unroll
-    for (int j = 0; j < NGL; ++j)
-#pragma unroll
-      for (int v = 0; v < NRV; ++v) Q2[j][v] = Qn[j][v];
-    const R g2 = gn;  // own gas variable of plane k+2 (gn is refilled with plane k+3 below)
+    for (int j = 0; j < NGL; ++j) {
+      rad_cell(s0, sc_own, gj[j], Q0[j]);
+      if (D >= 2) {
+        rad_cell((k + 1) & 3, sc_own, gj[j], Q1[j]);
+        rad_cell((k + 2) & 3, sc_own, gj[j], Q2[j]);
+      }
+    }
     // ---- B: reconstructions
     R ax[NGL][NRV], bx[NGL][NRV], am1[NGL][NRV], bm1[NGL][NRV], ay[NGL][NRV], by[NGL][NRV];
 #pragma unroll
@@ -890,22 +1001,11 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         rad_face(MD, bm0[j], am1[j], chi_of(s0, sc_own, j), chi_of((k + 1) & 3, sc_own, j), ell_m, vsm, rfm_new[j]);
     }
     __syncthreads();
-    // prefetch: own values of plane k+3 and the stage-2 base of plane k+1
-    R b1[NGL][NRV] = {}, bg1 = R(0);
-    if (D >= 2 && k + 1 < kend) {
-      own_rad(k + 3, Qn);
-      gn = own_gas(k + 3);
-      if (A.base != nullptr && cell_in) {
-        const uint32_t c1 = D == 2 ? (uint32_t)(k + 1) * nx + gx : ((uint32_t)(k + 1) * ny + gy) * nx + gx;
-#pragma unroll
-        for (int v = 0; v < NRV; ++v)
-#pragma unroll
-          for (int j = 0; j < NGL; ++j) b1[j][v] = A.base[NG * ncell + (v * ncell + c1) * G + gj[j]];
-        bg1 = A.base[gvar * ncell + c1];
-      }
-    }
     // ---- D: update: divergence, RK combine, coupling, store
     {
+      const R g0 = gas_at(s0, gvar, sc_own);  // own gas variable of plane k (lanes < NG)
+#pragma unroll
+      for (int j = 0; j < NGL; ++j) rad_cell(s0, sc_own, gj[j], Q0[j]);  // (not live across C)
       const int ipy = gy + 2;
       R fyl = R(0), fyr = R(0);
       if (D == 3) { fyl = ty(T_FL, ipy); fyr = ty(T_FR, ipy); }
@@ -947,7 +1047,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       }
       // gas: lane v < NG updates variable v, then the segment shares the cell's gas state
       R ug = g0 + dt * (gsrc - gnet);
-      if (stage2) ug = KR.alpha * bg0 + KR.beta * ug;
+      if (stage2) ug = KR.alpha * base_g() + KR.beta * ug;
       // The FP32 forms leave the interaction to couple_kernel (one thread per cell: each FP64
       // instruction of the FP64 Newton serves 32 cells, and the scalar steps are not repeated by
       // the group lanes); their per-lane carrier type is R.
@@ -971,7 +1071,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
             if (D >= 2) net = net + (rfm_new[j][v] * fm_r[c] - rfm_old[j][v] * fm_l[c]);
             const R cov = (sph && v >= 1) ? Q0[j][v] * hq[v - 1] : Q0[j][v];  // covariant F
             R u1 = cov + dt * (rsrc[j][v] - net);
-            if (stage2) u1 = KR.alpha * b0[j][v] + KR.beta * u1;
+            if (stage2) u1 = KR.alpha * base_r(v, j) + KR.beta * u1;
             if (v == 0) E[j] = (CT)u1; else F[j][v - 1] = (CT)u1;
           }
         }
@@ -1038,21 +1138,20 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         if (stbits) atomicOr(A.status, stbits);
       }
     }
+    // stage the stage-2 base of plane k+1 (its buffer was last read above, by this thread)
+    if (k + 1 < kend) {
+      issue_base(k + 1);
+      cp_async_commit();
+    }
     // slide the march window
 #pragma unroll
     for (int j = 0; j < NGL; ++j) {
 #pragma unroll
       for (int v = 0; v < NRV; ++v) {
-        Q0[j][v] = Q1[j][v];
-        Q1[j][v] = Q2[j][v];
         bm0[j][v] = bm1[j][v];
         rfm_old[j][v] = (D >= 2) ? rfm_new[j][v] : R(0);
-        b0[j][v] = b1[j][v];
       }
     }
-    g0 = g1;
-    g1 = g2;
-    bg0 = bg1;
   }
 }
 
