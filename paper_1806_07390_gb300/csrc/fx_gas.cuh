@@ -20,12 +20,14 @@ __device__ __forceinline__ void gas_face_dir(const StageArgs<R>& A, int64_t f) {
   const auto& g = A.g;
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const int nd = DIR == 0 ? n0 : (DIR == 1 ? n1 : n2);
-  const int ex = n0 + (DIR == 0), ey = n1 + (DIR == 1);
-  const int64_t nf = (int64_t)ex * ey * (n2 + (DIR == 2));
-  if (f >= nf) return;
-  const int i0 = (int)(f % ex), i1 = (int)((f / ex) % ey), i2 = (int)(f / ((int64_t)ex * ey));
+  // 32-bit index arithmetic: the host keeps every state and face-buffer offset below 2^32
+  const uint32_t ex = (uint32_t)(n0 + (DIR == 0)), ey = (uint32_t)(n1 + (DIR == 1));
+  const uint32_t nf = ex * ey * (uint32_t)(n2 + (DIR == 2));
+  if (f >= (int64_t)nf) return;
+  const uint32_t uf = (uint32_t)f, q = uf / ex;
+  const int i0 = (int)(uf - q * ex), i1 = (int)(q % ey), i2 = (int)(q / ey);
   const int id = DIR == 0 ? i0 : (DIR == 1 ? i1 : i2);
-  const int64_t ncell = g.ncell;
+  const uint32_t ncell = (uint32_t)g.ncell;
   const auto& KR = A.k(R(0));
   // curvilinear grids: the cell scale factors turn covariant momentum into physical velocity
   const bool sph = g.geom != 0;
@@ -39,7 +41,7 @@ __device__ __forceinline__ void gas_face_dir(const StageArgs<R>& A, int64_t f) {
     bool flip = false;
     const int cd = min(max(bc_map(id - 2 + m, nd, g.bc_lo[DIR], g.bc_hi[DIR], flip), 0), nd - 1);
     const int c0 = DIR == 0 ? cd : i0, c1 = DIR == 1 ? cd : i1, c2 = DIR == 2 ? cd : i2;
-    const int64_t ci = ((int64_t)c2 * n1 + c1) * n0 + c0;
+    const uint32_t ci = ((uint32_t)c2 * n1 + c1) * n0 + c0;
     R u[NG];
 #pragma unroll
     for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + ci];
@@ -71,11 +73,11 @@ __device__ __forceinline__ void gas_face_dir(const StageArgs<R>& A, int64_t f) {
   }
   hllc<R, D>(KR.gamma, Lr, Rr, fl, vs);
   R* out = A.faces_out + A.face_off[DIR];
-  out[f] = fl[0];
+  out[uf] = fl[0];
 #pragma unroll
-  for (int q = 0; q < D; ++q) out[(int64_t)(1 + (DIR + q) % D) * nf + f] = fl[1 + q];
-  out[(int64_t)(NG - 1) * nf + f] = fl[1 + D];
-  out[(int64_t)NG * nf + f] = vs;
+  for (int c = 0; c < D; ++c) out[(uint32_t)(1 + (DIR + c) % D) * nf + uf] = fl[1 + c];
+  out[(uint32_t)(NG - 1) * nf + uf] = fl[1 + D];
+  out[(uint32_t)NG * nf + uf] = vs;
 }
 
 template <class R, int D>

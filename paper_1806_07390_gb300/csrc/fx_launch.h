@@ -38,7 +38,7 @@ template <class R, class NT> constexpr bool split_interaction() {
 template <class R, int D, int GP>
 inline size_t stage_smem_gp(int G) {
   constexpr int GL = GP / groups_per_lane(sizeof(R) == 4, GP);
-  return stage_smem_bytes<R, D, TileShape<D, GL>::TX, TileShape<D, GL>::TY>(G);
+  return stage_smem_bytes<R, D, TileShape<D, GL>::TX, TileShape<D, GL>::TY>(stage_gstride<D, GP>(G));
 }
 template <class R, int D>
 inline size_t stage_smem(int GP, int G) {
@@ -59,7 +59,7 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
   constexpr int GL = GP / NGL;
   using TS = TileShape<D, GL>;
   auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL>;
-  const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(a.g.G);
+  const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(a.g.G));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,

@@ -416,6 +416,10 @@ struct StageLayout {
   }
 };
 
+// Group stride of stage_kernel's shared arrays (see there).
+template <int D, int GP> __host__ __device__ constexpr int stage_gstride(int G) { return D <= 2 ? GP : G; }
+
+// Shared memory of stage_kernel for a group stride GS (stage_gstride).
 template <class R, int D, int TX, int TY>
 inline size_t stage_smem_bytes(int G) {
   StageLayout<D, TX, TY> L(G);
@@ -473,7 +477,10 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* const sm = reinterpret_cast<R*>(smem_raw);
-  const LY L(G);
+  // group stride of the shared arrays: the padded group count GP in 1-d and 2-d (constant strides
+  // fold into the shared-memory addressing), the group count in 3-d (whose tile is large)
+  const int GS = stage_gstride<D, GP>(G);
+  const LY L(GS);
   R* const st = sm + L.st;
   R* const pk = sm + L.pk;
   R* const rbx = sm + L.rbx;
@@ -515,7 +522,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   };
   auto scell = [&](int sx, int sy) -> int { return (D == 3 ? (sy + 2) * PX : 0) + sx + 2; };
   auto rad_at = [&](int slot, int v, int sc, int gg) -> R& {
-    return st[((slot * NRV + v) * PC + sc) * G + gg];
+    return st[((slot * NRV + v) * PC + sc) * GS + gg];
   };
   auto gas_at = [&](int slot, int v, int sc) -> R& { return sgr[(slot * NG + v) * PC + sc]; };
   // opacity factors K = kappa0 rho^a T^b and S = sigma0 rho of one cell from its gas variables
@@ -715,7 +722,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   };
   // stage-2 base of the thread's cell on plane P, staged at the end of the previous step and read
   // back by the same thread in D
-  auto base_r = [&](int v, int j) -> R& { return sbr[(v * TC + tcell) * G + gj[j]]; };
+  auto base_r = [&](int v, int j) -> R& { return sbr[(v * TC + tcell) * GS + gj[j]]; };
   auto base_g = [&]() -> R& { return sbg[gvar * TC + tcell]; };
   auto issue_base = [&](int P) {
     if (A.base == nullptr || !cell_in) return;
@@ -898,7 +905,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       recon_rad(mcx, Qa, Q0[j], Qb, ax[j], bx[j]);
       if (hasj[j]) {
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1) + lx + 1) * G + gg] = bx[j][v];
+        for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1) + lx + 1) * GS + gg] = bx[j][v];
       }
       if (lx == 0) {  // halo cell -1: its upper-face state is the left state of face 0
         R Qc[NRV], ta[NRV], tb[NRV];
@@ -906,7 +913,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         recon_rad(mc_coef(tx, bc_pad(gx - 1)), Qc, Qa, Q0[j], ta, tb);
         if (hasj[j]) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * G + gg] = tb[v];
+          for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * GS + gg] = tb[v];
         }
       }
       if (lx == TX - 1) {  // halo cell TX: its lower-face state is the right state of face TX
@@ -915,7 +922,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         recon_rad(mc_coef(tx, bc_pad(gx + 1)), Q0[j], Qb, Qc, ta, tb);
         if (hasj[j]) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * G + gg] = ta[v];
+          for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * GS + gg] = ta[v];
         }
       }
       if (D == 3) {
@@ -925,7 +932,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         recon_rad(mc_coef(ty, bc_pad(gy)), Qa3, Q0[j], Qb3, ay[j], by[j]);
         if (hasj[j]) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rby[(v * NFY + (ly + 1) * TX + lx) * G + gg] = by[j][v];
+          for (int v = 0; v < NRV; ++v) rby[(v * NFY + (ly + 1) * TX + lx) * GS + gg] = by[j][v];
         }
         if (ly == 0) {
           R Qc[NRV], ta[NRV], tb[NRV];
@@ -933,7 +940,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           recon_rad(mc_coef(ty, bc_pad(gy - 1)), Qc, Qa3, Q0[j], ta, tb);
           if (hasj[j]) {
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) rby[(v * NFY + lx) * G + gg] = tb[v];
+            for (int v = 0; v < NRV; ++v) rby[(v * NFY + lx) * GS + gg] = tb[v];
           }
         }
         if (ly == TY - 1) {
@@ -942,7 +949,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           recon_rad(mc_coef(ty, bc_pad(gy + 1)), Q0[j], Qb3, Qc, ta, tb);
           if (hasj[j]) {
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) ray[(v * TX + lx) * G + gg] = ta[v];
+            for (int v = 0; v < NRV; ++v) ray[(v * TX + lx) * GS + gg] = ta[v];
           }
         }
       }
@@ -959,20 +966,20 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         const int fx = ly * (TX + 1) + lx;
         R QL[NRV], out[NRV];
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) QL[v] = rbx[(v * NFX + fx) * G + gg];
+        for (int v = 0; v < NRV; ++v) QL[v] = rbx[(v * NFX + fx) * GS + gg];
         rad_face(0, QL, ax[j], chi_of(s0, sc_own - 1, j), chi_of(s0, sc_own, j), ellx, vsx, out);
         if (hasj[j]) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx) * G + gg] = out[v];
+          for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx) * GS + gg] = out[v];
         }
         if (lx == TX - 1) {
           R QR[NRV];
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) QR[v] = rax[(v * TY + ly) * G + gg];
+          for (int v = 0; v < NRV; ++v) QR[v] = rax[(v * TY + ly) * GS + gg];
           rad_face(0, bx[j], QR, chi_of(s0, sc_own, j), chi_of(s0, sc_own + 1, j), tx(T_ELL, ipx + 1), vsx1, out);
           if (hasj[j]) {
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx + 1) * G + gg] = out[v];
+            for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx + 1) * GS + gg] = out[v];
           }
         }
       }
@@ -980,20 +987,20 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         const int fy = ly * TX + lx;
         R QL[NRV], out[NRV];
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) QL[v] = rby[(v * NFY + fy) * G + gg];
+        for (int v = 0; v < NRV; ++v) QL[v] = rby[(v * NFY + fy) * GS + gg];
         rad_face(1, QL, ay[j], chi_of(s0, sc_own - PX, j), chi_of(s0, sc_own, j), ty(T_ELL, bc_pad(gy)), vsy, out);
         if (hasj[j]) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy) * G + gg] = out[v];
+          for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy) * GS + gg] = out[v];
         }
         if (ly == TY - 1) {
           R QR[NRV];
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) QR[v] = ray[(v * TX + lx) * G + gg];
+          for (int v = 0; v < NRV; ++v) QR[v] = ray[(v * TX + lx) * GS + gg];
           rad_face(1, by[j], QR, chi_of(s0, sc_own, j), chi_of(s0, sc_own + PX, j), ty(T_ELL, bc_pad(gy + 1)), vsy1, out);
           if (hasj[j]) {
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy + TX) * G + gg] = out[v];
+            for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy + TX) * GS + gg] = out[v];
           }
         }
       }
@@ -1066,8 +1073,8 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           for (int v = 0; v < NRV; ++v) {
             const int c = v <= 2 ? v : 0;
             const int gg = gj[j];
-            R net = rfx[(v * NFX + fxa + 1) * G + gg] * fx_r[c] - rfx[(v * NFX + fxa) * G + gg] * fx_l[c];
-            if (D == 3) net = net + (rfy[(v * NFY + fya + TX) * G + gg] * fyr - rfy[(v * NFY + fya) * G + gg] * fyl);
+            R net = rfx[(v * NFX + fxa + 1) * GS + gg] * fx_r[c] - rfx[(v * NFX + fxa) * GS + gg] * fx_l[c];
+            if (D == 3) net = net + (rfy[(v * NFY + fya + TX) * GS + gg] * fyr - rfy[(v * NFY + fya) * GS + gg] * fyl);
             if (D >= 2) net = net + (rfm_new[j][v] * fm_r[c] - rfm_old[j][v] * fm_l[c]);
             const R cov = (sph && v >= 1) ? Q0[j][v] * hq[v - 1] : Q0[j][v];  // covariant F
             R u1 = cov + dt * (rsrc[j][v] - net);
@@ -1093,7 +1100,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         const uint32_t row = D == 1 ? 0u : D == 2 ? (uint32_t)k : (uint32_t)k * ny + gy;
 #pragma unroll
         for (int j = 0; j < NGL; ++j)
-          if (hasj[j]) A.phi_out[row * G + gj[j]] = rfx[(0 * NFX + fxa + 1) * G + gj[j]] * A.phi_area;
+          if (hasj[j]) A.phi_out[row * G + gj[j]] = rfx[(0 * NFX + fxa + 1) * GS + gj[j]] * A.phi_area;
       }
       unsigned stbits = 0;
       CT Tst = CT(0);
