@@ -98,8 +98,46 @@ __device__ __forceinline__ void planck_group(const PlanckTable& ptab, const Plan
   dB = fmaf(t, dLdu, 4.0f * t);  // d/dT (T^4 I) = T^3 I (4 + d ln I / d ln T)
 }
 
+// Copy between a contiguous run of nc*G floats in global memory (nc cells of G groups) and the
+// block's per-cell shared rows (stride RS): coalesced, in float4 units when the run is 16-byte
+// aligned and G is a multiple of 4 (a float4 then never straddles two rows).
+template <bool TO_SHARED>
+__device__ __forceinline__ void stage_rows(float* gmem, float* rows, int nc, int G, int RS) {
+  const int t = threadIdx.x;
+  if (G % 4 == 0 && (reinterpret_cast<uintptr_t>(gmem) & 15) == 0) {
+    const int G4 = G / 4, tot = nc * G4;
+    const int q0 = CPL_THREADS / G4, r0 = CPL_THREADS - q0 * G4;
+    int row = t / G4, c4 = t - row * G4;
+    float4* g4 = reinterpret_cast<float4*>(gmem);
+    for (int e = t; e < tot; e += CPL_THREADS) {
+      float* r = rows + row * RS + 4 * c4;
+      if (TO_SHARED) {
+        const float4 x = g4[e];
+        r[0] = x.x; r[1] = x.y; r[2] = x.z; r[3] = x.w;
+      } else {
+        g4[e] = make_float4(r[0], r[1], r[2], r[3]);
+      }
+      row += q0;
+      c4 += r0;
+      if (c4 >= G4) { c4 -= G4; ++row; }
+    }
+  } else {
+    const int tot = nc * G;
+    const int q0 = CPL_THREADS / G, r0 = CPL_THREADS - q0 * G;
+    int row = t / G, gg = t - row * G;
+    for (int e = t; e < tot; e += CPL_THREADS) {
+      if (TO_SHARED) rows[row * RS + gg] = gmem[e];
+      else gmem[e] = rows[row * RS + gg];
+      row += q0;
+      gg += r0;
+      if (gg >= G) { gg -= G; ++row; }
+    }
+  }
+}
+
+// (six resident blocks per SM with the FP64 Newton, whose latency wants warps: 85 registers)
 template <int D, class NT>
-__global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A) {
+__global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 1) couple_kernel(StageArgs<float> A) {
   using LT = float;
   constexpr int NG = 2 + D, NRV = 1 + D;
   const DevGrid& g = A.g;
@@ -121,23 +159,10 @@ __global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A)
     if (j < G) s_ef[j] = A.gc->efac32[j];
     s_ed[j] = A.gc->edge32[j];
   }
-  // the block's radiation rows: coalesced reads of the contiguous range [c0 G, (c0 + nc) G) of
-  // each moment, scattered into per-cell rows
-  {
-    const int tot = nc * G;
-    const int q0 = CPL_THREADS / G, r0 = CPL_THREADS - q0 * G;
-    for (int v = 0; v < NRV; ++v) {
-      const float* src = A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G;
-      float* dst = srow + v * CPL_THREADS * RS;
-      int row = t / G, gg = t - row * G;
-      for (int e = t; e < tot; e += CPL_THREADS) {
-        dst[row * RS + gg] = src[e];
-        row += q0;
-        gg += r0;
-        if (gg >= G) { gg -= G; ++row; }
-      }
-    }
-  }
+  // the block's radiation rows: the contiguous range [c0 G, (c0 + nc) G) of each moment
+#pragma unroll
+  for (int v = 0; v < NRV; ++v)
+    stage_rows<true>(A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, srow + v * CPL_THREADS * RS, nc, G, RS);
   float rho_f = 1.0f, m_f[3] = {0.0f, 0.0f, 0.0f}, rhoe_f = 1.0f;
   if (act) {
     rho_f = A.out[cid];
@@ -296,8 +321,9 @@ __global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A)
     const LT Tst = (LT)(Tm + dl);
     if (A.tstar_out != nullptr) A.tstar_out[cid] = Tst;
 
-    // ---- the accepted group energies, and the group sum of their changes as a float pair
-    // (each change split exactly by TwoSum, the sum keeping its rounding errors)
+    // ---- the accepted group energies, and the group sum of their changes as a float pair (the
+    // sum keeps its rounding errors, so the gas energy update sees the changes summed to about
+    // twice FP32 precision)
     float eh = 0.0f, el = 0.0f;
     {
       const LT Ta = (LT)(Tm + dacc);
@@ -312,15 +338,16 @@ __global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A)
         const LT inv = frcp(LT(1) + tau);
         LT Eg = (Em + tau * Bq) * inv;
         if (lin != LT(0)) Eg += (tau * dBq + (tau * hi) * (Bq - Eg)) * inv * lin;
-        float d, e;
-        two_sum(Eg, -Em, d, e);
-        pair_add(eh, el, d, e);
+        float s, e;
+        two_sum(eh, Eg - Em, s, e);
+        eh = s;
+        el += e;
         rE[j] = Eg;
       }
     }
     // ---- flux absorption at the converged temperature (Eq. 28) and the group sums of the flux
-    // changes
-    float fh[3] = {0.0f, 0.0f, 0.0f}, fl[3] = {0.0f, 0.0f, 0.0f};
+    // changes (in FP32: they reach the gas momentum and energy scaled by 1/c^2, Eqs. 31-32)
+    float fh[3] = {0.0f, 0.0f, 0.0f};
     {
       const LT kT = Kc * hpow(Tst, g.kap_T_h);
       for (int j = 0; j < G; ++j) {
@@ -330,9 +357,7 @@ __global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A)
           float* rF = srow + ((1 + q) * CPL_THREADS + t) * RS;
           const LT Fq = rF[j];
           const LT Fn = Fq * fac;
-          float d, e;
-          two_sum(Fn, -Fq, d, e);
-          pair_add(fh[q], fl[q], d, e);
+          fh[q] += Fn - Fq;
           rF[j] = Fn;
         }
       }
@@ -343,7 +368,7 @@ __global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A)
     NT work = NT(0);
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-      const NT SdF = (NT)fh[q] + (NT)fl[q];
+      const NT SdF = (NT)fh[q];
       const NT mq = (NT)m_f[q];
       work += (sph ? mq / (h[q] * h[q]) : mq) * ir * SdF;
       m_f[q] = (float)(mq - SdF * kn.ic2);
@@ -365,22 +390,10 @@ __global__ void __launch_bounds__(CPL_THREADS) couple_kernel(StageArgs<float> A)
     if (st) atomicOr(A.status, st);
   }
   __syncthreads();
-  // write the rows back: coalesced stores of each moment's contiguous range
-  {
-    const int tot = nc * G;
-    const int q0 = CPL_THREADS / G, r0 = CPL_THREADS - q0 * G;
-    for (int v = 0; v < NRV; ++v) {
-      float* dst = A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G;
-      const float* src = srow + v * CPL_THREADS * RS;
-      int row = t / G, gg = t - row * G;
-      for (int e = t; e < tot; e += CPL_THREADS) {
-        dst[e] = src[row * RS + gg];
-        row += q0;
-        gg += r0;
-        if (gg >= G) { gg -= G; ++row; }
-      }
-    }
-  }
+  // write the rows back
+#pragma unroll
+  for (int v = 0; v < NRV; ++v)
+    stage_rows<false>(A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, srow + v * CPL_THREADS * RS, nc, G, RS);
 }
 
 }  // namespace fx

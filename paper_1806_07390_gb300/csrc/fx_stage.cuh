@@ -122,25 +122,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   const float bv = s - a;
   e = (a - (s - bv)) + (b - bv);
 }
-// Adds a + b into the unevaluated pair (hi, lo), keeping the rounding error of the leading part.
-__device__ __forceinline__ void pair_add(float& hi, float& lo, float a, float b) {
-  float s, e;
-  two_sum(hi, a, s, e);
-  hi = s;
-  lo = (lo + b) + e;
-}
-// Segment sum of unevaluated float pairs hi + lo by cascaded TwoSum (the summation of Ogita, Rump
-// and Oishi, 2005): the result is as accurate as a sum carried in twice FP32's precision, at FP32
-// cost.  TwoSum's error term is exact, hence symmetric in its operands, so every lane of the
-// segment ends with the same pair.
-template <int GP> __device__ __forceinline__ void seg_sum2(float& hi, float& lo) {
-#pragma unroll
-  for (int o = GP / 2; o >= 1; o >>= 1) {
-    const float oh = __shfl_xor_sync(0xffffffffu, hi, o, GP);
-    const float ol = __shfl_xor_sync(0xffffffffu, lo, o, GP);
-    pair_add(hi, lo, oh, ol);
-  }
-}
 
 // ---------------------------------------------------------------------------------------------
 // Cell-local implicit interaction (Sec. 5.3): inner backward-Euler group update (Eq. 25) inside
