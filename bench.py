@@ -32,10 +32,11 @@ from paper_1806_07390_gb300 import workloads as W  # noqa: E402
 
 METRIC = "zone-group updates/s per RK stage"
 UNIT = "zone-group-stages/s"
-# DRAM bytes per radiation/update kernel launch (mean of the two RK stages) from the committed
-# ncu capture profiles/traffic_stage_kernel_kh2d_1024x1024x16.txt; None where not captured for
-# the current kernels.
-TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": None, "fp32": None, "fp64": None}}
+# DRAM bytes per launch (mean of the two RK stages) of the radiation/update kernel and of the
+# interaction kernel, from the committed ncu capture profiles/traffic_stage_kernel_kh2d_1024x1024x16.txt;
+# None where not captured for the current kernels.
+TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": 561.9e6, "fp32": 561.5e6, "fp64": 1211.8e6}}
+TRAFFIC_INTERACTION = {"kh2d": {"fp32n64": 372.4e6, "fp32": 370.8e6}}
 
 
 def load_peaks():
@@ -415,7 +416,8 @@ def main():
             out["interaction_kernel"] = {
                 "kernel": "couple_kernel (interaction, one thread per cell)",
                 "bytes_per_launch": cb, "avg_launch_ms": cs * 1e3, "achieved": cb / cs / 1e9,
-                "frac": cb / cs / 1e9 / peak, "share_of_step": kt["couple_ms"] / total}
+                "frac": cb / cs / 1e9 / peak, "share_of_step": kt["couple_ms"] / total,
+                "traffic": TRAFFIC_INTERACTION.get(args.workload, {}).get(kind)}
         return out
 
     e2e_steps = max(5, args.steps // 4)

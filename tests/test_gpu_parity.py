@@ -135,6 +135,22 @@ def test_fp32_forms_odd_group_counts(fxmod, form, G):
     H.assert_parity(pb, got, ref, 1e-4, natural=True)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32", 1e-5), ("fp32n64", 1e-5)])
+def test_rayleigh_jeans_groups(fxmod, precision, tol):
+    # every group far below kT (eps/T < 2^-14 at all band edges): the FP32 Planck path leaves its
+    # tables for the series x^3/3 - x^4/8 of each band (whose upper edge is the group's own), the
+    # FP64 path takes its small-x series
+    pb, prim = W.kh_2d(nx=24, ny=20, ngroups=6, nsteps=3, precision=precision)
+    pb.eps_min, pb.eps_max = 1e-6, 1e-5
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    if precision == "fp64":
+        H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
+    else:
+        H.assert_parity(pb, got, ref, tol, natural=True)
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32", 1e-4), ("fp32n64", 1e-4)])
 def test_kh2d_full_size_sampled_windows(fxmod, precision, tol):
     # 1024^2 x 16 groups, one step in the benchmark's launch configuration; windows of 8x8 cells
