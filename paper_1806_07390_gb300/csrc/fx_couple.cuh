@@ -135,9 +135,10 @@ __device__ __forceinline__ void stage_rows(float* gmem, float* rows, int nc, int
   }
 }
 
-// (six resident blocks per SM with the FP64 Newton, whose latency wants warps: 85 registers)
+// (six resident blocks per SM with the FP64 Newton, whose latency wants warps: 85 registers;
+// the all-FP32 kernel needs fewer registers unconstrained)
 template <int D, class NT>
-__global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 1) couple_kernel(StageArgs<float> A) {
+__global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_kernel(StageArgs<float> A) {
   using LT = float;
   constexpr int NG = 2 + D, NRV = 1 + D;
   const DevGrid& g = A.g;

@@ -8,9 +8,11 @@
 
 namespace fx {
 
-// Groups per lane of the stage kernel: two in the FP32 forms when a cell has more than 8
-// groups (GP >= 16), else one.  GP = next power of two >= G is the cell's padded group count.
-constexpr int groups_per_lane(bool fp32, int GP) { return (fp32 && GP >= 16) ? 2 : 1; }
+// Groups per lane of the stage kernel: two in the FP32 forms when a cell has more than 16
+// groups (GP = 32), else one.  GP = next power of two >= G is the cell's padded group count.
+// (With one group per lane a 256-thread tile holds 256/GP cells: at GP = 32 that is 8 cells and
+// a large halo share; below, one group per lane runs three blocks per SM and is the faster.)
+constexpr int groups_per_lane(bool fp32, int GP) { return (fp32 && GP >= 32) ? 2 : 1; }
 
 // Tile shape of the stage kernel for D dimensions and GL lanes per cell (256 threads per block).
 template <int D, int GL> struct TileShape {

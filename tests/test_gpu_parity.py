@@ -125,9 +125,10 @@ def test_fp32_form_small(fxmod, maker, tol, form):
 
 
 @pytest.mark.parametrize("form", ["fp32", "fp32n64"])
-@pytest.mark.parametrize("G", [9, 13])
+@pytest.mark.parametrize("G", [9, 13, 21])
 def test_fp32_forms_odd_group_counts(fxmod, form, G):
-    # two groups per lane with an odd group count: the last lane of each cell owns one group
+    # odd group counts: padded lanes of each cell (G = 9, 13: one group per lane), and two groups
+    # per lane with one group in the cell's last lane (G = 21, 32 padded groups)
     pb, prim = W.kh_2d(nx=44, ny=38, ngroups=G, nsteps=3, precision=form)
     got, st, _ = run_gpu(fxmod, pb, prim)
     ref, rst = run_oracle(pb, prim)
