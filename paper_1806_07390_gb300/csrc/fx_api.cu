@@ -943,19 +943,9 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
     h->ptab_u0 = T.u0;
   }
 
-  // chunk length along the march axis
-  // (32 planes; halved down to 8 while the grid would give fewer than two waves of blocks at
-  // three resident blocks on each of 152 SMs: short chunks re-read more halo planes)
-  if (P.dims >= 2) {
-    const int nm = (int)P.n[P.dims - 1];
-    const int TC = 256 / (h->GP / groups_per_lane(h->elem == 4, h->GP));  // cells per tile
-    const int TX = P.dims == 3 ? (TC >= 16 ? TC / 4 : TC / 2) : TC, TY = TC / TX;
-    int64_t tiles = (P.n[0] + TX - 1) / TX;
-    if (P.dims == 3) tiles *= (P.n[1] + TY - 1) / TY;
-    int chunk = 32;
-    while (chunk > 8 && tiles * ((nm + chunk - 1) / chunk) < 2 * 3 * 152) chunk /= 2;
-    h->chunk = std::min(nm, chunk);
-  }
+  // chunk length along the march axis: 32 planes until the workspace is bound, where it is fitted
+  // to the device (choose_chunk)
+  if (P.dims >= 2) h->chunk = std::min((int)P.n[P.dims - 1], 32);
   // workspace layout
   size_t off = 0;
   h->off_status = off; off = align_up(off + 64);
@@ -1100,6 +1090,45 @@ fx_status fx_state_set_density(fx_grid* h, const void* rho, int rho_precision, i
   return FX_OK;
 }
 
+// March chunk of the stage kernel (planes per block), fitted to the bound device: it minimises
+// (waves of blocks) x (planes per block + the prologue's share), with the device's multiprocessor
+// count and the kernel's resident blocks per multiprocessor.  A grid that overshoots a whole
+// number of waves by a little runs its last wave mostly empty; longer chunks spread the
+// prologue (three planes loaded, two march reconstructions) over more planes.
+fx_status choose_chunk(fx_grid* h) {
+  if (h->D < 2) return FX_OK;
+  int dev = 0, nsm = 0, nb = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    const int p = h->P.precision;
+    if (h->D == 2)
+      e = p == FX_FP64 ? stage_blocks_per_sm<double, 2, double>(h->GP, h->G, &nb)
+        : p == FX_FP32 ? stage_blocks_per_sm<float, 2, float>(h->GP, h->G, &nb)
+                       : stage_blocks_per_sm<float, 2, double>(h->GP, h->G, &nb);
+    else
+      e = p == FX_FP64 ? stage_blocks_per_sm<double, 3, double>(h->GP, h->G, &nb)
+        : p == FX_FP32 ? stage_blocks_per_sm<float, 3, float>(h->GP, h->G, &nb)
+                       : stage_blocks_per_sm<float, 3, double>(h->GP, h->G, &nb);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
+  const int nm = (int)h->P.n[h->D - 1];
+  const int TC = 256 / (h->GP / groups_per_lane(h->elem == 4, h->GP));  // cells per tile
+  const int TX = h->D == 3 ? (TC >= 16 ? TC / 4 : TC / 2) : TC, TY = TC / TX;
+  int64_t tiles = (h->P.n[0] + TX - 1) / TX;
+  if (h->D == 3) tiles *= (h->P.n[1] + TY - 1) / TY;
+  const double slots = (double)std::max(nsm, 1) * std::max(nb, 1);
+  double best = 1e300;
+  int bc = std::min(nm, 32);
+  for (int c = 8; c <= std::min(nm, 128); ++c) {
+    const double waves = std::ceil((double)(tiles * ((nm + c - 1) / c)) / slots);
+    const double cost = waves * (c + 1.5);
+    if (cost < best) { best = cost; bc = c; }
+  }
+  h->chunk = bc;
+  return FX_OK;
+}
+
 fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_stream) {
   if (!h) return FX_ERR_ARG;
   if (!dev_ptr || bytes < h->ws_bytes || (reinterpret_cast<uintptr_t>(dev_ptr) % kAlign) != 0)
@@ -1113,6 +1142,10 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
   }
   e = cudaMemsetAsync(h->ws + h->off_status, 0, 64, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
+  {
+    const fx_status cs = choose_chunk(h);
+    if (cs != FX_OK) return cs;
+  }
   for (int d = 0; d < h->D; ++d) {
     const std::vector<double>& T = h->tab[d];
     if (h->elem == 8) {

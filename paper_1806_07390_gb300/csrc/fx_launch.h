@@ -30,6 +30,11 @@ template <class R, int D, class NT>
 cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid,
                          cudaEvent_t mid2);
 
+// Resident blocks per multiprocessor of the stage kernel for GP padded groups and G groups
+// (the CUDA occupancy calculator; the host sizes the march chunks from it).
+template <class R, int D, class NT>
+cudaError_t stage_blocks_per_sm(int GP, int G, int* nb);
+
 // Whether the interaction runs in couple_kernel rather than inside the stage kernel: in both
 // forms with an FP32 state.
 template <class R, class NT> constexpr bool split_interaction() {
@@ -104,6 +109,30 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
     }
   }
   return e;
+}
+
+template <class R, int D, int GP, class NT>
+static cudaError_t blocks_gp(int G, int* nb) {
+  constexpr int NGL = groups_per_lane(sizeof(R) == 4, GP);
+  constexpr int GL = GP / NGL;
+  using TS = TileShape<D, GL>;
+  auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL>;
+  const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(G));
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, TS::TX * TS::TY * GL, smem);
+}
+
+template <class R, int D, class NT>
+cudaError_t stage_blocks_per_sm(int GP, int G, int* nb) {
+  switch (GP) {
+    case 8: return blocks_gp<R, D, 8, NT>(G, nb);
+    case 16: return blocks_gp<R, D, 16, NT>(G, nb);
+    case 32: return blocks_gp<R, D, 32, NT>(G, nb);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <class R, int D, class NT>

@@ -6,4 +6,5 @@
 namespace fx {
 template cudaError_t launch_stage<float, 1, float>(const StageArgs<float>&, int, cudaStream_t, cudaEvent_t,
                                                   cudaEvent_t);
+template cudaError_t stage_blocks_per_sm<float, 1, float>(int, int, int*);
 }  // namespace fx
