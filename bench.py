@@ -425,6 +425,7 @@ def main():
         e2e_sec, h2d, d2h = float("nan"), 0, 0
     else:
         e2e_sec, h2d, d2h = time_e2e(gh, pbh, e2e_steps, 2)
+    chunk_h = gh.march_chunk()
     gh.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -436,7 +437,8 @@ def main():
                        "l2": ("inputs larger than L2 (no flush)"
                               if pbh.state_size() * (8 if head == "fp64" else 4) * 2 > 129e6
                               else "state fits in L2 (no flush): L2-resident figure"),
-                       "precision": head, "parallelism": f"replicas{world}"},
+                       "precision": head, "parallelism": f"replicas{world}",
+                       "march_chunk": chunk_h},
             "roofline": roofline(head, kth),
             "e2e": {"value": world * zg * 2 * e2e_steps / e2e_sec, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

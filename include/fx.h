@@ -149,6 +149,12 @@ fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is
  * interaction kernel; and the objective's reduction while it is enabled). */
 int fx_launches_per_step(const fx_grid* h);
 
+/* Planes of the slowest axis that one block of the radiation/update kernel marches over: 32 (or
+ * the axis length) until the workspace is bound, then fitted to the bound device by
+ * fx_bind_workspace (fewest waves of blocks times planes per block).  0 for 1-d grids, -1 for a
+ * null handle. */
+int fx_march_chunk(const fx_grid* h);
+
 /* Per-kernel device timing (instrumentation, not part of the method).  While enabled, every
  * stage that fx_step enqueues records four CUDA events on the bound stream: before the gas face
  * kernel, after it, after the radiation/update kernel, and after the interaction kernel (which

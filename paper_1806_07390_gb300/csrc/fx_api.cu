@@ -990,6 +990,8 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
 
 size_t fx_state_elems(const fx_grid* h) { return h ? (size_t)h->ncell * h->NV : 0; }
 
+int fx_march_chunk(const fx_grid* h) { return h ? (h->D >= 2 ? h->chunk : 0) : -1; }
+
 int fx_launches_per_step(const fx_grid* h) {
   if (!h) return 0;
   const bool split = h->P.precision != FX_FP64 && h->P.couple;

@@ -27,7 +27,7 @@ NTOTALS = 6
 # every symbol include/fx.h declares
 EXPORTS = ["fx_grid_create", "fx_bind_workspace", "fx_state_elems", "fx_state_upload",
            "fx_state_init_equilibrium", "fx_step", "fx_sync", "fx_conserved_totals",
-           "fx_state_download", "fx_launches_per_step", "fx_debug_table", "fx_debug_ntab",
+           "fx_state_download", "fx_launches_per_step", "fx_march_chunk", "fx_debug_table", "fx_debug_ntab",
            "fx_debug_planck_table", "fx_state_init_equilibrium_noalloc",
            "fx_kernel_timing_enable", "fx_kernel_timing_read", "fx_objective_enable",
            "fx_boundary_energy_out", "fx_set_kappa0", "fx_state_set_density",
@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
         L.fx_conserved_totals.argtypes = [vp, dp]
         L.fx_state_download.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
         L.fx_launches_per_step.argtypes = [vp]
+        L.fx_march_chunk.argtypes = [vp]
         L.fx_debug_table.argtypes = [vp, ctypes.c_int, dp, sz]
         L.fx_debug_ntab.argtypes = []
         L.fx_debug_planck_table.argtypes = [vp, ctypes.POINTER(ctypes.c_float), sz,
@@ -227,6 +228,10 @@ class Grid:
 
     def launches_per_step(self) -> int:
         return int(self.L.fx_launches_per_step(self.h))
+
+    def march_chunk(self) -> int:
+        """Planes per block of the radiation/update kernel's march (fitted to the bound device)."""
+        return int(self.L.fx_march_chunk(self.h))
 
     def kernel_timing(self, on: bool) -> None:
         """Start (or stop) recording per-kernel CUDA-event durations of the stages fx_step enqueues."""
