@@ -363,18 +363,20 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
         }
       }
     }
-    // ---- gas energy by conservation (R12) and the momentum/energy feedback (Eqs. 31-32)
+    // ---- gas energy by conservation (R12) in NT; the momentum and energy feedback of the flux
+    // absorption (Eqs. 31-32) in FP32: it is scaled by 1/c^2, and the FP32 momentum it changes
+    // would round it to FP32 anyway
     const NT dEsum = (NT)eh + (NT)el;
-    NT re = ke + (um - dEsum);
-    NT work = NT(0);
+    const NT re = ke + (um - dEsum);
+    const float irf = (float)ir;
+    float work = 0.0f;
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-      const NT SdF = (NT)fh[q];
-      const NT mq = (NT)m_f[q];
-      work += (sph ? mq / (h[q] * h[q]) : mq) * ir * SdF;
-      m_f[q] = (float)(mq - SdF * kn.ic2);
+      const float hq = sph ? (float)h[q] : 1.0f;
+      work += (sph ? m_f[q] / (hq * hq) : m_f[q]) * irf * fh[q];
+      m_f[q] = fmaf(-fh[q], kl.ic2, m_f[q]);
     }
-    rhoe_f = (float)(re - work * kn.ic2);
+    rhoe_f = (float)(re - (NT)(work * kl.ic2));
     rho_f = (float)rr;
   }
   if (act) {
