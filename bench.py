@@ -164,28 +164,28 @@ def time_e2e(g, pb, steps, warmup):
 
     n = g.nelem
     dt_t = torch.float64 if pb.precision == "fp64" else torch.float32
-    h_in = torch.empty(n, dtype=dt_t, pin_memory=True)
-    h_out = torch.empty(n, dtype=dt_t, pin_memory=True)
+    # two pinned host buffers used in turn: each step uploads the previous step's result
+    bufs = [torch.empty(n, dtype=dt_t, pin_memory=True) for _ in range(2)]
     prec = 0 if pb.precision == "fp64" else 1
     import ctypes
     L = g.L
 
-    def one():
+    def one(i):
+        h_in, h_out = bufs[i % 2], bufs[(i + 1) % 2]
         g._check(L.fx_state_upload(g.h, ctypes.c_void_p(h_in.data_ptr()), prec, 0))
         g.step(pb.dt, 1)
         g._check(L.fx_state_download(g.h, ctypes.c_void_p(h_out.data_ptr()), prec, 0))
 
-    g._check(L.fx_state_download(g.h, ctypes.c_void_p(h_in.data_ptr()), prec, 0))
-    for _ in range(warmup):
-        one()
+    g._check(L.fx_state_download(g.h, ctypes.c_void_p(bufs[0].data_ptr()), prec, 0))
+    for i in range(warmup):
+        one(i)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(steps):
-        one()
-        h_in.copy_(h_out)  # next step's input is this step's result
+    for i in range(warmup, warmup + steps):
+        one(i)
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
-    return sec, n * h_in.element_size(), n * h_out.element_size()
+    return sec, n * bufs[0].element_size(), n * bufs[0].element_size()
 
 
 # Workloads: generator, default headline precision form, description, and the oracle sample used
