@@ -24,10 +24,14 @@ namespace fx {
 
 constexpr int CPL_THREADS = 128;  // cells (threads) per block of couple_kernel
 
-// Dynamic shared memory of couple_kernel: the block's rows of E and F_q, G + 1 floats per row
-// (the pad spreads the threads' row reads over all banks).
+// Rows of couple_kernel's shared memory per cell: E, then the F_q (which hold the first
+// evaluation's E_g and dE_g/dT during the Newton); at least three.
+constexpr int couple_rows(int D) { return 1 + D > 3 ? 1 + D : 3; }
+
+// Dynamic shared memory of couple_kernel: couple_rows(D) rows per cell of G + 1 floats (the pad
+// spreads the threads' row reads over all banks).
 template <int D> inline size_t couple_smem_bytes(int G) {
-  return (size_t)(1 + D) * CPL_THREADS * (size_t)(G + 1) * sizeof(float);
+  return (size_t)couple_rows(D) * CPL_THREADS * (size_t)(G + 1) * sizeof(float);
 }
 
 // 2^x for the table's fractional part (|x| < 2): the PTX base-2 exponential (relative error
@@ -160,10 +164,8 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
     if (j < G) s_ef[j] = A.gc->efac32[j];
     s_ed[j] = A.gc->edge32[j];
   }
-  // the block's radiation rows: the contiguous range [c0 G, (c0 + nc) G) of each moment
-#pragma unroll
-  for (int v = 0; v < NRV; ++v)
-    stage_rows<true>(A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, srow + v * CPL_THREADS * RS, nc, G, RS);
+  // the block's E rows: the contiguous range [c0 G, (c0 + nc) G) (the F rows follow the Newton)
+  stage_rows<true>(A.out + (size_t)NG * ncell + (size_t)c0 * G, srow, nc, G, RS);
   float rho_f = 1.0f, m_f[3] = {0.0f, 0.0f, 0.0f}, rhoe_f = 1.0f;
   if (act) {
     rho_f = A.out[cid];
@@ -185,26 +187,32 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
   __syncthreads();
 
   float* const rE = srow + t * RS;
+  float* const rE0 = srow + (CPL_THREADS + t) * RS;       // first evaluation: E_g
+  float* const rD0 = srow + (2 * CPL_THREADS + t) * RS;   // first evaluation: dE_g/dT
+  const bool work = act && g.couple;
   unsigned st = 0;
-  if (act && g.couple) {
+  NT rr = NT(1), ir = NT(1), ke = NT(0), um = NT(0);
+  LT Kc = LT(0), Sc = LT(0), Tst = LT(0);
+  float eh = 0.0f, el = 0.0f;
+  if (work) {
     // ---- floors, T^- = u^-/(rho c_v), the opacity factors of the (floored) density
-    NT rr = (NT)rho_f;
+    rr = (NT)rho_f;
     if (rr < kn.rho_floor) { rr = kn.rho_floor; st |= ST_FLOOR; }
     // 1/rho: for FP64, an FP32 seed refined by one Newton-Raphson step (relative error ~1e-14)
-    NT ir = (NT)(1.0f / (float)rr);
+    ir = (NT)(1.0f / (float)rr);
     if (sizeof(NT) == 8) ir = fma(ir, fma(-rr, ir, NT(1)), ir);
-    NT ke = NT(0);
 #pragma unroll
     for (int q = 0; q < D; ++q) {
       const NT mh = sph ? (NT)m_f[q] / h[q] : (NT)m_f[q];
       ke += NT(0.5) * mh * mh * ir;
     }
-    NT um = (NT)rhoe_f - ke;
+    um = (NT)rhoe_f - ke;
     if (um < kn.u_floor) { um = kn.u_floor; st |= ST_FLOOR; }
     const NT rcv = rr * kn.cv;
     const LT rcv_f = (LT)rcv;
     const NT Tm = um * ir * kn.gm1;  // c_v = 1/(gamma - 1)
-    const LT Kc = (LT)(kn.kappa0 * hpow(rr, g.kap_rho_h)), Sc = (LT)(kn.sigma0 * rr);
+    Kc = (LT)(kn.kappa0 * hpow(rr, g.kap_rho_h));
+    Sc = (LT)(kn.sigma0 * rr);
     // E^- with its silent positivity floor (Wien tails), and its group sum
     LT Esum = LT(0);
     for (int j = 0; j < G; ++j) {
@@ -214,8 +222,9 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
     }
     const NT ats = kn.atol * (um + (NT)Esum);
     const LT hh = LT(0.5) * (LT)g.kap_T_h;
-    // one evaluation at T: the group sums of E_g(T) - E_g^- (Eq. 25) and of dE_g/dT
-    auto eval = [&](LT Tl, LT& sa, LT& sb) {
+    // one evaluation at T: the group sums of E_g(T) - E_g^- (Eq. 25) and of dE_g/dT; the first
+    // one also keeps each group's E_g and dE_g/dT (most cells converge from it)
+    auto eval = [&](LT Tl, LT& sa, LT& sb, bool keep) {
       const PlanckAt p = planck_at(A.ptab, kl.aN, Tl);
       const LT ck = kl.cdts * (Kc * hpow(Tl, g.kap_T_h));
       const LT hi = hh * p.invT;
@@ -229,6 +238,7 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
         const LT inv = frcp(LT(1) + tau);
         const LT Eg = (Em + tau * Bq) * inv;
         const LT dEg = (tau * dBq + (tau * hi) * (Bq - Eg)) * inv;
+        if (keep) { rE0[j] = Eg; rD0[j] = dEg; }
         a += Eg - Em;
         b += dEg;
       }
@@ -244,10 +254,10 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
     LT Tacc = (LT)Tm;  // T at the accepted point, in FP32
     LT lin = LT(0);    // linearised step added to the accepted group energies at convergence
     int it = 0, ls = 0;
-    bool ok = false, done = false, need_dir = true;
+    bool ok = false, done = false, need_dir = true, first = true;  // first: accepted point is T^-
     {
       LT a, b;
-      eval(Tacc, a, b);
+      eval(Tacc, a, b, true);
       r = (NT)a;
       drf = rcv_f + b;
     }
@@ -274,12 +284,13 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
       const bool valid = Ttr > NT(0);
       const LT Tl = valid ? (LT)Ttr : Tacc;
       LT a, b;
-      eval(Tl, a, b);
+      eval(Tl, a, b, false);
       const NT rt = rcv * dtt + (NT)a;
       if (valid && fabs(rt) < fabs(r)) {
         dl = dtt;
         dacc = dtt;
         Tacc = Tl;
+        first = false;
         r = rt;
         drf = rcv_f + b;
         need_dir = true;
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
       NT Te = lo;
       for (int kk = 0; kk < 400 + g.bisect_maxit + 4 && phase < 3; ++kk) {
         LT a, b;
-        eval((LT)(Tm + Te), a, b);
+        eval((LT)(Tm + Te), a, b, false);
         const NT rq = rcv * Te + (NT)a;
         if (phase == 0) {
           if (rq > NT(0) && cnt < 200) { lo = NT(0.5) * (lo + Tm) - Tm; ++cnt; }  // T_lo /= 2
@@ -317,16 +328,28 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
       if (brk) dl = NT(0.5) * (lo + hi);
       dacc = dl;
       lin = LT(0);
+      first = false;
     }
     if (!ok) st |= ST_NEWTON;
-    const LT Tst = (LT)(Tm + dl);
+    Tst = (LT)(Tm + dl);
     if (A.tstar_out != nullptr) A.tstar_out[cid] = Tst;
 
-    // ---- the accepted group energies, and the group sum of their changes as a float pair (the
-    // sum keeps its rounding errors, so the gas energy update sees the changes summed to about
-    // twice FP32 precision)
-    float eh = 0.0f, el = 0.0f;
-    {
+    // ---- the accepted group energies (from the kept first evaluation when it is the accepted
+    // point, else evaluated again), and the group sum of their changes as a float pair (the sum
+    // keeps its rounding errors, so the gas energy update sees the changes summed to about twice
+    // FP32 precision)
+    if (first) {
+      for (int j = 0; j < G; ++j) {
+        const LT Em = rE[j];
+        LT Eg = rE0[j];
+        if (lin != LT(0)) Eg += rD0[j] * lin;
+        float s, e;
+        two_sum(eh, Eg - Em, s, e);
+        eh = s;
+        el += e;
+        rE[j] = Eg;
+      }
+    } else {
       const LT Ta = (LT)(Tm + dacc);
       const PlanckAt p = planck_at(A.ptab, kl.aN, Ta);
       const LT ck = kl.cdts * (Kc * hpow(Ta, g.kap_T_h));
@@ -346,6 +369,14 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
         rE[j] = Eg;
       }
     }
+  }
+  // the F rows (into the rows that held the first evaluation)
+  __syncthreads();
+#pragma unroll
+  for (int v = 1; v < NRV; ++v)
+    stage_rows<true>(A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, srow + v * CPL_THREADS * RS, nc, G, RS);
+  __syncthreads();
+  if (work) {
     // ---- flux absorption at the converged temperature (Eq. 28) and the group sums of the flux
     // changes (in FP32: they reach the gas momentum and energy scaled by 1/c^2, Eqs. 31-32)
     float fh[3] = {0.0f, 0.0f, 0.0f};
@@ -369,14 +400,14 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
     const NT dEsum = (NT)eh + (NT)el;
     const NT re = ke + (um - dEsum);
     const float irf = (float)ir;
-    float work = 0.0f;
+    float vdf = 0.0f;  // v . sum_g dF_g
 #pragma unroll
     for (int q = 0; q < D; ++q) {
       const float hq = sph ? (float)h[q] : 1.0f;
-      work += (sph ? m_f[q] / (hq * hq) : m_f[q]) * irf * fh[q];
+      vdf += (sph ? m_f[q] / (hq * hq) : m_f[q]) * irf * fh[q];
       m_f[q] = fmaf(-fh[q], kl.ic2, m_f[q]);
     }
-    rhoe_f = (float)(re - (NT)(work * kl.ic2));
+    rhoe_f = (float)(re - (NT)(vdf * kl.ic2));
     rho_f = (float)rr;
   }
   if (act) {
