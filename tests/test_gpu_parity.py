@@ -207,6 +207,23 @@ def test_newton_failure_is_reported(fxmod):
     assert st == 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32n64"])
+def test_bisection_fallback(fxmod, precision):
+    # one Newton iteration allowed, strong coupling, radiation twice the gas temperature: every
+    # cell falls back to the bisection on its bracket (reading R11), on both sides
+    pb, prim = W.kh_2d(nx=20, ny=16, ngroups=6, nsteps=2, precision=precision)
+    pb.kappa0, pb.newton_maxit = 1e4, 1
+    prim = prim.copy()
+    prim[-1] *= 2.0
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    if precision == "fp64":
+        H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
+    else:
+        H.assert_parity(pb, got, ref, 1e-4, natural=True)
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32", 1e-5), ("fp32n64", 1e-5)])
 def test_spherical_2d_small(fxmod, precision, tol):
     # log-r x theta grid with reflecting inner radius, outflow outer radius, polar-axis parity;
