@@ -1,6 +1,7 @@
 // Gas face kernel: for every cell face of every direction, the coordinate-moment parabolic
 // reconstruction of the two neighbouring cells (Sec. 5.1) and the HLLC flux with its contact
-// speed (Sec. 5.2).  One thread per face; the four cells of the stencil are read through L1.
+// speed (Sec. 5.2).  A block stages a tile's primitives in shared memory and reconstructs each
+// cell once, for both of its faces.
 // The stage kernel then uses the fluxes for the gas divergence and the contact speeds to upwind
 // the radiation advection (Eq. 19).
 #pragma once
@@ -13,65 +14,127 @@ __host__ __device__ inline int64_t faces_along(const int* n, int d) {
   return (int64_t)(n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2));
 }
 
-// Flux through one face of direction DIR (compile-time, so all index arrays stay in registers).
+// Tile of the gas face kernel for direction DIR, 288 threads: LR = LD + 1 rows of cells along DIR
+// by LX cells along x are reconstructed, one cell per thread (DIR = 0: a row segment of 288
+// cells; otherwise 9 cells along DIR by 32 along x, so that a warp reads consecutive x), and
+// the top LD rows own their lower faces.  Cells 0 .. n_d along DIR own the n_d + 1 faces of the
+// direction (cell n_d is a ghost from the boundary rules).
+constexpr int FACE_THREADS = 288;
+template <int DIR> struct FaceTile {
+  static constexpr int LX = DIR == 0 ? 1 : 32, LR = FACE_THREADS / LX, LD = LR - 1;
+  static constexpr int NWC = LR + 2;  // cells d0-2 .. d0+LD along DIR whose primitives are staged
+};
+constexpr int FACE_WCELLS = 352;  // max over DIR of FaceTile::NWC * LX
+constexpr int FACE_BCELLS = 288;  // FaceTile::LR * LX
+
+// Number of tiles of direction DIR (blocks of the face kernel's grid row DIR).
+__host__ __device__ inline unsigned face_tiles(const int* n, int D, int DIR) {
+  const int nd = n[DIR];
+  if (DIR == 0) {
+    constexpr int LD = FaceTile<0>::LD;
+    return (unsigned)((nd + 1 + LD - 1) / LD) * (unsigned)(n[1] * (D >= 3 ? n[2] : 1));
+  }
+  constexpr int LD = FaceTile<1>::LD;
+  const unsigned nxg = (unsigned)((n[0] + 31) / 32);
+  return (unsigned)((nd + 1 + LD - 1) / LD) * nxg * (unsigned)(DIR == 1 ? (D >= 3 ? n[2] : 1) : n[1]);
+}
+
+// Fluxes through the faces of one tile of direction DIR: the primitives of the tile's cells and
+// their halo along DIR go to shared memory once, each cell is reconstructed once (its upper-face
+// state serves the face above it, its lower-face state its own face), and each face gets HLLC.
 template <class R, int D, int DIR>
-__device__ __forceinline__ void gas_face_dir(const StageArgs<R>& A, int64_t f) {
+__device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned tile, R (*sw)[FACE_WCELLS],
+                                               R (*sb)[FACE_BCELLS]) {
   constexpr int NG = 2 + D, NW = 2 + D;
+  using FT = FaceTile<DIR>;
+  constexpr int LD = FT::LD, LX = FT::LX, NWC = FT::NWC;
   const auto& g = A.g;
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const int nd = DIR == 0 ? n0 : (DIR == 1 ? n1 : n2);
+  const unsigned nseg = (unsigned)((nd + 1 + LD - 1) / LD);
+  // tile -> (segment along DIR, x group, remaining index)
+  const unsigned seg = tile % nseg, rest = tile / nseg;
+  int xg = 0, i1 = 0, i2 = 0;  // x group (DIR != 0) and the two transverse indices
+  if (DIR == 0) { i1 = (int)(rest % (unsigned)n1); i2 = (int)(rest / (unsigned)n1); }
+  else {
+    const unsigned nxg = (unsigned)((n0 + 31) / 32);
+    xg = (int)(rest % nxg);
+    const int other = (int)(rest / nxg);
+    if (DIR == 1) i2 = other; else i1 = other;
+  }
+  const int d0 = (int)seg * LD;  // first face-owning cell of the tile along DIR
+  const int t = threadIdx.x;
   // 32-bit index arithmetic: the host keeps every state and face-buffer offset below 2^32
-  const uint32_t ex = (uint32_t)(n0 + (DIR == 0)), ey = (uint32_t)(n1 + (DIR == 1));
-  const uint32_t nf = ex * ey * (uint32_t)(n2 + (DIR == 2));
-  if (f >= (int64_t)nf) return;
-  const uint32_t uf = (uint32_t)f, q = uf / ex;
-  const int i0 = (int)(uf - q * ex), i1 = (int)(q % ey), i2 = (int)(q / ey);
-  const int id = DIR == 0 ? i0 : (DIR == 1 ? i1 : i2);
   const uint32_t ncell = (uint32_t)g.ncell;
   const auto& KR = A.k(R(0));
-  // curvilinear grids: the cell scale factors turn covariant momentum into physical velocity
   const bool sph = g.geom != 0;
   const Tab<R> t0{A.tab[0], n0 + 4, A.uniform[0] ? A.urow[0] : nullptr};
   const Tab<R> t1{A.tab[D >= 2 ? 1 : 0], (D >= 2 ? n1 : n0) + 4,
                   A.uniform[D >= 2 ? 1 : 0] ? A.urow[D >= 2 ? 1 : 0] : nullptr};
-  // primitives of the cells id-2 .. id+1 along DIR (ghosts from the boundary rules)
-  R W[4][NW];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
+  // ---- primitives of cells d0-2 .. d0+LD along DIR (ghosts from the boundary rules), for each
+  // of the tile's LX columns
+  for (int c = t; c < NWC * LX; c += FACE_THREADS) {
+    const int lx = c % LX, k = c / LX;
+    const int id = d0 - 2 + k;
+    const int x = DIR == 0 ? id : min(xg * 32 + lx, n0 - 1);
     bool flip = false;
-    const int cd = min(max(bc_map(id - 2 + m, nd, g.bc_lo[DIR], g.bc_hi[DIR], flip), 0), nd - 1);
-    const int c0 = DIR == 0 ? cd : i0, c1 = DIR == 1 ? cd : i1, c2 = DIR == 2 ? cd : i2;
+    const int cd = min(max(bc_map(id, nd, g.bc_lo[DIR], g.bc_hi[DIR], flip), 0), nd - 1);
+    const int c0 = DIR == 0 ? cd : x, c1 = DIR == 1 ? cd : i1, c2 = DIR == 2 ? cd : i2;
     const uint32_t ci = ((uint32_t)c2 * n1 + c1) * n0 + c0;
     R u[NG];
 #pragma unroll
     for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + ci];
     if (flip) u[1 + DIR] = -u[1 + DIR];
     if (sph) {  // physical components m_q / h_q (the 2-d spherical grid is r x theta)
-      const int cr = DIR == 0 ? id - 2 + m : i0, ct = DIR == 1 ? id - 2 + m : i1;
+      const int cr = DIR == 0 ? id : x, ct = DIR == 1 ? id : i1;
       u[1] *= frcp(t0(T_HA, bc_pad(cr)) * t1(T_HA, bc_pad(ct)));
       if (D >= 2) u[2] *= frcp(t0(T_HB, bc_pad(cr)) * t1(T_HB, bc_pad(ct)));
     }
     const R rho = u[0], irho = frcp(rho);
     R ke = R(0);
 #pragma unroll
-    for (int q = 0; q < D; ++q) { W[m][2 + q] = u[1 + q] * irho; ke += u[1 + q] * W[m][2 + q]; }
-    W[m][0] = rho;
-    W[m][1] = KR.gm1 * (u[NG - 1] - R(0.5) * ke);
+    for (int q = 0; q < D; ++q) {
+      const R vq = u[1 + q] * irho;
+      sw[2 + q][c] = vq;
+      ke += u[1 + q] * vq;
+    }
+    sw[0][c] = rho;
+    sw[1][c] = KR.gm1 * (u[NG - 1] - R(0.5) * ke);
   }
-  const Tab<R> t{A.tab[DIR], nd + 4, A.uniform[DIR] ? A.urow[DIR] : nullptr};
-  // left state: upper face of cell id-1; right state: lower face of cell id; velocity
-  // component 0 of the rotated states is the face normal
+  __syncthreads();
+  // ---- each thread reconstructs one cell along DIR (row r: cell d0 - 1 + r): the upper-face
+  // state to shared memory (the left state of the face above), the lower-face state kept for the
+  // cell's own face
+  const Tab<R> tt{A.tab[DIR], nd + 4, A.uniform[DIR] ? A.urow[DIR] : nullptr};
+  const int lx = t % LX, r = t / LX;
+  const int id = d0 - 1 + r;
+  auto w = [&](int v, int k) -> R { return sw[v][k * LX + lx]; };  // k: cell d0 - 2 + k
+  R Ra[NW];
+#pragma unroll
+  for (int v = 0; v < NW; ++v) {
+    R a, b;
+    recon_parabolic(tt, bc_pad(id), w(v, r), w(v, r + 1), w(v, r + 2), a, b);
+    Ra[v] = a;
+    sb[v][r * LX + lx] = b;
+  }
+  __syncthreads();
+  // ---- HLLC through the cell's lower face (rows 1 .. LD): left state = upper face of the cell
+  // below; velocity component 0 of the rotated states is the face normal
+  const int x = DIR == 0 ? id : xg * 32 + lx;
+  if (r == 0 || id > nd || (DIR != 0 && x >= n0)) return;
   R Lr[5], Rr[5], fl[5], vs;
 #pragma unroll
   for (int v = 0; v < NW; ++v) {
-    R a, b, a2, b2;
-    recon_parabolic(t, bc_pad(id - 1), W[0][v], W[1][v], W[2][v], a, b);
-    recon_parabolic(t, bc_pad(id), W[1][v], W[2][v], W[3][v], a2, b2);
     const int slot = v < 2 ? v : 2 + (v - 2 - DIR + D) % D;  // rotated position of variable v
-    Lr[slot] = b;
-    Rr[slot] = a2;
+    Lr[slot] = sb[v][(r - 1) * LX + lx];
+    Rr[slot] = Ra[v];
   }
   hllc<R, D>(KR.gamma, Lr, Rr, fl, vs);
+  const uint32_t ex = (uint32_t)(n0 + (DIR == 0)), ey = (uint32_t)(n1 + (DIR == 1));
+  const uint32_t nf = ex * ey * (uint32_t)(n2 + (DIR == 2));
+  const uint32_t uf = DIR == 0 ? ((uint32_t)i2 * n1 + i1) * ex + (uint32_t)id
+                    : DIR == 1 ? ((uint32_t)i2 * ey + (uint32_t)id) * n0 + (uint32_t)x
+                               : ((uint32_t)id * n1 + (uint32_t)i1) * n0 + (uint32_t)x;
   R* out = A.faces_out + A.face_off[DIR];
   out[uf] = fl[0];
 #pragma unroll
@@ -80,13 +143,17 @@ __device__ __forceinline__ void gas_face_dir(const StageArgs<R>& A, int64_t f) {
   out[(uint32_t)NG * nf + uf] = vs;
 }
 
+// One block per tile; grid row y is the direction (tiles beyond a direction's count return).
 template <class R, int D>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(FACE_THREADS, 3)
 gas_face_kernel(const __grid_constant__ StageArgs<R> A) {
-  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (blockIdx.y == 0) gas_face_dir<R, D, 0>(A, f);
-  else if (D >= 2 && blockIdx.y == 1) gas_face_dir<R, D, (D >= 2 ? 1 : 0)>(A, f);
-  else if (D >= 3) gas_face_dir<R, D, (D >= 3 ? 2 : 0)>(A, f);
+  __shared__ R sw[2 + D][FACE_WCELLS];
+  __shared__ R sb[2 + D][FACE_BCELLS];
+  const int DIR = blockIdx.y;
+  if (blockIdx.x >= face_tiles(A.g.n, D, DIR)) return;
+  if (DIR == 0) gas_faces_tile<R, D, 0>(A, blockIdx.x, sw, sb);
+  else if (D >= 2 && DIR == 1) gas_faces_tile<R, D, (D >= 2 ? 1 : 0)>(A, blockIdx.x, sw, sb);
+  else if (D >= 3) gas_faces_tile<R, D, (D >= 3 ? 2 : 0)>(A, blockIdx.x, sw, sb);
 }
 
 }  // namespace fx

@@ -72,11 +72,12 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
   e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                            cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  // gas faces first (same stream): fluxes and contact speeds of every face of every direction
-  int64_t nfmax = 0;
-  for (int d = 0; d < D; ++d) nfmax = nfmax > faces_along(a.g.n, d) ? nfmax : faces_along(a.g.n, d);
-  dim3 gg((unsigned)((nfmax + 255) / 256), D, 1);
-  gas_face_kernel<R, D><<<gg, 256, 0, s>>>(a);
+  // gas faces first (same stream): fluxes and contact speeds of every face of every direction,
+  // one block per tile of faces, one grid row per direction
+  unsigned ntmax = 0;
+  for (int d = 0; d < D; ++d) ntmax = ntmax > face_tiles(a.g.n, D, d) ? ntmax : face_tiles(a.g.n, D, d);
+  dim3 gg(ntmax, D, 1);
+  gas_face_kernel<R, D><<<gg, FACE_THREADS, 0, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mid) {
