@@ -379,8 +379,11 @@ struct StageLayout {
   static constexpr int NSLOT = (D >= 2) ? 4 : 1, TC = TX * TY;
   static constexpr int NFX = (TX + 1) * TY, NFY = (D == 3) ? TX * (TY + 1) : 0;
   int st, pk, rbx, rax, rby, ray, rfx, rfy, sg, sbr, sbg, end;
-  // (the face fluxes of C overwrite the left face states of B: each face's left state is read,
-  // and its flux written, by the thread that owns the face, between the same two barriers)
+  // The face fluxes of C have a region of their own in 1-d and 2-d, so that B of the next plane
+  // may write face states while D still reads fluxes (no barrier separates A from B there).  In
+  // 3-d they overwrite the left face states of B (each face's left state is read, and its flux
+  // written, by the thread that owns the face, between the same two barriers), which keeps the
+  // larger 3-d tile at two blocks per SM.
   __host__ __device__ explicit StageLayout(int G) {
     st = 0;
     pk = st + NSLOT * NRV * PC * G;       // radiation ring [slot][NRV][PC][G]
@@ -388,9 +391,10 @@ struct StageLayout {
     rax = rbx + NRV * NFX * G;            // left state of every x face [NRV][NFX][G]
     rby = rax + NRV * TY * G;             // right state of the last x face of each row
     ray = rby + NRV * NFY * G;            // left state of every y face (3-d)
-    sg = ray + (D == 3 ? NRV * TX * G : 0);  // right state of the last y face (3-d)
-    rfx = rbx;                            // radiation x-face fluxes [NRV][NFX][G]
+    const int fe = ray + (D == 3 ? NRV * TX * G : 0);  // right state of the last y face (3-d)
+    rfx = D == 3 ? rbx : fe;              // radiation x-face fluxes [NRV][NFX][G]
     rfy = rby;                            // radiation y-face fluxes (3-d)
+    sg = D == 3 ? fe : fe + NRV * NFX * G;
     sbr = sg + NSLOT * NG * PC;           // gas variables ring [slot][NG][PC]
     sbg = sbr + NRV * TC * G;             // stage-2 base, radiation [NRV][TC][G]
     end = sbg + NG * TC;                  // stage-2 base, gas [NG][TC]
@@ -864,7 +868,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       if (D >= 2)
         gnet = gnet + (gface(MD, gvar, face_m(k + 1)) * cls(fm_r) - gface(MD, gvar, face_m(k)) * cls(fm_l));
     }
-    __syncthreads();
+    // (B reads only planes finished two steps ago and the thread's own column; in 3-d the face
+    // states it writes share their space with the fluxes that D of the previous plane reads)
+    if (D == 3) __syncthreads();
     // the own column of planes k, k+1, k+2 from the ring
     R Q0[NGL][NRV], Q1[NGL][NRV], Q2[NGL][NRV];
 #pragma unroll
