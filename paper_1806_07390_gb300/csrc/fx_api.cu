@@ -123,6 +123,7 @@ struct fx_grid {
   float ptab_u0 = 0.0f;
   size_t off_ptab = 0;
   size_t off_faces = 0;           // gas face buffer [dir][NG+1][faces of dir]
+  size_t off_opk = 0;             // opacity factors of the stage input [K, S][cells]
   int64_t face_off[3] = {0, 0, 0};
   bool uniform[3] = {false, false, false};
   // per-kernel timing: one event triple (before the face kernel, between, after the stage
@@ -571,6 +572,7 @@ StageArgs<R> stage_args(fx_grid* h) {
   a.gc = reinterpret_cast<const GroupConst*>(h->ws + h->off_gc);
   a.faces = reinterpret_cast<const R*>(h->ws + h->off_faces);
   a.faces_out = reinterpret_cast<R*>(h->ws + h->off_faces);
+  a.opk = reinterpret_cast<R*>(h->ws + h->off_opk);
   for (int d = 0; d < 3; ++d) {
     a.face_off[d] = h->face_off[d];
     a.uniform[d] = d < h->D && h->uniform[d];
@@ -961,6 +963,8 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
     h->off_faces = off;
     off = align_up(off + (size_t)fo * h->elem);
   }
+  h->off_opk = off;
+  off = align_up(off + (size_t)2 * h->ncell * h->elem);
   // directions whose table rows are all equal (uniform Cartesian spacing) read one row
   for (int d = 0; d < P.dims; ++d) {
     const int np = (int)P.n[d] + 4;

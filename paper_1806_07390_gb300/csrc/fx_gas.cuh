@@ -1,9 +1,10 @@
 // Gas face kernel: for every cell face of every direction, the coordinate-moment parabolic
 // reconstruction of the two neighbouring cells (Sec. 5.1) and the HLLC flux with its contact
 // speed (Sec. 5.2).  A block stages a tile's primitives in shared memory and reconstructs each
-// cell once, for both of its faces.
-// The stage kernel then uses the fluxes for the gas divergence and the contact speeds to upwind
-// the radiation advection (Eq. 19).
+// cell once, for both of its faces.  It also forms every cell's opacity factors.
+// The stage kernel then uses the fluxes for the gas divergence, the contact speeds to upwind the
+// radiation advection (Eq. 19), and the opacity factors for the ε correction of the radiation
+// fluxes.
 #pragma once
 #include "fx_device.cuh"
 
@@ -102,6 +103,17 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
     sw[1][c] = KR.gm1 * (u[NG - 1] - R(0.5) * ke);
   }
   __syncthreads();
+  if (DIR == 0) {
+    // the opacity factors K = kappa0 rho^a T^b and S = sigma0 rho of the stage input, once per
+    // cell (each cell is a face owner of exactly one x tile), for the radiation/update kernel
+    const int r = t, id = d0 - 1 + r;
+    if (r >= 1 && id < n0) {
+      const R rho = sw[0][r + 1], T = sw[1][r + 1] * frcp(rho);
+      const uint32_t ci = ((uint32_t)i2 * n1 + i1) * n0 + (uint32_t)id;
+      A.opk[ci] = T > R(0) ? KR.kappa0 * hpow(rho, g.kap_rho_h) * hpow(T, g.kap_T_h) : R(0);
+      A.opk[ncell + ci] = KR.sigma0 * rho;
+    }
+  }
   // ---- each thread reconstructs one cell along DIR (row r: cell d0 - 1 + r): the upper-face
   // state to shared memory (the left state of the face above), the lower-face state kept for the
   // cell's own face

@@ -59,6 +59,8 @@ template <class R> struct StageArgs {
   PlanckTable ptab;
   const R* faces;      // gas face fluxes and contact speeds [dir][NG+1][faces of dir]
   R* faces_out;        // the same buffer, written by gas_face_kernel
+  R* opk;              // opacity factors K = kappa0 rho^a T^b, S = sigma0 rho of every cell of the
+                       // stage input [2][ncell]: gas_face_kernel writes, stage_kernel reads
   int64_t face_off[3]; // element offset of each direction's block in `faces`
   R urow[3][NTAB];     // the common table row of a uniform direction
   int uniform[3];      // direction d has identical table rows (Cartesian grids)
@@ -415,16 +417,17 @@ inline size_t stage_smem_bytes(int G) {
 // The radiation/update kernel (one launch per RK stage, after gas_face_kernel).  A block owns a
 // tile of TX x TY cells and marches along the slowest axis.  Each cell is served by a segment of
 // GL = GP/NGL lanes, and a thread owns NGL consecutive groups of its cell (NGL = 2 in the FP32
-// forms with G > 8: the per-cell work of a thread is shared by two groups and the two groups'
-// arithmetic interleaves).  Per plane k, between three barriers:
-//   A  its own radiation values of plane k+2 (prefetched into registers one step ahead) and the
-//      in-plane halo of plane k go to a four-plane shared ring; the cell's opacity factors are
-//      formed from its gas variables (held by lanes 0..NG-1);
-//   B  each cell is reconstructed once per direction: in-plane from shared memory, along the
-//      march from a register window of its own column;
+// forms with G > 16, else 1).  Per plane k:
+//   A  wait for the thread's copies of plane k+2 (staged during step k-1), mirror and physical
+//      conversions of what it copied, and stage plane k+3 (own cells, in-plane halo, gas
+//      variables, and the opacity factors that gas_face_kernel formed) with cp.async;
+//   B  each cell is reconstructed once per direction from the four-plane shared ring;
 //   C  the M1/HLL radiation fluxes of the cell's lower faces and of its march face k+1/2, using
 //      the contact speeds of the gas faces (Eq. 19);
-//   D  divergence (gas fluxes from the face buffer), RK combine, coupling, store of plane k.
+//   D  divergence (gas fluxes from the face buffer), RK combine, store of plane k (and, in the
+//      FP64 form, the interaction).
+// B | C and C | D are block barriers; in 3-d also A | B (its face fluxes share shared memory with
+// the face states).
 // ---------------------------------------------------------------------------------------------
 template <class R, int D, int GP, int TX, int TY, class LT, class NT, int NGL>
 __global__ void __launch_bounds__(TX * TY * (GP / NGL), (sizeof(R) == 4 && NGL == 1) ? 3 : 2)
@@ -510,7 +513,6 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     return st[((slot * NRV + v) * PC + sc) * GS + gg];
   };
   auto gas_at = [&](int slot, int v, int sc) -> R& { return sgr[(slot * NG + v) * PC + sc]; };
-  // opacity factors K = kappa0 rho^a T^b and S = sigma0 rho of one cell from its gas variables
   const bool sph = (D == 2) && g.geom != 0;  // spherical (r, theta): x = r, march = theta
   // scale factor of component q of the cell with x index ix on plane k
   auto hfac = [&](int q, int ix, int k) -> R {
@@ -518,34 +520,20 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     const int e = q == 0 ? T_HA : T_HB;
     return tx(e, bc_pad(ix)) * tm(e, bc_pad(k));
   };
-  auto opac = [&](const R* uc, int slot, int sc, int ix, int k) {
-    R u[NG];
-#pragma unroll
-    for (int v = 0; v < NG; ++v) u[v] = uc[v];
-    if (sph) { u[1] *= frcp(hfac(0, ix, k)); u[2] *= frcp(hfac(1, ix, k)); }
-    R rho = u[0], irho = frcp(rho), ke = R(0);
-#pragma unroll
-    for (int q = 0; q < D; ++q) ke += u[1 + q] * u[1 + q];
-    R T = KR.gm1 * (u[NG - 1] - R(0.5) * ke * irho) * irho;
-    pk[(slot * 2 + 0) * PC + sc] = (T > R(0)) ? KR.kappa0 * hpow(rho, g.kap_rho_h) * hpow(T, g.kap_T_h) : R(0);
-    pk[(slot * 2 + 1) * PC + sc] = KR.sigma0 * rho;
-  };
 
-  // Load `ncl` cells of plane k (enumerated by cell_of) into ring slot `slot`: gas (one thread
-  // per cell, for the opacity factors), radiation with one thread per (cell, group).
+  // Load `ncl` cells of plane k (enumerated by cell_of) into ring slot `slot`: gas variables and
+  // opacity factors (one thread per cell), radiation with one thread per (cell, group).
   auto load_cells = [&](int slot, int k, int ncl, auto cell_of) {
     for (int i = tid; i < ncl; i += NTH) {
       int sx, sy;
       cell_of(i, sx, sy);
       bool fl[3];
       const uint32_t gc_ = map_cell(sx, sy, k, fl);
-      R u[NG];
+      const int sc = scell(sx, sy);
 #pragma unroll
-      for (int v = 0; v < NG; ++v) {
-        u[v] = A.in[v * ncell + gc_];
-        gas_at(slot, v, scell(sx, sy)) = u[v];
-      }
-      opac(u, slot, scell(sx, sy), x0 + sx, k);
+      for (int v = 0; v < NG; ++v) gas_at(slot, v, sc) = A.in[v * ncell + gc_];
+      pk[(slot * 2 + 0) * PC + sc] = A.opk[gc_];
+      pk[(slot * 2 + 1) * PC + sc] = A.opk[ncell + gc_];
     }
     for (int t = tid; t < ncl * GP; t += NTH) {
       const int i = t / GP, gg = t % GP;
@@ -612,10 +600,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   const int gvar = lane < NG ? lane : 0;
   // ---- staging of plane P into ring slot P & 3 with cp.async, issued one march step before the
   // plane is first read: the own cell's groups by their threads (lane 0 also copies the cell's gas
-  // variables, from which it forms the opacity factors after its wait), the in-plane halo as
-  // (cell, group) items, and the halo cells' gas variables one thread per cell.  Each thread later
-  // finishes what it copied itself: mirror flips of ghost cells, physical flux components on the
-  // spherical grid, and the opacity factors.
+  // variables and opacity factors), the in-plane halo as (cell, group) items, and the halo cells'
+  // opacity factors one thread per cell.  Each thread later finishes what it copied itself:
+  // mirror flips of ghost cells and physical flux components on the spherical grid.
   auto issue_plane = [&](int P) {
     const int slot = P & 3;
     bool fl[3];
@@ -631,6 +618,8 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     if (lane == 0) {
 #pragma unroll
       for (int v = 0; v < NG; ++v) cp_async(&gas_at(slot, v, sc_own), A.in + v * ncell + gc_);
+      cp_async(&pk[(slot * 2 + 0) * PC + sc_own], A.opk + gc_);
+      cp_async(&pk[(slot * 2 + 1) * PC + sc_own], A.opk + ncell + gc_);
     }
     for (int t = tid; t < NHALO * GP; t += NTH) {
       const int i = t / GP, gg = t % GP;
@@ -648,8 +637,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       halo_of(i, sx, sy);
       bool f[3];
       const uint32_t c = map_cell(sx, sy, P, f);
-#pragma unroll
-      for (int v = 0; v < NG; ++v) cp_async(&gas_at(slot, v, scell(sx, sy)), A.in + v * ncell + c);
+      const int sc = scell(sx, sy);
+      cp_async(&pk[(slot * 2 + 0) * PC + sc], A.opk + c);
+      cp_async(&pk[(slot * 2 + 1) * PC + sc], A.opk + ncell + c);
     }
   };
   auto finish_plane = [&](int P) {
@@ -671,12 +661,6 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           }
         }
       }
-      if (lane == 0) {
-        R u[NG];
-#pragma unroll
-        for (int v = 0; v < NG; ++v) u[v] = gas_at(slot, v, sc_own);
-        opac(u, slot, sc_own, gx, P);
-      }
     }
     for (int t = tid; t < NHALO * GP; t += NTH) {
       const int i = t / GP, gg = t % GP;
@@ -695,14 +679,6 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           rad_at(slot, v, sc, gg) = x;
         }
       }
-    }
-    for (int i = tid; i < NHALO; i += NTH) {
-      int sx, sy;
-      halo_of(i, sx, sy);
-      R u[NG];
-#pragma unroll
-      for (int v = 0; v < NG; ++v) u[v] = gas_at(slot, v, scell(sx, sy));
-      opac(u, slot, scell(sx, sy), x0 + sx, P);
     }
   };
   // stage-2 base of the thread's cell on plane P, staged at the end of the previous step and read
