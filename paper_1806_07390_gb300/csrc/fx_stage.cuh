@@ -380,7 +380,7 @@ struct StageLayout {
   static constexpr int PX = TX + 4, PY = (D == 3) ? TY + 4 : 1, PC = PX * PY;
   static constexpr int NSLOT = (D >= 2) ? 4 : 1, TC = TX * TY;
   static constexpr int NFX = (TX + 1) * TY, NFY = (D == 3) ? TX * (TY + 1) : 0;
-  int st, pk, rbx, rax, rby, ray, rfx, rfy, sg, sbr, sbg, end;
+  int st, pk, rbx, rax, rby, ray, rfx, rfy, sg, sbr, sbg, scar, end;
   // The face fluxes of C have a region of their own in 1-d and 2-d, so that B of the next plane
   // may write face states while D still reads fluxes (no barrier separates A from B there).  In
   // 3-d they overwrite the left face states of B (each face's left state is read, and its flux
@@ -399,7 +399,8 @@ struct StageLayout {
     sg = D == 3 ? fe : fe + NRV * NFX * G;
     sbr = sg + NSLOT * NG * PC;           // gas variables ring [slot][NG][PC]
     sbg = sbr + NRV * TC * G;             // stage-2 base, radiation [NRV][TC][G]
-    end = sbg + NG * TC;                  // stage-2 base, gas [NG][TC]
+    scar = sbg + NG * TC;                 // stage-2 base, gas [NG][TC]
+    end = scar + (D == 2 ? 4 * NRV * TC * G : 0);  // 2-d march carry [plane parity][bm, rfm][NRV][TC][G]
   }
 };
 
@@ -480,6 +481,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   R* const sgr = sm + L.sg;   // gas variables of the ring's planes
   R* const sbr = sm + L.sbr;  // stage-2 base of the tile's cells (radiation), by plane parity
   R* const sbg = sm + L.sbg;  // stage-2 base (gas)
+  R* const scr = sm + L.scar; // 2-d: march carry (own cell's upper march-face state, march flux)
   GroupConst* sgc = reinterpret_cast<GroupConst*>(
       (reinterpret_cast<uintptr_t>(sm + L.end) + 15) & ~static_cast<uintptr_t>(15));
   for (int i = tid; i < (int)(sizeof(GroupConst) / sizeof(int)); i += NTH)
@@ -746,8 +748,15 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     return __ldg(A.faces + (uint32_t)A.face_off[d] + v * nfd[d] + f);
   };
 
+  // Carried along the march: the own cell's upper march-face state of plane k and the flux
+  // through its lower march face.  In 2-d they are kept in shared memory (thread-private slots by
+  // plane parity) instead of registers: the kernel runs at its register limit.
   R bm0[NGL][NRV] = {};                     // own march-direction upper-face states, plane k
   R rfm_old[NGL][NRV] = {};                 // radiation fluxes through the lower march face
+  constexpr bool SCAR = D == 2;
+  auto car = [&](int P, int w, int v, int j) -> R& {  // w = 0: upper-face state, 1: lower-face flux
+    return scr[((((P & 1) * 2 + w) * NRV + v) * TC + tcell) * GS + gj[j]];
+  };
 
   // ---------------------------------------------------------------- prologue
   if (D == 1) {
@@ -779,6 +788,13 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       recon_rad(m0, Qm1[j], Q0[j], Q1[j], a_, bm0[j]);
       rad_face(MD, bprev, a_, chi_of((kbeg - 1) & 3, sc_own, j), chi_of(kbeg & 3, sc_own, j), ell, vs,
                rfm_old[j]);
+      if (SCAR) {
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) {
+          car(kbeg, 0, v, j) = bm0[j][v];
+          car(kbeg, 1, v, j) = rfm_old[j][v];
+        }
+      }
     }
   }
   const int ipx = bc_pad(gx);  // the x-direction table row of this cell
@@ -917,6 +933,10 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         }
       }
       if (D >= 2) recon_rad(mc_coef(tm, bc_pad(k + 1)), Q0[j], Q1[j], Q2[j], am1[j], bm1[j]);
+      if (SCAR) {
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) car(k + 1, 0, v, j) = bm1[j][v];
+      }
     }
     __syncthreads();
     // ---- C: radiation face fluxes
@@ -967,8 +987,17 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           }
         }
       }
-      if (D >= 2)
+      if (D >= 2) {
+        if (SCAR) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) bm0[j][v] = car(k, 0, v, j);
+        }
         rad_face(MD, bm0[j], am1[j], chi_of(s0, sc_own, j), chi_of((k + 1) & 3, sc_own, j), ell_m, vsm, rfm_new[j]);
+        if (SCAR) {
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) car(k + 1, 1, v, j) = rfm_new[j][v];
+        }
+      }
     }
     __syncthreads();
     // ---- D: update: divergence, RK combine, coupling, store
@@ -1038,7 +1067,11 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
             const int gg = gj[j];
             R net = rfx[(v * NFX + fxa + 1) * GS + gg] * fx_r[c] - rfx[(v * NFX + fxa) * GS + gg] * fx_l[c];
             if (D == 3) net = net + (rfy[(v * NFY + fya + TX) * GS + gg] * fyr - rfy[(v * NFY + fya) * GS + gg] * fyl);
-            if (D >= 2) net = net + (rfm_new[j][v] * fm_r[c] - rfm_old[j][v] * fm_l[c]);
+            if (D >= 2) {
+              const R fu = SCAR ? car(k + 1, 1, v, j) : rfm_new[j][v];
+              const R fd = SCAR ? car(k, 1, v, j) : rfm_old[j][v];
+              net = net + (fu * fm_r[c] - fd * fm_l[c]);
+            }
             const R cov = (sph && v >= 1) ? Q0[j][v] * hq[v - 1] : Q0[j][v];  // covariant F
             R u1 = cov + dt * (rsrc[j][v] - net);
             if (stage2) u1 = KR.alpha * base_r(v, j) + KR.beta * u1;
@@ -1113,13 +1146,15 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       issue_base(k + 1);
       cp_async_commit();
     }
-    // slide the march window
+    // slide the march window (2-d: the carry lives in shared memory)
+    if (!SCAR) {
 #pragma unroll
-    for (int j = 0; j < NGL; ++j) {
+      for (int j = 0; j < NGL; ++j) {
 #pragma unroll
-      for (int v = 0; v < NRV; ++v) {
-        bm0[j][v] = bm1[j][v];
-        rfm_old[j][v] = (D >= 2) ? rfm_new[j][v] : R(0);
+        for (int v = 0; v < NRV; ++v) {
+          bm0[j][v] = bm1[j][v];
+          rfm_old[j][v] = (D >= 2) ? rfm_new[j][v] : R(0);
+        }
       }
     }
   }
