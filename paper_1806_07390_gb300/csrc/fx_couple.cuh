@@ -211,8 +211,11 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
     const NT rcv = rr * kn.cv;
     const LT rcv_f = (LT)rcv;
     const NT Tm = um * ir * kn.gm1;  // c_v = 1/(gamma - 1)
-    Kc = (LT)(kn.kappa0 * hpow(rr, g.kap_rho_h));
-    Sc = (LT)(kn.sigma0 * rr);
+    {  // opacity factors in FP32: they only enter the FP32 group arithmetic
+      const LT rrf = (LT)rr;
+      Kc = kl.kappa0 * hpow(rrf, g.kap_rho_h);
+      Sc = kl.sigma0 * rrf;
+    }
     // E^- with its silent positivity floor (Wien tails), and its group sum
     LT Esum = LT(0);
     for (int j = 0; j < G; ++j) {
