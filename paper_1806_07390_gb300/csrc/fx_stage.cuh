@@ -380,7 +380,11 @@ struct StageLayout {
   static constexpr int PX = TX + 4, PY = (D == 3) ? TY + 4 : 1, PC = PX * PY;
   static constexpr int NSLOT = (D >= 2) ? 4 : 1, TC = TX * TY;
   static constexpr int NFX = (TX + 1) * TY, NFY = (D == 3) ? TX * (TY + 1) : 0;
-  int st, pk, rbx, rax, rby, ray, rfx, rfy, sg, sbr, sbg, scar, end;
+  int st, pk, rbx, rax, rby, ray, rfx, rfy, sg, sbr, sbg, scar, sgf, end;
+  // Staged gas-face values per cell and plane (1-d and 2-d; 3-d reads them from global memory,
+  // where the extra shared memory would cost a resident block): 3 contact speeds, then 2D fluxes
+  // per gas variable.
+  static constexpr int NGF = (D <= 2) ? 3 + 2 * D * NG : 0;
   // The face fluxes of C have a region of their own in 1-d and 2-d, so that B of the next plane
   // may write face states while D still reads fluxes (no barrier separates A from B there).  In
   // 3-d they overwrite the left face states of B (each face's left state is read, and its flux
@@ -400,7 +404,8 @@ struct StageLayout {
     sbr = sg + NSLOT * NG * PC;           // gas variables ring [slot][NG][PC]
     sbg = sbr + NRV * TC * G;             // stage-2 base, radiation [NRV][TC][G]
     scar = sbg + NG * TC;                 // stage-2 base, gas [NG][TC]
-    end = scar + (D == 2 ? 4 * NRV * TC * G : 0);  // 2-d march carry [plane parity][bm, rfm][NRV][TC][G]
+    sgf = scar + (D == 2 ? 4 * NRV * TC * G : 0);  // 2-d march carry [plane parity][bm, rfm][NRV][TC][G]
+    end = sgf + 2 * TC * NGF;             // gas-face values [plane parity][TC][NGF]
   }
 };
 
@@ -482,6 +487,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   R* const sbr = sm + L.sbr;  // stage-2 base of the tile's cells (radiation), by plane parity
   R* const sbg = sm + L.sbg;  // stage-2 base (gas)
   R* const scr = sm + L.scar; // 2-d: march carry (own cell's upper march-face state, march flux)
+  R* const sgf = sm + L.sgf;  // gas-face values of the cell's faces, by plane parity
   GroupConst* sgc = reinterpret_cast<GroupConst*>(
       (reinterpret_cast<uintptr_t>(sm + L.end) + 15) & ~static_cast<uintptr_t>(15));
   for (int i = tid; i < (int)(sizeof(GroupConst) / sizeof(int)); i += NTH)
@@ -747,6 +753,36 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   auto gface = [&](int d, int v, uint32_t f) -> R {
     return __ldg(A.faces + (uint32_t)A.face_off[d] + v * nfd[d] + f);
   };
+  auto gface_p = [&](int d, int v, uint32_t f) -> const R* {
+    return A.faces + (uint32_t)A.face_off[d] + v * nfd[d] + f;
+  };
+  // 1-d and 2-d: the gas-face values a cell needs on plane P, staged with cp.async one plane
+  // ahead into shared slots by plane parity: slots 0-2 the contact speeds of its lower x face, of
+  // the x face above the tile's last column and of its upper march face (lane 0 copies them);
+  // slots 3 + 2Dv .. 2 + 2D(v+1) the fluxes of gas variable v through the cell's lower and upper
+  // x and march faces (lane v copies them).  The lanes of a cell read them after their wait and a
+  // warp barrier.
+  constexpr int GFV = 2 * D;
+  auto gfs = [&](int P, int slot) -> R& { return sgf[((P & 1) * TC + tcell) * LY::NGF + slot]; };
+  auto issue_gf = [&](int P) {
+    if constexpr (D <= 2) {
+      if (lane == 0) {
+        cp_async(&gfs(P, 0), gface_p(0, NG, face_x(P)));
+        if (lx == TX - 1 && gx < nx) cp_async(&gfs(P, 1), gface_p(0, NG, face_x(P) + 1));
+        if (D == 2) cp_async(&gfs(P, 2), gface_p(MD, NG, face_m(P + 1)));
+      }
+      if (lane < NG && cell_in) {  // (an overhanging cell's upper face would lie past the last face)
+        const int b = 3 + GFV * lane;
+        const uint32_t fxk = face_x(P);
+        cp_async(&gfs(P, b + 0), gface_p(0, lane, fxk));
+        cp_async(&gfs(P, b + 1), gface_p(0, lane, fxk + 1));
+        if (D == 2) {
+          cp_async(&gfs(P, b + 2), gface_p(MD, lane, face_m(P)));
+          cp_async(&gfs(P, b + 3), gface_p(MD, lane, face_m(P + 1)));
+        }
+      }
+    }
+  };
 
   // Carried along the march: the own cell's upper march-face state of plane k and the flux
   // through its lower march face.  In 2-d they are kept in shared memory (thread-private slots by
@@ -762,6 +798,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   if (D == 1) {
     load_cells(0, 0, TX + 4, all_of);
     issue_base(0);
+    issue_gf(0);
     cp_async_commit();
     __syncthreads();
   } else {
@@ -770,6 +807,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     for (int k = kbeg; k <= kbeg + 1; ++k) load_cells(k & 3, k, NHALO, halo_of);
     issue_plane(kbeg + 2);
     issue_base(kbeg);
+    issue_gf(kbeg);
     cp_async_commit();
     R Qm1[NGL][NRV], Qm2[NGL][NRV], Q0[NGL][NRV], Q1[NGL][NRV];
     own_rad(kbeg - 2, Qm2);
@@ -813,13 +851,26 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     __syncwarp();
     if (D >= 2) finish_plane(k + 2);
     if (D >= 2 && k + 1 < kend) issue_plane(k + 3);
-    cp_async_commit();
-    // gas face data of this plane: the cell's lower faces and the march face k+1/2
-    const R vsx = gface(0, NG, face_x(k));
-    const R vsx1 = (lx == TX - 1 && gx < nx) ? gface(0, NG, face_x(k) + 1) : R(0);
-    const R vsm = (D >= 2) ? gface(MD, NG, face_m(k + 1)) : R(0);
-    R vsy = R(0), vsy1 = R(0);
-    if (D == 3) {
+    // gas face data of this plane: the cell's lower faces and the march face k+1/2 (1-d and 2-d:
+    // staged during the previous step, and those of plane k+1 issued now), and the fluxes of the
+    // lane's gas variable through the cell's faces
+    R vsx, vsx1, vsm = R(0), vsy = R(0), vsy1 = R(0);
+    R gfl[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    if constexpr (D <= 2) {
+      vsx = gfs(k, 0);
+      vsx1 = (lx == TX - 1 && gx < nx) ? gfs(k, 1) : R(0);
+      if (D == 2) vsm = gfs(k, 2);
+      if (lane < NG && cell_in) {
+#pragma unroll
+        for (int c = 0; c < GFV; ++c) gfl[c] = gfs(k, 3 + GFV * lane + c);
+      }
+      if (k + 1 < kend) issue_gf(k + 1);
+      cp_async_commit();
+    } else {
+      cp_async_commit();
+      vsx = gface(0, NG, face_x(k));
+      vsx1 = (lx == TX - 1 && gx < nx) ? gface(0, NG, face_x(k) + 1) : R(0);
+      vsm = gface(MD, NG, face_m(k + 1));
       vsy = gface(1, NG, face_y3(k));
       vsy1 = (ly == TY - 1 && gy < ny) ? gface(1, NG, face_y3(k) + nx) : R(0);
     }
@@ -851,14 +902,19 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     auto cls = [&](const R* f) { return gcls == 0 ? f[0] : (gcls == 1 ? f[1] : f[2]); };
     R gnet = R(0);
     if (cell_in) {  // (an overhanging cell's upper face would lie past the last face)
-      const uint32_t fxk = face_x(k);
-      gnet = gface(0, gvar, fxk + 1) * cls(fx_r) - gface(0, gvar, fxk) * cls(fx_l);
-      if (D == 3) {
-        const uint32_t fyk = face_y3(k);
-        gnet = gnet + (gface(1, gvar, fyk + nx) * ty(T_FR, bc_pad(gy)) - gface(1, gvar, fyk) * ty(T_FL, bc_pad(gy)));
+      if constexpr (D == 3) {
+        const uint32_t fxk = face_x(k), fyk = face_y3(k);
+        gfl[0] = gface(0, gvar, fxk);
+        gfl[1] = gface(0, gvar, fxk + 1);
+        gfl[2] = gface(MD, gvar, face_m(k));
+        gfl[3] = gface(MD, gvar, face_m(k + 1));
+        gfl[4] = gface(1, gvar, fyk);
+        gfl[5] = gface(1, gvar, fyk + nx);
       }
-      if (D >= 2)
-        gnet = gnet + (gface(MD, gvar, face_m(k + 1)) * cls(fm_r) - gface(MD, gvar, face_m(k)) * cls(fm_l));
+      // (1-d, 2-d: lanes >= NG carry no gas variable and read zeros, unused)
+      gnet = gfl[1] * cls(fx_r) - gfl[0] * cls(fx_l);
+      if (D == 3) gnet = gnet + (gfl[5] * ty(T_FR, bc_pad(gy)) - gfl[4] * ty(T_FL, bc_pad(gy)));
+      if (D >= 2) gnet = gnet + (gfl[3] * cls(fm_r) - gfl[2] * cls(fm_l));
     }
     // (B reads only planes finished two steps ago and the thread's own column; in 3-d the face
     // states it writes share their space with the fluxes that D of the previous plane reads)
