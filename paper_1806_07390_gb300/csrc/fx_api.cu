@@ -627,9 +627,12 @@ fx_status launch_one_stage(fx_grid* h, const StageArgs<R>& a, const char* what) 
     if (e != cudaSuccess) return cuda_fail(h, e, "timing event");
   }
   switch (h->D) {
-    case 1: e = launch_stage<R, 1, NT>(a, h->GP, h->stream, e4[1], e4[2]); break;
-    case 2: e = launch_stage<R, 2, NT>(a, h->GP, h->stream, e4[1], e4[2]); break;
-    default: e = launch_stage<R, 3, NT>(a, h->GP, h->stream, e4[1], e4[2]); break;
+    case 1: e = launch_stage<R, 1, NT, false>(a, h->GP, h->stream, e4[1], e4[2]); break;
+    case 2:
+      e = h->P.geom == FX_SPH ? launch_stage<R, 2, NT, true>(a, h->GP, h->stream, e4[1], e4[2])
+                              : launch_stage<R, 2, NT, false>(a, h->GP, h->stream, e4[1], e4[2]);
+      break;
+    default: e = launch_stage<R, 3, NT, false>(a, h->GP, h->stream, e4[1], e4[2]); break;
   }
   if (e == cudaSuccess && e4[3]) e = cudaEventRecord(e4[3], h->stream);
   if (e == cudaSuccess && a.phi_out) {
@@ -1108,14 +1111,19 @@ fx_status choose_chunk(fx_grid* h) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
     const int p = h->P.precision;
-    if (h->D == 2)
-      e = p == FX_FP64 ? stage_blocks_per_sm<double, 2, double>(h->GP, h->G, &nb)
-        : p == FX_FP32 ? stage_blocks_per_sm<float, 2, float>(h->GP, h->G, &nb)
-                       : stage_blocks_per_sm<float, 2, double>(h->GP, h->G, &nb);
+    const bool sph = h->P.geom == FX_SPH;
+    if (h->D == 2 && sph)
+      e = p == FX_FP64 ? stage_blocks_per_sm<double, 2, double, true>(h->GP, h->G, &nb)
+        : p == FX_FP32 ? stage_blocks_per_sm<float, 2, float, true>(h->GP, h->G, &nb)
+                       : stage_blocks_per_sm<float, 2, double, true>(h->GP, h->G, &nb);
+    else if (h->D == 2)
+      e = p == FX_FP64 ? stage_blocks_per_sm<double, 2, double, false>(h->GP, h->G, &nb)
+        : p == FX_FP32 ? stage_blocks_per_sm<float, 2, float, false>(h->GP, h->G, &nb)
+                       : stage_blocks_per_sm<float, 2, double, false>(h->GP, h->G, &nb);
     else
-      e = p == FX_FP64 ? stage_blocks_per_sm<double, 3, double>(h->GP, h->G, &nb)
-        : p == FX_FP32 ? stage_blocks_per_sm<float, 3, float>(h->GP, h->G, &nb)
-                       : stage_blocks_per_sm<float, 3, double>(h->GP, h->G, &nb);
+      e = p == FX_FP64 ? stage_blocks_per_sm<double, 3, double, false>(h->GP, h->G, &nb)
+        : p == FX_FP32 ? stage_blocks_per_sm<float, 3, float, false>(h->GP, h->G, &nb)
+                       : stage_blocks_per_sm<float, 3, double, false>(h->GP, h->G, &nb);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
   const int nm = (int)h->P.n[h->D - 1];

@@ -139,10 +139,10 @@ __device__ __forceinline__ void stage_rows(float* gmem, float* rows, int nc, int
   }
 }
 
-// (six resident blocks per SM with the FP64 Newton, whose latency wants warps: 85 registers;
-// the all-FP32 kernel needs fewer registers unconstrained)
+// (resident blocks per SM, for the latency: six with the FP64 Newton, at most 85 registers; seven
+// in the all-FP32 form, 72 registers)
 template <int D, class NT>
-__global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_kernel(StageArgs<float> A) {
+__global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 7) couple_kernel(StageArgs<float> A) {
   using LT = float;
   constexpr int NG = 2 + D, NRV = 1 + D;
   const DevGrid& g = A.g;
@@ -175,14 +175,14 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
   }
   // covariant components: physical = m_q / h_q on the spherical (r, theta) grid
   const bool sph = (D == 2) && g.geom != 0;
-  NT h[2] = {NT(1), NT(1)};
+  float h[2] = {1.0f, 1.0f};
   if (sph && act) {
     const int nx = g.n[0], ny = g.n[1];
     const int gx = (int)(cid % (uint32_t)nx), gy = (int)(cid / (uint32_t)nx);
     const Tab<float> tx{A.tab[0], nx + 4, A.uniform[0] ? A.urow[0] : nullptr};
     const Tab<float> ty{A.tab[1], ny + 4, A.uniform[1] ? A.urow[1] : nullptr};
-    h[0] = (NT)(tx(T_HA, bc_pad(gx)) * ty(T_HA, bc_pad(gy)));
-    h[1] = (NT)(tx(T_HB, bc_pad(gx)) * ty(T_HB, bc_pad(gy)));
+    h[0] = tx(T_HA, bc_pad(gx)) * ty(T_HA, bc_pad(gy));
+    h[1] = tx(T_HB, bc_pad(gx)) * ty(T_HB, bc_pad(gy));
   }
   __syncthreads();
 
@@ -191,31 +191,32 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
   float* const rD0 = srow + (2 * CPL_THREADS + t) * RS;   // first evaluation: dE_g/dT
   const bool work = act && g.couple;
   unsigned st = 0;
-  NT rr = NT(1), ir = NT(1), ke = NT(0), um = NT(0);
+  // The density, its reciprocal, the kinetic energy and T^- are FP32: they come from the FP32
+  // state and set only the FP32 evaluation points of the group energies.  The internal energy u^-
+  // = (rho e)^- - kinetic, the iterate T - T^-, the residual and the gas energy update by
+  // conservation are NT.
+  float rr = 1.0f, ir = 1.0f, ke = 0.0f;
+  NT um = NT(0);
   LT Kc = LT(0), Sc = LT(0), Tst = LT(0);
   float eh = 0.0f, el = 0.0f;
   if (work) {
     // ---- floors, T^- = u^-/(rho c_v), the opacity factors of the (floored) density
-    rr = (NT)rho_f;
-    if (rr < kn.rho_floor) { rr = kn.rho_floor; st |= ST_FLOOR; }
-    // 1/rho: for FP64, an FP32 seed refined by one Newton-Raphson step (relative error ~1e-14)
-    ir = (NT)(1.0f / (float)rr);
-    if (sizeof(NT) == 8) ir = fma(ir, fma(-rr, ir, NT(1)), ir);
+    rr = rho_f;
+    if (rr < kl.rho_floor) { rr = kl.rho_floor; st |= ST_FLOOR; }
+    ir = frcp(rr);
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-      const NT mh = sph ? (NT)m_f[q] / h[q] : (NT)m_f[q];
-      ke += NT(0.5) * mh * mh * ir;
+      const float mh = sph ? m_f[q] * frcp(h[q]) : m_f[q];
+      ke += 0.5f * mh * mh * ir;
     }
-    um = (NT)rhoe_f - ke;
+    um = (NT)rhoe_f - (NT)ke;
     if (um < kn.u_floor) { um = kn.u_floor; st |= ST_FLOOR; }
-    const NT rcv = rr * kn.cv;
-    const LT rcv_f = (LT)rcv;
-    const NT Tm = um * ir * kn.gm1;  // c_v = 1/(gamma - 1)
-    {  // opacity factors in FP32: they only enter the FP32 group arithmetic
-      const LT rrf = (LT)rr;
-      Kc = kl.kappa0 * hpow(rrf, g.kap_rho_h);
-      Sc = kl.sigma0 * rrf;
-    }
+    const LT rcv_f = rr * kl.cv;
+    const NT rcv = (NT)rcv_f;
+    const LT Tm = (LT)um * ir * kl.gm1;  // c_v = 1/(gamma - 1)
+    // opacity factors (they only enter the FP32 group arithmetic)
+    Kc = kl.kappa0 * hpow(rr, g.kap_rho_h);
+    Sc = kl.sigma0 * rr;
     // E^- with its silent positivity floor (Wien tails), and its group sum
     LT Esum = LT(0);
     for (int j = 0; j < G; ++j) {
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
       if (e < kl.E_floor) { e = kl.E_floor; rE[j] = e; }
       Esum += e;
     }
-    const NT ats = kn.atol * (um + (NT)Esum);
+    const NT ats = (NT)(kl.atol * ((LT)um + Esum));
     const LT hh = LT(0.5) * (LT)g.kap_T_h;
     // one evaluation at T: the group sums of E_g(T) - E_g^- (Eq. 25) and of dE_g/dT; the first
     // one also keeps each group's E_g and dE_g/dT (most cells converge from it)
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
     // its residual), so dr/dT, the step and the step test are FP32.
     NT dl = NT(0), dacc = NT(0), r;
     LT drf, dTf = LT(0), lam = LT(1);
-    LT Tacc = (LT)Tm;  // T at the accepted point, in FP32
+    LT Tacc = Tm;      // T at the accepted point, in FP32
     LT lin = LT(0);    // linearised step added to the accepted group energies at convergence
     int it = 0, ls = 0;
     bool ok = false, done = false, need_dir = true, first = true;  // first: accepted point is T^-
@@ -283,9 +284,9 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
       }
       if (done) break;
       const NT dtt = dl + (NT)(lam * dTf);
-      const NT Ttr = Tm + dtt;
-      const bool valid = Ttr > NT(0);
-      const LT Tl = valid ? (LT)Ttr : Tacc;
+      const LT Ttr = Tm + (LT)dtt;
+      const bool valid = Ttr > LT(0);
+      const LT Tl = valid ? Ttr : Tacc;
       LT a, b;
       eval(Tl, a, b, false);
       const NT rt = rcv * dtt + (NT)a;
@@ -304,26 +305,27 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
     }
     // ---- bisection fallback on a bracket around [T^-, T_rad] (reading R11), in T - T^-
     if (!ok) {
+      const NT Tmn = (NT)Tm;
       const NT Tr = sqrt(sqrt((NT)Esum / (kn.aN * NT(6.4939394022668291491))));  // (sum E / a_R)^(1/4)
-      const NT Tc = Tm + dl;
-      NT lo = fmin(fmin(Tc, Tr), Tm) - Tm, hi = fmax(fmax(Tc, Tr), Tm) - Tm;
+      const NT Tc = Tmn + dl;
+      NT lo = fmin(fmin(Tc, Tr), Tmn) - Tmn, hi = fmax(fmax(Tc, Tr), Tmn) - Tmn;
       int phase = 0, cnt = 0;
       bool brk = false;
       NT Te = lo;
       for (int kk = 0; kk < 400 + g.bisect_maxit + 4 && phase < 3; ++kk) {
         LT a, b;
-        eval((LT)(Tm + Te), a, b, false);
+        eval((LT)(Tmn + Te), a, b, false);
         const NT rq = rcv * Te + (NT)a;
         if (phase == 0) {
-          if (rq > NT(0) && cnt < 200) { lo = NT(0.5) * (lo + Tm) - Tm; ++cnt; }  // T_lo /= 2
+          if (rq > NT(0) && cnt < 200) { lo = NT(0.5) * (lo + Tmn) - Tmn; ++cnt; }  // T_lo /= 2
           else { phase = 1; cnt = 0; brk = rq <= NT(0); }
         } else if (phase == 1) {
-          if (rq < NT(0) && cnt < 200) { hi = NT(2) * (hi + Tm) - Tm; ++cnt; }  // T_hi *= 2
+          if (rq < NT(0) && cnt < 200) { hi = NT(2) * (hi + Tmn) - Tmn; ++cnt; }  // T_hi *= 2
           else { brk = brk && rq >= NT(0); cnt = 0; phase = brk ? (g.bisect_maxit > 0 ? 2 : 3) : 3; }
         } else {
           if (rq > NT(0)) hi = Te; else lo = Te;
           ++cnt;
-          if (hi - lo <= kn.rtol * (hi + Tm)) { ok = true; phase = 3; }
+          if (hi - lo <= kn.rtol * (hi + Tmn)) { ok = true; phase = 3; }
           else if (cnt >= g.bisect_maxit) phase = 3;
         }
         Te = phase == 0 ? lo : (phase == 1 ? hi : (phase == 2 ? NT(0.5) * (lo + hi) : Te));
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
       first = false;
     }
     if (!ok) st |= ST_NEWTON;
-    Tst = (LT)(Tm + dl);
+    Tst = Tm + (LT)dl;
     if (A.tstar_out != nullptr) A.tstar_out[cid] = Tst;
 
     // ---- the accepted group energies (from the kept first evaluation when it is the accepted
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
         rE[j] = Eg;
       }
     } else {
-      const LT Ta = (LT)(Tm + dacc);
+      const LT Ta = Tm + (LT)dacc;
       const PlanckAt p = planck_at(A.ptab, kl.aN, Ta);
       const LT ck = kl.cdts * (Kc * hpow(Ta, g.kap_T_h));
       const LT hi = hh * p.invT;
@@ -401,17 +403,15 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 0) couple_k
     // absorption (Eqs. 31-32) in FP32: it is scaled by 1/c^2, and the FP32 momentum it changes
     // would round it to FP32 anyway
     const NT dEsum = (NT)eh + (NT)el;
-    const NT re = ke + (um - dEsum);
-    const float irf = (float)ir;
+    const NT re = (NT)ke + (um - dEsum);
     float vdf = 0.0f;  // v . sum_g dF_g
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-      const float hq = sph ? (float)h[q] : 1.0f;
-      vdf += (sph ? m_f[q] / (hq * hq) : m_f[q]) * irf * fh[q];
+      vdf += (sph ? m_f[q] * frcp(h[q] * h[q]) : m_f[q]) * ir * fh[q];
       m_f[q] = fmaf(-fh[q], kl.ic2, m_f[q]);
     }
     rhoe_f = (float)(re - (NT)(vdf * kl.ic2));
-    rho_f = (float)rr;
+    rho_f = rr;
   }
   if (act) {
     float chk = rho_f + rhoe_f;  // a NaN or inf anywhere in the cell's outputs makes this non-finite

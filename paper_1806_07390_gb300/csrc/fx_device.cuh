@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fx_types.h"
 
 namespace fx {
@@ -99,7 +101,12 @@ __device__ __forceinline__ void recon_linear_c(const MCCoef<R>& c, V pm, V p0, V
   V sL = (p0 - pm) * c.il;
   V sR = (pp - p0) * c.ir;
   V s = V(R(0));
-  if (sL * sR > R(0)) {
+  if constexpr (std::is_same<V, float>::value) {
+    // FP32: the limited slope computed unconditionally and selected (no divergent branch)
+    const V sC = (pp - pm) * c.ic;
+    const V m = fmin(fmin(R(2) * fabs(sL), R(2) * fabs(sR)), fabs(sC));
+    s = sL * sR > R(0) ? (sC > R(0) ? m : -m) : V(R(0));
+  } else if (sL * sR > R(0)) {
     V sC = (pp - pm) * c.ic;
     V m = fmin(fmin(R(2) * fabs(sL), R(2) * fabs(sR)), fabs(sC));
     s = sC > R(0) ? m : -m;
@@ -194,10 +201,28 @@ __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 // With s = sqrt(4 - 3f^2) the closure's two coefficients reduce exactly to
 //   (1 - chi)/2 = 1/3 - f^2/(2+s),   (3 chi - 1)/2 = 3 f^2/(2+s),
 // so P_{nq} = E [1/3 - f^2/(2+s)] delta_{nq} + 3 F_n F_q / ((2+s) c^2 E): one reciprocal of E, one
-// square root and one reciprocal per state, and F = 0 needs no special case.
+// square root and one reciprocal per state, and F = 0 needs no special case.  In FP32 the two
+// special cases (E <= 0: isotropic E/3; f > 1: the direction kept, f clamped to 1) are selects
+// instead of branches: 1/E is taken as 0 for E <= 0, which leaves exactly E/3 on the diagonal, and
+// the clamp factor min(1, 1/f^2) is computed for every state.
 // ---------------------------------------------------------------------------------------------
 template <class R, int D, class V = R>
 __device__ __forceinline__ void m1_row(R ic2, V E, const V* F, int n, V* P) {
+  if constexpr (std::is_same<V, float>::value) {
+    V F2 = F[0] * F[0];
+#pragma unroll
+    for (int q = 1; q < D; ++q) F2 += F[q] * F[q];
+    const V iE = E > R(0) ? frcp(E) : V(R(0));
+    V f2 = F2 * iE * iE * ic2;
+    const V scale = fminf(1.0f, frcp(fmaxf(f2, 1e-30f)));
+    f2 = fminf(f2, 1.0f);
+    const V qd = frcp(R(2) + sqrt(R(4) - R(3) * f2));
+    const V diag = E * (R(1.0 / 3.0) - f2 * qd);
+    const V w = R(3) * qd * iE * ic2 * scale * F[n];
+#pragma unroll
+    for (int q = 0; q < D; ++q) P[q] = w * F[q] + (q == n ? diag : V(R(0)));
+    return;
+  }
   if (!(E > R(0))) {
 #pragma unroll
     for (int q = 0; q < D; ++q) P[q] = q == n ? E * R(1.0 / 3.0) : V(R(0));

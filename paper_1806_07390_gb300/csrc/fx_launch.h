@@ -21,18 +21,18 @@ template <int D, int GL> struct TileShape {
   static constexpr int TY = TC / TX;
 };
 
-// Enqueue one stage (state type R, D dimensions, Newton/bookkeeping type NT) on stream s: the gas
-// face kernel, the radiation/update kernel and, in the FP32 form with the FP64 Newton, the
-// interaction kernel (one thread per cell).  When non-null, `mid` is recorded after the face
-// kernel and `mid2` after the radiation/update kernel (per-kernel timing).  Returns the CUDA
+// Enqueue one stage (state type R, D dimensions, Newton/bookkeeping type NT; SPH: the 2-d
+// spherical grid) on stream s: the gas face kernel, the radiation/update kernel and, in the FP32
+// forms, the interaction kernel (one thread per cell).  When non-null, `mid` is recorded after the
+// face kernel and `mid2` after the radiation/update kernel (per-kernel timing).  Returns the CUDA
 // error of the launches.
-template <class R, int D, class NT>
+template <class R, int D, class NT, bool SPH>
 cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid,
                          cudaEvent_t mid2);
 
 // Resident blocks per multiprocessor of the stage kernel for GP padded groups and G groups
 // (the CUDA occupancy calculator; the host sizes the march chunks from it).
-template <class R, int D, class NT>
+template <class R, int D, class NT, bool SPH>
 cudaError_t stage_blocks_per_sm(int GP, int G, int* nb);
 
 // Whether the interaction runs in couple_kernel rather than inside the stage kernel: in both
@@ -60,12 +60,13 @@ inline size_t stage_smem(int GP, int G) {
 #ifdef FX_LAUNCH_DEFINE
 // Definition, included only by the per-instantiation translation units.  The group arithmetic
 // type of the stage kernel is the state type R.
-template <class R, int D, int GP, class NT>
+template <class R, int D, int GP, class NT, bool SPH>
 static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t mid, cudaEvent_t mid2) {
   constexpr int NGL = groups_per_lane(sizeof(R) == 4, GP);
   constexpr int GL = GP / NGL;
   using TS = TileShape<D, GL>;
-  auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL>;
+  if ((a.g.geom != 0) != SPH) return cudaErrorInvalidValue;  // the grid's geometry decides SPH
+  auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH>;
   const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(a.g.G));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -112,12 +113,12 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
   return e;
 }
 
-template <class R, int D, int GP, class NT>
+template <class R, int D, int GP, class NT, bool SPH>
 static cudaError_t blocks_gp(int G, int* nb) {
   constexpr int NGL = groups_per_lane(sizeof(R) == 4, GP);
   constexpr int GL = GP / NGL;
   using TS = TileShape<D, GL>;
-  auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL>;
+  auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH>;
   const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(G));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -126,23 +127,23 @@ static cudaError_t blocks_gp(int G, int* nb) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, TS::TX * TS::TY * GL, smem);
 }
 
-template <class R, int D, class NT>
+template <class R, int D, class NT, bool SPH>
 cudaError_t stage_blocks_per_sm(int GP, int G, int* nb) {
   switch (GP) {
-    case 8: return blocks_gp<R, D, 8, NT>(G, nb);
-    case 16: return blocks_gp<R, D, 16, NT>(G, nb);
-    case 32: return blocks_gp<R, D, 32, NT>(G, nb);
+    case 8: return blocks_gp<R, D, 8, NT, SPH>(G, nb);
+    case 16: return blocks_gp<R, D, 16, NT, SPH>(G, nb);
+    case 32: return blocks_gp<R, D, 32, NT, SPH>(G, nb);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <class R, int D, class NT>
+template <class R, int D, class NT, bool SPH>
 cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid,
                          cudaEvent_t mid2) {
   switch (GP) {
-    case 8: return launch_gp<R, D, 8, NT>(a, s, mid, mid2);
-    case 16: return launch_gp<R, D, 16, NT>(a, s, mid, mid2);
-    case 32: return launch_gp<R, D, 32, NT>(a, s, mid, mid2);
+    case 8: return launch_gp<R, D, 8, NT, SPH>(a, s, mid, mid2);
+    case 16: return launch_gp<R, D, 16, NT, SPH>(a, s, mid, mid2);
+    case 32: return launch_gp<R, D, 32, NT, SPH>(a, s, mid, mid2);
     default: return cudaErrorInvalidValue;
   }
 }

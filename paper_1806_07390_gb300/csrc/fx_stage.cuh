@@ -433,11 +433,14 @@ inline size_t stage_smem_bytes(int G) {
 //   D  divergence (gas fluxes from the face buffer), RK combine, store of plane k (and, in the
 //      FP64 form, the interaction).
 // B | C and C | D are block barriers; in 3-d also A | B (its face fluxes share shared memory with
-// the face states).
+// the face states).  SPH selects the spherical (r, theta) geometry of a 2-d grid at compile time
+// (the host launches the instantiation that matches the grid): the Cartesian kernel carries none
+// of its scale factors and geometric sources.
 // ---------------------------------------------------------------------------------------------
-template <class R, int D, int GP, int TX, int TY, class LT, class NT, int NGL>
+template <class R, int D, int GP, int TX, int TY, class LT, class NT, int NGL, bool SPH>
 __global__ void __launch_bounds__(TX * TY * (GP / NGL), (sizeof(R) == 4 && NGL == 1) ? 3 : 2)
 stage_kernel(const __grid_constant__ StageArgs<R> A) {
+  static_assert(!SPH || D == 2, "the spherical geometry is 2-d (r, theta)");
   using LY = StageLayout<D, TX, TY>;
   constexpr int GL = GP / NGL;       // lanes per cell
   constexpr int NTH = TX * TY * GL;  // threads per block
@@ -521,7 +524,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     return st[((slot * NRV + v) * PC + sc) * GS + gg];
   };
   auto gas_at = [&](int slot, int v, int sc) -> R& { return sgr[(slot * NG + v) * PC + sc]; };
-  const bool sph = (D == 2) && g.geom != 0;  // spherical (r, theta): x = r, march = theta
+  constexpr bool sph = SPH;  // spherical (r, theta): x = r, march = theta
   // scale factor of component q of the cell with x index ix on plane k
   auto hfac = [&](int q, int ix, int k) -> R {
     if (!sph) return R(1);

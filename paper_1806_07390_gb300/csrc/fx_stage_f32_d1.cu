@@ -4,7 +4,7 @@
 #include "fx_launch.h"
 
 namespace fx {
-template cudaError_t launch_stage<float, 1, float>(const StageArgs<float>&, int, cudaStream_t, cudaEvent_t,
+template cudaError_t launch_stage<float, 1, float, false>(const StageArgs<float>&, int, cudaStream_t, cudaEvent_t,
                                                   cudaEvent_t);
-template cudaError_t stage_blocks_per_sm<float, 1, float>(int, int, int*);
+template cudaError_t stage_blocks_per_sm<float, 1, float, false>(int, int, int*);
 }  // namespace fx

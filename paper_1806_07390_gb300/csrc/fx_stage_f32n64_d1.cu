@@ -4,7 +4,7 @@
 #include "fx_launch.h"
 
 namespace fx {
-template cudaError_t launch_stage<float, 1, double>(const StageArgs<float>&, int, cudaStream_t, cudaEvent_t,
+template cudaError_t launch_stage<float, 1, double, false>(const StageArgs<float>&, int, cudaStream_t, cudaEvent_t,
                                                   cudaEvent_t);
-template cudaError_t stage_blocks_per_sm<float, 1, double>(int, int, int*);
+template cudaError_t stage_blocks_per_sm<float, 1, double, false>(int, int, int*);
 }  // namespace fx

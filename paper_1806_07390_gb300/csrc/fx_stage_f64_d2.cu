@@ -1,9 +1,9 @@
-// Stage kernel instantiations: state double, group arithmetic double, Newton/bookkeeping double, 2-d.
+// Stage kernel instantiations: state double, group arithmetic double, Newton/bookkeeping double, 2-d Cartesian.
 #define FX_LAUNCH_DEFINE
 #include "fx_launch.h"
 
 namespace fx {
-template cudaError_t launch_stage<double, 2, double>(const StageArgs<double>&, int, cudaStream_t, cudaEvent_t,
+template cudaError_t launch_stage<double, 2, double, false>(const StageArgs<double>&, int, cudaStream_t, cudaEvent_t,
                                                   cudaEvent_t);
-template cudaError_t stage_blocks_per_sm<double, 2, double>(int, int, int*);
+template cudaError_t stage_blocks_per_sm<double, 2, double, false>(int, int, int*);
 }  // namespace fx

@@ -1,0 +1,10 @@
+// Stage kernel instantiations: state double, group arithmetic double, Newton/bookkeeping double,
+// 2-d spherical (r, theta).
+#define FX_LAUNCH_DEFINE
+#include "fx_launch.h"
+
+namespace fx {
+template cudaError_t launch_stage<double, 2, double, true>(const StageArgs<double>&, int, cudaStream_t, cudaEvent_t,
+                                                  cudaEvent_t);
+template cudaError_t stage_blocks_per_sm<double, 2, double, true>(int, int, int*);
+}  // namespace fx

@@ -3,7 +3,7 @@
 #include "fx_launch.h"
 
 namespace fx {
-template cudaError_t launch_stage<double, 3, double>(const StageArgs<double>&, int, cudaStream_t, cudaEvent_t,
+template cudaError_t launch_stage<double, 3, double, false>(const StageArgs<double>&, int, cudaStream_t, cudaEvent_t,
                                                   cudaEvent_t);
-template cudaError_t stage_blocks_per_sm<double, 3, double>(int, int, int*);
+template cudaError_t stage_blocks_per_sm<double, 3, double, false>(int, int, int*);
 }  // namespace fx
