@@ -66,6 +66,35 @@ template <class R> struct Tab {
 template <class R, class V>
 __device__ __forceinline__ void recon_parabolic(const Tab<R>& t, int ip, V pm, V p0, V pp, V& a, V& b) {
   V dl = p0 - pm, dr = pp - p0;
+  if constexpr (std::is_same<V, float>::value) {
+    // FP32: the same decisions taken as selects over values computed for every cell, so a warp
+    // runs one path
+    const bool ext = dl * dr <= R(0);
+    V a0 = t(T_WA0, ip) * pm + t(T_WA1, ip) * p0 + t(T_WA2, ip) * pp;
+    V b0 = t(T_WB0, ip) * pm + t(T_WB1, ip) * p0 + t(T_WB2, ip) * pp;
+    {
+      const V l = pm + dl * t(T_SL2, ip), h = p0 - dl * t(T_TL2, ip);
+      const V lo = dl < R(0) ? h : l, hi = dl < R(0) ? l : h;
+      a0 = a0 < lo ? lo : (a0 > hi ? hi : a0);
+    }
+    {
+      const V l = p0 + dr * t(T_SR2, ip), h = pp - dr * t(T_TR2, ip);
+      const V lo = dr < R(0) ? h : l, hi = dr < R(0) ? l : h;
+      b0 = b0 < lo ? lo : (b0 > hi ? hi : b0);
+    }
+    const V sl = t(T_AL0, ip) * a0 + t(T_AL1, ip) * p0 + t(T_AL2, ip) * b0;
+    const V sr = t(T_AR0, ip) * a0 + t(T_AR1, ip) * p0 + t(T_AR2, ip) * b0;
+    const bool inc = !(sl * sr >= R(0));  // extremum inside the cell
+    const V asl = fabs(sl), asr = fabs(sr);
+    const bool flat = asl == asr, lower = asl < asr;
+    const V bz = a0 + (p0 - a0) * t(T_RHL, ip);  // zero slope at the lower face
+    const V az = b0 + (p0 - b0) * t(T_RHR, ip);  // zero slope at the upper face
+    const V an = inc ? (flat ? p0 : (lower ? a0 : az)) : a0;
+    const V bn = inc ? (flat ? p0 : (lower ? bz : b0)) : b0;
+    a = ext ? p0 : an;
+    b = ext ? p0 : bn;
+    return;
+  }
   if (dl * dr <= R(0)) { a = p0; b = p0; return; }  // extremum of the data (R4)
   a = t(T_WA0, ip) * pm + t(T_WA1, ip) * p0 + t(T_WA2, ip) * pp;
   b = t(T_WB0, ip) * pm + t(T_WB1, ip) * p0 + t(T_WB2, ip) * pp;
@@ -161,6 +190,30 @@ __device__ __forceinline__ void hllc(R gam, const V* L, const V* Rs, V* f, V& vs
   V dl = rl * (SL - ul), dr = rr * (SR - ur);
   V Ss = (pr - pl + ul * dl - ur * dr) / (dl - dr);
   vstar = Ss;
+  if constexpr (std::is_same<V, float>::value) {
+    // FP32: the side k (left when the face is supersonic to the right or the contact moves
+    // right) and its plain flux F_k for every face; the star correction S_k (U*_k - U_k) is
+    // added by a select where the face is subsonic
+    const bool supL = SL >= R(0), supR = !supL && SR < R(0), sup = supL || supR;
+    const bool left = supL || (!supR && Ss >= R(0));
+    const V rk = left ? rl : rr, pk = left ? pl : pr, uk = left ? ul : ur;
+    const V Ek = left ? El : Er, Sk = left ? SL : SR;
+    const V sku = Sk - uk;
+    const V fac = rk * sku / (Sk - Ss);
+    const V f0 = rk * uk, f1 = rk * uk * uk + pk;
+    f[0] = sup ? f0 : f0 + Sk * (fac - rk);
+    f[1] = sup ? f1 : f1 + Sk * (fac * Ss - rk * uk);
+#pragma unroll
+    for (int q = 1; q < D; ++q) {
+      const V wq = left ? L[2 + q] : Rs[2 + q];
+      const V fq = rk * uk * wq;
+      f[1 + q] = sup ? fq : fq + Sk * (fac * wq - rk * wq);
+    }
+    const V Es = fac * (Ek / rk + (Ss - uk) * (Ss + pk / (rk * sku)));
+    const V fE = (Ek + pk) * uk;
+    f[1 + D] = sup ? fE : fE + Sk * (Es - Ek);
+    return;
+  }
   if (SL >= R(0)) {
     f[0] = rl * ul;
     f[1] = rl * ul * ul + pl;

@@ -717,11 +717,12 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     m1_row<R, D>(KR.ic2, QR[0], QR + 1, d, PR);
     R tau = R(0.5) * (chiL + chiR) * ell;
     R eps = tau > R(1) ? frcp(tau) : R(1);
-    const R* Qu = vstar >= R(0) ? QL : QR;
-    out[0] = R(0.5) * (QL[1 + d] + QR[1 + d]) - eps * KR.hc * (QR[0] - QL[0]) + vstar * Qu[0];
+    const bool up = vstar >= R(0);  // upwind side of the advective terms (element-wise selects)
+    out[0] = R(0.5) * (QL[1 + d] + QR[1 + d]) - eps * KR.hc * (QR[0] - QL[0]) + vstar * (up ? QL[0] : QR[0]);
 #pragma unroll
     for (int q = 0; q < D; ++q)
-      out[1 + q] = KR.hc2 * (PL[q] + PR[q]) - KR.hc * (QR[1 + q] - QL[1 + q]) + vstar * Qu[1 + q];
+      out[1 + q] = KR.hc2 * (PL[q] + PR[q]) - KR.hc * (QR[1 + q] - QL[1 + q]) +
+                   vstar * (up ? QL[1 + q] : QR[1 + q]);
   };
   R ef[NGL];
 #pragma unroll
