@@ -8,11 +8,15 @@
 
 namespace fx {
 
-// Groups per lane of the stage kernel: two in the FP32 forms when a cell has more than 16
-// groups (GP = 32), else one.  GP = next power of two >= G is the cell's padded group count.
-// (With one group per lane a 256-thread tile holds 256/GP cells: at GP = 32 that is 8 cells and
-// a large halo share; below, one group per lane runs three blocks per SM and is the faster.)
-constexpr int groups_per_lane(bool fp32, int GP) { return (fp32 && GP >= 32) ? 2 : 1; }
+// Groups per lane of the stage kernel: two in the FP32 forms when a cell has more than 16 groups
+// (GP = 32), and in 1-d and 2-d already from 9 groups (GP = 16); else one.  GP = next power of two
+// >= G is the cell's padded group count.  Two groups per lane share the per-cell work of a thread
+// (indexing, opacity factors, gas variables, the halo branches) between two groups and double
+// the tile's cells (a smaller halo share); the kernel is then held to two blocks per SM instead of
+// three (kh2d, GP = 16: 0.547 -> 0.525 ms; lognormal3d, GP = 16: 18.6 -> 19.3 ms, so 3-d keeps one).
+constexpr int groups_per_lane(bool fp32, int D, int GP) {
+  return (fp32 && (GP >= 32 || (D <= 2 && GP >= 16))) ? 2 : 1;
+}
 
 // Tile shape of the stage kernel for D dimensions and GL lanes per cell (256 threads per block).
 template <int D, int GL> struct TileShape {
@@ -44,7 +48,7 @@ template <class R, class NT> constexpr bool split_interaction() {
 // Dynamic shared memory of the stage kernel (tile shape from D and GP).
 template <class R, int D, int GP>
 inline size_t stage_smem_gp(int G) {
-  constexpr int GL = GP / groups_per_lane(sizeof(R) == 4, GP);
+  constexpr int GL = GP / groups_per_lane(sizeof(R) == 4, D, GP);
   return stage_smem_bytes<R, D, TileShape<D, GL>::TX, TileShape<D, GL>::TY>(stage_gstride<D, GP>(G));
 }
 template <class R, int D>
@@ -62,7 +66,7 @@ inline size_t stage_smem(int GP, int G) {
 // type of the stage kernel is the state type R.
 template <class R, int D, int GP, class NT, bool SPH>
 static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t mid, cudaEvent_t mid2) {
-  constexpr int NGL = groups_per_lane(sizeof(R) == 4, GP);
+  constexpr int NGL = groups_per_lane(sizeof(R) == 4, D, GP);
   constexpr int GL = GP / NGL;
   using TS = TileShape<D, GL>;
   if ((a.g.geom != 0) != SPH) return cudaErrorInvalidValue;  // the grid's geometry decides SPH
@@ -115,7 +119,7 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
 
 template <class R, int D, int GP, class NT, bool SPH>
 static cudaError_t blocks_gp(int G, int* nb) {
-  constexpr int NGL = groups_per_lane(sizeof(R) == 4, GP);
+  constexpr int NGL = groups_per_lane(sizeof(R) == 4, D, GP);
   constexpr int GL = GP / NGL;
   using TS = TileShape<D, GL>;
   auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH>;
