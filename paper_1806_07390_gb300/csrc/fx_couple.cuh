@@ -414,14 +414,20 @@ __global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 7) couple_k
     rho_f = rr;
   }
   if (act) {
-    float chk = rho_f + rhoe_f;  // a NaN or inf anywhere in the cell's outputs makes this non-finite
+    // A NaN or inf anywhere in the cell's outputs makes chk non-finite: a non-finite E_g or F_g
+    // reaches the gas energy (through the group sum of the energy changes) or the momentum
+    // (through the group sums of the flux changes), so the rows need no scan of their own when
+    // the interaction ran.
+    float chk = rho_f + rhoe_f;
     A.out[cid] = rho_f;
 #pragma unroll
     for (int q = 0; q < D; ++q) { A.out[(1 + q) * ncell + cid] = m_f[q]; chk += m_f[q]; }
     A.out[(NG - 1) * ncell + cid] = rhoe_f;
-    for (int v = 0; v < NRV; ++v) {
-      const float* rv = srow + (v * CPL_THREADS + t) * RS;
-      for (int j = 0; j < G; ++j) chk += rv[j] * 0.0f;
+    if (!work) {
+      for (int v = 0; v < NRV; ++v) {
+        const float* rv = srow + (v * CPL_THREADS + t) * RS;
+        for (int j = 0; j < G; ++j) chk += rv[j] * 0.0f;
+      }
     }
     if (!isfinite(chk)) st |= ST_NONFINITE;
     if (st) atomicOr(A.status, st);

@@ -177,10 +177,16 @@ def test_kh2d_full_size_sampled_windows(fxmod, precision, tol):
             H.assert_parity(small, gcell, r, tol, natural=True)
 
 
-def test_nonfinite_state_is_reported(fxmod):
-    pb, prim = W.kh_2d(nx=16, ny=16, ngroups=4, nsteps=1)
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32n64"])
+@pytest.mark.parametrize("where", ["gas", "E", "F"])
+def test_nonfinite_state_is_reported(fxmod, precision, where):
+    # one NaN in a gas variable, a group energy or a group flux of one cell: every form reports it
+    pb, prim = W.kh_2d(nx=16, ny=16, ngroups=4, nsteps=1, precision=precision)
     s = oracle.init_equilibrium(pb, prim)
-    s[5] = np.nan
+    ncell, G, NG = 16 * 16, 4, 4
+    c = 37
+    idx = {"gas": c, "E": NG * ncell + c * G + 2, "F": NG * ncell + (ncell + c) * G + 1}[where]
+    s[idx] = np.nan
     g = fxmod.Grid(pb)
     g.upload(s)
     g.step(pb.dt, 1)
