@@ -448,6 +448,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   constexpr int PX = LY::PX, PC = LY::PC, TC = LY::TC, NFX = LY::NFX, NFY = LY::NFY;
   constexpr int MD = D - 1;  // march direction (D >= 2)
   static_assert(NGL == 1 || (sizeof(LT) == 4 && GL >= 2 + D), "two groups per lane: FP32 groups, gas in lanes < 2+D");
+  static_assert(TX >= 2 * NGL, "the x-halo lanes of the two tile edges are disjoint");
 
   const DevGrid& g = A.g;
   const Consts<R>& KR = A.k(R(0));
@@ -858,11 +859,11 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     // gas face data of this plane: the cell's lower faces and the march face k+1/2 (1-d and 2-d:
     // staged during the previous step, and those of plane k+1 issued now), and the fluxes of the
     // lane's gas variable through the cell's faces
-    R vsx, vsx1, vsm = R(0), vsy = R(0), vsy1 = R(0);
+    R vsx, vsx1 = R(0), vsm = R(0), vsy = R(0), vsy1 = R(0);
     R gfl[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     if constexpr (D <= 2) {
       vsx = gfs(k, 0);
-      vsx1 = (lx == TX - 1 && gx < nx) ? gfs(k, 1) : R(0);
+      if (NGL == 1) vsx1 = (lx == TX - 1 && gx < nx) ? gfs(k, 1) : R(0);
       if (D == 2) vsm = gfs(k, 2);
       if (lane < NG && cell_in) {
 #pragma unroll
@@ -873,7 +874,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     } else {
       cp_async_commit();
       vsx = gface(0, NG, face_x(k));
-      vsx1 = (lx == TX - 1 && gx < nx) ? gface(0, NG, face_x(k) + 1) : R(0);
+      if (NGL == 1) vsx1 = (lx == TX - 1 && gx < nx) ? gface(0, NG, face_x(k) + 1) : R(0);
       vsm = gface(MD, NG, face_m(k + 1));
       vsy = gface(1, NG, face_y3(k));
       vsy1 = (ly == TY - 1 && gy < ny) ? gface(1, NG, face_y3(k) + nx) : R(0);
@@ -946,22 +947,24 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
 #pragma unroll
         for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1) + lx + 1) * GS + gg] = bx[j][v];
       }
-      if (lx == 0) {  // halo cell -1: its upper-face state is the left state of face 0
-        R Qc[NRV], ta[NRV], tb[NRV];
-        rad_cell(s0, sc_own - 2, gg, Qc);
-        recon_rad(mc_coef(tx, bc_pad(gx - 1)), Qc, Qa, Q0[j], ta, tb);
-        if (hasj[j]) {
+      if constexpr (NGL == 1) {  // (two groups per lane: after the loop, one group per lane)
+        if (lx == 0) {  // halo cell -1: its upper-face state is the left state of face 0
+          R Qc[NRV], ta[NRV], tb[NRV];
+          rad_cell(s0, sc_own - 2, gg, Qc);
+          recon_rad(mc_coef(tx, bc_pad(gx - 1)), Qc, Qa, Q0[j], ta, tb);
+          if (hasj[j]) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * GS + gg] = tb[v];
+            for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * GS + gg] = tb[v];
+          }
         }
-      }
-      if (lx == TX - 1) {  // halo cell TX: its lower-face state is the right state of face TX
-        R Qc[NRV], ta[NRV], tb[NRV];
-        rad_cell(s0, sc_own + 2, gg, Qc);
-        recon_rad(mc_coef(tx, bc_pad(gx + 1)), Q0[j], Qb, Qc, ta, tb);
-        if (hasj[j]) {
+        if (lx == TX - 1) {  // halo cell TX: its lower-face state is the right state of face TX
+          R Qc[NRV], ta[NRV], tb[NRV];
+          rad_cell(s0, sc_own + 2, gg, Qc);
+          recon_rad(mc_coef(tx, bc_pad(gx + 1)), Q0[j], Qb, Qc, ta, tb);
+          if (hasj[j]) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * GS + gg] = ta[v];
+            for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * GS + gg] = ta[v];
+          }
         }
       }
       if (D == 3) {
@@ -998,6 +1001,35 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         for (int v = 0; v < NRV; ++v) car(k + 1, 0, v, j) = bm1[j][v];
       }
     }
+    // two groups per lane: the row's x halo cells -1 and TX (the upper-face state of cell -1, left
+    // state of face 0; the lower-face state of cell TX, right state of face TX), one group per
+    // lane of the NGL cells nearest each edge: the warp runs one reconstruction for them, not NGL
+    if (NGL > 1 && lx < NGL) {
+      const int h = lx * GL + lane;
+      if (h < G) {
+        const int sc0 = scell(0, ly);
+        R Qc[NRV], Qd[NRV], Qe[NRV], ta[NRV], tb[NRV];
+        rad_cell(s0, sc0 - 2, h, Qc);
+        rad_cell(s0, sc0 - 1, h, Qd);
+        rad_cell(s0, sc0, h, Qe);
+        recon_rad(mc_coef(tx, bc_pad(x0 - 1)), Qc, Qd, Qe, ta, tb);
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * GS + h] = tb[v];
+      }
+    }
+    if (NGL > 1 && lx >= TX - NGL) {
+      const int h = (lx - (TX - NGL)) * GL + lane;
+      if (h < G) {
+        const int sc1 = scell(TX - 1, ly);
+        R Qc[NRV], Qd[NRV], Qe[NRV], ta[NRV], tb[NRV];
+        rad_cell(s0, sc1, h, Qc);
+        rad_cell(s0, sc1 + 1, h, Qd);
+        rad_cell(s0, sc1 + 2, h, Qe);
+        recon_rad(mc_coef(tx, bc_pad(x0 + TX)), Qc, Qd, Qe, ta, tb);
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * GS + h] = ta[v];
+      }
+    }
     __syncthreads();
     // ---- C: radiation face fluxes
     R rfm_new[NGL][NRV] = {};
@@ -1015,7 +1047,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
 #pragma unroll
           for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx) * GS + gg] = out[v];
         }
-        if (lx == TX - 1) {
+        if (NGL == 1 && lx == TX - 1) {
           R QR[NRV];
 #pragma unroll
           for (int v = 0; v < NRV; ++v) QR[v] = rax[(v * TY + ly) * GS + gg];
@@ -1057,6 +1089,34 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
 #pragma unroll
           for (int v = 0; v < NRV; ++v) car(k + 1, 1, v, j) = rfm_new[j][v];
         }
+      }
+    }
+    // two groups per lane: the row's face TX (between the tile's last cell and the halo cell TX),
+    // one group per lane of the NGL cells nearest the upper edge: left state from the face-state
+    // buffer, right state from the halo reconstruction, the contact speed of the gas face
+    if (NGL > 1 && lx >= TX - NGL) {
+      const int h = (lx - (TX - NGL)) * GL + lane;
+      if (h < G) {
+        const int fT = ly * (TX + 1) + TX;  // face TX of row ly
+        const int sc1 = scell(TX - 1, ly);
+        const int xl = x0 + TX - 1;         // the tile's last cell of the row
+        R QL[NRV], QR[NRV], out[NRV];
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) {
+          QL[v] = rbx[(v * NFX + fT) * GS + h];
+          QR[v] = rax[(v * TY + ly) * GS + h];
+        }
+        const R eh = R(sgc->efac_of(h, R(0)));
+        const R chiL = pk[(s0 * 2) * PC + sc1] * eh + pk[(s0 * 2 + 1) * PC + sc1];
+        const R chiR = pk[(s0 * 2) * PC + sc1 + 1] * eh + pk[(s0 * 2 + 1) * PC + sc1 + 1];
+        R vsT = R(0);
+        if (xl < nx) {
+          if constexpr (D <= 2) vsT = sgf[((k & 1) * TC + ly * TX + TX - 1) * LY::NGF + 1];
+          else vsT = gface(0, NG, ((uint32_t)k * ny + gyc) * fx_nx + (uint32_t)xl + 1);
+        }
+        rad_face(0, QL, QR, chiL, chiR, tx(T_ELL, bc_pad(xl) + 1), vsT, out);
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fT) * GS + h] = out[v];
       }
     }
     __syncthreads();
