@@ -582,6 +582,7 @@ StageArgs<R> stage_args(fx_grid* h) {
   a.ptab.tab = reinterpret_cast<const float4*>(h->ws + h->off_ptab);
   a.ptab.nu = h->ptab_nu;
   a.ptab.u0 = h->ptab_u0;
+  a.ptab.ng = h->G;
   a.pk = h->pk;
   a.status = reinterpret_cast<unsigned*>(h->ws + h->off_status);
   a.chunk = h->chunk;
@@ -1182,9 +1183,15 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
     if (e != cudaSuccess) return cuda_fail(h, e, "volume upload");
     off += align_up((size_t)np * sizeof(double));
   }
-  e = cudaMemcpyAsync(h->ws + h->off_ptab, h->ptab.data(), h->ptab.size() * sizeof(float4),
-                      cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  {  // the device copy is node-major ([nu][G]); the host keeps the group-major table
+    const int G = h->G, nu = h->ptab_nu;
+    std::vector<float4> nm((size_t)G * nu);
+    for (int g = 0; g < G; ++g)
+      for (int i = 0; i < nu; ++i) nm[(size_t)i * G + g] = h->ptab[(size_t)g * nu + i];
+    e = cudaMemcpyAsync(h->ws + h->off_ptab, nm.data(), nm.size() * sizeof(float4),
+                        cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "Planck table upload");
   e = cudaMemcpyAsync(h->ws + h->off_gc, &h->gc, sizeof(GroupConst), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

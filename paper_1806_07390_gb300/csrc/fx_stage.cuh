@@ -49,9 +49,12 @@ struct PlanckParams {
 // (L, h dL/du) with L = log2 Int_{eps_g-1/2/T}^{eps_g+1/2/T} t^3/(e^t-1) dt, built on the host in
 // FP64 and interpolated with cubic Hermite polynomials.
 struct PlanckTable {
-  const float4* tab;  // [G][nu]: (L - floor(L), h dL/du, floor(L), 2^floor(L) or 0 below 2^-126)
+  // [nu][G], node-major (an evaluation reads nodes i and i+1 of every group: two contiguous
+  // runs): (L - floor(L), h dL/du, floor(L), 2^floor(L) or 0 below 2^-126)
+  const float4* tab;
   int nu;
   float u0;
+  int ng;  // groups per node
 };
 
 template <class R> struct StageArgs {
@@ -166,8 +169,8 @@ struct Coupler {
     } else {
       const int i = (int)s;
       const float t = s - (float)i;
-      const float4 p0 = __ldg(ptab.tab + lane * ptab.nu + i);
-      const float4 p1 = __ldg(ptab.tab + lane * ptab.nu + i + 1);
+      const float4 p0 = __ldg(ptab.tab + i * ptab.ng + lane);
+      const float4 p1 = __ldg(ptab.tab + (i + 1) * ptab.ng + lane);
       const float t2 = t * t, t3 = t2 * t;
       // node values relative to floor(L) of the left node: small numbers, full FP32 precision
       const float d1 = (p1.z - p0.z) + p1.x;
