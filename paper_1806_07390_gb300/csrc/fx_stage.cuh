@@ -373,6 +373,14 @@ template <class R> __device__ __forceinline__ void cp_async(R* smem, const R* gm
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Named barrier `id` (1..15) of `n` threads: arrive without waiting, or arrive and wait.  The
+// shared-memory writes a thread made before arriving are visible to the threads that waited.
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_wait(int id, int n) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Shared-memory layout of stage_kernel (offsets in elements of R; used by the kernel and by the
@@ -452,6 +460,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   constexpr int MD = D - 1;  // march direction (D >= 2)
   static_assert(NGL == 1 || (sizeof(LT) == 4 && GL >= 2 + D), "two groups per lane: FP32 groups, gas in lanes < 2+D");
   static_assert(TX >= 2 * NGL, "the x-halo lanes of the two tile edges are disjoint");
+  static_assert(NTH % 32 == 0 && NTH / 32 <= 16 && 32 % GL == 0, "whole warps, whole cells per warp, named barriers");
 
   const DevGrid& g = A.g;
   const Consts<R>& KR = A.k(R(0));
@@ -647,7 +656,13 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
 #pragma unroll
       for (int v = 0; v < NRV; ++v) cp_async(&rad_at(slot, v, sc, gg), A.in + NG * ncell + (v * ncell + c) * G + gg);
     }
-    for (int i = tid; i < NHALO; i += NTH) {
+    // halo opacity factors: in 2-d the lower halo cells (-2, -1) by the first warp and the upper
+    // ones (TX, TX+1) by the last, the warps whose edge cells read them in phase C (so that their
+    // restaging needs no block barrier after C; see the C | D hand-off)
+    static_assert(D != 2 || NHALO == 4, "2-d tiles are one row: four halo cells");
+    const int ih = D == 2 ? (tid < 2 ? tid : (tid >= NTH - 2 ? tid - (NTH - 4) : -1)) : (tid < NHALO ? tid : -1);
+    if (ih >= 0) {
+      const int i = ih;
       int sx, sy;
       halo_of(i, sx, sy);
       bool f[3];
@@ -1122,7 +1137,23 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fT) * GS + h] = out[v];
       }
     }
-    __syncthreads();
+    if constexpr (D == 2 && NGL > 1) {
+      // C | D hand-off in 2-d with two groups per lane: a cell's update needs the flux through
+      // its upper x face, computed by the next cell, which is in the next warp only at a warp's
+      // last cell.  So each warp signals the warp below it (named barrier w) and waits only for
+      // the warp above it (named barrier w+1), instead of a block barrier.  What a block barrier
+      // also ordered is ordered here as well: a warp restages its cells' opacity factors of this
+      // plane (read in C by the next cell) only after the warp above has passed C, and the halo
+      // opacity factors are staged by the warp that reads them.  (At one group per lane, three
+      // blocks per SM at 80 registers, the barrier indices cost spills: the block barrier stays.)
+      constexpr int NW = NTH / 32;
+      const int w = tid >> 5;
+      __syncwarp();
+      if (w > 0) bar_arrive(w, 64);
+      if (w < NW - 1) bar_wait(w + 1, 64);
+    } else {
+      __syncthreads();
+    }
     // ---- D: update: divergence, RK combine, coupling, store
     {
       const R g0 = gas_at(s0, gvar, sc_own);  // own gas variable of plane k (lanes < NG)
