@@ -79,8 +79,8 @@ __device__ __forceinline__ void planck_group(const PlanckTable& ptab, const Plan
                                              const float* edge, float& B, float& dB) {
   float I, dLdu;
   if (p.mode == 1) {
-    const float4 p0 = __ldg(ptab.tab + p.i * ptab.ng + g);
-    const float4 p1 = __ldg(ptab.tab + (p.i + 1) * ptab.ng + g);
+    const float4 p0 = __ldg(ptab.tab + p.i * ptab.si + g * ptab.sg);
+    const float4 p1 = __ldg(ptab.tab + (p.i + 1) * ptab.si + g * ptab.sg);
     // node values relative to floor(L) of the left node (small numbers, full FP32 precision);
     // I = 2^(L - floor L) 2^floor(L), the second factor exact from the table
     const float d1 = (p1.z - p0.z) + p1.x;

@@ -49,12 +49,13 @@ struct PlanckParams {
 // (L, h dL/du) with L = log2 Int_{eps_g-1/2/T}^{eps_g+1/2/T} t^3/(e^t-1) dt, built on the host in
 // FP64 and interpolated with cubic Hermite polynomials.
 struct PlanckTable {
-  // [nu][G], node-major (an evaluation reads nodes i and i+1 of every group: two contiguous
-  // runs): (L - floor(L), h dL/du, floor(L), 2^floor(L) or 0 below 2^-126)
+  // entry (node i, group g) at tab[i * si + g * sg]: (L - floor(L), h dL/du, floor(L), 2^floor(L)
+  // or 0 below 2^-126).  An evaluation reads nodes i and i+1 of every group; the host picks the
+  // layout (node-major si = G, sg = 1, or group-major si = 1, sg = nu)
   const float4* tab;
   int nu;
   float u0;
-  int ng;  // groups per node
+  int si, sg;
 };
 
 template <class R> struct StageArgs {
@@ -169,8 +170,8 @@ struct Coupler {
     } else {
       const int i = (int)s;
       const float t = s - (float)i;
-      const float4 p0 = __ldg(ptab.tab + i * ptab.ng + lane);
-      const float4 p1 = __ldg(ptab.tab + (i + 1) * ptab.ng + lane);
+      const float4 p0 = __ldg(ptab.tab + i * ptab.si + lane * ptab.sg);
+      const float4 p1 = __ldg(ptab.tab + (i + 1) * ptab.si + lane * ptab.sg);
       const float t2 = t * t, t3 = t2 * t;
       // node values relative to floor(L) of the left node: small numbers, full FP32 precision
       const float d1 = (p1.z - p0.z) + p1.x;
