@@ -371,11 +371,12 @@ void build_planck_table(const fx_params& P, const GroupConst& gc, const PlanckPa
     }
 }
 
-// Layout of the device Planck table (measured on the interaction kernel): node-major in 1-d and
-// 2-d (kh2d 0.156 -> 0.142 ms per launch against group-major), group-major in 3-d (lognormal3d
-// 3.77 -> 3.47 ms).  A warp's cells read nodes i and i+1 of every group; which layout shares
-// more cache sectors across its lanes depends on how their temperatures spread over the nodes.
-bool ptab_node_major(const fx_grid* h) { return h->D <= 2; }
+// Layout of the device Planck table, a measured choice (interaction kernel per launch, node-major
+// against group-major): kh2d (2-d, 16 groups) 0.142 against 0.156 ms; lognormal3d (3-d, 12
+// groups) 3.77 against 3.47 ms; blobs2d (2-d, 8 groups) 0.033 against 0.029 ms.  A warp's cells
+// read nodes i and i+1 of every group: group-major keeps the lanes' nodes of one group on one
+// cache line when their temperatures differ, node-major keeps a lane's groups together.
+bool ptab_node_major(const fx_grid* h) { return h->D <= 2 && h->G >= 16; }
 
 template <class R> const R* dev_tab(const fx_grid* h, int d) {
   return reinterpret_cast<const R*>(h->ws + h->off_tab[d]);
