@@ -96,6 +96,21 @@ def test_lognormal3d_small_fp64(fxmod):
     check_totals(pb, tot, ref)
 
 
+@pytest.mark.parametrize("form", ["fp32", "fp32n64"])
+@pytest.mark.parametrize("G", [8, 16, 21])
+def test_reflecting_walls_fp32_forms(fxmod, form, G):
+    # mirror ghosts (negated normal components of v and F) on both x walls and the upper march
+    # wall, with one group per lane (G = 8) and two (G = 16, 21: 32-cell and 16-cell tiles whose
+    # planes are ordered by warp-to-warp hand-offs); three tiles across x with a ragged last one
+    pb, prim = W.kh_2d(nx=70, ny=30, ngroups=G, nsteps=3, precision=form)
+    pb.bc_lo = ("reflect", "outflow", "periodic")
+    pb.bc_hi = ("reflect", "reflect", "periodic")
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, 1e-4, natural=True)
+
+
 def test_reflecting_walls_and_random_state_fp64(fxmod):
     pb, _ = W.kh_2d(nx=20, ny=18, ngroups=6, nsteps=2)
     pb.bc_lo = ("reflect", "outflow", "periodic")
