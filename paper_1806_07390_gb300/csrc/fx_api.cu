@@ -1136,7 +1136,8 @@ fx_status choose_chunk(fx_grid* h) {
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
   const int nm = (int)h->P.n[h->D - 1];
-  const int TC = 256 / (h->GP / groups_per_lane(h->elem == 4, h->D, h->GP));  // cells per tile
+  const int ngl = groups_per_lane(h->elem == 4, h->D, h->GP);
+  const int TC = tile_cells(h->D, h->GP / ngl, ngl);  // cells per tile
   const int TX = h->D == 3 ? (TC >= 16 ? TC / 4 : TC / 2) : TC, TY = TC / TX;
   int64_t tiles = (h->P.n[0] + TX - 1) / TX;
   if (h->D == 3) tiles *= (h->P.n[1] + TY - 1) / TY;

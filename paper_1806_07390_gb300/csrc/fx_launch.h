@@ -12,15 +12,25 @@ namespace fx {
 // (GP = 32), and in 1-d and 2-d already from 9 groups (GP = 16); else one.  GP = next power of two
 // >= G is the cell's padded group count.  Two groups per lane share the per-cell work of a thread
 // (indexing, opacity factors, gas variables, the halo branches) between two groups and double
-// the tile's cells (a smaller halo share); the kernel is then held to two blocks per SM instead of
-// three (kh2d, GP = 16: 0.547 -> 0.525 ms; lognormal3d, GP = 16: 18.6 -> 19.3 ms, so 3-d keeps one).
+// the tile's cells (a smaller halo share), at more registers per thread (kh2d, GP = 16: stage
+// kernel 0.547 -> 0.525 ms with 32-cell tiles; lognormal3d, GP = 16: 18.6 -> 19.3 ms, so 3-d keeps
+// one).
 constexpr int groups_per_lane(bool fp32, int D, int GP) {
   return (fp32 && (GP >= 32 || (D <= 2 && GP >= 16))) ? 2 : 1;
 }
 
-// Tile shape of the stage kernel for D dimensions and GL lanes per cell (256 threads per block).
-template <int D, int GL> struct TileShape {
-  static constexpr int TC = 256 / GL;                       // cells per tile
+// Cells per tile of the stage kernel for D dimensions and GL lanes per cell: 256 threads per
+// block, except 2-d with two groups per lane of 8 lanes (16 padded groups): a 20-cell tile of 160
+// threads, four blocks (20 warps) per SM at 96 registers instead of two blocks of 256 threads
+// (16 warps) at 121: the kernel is latency-bound there (kh2d stage kernel 0.462 -> 0.455 ms;
+// 16-, 24- and 28-cell tiles were slower).
+__host__ __device__ constexpr int tile_cells(int D, int GL, int NGL) {
+  return (D == 2 && GL == 8 && NGL == 2) ? 20 : 256 / GL;
+}
+
+// Tile shape of the stage kernel for D dimensions, GL lanes per cell and NGL groups per lane.
+template <int D, int GL, int NGL> struct TileShape {
+  static constexpr int TC = tile_cells(D, GL, NGL);         // cells per tile
   static constexpr int TX = (D == 3) ? (TC >= 16 ? TC / 4 : TC / 2) : TC;
   static constexpr int TY = TC / TX;
 };
@@ -48,8 +58,9 @@ template <class R, class NT> constexpr bool split_interaction() {
 // Dynamic shared memory of the stage kernel (tile shape from D and GP).
 template <class R, int D, int GP>
 inline size_t stage_smem_gp(int G) {
-  constexpr int GL = GP / groups_per_lane(sizeof(R) == 4, D, GP);
-  return stage_smem_bytes<R, D, TileShape<D, GL>::TX, TileShape<D, GL>::TY>(stage_gstride<D, GP>(G));
+  constexpr int NGL = groups_per_lane(sizeof(R) == 4, D, GP);
+  using TS = TileShape<D, GP / NGL, NGL>;
+  return stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(G));
 }
 template <class R, int D>
 inline size_t stage_smem(int GP, int G) {
@@ -68,7 +79,7 @@ template <class R, int D, int GP, class NT, bool SPH>
 static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t mid, cudaEvent_t mid2) {
   constexpr int NGL = groups_per_lane(sizeof(R) == 4, D, GP);
   constexpr int GL = GP / NGL;
-  using TS = TileShape<D, GL>;
+  using TS = TileShape<D, GL, NGL>;
   if ((a.g.geom != 0) != SPH) return cudaErrorInvalidValue;  // the grid's geometry decides SPH
   auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH>;
   const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(a.g.G));
@@ -121,7 +132,7 @@ template <class R, int D, int GP, class NT, bool SPH>
 static cudaError_t blocks_gp(int G, int* nb) {
   constexpr int NGL = groups_per_lane(sizeof(R) == 4, D, GP);
   constexpr int GL = GP / NGL;
-  using TS = TileShape<D, GL>;
+  using TS = TileShape<D, GL, NGL>;
   auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH>;
   const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(G));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

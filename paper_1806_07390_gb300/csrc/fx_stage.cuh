@@ -450,7 +450,8 @@ inline size_t stage_smem_bytes(int G) {
 // of its scale factors and geometric sources.
 // ---------------------------------------------------------------------------------------------
 template <class R, int D, int GP, int TX, int TY, class LT, class NT, int NGL, bool SPH>
-__global__ void __launch_bounds__(TX * TY * (GP / NGL), (sizeof(R) == 4 && NGL == 1) ? 3 : 2)
+__global__ void __launch_bounds__(TX * TY * (GP / NGL),
+                                  (sizeof(R) == 4 && NGL == 1) ? 3 : (TX * TY * (GP / NGL) <= 160 ? 4 : 2))
 stage_kernel(const __grid_constant__ StageArgs<R> A) {
   static_assert(!SPH || D == 2, "the spherical geometry is 2-d (r, theta)");
   using LY = StageLayout<D, TX, TY>;
