@@ -8,15 +8,15 @@
 
 namespace fx {
 
-// Groups per lane of the stage kernel: two in the FP32 forms when a cell has more than 16 groups
-// (GP = 32), and in 1-d and 2-d already from 9 groups (GP = 16); else one.  GP = next power of two
-// >= G is the cell's padded group count.  Two groups per lane share the per-cell work of a thread
-// (indexing, opacity factors, gas variables, the halo branches) between two groups and double
-// the tile's cells (a smaller halo share), at more registers per thread (kh2d, GP = 16: stage
-// kernel 0.547 -> 0.525 ms with 32-cell tiles; lognormal3d, GP = 16: 18.6 -> 19.3 ms, so 3-d keeps
-// one).
+// Groups per lane of the stage kernel: two in the FP32 forms when a cell has more than 8 groups
+// (GP >= 16), else one.  GP = next power of two >= G is the cell's padded group count.  Two groups
+// per lane share the per-cell work of a thread (indexing, opacity factors, gas variables, the
+// halo branches) between two groups and double the tile's cells (a smaller halo share), at more
+// registers per thread (GP = 16: kh2d stage kernel 0.547 -> 0.525 ms with 32-cell tiles;
+// lognormal3d 18.6 -> 17.3 ms once the tile-edge work ran one group per lane).
 constexpr int groups_per_lane(bool fp32, int D, int GP) {
-  return (fp32 && (GP >= 32 || (D <= 2 && GP >= 16))) ? 2 : 1;
+  (void)D;
+  return (fp32 && GP >= 16) ? 2 : 1;
 }
 
 // Cells per tile of the stage kernel for D dimensions and GL lanes per cell: 256 threads per
