@@ -69,7 +69,9 @@ enum { FX_NTOTALS = 6 };
  *                      FX_FP32_F64NEWTON: as FX_FP32, but the temperature iterate, residual
  *                      and energy/momentum bookkeeping of the coupling in FP64.
  *                      State buffers are double for FX_FP64 and float otherwise.
- *   rad_recon_order    1 = linear + MC limiter (the paper's choice for radiation).
+ *   rad_recon_order    1 = linear + MC limiter (the paper's choice for radiation); 2 = the
+ *                      gas's n = 2 parabola with its limiters, per group and moment (the
+ *                      forward step only: fx_adjoint returns FX_ERR_UNSUPPORTED).
  *   couple             1 = apply the implicit interaction after each RK stage.
  *   newton_maxit, bisect_maxit, newton_rtol
  *                      coupling iteration caps and the relative temperature step tolerance.

@@ -883,7 +883,7 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   }
   if (P.precision != FX_FP64 && P.precision != FX_FP32 && P.precision != FX_FP32_F64NEWTON)
     return FX_ERR_ARG;
-  if (P.rad_recon_order != 1) return FX_ERR_UNSUPPORTED;
+  if (P.rad_recon_order != 1 && P.rad_recon_order != 2) return FX_ERR_ARG;
   if (!(P.gamma > 1.0) || !(P.c_light > 0.0) || !(P.a_rad > 0.0)) return FX_ERR_ARG;
   if (!half_integer(P.kap_rho_exp) || !half_integer(P.kap_T_exp)) return FX_ERR_UNSUPPORTED;
   if (!(P.eps_min > 0.0) || !(P.eps_max > P.eps_min)) return FX_ERR_ARG;
@@ -925,6 +925,7 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
     g.bc_hi[d] = d < P.dims ? P.bc_hi[d] : FX_PERIODIC;
   }
   g.geom = P.geom;
+  g.rad_order = P.rad_recon_order;
   g.ncell = h->ncell;
   g.gamma = P.gamma;
   g.c = P.c_light;
@@ -1054,6 +1055,8 @@ static fx_status adjoint_entry(fx_grid* h, double dt, int nsteps, int k, void* a
   if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
   if (!(dt > 0.0) || nsteps < 0 || k < 1) return fail(h, FX_ERR_ARG, "dt must be > 0, nsteps >= 0, k >= 1");
   if (h->P.geom != FX_CART) return fail(h, FX_ERR_UNSUPPORTED, "the adjoint supports Cartesian grids");
+  if (h->P.rad_recon_order != 1)
+    return fail(h, FX_ERR_UNSUPPORTED, "the adjoint supports the linear radiation reconstruction");
   if (!adj_ws || adj_bytes < adj_layout(h, nsteps, k).bytes || (reinterpret_cast<uintptr_t>(adj_ws) % kAlign) != 0)
     return fail(h, FX_ERR_WORKSPACE, "adjoint workspace missing, too small or not 256-byte aligned");
   unsigned char* ws = static_cast<unsigned char*>(adj_ws);
@@ -1122,17 +1125,17 @@ fx_status choose_chunk(fx_grid* h) {
     const int p = h->P.precision;
     const bool sph = h->P.geom == FX_SPH;
     if (h->D == 2 && sph)
-      e = p == FX_FP64 ? stage_blocks_per_sm<double, 2, double, true>(h->GP, h->G, &nb)
-        : p == FX_FP32 ? stage_blocks_per_sm<float, 2, float, true>(h->GP, h->G, &nb)
-                       : stage_blocks_per_sm<float, 2, double, true>(h->GP, h->G, &nb);
+      e = p == FX_FP64 ? stage_blocks_per_sm<double, 2, double, true>(h->GP, h->G, h->P.rad_recon_order, &nb)
+        : p == FX_FP32 ? stage_blocks_per_sm<float, 2, float, true>(h->GP, h->G, h->P.rad_recon_order, &nb)
+                       : stage_blocks_per_sm<float, 2, double, true>(h->GP, h->G, h->P.rad_recon_order, &nb);
     else if (h->D == 2)
-      e = p == FX_FP64 ? stage_blocks_per_sm<double, 2, double, false>(h->GP, h->G, &nb)
-        : p == FX_FP32 ? stage_blocks_per_sm<float, 2, float, false>(h->GP, h->G, &nb)
-                       : stage_blocks_per_sm<float, 2, double, false>(h->GP, h->G, &nb);
+      e = p == FX_FP64 ? stage_blocks_per_sm<double, 2, double, false>(h->GP, h->G, h->P.rad_recon_order, &nb)
+        : p == FX_FP32 ? stage_blocks_per_sm<float, 2, float, false>(h->GP, h->G, h->P.rad_recon_order, &nb)
+                       : stage_blocks_per_sm<float, 2, double, false>(h->GP, h->G, h->P.rad_recon_order, &nb);
     else
-      e = p == FX_FP64 ? stage_blocks_per_sm<double, 3, double, false>(h->GP, h->G, &nb)
-        : p == FX_FP32 ? stage_blocks_per_sm<float, 3, float, false>(h->GP, h->G, &nb)
-                       : stage_blocks_per_sm<float, 3, double, false>(h->GP, h->G, &nb);
+      e = p == FX_FP64 ? stage_blocks_per_sm<double, 3, double, false>(h->GP, h->G, h->P.rad_recon_order, &nb)
+        : p == FX_FP32 ? stage_blocks_per_sm<float, 3, float, false>(h->GP, h->G, h->P.rad_recon_order, &nb)
+                       : stage_blocks_per_sm<float, 3, double, false>(h->GP, h->G, h->P.rad_recon_order, &nb);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
   const int nm = (int)h->P.n[h->D - 1];

@@ -44,10 +44,11 @@ template <class R, int D, class NT, bool SPH>
 cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEvent_t mid,
                          cudaEvent_t mid2);
 
-// Resident blocks per multiprocessor of the stage kernel for GP padded groups and G groups
-// (the CUDA occupancy calculator; the host sizes the march chunks from it).
+// Resident blocks per multiprocessor of the stage kernel for GP padded groups, G groups and
+// radiation reconstruction order ro (the CUDA occupancy calculator; the host sizes the march
+// chunks from it).
 template <class R, int D, class NT, bool SPH>
-cudaError_t stage_blocks_per_sm(int GP, int G, int* nb);
+cudaError_t stage_blocks_per_sm(int GP, int G, int ro, int* nb);
 
 // Whether the interaction runs in couple_kernel rather than inside the stage kernel: in both
 // forms with an FP32 state.
@@ -81,7 +82,8 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
   constexpr int GL = GP / NGL;
   using TS = TileShape<D, GL, NGL>;
   if ((a.g.geom != 0) != SPH) return cudaErrorInvalidValue;  // the grid's geometry decides SPH
-  auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH>;
+  auto kern = a.g.rad_order == 2 ? stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 2>
+                                 : stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 1>;
   const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(a.g.G));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -129,11 +131,12 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
 }
 
 template <class R, int D, int GP, class NT, bool SPH>
-static cudaError_t blocks_gp(int G, int* nb) {
+static cudaError_t blocks_gp(int G, int ro, int* nb) {
   constexpr int NGL = groups_per_lane(sizeof(R) == 4, D, GP);
   constexpr int GL = GP / NGL;
   using TS = TileShape<D, GL, NGL>;
-  auto kern = stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH>;
+  auto kern = ro == 2 ? stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 2>
+                      : stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 1>;
   const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(G));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -143,11 +146,11 @@ static cudaError_t blocks_gp(int G, int* nb) {
 }
 
 template <class R, int D, class NT, bool SPH>
-cudaError_t stage_blocks_per_sm(int GP, int G, int* nb) {
+cudaError_t stage_blocks_per_sm(int GP, int G, int ro, int* nb) {
   switch (GP) {
-    case 8: return blocks_gp<R, D, 8, NT, SPH>(G, nb);
-    case 16: return blocks_gp<R, D, 16, NT, SPH>(G, nb);
-    case 32: return blocks_gp<R, D, 32, NT, SPH>(G, nb);
+    case 8: return blocks_gp<R, D, 8, NT, SPH>(G, ro, nb);
+    case 16: return blocks_gp<R, D, 16, NT, SPH>(G, ro, nb);
+    case 32: return blocks_gp<R, D, 32, NT, SPH>(G, ro, nb);
     default: return cudaErrorInvalidValue;
   }
 }

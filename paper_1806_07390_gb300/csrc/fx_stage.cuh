@@ -447,9 +447,11 @@ inline size_t stage_smem_bytes(int G) {
 // B | C and C | D are block barriers; in 3-d also A | B (its face fluxes share shared memory with
 // the face states).  SPH selects the spherical (r, theta) geometry of a 2-d grid at compile time
 // (the host launches the instantiation that matches the grid): the Cartesian kernel carries none
-// of its scale factors and geometric sources.
+// of its scale factors and geometric sources.  RO is the radiation reconstruction (1: linear with
+// the MC limiter, the paper's; 2: the gas's parabola), also a compile-time choice: a run-time one
+// cost the kernel spills.
 // ---------------------------------------------------------------------------------------------
-template <class R, int D, int GP, int TX, int TY, class LT, class NT, int NGL, bool SPH>
+template <class R, int D, int GP, int TX, int TY, class LT, class NT, int NGL, bool SPH, int RO>
 __global__ void __launch_bounds__(TX * TY * (GP / NGL),
                                   (sizeof(R) == 4 && NGL == 1) ? 3 : (TX * TY * (GP / NGL) <= 160 ? 4 : 2))
 stage_kernel(const __grid_constant__ StageArgs<R> A) {
@@ -751,9 +753,17 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   auto chi_of = [&](int slot, int sc, int j) {
     return pk[(slot * 2) * PC + sc] * ef[j] + pk[(slot * 2 + 1) * PC + sc];
   };
-  auto recon_rad = [&](const MCCoef<R>& c, const R* Qm, const R* Q0, const R* Qp, R* a, R* b) {
+  // radiation reconstruction of one cell from its neighbours along a direction (table t, row ip;
+  // c: its MC coefficients): linear with the MC limiter, or (RO 2) the gas's parabola
+  auto recon_rad = [&](const MCCoef<R>& c, const Tab<R>& t, int ip, const R* Qm, const R* Q0, const R* Qp,
+                       R* a, R* b) {
+    if constexpr (RO == 2) {
 #pragma unroll
-    for (int v = 0; v < NRV; ++v) recon_linear_c(c, Qm[v], Q0[v], Qp[v], a[v], b[v]);
+      for (int v = 0; v < NRV; ++v) recon_parabolic(t, ip, Qm[v], Q0[v], Qp[v], a[v], b[v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) recon_linear_c(c, Qm[v], Q0[v], Qp[v], a[v], b[v]);
+    }
   };
   auto rad_cell = [&](int slot, int sc, int gg, R* Q) {
 #pragma unroll
@@ -847,8 +857,8 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
 #pragma unroll
     for (int j = 0; j < NGL; ++j) {
       R a_[NRV], bprev[NRV];
-      recon_rad(mp, Qm2[j], Qm1[j], Q0[j], a_, bprev);
-      recon_rad(m0, Qm1[j], Q0[j], Q1[j], a_, bm0[j]);
+      recon_rad(mp, tm, bc_pad(kbeg - 1), Qm2[j], Qm1[j], Q0[j], a_, bprev);
+      recon_rad(m0, tm, bc_pad(kbeg), Qm1[j], Q0[j], Q1[j], a_, bm0[j]);
       rad_face(MD, bprev, a_, chi_of((kbeg - 1) & 3, sc_own, j), chi_of(kbeg & 3, sc_own, j), ell, vs,
                rfm_old[j]);
       if (SCAR) {
@@ -962,7 +972,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       R Qa[NRV], Qb[NRV];
       rad_cell(s0, sc_own - 1, gg, Qa);
       rad_cell(s0, sc_own + 1, gg, Qb);
-      recon_rad(mcx, Qa, Q0[j], Qb, ax[j], bx[j]);
+      recon_rad(mcx, tx, ipx, Qa, Q0[j], Qb, ax[j], bx[j]);
       if (hasj[j]) {
 #pragma unroll
         for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1) + lx + 1) * GS + gg] = bx[j][v];
@@ -971,7 +981,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         if (lx == 0) {  // halo cell -1: its upper-face state is the left state of face 0
           R Qc[NRV], ta[NRV], tb[NRV];
           rad_cell(s0, sc_own - 2, gg, Qc);
-          recon_rad(mc_coef(tx, bc_pad(gx - 1)), Qc, Qa, Q0[j], ta, tb);
+          recon_rad(mc_coef(tx, bc_pad(gx - 1)), tx, bc_pad(gx - 1), Qc, Qa, Q0[j], ta, tb);
           if (hasj[j]) {
 #pragma unroll
             for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * GS + gg] = tb[v];
@@ -980,7 +990,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         if (lx == TX - 1) {  // halo cell TX: its lower-face state is the right state of face TX
           R Qc[NRV], ta[NRV], tb[NRV];
           rad_cell(s0, sc_own + 2, gg, Qc);
-          recon_rad(mc_coef(tx, bc_pad(gx + 1)), Q0[j], Qb, Qc, ta, tb);
+          recon_rad(mc_coef(tx, bc_pad(gx + 1)), tx, bc_pad(gx + 1), Q0[j], Qb, Qc, ta, tb);
           if (hasj[j]) {
 #pragma unroll
             for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * GS + gg] = ta[v];
@@ -991,7 +1001,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         R Qa3[NRV], Qb3[NRV];
         rad_cell(s0, sc_own - PX, gg, Qa3);
         rad_cell(s0, sc_own + PX, gg, Qb3);
-        recon_rad(mc_coef(ty, bc_pad(gy)), Qa3, Q0[j], Qb3, ay[j], by[j]);
+        recon_rad(mc_coef(ty, bc_pad(gy)), ty, bc_pad(gy), Qa3, Q0[j], Qb3, ay[j], by[j]);
         if (hasj[j]) {
 #pragma unroll
           for (int v = 0; v < NRV; ++v) rby[(v * NFY + (ly + 1) * TX + lx) * GS + gg] = by[j][v];
@@ -999,7 +1009,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         if (ly == 0) {
           R Qc[NRV], ta[NRV], tb[NRV];
           rad_cell(s0, sc_own - 2 * PX, gg, Qc);
-          recon_rad(mc_coef(ty, bc_pad(gy - 1)), Qc, Qa3, Q0[j], ta, tb);
+          recon_rad(mc_coef(ty, bc_pad(gy - 1)), ty, bc_pad(gy - 1), Qc, Qa3, Q0[j], ta, tb);
           if (hasj[j]) {
 #pragma unroll
             for (int v = 0; v < NRV; ++v) rby[(v * NFY + lx) * GS + gg] = tb[v];
@@ -1008,14 +1018,14 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         if (ly == TY - 1) {
           R Qc[NRV], ta[NRV], tb[NRV];
           rad_cell(s0, sc_own + 2 * PX, gg, Qc);
-          recon_rad(mc_coef(ty, bc_pad(gy + 1)), Q0[j], Qb3, Qc, ta, tb);
+          recon_rad(mc_coef(ty, bc_pad(gy + 1)), ty, bc_pad(gy + 1), Q0[j], Qb3, Qc, ta, tb);
           if (hasj[j]) {
 #pragma unroll
             for (int v = 0; v < NRV; ++v) ray[(v * TX + lx) * GS + gg] = ta[v];
           }
         }
       }
-      if (D >= 2) recon_rad(mc_coef(tm, bc_pad(k + 1)), Q0[j], Q1[j], Q2[j], am1[j], bm1[j]);
+      if (D >= 2) recon_rad(mc_coef(tm, bc_pad(k + 1)), tm, bc_pad(k + 1), Q0[j], Q1[j], Q2[j], am1[j], bm1[j]);
       if (SCAR) {
 #pragma unroll
         for (int v = 0; v < NRV; ++v) car(k + 1, 0, v, j) = bm1[j][v];
@@ -1032,7 +1042,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         rad_cell(s0, sc0 - 2, h, Qc);
         rad_cell(s0, sc0 - 1, h, Qd);
         rad_cell(s0, sc0, h, Qe);
-        recon_rad(mc_coef(tx, bc_pad(x0 - 1)), Qc, Qd, Qe, ta, tb);
+        recon_rad(mc_coef(tx, bc_pad(x0 - 1)), tx, bc_pad(x0 - 1), Qc, Qd, Qe, ta, tb);
 #pragma unroll
         for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * GS + h] = tb[v];
       }
@@ -1045,7 +1055,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         rad_cell(s0, sc1, h, Qc);
         rad_cell(s0, sc1 + 1, h, Qd);
         rad_cell(s0, sc1 + 2, h, Qe);
-        recon_rad(mc_coef(tx, bc_pad(x0 + TX)), Qc, Qd, Qe, ta, tb);
+        recon_rad(mc_coef(tx, bc_pad(x0 + TX)), tx, bc_pad(x0 + TX), Qc, Qd, Qe, ta, tb);
 #pragma unroll
         for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * GS + h] = ta[v];
       }

@@ -6,5 +6,5 @@
 namespace fx {
 template cudaError_t launch_stage<float, 2, double, false>(const StageArgs<float>&, int, cudaStream_t, cudaEvent_t,
                                                   cudaEvent_t);
-template cudaError_t stage_blocks_per_sm<float, 2, double, false>(int, int, int*);
+template cudaError_t stage_blocks_per_sm<float, 2, double, false>(int, int, int, int*);
 }  // namespace fx

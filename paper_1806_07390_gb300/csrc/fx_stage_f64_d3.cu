@@ -5,5 +5,5 @@
 namespace fx {
 template cudaError_t launch_stage<double, 3, double, false>(const StageArgs<double>&, int, cudaStream_t, cudaEvent_t,
                                                   cudaEvent_t);
-template cudaError_t stage_blocks_per_sm<double, 3, double, false>(int, int, int*);
+template cudaError_t stage_blocks_per_sm<double, 3, double, false>(int, int, int, int*);
 }  // namespace fx

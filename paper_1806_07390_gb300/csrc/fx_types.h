@@ -35,6 +35,7 @@ struct DevGrid {
   int newton_maxit, bisect_maxit;
   double newton_rtol;
   int couple;
+  int rad_order;  // radiation reconstruction: 1 linear with the MC limiter, 2 the gas's parabola
 };
 
 }  // namespace fx

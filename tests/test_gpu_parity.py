@@ -259,6 +259,45 @@ def test_spherical_2d_small(fxmod, precision, tol):
         H.assert_parity(pb, got, ref, tol, natural=True)
 
 
+@pytest.mark.parametrize("maker", ["kh", "lognormal", "spherical"])
+def test_second_order_radiation_reconstruction_fp64(fxmod, maker):
+    # rad_recon_order = 2: the gas's n = 2 parabola with its limiters for E and F, per group
+    # (reading R1), on a Cartesian 2-d, a 3-d and the spherical grid
+    if maker == "kh":
+        pb, prim = W.kh_2d(nx=40, ny=36, ngroups=6, nsteps=3)
+    elif maker == "lognormal":
+        pb, prim = W.lognormal_3d(shape=(12, 10, 9), ngroups=5, nsteps=2, precision="fp64")
+    else:
+        pb, prim = W.spherical_2d(nr=30, nth=16, ngroups=6, nsteps=3, precision="fp64")
+    pb.rad_recon_order = 2
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp32n64"])
+@pytest.mark.parametrize("G", [8, 16])
+def test_second_order_radiation_reconstruction_fp32_forms(fxmod, form, G):
+    pb, prim = W.kh_2d(nx=48, ny=40, ngroups=G, nsteps=3, precision=form)
+    pb.rad_recon_order = 2
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, 1e-4, natural=True)
+
+
+def test_second_order_radiation_reconstruction_has_no_adjoint(fxmod):
+    pb, prim = W.blobs_2d(shape=(24, 20), ngroups=4, nsteps=2, precision="fp64")
+    pb.rad_recon_order = 2
+    g = fxmod.Grid(pb)
+    g.init_equilibrium(prim)
+    with pytest.raises(fxmod.FxError) as e:
+        g.adjoint_forward(g.adjoint_workspace(2, 1), pb.dt, 2, 1)
+    assert e.value.status == -7
+    g.close()
+
+
 def test_spherical_static_atmosphere_gpu(fxmod):
     # uniform p and E, v = F = 0: flux divergence and geometric sources cancel (Eqs. 84-85)
     pb, _ = W.spherical_2d(nr=24, nth=16, ngroups=3, nsteps=1, precision="fp64")
