@@ -139,10 +139,10 @@ __device__ __forceinline__ void stage_rows(float* gmem, float* rows, int nc, int
   }
 }
 
-// (resident blocks per SM, for the latency: six with the FP64 Newton, at most 85 registers; seven
-// in the all-FP32 form, 72 registers)
+// (seven resident blocks per SM, at most 72 registers, for the latency: with the FP64 Newton
+// 0.142 -> 0.133 ms per kh2d launch against six blocks at 80 registers; eight gained nothing more)
 template <int D, class NT>
-__global__ void __launch_bounds__(CPL_THREADS, sizeof(NT) == 8 ? 6 : 7) couple_kernel(StageArgs<float> A) {
+__global__ void __launch_bounds__(CPL_THREADS, 7) couple_kernel(StageArgs<float> A) {
   using LT = float;
   constexpr int NG = 2 + D, NRV = 1 + D;
   const DevGrid& g = A.g;
