@@ -35,8 +35,8 @@ UNIT = "zone-group-stages/s"
 # DRAM bytes per launch (mean of the two RK stages) of the radiation/update kernel and of the
 # interaction kernel, from the committed ncu capture profiles/traffic_stage_kernel_kh2d_1024x1024x16.txt;
 # None where not captured for the current kernels.
-TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": 570.0e6, "fp32": 569.8e6, "fp64": 1186.3e6}}
-TRAFFIC_INTERACTION = {"kh2d": {"fp32n64": None, "fp32": None}}
+TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": 569.7e6, "fp32": 569.7e6, "fp64": 1184.9e6}}
+TRAFFIC_INTERACTION = {"kh2d": {"fp32n64": 370.9e6, "fp32": 370.9e6}}
 
 
 def load_peaks():
