@@ -45,7 +45,8 @@ typedef enum {
 
 enum { FX_OUTFLOW = 0, FX_PERIODIC = 1, FX_REFLECT = 2, FX_AXIS = 3 }; /* Sec. 7.5 */
 enum { FX_CART = 0, FX_SPH = 1 };       /* Cartesian, or spherical (x1 -> r, x2 -> theta)  */
-enum { FX_MAP_ID = 0, FX_MAP_EXP = 1 }; /* radial map r = x1 or r = exp(x1) (Appendix A)   */
+/* radial map (Appendix A): r = x1, r = exp(x1), or r = r_t sinh(x1 / r_t) (r_t = map_rt) */
+enum { FX_MAP_ID = 0, FX_MAP_EXP = 1, FX_MAP_SINH = 2 };
 enum { FX_FP64 = 0, FX_FP32 = 1, FX_FP32_F64NEWTON = 2 }; /* precision forms (see fx_params)  */
 enum { FX_NTOTALS = 6 };
 
@@ -54,6 +55,8 @@ enum { FX_NTOTALS = 6 };
  *                      d >= dims); each direction is uniform in its generic coordinate x^d
  *                      on [x_lo[d], x_hi[d]].
  *   geom, map1         FX_CART, or FX_SPH with dims == 2: x1 -> r through map1, x2 = theta.
+ *   map_rt             r_t of FX_MAP_SINH (> 0; ignored by the other maps): nearly uniform in r
+ *                      for r << r_t, logarithmic for r >> r_t.
  *   bc_lo/bc_hi        boundary condition per direction and side.
  *   ngroups            energy groups (1..32), logarithmically spaced edges
  *                      eps_min (eps_max/eps_min)^(g/ngroups) (Sec. 4).
@@ -96,6 +99,7 @@ typedef struct {
   int newton_maxit, bisect_maxit;
   double newton_rtol;
   double rho_floor, p_floor, E_floor;
+  double map_rt;
 } fx_params;
 
 /* State layout (upload, download, and the device copy inside the workspace): ncell = prod n[d],

@@ -43,6 +43,7 @@ class OrcParams(ctypes.Structure):
         ("newton_maxit", ctypes.c_int), ("bisect_maxit", ctypes.c_int),
         ("newton_rtol", ctypes.c_double), ("rho_floor", ctypes.c_double),
         ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double), ("nthreads", ctypes.c_int),
+        ("map_rt", ctypes.c_double),
     ]
 
 
@@ -94,6 +95,7 @@ def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0) -> OrcParams:
         P.bc_hi[d] = BC_CODES[pb.bc_hi[d]]
     P.geom = GEOM_CODES[pb.geom]
     P.map1 = MAP_CODES[pb.map1]
+    P.map_rt = pb.map_rt
     P.ngroups = pb.ngroups
     P.eps_min, P.eps_max = pb.eps_min, pb.eps_max
     P.gamma, P.c_light, P.a_rad = pb.gamma, pb.c_light, pb.a_rad

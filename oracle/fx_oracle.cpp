@@ -125,12 +125,13 @@ static inline void branch(unsigned site, unsigned outcome) {
 extern "C" {
 enum { ORC_OUTFLOW = 0, ORC_PERIODIC = 1, ORC_REFLECT = 2, ORC_AXIS = 3 };
 enum { ORC_CART = 0, ORC_SPH = 1 };
-enum { ORC_MAP_ID = 0, ORC_MAP_EXP = 1 };
+enum { ORC_MAP_ID = 0, ORC_MAP_EXP = 1, ORC_MAP_SINH = 2 };
 struct orc_params {
   int dims;
   int n[3];
   int geom;           // ORC_CART, or ORC_SPH: x^1 -> r, x^2 -> theta (x^3 -> phi, ignorable)
-  int map1;           // radial map: ORC_MAP_ID (r = x^1) or ORC_MAP_EXP (r = exp(x^1))
+  int map1;           // radial map: ORC_MAP_ID (r = x^1), ORC_MAP_EXP (r = exp(x^1)) or
+                      // ORC_MAP_SINH (r = r_t sinh(x^1 / r_t), r_t = map_rt; Appendix A)
   double x_lo[3], x_hi[3];
   int bc_lo[3], bc_hi[3];
   int ngroups;
@@ -144,6 +145,7 @@ struct orc_params {
   double newton_rtol;
   double rho_floor, p_floor, E_floor;
   int nthreads;
+  double map_rt;
 };
 }
 
@@ -234,6 +236,10 @@ static double weight1(const orc_params& P, int d, double x) {
   if (P.geom == ORC_CART || d == 2) return 1.0;
   if (d == 0) {
     if (P.map1 == ORC_MAP_EXP) { double r = std::exp(x); return r * r * r; }
+    if (P.map1 == ORC_MAP_SINH) {
+      const double r = P.map_rt * std::sinh(x / P.map_rt);
+      return r * r * std::cosh(x / P.map_rt);
+    }
     return x * x;
   }
   return std::fabs(std::sin(x));
@@ -281,8 +287,14 @@ struct Geometry {
   std::vector<double> G222, G332;        // per padded theta cell: <Gamma^2_22>, <Gamma^3_32>
 };
 
-static double rmap(const orc_params& P, double x) { return P.map1 == ORC_MAP_EXP ? std::exp(x) : x; }
-static double drmap(const orc_params& P, double x) { return P.map1 == ORC_MAP_EXP ? std::exp(x) : 1.0; }
+static double rmap(const orc_params& P, double x) {
+  if (P.map1 == ORC_MAP_SINH) return P.map_rt * std::sinh(x / P.map_rt);
+  return P.map1 == ORC_MAP_EXP ? std::exp(x) : x;
+}
+static double drmap(const orc_params& P, double x) {
+  if (P.map1 == ORC_MAP_SINH) return std::cosh(x / P.map_rt);
+  return P.map1 == ORC_MAP_EXP ? std::exp(x) : 1.0;
+}
 
 static void build_geometry(const orc_params& P, Geometry& G) {
   init_gl();

@@ -154,9 +154,37 @@ fx_status cuda_fail(fx_grid* h, cudaError_t e, const char* where) {
 
 bool half_integer(double x) { return std::fabs(2.0 * x - std::round(2.0 * x)) < 1e-12; }
 
-// Radial map r(x1) and its derivative.
-double rmap(int map1, double x) { return map1 == FX_MAP_EXP ? std::exp(x) : x; }
-double drmap(int map1, double x) { return map1 == FX_MAP_EXP ? std::exp(x) : 1.0; }
+// Radial map r(x1) and its derivative (Appendix A).
+double rmap(const fx_params& P, double x) {
+  if (P.map1 == FX_MAP_EXP) return std::exp(x);
+  if (P.map1 == FX_MAP_SINH) return P.map_rt * std::sinh(x / P.map_rt);
+  return x;
+}
+double drmap(const fx_params& P, double x) {
+  if (P.map1 == FX_MAP_EXP) return std::exp(x);
+  if (P.map1 == FX_MAP_SINH) return std::cosh(x / P.map_rt);
+  return 1.0;
+}
+
+// Moments of the radial volume weight r^2 dr/dx1 over a cell centred at xc of width h by
+// Gauss-Legendre quadrature (16 points: two 8-point halves); the integrand is smooth and has no
+// closed form that avoids cancellation near the origin for the sinh map.
+Moments moments_quad(const fx_params& P, double xc, double h) {
+  static const double xg[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+  static const double wg[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+  double M[3] = {0.0, 0.0, 0.0};
+  for (int half = 0; half < 2; ++half) {
+    const double c = xc + (half ? 0.25 : -0.25) * h, hw = 0.25 * h;
+    for (int k = 0; k < 8; ++k) {
+      const double xi = (k < 4 ? 1.0 : -1.0) * hw * xg[k % 4] + (c - xc);
+      const double x = xc + xi, r = rmap(P, x), w = wg[k % 4] * hw * r * r * drmap(P, x);
+      M[0] += w;
+      M[1] += w * xi;
+      M[2] += w * xi * xi;
+    }
+  }
+  return {M[0], M[1] / M[0], M[2] / M[0]};
+}
 
 Moments cell_moments(const fx_params& P, int d, double xc, double h) {
   if (P.geom == FX_CART || d >= 2) return {h, 0.0, h * h / 12.0};
@@ -166,6 +194,7 @@ Moments cell_moments(const fx_params& P, int d, double xc, double h) {
       m.w0 *= std::exp(3.0 * xc);
       return m;
     }
+    if (P.map1 == FX_MAP_SINH) return moments_quad(P, xc, h);
     return moments_r2(xc, h);
   }
   return moments_sin(xc, h);
@@ -238,8 +267,8 @@ void build_table(const fx_params& P, int d, std::vector<double>& T) {
     }
     if (d == 0) {  // radius r(x1): faces carry r^2 (scalar), r^2 dr/dx1 (r comp.), r^3 (theta comp.)
       const double Vr = mo[ip + 1].w0;
-      const double rl = rmap(P.map1, xl_abs), rr = rmap(P.map1, xr_abs);
-      const double ql = drmap(P.map1, xl_abs), qr = drmap(P.map1, xr_abs);
+      const double rl = rmap(P, xl_abs), rr = rmap(P, xr_abs);
+      const double ql = drmap(P, xl_abs), qr = drmap(P, xr_abs);
       put(T_FL, ip, rl * rl / Vr);
       put(T_FR, ip, rr * rr / Vr);
       put(T_FL1, ip, rl * rl * ql / Vr);
@@ -255,18 +284,18 @@ void build_table(const fx_params& P, int d, std::vector<double>& T) {
         for (int k = 0; k < 4; ++k) sum += wg[k] * (f(c + hw * xg[k]) + f(c - hw * xg[k]));
         return sum * hw;
       };
-      const double ra = gl([&](double x) { return std::fabs(rmap(P.map1, x)) * drmap(P.map1, x); });
-      const double rb = gl([&](double x) { double q = drmap(P.map1, x); return std::fabs(rmap(P.map1, x)) * q * q; });
-      const double rc = gl([&](double x) { double r = rmap(P.map1, x); return r * r * drmap(P.map1, x); });
+      const double ra = gl([&](double x) { return std::fabs(rmap(P, x)) * drmap(P, x); });
+      const double rb = gl([&](double x) { double q = drmap(P, x); return std::fabs(rmap(P, x)) * q * q; });
+      const double rc = gl([&](double x) { double r = rmap(P, x); return r * r * drmap(P, x); });
       put(T_XS, ip, ra / Vr);
       put(T_X1, ip, rb / Vr);
       put(T_X2, ip, rc / Vr);
       put(T_XH, ip, rc / ra);
       // cell scale factors sqrt<g_11>, sqrt<g_22> (identity theta map: g_22 = r^2)
-      put(T_HA, ip, std::sqrt(gl([&](double x) { double q = drmap(P.map1, x), r = rmap(P.map1, x); return q * q * std::fabs(r * r * q); }) / Vr));
-      put(T_HB, ip, std::sqrt(gl([&](double x) { double q = drmap(P.map1, x), r = rmap(P.map1, x); return r * r * std::fabs(r * r * q); }) / Vr));
-      const double g221 = gl([&](double x) { double q = drmap(P.map1, x), r = rmap(P.map1, x); return q / r * std::fabs(r * r * q); }) / Vr;
-      const double g122 = -gl([&](double x) { double q = drmap(P.map1, x), r = rmap(P.map1, x); return r / q * std::fabs(r * r * q); }) / Vr;
+      put(T_HA, ip, std::sqrt(gl([&](double x) { double q = drmap(P, x), r = rmap(P, x); return q * q * std::fabs(r * r * q); }) / Vr));
+      put(T_HB, ip, std::sqrt(gl([&](double x) { double q = drmap(P, x), r = rmap(P, x); return r * r * std::fabs(r * r * q); }) / Vr));
+      const double g221 = gl([&](double x) { double q = drmap(P, x), r = rmap(P, x); return q / r * std::fabs(r * r * q); }) / Vr;
+      const double g122 = -gl([&](double x) { double q = drmap(P, x), r = rmap(P, x); return r / q * std::fabs(r * r * q); }) / Vr;
       // pressure balance in r: <Gamma^1_11> = dA_1/dV - <Gamma^2_21> - <Gamma^3_31>
       const double g111 = (rr * rr * qr - rl * rl * ql) / Vr - 2.0 * g221;
       put(T_GA, ip, g111);
@@ -877,9 +906,11 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   if (P.geom != FX_CART && P.geom != FX_SPH) return FX_ERR_ARG;
   if (P.geom == FX_SPH) {
     // spherical (r, theta) grids: 2-d, radial map identity or exponential, theta in [0, pi]
-    if (P.dims != 2 || (P.map1 != FX_MAP_ID && P.map1 != FX_MAP_EXP)) return FX_ERR_UNSUPPORTED;
+    if (P.dims != 2 || (P.map1 != FX_MAP_ID && P.map1 != FX_MAP_EXP && P.map1 != FX_MAP_SINH))
+      return FX_ERR_UNSUPPORTED;
+    if (P.map1 == FX_MAP_SINH && !(P.map_rt > 0.0)) return FX_ERR_ARG;
     if (P.x_lo[1] < 0.0 || P.x_hi[1] > M_PI + 1e-12) return FX_ERR_ARG;
-    if (P.map1 == FX_MAP_ID && !(P.x_lo[0] > 0.0)) return FX_ERR_UNSUPPORTED;
+    if (P.map1 != FX_MAP_EXP && !(P.x_lo[0] > 0.0)) return FX_ERR_UNSUPPORTED;
   }
   if (P.precision != FX_FP64 && P.precision != FX_FP32 && P.precision != FX_FP32_F64NEWTON)
     return FX_ERR_ARG;

@@ -53,7 +53,7 @@ class FxParams(ctypes.Structure):
         ("rad_recon_order", ctypes.c_int), ("couple", ctypes.c_int),
         ("newton_maxit", ctypes.c_int), ("bisect_maxit", ctypes.c_int),
         ("newton_rtol", ctypes.c_double), ("rho_floor", ctypes.c_double),
-        ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double),
+        ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double), ("map_rt", ctypes.c_double),
     ]
 
 
@@ -121,6 +121,7 @@ def params(pb: Problem) -> FxParams:
         P.x_lo[d], P.x_hi[d] = pb.x_lo[d], pb.x_hi[d]
         P.bc_lo[d], P.bc_hi[d] = BC_CODES[pb.bc_lo[d]], BC_CODES[pb.bc_hi[d]]
     P.geom, P.map1 = GEOM_CODES[pb.geom], MAP_CODES[pb.map1]
+    P.map_rt = pb.map_rt
     P.ngroups, P.eps_min, P.eps_max = pb.ngroups, pb.eps_min, pb.eps_max
     P.gamma, P.c_light, P.a_rad = pb.gamma, pb.c_light, pb.a_rad
     P.kappa0, P.kap_rho_exp, P.kap_T_exp = pb.kappa0, pb.kap_rho_exp, pb.kap_T_exp

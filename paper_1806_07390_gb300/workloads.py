@@ -25,7 +25,7 @@ import numpy as np
 
 BC_CODES = {"outflow": 0, "periodic": 1, "reflect": 2, "axis": 3}
 GEOM_CODES = {"cart": 0, "sph": 1}
-MAP_CODES = {"id": 0, "exp": 1}
+MAP_CODES = {"id": 0, "exp": 1, "sinh": 2}
 
 
 @dataclasses.dataclass
@@ -52,6 +52,7 @@ class Problem:
     c_light: float = 0.0
     geom: str = "cart"
     map1: str = "id"
+    map_rt: float = 1.0  # r_t of the sinh map r = r_t sinh(x1 / r_t)
     rad_recon_order: int = 1
     couple: int = 1
     newton_maxit: int = 50
@@ -116,8 +117,12 @@ def _max_inverse_crossing(pb: Problem, prim: np.ndarray) -> float:
         lam = np.maximum(np.abs(prim[2 + d]).reshape(pb.shape) + a_s.reshape(pb.shape), pb.c_light)
         if pb.geom == "sph":
             xl = pb.cell_lower_faces(0)
-            r = np.exp(xl) if pb.map1 == "exp" else np.maximum(xl, 1e-300)
-            dr = np.exp(xl) if pb.map1 == "exp" else np.ones_like(xl)
+            if pb.map1 == "exp":
+                r, dr = np.exp(xl), np.exp(xl)
+            elif pb.map1 == "sinh":
+                r, dr = pb.map_rt * np.sinh(xl / pb.map_rt), np.cosh(xl / pb.map_rt)
+            else:
+                r, dr = np.maximum(xl, 1e-300), np.ones_like(xl)
             h = dr if d == 0 else r  # h_1 = dr/dx1, h_2 = r (identity theta map)
             hb = np.broadcast_to(h[np.newaxis, :], pb.shape) if D > 1 else h
             tot = tot + lam / (hb * dx)
@@ -223,16 +228,24 @@ def blobs_2d(n: int = 512, ngroups: int = 8, nsteps: int = 50, seed: int = 3, nb
 
 
 def spherical_2d(nr: int = 640, nth: int = 128, ngroups: int = 20, nsteps: int = 200,
-                 seed: int = 4, precision: str = "fp32") -> Tuple[Problem, np.ndarray]:
-    """2-d spherical (r, theta) atmosphere, log-r grid over [1, 1000], rho ~ r^-2, p ~ r^-2.5."""
+                 seed: int = 4, precision: str = "fp32", map1: str = "exp",
+                 map_rt: float = 10.0) -> Tuple[Problem, np.ndarray]:
+    """2-d spherical (r, theta) atmosphere over r in [1, 1000], rho ~ r^-2, p ~ r^-2.5: a log-r grid,
+    or (map1 = "sinh") r = r_t sinh(x1 / r_t), nearly uniform inside r_t and logarithmic outside."""
+    if map1 == "sinh":
+        x0, x1 = map_rt * math.asinh(1.0 / map_rt), map_rt * math.asinh(1000.0 / map_rt)
+    else:
+        x0, x1 = 0.0, math.log(1000.0)
     pb = Problem(name=f"sph2d_{nr}x{nth}x{ngroups}g", dims=2, n=(nr, nth, 1),
-                 x_lo=(0.0, 0.0, 0.0), x_hi=(math.log(1000.0), math.pi, 1.0),
+                 x_lo=(x0, 0.0, 0.0), x_hi=(x1, math.pi, 1.0),
                  bc_lo=("reflect", "axis", "periodic"), bc_hi=("outflow", "axis", "periodic"),
                  ngroups=ngroups, gamma=5.0 / 3.0, kappa0=1e3, kap_rho_exp=2.0, kap_T_exp=-1.5,
-                 kap_eps_exp=-2.0, geom="sph", map1="exp", nsteps=nsteps, precision=precision)
+                 kap_eps_exp=-2.0, geom="sph", map1=map1, map_rt=map_rt, nsteps=nsteps,
+                 precision=precision)
     rng = np.random.default_rng(seed)
     xi = rng.uniform(-1.0, 1.0, size=nth)
-    r = np.exp(pb.cell_centres(0))[None, :]
+    xc = pb.cell_centres(0)
+    r = (map_rt * np.sinh(xc / map_rt) if map1 == "sinh" else np.exp(xc))[None, :]
     rho = r ** -2.0 * (1.0 + 1e-3 * xi[:, None])
     p = r ** -2.5 * np.ones((nth, 1))
     z = np.zeros_like(rho)

@@ -175,10 +175,11 @@ def test_fp32_planck_tables_interpolate_the_band_integrals(L):
     assert worst < 3e-7, worst
 
 
-def test_spherical_tables_match_oracle_geometry(L):
+@pytest.mark.parametrize("map1", ["exp", "sinh"])
+def test_spherical_tables_match_oracle_geometry(L, map1):
     # volumes, connection coefficients and face factors of the library's host tables against
-    # the oracle's independently integrated geometry (Appendices A-D)
-    pb, _ = W.spherical_2d(nr=20, nth=12, ngroups=2)
+    # the oracle's independently integrated geometry (Appendices A-D), log-r and sinh radial maps
+    pb, _ = W.spherical_2d(nr=20, nth=12, ngroups=2, map1=map1)
     st, h, _ = create(pb)
     assert st == 0
     ntab = L.fx_debug_ntab()
@@ -204,8 +205,9 @@ def test_spherical_tables_match_oracle_geometry(L):
     np.testing.assert_allclose(T[0][e["GC"]], G["G122"], rtol=1e-12)
     np.testing.assert_allclose(T[1][e["GA"]], G["G222"], rtol=1e-11, atol=1e-12)
     np.testing.assert_allclose(T[1][e["GB"]], G["G332"], rtol=1e-12, atol=1e-14)
-    # radial faces: r^2 / V_r from the exponential map
+    # radial faces: r^2 / V_r and r^3 / V_r from the map
     xf = np.linspace(pb.x_lo[0], pb.x_hi[0], pb.n[0] + 1)
-    np.testing.assert_allclose(T[0][e["FL"]], np.exp(2 * xf[:-1]) / vol_r, rtol=1e-13)
-    np.testing.assert_allclose(T[0][e["FR2"]], np.exp(3 * xf[1:]) / vol_r, rtol=1e-13)
+    rf = np.exp(xf) if map1 == "exp" else pb.map_rt * np.sinh(xf / pb.map_rt)
+    np.testing.assert_allclose(T[0][e["FL"]], rf[:-1] ** 2 / vol_r, rtol=1e-13)
+    np.testing.assert_allclose(T[0][e["FR2"]], rf[1:] ** 3 / vol_r, rtol=1e-13)
     L.fx_grid_destroy(h)

@@ -298,6 +298,20 @@ def test_second_order_radiation_reconstruction_has_no_adjoint(fxmod):
     g.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_L1), ("fp32n64", 1e-5)])
+def test_spherical_2d_sinh_map(fxmod, precision, tol):
+    # the sinh radial map r = r_t sinh(x1 / r_t): nearly uniform in r at the inner boundary,
+    # logarithmic outside r_t; the kernels see it only through the geometry tables
+    pb, prim = W.spherical_2d(nr=36, nth=20, ngroups=20, nsteps=3, precision=precision, map1="sinh")
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    if precision == "fp64":
+        H.assert_parity(pb, got, ref, tol, FP64_MAX)
+    else:
+        H.assert_parity(pb, got, ref, tol, natural=True)
+
+
 def test_spherical_static_atmosphere_gpu(fxmod):
     # uniform p and E, v = F = 0: flux divergence and geometric sources cancel (Eqs. 84-85)
     pb, _ = W.spherical_2d(nr=24, nth=16, ngroups=3, nsteps=1, precision="fp64")

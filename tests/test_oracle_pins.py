@@ -485,6 +485,26 @@ def test_hll_correction_scales_dissipation_by_inverse_depth():
 
 
 # ------------------------------------------------------------------ geometry (Appendices A-D)
+def test_sinh_radial_map_closed_forms():
+    # r = r_t sinh(u), u = x1/r_t: V = [r^3]/3; with dr/dx1 = cosh u the volume averages of the
+    # connection coefficients integrate in closed form: <(dr/dx1)/r> = r_t^2 [cosh^3 u]/3 / V,
+    # <r/(dr/dx1)> = r_t^4 [cosh^3 u/3 - cosh u] / V, <(d2r/dx1^2)/(dr/dx1)> = r_t^2 [cosh^3 u/3 -
+    # cosh u] / V
+    pb, _ = W.spherical_2d(nr=16, nth=8, ngroups=1, map1="sinh", map_rt=10.0)
+    rt = pb.map_rt
+    xf = np.linspace(pb.x_lo[0], pb.x_hi[0], 17)
+    r, u = rt * np.sinh(xf / rt), xf / rt
+    vol_r, _, _ = oracle.geometry(pb, 0)
+    V = (r[1:] ** 3 - r[:-1] ** 3) / 3.0
+    np.testing.assert_allclose(vol_r, V, rtol=1e-13)
+    c3 = np.diff(np.cosh(u) ** 3 / 3.0)
+    c3m = np.diff(np.cosh(u) ** 3 / 3.0 - np.cosh(u))
+    G = oracle.christoffel(pb)
+    np.testing.assert_allclose(G["G221"], rt ** 2 * c3 / V, rtol=1e-12)
+    np.testing.assert_allclose(G["G122"], -rt ** 4 * c3m / V, rtol=1e-12)
+    np.testing.assert_allclose(G["G111"], rt ** 2 * c3m / V, rtol=1e-11)
+
+
 def test_spherical_geometry_closed_forms():
     pb, _ = W.spherical_2d(nr=16, nth=8, ngroups=1)
     vol_r, cen_r, _ = oracle.geometry(pb, 0)
