@@ -43,7 +43,7 @@ class OrcParams(ctypes.Structure):
         ("newton_maxit", ctypes.c_int), ("bisect_maxit", ctypes.c_int),
         ("newton_rtol", ctypes.c_double), ("rho_floor", ctypes.c_double),
         ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double), ("nthreads", ctypes.c_int),
-        ("map_rt", ctypes.c_double),
+        ("map_rt", ctypes.c_double), ("r10_full_dt", ctypes.c_int),
     ]
 
 
@@ -84,7 +84,7 @@ def lib():
     return _lib
 
 
-def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0) -> OrcParams:
+def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0, r10_full_dt: int = 0) -> OrcParams:
     P = OrcParams()
     P.dims = pb.dims
     for d in range(3):
@@ -105,6 +105,7 @@ def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0) -> OrcParams:
     P.newton_maxit, P.bisect_maxit, P.newton_rtol = pb.newton_maxit, pb.bisect_maxit, pb.newton_rtol
     P.rho_floor, P.p_floor, P.E_floor = pb.rho_floor, pb.p_floor, pb.E_floor
     P.nthreads = nthreads
+    P.r10_full_dt = r10_full_dt
     return P
 
 

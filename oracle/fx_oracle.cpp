@@ -146,6 +146,8 @@ struct orc_params {
   double rho_floor, p_floor, E_floor;
   int nthreads;
   double map_rt;
+  int r10_full_dt;          // test switch: 1 takes dt (not dt/2) as the coupling step after stage 2,
+                            // the inconsistent alternative to reading R10 (the R10 pin must fail it)
 };
 }
 
@@ -1083,7 +1085,7 @@ static int rk2_step(const Oracle& O, std::vector<S>& U, double dt, S* J = nullpt
   fill_ghosts(O.P, L, U1);
   explicit_rhs(O.P, O.geo, L, O.gr, U1, dU, J ? &phi1 : nullptr);
   for (size_t q = 0; q < N; ++q) U[q] = 0.5 * U0[q] + 0.5 * (U1[q] + dt * dU[q]);
-  if (O.P.couple) status |= couple_all(O, U, 0.5 * dt);
+  if (O.P.couple) status |= couple_all(O, U, O.P.r10_full_dt ? dt : 0.5 * dt);
   if (J) *J += dt * (0.5 * phi0 + 0.5 * phi1);
   return status;
 }
