@@ -151,8 +151,8 @@ fx_status fx_conserved_totals(fx_grid* h, double out[FX_NTOTALS]);
 fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is_device);
 
 /* Number of kernel launches enqueued by one fx_step(dt, 1) call (per RK stage: the gas face
- * kernel and the radiation/update kernel; in FX_FP32_F64NEWTON with the interaction on, the
- * interaction kernel; and the objective's reduction while it is enabled). */
+ * kernel, the radiation/update kernel, with the interaction on the interaction kernel, and the
+ * objective's reduction while it is enabled). */
 int fx_launches_per_step(const fx_grid* h);
 
 /* Planes of the slowest axis that one block of the radiation/update kernel marches over: 32 (or
@@ -163,14 +163,14 @@ int fx_march_chunk(const fx_grid* h);
 
 /* Per-kernel device timing (instrumentation, not part of the method).  While enabled, every
  * stage that fx_step enqueues records four CUDA events on the bound stream: before the gas face
- * kernel, after it, after the radiation/update kernel, and after the interaction kernel (which
- * runs as a kernel of its own in FX_FP32_F64NEWTON; elsewhere the last two events coincide).
+ * kernel, after it, after the radiation/update kernel, and after the interaction kernel (one
+ * thread per cell, in every form; with the interaction off the last two events coincide).
  * fx_kernel_timing_enable(h, on) switches this on or off and discards what was recorded.
  * fx_kernel_timing_read(h, out) waits for the last recorded event and writes
  * out[0] = total milliseconds of the radiation/update kernel, out[1] = its launches,
  * out[2] = total milliseconds of the gas face kernel, out[3] = its launches,
- * out[4] = total milliseconds of the interaction kernel, out[5] = its launches (0 when the
- * interaction runs inside the radiation/update kernel), summed over the stages recorded since
+ * out[4] = total milliseconds of the interaction kernel, out[5] = its launches (0 with the
+ * interaction off), summed over the stages recorded since
  * enable or the previous read; it then starts a new record.  Each duration includes the launch
  * gap between the bracketing events (~1 us).  Both return FX_ERR_ARG for a null handle or output
  * and FX_ERR_CUDA when an event call fails. */
@@ -207,14 +207,20 @@ int fx_debug_planck_table(const fx_grid* h, float* out, size_t cap, int* nu, flo
  *   - Every call uses the same array and leaves its contents behind; calls that overlap on the
  *     GPU (other streams, other host threads) race on it.  Order them on one stream.
  *   - Asynchronous: the copies are enqueued on the stream; the host array may be reused when
- *     the call returns (pageable source memory makes the staging copy synchronous). */
+ *     the call returns when it is pageable (the staging copy is then synchronous); page-locked
+ *     (pinned) host memory is read by the copy engine later, so it must stay unchanged until
+ *     the stream has executed the copy (synchronise the stream before reusing it).
+ *   - Like every other entry point, returns the sticky status of an earlier device failure of
+ *     the handle without enqueuing anything. */
 #define FX_NOALLOC_STAGE_BYTES (64u << 20)
 fx_status fx_state_init_equilibrium_noalloc(fx_grid* h, const double* prim, void* state,
                                             int state_precision, void* cuda_stream);
 
 /* ---- Objective and adjoint (Cartesian grids) --------------------------------------------
  *
- * Objective J (reading R19 of the design notes): the radiation energy that the update itself
+ * Objective J (the paper defines no objective; the one here is the boundary outflow that the
+ * discrete update applies, so that its gradient is exact for the discrete map): the radiation
+ * energy that the update itself
  * moves out through the upper x boundary, J = sum over steps of dt (Phi(U^n) + Phi(U^(1)))/2,
  * Phi = sum over groups and upper-x faces of face area x (corrected HLL energy flux + v* E
  * upwind term), Sec. 4 and Eqs. 17-19 of the paper.  Its gradient with respect to the initial

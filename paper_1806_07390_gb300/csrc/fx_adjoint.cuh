@@ -135,10 +135,8 @@ __global__ void __launch_bounds__(256) adj_couple_kernel(const __grid_constant__
   // Planck group energy and its T derivative at the converged temperature
   R B, dB;
   {
-    Coupler<GP, R, R> cp{g, A.pk, A.ptab, lane, has, (G == GP) && (lane == G - 1), rho * KR.cv,
-                         (rhoe - ke) * irho / KR.cv, KR.kappa0 * hpow(rho, g.kap_rho_h),
-                         KR.sigma0 * rho, cdts, E, KR.aN, ef, R(gc.edge_of(lane <= G ? lane : G, R(0))),
-                         R(gc.edge_of(lane < G ? lane + 1 : G, R(0)))};
+    LanePlanck<GP, R> cp{A.pk, A.ptab, lane, has, (G == GP) && (lane == G - 1), KR.aN,
+                         R(gc.edge_of(lane <= G ? lane : G, R(0))), R(gc.edge_of(lane < G ? lane + 1 : G, R(0)))};
     cp.planck(T, R(1) / T, B, dB);
     if (!has) { B = R(0); dB = R(0); }
   }

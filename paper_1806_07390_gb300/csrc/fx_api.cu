@@ -1042,7 +1042,7 @@ int fx_march_chunk(const fx_grid* h) { return h ? (h->D >= 2 ? h->chunk : 0) : -
 
 int fx_launches_per_step(const fx_grid* h) {
   if (!h) return 0;
-  const bool split = h->P.precision != FX_FP64 && h->P.couple;
+  const bool split = h->P.couple != 0;  // the interaction kernel runs in every form
   return 2 * (2 + (split ? 1 : 0) + (h->objective ? 1 : 0));
 }
 
@@ -1412,7 +1412,7 @@ fx_status fx_kernel_timing_read(fx_grid* h, double out[6]) {
   if (h->nev == 0) return FX_OK;
   cudaError_t e = cudaEventSynchronize(h->ev[h->nev - 1]);
   if (e != cudaSuccess) return cuda_fail(h, e, "timing read");
-  const bool split = h->P.precision != FX_FP64 && h->P.couple;
+  const bool split = h->P.couple != 0;  // the interaction kernel runs in every form
   for (size_t i = 0; i < h->nev; i += 4) {
     float face = 0.f, stage = 0.f, inter = 0.f;
     e = cudaEventElapsedTime(&face, h->ev[i], h->ev[i + 1]);
@@ -1483,6 +1483,7 @@ extern "C" fx_status fx_state_init_equilibrium_noalloc(fx_grid* h, const double*
                                                       int state_precision, void* cuda_stream) {
   if (!h || !prim || !state) return FX_ERR_ARG;
   if (state_precision != FX_FP64 && state_precision != FX_FP32) return fail(h, FX_ERR_ARG, "state precision must be FX_FP64 or FX_FP32");
+  if (h->sticky != FX_OK) return h->sticky;
   const size_t pbytes = (size_t)(3 + h->D) * h->ncell * sizeof(double);
   if (pbytes > kNoAllocBytes - kNoAllocGcBytes)
     return fail(h, FX_ERR_UNSUPPORTED,
@@ -1527,5 +1528,3 @@ extern "C" fx_status fx_state_init_equilibrium_noalloc(fx_grid* h, const double*
   return FX_OK;
 }
 
-extern "C" {
-}  // extern "C"

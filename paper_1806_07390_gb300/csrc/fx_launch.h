@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "fx_couple.cuh"
+#include "fx_couple64.cuh"
 #include "fx_stage.cuh"
 
 namespace fx {
@@ -36,8 +37,8 @@ template <int D, int GL, int NGL> struct TileShape {
 };
 
 // Enqueue one stage (state type R, D dimensions, Newton/bookkeeping type NT; SPH: the 2-d
-// spherical grid) on stream s: the gas face kernel, the radiation/update kernel and, in the FP32
-// forms, the interaction kernel (one thread per cell).  When non-null, `mid` is recorded after the
+// spherical grid) on stream s: the gas face kernel, the radiation/update kernel and, with the
+// interaction on, the interaction kernel (one thread per cell).  When non-null, `mid` is recorded after the
 // face kernel and `mid2` after the radiation/update kernel (per-kernel timing).  Returns the CUDA
 // error of the launches.
 template <class R, int D, class NT, bool SPH>
@@ -49,12 +50,6 @@ cudaError_t launch_stage(const StageArgs<R>& a, int GP, cudaStream_t s, cudaEven
 // chunks from it).
 template <class R, int D, class NT, bool SPH>
 cudaError_t stage_blocks_per_sm(int GP, int G, int ro, int* nb);
-
-// Whether the interaction runs in couple_kernel rather than inside the stage kernel: in both
-// forms with an FP32 state.
-template <class R, class NT> constexpr bool split_interaction() {
-  return std::is_same<R, float>::value;
-}
 
 // Dynamic shared memory of the stage kernel (tile shape from D and GP).
 template <class R, int D, int GP>
@@ -116,16 +111,24 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
     e = cudaEventRecord(mid2, s);
     if (e != cudaSuccess) return e;
   }
-  if constexpr (split_interaction<R, NT>()) {
-    if (a.g.couple) {
+  // the interaction, one thread per cell (FP32 state: couple_kernel; FP64 state: couple64_kernel)
+  if (a.g.couple) {
+    if constexpr (std::is_same<R, float>::value) {
       auto ck = couple_kernel<D, NT>;
       const size_t cs = couple_smem_bytes<D>(a.g.G);
       e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
       if (e != cudaSuccess) return e;
       const unsigned nb = (unsigned)((a.g.ncell + CPL_THREADS - 1) / CPL_THREADS);
       ck<<<nb, CPL_THREADS, cs, s>>>(a);
-      e = cudaGetLastError();
+    } else {
+      auto ck = couple64_kernel<D>;
+      const size_t cs = couple64_smem_bytes<D>(a.g.G);
+      e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
+      if (e != cudaSuccess) return e;
+      const unsigned nb = (unsigned)((a.g.ncell + CPL64_THREADS - 1) / CPL64_THREADS);
+      ck<<<nb, CPL64_THREADS, cs, s>>>(a);
     }
+    e = cudaGetLastError();
   }
   return e;
 }

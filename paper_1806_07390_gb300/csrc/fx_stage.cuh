@@ -1,6 +1,7 @@
 // Fused SSP-RK2 stage kernel: explicit transport (reconstruction, HLLC, M1/HLL radiation fluxes,
-// flux divergence) + RK combine, and in the FP64 form the cell-local implicit interaction, in one
-// pass over HBM (the FP32 forms run the interaction in couple_kernel, fx_couple.cuh).
+// flux divergence) + RK combine in one pass over HBM.  The cell-local implicit interaction runs
+// after it as a kernel of its own, one thread per cell (couple_kernel in fx_couple.cuh for the
+// FP32 state, couple64_kernel in fx_couple64.cuh for the FP64 state).
 //
 // Work decomposition.  A thread block owns a tile of TX (x) by TY (y, 3-d only) cells and
 // marches along the slowest active axis (y in 2-d, z in 3-d) over `chunk` planes.  Each cell is
@@ -129,29 +130,59 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bv)) + (b - bv);
 }
 
+// Finite-volume update of one conserved variable (Eq. 8), and the RK combination of stage 2:
+//   u = cov + dt (src - net),  net = sum_k Fp_k Ap_k - sum_k Fm_k Am_k,  then alpha base + beta u,
+// with Fp/Fm the fluxes through the upper/lower faces of each direction and Ap/Am their area over
+// volume factors.  In FP32 (precision form (1)) the divergence is a compensated sum: the face
+// terms are added with TwoSum and their rounding errors carried in a second float that joins the
+// sum before the update (Neumaier's compensated summation), so the divergence is exact up to the
+// rounding of each face term; in FP64 the plain sum.
+template <int K>
+__device__ __forceinline__ float fv_update(const float (&Fp)[K], const float (&Ap)[K], const float (&Fm)[K],
+                                           const float (&Am)[K], float cov, float src, float dt,
+                                           bool stage2, float base, float alpha, float beta) {
+  float s = Fp[0] * Ap[0], c, t;
+  two_sum(s, -(Fm[0] * Am[0]), t, c);
+  s = t;
+#pragma unroll
+  for (int k = 1; k < K; ++k) {
+    float e;
+    two_sum(s, Fp[k] * Ap[k], t, e);
+    s = t;
+    c += e;
+    two_sum(s, -(Fm[k] * Am[k]), t, e);
+    s = t;
+    c += e;
+  }
+  const float u = fmaf(dt, (src - s) - c, cov);
+  return stage2 ? fmaf(alpha, base, beta * u) : u;
+}
+template <int K>
+__device__ __forceinline__ double fv_update(const double (&Fp)[K], const double (&Ap)[K], const double (&Fm)[K],
+                                            const double (&Am)[K], double cov, double src, double dt,
+                                            bool stage2, double base, double alpha, double beta) {
+  double net = Fp[0] * Ap[0] - Fm[0] * Am[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) net = net + (Fp[k] * Ap[k] - Fm[k] * Am[k]);
+  const double u = cov + dt * (src - net);
+  return stage2 ? alpha * base + beta * u : u;
+}
+
 // ---------------------------------------------------------------------------------------------
-// Cell-local implicit interaction (Sec. 5.3): inner backward-Euler group update (Eq. 25) inside
-// an outer Newton iteration on T (Eqs. 26-27; reading R11), energy update by conservation (R12),
-// then the flux absorption update and its momentum/energy feedback (Eqs. 28, 31, 32).
-// Executed by all GP lanes of a cell; the loop is warp-uniform so that shuffles stay converged.
-//
-// LT: type of the per-group arithmetic (Planck band, opacity, backward Euler).
-// NT: type of the temperature iterate, the residual and the energy/momentum bookkeeping.
-// The Newton variable is dl = T - T^-, with T^- = u^-/(rho c_v): the residual
-//   r = rho c_v dl + sum_g (E_g(T) - E_g^-)
-// is the paper's r_E (u^k - u^- + dE^k, Eq. 27) without the cancellation of u(T) against u^-, so
-// an FP32 iterate resolves T to FP32 precision of the change, not of T itself.
+// Planck group energy B_g(T) and dB_g/dT of one lane's group, for code that spreads a cell's
+// groups over the lanes of a segment of GP lanes (the adjoint of the interaction): in FP32 from
+// the band table of the group; in FP64 from the edge series, each lane evaluating its lower edge
+// and taking its upper edge from the next lane (the last group's lane also evaluates the top
+// edge).  All lanes of the segment take part.
 // ---------------------------------------------------------------------------------------------
-template <int GP, class LT, class NT>
-struct Coupler {
-  const DevGrid& g;
+template <int GP, class LT>
+struct LanePlanck {
   const PlanckParams& pk;
   const PlanckTable& ptab;
   int lane;
   bool has;       // lane < G
   bool top2;      // this lane also evaluates the top edge (G == GP)
-  NT rcv, Tm;
-  LT K, Sg, cdts, Em, aN, efac;
+  LT aN;          // a_R 15 / pi^4
   LT elo, etop;   // lower and upper edge of this lane's group
 
   // FP32 group energy B_g(T) and T dB_g/dT from the band table of this lane's group
@@ -209,158 +240,7 @@ struct Coupler {
       dBq = aN * T3 * (LT(4) * I + (LT)(lo.w - hi.w));
     }
   }
-
-  // residual and derivative at T = Tm + dl; this lane's E_g(T) and dE_g/dT
-  __device__ __forceinline__ void eval(NT dl, NT& r, NT& dr, LT& Eg, LT& dEg) const {
-    LT Tl = (LT)(Tm + dl);
-    LT invT = frcp(Tl);
-    LT Bq, dBq;
-    planck(Tl, invT, Bq, dBq);
-    LT kap = K * hpow(Tl, g.kap_T_h) * efac;
-    LT tau = cdts * kap;
-    LT dtau = tau * (LT(0.5) * (LT)g.kap_T_h) * invT;
-    LT inv = frcp(LT(1) + tau);
-    Eg = (Em + tau * Bq) * inv;
-    dEg = (tau * dBq + dtau * (Bq - Eg)) * inv;
-    LT s1 = seg_sum<GP>(has ? Eg - Em : LT(0));
-    LT s2 = seg_sum<GP>(has ? dEg : LT(0));
-    r = rcv * dl + (NT)s1;
-    dr = rcv + (NT)s2;
-  }
 };
-
-template <int D, int GP, class LT, class NT>
-__device__ __forceinline__ unsigned couple_cell(const DevGrid& g, const GroupConst& gc,
-                                                const PlanckParams& pk, const PlanckTable& ptab,
-                                                const Consts<NT>& kn,
-                                                const Consts<LT>& kl, bool active,
-                                                int lane, const NT* h, NT& rho, NT* m,
-                                                NT& rhoe, NT& E, NT* F, NT* Tout = nullptr) {
-  const int G = g.G;
-  unsigned st = 0;
-  const NT cv = kn.cv;
-  if (rho < kn.rho_floor) { rho = kn.rho_floor; st |= ST_FLOOR; }
-  const NT irho = frcp(rho);
-  NT ke = NT(0);
-#pragma unroll
-  for (int q = 0; q < D; ++q) { NT mh = h ? m[q] * frcp(h[q]) : m[q]; ke += NT(0.5) * mh * mh * irho; }
-  NT u_m = rhoe - ke;
-  if (u_m < kn.u_floor) { u_m = kn.u_floor; rhoe = ke + u_m; st |= ST_FLOOR; }
-  const bool has = lane < G;
-  NT Em = has ? E : NT(0);
-  if (has && Em < kn.E_floor) Em = kn.E_floor;  // silent positivity floor (Wien tails)
-  const NT Esum = seg_sum<GP>(Em);
-  const NT rcv = rho * cv;
-
-  Coupler<GP, LT, NT> cp{g, pk, ptab, lane, has, (G == GP) && (lane == G - 1), rcv, u_m * frcp(rcv),
-                         (LT)(kn.kappa0 * hpow(rho, g.kap_rho_h)), (LT)(kn.sigma0 * rho),
-                         kl.cdts, (LT)Em, kl.aN,
-                         gc.efac_of(has ? lane : 0, LT(0)), gc.edge_of(lane <= G ? lane : G, LT(0)),
-                         gc.edge_of(lane < G ? lane + 1 : G, LT(0))};
-  NT dl = NT(0);
-  NT r, dr;
-  LT Eg, dEg;
-  cp.eval(dl, r, dr, Eg, dEg);
-  const NT scale = u_m + Esum;
-  // FP32 iterates stop at FP32 resolution (the paper's own tolerance is 1e-6, Sec. 5.3)
-  const NT rtol = kn.rtol, atol = kn.atol;
-  bool done = !active, ok = !active, need_dir = true;
-  int it = 0, ls = 0;
-  NT dT = NT(0), lam = NT(1);
-  const int guard = g.newton_maxit * 41 + 2;
-  for (int k = 0; k < guard; ++k) {
-    if (!done && need_dir) {
-      if (it >= g.newton_maxit) { done = true; }
-      else if (fabs(r) <= atol * scale) { done = true; ok = true; }
-      else {
-        dT = -r / dr;
-        ++it;
-        if (fabs(dT) <= rtol * (cp.Tm + dl)) {
-          // converged: the group energies at T + dT follow from the linearisation, exact to
-          // O(dT^2) (relative 1e-26 at the FP64 tolerance)
-          dl += dT;
-          Eg += dEg * (LT)dT;
-          done = true;
-          ok = true;
-        } else { lam = NT(1); ls = 0; need_dir = false; }
-      }
-    }
-    if (__all_sync(0xffffffffu, done)) break;
-    NT dt_ = dl + lam * dT;
-    bool valid = !done && (cp.Tm + dt_) > NT(0);
-    NT rt, drt;
-    LT Et, dEt;
-    cp.eval(valid ? dt_ : dl, rt, drt, Et, dEt);
-    if (!done) {
-      if (valid && fabs(rt) < fabs(r)) { dl = dt_; r = rt; dr = drt; Eg = Et; dEg = dEt; need_dir = true; }
-      else { lam *= NT(0.5); if (++ls >= 40) done = true; }
-    }
-  }
-  // bisection fallback on a bracket around [T^-, T_rad] (reading R11), in T - T^-
-  if (__any_sync(0xffffffffu, active && !ok)) {
-    bool need = active && !ok;
-    NT Tm = cp.Tm;
-    NT Tr = sqrt(sqrt(Esum * frcp(kn.aN * NT(6.4939394022668291491))));  // (sum E / a_R)^(1/4)
-    NT T = Tm + dl;
-    NT lo = fmin(fmin(T, Tr), Tm) - Tm, hi = fmax(fmax(T, Tr), Tm) - Tm;
-    int phase = need ? 0 : 3, cnt = 0;
-    bool brk = false;
-    NT rr, dd;
-    LT ee, de;
-    for (int k = 0; k < 400 + g.bisect_maxit + 4; ++k) {
-      if (__all_sync(0xffffffffu, phase == 3)) break;
-      NT Te = phase == 0 ? lo : (phase == 1 ? hi : (phase == 2 ? NT(0.5) * (lo + hi) : dl));
-      cp.eval(Te, rr, dd, ee, de);
-      if (phase == 0) {
-        if (rr > NT(0) && cnt < 200) { lo = NT(0.5) * (lo + Tm) - Tm; ++cnt; }  // T_lo /= 2
-        else { phase = 1; cnt = 0; brk = rr <= NT(0); }
-      } else if (phase == 1) {
-        if (rr < NT(0) && cnt < 200) { hi = NT(2) * (hi + Tm) - Tm; ++cnt; }   // T_hi *= 2
-        else {
-          brk = brk && rr >= NT(0);
-          cnt = 0;
-          phase = brk ? (g.bisect_maxit > 0 ? 2 : 3) : 3;
-        }
-      } else if (phase == 2) {
-        if (rr > NT(0)) hi = Te; else lo = Te;
-        ++cnt;
-        if (hi - lo <= rtol * (hi + Tm)) { ok = true; phase = 3; }
-        else if (cnt >= g.bisect_maxit) phase = 3;
-      }
-    }
-    if (need && brk) dl = NT(0.5) * (lo + hi);
-    NT r2, d2;
-    LT e2, de2;
-    cp.eval(dl, r2, d2, e2, de2);
-    if (need) Eg = e2;
-  }
-  if (active && !ok) st |= ST_NEWTON;
-  if (Tout) *Tout = cp.Tm + dl;
-  // energy update by conservation (R12)
-  NT dEsum = seg_sum<GP>(has ? (NT)Eg - Em : NT(0));
-  rhoe = ke + (u_m - dEsum);
-  if (has) E = (NT)Eg;
-  // momentum coupling at the converged temperature (Eq. 28; Eqs. 31-32)
-  LT kap = cp.K * hpow((LT)(cp.Tm + dl), g.kap_T_h) * cp.efac;
-  LT fac = frcp(LT(1) + cp.cdts * (kap + cp.Sg));
-  NT dF[3] = {NT(0), NT(0), NT(0)};
-  NT dwork = NT(0);
-#pragma unroll
-  for (int q = 0; q < D; ++q) {
-    if (has) {
-      LT Fq = (LT)F[q];
-      LT Fn = Fq * fac;
-      dF[q] = (NT)(Fn - Fq);
-      F[q] = (NT)Fn;
-    }
-    dwork += (h ? m[q] * frcp(h[q] * h[q]) : m[q]) * irho * dF[q];
-  }
-  const NT ic2 = kn.ic2;
-#pragma unroll
-  for (int q = 0; q < D; ++q) m[q] -= seg_sum<GP>(dF[q]) * ic2;
-  rhoe -= seg_sum<GP>(dwork) * ic2;
-  return st;
-}
 
 // Asynchronous global -> shared copies of single elements (cp.async, sm_80 and later): the
 // stage kernel stages each march plane into shared memory one step ahead, without passing the
@@ -935,7 +815,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     // value: a lane-dependent array index would place the factor arrays in local memory)
     const int gcls = (gvar >= 1 && gvar <= 2 && gvar <= D) ? gvar : 0;
     auto cls = [&](const R* f) { return gcls == 0 ? f[0] : (gcls == 1 ? f[1] : f[2]); };
-    R gnet = R(0);
+    R gFp[D], gAp[D], gFm[D], gAm[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) gFp[q] = gAp[q] = gFm[q] = gAm[q] = R(0);
     if (cell_in) {  // (an overhanging cell's upper face would lie past the last face)
       if constexpr (D == 3) {
         const uint32_t fxk = face_x(k), fyk = face_y3(k);
@@ -947,9 +829,10 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         gfl[5] = gface(1, gvar, fyk + nx);
       }
       // (1-d, 2-d: lanes >= NG carry no gas variable and read zeros, unused)
-      gnet = gfl[1] * cls(fx_r) - gfl[0] * cls(fx_l);
-      if (D == 3) gnet = gnet + (gfl[5] * ty(T_FR, bc_pad(gy)) - gfl[4] * ty(T_FL, bc_pad(gy)));
-      if (D >= 2) gnet = gnet + (gfl[3] * cls(fm_r) - gfl[2] * cls(fm_l));
+      // face terms of the divergence, direction by direction: x, (3-d) y, the march direction
+      gFp[0] = gfl[1]; gAp[0] = cls(fx_r); gFm[0] = gfl[0]; gAm[0] = cls(fx_l);
+      if (D == 3) { gFp[1] = gfl[5]; gAp[1] = ty(T_FR, bc_pad(gy)); gFm[1] = gfl[4]; gAm[1] = ty(T_FL, bc_pad(gy)); }
+      if (D >= 2) { gFp[D - 1] = gfl[3]; gAp[D - 1] = cls(fm_r); gFm[D - 1] = gfl[2]; gAm[D - 1] = cls(fm_l); }
     }
     // (B reads only planes finished two steps ago and the thread's own column; in 3-d the face
     // states it writes share their space with the fluxes that D of the previous plane reads)
@@ -1211,37 +1094,36 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         }
       }
       // gas: lane v < NG updates variable v, then the segment shares the cell's gas state
-      R ug = g0 + dt * (gsrc - gnet);
-      if (stage2) ug = KR.alpha * base_g() + KR.beta * ug;
-      // The FP32 forms leave the interaction to couple_kernel (one thread per cell: each FP64
-      // instruction of the FP64 Newton serves 32 cells, and the scalar steps are not repeated by
-      // the group lanes); their per-lane carrier type is R.
-      constexpr bool coop = std::is_same<LT, float>::value;
-      using CT = typename std::conditional<coop, R, NT>::type;
-      CT gas[NG];
-#pragma unroll
-      for (int v = 0; v < NG; ++v) gas[v] = (CT)__shfl_sync(0xffffffffu, ug, v, GL);
-      CT E[NGL], F[NGL][3];
+      const R ug = fv_update(gFp, gAp, gFm, gAm, g0, gsrc, dt, stage2, stage2 ? base_g() : R(0), KR.alpha, KR.beta);
+      // The interaction runs in a kernel of its own (couple_kernel, couple64_kernel: one thread
+      // per cell, so that each FP64 instruction of the Newton iteration serves 32 cells and its
+      // scalar steps are not repeated by the group lanes); this kernel stores the state after the
+      // explicit update and the RK combination.
+      R E[NGL], F[NGL][3];
 #pragma unroll
       for (int j = 0; j < NGL; ++j) {
-        E[j] = CT(0);
-        F[j][0] = F[j][1] = F[j][2] = CT(0);
+        E[j] = R(0);
+        F[j][0] = F[j][1] = F[j][2] = R(0);
         if (hasj[j] && cell_in) {
 #pragma unroll
           for (int v = 0; v < NRV; ++v) {
             const int c = v <= 2 ? v : 0;
             const int gg = gj[j];
-            R net = rfx[(v * NFX + fxa + 1) * GS + gg] * fx_r[c] - rfx[(v * NFX + fxa) * GS + gg] * fx_l[c];
-            if (D == 3) net = net + (rfy[(v * NFY + fya + TX) * GS + gg] * fyr - rfy[(v * NFY + fya) * GS + gg] * fyl);
+            R Fp[D], Ap[D], Fm[D], Am[D];
+            Fp[0] = rfx[(v * NFX + fxa + 1) * GS + gg]; Ap[0] = fx_r[c];
+            Fm[0] = rfx[(v * NFX + fxa) * GS + gg]; Am[0] = fx_l[c];
+            if (D == 3) {
+              Fp[1] = rfy[(v * NFY + fya + TX) * GS + gg]; Ap[1] = fyr;
+              Fm[1] = rfy[(v * NFY + fya) * GS + gg]; Am[1] = fyl;
+            }
             if (D >= 2) {
-              const R fu = SCAR ? car(k + 1, 1, v, j) : rfm_new[j][v];
-              const R fd = SCAR ? car(k, 1, v, j) : rfm_old[j][v];
-              net = net + (fu * fm_r[c] - fd * fm_l[c]);
+              Fp[D - 1] = SCAR ? car(k + 1, 1, v, j) : rfm_new[j][v]; Ap[D - 1] = fm_r[c];
+              Fm[D - 1] = SCAR ? car(k, 1, v, j) : rfm_old[j][v]; Am[D - 1] = fm_l[c];
             }
             const R cov = (sph && v >= 1) ? Q0[j][v] * hq[v - 1] : Q0[j][v];  // covariant F
-            R u1 = cov + dt * (rsrc[j][v] - net);
-            if (stage2) u1 = KR.alpha * base_r(v, j) + KR.beta * u1;
-            if (v == 0) E[j] = (CT)u1; else F[j][v - 1] = (CT)u1;
+            const R u1 = fv_update(Fp, Ap, Fm, Am, cov, rsrc[j][v], dt, stage2, stage2 ? base_r(v, j) : R(0),
+                                   KR.alpha, KR.beta);
+            if (v == 0) E[j] = u1; else F[j][v - 1] = u1;
           }
         }
       }
@@ -1264,45 +1146,24 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         for (int j = 0; j < NGL; ++j)
           if (hasj[j]) A.phi_out[row * G + gj[j]] = rfx[(0 * NFX + fxa + 1) * GS + gj[j]] * A.phi_area;
       }
-      unsigned stbits = 0;
-      CT Tst = CT(0);
-      if (g.couple && !coop) {
-        // covariant components: physical = m_q / h_q on curvilinear grids (Cartesian: no scaling)
-        CT h[3] = {(CT)hq[0], (CT)hq[1], CT(1)};
-        CT m[3] = {gas[1], D > 1 ? gas[2] : CT(0), D > 2 ? gas[3] : CT(0)};
-        CT rho = gas[0], rhoe = gas[NG - 1];
-        if constexpr (coop) {
-          // (not reached: couple_kernel)
-        } else {
-          stbits = couple_cell<D, GP, LT, NT>(g, *sgc, A.pk, A.ptab, A.k(NT(0)), A.k(LT(0)), cell_in, lane,
-                                              sph ? h : nullptr, rho, m, rhoe, E[0], F[0], &Tst);
-        }
-        gas[0] = rho;
-#pragma unroll
-        for (int q = 0; q < D; ++q) gas[1 + q] = m[q];
-        gas[NG - 1] = rhoe;
-        if (A.tstar_out != nullptr && cell_in && lane == 0) A.tstar_out[cidx] = R(Tst);
-      }
       if (cell_in) {
-        CT chk = CT(0);  // a NaN or inf anywhere in the cell's outputs makes this sum non-finite
+        R chk = R(0);  // a NaN or inf anywhere in the cell's outputs makes this sum non-finite
         if (lane < NG) {
-          CT val = gas[0];
-#pragma unroll
-          for (int v = 1; v < NG; ++v) if (lane == v) val = gas[v];
-          A.out[lane * ncell + cidx] = R(val);
-          chk += val;
+          A.out[lane * ncell + cidx] = ug;
+          chk += ug;
         }
 #pragma unroll
         for (int j = 0; j < NGL; ++j) {
           if (hasj[j]) {
 #pragma unroll
             for (int v = 0; v < NRV; ++v) {
-              CT val = v == 0 ? E[j] : F[j][v - 1];
-              A.out[NG * ncell + (v * ncell + cidx) * G + gj[j]] = R(val);
-              chk += val * CT(0);
+              const R val = v == 0 ? E[j] : F[j][v - 1];
+              A.out[NG * ncell + (v * ncell + cidx) * G + gj[j]] = val;
+              chk += val * R(0);
             }
           }
         }
+        unsigned stbits = 0;
         if (!isfinite(chk)) stbits |= ST_NONFINITE;
         if (stbits) atomicOr(A.status, stbits);
       }

@@ -48,7 +48,7 @@ def test_create_validates_parameters(L):
     st, h, ws = create(pb)
     assert st == 0 and ws > 0
     assert L.fx_state_elems(h) == pb.state_size()
-    assert L.fx_launches_per_step(h) == 4
+    assert L.fx_launches_per_step(h) == 6  # per stage: gas faces, radiation/update, interaction
     assert L.fx_march_chunk(h) == 12  # the march axis is shorter than the default 32 planes
     # workspace size covers two FP64 states
     assert ws >= 2 * pb.state_size() * 8

@@ -49,7 +49,7 @@ def test_objective_matches_oracle_fp64(fxmod):
     g.objective(True)
     g.step(pb.dt, 6)
     J = g.boundary_energy_out()
-    assert g.launches_per_step() == 6
+    assert g.launches_per_step() == 8  # per stage: gas faces, radiation/update, interaction, objective
     g.objective(False)
     g.close()
     assert Jr > 0
