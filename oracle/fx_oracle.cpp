@@ -21,7 +21,7 @@
 //   * the objective J: RK-weighted radiation energy leaving through the upper x boundary (R19),
 //     with its tangent (initial-state and kappa0 directions) through the dual-number instantiation
 //
-// Readings where the paper is silent or ambiguous (numbered as in the design notes):
+// Readings where the paper is silent or ambiguous (numbered R1-R20, the labels the tests use):
 //   R1 radiation reconstructed linearly with an MC slope limiter in moment form (Sec. 2 says linear).
 //   R2 face-interval monotonicity reset: clamp the face value so that the quadratic through the
 //      two neighbouring centroids and the face is monotone (zero slope at the nearer endpoint).

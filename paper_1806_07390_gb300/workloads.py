@@ -17,6 +17,7 @@ initial state (the paper's example choice c = 10 (v0 + a0), Sec. 9.5).
 """
 from __future__ import annotations
 
+import copy
 import dataclasses
 import math
 from typing import Optional, Tuple
@@ -295,3 +296,63 @@ def random_state(pb: Problem, seed: int, flux_frac: float = 0.5) -> np.ndarray:
     mag = rng.uniform(0.0, flux_frac, (N, G)) * pb.c_light * E
     rad = [E.reshape(-1)] + [(dirs[q] * mag).reshape(-1) for q in range(D)]
     return np.concatenate([gas, np.concatenate(rad)])
+
+
+# ---------------------------------------------------------------------------------------------
+# Windows of a large grid: sub-problems that the oracle can run in seconds, for the sampled
+# parity checks of full-size grids and the CPU baseline.  Input slicing only.
+# ---------------------------------------------------------------------------------------------
+def window(pb: Problem, prim: np.ndarray, start, size, halo):
+    """Sub-problem of `size` cells per active direction starting at `start` (interior index), with
+    `halo` extra cells on each side taken with the grid's own boundary rules, outflow boundaries
+    at the window edge.  Cells farther than the dependency radius from the edge are exact."""
+    D = pb.dims
+    sub = copy.deepcopy(pb)
+    idx = []
+    n_sub = []
+    for d in range(D):
+        n = pb.n[d]
+        m = size[d] + 2 * halo
+        raw = np.arange(start[d] - halo, start[d] - halo + m)
+        if pb.bc_lo[d] == "periodic":
+            ii = raw % n
+        else:
+            ii = np.clip(raw, 0, n - 1)
+        idx.append(ii)
+        n_sub.append(m)
+    dx = [(pb.x_hi[d] - pb.x_lo[d]) / pb.n[d] for d in range(D)]
+    sub.n = tuple(n_sub) + (1,) * (3 - D)
+    sub.x_lo = (0.0, 0.0, 0.0)
+    sub.x_hi = tuple(n_sub[d] * dx[d] for d in range(D)) + (1.0,) * (3 - D)
+    sub.bc_lo = ("outflow",) * 3
+    sub.bc_hi = ("outflow",) * 3
+    shape = pb.shape
+    grids = np.ix_(*reversed(idx))  # numpy axes are (z, y, x)
+    sub_prim = np.stack([p.reshape(shape)[grids].reshape(-1) for p in prim])
+    return sub, sub_prim
+
+
+def window_cells(pb: Problem, start, size):
+    """Flat cell indices (x fastest) of the window interior in the full grid."""
+    D = pb.dims
+    axes = [np.arange(start[d], start[d] + size[d]) % pb.n[d] for d in range(D)]
+    if D == 1:
+        return axes[0]
+    if D == 2:
+        y, x = np.meshgrid(axes[1], axes[0], indexing="ij")
+        return (y * pb.n[0] + x).reshape(-1)
+    z, y, x = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+    return ((z * pb.n[1] + y) * pb.n[0] + x).reshape(-1)
+
+
+def sub_cells(sub: Problem, size, halo):
+    """Flat indices of the window interior inside the sub-problem."""
+    D = sub.dims
+    axes = [np.arange(halo, halo + size[d]) for d in range(D)]
+    if D == 1:
+        return axes[0]
+    if D == 2:
+        y, x = np.meshgrid(axes[1], axes[0], indexing="ij")
+        return (y * sub.n[0] + x).reshape(-1)
+    z, y, x = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+    return ((z * sub.n[1] + y) * sub.n[0] + x).reshape(-1)
