@@ -9,6 +9,7 @@
 
 #include <type_traits>
 
+#include "fx_pair.cuh"
 #include "fx_types.h"
 
 namespace fx {
@@ -142,6 +143,18 @@ __device__ __forceinline__ void recon_linear_c(const MCCoef<R>& c, V pm, V p0, V
   }
   a = p0 + s * c.dl;
   b = p0 + s * c.dr;
+}
+
+// The same for the two groups of a lane (packed FP32 arithmetic; the limiter's decisions per
+// group).
+template <class R>
+__device__ __forceinline__ void recon_linear_c(const MCCoef<R>& c, F2 pm, F2 p0, F2 pp, F2& a, F2& b) {
+  const F2 sL = (p0 - pm) * c.il, sR = (pp - p0) * c.ir, sC = (pp - pm) * c.ic;
+  const F2 m = vmin(vmin(R(2) * vabs(sL), R(2) * vabs(sR)), vabs(sC));
+  const F2 pr = sL * sR;
+  const F2 s(pr.x > R(0) ? (sC.x > R(0) ? m.x : -m.x) : R(0), pr.y > R(0) ? (sC.y > R(0) ? m.y : -m.y) : R(0));
+  a = vfma(s, c.dl, p0);
+  b = vfma(s, c.dr, p0);
 }
 
 // Linear reconstruction with the MC limiter on centroid gaps (radiation; reading R1).
@@ -293,6 +306,23 @@ __device__ __forceinline__ void m1_row(R ic2, V E, const V* F, int n, V* P) {
   const V w = R(3) * qd * iE * ic2 * scale * F[n];
 #pragma unroll
   for (int q = 0; q < D; ++q) P[q] = w * F[q] + (q == n ? diag : V(R(0)));
+}
+
+// The same for the two groups of a lane (packed FP32 arithmetic; the FP32 selects per group).
+template <int D>
+__device__ __forceinline__ void m1_row(float ic2, F2 E, const F2* F, int n, F2* P) {
+  F2 F2s = F[0] * F[0];
+#pragma unroll
+  for (int q = 1; q < D; ++q) F2s = vfma(F[q], F[q], F2s);
+  const F2 iE(E.x > 0.0f ? frcp(E.x) : 0.0f, E.y > 0.0f ? frcp(E.y) : 0.0f);
+  F2 f2 = F2s * iE * iE * ic2;
+  const F2 scale = vmin(F2(1.0f), frcp(vmax(f2, F2(1e-30f))));
+  f2 = vmin(f2, F2(1.0f));
+  const F2 qd = frcp(2.0f + vsqrt(vfma(F2(-3.0f), f2, F2(4.0f))));
+  const F2 diag = E * vfma(-f2, qd, F2(1.0f / 3.0f));
+  const F2 w = 3.0f * qd * iE * ic2 * scale * F[n];
+#pragma unroll
+  for (int q = 0; q < D; ++q) P[q] = q == n ? vfma(w, F[q], diag) : w * F[q];
 }
 
 // Full diagonal and the (0,1) entry of P, for the geometric sources of curvilinear grids.

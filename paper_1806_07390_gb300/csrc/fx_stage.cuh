@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "fx_device.cuh"
+#include "fx_pair.cuh"
 
 namespace fx {
 
@@ -156,6 +157,39 @@ __device__ __forceinline__ float fv_update(const float (&Fp)[K], const float (&A
   }
   const float u = fmaf(dt, (src - s) - c, cov);
   return stage2 ? fmaf(alpha, base, beta * u) : u;
+}
+// The same for the two groups of a lane, in packed FP32 arithmetic (TwoSum is exact in the
+// packed instructions as in the scalar ones: each is the correctly rounded scalar operation).
+__device__ __forceinline__ void two_sum(F2 a, F2 b, F2& s, F2& e) {
+  s = a + b;
+  const F2 bv = s - a;
+  e = (a - (s - bv)) + (b - bv);
+}
+// s = fl(a - b) and s + e = a - b exactly (TwoSum of a and -b, without forming -b).
+__device__ __forceinline__ void two_diff(F2 a, F2 b, F2& s, F2& e) {
+  s = a - b;
+  const F2 bv = s - a;
+  e = (a - (s - bv)) - (b + bv);
+}
+template <int K>
+__device__ __forceinline__ F2 fv_update(const F2 (&Fp)[K], const float (&Ap)[K], const F2 (&Fm)[K],
+                                        const float (&Am)[K], F2 cov, F2 src, float dt, bool stage2,
+                                        F2 base, float alpha, float beta) {
+  F2 s = Fp[0] * Ap[0], c, t;
+  two_diff(s, Fm[0] * Am[0], t, c);
+  s = t;
+#pragma unroll
+  for (int k = 1; k < K; ++k) {
+    F2 e;
+    two_sum(s, Fp[k] * Ap[k], t, e);
+    s = t;
+    c = c + e;
+    two_diff(s, Fm[k] * Am[k], t, e);
+    s = t;
+    c = c + e;
+  }
+  const F2 u = vfma(F2(dt), (src - s) - c, cov);
+  return stage2 ? vfma(F2(alpha), base, beta * u) : u;
 }
 template <int K>
 __device__ __forceinline__ double fv_update(const double (&Fp)[K], const double (&Ap)[K], const double (&Fm)[K],
@@ -301,8 +335,9 @@ struct StageLayout {
   }
 };
 
-// Group stride of stage_kernel's shared arrays (see there).
-template <int D, int GP> __host__ __device__ constexpr int stage_gstride(int G) { return D <= 2 ? GP : G; }
+// Group stride of stage_kernel's shared arrays (see there): even, so that a lane's two groups
+// are one 8-byte access.
+template <int D, int GP> __host__ __device__ constexpr int stage_gstride(int G) { return D <= 2 ? GP : G + (G & 1); }
 
 // Shared memory of stage_kernel for a group stride GS (stage_gstride).
 template <class R, int D, int TX, int TY>
@@ -492,17 +527,19 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     fl[MD] = fm;
     return own_xy + (uint32_t)km * (D == 2 ? (uint32_t)nx : (uint32_t)nx * ny);
   };
-  auto own_rad = [&](int k, R (*Q)[NRV]) {
+  auto own_rad = [&](int k, auto* Q) {
     bool fl[3];
     const uint32_t gc_ = own_idx(k, fl);
 #pragma unroll
     for (int v = 0; v < NRV; ++v) {
+      R q[NGL];
 #pragma unroll
       for (int j = 0; j < NGL; ++j) {
         R val = A.in[NG * ncell + (v * ncell + gc_) * G + gj[j]];
-        Q[j][v] = (v >= 1 && fl[v - 1]) ? -val : val;
-        if (sph && v >= 1) Q[j][v] *= frcp(hfac(v - 1, gx, k));  // physical component
+        q[j] = (v >= 1 && fl[v - 1]) ? -val : val;
+        if (sph && v >= 1) q[j] *= frcp(hfac(v - 1, gx, k));  // physical component
       }
+      Q[v] = vpair(q[0], q[NGL - 1], Q[v]);
     }
   };
   const int gvar = lane < NG ? lane : 0;
@@ -630,9 +667,6 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   R ef[NGL];
 #pragma unroll
   for (int j = 0; j < NGL; ++j) ef[j] = R(sgc->efac_of(gj[j], R(0)));
-  auto chi_of = [&](int slot, int sc, int j) {
-    return pk[(slot * 2) * PC + sc] * ef[j] + pk[(slot * 2 + 1) * PC + sc];
-  };
   // radiation reconstruction of one cell from its neighbours along a direction (table t, row ip;
   // c: its MC coefficients): linear with the MC limiter, or (RO 2) the gas's parabola
   auto recon_rad = [&](const MCCoef<R>& c, const Tab<R>& t, int ip, const R* Qm, const R* Q0, const R* Qp,
@@ -648,6 +682,64 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   auto rad_cell = [&](int slot, int sc, int gg, R* Q) {
 #pragma unroll
     for (int v = 0; v < NRV; ++v) Q[v] = rad_at(slot, v, sc, gg);
+  };
+
+  // ---- The lane's groups as one value of type V: with two groups per lane a pair of FP32 values
+  // (F2), so that their arithmetic runs on the packed FP32 instructions, two groups per
+  // instruction; else R.  The shared arrays are strided by an even group count and a lane's first
+  // group g0 is even with two groups per lane, so a lane's pair is one 8-byte shared access.
+  using V = typename std::conditional<NGL == 2, F2, R>::type;
+  const int g0 = gj[0];
+  const bool h0 = hasj[0], h1 = hasj[NGL - 1];  // (NGL == 1: h1 is not used)
+  auto ldv = [&](const R* p) -> V { return ld_lane(p, V()); };
+  auto stv = [&](R* p, const V& x) { st_lane(p, x, h0, h1); };
+  auto rad_v = [&](int slot, int sc, V* Q) {
+#pragma unroll
+    for (int v = 0; v < NRV; ++v) Q[v] = ldv(&rad_at(slot, v, sc, g0));
+  };
+  const V efv = vpair(ef[0], ef[NGL - 1], V());
+  auto chi_v = [&](int slot, int sc) {
+    return vfma(efv, V(pk[(slot * 2) * PC + sc]), V(pk[(slot * 2 + 1) * PC + sc]));
+  };
+  auto recon_rad_v = [&](const MCCoef<R>& c, const Tab<R>& t, int ip, const V* Qm, const V* Q0, const V* Qp,
+                         V* a, V* b) {
+    if constexpr (RO == 2 && NGL == 2) {
+      // (the gas's parabola has no packed form: group by group)
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) {
+        R a0, b0, a1, b1;
+        recon_parabolic(t, ip, Qm[v].x, Q0[v].x, Qp[v].x, a0, b0);
+        recon_parabolic(t, ip, Qm[v].y, Q0[v].y, Qp[v].y, a1, b1);
+        a[v] = V(a0, a1);
+        b[v] = V(b0, b1);
+      }
+    } else if constexpr (RO == 2) {
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) recon_parabolic(t, ip, Qm[v], Q0[v], Qp[v], a[v], b[v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) recon_linear_c(c, Qm[v], Q0[v], Qp[v], a[v], b[v]);
+    }
+  };
+  // the radiation face flux of rad_face for the lane's groups
+  auto rad_face_v = [&](int d, const V* QL, const V* QR, V chiL, V chiR, R ell, R vstar, V* out) {
+    V PL[3], PR[3];
+    if constexpr (NGL == 2) {
+      m1_row<D>(KR.ic2, QL[0], QL + 1, d, PL);
+      m1_row<D>(KR.ic2, QR[0], QR + 1, d, PR);
+    } else {
+      m1_row<R, D>(KR.ic2, QL[0], QL + 1, d, PL);
+      m1_row<R, D>(KR.ic2, QR[0], QR + 1, d, PR);
+    }
+    const V tau = V(R(0.5)) * (chiL + chiR) * ell;
+    const V eps = vsel_gt(tau, R(1), frcp(tau), V(R(1)));
+    const bool up = vstar >= R(0);  // upwind side of the advective terms (element-wise selects)
+    out[0] = vfma(V(vstar), up ? QL[0] : QR[0],
+                  vfma(eps * (-KR.hc), QR[0] - QL[0], V(R(0.5)) * (QL[1 + d] + QR[1 + d])));
+#pragma unroll
+    for (int q = 0; q < D; ++q)
+      out[1 + q] = vfma(V(vstar), up ? QL[1 + q] : QR[1 + q],
+                        vfma(V(-KR.hc), QR[1 + q] - QL[1 + q], V(KR.hc2) * (PL[q] + PR[q])));
   };
 
   // gas face buffer: lower-face index of cell (gx, gy, k) along direction d
@@ -702,11 +794,13 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   // Carried along the march: the own cell's upper march-face state of plane k and the flux
   // through its lower march face.  In 2-d they are kept in shared memory (thread-private slots by
   // plane parity) instead of registers: the kernel runs at its register limit.
-  R bm0[NGL][NRV] = {};                     // own march-direction upper-face states, plane k
-  R rfm_old[NGL][NRV] = {};                 // radiation fluxes through the lower march face
+  V bm0[NRV], rfm_old[NRV];  // own march-direction upper-face states of plane k; fluxes through
+                             // the lower march face
+#pragma unroll
+  for (int v = 0; v < NRV; ++v) bm0[v] = rfm_old[v] = V(R(0));
   constexpr bool SCAR = D == 2;
-  auto car = [&](int P, int w, int v, int j) -> R& {  // w = 0: upper-face state, 1: lower-face flux
-    return scr[((((P & 1) * 2 + w) * NRV + v) * TC + tcell) * GS + gj[j]];
+  auto car = [&](int P, int w, int v) -> R* {  // w = 0: upper-face state, 1: lower-face flux
+    return &scr[((((P & 1) * 2 + w) * NRV + v) * TC + tcell) * GS + g0];
   };
 
   // ---------------------------------------------------------------- prologue
@@ -724,7 +818,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     issue_base(kbeg);
     issue_gf(kbeg);
     cp_async_commit();
-    R Qm1[NGL][NRV], Qm2[NGL][NRV], Q0[NGL][NRV], Q1[NGL][NRV];
+    V Qm1[NRV], Qm2[NRV], Q0[NRV], Q1[NRV];
     own_rad(kbeg - 2, Qm2);
     own_rad(kbeg - 1, Qm1);
     own_rad(kbeg, Q0);
@@ -734,19 +828,15 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     const MCCoef<R> mp = mc_coef(tm, bc_pad(kbeg - 1)), m0 = mc_coef(tm, bc_pad(kbeg));
     const R vs = gface(MD, NG, face_m(kbeg));
     const R ell = sph ? tm(T_ELL, bc_pad(kbeg)) * tx(T_XH, bc_pad(gx)) : tm(T_ELL, bc_pad(kbeg));
+    V a_[NRV], bprev[NRV];
+    recon_rad_v(mp, tm, bc_pad(kbeg - 1), Qm2, Qm1, Q0, a_, bprev);
+    recon_rad_v(m0, tm, bc_pad(kbeg), Qm1, Q0, Q1, a_, bm0);
+    rad_face_v(MD, bprev, a_, chi_v((kbeg - 1) & 3, sc_own), chi_v(kbeg & 3, sc_own), ell, vs, rfm_old);
+    if (SCAR) {
 #pragma unroll
-    for (int j = 0; j < NGL; ++j) {
-      R a_[NRV], bprev[NRV];
-      recon_rad(mp, tm, bc_pad(kbeg - 1), Qm2[j], Qm1[j], Q0[j], a_, bprev);
-      recon_rad(m0, tm, bc_pad(kbeg), Qm1[j], Q0[j], Q1[j], a_, bm0[j]);
-      rad_face(MD, bprev, a_, chi_of((kbeg - 1) & 3, sc_own, j), chi_of(kbeg & 3, sc_own, j), ell, vs,
-               rfm_old[j]);
-      if (SCAR) {
-#pragma unroll
-        for (int v = 0; v < NRV; ++v) {
-          car(kbeg, 0, v, j) = bm0[j][v];
-          car(kbeg, 1, v, j) = rfm_old[j][v];
-        }
+      for (int v = 0; v < NRV; ++v) {
+        stv(car(kbeg, 0, v), bm0[v]);
+        stv(car(kbeg, 1, v), rfm_old[v]);
       }
     }
   }
@@ -838,80 +928,63 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     // states it writes share their space with the fluxes that D of the previous plane reads)
     if (D == 3) __syncthreads();
     // the own column of planes k, k+1, k+2 from the ring
-    R Q0[NGL][NRV], Q1[NGL][NRV], Q2[NGL][NRV];
-#pragma unroll
-    for (int j = 0; j < NGL; ++j) {
-      rad_cell(s0, sc_own, gj[j], Q0[j]);
-      if (D >= 2) {
-        rad_cell((k + 1) & 3, sc_own, gj[j], Q1[j]);
-        rad_cell((k + 2) & 3, sc_own, gj[j], Q2[j]);
-      }
+    V Q0[NRV], Q1[NRV], Q2[NRV];
+    rad_v(s0, sc_own, Q0);
+    if (D >= 2) {
+      rad_v((k + 1) & 3, sc_own, Q1);
+      rad_v((k + 2) & 3, sc_own, Q2);
     }
     // ---- B: reconstructions
-    R ax[NGL][NRV], bx[NGL][NRV], am1[NGL][NRV], bm1[NGL][NRV], ay[NGL][NRV], by[NGL][NRV];
+    V ax[NRV], bx[NRV], am1[NRV], bm1[NRV], ay[NRV], by[NRV];
+    {
+      V Qa[NRV], Qb[NRV];
+      rad_v(s0, sc_own - 1, Qa);
+      rad_v(s0, sc_own + 1, Qb);
+      recon_rad_v(mcx, tx, ipx, Qa, Q0, Qb, ax, bx);
 #pragma unroll
-    for (int j = 0; j < NGL; ++j) {
-      const int gg = gj[j];
-      R Qa[NRV], Qb[NRV];
-      rad_cell(s0, sc_own - 1, gg, Qa);
-      rad_cell(s0, sc_own + 1, gg, Qb);
-      recon_rad(mcx, tx, ipx, Qa, Q0[j], Qb, ax[j], bx[j]);
-      if (hasj[j]) {
-#pragma unroll
-        for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1) + lx + 1) * GS + gg] = bx[j][v];
-      }
-      if constexpr (NGL == 1) {  // (two groups per lane: after the loop, one group per lane)
+      for (int v = 0; v < NRV; ++v) stv(&rbx[(v * NFX + ly * (TX + 1) + lx + 1) * GS + g0], bx[v]);
+      if constexpr (NGL == 1) {  // (two groups per lane: after this block, one group per lane)
         if (lx == 0) {  // halo cell -1: its upper-face state is the left state of face 0
-          R Qc[NRV], ta[NRV], tb[NRV];
-          rad_cell(s0, sc_own - 2, gg, Qc);
-          recon_rad(mc_coef(tx, bc_pad(gx - 1)), tx, bc_pad(gx - 1), Qc, Qa, Q0[j], ta, tb);
-          if (hasj[j]) {
+          V Qc[NRV], ta[NRV], tb[NRV];
+          rad_v(s0, sc_own - 2, Qc);
+          recon_rad_v(mc_coef(tx, bc_pad(gx - 1)), tx, bc_pad(gx - 1), Qc, Qa, Q0, ta, tb);
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * GS + gg] = tb[v];
-          }
+          for (int v = 0; v < NRV; ++v) stv(&rbx[(v * NFX + ly * (TX + 1)) * GS + g0], tb[v]);
         }
         if (lx == TX - 1) {  // halo cell TX: its lower-face state is the right state of face TX
-          R Qc[NRV], ta[NRV], tb[NRV];
-          rad_cell(s0, sc_own + 2, gg, Qc);
-          recon_rad(mc_coef(tx, bc_pad(gx + 1)), tx, bc_pad(gx + 1), Q0[j], Qb, Qc, ta, tb);
-          if (hasj[j]) {
+          V Qc[NRV], ta[NRV], tb[NRV];
+          rad_v(s0, sc_own + 2, Qc);
+          recon_rad_v(mc_coef(tx, bc_pad(gx + 1)), tx, bc_pad(gx + 1), Q0, Qb, Qc, ta, tb);
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * GS + gg] = ta[v];
-          }
+          for (int v = 0; v < NRV; ++v) stv(&rax[(v * TY + ly) * GS + g0], ta[v]);
         }
       }
       if (D == 3) {
-        R Qa3[NRV], Qb3[NRV];
-        rad_cell(s0, sc_own - PX, gg, Qa3);
-        rad_cell(s0, sc_own + PX, gg, Qb3);
-        recon_rad(mc_coef(ty, bc_pad(gy)), ty, bc_pad(gy), Qa3, Q0[j], Qb3, ay[j], by[j]);
-        if (hasj[j]) {
+        V Qa3[NRV], Qb3[NRV];
+        rad_v(s0, sc_own - PX, Qa3);
+        rad_v(s0, sc_own + PX, Qb3);
+        recon_rad_v(mc_coef(ty, bc_pad(gy)), ty, bc_pad(gy), Qa3, Q0, Qb3, ay, by);
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rby[(v * NFY + (ly + 1) * TX + lx) * GS + gg] = by[j][v];
-        }
+        for (int v = 0; v < NRV; ++v) stv(&rby[(v * NFY + (ly + 1) * TX + lx) * GS + g0], by[v]);
         if (ly == 0) {
-          R Qc[NRV], ta[NRV], tb[NRV];
-          rad_cell(s0, sc_own - 2 * PX, gg, Qc);
-          recon_rad(mc_coef(ty, bc_pad(gy - 1)), ty, bc_pad(gy - 1), Qc, Qa3, Q0[j], ta, tb);
-          if (hasj[j]) {
+          V Qc[NRV], ta[NRV], tb[NRV];
+          rad_v(s0, sc_own - 2 * PX, Qc);
+          recon_rad_v(mc_coef(ty, bc_pad(gy - 1)), ty, bc_pad(gy - 1), Qc, Qa3, Q0, ta, tb);
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) rby[(v * NFY + lx) * GS + gg] = tb[v];
-          }
+          for (int v = 0; v < NRV; ++v) stv(&rby[(v * NFY + lx) * GS + g0], tb[v]);
         }
         if (ly == TY - 1) {
-          R Qc[NRV], ta[NRV], tb[NRV];
-          rad_cell(s0, sc_own + 2 * PX, gg, Qc);
-          recon_rad(mc_coef(ty, bc_pad(gy + 1)), ty, bc_pad(gy + 1), Q0[j], Qb3, Qc, ta, tb);
-          if (hasj[j]) {
+          V Qc[NRV], ta[NRV], tb[NRV];
+          rad_v(s0, sc_own + 2 * PX, Qc);
+          recon_rad_v(mc_coef(ty, bc_pad(gy + 1)), ty, bc_pad(gy + 1), Q0, Qb3, Qc, ta, tb);
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) ray[(v * TX + lx) * GS + gg] = ta[v];
-          }
+          for (int v = 0; v < NRV; ++v) stv(&ray[(v * TX + lx) * GS + g0], ta[v]);
         }
       }
-      if (D >= 2) recon_rad(mc_coef(tm, bc_pad(k + 1)), tm, bc_pad(k + 1), Q0[j], Q1[j], Q2[j], am1[j], bm1[j]);
+      if (D >= 2) recon_rad_v(mc_coef(tm, bc_pad(k + 1)), tm, bc_pad(k + 1), Q0, Q1, Q2, am1, bm1);
       if (SCAR) {
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) car(k + 1, 0, v, j) = bm1[j][v];
+        for (int v = 0; v < NRV; ++v) stv(car(k + 1, 0, v), bm1[v]);
       }
     }
     // two groups per lane: the row's x halo cells -1 and TX (the upper-face state of cell -1, left
@@ -945,62 +1018,55 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     }
     __syncthreads();
     // ---- C: radiation face fluxes
-    R rfm_new[NGL][NRV] = {};
-    const R ell_m = sph ? tm(T_ELL, bc_pad(k + 1)) * tx(T_XH, ipx) : tm(T_ELL, bc_pad(k + 1));
+    V rfm_new[NRV];
 #pragma unroll
-    for (int j = 0; j < NGL; ++j) {
-      const int gg = gj[j];
+    for (int v = 0; v < NRV; ++v) rfm_new[v] = V(R(0));
+    const R ell_m = sph ? tm(T_ELL, bc_pad(k + 1)) * tx(T_XH, ipx) : tm(T_ELL, bc_pad(k + 1));
+    {
+      const V chi0 = chi_v(s0, sc_own);
       {
         const int fx = ly * (TX + 1) + lx;
-        R QL[NRV], out[NRV];
+        V QL[NRV], out[NRV];
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) QL[v] = rbx[(v * NFX + fx) * GS + gg];
-        rad_face(0, QL, ax[j], chi_of(s0, sc_own - 1, j), chi_of(s0, sc_own, j), ellx, vsx, out);
-        if (hasj[j]) {
+        for (int v = 0; v < NRV; ++v) QL[v] = ldv(&rbx[(v * NFX + fx) * GS + g0]);
+        rad_face_v(0, QL, ax, chi_v(s0, sc_own - 1), chi0, ellx, vsx, out);
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx) * GS + gg] = out[v];
-        }
+        for (int v = 0; v < NRV; ++v) stv(&rfx[(v * NFX + fx) * GS + g0], out[v]);
         if (NGL == 1 && lx == TX - 1) {
-          R QR[NRV];
+          V QR[NRV];
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) QR[v] = rax[(v * TY + ly) * GS + gg];
-          rad_face(0, bx[j], QR, chi_of(s0, sc_own, j), chi_of(s0, sc_own + 1, j), tx(T_ELL, ipx + 1), vsx1, out);
-          if (hasj[j]) {
+          for (int v = 0; v < NRV; ++v) QR[v] = ldv(&rax[(v * TY + ly) * GS + g0]);
+          rad_face_v(0, bx, QR, chi0, chi_v(s0, sc_own + 1), tx(T_ELL, ipx + 1), vsx1, out);
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fx + 1) * GS + gg] = out[v];
-          }
+          for (int v = 0; v < NRV; ++v) stv(&rfx[(v * NFX + fx + 1) * GS + g0], out[v]);
         }
       }
       if (D == 3) {
         const int fy = ly * TX + lx;
-        R QL[NRV], out[NRV];
+        V QL[NRV], out[NRV];
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) QL[v] = rby[(v * NFY + fy) * GS + gg];
-        rad_face(1, QL, ay[j], chi_of(s0, sc_own - PX, j), chi_of(s0, sc_own, j), ty(T_ELL, bc_pad(gy)), vsy, out);
-        if (hasj[j]) {
+        for (int v = 0; v < NRV; ++v) QL[v] = ldv(&rby[(v * NFY + fy) * GS + g0]);
+        rad_face_v(1, QL, ay, chi_v(s0, sc_own - PX), chi0, ty(T_ELL, bc_pad(gy)), vsy, out);
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy) * GS + gg] = out[v];
-        }
+        for (int v = 0; v < NRV; ++v) stv(&rfy[(v * NFY + fy) * GS + g0], out[v]);
         if (ly == TY - 1) {
-          R QR[NRV];
+          V QR[NRV];
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) QR[v] = ray[(v * TX + lx) * GS + gg];
-          rad_face(1, by[j], QR, chi_of(s0, sc_own, j), chi_of(s0, sc_own + PX, j), ty(T_ELL, bc_pad(gy + 1)), vsy1, out);
-          if (hasj[j]) {
+          for (int v = 0; v < NRV; ++v) QR[v] = ldv(&ray[(v * TX + lx) * GS + g0]);
+          rad_face_v(1, by, QR, chi0, chi_v(s0, sc_own + PX), ty(T_ELL, bc_pad(gy + 1)), vsy1, out);
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fy + TX) * GS + gg] = out[v];
-          }
+          for (int v = 0; v < NRV; ++v) stv(&rfy[(v * NFY + fy + TX) * GS + g0], out[v]);
         }
       }
       if (D >= 2) {
         if (SCAR) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) bm0[j][v] = car(k, 0, v, j);
+          for (int v = 0; v < NRV; ++v) bm0[v] = ldv(car(k, 0, v));
         }
-        rad_face(MD, bm0[j], am1[j], chi_of(s0, sc_own, j), chi_of((k + 1) & 3, sc_own, j), ell_m, vsm, rfm_new[j]);
+        rad_face_v(MD, bm0, am1, chi0, chi_v((k + 1) & 3, sc_own), ell_m, vsm, rfm_new);
         if (SCAR) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) car(k + 1, 1, v, j) = rfm_new[j][v];
+          for (int v = 0; v < NRV; ++v) stv(car(k + 1, 1, v), rfm_new[v]);
         }
       }
     }
@@ -1049,11 +1115,10 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     } else {
       __syncthreads();
     }
-    // ---- D: update: divergence, RK combine, coupling, store
+    // ---- D: update: divergence, RK combine, store
     {
-      const R g0 = gas_at(s0, gvar, sc_own);  // own gas variable of plane k (lanes < NG)
-#pragma unroll
-      for (int j = 0; j < NGL; ++j) rad_cell(s0, sc_own, gj[j], Q0[j]);  // (not live across C)
+      const R gown = gas_at(s0, gvar, sc_own);  // own gas variable of plane k (lanes < NG)
+      rad_v(s0, sc_own, Q0);  // (not live across C)
       const int ipy = gy + 2;
       R fyl = R(0), fyr = R(0);
       if (D == 3) { fyl = ty(T_FL, ipy); fyr = ty(T_FR, ipy); }
@@ -1065,7 +1130,10 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       const R dt = KR.dt;
       const bool stage2 = A.base != nullptr;
       // geometric sources <Gamma^l_jk> T^k_l of the stage's input state (Eq. 9; Appendix D)
-      R hq[3] = {R(1), R(1), R(1)}, gsrc = R(0), rsrc[NGL][NRV] = {};
+      R hq[3] = {R(1), R(1), R(1)}, gsrc = R(0);
+      V rsrc[NRV];
+#pragma unroll
+      for (int v = 0; v < NRV; ++v) rsrc[v] = V(R(0));
       if (sph) {
         const int ipm = bc_pad(k);
         hq[0] = hfac(0, gx, k);
@@ -1074,7 +1142,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         const R g222 = tm(T_GA, ipm), g332 = tm(T_GB, ipm);
         R gc[NG];
 #pragma unroll
-        for (int v = 0; v < NG; ++v) gc[v] = __shfl_sync(0xffffffffu, g0, v, GL);
+        for (int v = 0; v < NG; ++v) gc[v] = __shfl_sync(0xffffffffu, gown, v, GL);
         const R rho = gc[0], irho = frcp(rho);
         const R v1 = gc[1] * irho * frcp(hq[0]), v2 = gc[2] * irho * frcp(hq[1]);
         const R p = KR.gm1 * (gc[NG - 1] - R(0.5) * rho * (v1 * v1 + v2 * v2));
@@ -1083,48 +1151,49 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         if (gvar == 2)
           gsrc = g122 * (rho * v1 * v2 * r12) + g221 * (rho * v1 * v2 * r21) + g222 * (rho * v2 * v2 + p) + g332 * p;
         const R c2 = KR.c * KR.c;
+        R s1[NGL], s2[NGL];
 #pragma unroll
         for (int j = 0; j < NGL; ++j) {
-          R Pd[3], P01;
-          m1_full<R, D>(KR.c, Q0[j][0], Q0[j] + 1, Pd, P01);
-          const R R11 = c2 * Pd[0] + v1 * Q0[j][1], R22 = c2 * Pd[1] + v2 * Q0[j][2], R33 = c2 * Pd[2];
-          const R R21 = (c2 * P01 + v2 * Q0[j][1]) * r12, R12 = (c2 * P01 + v1 * Q0[j][2]) * r21;
-          rsrc[j][1] = g111 * R11 + g221 * R22 + g221 * R33;
-          rsrc[j][2] = g122 * R21 + g221 * R12 + g222 * R22 + g332 * R33;
+          R Qj[NRV], Pd[3], P01;
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) Qj[v] = vget(Q0[v], j);
+          m1_full<R, D>(KR.c, Qj[0], Qj + 1, Pd, P01);
+          const R R11 = c2 * Pd[0] + v1 * Qj[1], R22 = c2 * Pd[1] + v2 * Qj[2], R33 = c2 * Pd[2];
+          const R R21 = (c2 * P01 + v2 * Qj[1]) * r12, R12 = (c2 * P01 + v1 * Qj[2]) * r21;
+          s1[j] = g111 * R11 + g221 * R22 + g221 * R33;
+          s2[j] = g122 * R21 + g221 * R12 + g222 * R22 + g332 * R33;
         }
+        rsrc[1] = vpair(s1[0], s1[NGL - 1], V());
+        rsrc[2] = vpair(s2[0], s2[NGL - 1], V());
       }
-      // gas: lane v < NG updates variable v, then the segment shares the cell's gas state
-      const R ug = fv_update(gFp, gAp, gFm, gAm, g0, gsrc, dt, stage2, stage2 ? base_g() : R(0), KR.alpha, KR.beta);
+      // gas: lane v < NG updates variable v
+      const R ug = fv_update(gFp, gAp, gFm, gAm, gown, gsrc, dt, stage2, stage2 ? base_g() : R(0), KR.alpha, KR.beta);
       // The interaction runs in a kernel of its own (couple_kernel, couple64_kernel: one thread
       // per cell, so that each FP64 instruction of the Newton iteration serves 32 cells and its
       // scalar steps are not repeated by the group lanes); this kernel stores the state after the
       // explicit update and the RK combination.
-      R E[NGL], F[NGL][3];
+      V U[NRV];  // E, F_q of the lane's groups
 #pragma unroll
-      for (int j = 0; j < NGL; ++j) {
-        E[j] = R(0);
-        F[j][0] = F[j][1] = F[j][2] = R(0);
-        if (hasj[j] && cell_in) {
+      for (int v = 0; v < NRV; ++v) U[v] = V(R(0));
+      if (h0 && cell_in) {
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) {
-            const int c = v <= 2 ? v : 0;
-            const int gg = gj[j];
-            R Fp[D], Ap[D], Fm[D], Am[D];
-            Fp[0] = rfx[(v * NFX + fxa + 1) * GS + gg]; Ap[0] = fx_r[c];
-            Fm[0] = rfx[(v * NFX + fxa) * GS + gg]; Am[0] = fx_l[c];
-            if (D == 3) {
-              Fp[1] = rfy[(v * NFY + fya + TX) * GS + gg]; Ap[1] = fyr;
-              Fm[1] = rfy[(v * NFY + fya) * GS + gg]; Am[1] = fyl;
-            }
-            if (D >= 2) {
-              Fp[D - 1] = SCAR ? car(k + 1, 1, v, j) : rfm_new[j][v]; Ap[D - 1] = fm_r[c];
-              Fm[D - 1] = SCAR ? car(k, 1, v, j) : rfm_old[j][v]; Am[D - 1] = fm_l[c];
-            }
-            const R cov = (sph && v >= 1) ? Q0[j][v] * hq[v - 1] : Q0[j][v];  // covariant F
-            const R u1 = fv_update(Fp, Ap, Fm, Am, cov, rsrc[j][v], dt, stage2, stage2 ? base_r(v, j) : R(0),
-                                   KR.alpha, KR.beta);
-            if (v == 0) E[j] = u1; else F[j][v - 1] = u1;
+        for (int v = 0; v < NRV; ++v) {
+          const int c = v <= 2 ? v : 0;
+          V Fp[D], Fm[D];
+          R Ap[D], Am[D];
+          Fp[0] = ldv(&rfx[(v * NFX + fxa + 1) * GS + g0]); Ap[0] = fx_r[c];
+          Fm[0] = ldv(&rfx[(v * NFX + fxa) * GS + g0]); Am[0] = fx_l[c];
+          if (D == 3) {
+            Fp[1] = ldv(&rfy[(v * NFY + fya + TX) * GS + g0]); Ap[1] = fyr;
+            Fm[1] = ldv(&rfy[(v * NFY + fya) * GS + g0]); Am[1] = fyl;
           }
+          if (D >= 2) {
+            Fp[D - 1] = SCAR ? ldv(car(k + 1, 1, v)) : rfm_new[v]; Ap[D - 1] = fm_r[c];
+            Fm[D - 1] = SCAR ? ldv(car(k, 1, v)) : rfm_old[v]; Am[D - 1] = fm_l[c];
+          }
+          const V cov = (sph && v >= 1) ? Q0[v] * hq[v - 1] : Q0[v];  // covariant F
+          U[v] = fv_update(Fp, Ap, Fm, Am, cov, rsrc[v], dt, stage2, stage2 ? ldv(&base_r(v, 0)) : V(R(0)),
+                           KR.alpha, KR.beta);
         }
       }
       // recording for the adjoint: the pre-interaction state
@@ -1134,8 +1203,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         for (int j = 0; j < NGL; ++j) {
           if (hasj[j]) {
 #pragma unroll
-            for (int v = 0; v < NRV; ++v)
-              A.pre_out[NG * ncell + (v * ncell + cidx) * G + gj[j]] = R(v == 0 ? E[j] : F[j][v - 1]);
+            for (int v = 0; v < NRV; ++v) A.pre_out[NG * ncell + (v * ncell + cidx) * G + gj[j]] = vget(U[v], j);
           }
         }
       }
@@ -1157,7 +1225,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           if (hasj[j]) {
 #pragma unroll
             for (int v = 0; v < NRV; ++v) {
-              const R val = v == 0 ? E[j] : F[j][v - 1];
+              const R val = vget(U[v], j);
               A.out[NG * ncell + (v * ncell + cidx) * G + gj[j]] = val;
               chk += val * R(0);
             }
@@ -1176,12 +1244,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     // slide the march window (2-d: the carry lives in shared memory)
     if (!SCAR) {
 #pragma unroll
-      for (int j = 0; j < NGL; ++j) {
-#pragma unroll
-        for (int v = 0; v < NRV; ++v) {
-          bm0[j][v] = bm1[j][v];
-          rfm_old[j][v] = (D >= 2) ? rfm_new[j][v] : R(0);
-        }
+      for (int v = 0; v < NRV; ++v) {
+        bm0[v] = bm1[v];
+        rfm_old[v] = (D >= 2) ? rfm_new[v] : V(R(0));
       }
     }
   }
