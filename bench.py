@@ -33,10 +33,14 @@ from paper_1806_07390_gb300 import workloads as W  # noqa: E402
 METRIC = "zone-group updates/s per RK stage"
 UNIT = "zone-group-stages/s"
 # DRAM bytes per launch (mean of the two RK stages) of the radiation/update kernel and of the
-# interaction kernel, from the committed ncu capture profiles/traffic_stage_kernel_kh2d_1024x1024x16.txt;
-# None where not captured for the current kernels.
-TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": 569.7e6, "fp32": 569.7e6, "fp64": 1184.9e6}}
-TRAFFIC_INTERACTION = {"kh2d": {"fp32n64": 370.9e6, "fp32": 370.9e6}}
+# interaction kernel, from the committed ncu capture profiles/traffic_kh2d_1024x1024x16.txt; None
+# where not captured for the current kernels.
+TRAFFIC_PER_LAUNCH = {"kh2d": {}}
+TRAFFIC_INTERACTION = {"kh2d": {}}
+# FP64 lane operations (DFMA + DADD + DMUL thread instructions) per zone-group of the FP64 form's
+# radiation/update and interaction kernels, from the committed ncu capture
+# profiles/fp64_pipe_kh2d_512x512x16.txt (kh2d recipe at 512 x 512 cells x 16 groups).
+FP64_OPS_PER_ZG = {"kh2d": {"stage": 315.8, "interaction": 217.2}}
 
 
 def load_peaks():
@@ -412,9 +416,21 @@ def main():
     value = whole_job_rate(zg * 2 * args.steps, world, sech)
     nv = pbh.nvar
 
+    sm_max = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            sm_max = float(json.load(f).get("sm_max_mhz", sm_max))
+    except (OSError, ValueError):
+        pass
+    # FP64 pipe of GB300: 2 FP64 lane operations per cycle per SM (a warp instruction holds the
+    # pipe 16 cycles), 152 SMs at the maximum SM clock
+    fp64_peak = 152 * 2 * sm_max * 1e6
+
     def roofline(kind, kt):
         """Radiation/update kernel (the dominant one): algorithmic bytes per launch over its
-        average CUDA-event launch duration in the timed region."""
+        average CUDA-event launch duration in the timed region.  In the FP64 form the kernels are
+        bound by the FP64 pipe: the line reports that bound (FP64 lane operations per second
+        against the pipe's peak) and keeps the HBM figures under "hbm"."""
         b = 8 if kind == "fp64" else 4
         per_launch = 2.5 * b * nv * pbh.ncell  # 2.5 N_v words per cell per stage
         avg_s = kt["stage_ms"] / max(kt["stage_launches"], 1) / 1e3
@@ -427,16 +443,26 @@ def main():
                "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3,
                "face_kernel_avg_ms": kt["face_ms"] / max(kt["face_launches"], 1),
                "stage_share_of_step": kt["stage_ms"] / total}
-        if kt["couple_launches"]:
-            # the interaction kernel of the FP32 form with the FP64 Newton reads and writes the
-            # state once per stage
+        cs = kt["couple_ms"] / kt["couple_launches"] / 1e3 if kt["couple_launches"] else None
+        if cs:
+            # the interaction kernel reads and writes the state once per stage
             cb = 2.0 * b * nv * pbh.ncell
-            cs = kt["couple_ms"] / kt["couple_launches"] / 1e3
             out["interaction_kernel"] = {
-                "kernel": "couple_kernel (interaction, one thread per cell)",
+                "kernel": "couple_kernel / couple64_kernel (interaction, one thread per cell)",
                 "bytes_per_launch": cb, "avg_launch_ms": cs * 1e3, "achieved": cb / cs / 1e9,
                 "frac": cb / cs / 1e9 / peak, "share_of_step": kt["couple_ms"] / total,
                 "traffic": TRAFFIC_INTERACTION.get(args.workload, {}).get(kind)}
+        ops = FP64_OPS_PER_ZG.get(args.workload)
+        if kind == "fp64" and ops:
+            hbm = {k: out[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "peak_kind")}
+            a64 = ops["stage"] * zg / avg_s
+            out.update({"bound": "alu", "achieved": a64, "peak": fp64_peak, "unit": "FP64 lane-op/s",
+                        "frac": a64 / fp64_peak, "peak_kind": "FP64 pipe: 152 SMs x 2 lane-ops/clk x max SM clock",
+                        "ops_per_zone_group": ops["stage"], "hbm": hbm})
+            if cs:
+                ai = ops["interaction"] * zg / cs
+                out["interaction_kernel"].update({"alu_achieved": ai, "alu_frac": ai / fp64_peak,
+                                                  "ops_per_zone_group": ops["interaction"]})
         return out
 
     e2e_steps = max(5, args.steps // 4)
