@@ -137,6 +137,12 @@ struct fx_grid {
   size_t off_phi = 0, off_obj = 0;
   int64_t phi_rows = 0;
   double phi_area = 0.0;
+  // adjoint: the forward pass records the stages of the last checkpoint segment in the adjoint
+  // workspace, so that the backward pass need not recompute that segment.  The records are valid
+  // for the workspace, step count, checkpoint interval and step recorded here (none: null).
+  const void* adj_rec_ws = nullptr;
+  int adj_rec_nsteps = 0, adj_rec_k = 0;
+  double adj_rec_dt = 0.0;
 };
 
 namespace {
@@ -740,9 +746,11 @@ AdjLayout adj_layout(const fx_grid* h, int nsteps, int k) {
 
 // Pass 1 (forward): from the current state, nsteps steps with the objective, a checkpoint of
 // the state every k steps (checkpoint 0 = the current state); the handle's state is unchanged.
+// The steps of the last segment also record each stage's pre-interaction state and temperature.
 // Pass 2 (backward): segment by segment from the last checkpoint, recompute the segment's
-// steps recording each stage's pre-interaction state and temperature, then run the stage
-// adjoints backwards through it.  seed scales the objective (the adjoint of J).
+// steps recording each stage's pre-interaction state and temperature (except for the last
+// segment when the forward pass of the same workspace recorded it), then run the stage adjoints
+// backwards through it.  seed scales the objective (the adjoint of J).
 template <class R, class NT>
 fx_status adjoint_impl(fx_grid* h, double dt, int nsteps, int k, unsigned char* ws, bool fwd, bool bwd,
                        double seed, void* grad_state, void* grad_rho, double* J, double* dJ_dkappa0) {
@@ -770,21 +778,39 @@ fx_status adjoint_impl(fx_grid* h, double dt, int nsteps, int k, unsigned char* 
   const bool tim = h->timing;
   h->timing = false;
   if (fwd) {
+    h->adj_rec_ws = nullptr;
     e = cudaMemsetAsync(obj, 0, sizeof(double), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ckpt(0), h->ws + h->off_A, h->state_bytes, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) { h->timing = tim; return cuda_fail(h, e, "adjoint setup"); }
     a1.phi_out = a2.phi_out = reinterpret_cast<R*>(h->ws + h->off_phi);
     R* cur = ckpt(0);
+    const int last0 = (L.nseg - 1) * k;  // first step of the last segment
     for (int n = 0; n < nsteps; ++n) {
-      R* nxt = ((n + 1) % k == 0 && n + 1 < nsteps) ? ckpt((n + 1) / k) : Ub(n & 1);
-      a1.in = cur; a1.base = nullptr; a1.out = U1b(0);
-      a2.in = U1b(0); a2.base = cur; a2.out = nxt;
+      if (n >= last0) {
+        // last segment: the layout and records of the backward pass's recomputation
+        const int m = n - last0;
+        R* Um = m == 0 ? ckpt(L.nseg - 1) : Ub(m);
+        a1.in = Um; a1.base = nullptr; a1.out = U1b(m); a1.pre_out = pre1(m); a1.tstar_out = t1(m);
+        a2.in = U1b(m); a2.base = Um; a2.out = Ub(m + 1); a2.pre_out = pre2(m); a2.tstar_out = t2(m);
+      } else {
+        R* nxt = ((n + 1) % k == 0 && n + 1 < nsteps) ? ckpt((n + 1) / k) : Ub(n & 1);
+        a1.in = cur; a1.base = nullptr; a1.out = U1b(0);
+        a2.in = U1b(0); a2.base = cur; a2.out = nxt;
+        cur = nxt;
+      }
       fx_status s1 = launch_one_stage<R, NT>(h, a1, "adjoint forward pass");
       if (s1 == FX_OK) s1 = launch_one_stage<R, NT>(h, a2, "adjoint forward pass");
       if (s1 != FX_OK) { h->timing = tim; return s1; }
-      cur = nxt;
     }
     a1.phi_out = a2.phi_out = nullptr;
+    a1.pre_out = a2.pre_out = nullptr;
+    a1.tstar_out = a2.tstar_out = nullptr;
+    if (nsteps > 0) {
+      h->adj_rec_ws = ws;
+      h->adj_rec_nsteps = nsteps;
+      h->adj_rec_k = k;
+      h->adj_rec_dt = dt;
+    }
     if (J) {
       e = cudaMemcpyAsync(J, obj, sizeof(double), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -841,10 +867,15 @@ fx_status adjoint_impl(fx_grid* h, double dt, int nsteps, int k, unsigned char* 
     k_sum_into<double><<<1, 1024, 0, st>>>(kpart, L.nblk, 1.0, obj + 1);
     return cudaGetLastError();
   };
+  const bool recorded = h->adj_rec_ws == ws && h->adj_rec_nsteps == nsteps && h->adj_rec_k == k &&
+                        h->adj_rec_dt == dt;
   for (int j = L.nseg - 1; j >= 0 && nsteps > 0; --j) {
     const int s0 = j * k, s1 = std::min(s0 + k, nsteps), ns = s1 - s0;
-    // recompute the segment, recording each stage's pre-interaction state and temperature
-    for (int m = 0; m < ns; ++m) {
+    // recompute the segment, recording each stage's pre-interaction state and temperature (the
+    // forward pass recorded the last one); recomputing overwrites the last segment's records
+    const bool have = recorded && j == L.nseg - 1;
+    if (!have) h->adj_rec_ws = nullptr;
+    for (int m = 0; m < ns && !have; ++m) {
       R* Um = m == 0 ? ckpt(j) : Ub(m);
       a1.in = Um; a1.base = nullptr; a1.out = U1b(m); a1.pre_out = pre1(m); a1.tstar_out = t1(m);
       a2.in = U1b(m); a2.base = Um; a2.out = Ub(m + 1); a2.pre_out = pre2(m); a2.tstar_out = t2(m);
