@@ -48,7 +48,7 @@ enum { FX_CART = 0, FX_SPH = 1 };       /* Cartesian, or spherical (x1 -> r, x2 
 /* radial map (Appendix A): r = x1, r = exp(x1), or r = r_t sinh(x1 / r_t) (r_t = map_rt) */
 enum { FX_MAP_ID = 0, FX_MAP_EXP = 1, FX_MAP_SINH = 2 };
 enum { FX_FP64 = 0, FX_FP32 = 1, FX_FP32_F64NEWTON = 2 }; /* precision forms (see fx_params)  */
-enum { FX_NTOTALS = 6 };
+enum { FX_NTOTALS = 6, FX_NBUDGET = 8 };
 
 /* Grid, physics and solver parameters (plain data, copied at fx_grid_create).
  *   dims, n[d]         number of dimensions (1..3) and cells per direction (n[d] ignored for
@@ -146,6 +146,29 @@ fx_status fx_sync(fx_grid* h);
  * out[5] radiation energy sum_g E_g; each sum_cells V (...) in FP64 with compensated
  * summation. */
 fx_status fx_conserved_totals(fx_grid* h, double out[FX_NTOTALS]);
+
+/* Budgets of the conserved totals (reading R13 of the paper's update: the comoving-frame
+ * momentum coupling, Eqs. 31-32, does not conserve the total energy, and open boundaries let
+ * every total change).  While enabled, every fx_step stage accumulates, in FP64 on the device:
+ *   out[0] mass, out[1..3] momentum components (gas momentum plus the radiation momentum
+ *   sum_g F_g/c^2) and out[4] total energy rho e + sum_g E_g, out[5] radiation energy, that
+ *   leave through the faces of the non-periodic boundaries (outward flux times face area,
+ *   weighted dt/2 per stage as the SSP-RK2 update weighs them; momentum components are
+ *   covariant, meaningful as a budget on Cartesian grids);
+ *   out[6] the energy the gas gives up to the flux absorption, sum_cells V (1/c^2) v . sum_g
+ *   (F_g^new - F_g^-) (weight 1/2 after stage 1, 1 after stage 2);
+ *   out[7] the radiation energy the silent positivity floor of E_g adds (same weights).
+ * Then, from the totals T of fx_conserved_totals at two times, T_mass(0) - T_mass(n) = out[0],
+ * T_mom(0) - T_mom(n) = out[1..3] (Cartesian), T_E(0) - T_E(n) = out[4] + out[6] - out[7], to
+ * round-off in FX_FP64 (in the FP32 forms, to the FP32 state's rounding).
+ * fx_budgets_enable(h, 1) zeroes the accumulators (enqueued on the bound stream) and starts
+ * accumulating; fx_budgets_enable(h, 0) stops (the default: the accumulation costs the kernels
+ * registers and reductions, and the adjoint passes never add to it).  fx_budgets synchronises
+ * and returns the sums since the last enable.  Both return FX_ERR_ARG for a null argument,
+ * FX_ERR_WORKSPACE without a workspace, FX_ERR_CUDA on a failed copy, and the sticky status
+ * first. */
+fx_status fx_budgets_enable(fx_grid* h, int on);
+fx_status fx_budgets(fx_grid* h, double out[FX_NBUDGET]);
 
 /* Copy the state out, converting to dst_precision, to host (synchronous) or device memory. */
 fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is_device);

@@ -58,6 +58,7 @@ def lib():
         P = ctypes.POINTER(OrcParams)
         L.orc_run.argtypes = [P, _DP, ctypes.c_double, ctypes.c_int]
         L.orc_run_tangent.argtypes = [P, _DP, _DP, ctypes.c_double, ctypes.c_int]
+        L.orc_run_budget.argtypes = [P, _DP, ctypes.c_double, ctypes.c_int, _DP]
         L.orc_run_objective.argtypes = [P, _DP, _DP, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int, ctypes.c_int, _DP]
         L.orc_rhs.argtypes = [P, _DP, _DP]
@@ -128,6 +129,18 @@ def run(pb: Problem, state: np.ndarray, dt: float, nsteps: int, nthreads: int = 
     out = np.array(state, dtype=np.float64, copy=True)
     st = lib().orc_run(ctypes.byref(P), _ptr(out), dt, nsteps)
     return out, st
+
+
+def run_budget(pb: Problem, state: np.ndarray, dt: float, nsteps: int, nthreads: int = 1):
+    """orc_run with the budget terms of reading R13: returns (state, status, budget) with budget =
+    boundary outflows [mass, momentum 1..3 (incl. radiation / c^2), total energy, radiation
+    energy], the coupling work and the energy the positivity floor of E_g added, accumulated over
+    the steps."""
+    P = params(pb, nthreads=nthreads)
+    out = np.array(state, dtype=np.float64, copy=True)
+    bud = np.zeros(8)
+    st = lib().orc_run_budget(ctypes.byref(P), _ptr(out), dt, nsteps, _ptr(bud))
+    return out, st, bud
 
 
 def run_tangent(pb: Problem, state: np.ndarray, tangent: np.ndarray, dt: float, nsteps: int):

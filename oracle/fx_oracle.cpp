@@ -731,7 +731,11 @@ template <class S> static void planck_group(const orc_params& P, const Groups& g
 //   1 = Newton/bisection failed, 2 = floor applied.
 // ---------------------------------------------------------------------------------------------
 template <class S>
-static int couple_cell(const orc_params& P, const Groups& gr, int D, const double h[3], S* U, double dt) {
+static int couple_cell(const orc_params& P, const Groups& gr, int D, const double h[3], S* U, double dt,
+                       double* work = nullptr) {
+  // work (optional): [0] the energy the gas gives up to the flux absorption, [1] the radiation
+  // energy the silent positivity floor of E_g adds (R13, R18); per unit volume
+  double floor_add = 0.0;
   const int G = gr.G, NG = 2 + D, NRV = 1 + D;
   const double c = P.c_light, cv = 1.0 / (P.gamma - 1.0);
   int status = 0;
@@ -748,7 +752,10 @@ static int couple_cell(const orc_params& P, const Groups& gr, int D, const doubl
   S Esum = 0.0;
   for (int g = 0; g < G; ++g) {
     S& E = U[NG + g * NRV];
-    if (val(E) < P.E_floor) E = P.E_floor;  // positivity floor; tiny Wien-tail energies are physical
+    if (val(E) < P.E_floor) {  // positivity floor; tiny Wien-tail energies are physical
+      floor_add += P.E_floor - val(E);
+      E = P.E_floor;
+    }
     Em[g] = E;
     Esum += E;
   }
@@ -847,6 +854,10 @@ static int couple_cell(const orc_params& P, const Groups& gr, int D, const doubl
   }
   for (int q = 0; q < D; ++q) U[1 + q] = U[1 + q] - dm[q] / (c * c);
   U[NG - 1] = U[NG - 1] - dwork / (c * c);
+  if (work) {
+    work[0] = val(dwork) / (c * c);
+    work[1] = floor_add;
+  }
   return status;
 }
 
@@ -857,9 +868,13 @@ static int couple_cell(const orc_params& P, const Groups& gr, int D, const doubl
 // When phi is non-null it receives Phi(U) of R19: the radiation energy flux (corrected HLL + v* E
 // upwind, Eqs. 17, 19) times the face area, summed over the groups and the faces of the upper x
 // boundary, rows added in a fixed order.
+// When bflux is non-null it receives, for the faces of every non-periodic boundary, the outward
+// fluxes times the face area (R13): [0] mass, [1..3] momentum including the radiation momentum
+// flux / c^2, [4] total energy (gas + radiation), [5] radiation energy; rows added in a fixed order.
 template <class S>
 static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout& L, const Groups& gr,
-                         const std::vector<S>& U, std::vector<S>& dU, S* phi = nullptr) {
+                         const std::vector<S>& U, std::vector<S>& dU, S* phi = nullptr,
+                         double* bflux = nullptr) {
   const int D = L.D, G = L.G, NG = L.NG, NRV = L.NRV, NV = L.NV;
   const double c = P.c_light, gam = P.gamma;
   std::fill(dU.begin(), dU.end(), S(0.0));
@@ -898,12 +913,15 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
       }
   // boundary outflow per row of the upper x boundary (R19)
   std::vector<S> phi_row((size_t)L.n[1] * L.n[2], S(0.0));
+  // boundary outflow per direction and row (R13), 6 quantities each
+  std::vector<double> brow[3];
   // flux divergence, one direction at a time
   for (int d = 0; d < D; ++d) {
     const Dir& ad = geo.dir[d];
     int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
     net[d].assign(dU.size(), S(0.0));
     std::vector<S>& acc = net[d];
+    brow[d].assign((size_t)L.np[o1] * L.np[o2] * 6, 0.0);
     // rows along d are independent: each touches only its own cells
     const int nthreads = P.nthreads > 0 ? P.nthreads : 1;
     (void)nthreads;
@@ -951,6 +969,16 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
             acc[il * NV + v] += Fg[v];
             acc[ir * NV + v] -= Fg[v];
           }
+          // outward sign of a boundary face (0 for interior faces and periodic boundaries)
+          const bool lob = f == L.ng[d] && P.bc_lo[d] != ORC_PERIODIC;
+          const bool hib = f == L.ng[d] + L.n[d] && P.bc_hi[d] != ORC_PERIODIC;
+          const double osgn = lob ? -1.0 : (hib ? 1.0 : 0.0);
+          double* bo = &brow[d][((size_t)b * L.np[o1] + a) * 6];
+          if (osgn != 0.0) {
+            bo[0] += osgn * val(Fg[0]);
+            for (int q = 0; q < D; ++q) bo[1 + q] += osgn * val(Fg[1 + q]);
+            bo[4] += osgn * val(Fg[NG - 1]);
+          }
           // radiation, per group (R1, R7-R9, Eqs. 17-19)
           double ell = (ad.xc[f] + ad.m1[f]) - (ad.xc[f - 1] + ad.m1[f - 1]);
           for (int g = 0; g < G; ++g) {
@@ -982,6 +1010,10 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
             S fE = FE * Aph;
             acc[il * NV + o] += fE;
             acc[ir * NV + o] -= fE;
+            if (osgn != 0.0) {
+              bo[4] += osgn * val(fE);
+              bo[5] += osgn * val(fE);
+            }
             if (d == 0 && f == L.ng[0] + L.n[0])
               phi_row[(size_t)(b - L.ng[2]) * L.n[1] + (a - L.ng[1])] += fE;
             for (int q = 0; q < D; ++q) {
@@ -989,6 +1021,7 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
               S fF = FF * Ah[q];
               acc[il * NV + o + 1 + q] += fF;
               acc[ir * NV + o + 1 + q] -= fF;
+              if (osgn != 0.0) bo[1 + q] += osgn * val(fF) / (c * c);
             }
           }
         }
@@ -998,6 +1031,12 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
     S sum = 0.0;
     for (size_t r = 0; r < phi_row.size(); ++r) sum += phi_row[r];
     *phi = sum;
+  }
+  if (bflux) {
+    for (int q = 0; q < 6; ++q) bflux[q] = 0.0;
+    for (int d = 0; d < D; ++d)
+      for (size_t r = 0; r < brow[d].size(); r += 6)
+        for (int q = 0; q < 6; ++q) bflux[q] += brow[d][r + q];
   }
   // divide by the cell volume; add geometric sources (spherical only)
   for (int k = L.ng[2]; k < L.ng[2] + L.n[2]; ++k)
@@ -1052,10 +1091,14 @@ struct Oracle {
   Groups gr;
 };
 
+// When work is non-null, work[0] receives sum_cells V (1/c^2) v . sum_g (F_g^new - F_g^-), the
+// energy the gas gives up to the flux absorption (Eq. 32; R13), and work[1] the radiation energy
+// that the positivity floor of E_g adds (R18), each summed over cells in a fixed order.
 template <class S>
-static int couple_all(const Oracle& O, std::vector<S>& U, double dt) {
+static int couple_all(const Oracle& O, std::vector<S>& U, double dt, double* work = nullptr) {
   const Layout& L = O.L;
   int status = 0;
+  std::vector<double> wcell(work ? 2 * L.ncell_p : 0, 0.0);
   const int nthreads = O.P.nthreads > 0 ? O.P.nthreads : 1;
   (void)nthreads;
 #pragma omp parallel for collapse(2) reduction(| : status) num_threads(nthreads) if (nthreads > 1)
@@ -1064,29 +1107,52 @@ static int couple_all(const Oracle& O, std::vector<S>& U, double dt) {
       for (int i = L.ng[0]; i < L.ng[0] + L.n[0]; ++i) {
         double h[3];
         cell_h(O.P, O.geo, i, j, h);
-        status |= couple_cell(O.P, O.gr, L.D, h, &U[L.idx(i, j, k) * L.NV], dt);
+        const size_t id = L.idx(i, j, k);
+        double w[2] = {0.0, 0.0};
+        status |= couple_cell(O.P, O.gr, L.D, h, &U[id * L.NV], dt, work ? w : nullptr);
+        if (work) {
+          const double V = O.geo.dir[0].vol[i] * O.geo.dir[1].vol[j] * O.geo.dir[2].vol[k];
+          wcell[2 * id] = w[0] * V;
+          wcell[2 * id + 1] = w[1] * V;
+        }
       }
+  if (work) {
+    double s0 = 0.0, s1 = 0.0;
+    for (size_t q = 0; q < wcell.size(); q += 2) { s0 += wcell[q]; s1 += wcell[q + 1]; }
+    work[0] = s0;
+    work[1] = s1;
+  }
   return status;
 }
 
 // One SSP-RK2 step.  When J is non-null the step's share of the objective (R19) is added:
 // dt (Phi(U^n) + Phi(U^(1)))/2, the same weights the update gives the boundary fluxes.
+// When bud is non-null the step's budget terms are added to it (R13): bud[0..5] the boundary
+// outflows of explicit_rhs weighted as the update weighs them (dt/2 for each stage), bud[6] the
+// coupling work and bud[7] the energy added by the positivity floor of E_g (the stage-1
+// interaction enters U^(n+1) with the weight 1/2 of U^(1), the stage-2 one with weight 1).
 template <class S>
-static int rk2_step(const Oracle& O, std::vector<S>& U, double dt, S* J = nullptr) {
+static int rk2_step(const Oracle& O, std::vector<S>& U, double dt, S* J = nullptr, double* bud = nullptr) {
   const Layout& L = O.L;
   const size_t N = L.ncell_p * L.NV;
   std::vector<S> U0 = U, dU(N), U1(N);
   int status = 0;
   S phi0 = 0.0, phi1 = 0.0;
+  double bf0[6], bf1[6], w1[2] = {0.0, 0.0}, w2[2] = {0.0, 0.0};
   fill_ghosts(O.P, L, U0);
-  explicit_rhs(O.P, O.geo, L, O.gr, U0, dU, J ? &phi0 : nullptr);
+  explicit_rhs(O.P, O.geo, L, O.gr, U0, dU, J ? &phi0 : nullptr, bud ? bf0 : nullptr);
   for (size_t q = 0; q < N; ++q) U1[q] = U0[q] + dt * dU[q];
-  if (O.P.couple) status |= couple_all(O, U1, dt);
+  if (O.P.couple) status |= couple_all(O, U1, dt, bud ? w1 : nullptr);
   fill_ghosts(O.P, L, U1);
-  explicit_rhs(O.P, O.geo, L, O.gr, U1, dU, J ? &phi1 : nullptr);
+  explicit_rhs(O.P, O.geo, L, O.gr, U1, dU, J ? &phi1 : nullptr, bud ? bf1 : nullptr);
   for (size_t q = 0; q < N; ++q) U[q] = 0.5 * U0[q] + 0.5 * (U1[q] + dt * dU[q]);
-  if (O.P.couple) status |= couple_all(O, U, O.P.r10_full_dt ? dt : 0.5 * dt);
+  if (O.P.couple) status |= couple_all(O, U, O.P.r10_full_dt ? dt : 0.5 * dt, bud ? w2 : nullptr);
   if (J) *J += dt * (0.5 * phi0 + 0.5 * phi1);
+  if (bud) {
+    for (int q = 0; q < 6; ++q) bud[q] += 0.5 * dt * bf0[q] + 0.5 * dt * bf1[q];
+    bud[6] += 0.5 * w1[0] + w2[0];
+    bud[7] += 0.5 * w1[1] + w2[1];
+  }
   return status;
 }
 
@@ -1174,6 +1240,23 @@ int orc_run(const orc_params* P, double* state, double dt, int nsteps) {
   unpack(O, state, U, (const double*)nullptr);
   int status = 0;
   for (int s = 0; s < nsteps; ++s) status |= rk2_step(O, U, dt);
+  pack(O, U, state, (double*)nullptr);
+  return status;
+}
+
+// Run with budgets (R13): like orc_run, and budget[0..7] receives the boundary outflows of mass,
+// momentum 1..3 (including radiation momentum / c^2), total energy and radiation energy, the
+// coupling work and the energy added by the positivity floor of E_g, accumulated over the steps,
+// so that for every conserved total T(0) - T(nsteps) = outflow (+ work - floor energy for the
+// total energy).
+int orc_run_budget(const orc_params* P, double* state, double dt, int nsteps, double* budget) {
+  Oracle O;
+  setup(O, P);
+  std::vector<double> U;
+  unpack(O, state, U, (const double*)nullptr);
+  for (int q = 0; q < 8; ++q) budget[q] = 0.0;
+  int status = 0;
+  for (int s = 0; s < nsteps; ++s) status |= rk2_step(O, U, dt, (double*)nullptr, budget);
   pack(O, U, state, (double*)nullptr);
   return status;
 }

@@ -135,6 +135,8 @@ struct fx_grid {
   // [rows][G] and FP64 accumulators obj[0] = J, obj[1] = dJ/dkappa0 (adjoint)
   bool objective = false;
   size_t off_phi = 0, off_obj = 0;
+  size_t off_bud = 0;  // budgets (reading R13): rows of FP64 accumulators, see StageArgs::budget
+  bool budgets = false;  // accumulate the budgets during fx_step
   int64_t phi_rows = 0;
   double phi_area = 0.0;
   // adjoint: the forward pass records the stages of the last checkpoint segment in the adjoint
@@ -639,6 +641,8 @@ template <class R>
 void set_stage(fx_grid* h, StageArgs<R>& a, int stage, double dt) {
   const bool f32n = sizeof(R) == 4;  // FP32 group sums bound the attainable residual
   a.dt = dt;
+  a.bw_flux = 0.5 * dt;                // both stages' fluxes enter U^(n+1) with weight dt/2
+  a.bw_cpl = stage == 1 ? 0.5 : 1.0;   // U^(1) enters U^(n+1) with weight 1/2
   if (stage == 1) {
     a.dts = dt;
     a.alpha = 0.0;
@@ -695,6 +699,11 @@ fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
   R* A = reinterpret_cast<R*>(h->ws + h->off_A);
   R* B = reinterpret_cast<R*>(h->ws + h->off_B);
   if (h->objective) a.phi_out = reinterpret_cast<R*>(h->ws + h->off_phi);
+  if (h->budgets) {
+    a.budget = reinterpret_cast<double*>(h->ws + h->off_bud);
+    for (int d = 0; d < h->D; ++d)
+      if (h->P.bc_lo[d] != FX_PERIODIC || h->P.bc_hi[d] != FX_PERIODIC) a.budget_bnd = 1;
+  }
   StageArgs<R> a1 = a, a2 = a;
   set_stage(h, a1, 1, dt);
   set_stage(h, a2, 2, dt);
@@ -1061,6 +1070,7 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   for (int d = 1; d < P.dims; ++d) h->phi_area *= (P.x_hi[d] - P.x_lo[d]) / (double)P.n[d];
   h->off_phi = off; off = align_up(off + (size_t)h->phi_rows * h->G * h->elem);
   h->off_obj = off; off = align_up(off + 8 * sizeof(double));
+  h->off_bud = off; off = align_up(off + (size_t)BUDGET_SLOTS * NBUDGET * sizeof(double));
   h->ws_bytes = off;
   *workspace_bytes = off;
   *out = h;
@@ -1070,6 +1080,33 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
 size_t fx_state_elems(const fx_grid* h) { return h ? (size_t)h->ncell * h->NV : 0; }
 
 int fx_march_chunk(const fx_grid* h) { return h ? (h->D >= 2 ? h->chunk : 0) : -1; }
+
+fx_status fx_budgets_enable(fx_grid* h, int on) {
+  if (!h) return FX_ERR_ARG;
+  if (h->sticky != FX_OK) return h->sticky;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  h->budgets = on != 0;
+  cudaError_t e = cudaMemsetAsync(h->ws + h->off_bud, 0, (size_t)BUDGET_SLOTS * NBUDGET * sizeof(double), h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "budget reset");
+  return FX_OK;
+}
+
+fx_status fx_budgets(fx_grid* h, double out[FX_NBUDGET]) {
+  if (!h || !out) return FX_ERR_ARG;
+  if (h->sticky != FX_OK) return h->sticky;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  std::vector<double> rows((size_t)BUDGET_SLOTS * NBUDGET);
+  cudaError_t e = cudaMemcpyAsync(rows.data(), h->ws + h->off_bud, rows.size() * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "budget read");
+  for (int q = 0; q < NBUDGET; ++q) {
+    double sum = 0.0;
+    for (int r = 0; r < BUDGET_SLOTS; ++r) sum += rows[(size_t)r * NBUDGET + q];
+    out[q] = sum;
+  }
+  return FX_OK;
+}
 
 int fx_launches_per_step(const fx_grid* h) {
   if (!h) return 0;
@@ -1231,6 +1268,8 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
   }
   e = cudaMemsetAsync(h->ws + h->off_status, 0, 64, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
+  e = cudaMemsetAsync(h->ws + h->off_bud, 0, (size_t)BUDGET_SLOTS * NBUDGET * sizeof(double), h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "budget reset");
   {
     const fx_status cs = choose_chunk(h);
     if (cs != FX_OK) return cs;
@@ -1505,6 +1544,7 @@ constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // FX_NOALLOC_STAGE_BYTES in
 static __device__ __align__(256) unsigned char g_noalloc_stage[kNoAllocBytes];
 constexpr size_t kNoAllocGcBytes = 1024;  // GroupConst slot at the start of the array
 static_assert(sizeof(GroupConst) <= kNoAllocGcBytes, "group constants do not fit their slot");
+static_assert(NBUDGET == FX_NBUDGET, "budget accumulators per row and the ABI's budget count differ");
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {nullptr};

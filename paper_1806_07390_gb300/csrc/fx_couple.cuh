@@ -196,6 +196,11 @@ __global__ void __launch_bounds__(CPL_THREADS, 7) couple_kernel(StageArgs<float>
   // = (rho e)^- - kinetic, the iterate T - T^-, the residual and the gas energy update by
   // conservation are NT.
   float rr = 1.0f, ir = 1.0f, ke = 0.0f;
+  // budget terms of this cell (reading R13; FP32 like the state they come from, summed in FP64
+  // only when the budgets are on): the energy the E floor adds waits in shared memory while the
+  // Newton runs (a register held across it cost the loop spills)
+  __shared__ float s_floor[CPL_THREADS];
+  float work_out = 0.0f;
   NT um = NT(0);
   LT Kc = LT(0), Sc = LT(0), Tst = LT(0);
   float eh = 0.0f, el = 0.0f;
@@ -219,10 +224,18 @@ __global__ void __launch_bounds__(CPL_THREADS, 7) couple_kernel(StageArgs<float>
     Sc = kl.sigma0 * rr;
     // E^- with its silent positivity floor (Wien tails), and its group sum
     LT Esum = LT(0);
-    for (int j = 0; j < G; ++j) {
-      LT e = rE[j];
-      if (e < kl.E_floor) { e = kl.E_floor; rE[j] = e; }
-      Esum += e;
+    {
+      float fadd = 0.0f;
+      for (int j = 0; j < G; ++j) {
+        LT e = rE[j];
+        if (e < kl.E_floor) {
+          fadd += kl.E_floor - e;
+          e = kl.E_floor;
+          rE[j] = e;
+        }
+        Esum += e;
+      }
+      if (A.budget != nullptr) s_floor[t] = fadd;
     }
     const NT ats = (NT)(kl.atol * ((LT)um + Esum));
     const LT hh = LT(0.5) * (LT)g.kap_T_h;
@@ -412,6 +425,7 @@ __global__ void __launch_bounds__(CPL_THREADS, 7) couple_kernel(StageArgs<float>
     }
     rhoe_f = (float)(re - (NT)(vdf * kl.ic2));
     rho_f = rr;
+    work_out = vdf * kl.ic2;
   }
   if (act) {
     // A NaN or inf anywhere in the cell's outputs makes chk non-finite: a non-finite E_g or F_g
@@ -431,6 +445,10 @@ __global__ void __launch_bounds__(CPL_THREADS, 7) couple_kernel(StageArgs<float>
     }
     if (!isfinite(chk)) st |= ST_NONFINITE;
     if (st) atomicOr(A.status, st);
+  }
+  if (A.budget != nullptr) {
+    const double wv = work ? cell_volume(A, cid) * A.bw_cpl : 0.0;
+    block_add2((double)work_out * wv, work ? (double)s_floor[t] * wv : 0.0, A.budget + (size_t)(blockIdx.x % BUDGET_SLOTS) * NBUDGET + 6);
   }
   __syncthreads();
   // write the rows back

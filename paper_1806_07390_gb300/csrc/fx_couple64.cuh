@@ -115,6 +115,10 @@ __global__ void __launch_bounds__(CPL64_THREADS) couple64_kernel(StageArgs<doubl
   const bool work = act && g.couple;
   unsigned st = 0;
   double irho = 1.0, ke = 0.0, Tst = 0.0, K = 0.0, Sg = 0.0;
+  // budget terms of this cell (reading R13): the energy the E floor adds waits in shared memory
+  // while the Newton runs
+  __shared__ double s_floor[CPL64_THREADS];
+  double work_out = 0.0;
   if (work) {
     // ---- floors, kinetic energy, u^- and T^- = u^-/(rho c_v)
     if (rho < kn.rho_floor) { rho = kn.rho_floor; st |= ST_FLOOR; }
@@ -126,12 +130,17 @@ __global__ void __launch_bounds__(CPL64_THREADS) couple64_kernel(StageArgs<doubl
     }
     double um = rhoe - ke;
     if (um < kn.u_floor) { um = kn.u_floor; rhoe = ke + um; st |= ST_FLOOR; }
-    double Esum = 0.0;
+    double Esum = 0.0, fadd = 0.0;
     for (int j = 0; j < G; ++j) {
       double e = rE[j];
-      if (e < kn.E_floor) { e = kn.E_floor; rE[j] = e; }  // silent positivity floor (Wien tails)
+      if (e < kn.E_floor) {  // silent positivity floor (Wien tails)
+        fadd += kn.E_floor - e;
+        e = kn.E_floor;
+        rE[j] = e;
+      }
       Esum += e;
     }
+    if (A.budget != nullptr) s_floor[t] = fadd;
     const double rcv = rho * kn.cv;
     const double Tm = um * frcp(rcv);
     K = kn.kappa0 * hpow(rho, g.kap_rho_h);
@@ -269,6 +278,7 @@ __global__ void __launch_bounds__(CPL64_THREADS) couple64_kernel(StageArgs<doubl
 #pragma unroll
     for (int q = 0; q < D; ++q) m[q] -= SdF[q] * kn.ic2;
     rhoe -= dwork * kn.ic2;
+    work_out = dwork * kn.ic2;
   }
   if (act) {
     // A NaN or inf anywhere in the cell's outputs makes chk non-finite (with the interaction on,
@@ -286,6 +296,10 @@ __global__ void __launch_bounds__(CPL64_THREADS) couple64_kernel(StageArgs<doubl
     }
     if (!isfinite(chk)) st |= ST_NONFINITE;
     if (st) atomicOr(A.status, st);
+  }
+  if (A.budget != nullptr) {
+    const double wv = work ? cell_volume(A, cid) * A.bw_cpl : 0.0;
+    block_add2(work_out * wv, work ? s_floor[t] * wv : 0.0, A.budget + (size_t)(blockIdx.x % BUDGET_SLOTS) * NBUDGET + 6);
   }
   __syncthreads();
 #pragma unroll

@@ -77,8 +77,11 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
   constexpr int GL = GP / NGL;
   using TS = TileShape<D, GL, NGL>;
   if ((a.g.geom != 0) != SPH) return cudaErrorInvalidValue;  // the grid's geometry decides SPH
-  auto kern = a.g.rad_order == 2 ? stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 2>
-                                 : stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 1>;
+  // (the boundary budgets are compiled into the kernel for grids with a non-periodic boundary;
+  // the second-order radiation reconstruction always carries them)
+  auto kern = a.g.rad_order == 2 ? stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 2, true>
+              : (a.budget_bnd ? stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 1, true>
+                              : stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 1, false>);
   const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(a.g.G));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -138,8 +141,8 @@ static cudaError_t blocks_gp(int G, int ro, int* nb) {
   constexpr int NGL = groups_per_lane(sizeof(R) == 4, D, GP);
   constexpr int GL = GP / NGL;
   using TS = TileShape<D, GL, NGL>;
-  auto kern = ro == 2 ? stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 2>
-                      : stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 1>;
+  auto kern = ro == 2 ? stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 2, true>
+                      : stage_kernel<R, D, GP, TS::TX, TS::TY, R, NT, NGL, SPH, 1, false>;
   const size_t smem = stage_smem_bytes<R, D, TS::TX, TS::TY>(stage_gstride<D, GP>(G));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -89,6 +89,15 @@ template <class R> struct StageArgs {
   R* tstar_out;
   R* phi_out;
   R phi_area;
+  // Budgets (reading R13; null when not accumulated): [0] mass, [1..3] momentum (with the
+  // radiation momentum / c^2), [4] total energy and [5] radiation energy that leave through the
+  // non-periodic boundaries, [6] the energy the gas gives up to the flux absorption, [7] the
+  // radiation energy the positivity floor of E_g adds.  bw_flux weighs this stage's boundary
+  // fluxes (dt/2), bw_cpl its interaction (1/2 after stage 1, 1 after stage 2), as the RK
+  // combination weighs them in U^(n+1).
+  double* budget;
+  double bw_flux, bw_cpl;
+  int budget_bnd;  // the grid has a non-periodic boundary: the stage kernel adds its outflows
   Consts<double> kd;
   Consts<float> kf;
   __device__ __forceinline__ const Consts<double>& k(double) const { return kd; }
@@ -276,6 +285,46 @@ struct LanePlanck {
   }
 };
 
+// Volume of cell cid (the product of its 1-d volume factors), for the budgets (reading R13).
+template <class R> __device__ __forceinline__ double cell_volume(const StageArgs<R>& A, uint32_t cid) {
+  const DevGrid& g = A.g;
+  if (A.uniform[0] && (g.D < 2 || A.uniform[1]) && (g.D < 3 || A.uniform[2])) {
+    // uniform spacing in every direction: every cell has the same volume
+    double v = (double)A.urow[0][T_VOL];
+    if (g.D >= 2) v *= (double)A.urow[1][T_VOL];
+    if (g.D >= 3) v *= (double)A.urow[2][T_VOL];
+    return v;
+  }
+  const uint32_t nx = (uint32_t)g.n[0], ny = (uint32_t)g.n[1];
+  const int gx = (int)(cid % nx), gy = (int)((cid / nx) % ny), gz = (int)(cid / (nx * ny));
+  double v = (double)Tab<R>{A.tab[0], g.n[0] + 4, A.uniform[0] ? A.urow[0] : nullptr}(T_VOL, bc_pad(gx));
+  if (g.D >= 2) v *= (double)Tab<R>{A.tab[1], g.n[1] + 4, A.uniform[1] ? A.urow[1] : nullptr}(T_VOL, bc_pad(gy));
+  if (g.D >= 3) v *= (double)Tab<R>{A.tab[2], g.n[2] + 4, A.uniform[2] ? A.urow[2] : nullptr}(T_VOL, bc_pad(gz));
+  return v;
+}
+
+// Block sums of a and b (blocks of whole warps, at most 1024 threads) added to out[0], out[1] by
+// one thread.  Every thread of the block calls it.
+__device__ __forceinline__ void block_add2(double a, double b, double* out) {
+  __shared__ double red[2][32];
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sa += red[0][w]; sb += red[1][w]; }
+    if (sa != 0.0) atomicAdd(out, sa);
+    if (sb != 0.0) atomicAdd(out + 1, sb);
+  }
+}
+
 // Asynchronous global -> shared copies of single elements (cp.async, sm_80 and later): the
 // stage kernel stages each march plane into shared memory one step ahead, without passing the
 // values through registers.  A thread's copies are complete, and visible to that thread, after
@@ -364,9 +413,10 @@ inline size_t stage_smem_bytes(int G) {
 // (the host launches the instantiation that matches the grid): the Cartesian kernel carries none
 // of its scale factors and geometric sources.  RO is the radiation reconstruction (1: linear with
 // the MC limiter, the paper's; 2: the gas's parabola), also a compile-time choice: a run-time one
-// cost the kernel spills.
+// cost the kernel spills.  BUD compiles in the boundary-outflow budgets (reading R13) for grids
+// with a non-periodic boundary: on a fully periodic grid the code would only cost registers.
 // ---------------------------------------------------------------------------------------------
-template <class R, int D, int GP, int TX, int TY, class LT, class NT, int NGL, bool SPH, int RO>
+template <class R, int D, int GP, int TX, int TY, class LT, class NT, int NGL, bool SPH, int RO, bool BUD>
 __global__ void __launch_bounds__(TX * TY * (GP / NGL),
                                   (sizeof(R) == 4 && NGL == 1) ? 3 : (TX * TY * (GP / NGL) <= 160 ? 4 : 2))
 stage_kernel(const __grid_constant__ StageArgs<R> A) {
@@ -1194,6 +1244,72 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           const V cov = (sph && v >= 1) ? Q0[v] * hq[v - 1] : Q0[v];  // covariant F
           U[v] = fv_update(Fp, Ap, Fm, Am, cov, rsrc[v], dt, stage2, stage2 ? ldv(&base_r(v, 0)) : V(R(0)),
                            KR.alpha, KR.beta);
+        }
+      }
+      // budgets (reading R13): the outward fluxes through this cell's faces on non-periodic
+      // boundaries, times the face area (the area/volume factor times the cell volume) and the
+      // stage's weight, added to one of BUDGET_SLOTS rows of accumulators (summed when read, so
+      // that few blocks add to the same address).  The face values are read again (gas: the
+      // staged face values, or global memory in 3-d; radiation: the face fluxes in shared memory).
+      if (BUD && A.budget != nullptr && cell_in) {
+        const bool xl = gx == 0 && g.bc_lo[0] != 1, xh = gx == nx - 1 && g.bc_hi[0] != 1;
+        const bool yl = D == 3 && gy == 0 && g.bc_lo[1] != 1, yh = D == 3 && gy == ny - 1 && g.bc_hi[1] != 1;
+        const bool ml = D >= 2 && k == 0 && g.bc_lo[MD] != 1;
+        const bool mh = D >= 2 && k == nmarch - 1 && g.bc_hi[MD] != 1;
+        if (xl || xh || yl || yh || ml || mh) {
+          double vol = (double)tx(T_VOL, ipx);
+          if (D == 3) vol *= (double)ty(T_VOL, ipy);
+          if (D >= 2) vol *= (double)tm(T_VOL, bc_pad(k));
+          const double bs = vol * A.bw_flux;
+          const unsigned blin = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+          double* const bud = A.budget + (size_t)(blin % BUDGET_SLOTS) * NBUDGET;
+          if (lane < NG) {
+            R f[6];
+            if constexpr (D <= 2) {
+#pragma unroll
+              for (int c = 0; c < GFV; ++c) f[c] = gfs(k, 3 + GFV * lane + c);
+            } else {
+              const uint32_t fxk = face_x(k), fyk = face_y3(k);
+              f[0] = gface(0, gvar, fxk);
+              f[1] = gface(0, gvar, fxk + 1);
+              f[2] = gface(MD, gvar, face_m(k));
+              f[3] = gface(MD, gvar, face_m(k + 1));
+              f[4] = gface(1, gvar, fyk);
+              f[5] = gface(1, gvar, fyk + nx);
+            }
+            double o = 0.0;
+            if (xh) o += (double)(f[1] * cls(fx_r));
+            if (xl) o -= (double)(f[0] * cls(fx_l));
+            if (D >= 2 && mh) o += (double)(f[3] * cls(fm_r));
+            if (D >= 2 && ml) o -= (double)(f[2] * cls(fm_l));
+            if (D == 3 && yh) o += (double)(f[5] * fyr);
+            if (D == 3 && yl) o -= (double)(f[4] * fyl);
+            if (o != 0.0) atomicAdd(bud + (gvar == NG - 1 ? 4 : gvar), o * bs);
+          }
+#pragma unroll
+          for (int v = 0; v < NRV; ++v) {
+            const int c = v <= 2 ? v : 0;
+            double o = 0.0;
+#pragma unroll
+            for (int j = 0; j < NGL; ++j) {
+              if (!hasj[j]) continue;
+              const int gg = gj[j];
+              if (xh) o += (double)(rfx[(v * NFX + fxa + 1) * GS + gg] * fx_r[c]);
+              if (xl) o -= (double)(rfx[(v * NFX + fxa) * GS + gg] * fx_l[c]);
+              if (D == 3 && yh) o += (double)(rfy[(v * NFY + fya + TX) * GS + gg] * fyr);
+              if (D == 3 && yl) o -= (double)(rfy[(v * NFY + fya) * GS + gg] * fyl);
+              if (D >= 2 && mh) o += (double)((SCAR ? car(k + 1, 1, v)[j] : vget(rfm_new[v], j)) * fm_r[c]);
+              if (D >= 2 && ml) o -= (double)((SCAR ? car(k, 1, v)[j] : vget(rfm_old[v], j)) * fm_l[c]);
+            }
+            if (o != 0.0) {
+              if (v == 0) {
+                atomicAdd(bud + 4, o * bs);
+                atomicAdd(bud + 5, o * bs);
+              } else {
+                atomicAdd(bud + v, o * bs * (double)KR.ic2);
+              }
+            }
+          }
         }
       }
       // recording for the adjoint: the pre-interaction state

@@ -10,6 +10,8 @@ constexpr int NPLANCK_LO = 27;    // FP64 Bernoulli-series terms (x < XSPLIT, er
 constexpr int NPLANCK_LO32 = 13;  // FP32 Bernoulli-series terms (error < 1e-8)
 constexpr int NPLANCK_UP = 48;    // cap of the FP64 exponential series (x >= XSPLIT: 14 terms)
 constexpr double XSPLIT = 3.0;    // lower/upper Planck series switch
+constexpr int NBUDGET = 8;        // budget accumulators per row (see StageArgs::budget)
+constexpr int BUDGET_SLOTS = 64;  // rows of budget accumulators that blocks add to (summed when read)
 constexpr int PTAB_PER_OCT = 32;  // FP32 Planck band tables: nodes per octave of T
 constexpr double PTAB_XMAX = 88.0;   // below T = eps_min/88 every band underflows in FP32
 constexpr double PTAB_XMIN = 6.103515625e-05;  // 2^-14: above T = eps_max/2^-14, series in x

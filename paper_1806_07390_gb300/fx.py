@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "FX_OK", -1: "FX_ERR_ARG", -2: "FX_ERR_CUDA", -3: "FX_ERR_WOR
                 -7: "FX_ERR_UNSUPPORTED"}
 FX_FP64, FX_FP32, FX_FP32_F64NEWTON = 0, 1, 2
 NTOTALS = 6
+NBUDGET = 8
 
 # every symbol include/fx.h declares
 EXPORTS = ["fx_grid_create", "fx_bind_workspace", "fx_state_elems", "fx_state_upload",
@@ -32,7 +33,7 @@ EXPORTS = ["fx_grid_create", "fx_bind_workspace", "fx_state_elems", "fx_state_up
            "fx_kernel_timing_enable", "fx_kernel_timing_read", "fx_objective_enable",
            "fx_boundary_energy_out", "fx_set_kappa0", "fx_state_set_density",
            "fx_adjoint_workspace_bytes", "fx_adjoint_forward", "fx_adjoint_backward", "fx_adjoint",
-           "fx_last_error", "fx_clear_error", "fx_grid_destroy"]
+           "fx_budgets_enable", "fx_budgets", "fx_last_error", "fx_clear_error", "fx_grid_destroy"]
 
 
 class FxError(RuntimeError):
@@ -98,6 +99,8 @@ def lib() -> ctypes.CDLL:
         L.fx_adjoint_backward.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, sz,
                                           ctypes.c_double, vp, vp, dp]
         L.fx_adjoint.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, sz, vp, vp, dp, dp]
+        L.fx_budgets_enable.argtypes = [vp, ctypes.c_int]
+        L.fx_budgets.argtypes = [vp, dp]
         L.fx_last_error.argtypes = [vp]
         L.fx_last_error.restype = ctypes.c_char_p
         L.fx_clear_error.argtypes = [vp]
@@ -107,7 +110,7 @@ def lib() -> ctypes.CDLL:
                   "fx_state_download", "fx_kernel_timing_enable", "fx_kernel_timing_read",
                   "fx_objective_enable", "fx_boundary_energy_out", "fx_set_kappa0",
                   "fx_state_set_density", "fx_adjoint_workspace_bytes", "fx_adjoint_forward",
-                  "fx_adjoint_backward", "fx_adjoint"):
+                  "fx_adjoint_backward", "fx_adjoint", "fx_budgets_enable", "fx_budgets"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -225,6 +228,17 @@ class Grid:
     def totals(self) -> np.ndarray:
         out = np.zeros(NTOTALS)
         self._check(self.L.fx_conserved_totals(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def budgets_enable(self, on: bool = True) -> None:
+        """Start (zeroing them) or stop accumulating the budgets of reading R13 in fx_step."""
+        self._check(self.L.fx_budgets_enable(self.h, int(bool(on))))
+
+    def budgets(self) -> np.ndarray:
+        """Budget terms accumulated since the reset (synchronising): boundary outflows of mass,
+        momentum 1..3, total energy and radiation energy; coupling work; floor energy."""
+        out = np.zeros(NBUDGET)
+        self._check(self.L.fx_budgets(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
 
     def launches_per_step(self) -> int:

@@ -324,3 +324,65 @@ def test_spherical_static_atmosphere_gpu(fxmod):
     got, st, _ = run_gpu(fxmod, pb, state=s, nsteps=2)
     assert st == 0
     assert np.max(np.abs(got - s)) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["blobs", "sod", "box3d"])
+def test_budgets_match_the_oracle_and_close(fxmod, case):
+    # reading R13: boundary outflows, coupling work and floor energy accumulated by the kernels
+    # equal the oracle's, and with the library's own totals every budget closes to round-off
+    if case == "blobs":
+        pb, _ = W.blobs_2d(shape=(40, 34), ngroups=6, nsteps=4, precision="fp64")
+        pb.c_light, pb.kappa0 = 6.0, 5.0
+    elif case == "sod":
+        pb, _ = W.sod_1d(n=64, ngroups=5)
+        pb.c_light = 8.0
+    else:
+        pb, _ = W.lognormal_3d(shape=(14, 10, 9), ngroups=4, precision="fp64")
+        pb.bc_lo = ("outflow", "reflect", "periodic")
+        pb.bc_hi = ("reflect", "outflow", "periodic")
+        pb.c_light = 5.0
+    pb.dt = 0.2 / pb.n[0] / pb.c_light
+    s = W.random_state(pb, seed=17, flux_frac=0.6)
+    ref, rst, rbud = oracle.run_budget(pb, s, pb.dt, 4, nthreads=8)
+    g = fxmod.Grid(pb)
+    g.upload(s)
+    t0 = g.totals()
+    g.budgets_enable(True)
+    g.step(pb.dt, 4)
+    assert g.status() == 0 and rst == 0
+    bud = g.budgets()
+    t1 = g.totals()
+    g.close()
+    scale = np.array([abs(t0[0])] * 4 + [abs(t0[4])] * 4)
+    assert np.all(np.abs(bud - rbud) <= 1e-12 * scale), (bud, rbud)
+    assert abs(t0[0] - t1[0] - bud[0]) <= 1e-13 * abs(t0[0])
+    for q in range(pb.dims):
+        assert abs(t0[1 + q] - t1[1 + q] - bud[1 + q]) <= 1e-13 * abs(t0[0])
+    assert abs(t0[4] - t1[4] - bud[4] - bud[6] + bud[7]) <= 1e-13 * abs(t0[4])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32n64"])
+def test_density_floor_is_reported(fxmod, precision):
+    # reading R18: a host-uploaded state with a block of cells below the density floor (at the
+    # temperature of their neighbours; wide enough that transport cannot lift its centre above
+    # the floor in one stage) is floored by the interaction and the status says so; the oracle
+    # applies the same floor and flags it
+    pb, prim = W.kh_2d(nx=24, ny=24, ngroups=4, nsteps=1, precision=precision)
+    pb64 = W.Problem(**{**pb.__dict__, "precision": "fp64"})
+    s = oracle.init_equilibrium(pb64, prim)
+    N = pb.ncell
+    y, x = np.divmod(np.arange(N), 24)
+    blk = (x >= 5) & (x < 19) & (y >= 5) & (y < 19)
+    T = prim[1] / prim[0]
+    rho = 0.5 * pb.rho_floor
+    s[:N][blk] = rho
+    s[N:2 * N][blk] = 0.0
+    s[2 * N:3 * N][blk] = 0.0
+    s[3 * N:4 * N][blk] = rho * T[blk] / (pb.gamma - 1.0)
+    _, rst = oracle.run(pb64, s, pb.dt, 1)
+    assert rst & 2  # the oracle's floor bit
+    g = fxmod.Grid(pb)
+    g.upload(s)
+    g.step(pb.dt, 1)
+    assert g.status() == -5
+    g.close()

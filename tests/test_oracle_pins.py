@@ -790,3 +790,40 @@ def test_coupling_inside_rk2_relaxes_at_the_turner_stone_rate():
     assert errs[-1] < 2e-3 and np.all(np.abs(order - 1.0) < 0.15), (errs, order)
     bad = errors(1)
     assert bad[-1] > 10 * errs[-1] and np.log2(bad[-2] / bad[-1]) < 0.3, bad
+
+
+# ------------------------------------------------------------------ budgets (reading R13)
+@pytest.mark.parametrize("case", ["blobs", "sod", "box3d"])
+def test_budgets_close_on_open_coupled_runs(case):
+    # Sec. 4 (conservation form) and Sec. 5.3 (Eqs. 31-32): mass and momentum (with the radiation
+    # momentum F/c^2) change only by what crosses the boundary; the total energy rho e + sum E
+    # also by the work of the flux absorption on the moving gas, which the comoving-frame update
+    # does not conserve (the remark after Eq. 32), and by the energy the silent positivity floor
+    # of E_g adds (reading R18; these random states drive some group energies negative).  With
+    # the outflows, that work and the floor energy accumulated as the update weighs them, every
+    # budget closes to round-off.
+    if case == "blobs":
+        pb, _ = W.blobs_2d(shape=(14, 10), ngroups=4, nsteps=5, precision="fp64")
+        pb.c_light, pb.kappa0 = 6.0, 5.0
+    elif case == "sod":
+        pb, _ = W.sod_1d(n=32, ngroups=5)
+        pb.c_light = 8.0
+    else:
+        pb, _ = W.lognormal_3d(shape=(6, 5, 4), ngroups=2, precision="fp64")
+        pb.bc_lo = ("outflow", "reflect", "periodic")
+        pb.bc_hi = ("reflect", "outflow", "periodic")
+        pb.c_light = 5.0
+    pb.dt = 0.2 / pb.n[0] / pb.c_light
+    s = W.random_state(pb, seed=17, flux_frac=0.6)
+    t0 = oracle.totals(pb, s)
+    out, st, bud = oracle.run_budget(pb, s, pb.dt, 5)
+    assert st == 0
+    t1 = oracle.totals(pb, out)
+    assert abs(bud[6]) > 0 and abs(bud[4]) > 0  # both terms are exercised
+    scale = np.abs(t0[0])
+    assert abs(t0[0] - t1[0] - bud[0]) <= 1e-14 * scale
+    for q in range(pb.dims):
+        assert abs(t0[1 + q] - t1[1 + q] - bud[1 + q]) <= 1e-14 * scale, q
+    assert abs(t0[4] - t1[4] - bud[4] - bud[6] + bud[7]) <= 1e-14 * abs(t0[4])
+    # without the work term the energy budget is off by more than round-off
+    assert abs(t0[4] - t1[4] - bud[4] + bud[7]) > 1e3 * 1e-14 * abs(t0[4])
