@@ -22,9 +22,10 @@ constexpr int groups_per_lane(bool fp32, int D, int GP) {
 
 // Cells per tile of the stage kernel for D dimensions and GL lanes per cell: 256 threads per
 // block, except 2-d with two groups per lane of 8 lanes (16 padded groups): a 20-cell tile of 160
-// threads, four blocks (20 warps) per SM at 96 registers instead of two blocks of 256 threads
-// (16 warps) at 121: the kernel is latency-bound there (kh2d stage kernel 0.462 -> 0.455 ms;
-// 16-, 24- and 28-cell tiles were slower).
+// threads (kh2d stage kernel 0.462 -> 0.455 ms against 32-cell tiles of 256 threads; 16-, 24-
+// and 28-cell tiles were slower).  It ran at four blocks per SM (96 registers) until the packed
+// pair arithmetic made that bound spill; at three blocks per SM it does not spill and is as fast
+// (0.482 -> 0.480 ms).
 __host__ __device__ constexpr int tile_cells(int D, int GL, int NGL) {
   return (D == 2 && GL == 8 && NGL == 2) ? 20 : 256 / GL;
 }

@@ -417,8 +417,7 @@ inline size_t stage_smem_bytes(int G) {
 // with a non-periodic boundary: on a fully periodic grid the code would only cost registers.
 // ---------------------------------------------------------------------------------------------
 template <class R, int D, int GP, int TX, int TY, class LT, class NT, int NGL, bool SPH, int RO, bool BUD>
-__global__ void __launch_bounds__(TX * TY * (GP / NGL),
-                                  (sizeof(R) == 4 && NGL == 1) ? 3 : (TX * TY * (GP / NGL) <= 160 ? 4 : 2))
+__global__ void __launch_bounds__(TX * TY * (GP / NGL), (sizeof(R) == 4 && (NGL == 1 || TX * TY * (GP / NGL) <= 160)) ? 3 : 2)
 stage_kernel(const __grid_constant__ StageArgs<R> A) {
   static_assert(!SPH || D == 2, "the spherical geometry is 2-d (r, theta)");
   using LY = StageLayout<D, TX, TY>;
