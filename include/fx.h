@@ -48,6 +48,7 @@ enum { FX_CART = 0, FX_SPH = 1 };       /* Cartesian, or spherical (x1 -> r, x2 
 /* radial map (Appendix A): r = x1, r = exp(x1), or r = r_t sinh(x1 / r_t) (r_t = map_rt) */
 enum { FX_MAP_ID = 0, FX_MAP_EXP = 1, FX_MAP_SINH = 2 };
 enum { FX_FP64 = 0, FX_FP32 = 1, FX_FP32_F64NEWTON = 2 }; /* precision forms (see fx_params)  */
+enum { FX_HLLC = 0, FX_HLLE = 1, FX_LLF = 2 };            /* gas Riemann solvers (Sec. 5.2)   */
 enum { FX_NTOTALS = 6, FX_NBUDGET = 8 };
 
 /* Grid, physics and solver parameters (plain data, copied at fx_grid_create).
@@ -81,6 +82,15 @@ enum { FX_NTOTALS = 6, FX_NBUDGET = 8 };
  *   rho_floor, p_floor, E_floor
  *                      floors; applying the density or pressure floor sets FX_ERR_FLOOR, the
  *                      radiation-energy floor is a silent positivity floor.
+ *   map_rt             see geom, map1.
+ *   riemann            gas Riemann solver (Sec. 5.2): FX_HLLC (0, the paper's default), FX_HLLE
+ *                      or FX_LLF (local Lax-Friedrichs).  The radiation advection is upwinded on
+ *                      the HLLC contact speed of the face's states with every solver.
+ *   shock_guard        carbuncle guard (Sec. 5.2), 0 = off: a face lies in a shock when the
+ *                      pressures of its two cells differ by more than the factor 1 + shock_guard,
+ *                      and with FX_HLLC a face of direction d takes HLLE when one of its cells
+ *                      has such a face in another direction.  The adjoint needs FX_HLLC without
+ *                      the guard (otherwise FX_ERR_UNSUPPORTED).
  */
 typedef struct {
   int dims;
@@ -100,6 +110,8 @@ typedef struct {
   double newton_rtol;
   double rho_floor, p_floor, E_floor;
   double map_rt;
+  int riemann;
+  double shock_guard;
 } fx_params;
 
 /* State layout (upload, download, and the device copy inside the workspace): ncell = prod n[d],
@@ -174,8 +186,9 @@ fx_status fx_budgets(fx_grid* h, double out[FX_NBUDGET]);
 fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is_device);
 
 /* Number of kernel launches enqueued by one fx_step(dt, 1) call (per RK stage: the gas face
- * kernel, the radiation/update kernel, with the interaction on the interaction kernel, and the
- * objective's reduction while it is enabled). */
+ * kernel, the radiation/update kernel, with the interaction on the interaction kernel, with
+ * the carbuncle guard on the shock-flag kernel, and the objective's reduction while it is
+ * enabled). */
 int fx_launches_per_step(const fx_grid* h);
 
 /* Planes of the slowest axis that one block of the radiation/update kernel marches over: 32 (or

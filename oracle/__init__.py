@@ -12,7 +12,7 @@ import subprocess
 
 import numpy as np
 
-from paper_1806_07390_gb300.workloads import BC_CODES, GEOM_CODES, MAP_CODES, Problem
+from paper_1806_07390_gb300.workloads import BC_CODES, GEOM_CODES, MAP_CODES, RIEMANN_CODES, Problem
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fx_oracle.cpp")
@@ -43,7 +43,8 @@ class OrcParams(ctypes.Structure):
         ("newton_maxit", ctypes.c_int), ("bisect_maxit", ctypes.c_int),
         ("newton_rtol", ctypes.c_double), ("rho_floor", ctypes.c_double),
         ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double), ("nthreads", ctypes.c_int),
-        ("map_rt", ctypes.c_double), ("r10_full_dt", ctypes.c_int),
+        ("map_rt", ctypes.c_double), ("r10_full_dt", ctypes.c_int), ("riemann", ctypes.c_int),
+        ("shock_guard", ctypes.c_double),
     ]
 
 
@@ -78,6 +79,7 @@ def lib():
         L.orc_recon_cell.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, _DP, _DP]
         L.orc_hllc.argtypes = [ctypes.c_int, ctypes.c_double, _DP, _DP, _DP, _DP]
+        L.orc_gas_flux.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _DP, _DP, _DP, _DP]
         L.orc_planck_group.argtypes = [P, ctypes.c_int, ctypes.c_double, _DP, _DP]
         L.orc_geometry.argtypes = [P, ctypes.c_int, _DP, _DP, _DP]
         L.orc_christoffel.argtypes = [P, _DP, _DP, _DP, _DP, _DP]
@@ -107,6 +109,8 @@ def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0, r10_full_dt: int
     P.rho_floor, P.p_floor, P.E_floor = pb.rho_floor, pb.p_floor, pb.E_floor
     P.nthreads = nthreads
     P.r10_full_dt = r10_full_dt
+    P.riemann = RIEMANN_CODES[pb.riemann]
+    P.shock_guard = pb.shock_guard
     return P
 
 
@@ -216,6 +220,18 @@ def hllc(D: int, gamma: float, WL, WR) -> tuple[np.ndarray, float]:
     fl = np.zeros(5)
     vs = ctypes.c_double()
     lib().orc_hllc(D, gamma, _ptr(wl), _ptr(wr), _ptr(fl), ctypes.byref(vs))
+    return fl[: 2 + D], vs.value
+
+
+def gas_flux(solver: str, D: int, gamma: float, WL, WR) -> tuple[np.ndarray, float]:
+    """Gas flux of one face by the solver "hllc", "hlle" or "llf" (states as for hllc)."""
+    wl = np.zeros(5)
+    wr = np.zeros(5)
+    wl[: len(WL)] = WL
+    wr[: len(WR)] = WR
+    fl = np.zeros(5)
+    vs = ctypes.c_double()
+    lib().orc_gas_flux(RIEMANN_CODES[solver], D, gamma, _ptr(wl), _ptr(wr), _ptr(fl), ctypes.byref(vs))
     return fl[: 2 + D], vs.value
 
 

@@ -42,6 +42,12 @@
 //   R18 floors on rho and p (reported) and a silent positivity floor on E_g.
 //   R19 J = sum_steps dt (Phi(U^n) + Phi(U^(1)))/2, Phi = sum over groups and upper-x faces of
 //      face area x (corrected HLL energy flux + v* E upwind): the outflow the update itself uses.
+//   R21 HLLE uses the speed bounds of R6 (b_L = min(S_L, 0), b_R = max(S_R, 0)); local
+//      Lax-Friedrichs uses s = max(|u_L| + a_L, |u_R| + a_R).  Neither has a contact: the
+//      radiation advection (Eq. 19) is upwinded on the HLLC contact speed of the same states.
+//   R22 carbuncle guard: a face is in a shock when the pressures of its two cells differ by more
+//      than the factor 1 + shock_guard; a face of direction d takes HLLE when one of its two
+//      cells has such a face in a direction other than d.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -126,6 +132,7 @@ extern "C" {
 enum { ORC_OUTFLOW = 0, ORC_PERIODIC = 1, ORC_REFLECT = 2, ORC_AXIS = 3 };
 enum { ORC_CART = 0, ORC_SPH = 1 };
 enum { ORC_MAP_ID = 0, ORC_MAP_EXP = 1, ORC_MAP_SINH = 2 };
+enum { ORC_HLLC = 0, ORC_HLLE = 1, ORC_LLF = 2 };
 struct orc_params {
   int dims;
   int n[3];
@@ -148,6 +155,8 @@ struct orc_params {
   double map_rt;
   int r10_full_dt;          // test switch: 1 takes dt (not dt/2) as the coupling step after stage 2,
                             // the inconsistent alternative to reading R10 (the R10 pin must fail it)
+  int riemann;              // gas Riemann solver: ORC_HLLC (default), ORC_HLLE or ORC_LLF (R21)
+  double shock_guard;       // carbuncle guard (R22): pressure-jump threshold; 0 = off
 };
 }
 
@@ -652,6 +661,57 @@ static void hllc(int D, double gam, const S WL[5], const S WR[5], S flux[5], S& 
 }
 
 // ---------------------------------------------------------------------------------------------
+// Gas flux of one face by the selected solver (Sec. 5.2 names local Lax-Friedrichs, HLLE and
+// HLLC; reading R21).  States and orientation as for hllc; vstar is always the HLLC contact
+// speed of the two states.
+// ---------------------------------------------------------------------------------------------
+template <class S>
+static void gas_flux(int solver, int D, double gam, const S WL[5], const S WR[5], S flux[5], S& vstar) {
+  const int nv = 2 + D;
+  S fc[5];
+  hllc(D, gam, WL, WR, fc, vstar);
+  if (solver == ORC_HLLC) {
+    for (int v = 0; v < nv; ++v) flux[v] = fc[v];
+    return;
+  }
+  // conserved states and physical fluxes of the two states
+  S rl = WL[0], pl = WL[1], rr = WR[0], pr = WR[1], ul = WL[2], ur = WR[2];
+  S kel = 0.0, ker = 0.0;
+  for (int q = 0; q < D; ++q) { kel += WL[2 + q] * WL[2 + q]; ker += WR[2 + q] * WR[2 + q]; }
+  S El = pl / (gam - 1.0) + 0.5 * rl * kel, Er = pr / (gam - 1.0) + 0.5 * rr * ker;
+  S al = sqrt(gam * pl / rl), ar = sqrt(gam * pr / rr);
+  S UL[5], UR[5], FL[5], FR[5];
+  UL[0] = rl; UR[0] = rr;
+  for (int q = 0; q < D; ++q) { UL[1 + q] = rl * WL[2 + q]; UR[1 + q] = rr * WR[2 + q]; }
+  UL[1 + D] = El; UR[1 + D] = Er;
+  FL[0] = rl * ul; FR[0] = rr * ur;
+  for (int q = 0; q < D; ++q) { FL[1 + q] = rl * ul * WL[2 + q]; FR[1 + q] = rr * ur * WR[2 + q]; }
+  FL[1] = FL[1] + pl; FR[1] = FR[1] + pr;
+  FL[1 + D] = (El + pl) * ul; FR[1 + D] = (Er + pr) * ur;
+  if (solver == ORC_LLF) {
+    S s = smax(fabs(ul) + al, fabs(ur) + ar);
+    branch(13, val(fabs(ul) + al) >= val(fabs(ur) + ar));
+    for (int v = 0; v < nv; ++v) flux[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * s * (UR[v] - UL[v]);
+    return;
+  }
+  // HLLE with the Einfeldt / Roe-average bounds of R6
+  S sl = sqrt(rl), sr = sqrt(rr), wsum = sl + sr;
+  S Ht = (sl * (El + pl) / rl + sr * (Er + pr) / rr) / wsum;
+  S vt2 = 0.0, ut = 0.0;
+  for (int q = 0; q < D; ++q) {
+    S vq = (sl * WL[2 + q] + sr * WR[2 + q]) / wsum;
+    vt2 += vq * vq;
+    if (q == 0) ut = vq;
+  }
+  S at2 = (gam - 1.0) * (Ht - 0.5 * vt2);
+  S at = sqrt(smax(at2, S(0.0)));
+  S bl = smin(smin(ul - al, ut - at), S(0.0));
+  S br = smax(smax(ur + ar, ut + at), S(0.0));
+  branch(14, 2 * (val(bl) < 0.0) + (val(br) > 0.0));
+  for (int v = 0; v < nv; ++v) flux[v] = (br * FL[v] - bl * FR[v] + bl * br * (UR[v] - UL[v])) / (br - bl);
+}
+
+// ---------------------------------------------------------------------------------------------
 // M1 closure (R7): Eddington factor chi(f) and the normal row of the pressure tensor.
 // Given E and physical F (D components), returns P_{n j} (j = 0..D-1) for normal n.
 // ---------------------------------------------------------------------------------------------
@@ -911,6 +971,27 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
           branch(8, val(T) > 0.0);
         }
       }
+  // carbuncle guard (R22): bit e of a cell's flag is set when one of its two faces of direction e
+  // joins pressures that differ by more than the factor 1 + shock_guard
+  std::vector<unsigned char> sflag(P.shock_guard > 0.0 ? NC : 0, 0);
+  if (P.shock_guard > 0.0) {
+    for (int e = 0; e < D; ++e)
+      for (int k = 0; k < L.np[2]; ++k)
+        for (int j = 0; j < L.np[1]; ++j)
+          for (int i = 0; i < L.np[0]; ++i) {
+            int c[3] = {i, j, k};
+            if (c[e] + 1 >= L.np[e]) continue;
+            size_t ia = L.idx(i, j, k);
+            c[e] += 1;
+            size_t ib = L.idx(c[0], c[1], c[2]);
+            const double pa = val(W[ia * NW + 1]), pb = val(W[ib * NW + 1]);
+            const double lo = std::min(pa, pb), hi = std::max(pa, pb);
+            if (hi > (1.0 + P.shock_guard) * lo) {
+              sflag[ia] |= (unsigned char)(1u << e);
+              sflag[ib] |= (unsigned char)(1u << e);
+            }
+          }
+  }
   // boundary outflow per row of the upper x boundary (R19)
   std::vector<S> phi_row((size_t)L.n[1] * L.n[2], S(0.0));
   // boundary outflow per direction and row (R13), 6 quantities each
@@ -954,7 +1035,14 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
           WLr[0] = WL[0]; WLr[1] = WL[1]; WRr[0] = WR[0]; WRr[1] = WR[1];
           for (int q = 0; q < D; ++q) { WLr[2 + q] = WL[2 + (d + q) % D]; WRr[2 + q] = WR[2 + (d + q) % D]; }
           S fl[5], vstar;
-          hllc(D, gam, WLr, WRr, fl, vstar);
+          int solver = P.riemann;
+          if (P.shock_guard > 0.0 && solver == ORC_HLLC) {
+            // a shock across a face of another direction at either cell: HLLE here (R22)
+            const unsigned tr = (unsigned)(sflag[il] | sflag[ir]) & ~(1u << d);
+            branch(15, tr != 0);
+            if (tr) solver = ORC_HLLE;
+          }
+          gas_flux(solver, D, gam, WLr, WRr, fl, vstar);
           double Aph, Ah[3], hn;
           face_geometry(P, geo, d, f, cl, Aph, Ah, hn);
           // gas fluxes into covariant components
@@ -1419,6 +1507,9 @@ void orc_recon_cell(const orc_params* P, int d, int i, double pm, double p0, dou
 }
 void orc_hllc(int D, double gam, const double* WL, const double* WR, double* flux, double* vstar) {
   hllc(D, gam, WL, WR, flux, *vstar);
+}
+void orc_gas_flux(int solver, int D, double gam, const double* WL, const double* WR, double* flux, double* vstar) {
+  gas_flux(solver, D, gam, WL, WR, flux, *vstar);
 }
 // Planck group energy density for group g at temperature T (and derivative).
 void orc_planck_group(const orc_params* P, int g, double T, double* B, double* dB) {

@@ -124,6 +124,7 @@ struct fx_grid {
   size_t off_ptab = 0;
   size_t off_faces = 0;           // gas face buffer [dir][NG+1][faces of dir]
   size_t off_opk = 0;             // opacity factors of the stage input [K, S][cells]
+  size_t off_sflag = 0;           // shock flags of the stage input [cells] (carbuncle guard)
   int64_t face_off[3] = {0, 0, 0};
   bool uniform[3] = {false, false, false};
   // per-kernel timing: one event triple (before the face kernel, between, after the stage
@@ -617,6 +618,7 @@ StageArgs<R> stage_args(fx_grid* h) {
   a.faces = reinterpret_cast<const R*>(h->ws + h->off_faces);
   a.faces_out = reinterpret_cast<R*>(h->ws + h->off_faces);
   a.opk = reinterpret_cast<R*>(h->ws + h->off_opk);
+  a.sflag = h->P.shock_guard > 0.0 ? reinterpret_cast<unsigned char*>(h->ws + h->off_sflag) : nullptr;
   for (int d = 0; d < 3; ++d) {
     a.face_off[d] = h->face_off[d];
     a.uniform[d] = d < h->D && h->uniform[d];
@@ -955,6 +957,7 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   if (P.precision != FX_FP64 && P.precision != FX_FP32 && P.precision != FX_FP32_F64NEWTON)
     return FX_ERR_ARG;
   if (P.rad_recon_order != 1 && P.rad_recon_order != 2) return FX_ERR_ARG;
+  if (P.riemann < FX_HLLC || P.riemann > FX_LLF || !(P.shock_guard >= 0.0)) return FX_ERR_ARG;
   if (!(P.gamma > 1.0) || !(P.c_light > 0.0) || !(P.a_rad > 0.0)) return FX_ERR_ARG;
   if (!half_integer(P.kap_rho_exp) || !half_integer(P.kap_T_exp)) return FX_ERR_UNSUPPORTED;
   if (!(P.eps_min > 0.0) || !(P.eps_max > P.eps_min)) return FX_ERR_ARG;
@@ -1012,6 +1015,8 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   g.bisect_maxit = P.bisect_maxit;
   g.newton_rtol = P.newton_rtol;
   g.couple = P.couple;
+  g.riemann = P.riemann;
+  g.shock_guard = P.shock_guard;
 
   for (int d = 0; d < P.dims; ++d) build_table(P, d, h->tab[d]);
   for (int j = 0; j <= h->G; ++j)
@@ -1049,6 +1054,8 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   }
   h->off_opk = off;
   off = align_up(off + (size_t)2 * h->ncell * h->elem);
+  h->off_sflag = off;  // carbuncle guard: shock flags, one byte per cell
+  off = align_up(off + (P.shock_guard > 0.0 ? (size_t)h->ncell : 0));
   // directions whose table rows are all equal (uniform Cartesian spacing) read one row
   for (int d = 0; d < P.dims; ++d) {
     const int np = (int)P.n[d] + 4;
@@ -1111,7 +1118,7 @@ fx_status fx_budgets(fx_grid* h, double out[FX_NBUDGET]) {
 int fx_launches_per_step(const fx_grid* h) {
   if (!h) return 0;
   const bool split = h->P.couple != 0;  // the interaction kernel runs in every form
-  return 2 * (2 + (split ? 1 : 0) + (h->objective ? 1 : 0));
+  return 2 * (2 + (split ? 1 : 0) + (h->objective ? 1 : 0) + (h->P.shock_guard > 0.0 ? 1 : 0));
 }
 
 fx_status fx_objective_enable(fx_grid* h, int on) {
@@ -1156,6 +1163,8 @@ static fx_status adjoint_entry(fx_grid* h, double dt, int nsteps, int k, void* a
   if (h->P.geom != FX_CART) return fail(h, FX_ERR_UNSUPPORTED, "the adjoint supports Cartesian grids");
   if (h->P.rad_recon_order != 1)
     return fail(h, FX_ERR_UNSUPPORTED, "the adjoint supports the linear radiation reconstruction");
+  if (h->P.riemann != FX_HLLC || h->P.shock_guard > 0.0)
+    return fail(h, FX_ERR_UNSUPPORTED, "the adjoint supports HLLC without the carbuncle guard");
   if (!adj_ws || adj_bytes < adj_layout(h, nsteps, k).bytes || (reinterpret_cast<uintptr_t>(adj_ws) % kAlign) != 0)
     return fail(h, FX_ERR_WORKSPACE, "adjoint workspace missing, too small or not 256-byte aligned");
   unsigned char* ws = static_cast<unsigned char*>(adj_ws);

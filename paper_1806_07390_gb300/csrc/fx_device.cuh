@@ -257,6 +257,52 @@ __device__ __forceinline__ void hllc(R gam, const V* L, const V* Rs, V* f, V& vs
   f[1 + D] = (Ek + pk) * uk + Sk * (Es - Ek);
 }
 
+// Gas flux of one face by the selected solver (Sec. 5.2 names local Lax-Friedrichs, HLLE and
+// HLLC; reading R21): 0 HLLC, 1 HLLE with the speed bounds of R6 (b_L = min(S_L, 0),
+// b_R = max(S_R, 0)), 2 local Lax-Friedrichs with s = max(|u_L| + a_L, |u_R| + a_R).  vstar is
+// always the HLLC contact speed of the two states (the upwind velocity of Eq. 19).
+template <class R, int D>
+__device__ __forceinline__ void gas_riemann(int solver, R gam, const R* L, const R* Rs, R* f, R& vstar) {
+  hllc<R, D>(gam, L, Rs, f, vstar);
+  if (solver == 0) return;
+  const R gm1 = gam - R(1);
+  const R rl = L[0], pl = L[1], ul = L[2], rr = Rs[0], pr = Rs[1], ur = Rs[2];
+  R kl = ul * ul, kr = ur * ur;
+#pragma unroll
+  for (int q = 1; q < D; ++q) { kl += L[2 + q] * L[2 + q]; kr += Rs[2 + q] * Rs[2 + q]; }
+  const R El = pl / gm1 + R(0.5) * rl * kl, Er = pr / gm1 + R(0.5) * rr * kr;
+  const R al = sqrt(gam * pl / rl), ar = sqrt(gam * pr / rr);
+  R UL[2 + D], UR[2 + D], FL[2 + D], FR[2 + D];
+  UL[0] = rl; UR[0] = rr;
+  FL[0] = rl * ul; FR[0] = rr * ur;
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    UL[1 + q] = rl * L[2 + q]; UR[1 + q] = rr * Rs[2 + q];
+    FL[1 + q] = rl * ul * L[2 + q]; FR[1 + q] = rr * ur * Rs[2 + q];
+  }
+  FL[1] += pl; FR[1] += pr;
+  UL[1 + D] = El; UR[1 + D] = Er;
+  FL[1 + D] = (El + pl) * ul; FR[1 + D] = (Er + pr) * ur;
+  if (solver == 2) {
+    const R sm = fmax(fabs(ul) + al, fabs(ur) + ar);
+#pragma unroll
+    for (int v = 0; v < 2 + D; ++v) f[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * sm * (UR[v] - UL[v]);
+    return;
+  }
+  const R sl = sqrt(rl), sr = sqrt(rr), iw = R(1) / (sl + sr);
+  const R Ht = (sl * ((El + pl) / rl) + sr * ((Er + pr) / rr)) * iw;
+  const R ut = (sl * ul + sr * ur) * iw;
+  R v2 = ut * ut;
+#pragma unroll
+  for (int q = 1; q < D; ++q) { const R vq = (sl * L[2 + q] + sr * Rs[2 + q]) * iw; v2 += vq * vq; }
+  const R at2 = gm1 * (Ht - R(0.5) * v2);
+  const R at = sqrt(at2 > R(0) ? at2 : R(0));
+  const R bl = fmin(fmin(ul - al, ut - at), R(0)), br = fmax(fmax(ur + ar, ut + at), R(0));
+  const R ib = R(1) / (br - bl);
+#pragma unroll
+  for (int v = 0; v < 2 + D; ++v) f[v] = (br * FL[v] - bl * FR[v] + bl * br * (UR[v] - UL[v])) * ib;
+}
+
 // Reciprocal: IEEE division in FP64; the hardware approximation (2 ulp) in FP32.
 __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }

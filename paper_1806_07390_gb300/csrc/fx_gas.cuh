@@ -1,6 +1,7 @@
 // Gas face kernel: for every cell face of every direction, the coordinate-moment parabolic
-// reconstruction of the two neighbouring cells (Sec. 5.1) and the HLLC flux with its contact
-// speed (Sec. 5.2).  A block stages a tile's primitives in shared memory and reconstructs each
+// reconstruction of the two neighbouring cells (Sec. 5.1) and the Riemann flux (HLLC, or the
+// HLLE / local Lax-Friedrichs options and the carbuncle guard) with the HLLC contact speed
+// (Sec. 5.2).  A block stages a tile's primitives in shared memory and reconstructs each
 // cell once, for both of its faces.  It also forms every cell's opacity factors.
 // The stage kernel then uses the fluxes for the gas divergence, the contact speeds to upwind the
 // radiation advection (Eq. 19), and the opacity factors for the ε correction of the radiation
@@ -42,7 +43,8 @@ __host__ __device__ inline unsigned face_tiles(const int* n, int D, int DIR) {
 
 // Fluxes through the faces of one tile of direction DIR: the primitives of the tile's cells and
 // their halo along DIR go to shared memory once, each cell is reconstructed once (its upper-face
-// state serves the face above it, its lower-face state its own face), and each face gets HLLC.
+// state serves the face above it, its lower-face state its own face), and each face gets the
+// selected Riemann flux.
 template <class R, int D, int DIR>
 __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned tile, R (*sw)[FACE_WCELLS],
                                                R (*sb)[FACE_BCELLS]) {
@@ -141,7 +143,22 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
     Lr[slot] = sb[v][(r - 1) * LX + lx];
     Rr[slot] = Ra[v];
   }
-  hllc<R, D>(KR.gamma, Lr, Rr, fl, vs);
+  int solver = g.riemann;
+  if (A.sflag != nullptr && solver == 0) {
+    // carbuncle guard (reading R22): HLLE when one of the face's two cells lies in a shock
+    // across a face of another direction (ghosts take the flags of the cell they map to)
+    unsigned fl2 = 0;
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2) {
+      bool flip = false;
+      const int cd = min(max(bc_map(id - 1 + s2, nd, g.bc_lo[DIR], g.bc_hi[DIR], flip), 0), nd - 1);
+      const int c0 = DIR == 0 ? cd : x, c1 = DIR == 1 ? cd : i1, c2 = DIR == 2 ? cd : i2;
+      fl2 |= A.sflag[((uint32_t)c2 * n1 + c1) * n0 + c0];
+    }
+    if (fl2 & ~(1u << DIR)) solver = 1;
+  }
+  if (solver == 0) hllc<R, D>(KR.gamma, Lr, Rr, fl, vs);
+  else gas_riemann<R, D>(solver, KR.gamma, Lr, Rr, fl, vs);
   const uint32_t ex = (uint32_t)(n0 + (DIR == 0)), ey = (uint32_t)(n1 + (DIR == 1));
   const uint32_t nf = ex * ey * (uint32_t)(n2 + (DIR == 2));
   const uint32_t uf = DIR == 0 ? ((uint32_t)i2 * n1 + i1) * ex + (uint32_t)id
@@ -153,6 +170,56 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
   for (int c = 0; c < D; ++c) out[(uint32_t)(1 + (DIR + c) % D) * nf + uf] = fl[1 + c];
   out[(uint32_t)(NG - 1) * nf + uf] = fl[1 + D];
   out[(uint32_t)NG * nf + uf] = vs;
+}
+
+// Carbuncle guard (Sec. 5.2; reading R22): for every cell of the stage input, bit e of sflag is
+// set when the pressure across one of its two faces of direction e changes by more than the
+// factor 1 + shock_guard.  Neighbours beyond the boundary are the ghosts of the boundary rules
+// (their pressure with the scale factors of the ghost's own position, as the face kernel's).
+template <class R, int D>
+__global__ void __launch_bounds__(256) shock_flag_kernel(const __grid_constant__ StageArgs<R> A) {
+  constexpr int NG = 2 + D;
+  const DevGrid& g = A.g;
+  const uint32_t ncell = (uint32_t)g.ncell;
+  const uint32_t c = blockIdx.x * 256u + threadIdx.x;
+  if (c >= ncell) return;
+  const int n0 = g.n[0], n1 = g.n[1];
+  const int ix = (int)(c % (uint32_t)n0), iy = (int)((c / (uint32_t)n0) % (uint32_t)n1);
+  const int iz = (int)(c / ((uint32_t)n0 * n1));
+  const auto& KR = A.k(R(0));
+  const bool sph = g.geom != 0;
+  const Tab<R> t0{A.tab[0], n0 + 4, A.uniform[0] ? A.urow[0] : nullptr};
+  const Tab<R> t1{A.tab[D >= 2 ? 1 : 0], (D >= 2 ? n1 : n0) + 4,
+                  A.uniform[D >= 2 ? 1 : 0] ? A.urow[D >= 2 ? 1 : 0] : nullptr};
+  auto pres = [&](int x, int y, int z) -> R {
+    bool f = false;
+    const int mx = min(max(bc_map(x, n0, g.bc_lo[0], g.bc_hi[0], f), 0), n0 - 1);
+    const int my = D >= 2 ? min(max(bc_map(y, n1, g.bc_lo[1], g.bc_hi[1], f), 0), n1 - 1) : 0;
+    const int mz = D >= 3 ? min(max(bc_map(z, g.n[2], g.bc_lo[2], g.bc_hi[2], f), 0), g.n[2] - 1) : 0;
+    const uint32_t ci = ((uint32_t)mz * n1 + my) * n0 + mx;
+    R u[NG];
+#pragma unroll
+    for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + ci];
+    if (sph) {  // physical components with the scale factors of the (ghost) position
+      u[1] *= frcp(t0(T_HA, bc_pad(x)) * t1(T_HA, bc_pad(y)));
+      if (D >= 2) u[2] *= frcp(t0(T_HB, bc_pad(x)) * t1(T_HB, bc_pad(y)));
+    }
+    const R irho = frcp(u[0]);
+    R ke = R(0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) ke += u[1 + q] * (u[1 + q] * irho);
+    return KR.gm1 * (u[NG - 1] - R(0.5) * ke);
+  };
+  const R p0 = pres(ix, iy, iz), thr = R(1) + R(g.shock_guard);
+  unsigned char fl = 0;
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    const R pm = pres(ix - (e == 0), iy - (e == 1), iz - (e == 2));
+    const R pp = pres(ix + (e == 0), iy + (e == 1), iz + (e == 2));
+    const bool sm = fmax(p0, pm) > thr * fmin(p0, pm), sp = fmax(p0, pp) > thr * fmin(p0, pp);
+    if (sm || sp) fl |= (unsigned char)(1u << e);
+  }
+  A.sflag[c] = fl;
 }
 
 // One block per tile; grid row y is the direction (tiles beyond a direction's count return).

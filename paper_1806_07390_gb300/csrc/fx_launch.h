@@ -94,6 +94,11 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
   unsigned ntmax = 0;
   for (int d = 0; d < D; ++d) ntmax = ntmax > face_tiles(a.g.n, D, d) ? ntmax : face_tiles(a.g.n, D, d);
   dim3 gg(ntmax, D, 1);
+  if (a.sflag != nullptr) {  // carbuncle guard: shock flags of the stage input first
+    shock_flag_kernel<R, D><<<(unsigned)((a.g.ncell + 255) / 256), 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   gas_face_kernel<R, D><<<gg, FACE_THREADS, 0, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

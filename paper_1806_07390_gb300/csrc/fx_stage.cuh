@@ -67,6 +67,8 @@ template <class R> struct StageArgs {
   R* faces_out;        // the same buffer, written by gas_face_kernel
   R* opk;              // opacity factors K = kappa0 rho^a T^b, S = sigma0 rho of every cell of the
                        // stage input [2][ncell]: gas_face_kernel writes, stage_kernel reads
+  unsigned char* sflag;  // carbuncle guard (null when off): bit e of a cell's byte is set when a
+                         // face of direction e of the cell lies in a shock (shock_flag_kernel)
   int64_t face_off[3]; // element offset of each direction's block in `faces`
   R urow[3][NTAB];     // the common table row of a uniform direction
   int uniform[3];      // direction d has identical table rows (Cartesian grids)

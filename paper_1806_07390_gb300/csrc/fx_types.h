@@ -38,6 +38,8 @@ struct DevGrid {
   double newton_rtol;
   int couple;
   int rad_order;  // radiation reconstruction: 1 linear with the MC limiter, 2 the gas's parabola
+  int riemann;        // gas solver: 0 HLLC, 1 HLLE, 2 local Lax-Friedrichs
+  double shock_guard; // carbuncle guard pressure-jump threshold (0: off)
 };
 
 }  // namespace fx

@@ -12,7 +12,7 @@ from typing import Optional
 
 import numpy as np
 
-from .workloads import BC_CODES, GEOM_CODES, MAP_CODES, Problem
+from .workloads import BC_CODES, GEOM_CODES, MAP_CODES, RIEMANN_CODES, Problem
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfx.so")
@@ -55,6 +55,7 @@ class FxParams(ctypes.Structure):
         ("newton_maxit", ctypes.c_int), ("bisect_maxit", ctypes.c_int),
         ("newton_rtol", ctypes.c_double), ("rho_floor", ctypes.c_double),
         ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double), ("map_rt", ctypes.c_double),
+        ("riemann", ctypes.c_int), ("shock_guard", ctypes.c_double),
     ]
 
 
@@ -133,6 +134,7 @@ def params(pb: Problem) -> FxParams:
     P.rad_recon_order, P.couple = pb.rad_recon_order, pb.couple
     P.newton_maxit, P.bisect_maxit, P.newton_rtol = pb.newton_maxit, pb.bisect_maxit, pb.newton_rtol
     P.rho_floor, P.p_floor, P.E_floor = pb.rho_floor, pb.p_floor, pb.E_floor
+    P.riemann, P.shock_guard = RIEMANN_CODES[pb.riemann], pb.shock_guard
     return P
 
 

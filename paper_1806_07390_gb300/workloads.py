@@ -27,6 +27,7 @@ import numpy as np
 BC_CODES = {"outflow": 0, "periodic": 1, "reflect": 2, "axis": 3}
 GEOM_CODES = {"cart": 0, "sph": 1}
 MAP_CODES = {"id": 0, "exp": 1, "sinh": 2}
+RIEMANN_CODES = {"hllc": 0, "hlle": 1, "llf": 2}
 
 
 @dataclasses.dataclass
@@ -55,6 +56,8 @@ class Problem:
     map1: str = "id"
     map_rt: float = 1.0  # r_t of the sinh map r = r_t sinh(x1 / r_t)
     rad_recon_order: int = 1
+    riemann: str = "hllc"      # gas Riemann solver: "hllc", "hlle" or "llf" (Sec. 5.2)
+    shock_guard: float = 0.0   # carbuncle guard pressure-jump threshold (0: off)
     couple: int = 1
     newton_maxit: int = 50
     bisect_maxit: int = 200

@@ -827,3 +827,119 @@ def test_budgets_close_on_open_coupled_runs(case):
     assert abs(t0[4] - t1[4] - bud[4] - bud[6] + bud[7]) <= 1e-14 * abs(t0[4])
     # without the work term the energy budget is off by more than round-off
     assert abs(t0[4] - t1[4] - bud[4] + bud[7]) > 1e3 * 1e-14 * abs(t0[4])
+
+
+# ------------------------------------------------------------------ Riemann solver options (Sec. 5.2)
+@pytest.mark.parametrize("solver", ["hlle", "llf"])
+def test_alternative_solvers_are_consistent_and_mirror_symmetric(solver):
+    gam = 1.4
+    rng = np.random.default_rng(4)
+    for D in (1, 2, 3):
+        for _ in range(40):
+            Wd = [rng.uniform(0.1, 2), rng.uniform(0.1, 2)] + list(rng.uniform(-1, 1, D))
+            f, vs = oracle.gas_flux(solver, D, gam, Wd, Wd)
+            np.testing.assert_allclose(f, euler_flux(D, gam, Wd), rtol=1e-13, atol=1e-14)
+            assert abs(vs - Wd[2]) < 1e-13
+        WL = [rng.uniform(0.1, 2), rng.uniform(0.1, 2)] + list(rng.uniform(-1, 1, D))
+        WR = [rng.uniform(0.1, 2), rng.uniform(0.1, 2)] + list(rng.uniform(-1, 1, D))
+        f, vs = oracle.gas_flux(solver, D, gam, WL, WR)
+        mL = [WR[0], WR[1], -WR[2]] + WR[3:]
+        mR = [WL[0], WL[1], -WL[2]] + WL[3:]
+        g, ws = oracle.gas_flux(solver, D, gam, mL, mR)
+        sign = np.array([-1.0, 1.0] + [-1.0] * (D - 1) + [-1.0])
+        np.testing.assert_allclose(g, sign * f, rtol=1e-12, atol=1e-14)
+        assert abs(ws + vs) < 1e-13
+    # HLLE is upwind for supersonic flow (its lower bound is 0); local Lax-Friedrichs is not
+    WL, WR = [1.0, 1.0, 5.0, 0.3], [0.5, 0.2, 4.0, -0.2]
+    f, _ = oracle.gas_flux(solver, 2, gam, WL, WR)
+    if solver == "hlle":
+        np.testing.assert_allclose(f, euler_flux(2, gam, WL), rtol=1e-14)
+    else:
+        assert np.max(np.abs(f - euler_flux(2, gam, WL))) > 1e-3
+
+
+def test_alternative_solvers_converge_and_hllc_is_least_diffusive():
+    # Sec. 5.2: HLLC, with the most complete wave structure, is the least diffusive of the three;
+    # all three converge to the exact Riemann solution (Toro ch. 4) of the Sod problem, and only
+    # HLLC keeps a stationary contact exactly
+    errs = {}
+    for solver in ("hllc", "hlle", "llf"):
+        e = []
+        for n in (64, 128, 256):
+            pb = hydro_problem(n)
+            pb.riemann = solver
+            x = (np.arange(n) + 0.5) / n
+            s = gas_state(pb, np.where(x < 0.5, 1.0, 0.125), np.zeros(n), np.where(x < 0.5, 1.0, 0.1))
+            dt = 0.4 / n / 2.0
+            nsteps = int(round(0.2 / dt))
+            out, st = oracle.run(pb, s, 0.2 / nsteps, nsteps)
+            exact = exact_riemann.cell_averages(np.linspace(0, 1, n + 1), 0.2, 0.5, (1.0, 0.0, 1.0),
+                                                (0.125, 0.0, 0.1), 1.4)
+            e.append(np.mean(np.abs(out[:n] - exact[0])))
+        errs[solver] = np.array(e)
+        assert np.all(np.log2(errs[solver][:-1] / errs[solver][1:]) > 0.6), (solver, errs[solver])
+    assert np.all(errs["hllc"] < errs["hlle"]) and np.all(errs["hlle"] < errs["llf"]), errs
+    WL, WR = [1.0, 0.7, 0.0, 0.2], [0.1, 0.7, 0.0, -0.4]
+    for solver in ("hlle", "llf"):
+        f, _ = oracle.gas_flux(solver, 2, 5.0 / 3.0, WL, WR)
+        assert abs(f[0]) > 1e-3  # mass diffuses across the contact
+
+
+def test_carbuncle_guard_switches_only_the_transverse_faces_of_shocked_cells():
+    # reading R22: with a pressure jump across the x face between columns 5 and 6 only, the
+    # cells of those two columns are in the shock; their y faces take HLLE, every x face keeps
+    # HLLC.  rhs(guard) - rhs(no guard) is therefore non-zero in columns 5 and 6 and zero
+    # elsewhere (y faces join cells of one column; the radiation's v* is HLLC's either way)
+    nx, ny = 12, 10
+    pb = W.Problem(name="guard", dims=2, n=(nx, ny, 1), x_lo=(0, 0, 0), x_hi=(1, 1, 1),
+                   bc_lo=("outflow", "periodic", "periodic"), bc_hi=("outflow", "periodic", "periodic"),
+                   ngroups=2, gamma=1.4, kappa0=1.0, kap_rho_exp=0.0, kap_T_exp=0.0, kap_eps_exp=0.0,
+                   c_light=30.0, couple=0)
+    y, x = np.divmod(np.arange(pb.ncell), nx)
+    rho = 1.0 + 0.1 * np.sin(2 * np.pi * (y + 0.5) / ny)
+    p = np.where(x < 6, 1.0, 10.0)
+    vy = 0.3 * np.cos(2 * np.pi * (y + 0.5) / ny)
+    s = gas_state(pb, rho, np.zeros(pb.ncell), p, v=vy)
+    N = pb.ncell
+    s[4 * N: 4 * N + N * 2] = 0.3
+    L0 = oracle.rhs(pb, s)
+    pb.shock_guard = 1.0
+    L1 = oracle.rhs(pb, s)
+    diff = np.abs(L1 - L0)[: 4 * N].reshape(4, ny, nx).max(axis=(0, 1))
+    assert np.all(diff[[5, 6]] > 1e-6), diff
+    assert np.all(np.delete(diff, [5, 6]) == 0.0), diff
+    assert np.all(L1[4 * N:] == L0[4 * N:])
+    pb.shock_guard = 20.0  # above the jump: nothing is tagged
+    np.testing.assert_array_equal(oracle.rhs(pb, s), L0)
+
+
+def test_carbuncle_guard_suppresses_odd_even_decoupling():
+    # Sec. 5.2: three-wave solvers are prone to the carbuncle / odd-even instability, and the
+    # shock tag with HLLE on the transverse faces prevents it.  A Mach-6 planar shock runs along
+    # a periodic channel whose centre row carries an odd-even density perturbation of 1e-3
+    # (Quirk's test): with plain HLLC the transverse velocity grows to O(0.1); with the guard it
+    # stays at the level of HLLE everywhere.
+    nx, ny, g = 160, 24, 1.4
+
+    def run(guard, solver="hllc"):
+        pb = W.Problem(name="quirk", dims=2, n=(nx, ny, 1), x_lo=(0, 0, 0), x_hi=(nx / ny, 1, 1),
+                       bc_lo=("outflow", "periodic", "periodic"), bc_hi=("outflow", "periodic", "periodic"),
+                       ngroups=0, gamma=g, kappa0=0.0, kap_rho_exp=0.0, kap_T_exp=0.0,
+                       kap_eps_exp=0.0, c_light=1.0, couple=0)
+        pb.shock_guard, pb.riemann = guard, solver
+        y, x = np.divmod(np.arange(pb.ncell), nx)
+        M = 6.0
+        r2 = (g + 1) * M ** 2 / ((g - 1) * M ** 2 + 2)      # Rankine-Hugoniot post-shock state of a
+        p2 = (2 * g * M ** 2 - (g - 1)) / (g + 1)           # Mach-M shock into rho = p = 1, u = 0
+        u2 = M * math.sqrt(g) * (1 - 1 / r2)
+        rho = np.where(x < 10, r2, 1.0)
+        mid = y == ny // 2
+        rho[mid] *= 1 + 1e-3 * (2 * (x[mid] % 2) - 1)
+        s = gas_state(pb, rho, np.where(x < 10, u2, 0.0), np.where(x < 10, p2, 1.0), v=np.zeros(pb.ncell))
+        dt = 0.3 / ny / (u2 + math.sqrt(g * p2 / r2))
+        out, st = oracle.run(pb, s, dt, 400, nthreads=8)
+        assert st == 0
+        return np.max(np.abs(out[2 * pb.ncell: 3 * pb.ncell] / out[: pb.ncell]))
+
+    plain, guarded, hlle = run(0.0), run(1.0), run(0.0, "hlle")
+    assert plain > 1e-2 and guarded < 1e-4 and hlle < 1e-4, (plain, guarded, hlle)
