@@ -455,3 +455,21 @@ def test_carbuncle_guard_on_the_gpu(fxmod):
             # (the transverse momentum is perturbation-sized: measured against sqrt(rho rho e))
             H.assert_parity(pb, got, ref, FP64_L1, natural=True)
     assert vy[0.0] > 1e-2 and vy[1.0] < 1e-4, vy
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32n64"])
+def test_scattering_matches_the_oracle(fxmod, precision):
+    # scattering sigma = sigma0 rho in the flux absorption (Eq. 28) and the optical depth of the
+    # HLL correction (R9), beside absorption, on the shear layer with a flux-carrying state
+    pb, prim = W.kh_2d(nx=40, ny=36, ngroups=8, nsteps=3, precision=precision)
+    pb.sigma0 = 25.0
+    got, st, _ = run_gpu(fxmod, pb, prim)
+    ref, rst = run_oracle(pb, prim)
+    assert st == 0 and rst == 0
+    if precision == "fp64":
+        H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
+    else:
+        H.assert_parity(pb, got, ref, 1e-4, natural=True)
+    pb.sigma0 = 0.0
+    plain, _, _ = run_gpu(fxmod, pb, prim)
+    assert np.max(np.abs(plain - got)) > 1e-6 * np.max(np.abs(got))  # sigma changes the result

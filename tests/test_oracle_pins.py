@@ -943,3 +943,58 @@ def test_carbuncle_guard_suppresses_odd_even_decoupling():
 
     plain, guarded, hlle = run(0.0), run(1.0), run(0.0, "hlle")
     assert plain > 1e-2 and guarded < 1e-4 and hlle < 1e-4, (plain, guarded, hlle)
+
+
+# ------------------------------------------------------------------ scattering (Sec. 3.2, Eq. 28)
+def test_scattering_damps_the_flux_only():
+    # kappa = 0, sigma = sigma0 rho: the interaction leaves E and the gas energy exchange at zero
+    # and damps F by 1/(1 + c dt sigma) (Eq. 28); the gas momentum takes the difference / c^2
+    # (Eq. 31); the energy feedback is the work v . dF / c^2 (Eq. 32)
+    pb = W.Problem(name="scat", dims=1, n=(4, 1, 1), x_lo=(0, 0, 0), x_hi=(1, 1, 1),
+                   bc_lo=("periodic",) * 3, bc_hi=("periodic",) * 3, ngroups=3, gamma=5 / 3,
+                   kappa0=0.0, kap_rho_exp=0.0, kap_T_exp=0.0, kap_eps_exp=0.0, sigma0=7.0,
+                   c_light=10.0)
+    s = W.random_state(pb, seed=3, flux_frac=0.6)
+    dt = 0.01
+    out, st = oracle.couple(pb, s, dt)
+    assert st == 0
+    g0, r0 = oracle.split_state(pb, s)
+    g1, r1 = oracle.split_state(pb, out)
+    np.testing.assert_array_equal(r1[0], r0[0])
+    fac = 1.0 / (1.0 + pb.c_light * dt * pb.sigma0 * g0[0])
+    np.testing.assert_allclose(r1[1], r0[1] * fac[:, None], rtol=1e-15)
+    dF = (r1[1] - r0[1]).sum(1)
+    np.testing.assert_allclose(g1[1], g0[1] - dF / pb.c_light ** 2, rtol=1e-15)
+    np.testing.assert_allclose(g1[2], g0[2] - g0[1] / g0[0] * dF / pb.c_light ** 2, rtol=1e-14)
+
+
+def test_scattering_diffusion_limit_and_depth():
+    # a thick scattering medium (kappa = 0): the operator-split flux update tends to Fick's law
+    # F = -c/(3 sigma) dE/dx (Sec. 5.3), and the HLL correction eps = 1/tau counts sigma in the
+    # optical depth (R9)
+    n = 256
+    pb = W.Problem(name="fick_s", dims=1, n=(n, 1, 1), x_lo=(0, 0, 0), x_hi=(1, 1, 1),
+                   bc_lo=("periodic",) * 3, bc_hi=("periodic",) * 3, ngroups=1, gamma=5 / 3,
+                   kappa0=0.0, kap_rho_exp=0.0, kap_T_exp=0.0, kap_eps_exp=0.0, sigma0=1e6,
+                   eps_min=1e-7, eps_max=2e3, c_light=10.0, couple=1)
+    x = (np.arange(n) + 0.5) / n
+    faces = np.linspace(0, 1, n + 1)
+    amp = 0.05
+    Eavg = 0.1 * (1 + amp * (np.sin(2 * np.pi * faces[1:]) - np.sin(2 * np.pi * faces[:-1])) * n / (2 * np.pi))
+    s = np.zeros(pb.state_size())
+    s[:n] = 1.0
+    s[2 * n: 3 * n] = 1.0
+    s[3 * n: 4 * n] = Eavg
+    dt = 0.2 / n / pb.c_light
+    s1 = s + dt * oracle.rhs(pb, s)
+    out, st = oracle.couple(pb, s1, dt)
+    F = out[4 * n:]
+    fick = -pb.c_light / (3 * pb.sigma0) * (-0.1 * amp * 2 * np.pi * np.sin(2 * np.pi * x))
+    assert np.sum(np.abs(F - fick)) <= 0.003 * np.sum(np.abs(fick))
+    # eps = 1/tau with tau = sigma dx: the energy flux's dissipation scales by sigma
+    def dEdt(sig):
+        q = W.Problem(**{**pb.__dict__, "sigma0": sig, "couple": 0})
+        t = np.array(s)
+        t[3 * n: 4 * n] = np.where(np.arange(n) < n // 2, 1.0, 0.5)
+        return oracle.rhs(q, t)[3 * n: 4 * n]
+    np.testing.assert_allclose(dEdt(4 * n), dEdt(0.5 * n) / 4.0, rtol=1e-14, atol=1e-14)
