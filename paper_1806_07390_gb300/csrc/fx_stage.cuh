@@ -1017,14 +1017,14 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         recon_rad_v(mc_coef(ty, bc_pad(gy)), ty, bc_pad(gy), Qa3, Q0, Qb3, ay, by);
 #pragma unroll
         for (int v = 0; v < NRV; ++v) stv(&rby[(v * NFY + (ly + 1) * TX + lx) * GS + g0], by[v]);
-        if (ly == 0) {
+        if (NGL == 1 && ly == 0) {  // (two groups per lane: after this block, one group per lane)
           V Qc[NRV], ta[NRV], tb[NRV];
           rad_v(s0, sc_own - 2 * PX, Qc);
           recon_rad_v(mc_coef(ty, bc_pad(gy - 1)), ty, bc_pad(gy - 1), Qc, Qa3, Q0, ta, tb);
 #pragma unroll
           for (int v = 0; v < NRV; ++v) stv(&rby[(v * NFY + lx) * GS + g0], tb[v]);
         }
-        if (ly == TY - 1) {
+        if (NGL == 1 && ly == TY - 1) {
           V Qc[NRV], ta[NRV], tb[NRV];
           rad_v(s0, sc_own + 2 * PX, Qc);
           recon_rad_v(mc_coef(ty, bc_pad(gy + 1)), ty, bc_pad(gy + 1), Q0, Qb3, Qc, ta, tb);
@@ -1067,6 +1067,36 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * GS + h] = ta[v];
       }
     }
+    // 3-d, two groups per lane: likewise the y halo rows -1 (the upper-face state of each column's
+    // cell -1, left state of its y face 0) and TY (the lower-face state of cell TY, right state of
+    // face TY), one group per lane of the NGL rows nearest each y edge, so that the edge rows' warps
+    // do not carry the whole halo work alone
+    if (D == 3 && NGL > 1 && ly < NGL) {
+      const int h = ly * GL + lane;
+      if (h < G) {
+        const int sc0 = scell(lx, 0);
+        R Qc[NRV], Qd[NRV], Qe[NRV], ta[NRV], tb[NRV];
+        rad_cell(s0, sc0 - 2 * PX, h, Qc);
+        rad_cell(s0, sc0 - PX, h, Qd);
+        rad_cell(s0, sc0, h, Qe);
+        recon_rad(mc_coef(ty, bc_pad(y0 - 1)), ty, bc_pad(y0 - 1), Qc, Qd, Qe, ta, tb);
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rby[(v * NFY + lx) * GS + h] = tb[v];
+      }
+    }
+    if (D == 3 && NGL > 1 && ly >= TY - NGL) {
+      const int h = (ly - (TY - NGL)) * GL + lane;
+      if (h < G) {
+        const int sc1 = scell(lx, TY - 1);
+        R Qc[NRV], Qd[NRV], Qe[NRV], ta[NRV], tb[NRV];
+        rad_cell(s0, sc1, h, Qc);
+        rad_cell(s0, sc1 + PX, h, Qd);
+        rad_cell(s0, sc1 + 2 * PX, h, Qe);
+        recon_rad(mc_coef(ty, bc_pad(y0 + TY)), ty, bc_pad(y0 + TY), Qc, Qd, Qe, ta, tb);
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) ray[(v * TX + lx) * GS + h] = ta[v];
+      }
+    }
     __syncthreads();
     // ---- C: radiation face fluxes
     V rfm_new[NRV];
@@ -1100,7 +1130,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         rad_face_v(1, QL, ay, chi_v(s0, sc_own - PX), chi0, ty(T_ELL, bc_pad(gy)), vsy, out);
 #pragma unroll
         for (int v = 0; v < NRV; ++v) stv(&rfy[(v * NFY + fy) * GS + g0], out[v]);
-        if (ly == TY - 1) {
+        if (NGL == 1 && ly == TY - 1) {
           V QR[NRV];
 #pragma unroll
           for (int v = 0; v < NRV; ++v) QR[v] = ldv(&ray[(v * TX + lx) * GS + g0]);
@@ -1147,6 +1177,31 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         rad_face(0, QL, QR, chiL, chiR, tx(T_ELL, bc_pad(xl) + 1), vsT, out);
 #pragma unroll
         for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fT) * GS + h] = out[v];
+      }
+    }
+    // 3-d, two groups per lane: the y face TY of each column (between the tile's last row and the
+    // halo row TY), one group per lane of the NGL rows nearest the upper y edge (its left state
+    // and flux share their shared-memory slot; only these threads touch it)
+    if (D == 3 && NGL > 1 && ly >= TY - NGL) {
+      const int h = (ly - (TY - NGL)) * GL + lane;
+      if (h < G) {
+        const int fT = TY * TX + lx;        // face TY of column lx
+        const int sc1 = scell(lx, TY - 1);
+        const int yl = y0 + TY - 1;         // the tile's last row
+        R QL[NRV], QR[NRV], out[NRV];
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) {
+          QL[v] = rby[(v * NFY + fT) * GS + h];
+          QR[v] = ray[(v * TX + lx) * GS + h];
+        }
+        const R eh = R(sgc->efac_of(h, R(0)));
+        const R chiL = pk[(s0 * 2) * PC + sc1] * eh + pk[(s0 * 2 + 1) * PC + sc1];
+        const R chiR = pk[(s0 * 2) * PC + sc1 + PX] * eh + pk[(s0 * 2 + 1) * PC + sc1 + PX];
+        const R vsT = (yl < ny && gx < nx) ? gface(1, NG, ((uint32_t)k * (ny + 1) + (uint32_t)(yl + 1)) * nx + gxc)
+                                           : R(0);
+        rad_face(1, QL, QR, chiL, chiR, ty(T_ELL, bc_pad(yl) + 1), vsT, out);
+#pragma unroll
+        for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fT) * GS + h] = out[v];
       }
     }
     if constexpr (D == 2 && NGL > 1) {
