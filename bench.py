@@ -35,12 +35,12 @@ UNIT = "zone-group-stages/s"
 # DRAM bytes per launch (mean of the two RK stages) of the radiation/update kernel and of the
 # interaction kernel, from the committed ncu capture profiles/traffic_kh2d_1024x1024x16.txt; None
 # where not captured for the current kernels.
-TRAFFIC_PER_LAUNCH = {"kh2d": {}}
-TRAFFIC_INTERACTION = {"kh2d": {}}
+TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": 570.7e6}}
+TRAFFIC_INTERACTION = {"kh2d": {"fp32n64": 371.2e6}}
 # FP64 lane operations (DFMA + DADD + DMUL thread instructions) per zone-group of the FP64 form's
 # radiation/update and interaction kernels, from the committed ncu capture
 # profiles/fp64_pipe_kh2d_512x512x16.txt (kh2d recipe at 512 x 512 cells x 16 groups).
-FP64_OPS_PER_ZG = {"kh2d": {"stage": 315.8, "interaction": 217.2}}
+FP64_OPS_PER_ZG = {"kh2d": {"stage": 315.8, "interaction": 217.3}}
 
 
 def load_peaks():
