@@ -44,7 +44,8 @@ class OrcParams(ctypes.Structure):
         ("newton_rtol", ctypes.c_double), ("rho_floor", ctypes.c_double),
         ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double), ("nthreads", ctypes.c_int),
         ("map_rt", ctypes.c_double), ("r10_full_dt", ctypes.c_int), ("riemann", ctypes.c_int),
-        ("shock_guard", ctypes.c_double),
+        ("shock_guard", ctypes.c_double), ("vterms", ctypes.c_int), ("frozen_gas", ctypes.c_int),
+        ("edges", ctypes.c_void_p), ("inflow", ctypes.c_void_p),
     ]
 
 
@@ -83,11 +84,20 @@ def lib():
         L.orc_planck_group.argtypes = [P, ctypes.c_int, ctypes.c_double, _DP, _DP]
         L.orc_geometry.argtypes = [P, ctypes.c_int, _DP, _DP, _DP]
         L.orc_christoffel.argtypes = [P, _DP, _DP, _DP, _DP, _DP]
+        L.orc_vterms.argtypes = [P, _DP, _DP, _DP]
+        L.orc_vterms.restype = ctypes.c_double
+        L.orc_vgrad.argtypes = [P, _DP, _DP]
         _lib = L
     return _lib
 
 
-def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0, r10_full_dt: int = 0) -> OrcParams:
+def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0, r10_full_dt: int = 0,
+           edges=None, inflow=None, frozen_gas: int = 0) -> OrcParams:
+    """Oracle parameters of a problem.  edges (G + 1 group edges), inflow (E_g then the normal
+    F_g of a radiation inflow through the lower x boundary) and frozen_gas are the oracle-only
+    test aids of reading R28."""
+    if pb.vterms and pb.geom != "cart":
+        raise ValueError("the velocity-dependent terms are built for Cartesian grids only")
     P = OrcParams()
     P.dims = pb.dims
     for d in range(3):
@@ -111,6 +121,21 @@ def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0, r10_full_dt: int
     P.r10_full_dt = r10_full_dt
     P.riemann = RIEMANN_CODES[pb.riemann]
     P.shock_guard = pb.shock_guard
+    P.vterms = pb.vterms
+    P.frozen_gas = frozen_gas
+    keep = []
+    if edges is not None:
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        assert e.shape == (pb.ngroups + 1,)
+        keep.append(e)
+        P.edges = e.ctypes.data
+    if inflow is not None:
+        f = np.ascontiguousarray(inflow, dtype=np.float64)
+        assert f.shape == (2 * pb.ngroups,)
+        keep.append(f)
+        P.inflow = f.ctypes.data
+        P.bc_lo[0] = 4  # ORC_INFLOW
+    P._keep = keep  # the arrays must outlive the calls that read P
     return P
 
 
@@ -138,11 +163,11 @@ def run(pb: Problem, state: np.ndarray, dt: float, nsteps: int, nthreads: int = 
 def run_budget(pb: Problem, state: np.ndarray, dt: float, nsteps: int, nthreads: int = 1):
     """orc_run with the budget terms of reading R13: returns (state, status, budget) with budget =
     boundary outflows [mass, momentum 1..3 (incl. radiation / c^2), total energy, radiation
-    energy], the coupling work and the energy the positivity floor of E_g added, accumulated over
-    the steps."""
+    energy], the coupling work, the energy the positivity floor of E_g added and the radiation
+    energy the velocity-dependent terms added, accumulated over the steps."""
     P = params(pb, nthreads=nthreads)
     out = np.array(state, dtype=np.float64, copy=True)
-    bud = np.zeros(8)
+    bud = np.zeros(9)
     st = lib().orc_run_budget(ctypes.byref(P), _ptr(out), dt, nsteps, _ptr(bud))
     return out, st, bud
 
@@ -266,3 +291,26 @@ def split_state(pb: Problem, state: np.ndarray):
     gas = state[: NG * pb.ncell].reshape(NG, pb.ncell)
     rad = state[NG * pb.ncell:].reshape(1 + pb.dims, pb.ncell, pb.ngroups)
     return gas, rad
+
+
+def vterms(pb: Problem, V, rad, edges=None) -> tuple[np.ndarray, float]:
+    """Velocity-dependent radiation terms of one cell (readings R23-R27): V = <v^i_;j> (D x D),
+    rad = [G, 1 + D] (E_g, physical F_g).  Returns (their time derivatives [G, 1 + D],
+    sum_g dE_g/dt)."""
+    P = params(pb, edges=edges)
+    Vm = np.zeros((3, 3))
+    Va = np.asarray(V, dtype=np.float64)
+    Vm[: Va.shape[0], : Va.shape[1]] = Va
+    r = np.ascontiguousarray(rad, dtype=np.float64)
+    out = np.zeros_like(r)
+    s = lib().orc_vterms(ctypes.byref(P), _ptr(np.ascontiguousarray(Vm.ravel())), _ptr(r), _ptr(out))
+    return out, s
+
+
+def vgrad(pb: Problem, state: np.ndarray) -> np.ndarray:
+    """<v^i_;j> of every cell (readings R24-R25), [ncell, 3, 3] in x-fastest cell order."""
+    P = params(pb)
+    s = np.ascontiguousarray(state, dtype=np.float64)
+    out = np.zeros((pb.ncell, 3, 3))
+    lib().orc_vgrad(ctypes.byref(P), _ptr(s), _ptr(out.reshape(-1)))
+    return out

@@ -17,11 +17,13 @@
 //   * SSP-RK2 (Shu & Osher 1988)          -- Sec. 4
 //   * energy coupling (BE + Newton on T)  -- Sec. 5.3, Eqs. 24-27
 //   * momentum coupling (BE flux update)  -- Sec. 5.3, Eqs. 28, 31-32
+//   * velocity-dependent radiation terms -- Sec. 3.2 (group form of the moment equations),
+//     Sec. 5.2 (<v^i_;j> from the face velocities, upwind frequency fluxes), Step 2 of Sec. 6
 //   * conserved totals (compensated sums)
 //   * the objective J: RK-weighted radiation energy leaving through the upper x boundary (R19),
 //     with its tangent (initial-state and kappa0 directions) through the dual-number instantiation
 //
-// Readings where the paper is silent or ambiguous (numbered R1-R20, the labels the tests use):
+// Readings where the paper is silent or ambiguous (numbered R1-R28, the labels the tests use):
 //   R1 radiation reconstructed linearly with an MC slope limiter in moment form (Sec. 2 says linear).
 //   R2 face-interval monotonicity reset: clamp the face value so that the quadratic through the
 //      two neighbouring centroids and the face is monotone (zero slope at the nearer endpoint).
@@ -48,6 +50,28 @@
 //   R22 carbuncle guard: a face is in a shock when the pressures of its two cells differ by more
 //      than the factor 1 + shock_guard; a face of direction d takes HLLE when one of its two
 //      cells has such a face in a direction other than d.
+//   R23 heat-flux tensor of the M1 field: with f = |F|/(cE), n = F/|F| and q(f) = f (2 + 3 chi)/5,
+//      Q_ijk = cE [(f - q)/2 (n_i d_jk + n_j d_ik + n_k d_ij) + (5q - 3f)/2 n_i n_j n_k].  Its
+//      trace Q_ijj is F_i for every f; it is the exact third moment of the intensity
+//      (cE/4pi)(1 + 3 f.n) to first order in f (Q = (F d + ...)/5) and of a beam at f = 1.
+//   R24 face velocity vector: normal component v* (the HLLC contact speed of R6, with every gas
+//      solver), transverse components those of the reconstructed state on the v* upwind side
+//      (v* >= 0: left), the transverse velocity of the HLLC face state.
+//   R25 <v^i_;j> on Cartesian grids: (v^i at the upper j face - v^i at the lower j face) / dx^j,
+//      the derivative of the linear intracell profile; Gamma = 0.  Curvilinear grids: not built.
+//   R26 frequency fluxes: the spectral density x_g = X_g / dnu_g of each component of P (E
+//      equation) and Q (F equations) is reconstructed linearly in nu about the group midpoint
+//      with the MC limiter of R1 (zero slope in the first and last group), upwinded per component
+//      pair (i, j) on the sign of v^i_;j (v^i_;j < 0: the lower group's upper-edge value); no
+//      flux through the ends of the group range (R14's truncated range).
+//   R27 the velocity terms are explicit, part of each RK stage's operator with the transport
+//      (Sec. 4: the non-stiff terms are evolved together, unsplit): E gets -v^i_;j P^j_i plus the
+//      frequency fluxes of nu P, F_j gets -v^i_;j F_i plus those of nu Q.  Step 1 of Sec. 6 lists
+//      a further -v^i_;k Q^k_ji in the flux equation that the moment equations (Sec. 3.2, and
+//      their group form) do not have; the equations are followed.
+//   R28 test aids for the Doppler-shift test of Sec. 9 (oracle only): explicit group edges, a
+//      lower-x radiation inflow boundary (fixed E_g, F_g in the ghosts, gas as outflow) and a
+//      frozen gas state (the velocity field held fixed, as the test's stated profile is).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -129,7 +153,7 @@ static inline void branch(unsigned site, unsigned outcome) {
 // Parameters (C layout, filled from Python).
 // ---------------------------------------------------------------------------------------------
 extern "C" {
-enum { ORC_OUTFLOW = 0, ORC_PERIODIC = 1, ORC_REFLECT = 2, ORC_AXIS = 3 };
+enum { ORC_OUTFLOW = 0, ORC_PERIODIC = 1, ORC_REFLECT = 2, ORC_AXIS = 3, ORC_INFLOW = 4 };
 enum { ORC_CART = 0, ORC_SPH = 1 };
 enum { ORC_MAP_ID = 0, ORC_MAP_EXP = 1, ORC_MAP_SINH = 2 };
 enum { ORC_HLLC = 0, ORC_HLLE = 1, ORC_LLF = 2 };
@@ -157,6 +181,11 @@ struct orc_params {
                             // the inconsistent alternative to reading R10 (the R10 pin must fail it)
   int riemann;              // gas Riemann solver: ORC_HLLC (default), ORC_HLLE or ORC_LLF (R21)
   double shock_guard;       // carbuncle guard (R22): pressure-jump threshold; 0 = off
+  int vterms;               // 1: the velocity-dependent radiation terms (R23-R27; Cartesian)
+  int frozen_gas;           // test aid (R28): the gas state is held fixed
+  const double* edges;      // test aid (R28): G + 1 group edges, or null for the log spacing
+  const double* inflow;     // test aid (R28): with bc ORC_INFLOW, the ghosts' E_g (G values) and
+                            // normal F_g (G values)
 };
 }
 
@@ -448,13 +477,20 @@ template <class S> static void fill_ghosts(const orc_params& P, const Layout& L,
             int src;
             bool flip = false;
             if (bc == ORC_PERIODIC) src = side == 0 ? ng + n - 1 - g : ng + g;
-            else if (bc == ORC_OUTFLOW) src = side == 0 ? ng : ng + n - 1;
+            else if (bc == ORC_OUTFLOW || bc == ORC_INFLOW) src = side == 0 ? ng : ng + n - 1;
             else { src = side == 0 ? ng + g : ng + n - 1 - g; flip = true; }
             int cd[3], cs[3];
             cd[d] = dst; cd[o1] = a; cd[o2] = b;
             cs[d] = src; cs[o1] = a; cs[o2] = b;
             size_t id = L.idx(cd[0], cd[1], cd[2]), is = L.idx(cs[0], cs[1], cs[2]);
             for (int v = 0; v < L.NV; ++v) U[id * L.NV + v] = U[is * L.NV + v];
+            if (bc == ORC_INFLOW) {  // fixed radiation (R28): E_g and the normal flux component
+              for (int gg = 0; gg < L.G; ++gg) {
+                S* r = &U[id * L.NV + L.NG + (size_t)gg * L.NRV];
+                r[0] = P.inflow[gg];
+                for (int q = 0; q < L.D; ++q) r[1 + q] = q == d ? S(P.inflow[L.G + gg]) : S(0.0);
+              }
+            }
             if (flip) {
               U[id * L.NV + 1 + d] = -U[id * L.NV + 1 + d];
               for (int gg = 0; gg < L.G; ++gg) {
@@ -763,7 +799,8 @@ static Groups make_groups(const orc_params& P) {
   g.G = P.ngroups;
   g.edge.resize(g.G + 1);
   g.centre.resize(g.G);
-  for (int k = 0; k <= g.G; ++k) g.edge[k] = P.eps_min * std::pow(P.eps_max / P.eps_min, (double)k / g.G);
+  for (int k = 0; k <= g.G; ++k)
+    g.edge[k] = P.edges ? P.edges[k] : P.eps_min * std::pow(P.eps_max / P.eps_min, (double)k / g.G);
   for (int k = 0; k < g.G; ++k) g.centre[k] = std::sqrt(g.edge[k] * g.edge[k + 1]);
   return g;
 }
@@ -782,6 +819,133 @@ template <class S> static void planck_group(const orc_params& P, const Groups& g
   S T3 = T * T * T;
   B = P.a_rad * norm * T3 * T * I;
   dB = P.a_rad * norm * (4.0 * T3 * I + T3 * (planck_edge_weight(a) - planck_edge_weight(b)));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Velocity-dependent radiation terms of one cell (Sec. 3.2, the group form of the moment
+// equations; Sec. 5.2; Step 2 of Sec. 6; R23-R27).  V[i][j] = <v^i_;j>.  In the E equation
+// these are -v^i_;j P^j_gi + v^i_;j [(nu P^j_i)_{g+1/2} - (nu P^j_i)_{g-1/2}], in the F_j
+// equation -v^i_;j F_gi + v^i_;k [(nu Q^k_ji)_{g+1/2} - (nu Q^k_ji)_{g-1/2}].
+// ---------------------------------------------------------------------------------------------
+// Heat-flux factor q = n_i n_j n_k Q_ijk / (cE) of the M1 field (R23).
+template <class S> static S m1_heat_q(S f) { return f * (2.0 + 3.0 * m1_chi(f)) / 5.0; }
+
+// Pressure tensor P_ij (units of E; R7) and heat-flux tensor Q_kji (units of F; R23) of one group
+// from E and the physical flux F (D components); indices run over the D grid directions.
+template <class S> static void m1_moments(int D, double c, S E, const S* F, S Pt[3][3], S Qt[3][3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Pt[i][j] = 0.0;
+      for (int k = 0; k < 3; ++k) Qt[i][j][k] = 0.0;
+    }
+  S F2 = 0.0;
+  for (int q = 0; q < D; ++q) F2 += F[q] * F[q];
+  S Fm = sqrt(F2);
+  if (val(Fm) <= 0.0 || val(E) <= 0.0) {
+    for (int i = 0; i < D; ++i) Pt[i][i] = E / 3.0;
+    return;
+  }
+  S f = Fm / (c * E);
+  if (val(f) > 1.0) f = 1.0;
+  S chi = m1_chi(f), q = m1_heat_q(f);
+  S n[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < D; ++i) n[i] = F[i] / Fm;
+  S a = 0.5 * (1.0 - chi), b = 0.5 * (3.0 * chi - 1.0);
+  S qa = 0.5 * (f - q) * c * E, qb = 0.5 * (5.0 * q - 3.0 * f) * c * E;
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      Pt[i][j] = E * ((i == j ? a : S(0.0)) + b * n[i] * n[j]);
+      for (int k = 0; k < D; ++k)
+        Qt[k][j][i] = qa * ((j == i ? n[k] : S(0.0)) + (k == i ? n[j] : S(0.0)) + (k == j ? n[i] : S(0.0)))
+                    + qb * n[k] * n[j] * n[i];
+    }
+}
+
+// MC slope from the one-sided and centred differences (R1's limiter).
+template <class S> static S mc_limit(S sL, S sR, S sC) {
+  if (val(sL) * val(sR) <= 0.0) return S(0.0);
+  S m = smin(smin(2.0 * fabs(sL), 2.0 * fabs(sR)), fabs(sC));
+  return val(sC) > 0.0 ? m : -m;
+}
+
+// rad: the cell's radiation variables, group by group (E_g, physical F_g1..F_gD); their time
+// derivatives from these terms are added to out (same layout).  Returns sum_g dE_g/dt.
+template <class S>
+static S velocity_terms(const orc_params& P, const Groups& gr, int D, const S V[3][3], const S* rad, S* out) {
+  const int G = gr.G, NRV = 1 + D;
+  const double c = P.c_light;
+  // spectral densities of the components: xp[g][i][j] = P_ij / dnu_g, xq[g][k][j][i] = Q_kji / dnu_g
+  std::vector<S> xp((size_t)G * 9), xq((size_t)G * 27), Pc((size_t)G * 9);
+  std::vector<double> mid(G), dnu(G);
+  for (int g = 0; g < G; ++g) {
+    dnu[g] = gr.edge[g + 1] - gr.edge[g];
+    mid[g] = 0.5 * (gr.edge[g] + gr.edge[g + 1]);
+    S Pt[3][3], Qt[3][3][3];
+    m1_moments(D, c, rad[g * NRV], &rad[g * NRV + 1], Pt, Qt);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        Pc[g * 9 + 3 * i + j] = Pt[i][j];
+        xp[g * 9 + 3 * i + j] = Pt[i][j] / dnu[g];
+        for (int k = 0; k < 3; ++k) xq[g * 27 + 9 * i + 3 * j + k] = Qt[i][j][k] / dnu[g];
+      }
+  }
+  // values at the lower (lo) and upper (hi) edge of each group, per component (R26)
+  auto edges_of = [&](const std::vector<S>& x, int nc, std::vector<S>& lo, std::vector<S>& hi) {
+    lo.assign(x.size(), S(0.0));
+    hi.assign(x.size(), S(0.0));
+    for (int g = 0; g < G; ++g)
+      for (int m = 0; m < nc; ++m) {
+        S sl = 0.0;
+        if (g > 0 && g < G - 1) {
+          S xm = x[(g - 1) * nc + m], x0 = x[g * nc + m], xpp = x[(g + 1) * nc + m];
+          sl = mc_limit((x0 - xm) / (mid[g] - mid[g - 1]), (xpp - x0) / (mid[g + 1] - mid[g]),
+                        (xpp - xm) / (mid[g + 1] - mid[g - 1]));
+        }
+        lo[g * nc + m] = x[g * nc + m] - sl * (mid[g] - gr.edge[g]);
+        hi[g * nc + m] = x[g * nc + m] + sl * (gr.edge[g + 1] - mid[g]);
+      }
+  };
+  std::vector<S> plo, phi, qlo, qhi;
+  edges_of(xp, 9, plo, phi);
+  edges_of(xq, 27, qlo, qhi);
+  // upwind fluxes through the interior group edges e = 1 .. G-1 (zero through edges 0 and G)
+  std::vector<S> fE((size_t)G + 1, S(0.0)), fF(((size_t)G + 1) * 3, S(0.0));
+  for (int e = 1; e < G; ++e) {
+    const double nu = gr.edge[e];
+    S sE = 0.0;
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) {
+        const S v = V[i][j];
+        const S xe = val(v) < 0.0 ? phi[(e - 1) * 9 + 3 * i + j] : plo[e * 9 + 3 * i + j];
+        sE += v * xe;
+      }
+    fE[e] = nu * sE;
+    for (int j = 0; j < D; ++j) {
+      S sF = 0.0;
+      for (int i = 0; i < D; ++i)
+        for (int k = 0; k < D; ++k) {
+          const S v = V[i][k];
+          const S xe = val(v) < 0.0 ? qhi[(e - 1) * 27 + 9 * k + 3 * j + i] : qlo[e * 27 + 9 * k + 3 * j + i];
+          sF += v * xe;
+        }
+      fF[e * 3 + j] = nu * sF;
+    }
+  }
+  S dEsum = 0.0;
+  for (int g = 0; g < G; ++g) {
+    S work = 0.0;
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) work += V[i][j] * Pc[g * 9 + 3 * i + j];
+    S dE = (fE[g + 1] - fE[g]) - work;
+    out[g * NRV] += dE;
+    dEsum += dE;
+    for (int j = 0; j < D; ++j) {
+      S wF = 0.0;
+      for (int i = 0; i < D; ++i) wF += V[i][j] * rad[g * NRV + 1 + i];
+      out[g * NRV + 1 + j] += (fF[(g + 1) * 3 + j] - fF[g * 3 + j]) - wF;
+    }
+  }
+  return dEsum;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -934,7 +1098,7 @@ static int couple_cell(const orc_params& P, const Groups& gr, int D, const doubl
 template <class S>
 static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout& L, const Groups& gr,
                          const std::vector<S>& U, std::vector<S>& dU, S* phi = nullptr,
-                         double* bflux = nullptr) {
+                         double* bflux = nullptr, double* vwork = nullptr, std::vector<S>* vgrad = nullptr) {
   const int D = L.D, G = L.G, NG = L.NG, NRV = L.NRV, NV = L.NV;
   const double c = P.c_light, gam = P.gamma;
   std::fill(dU.begin(), dU.end(), S(0.0));
@@ -992,6 +1156,10 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
             }
           }
   }
+  // velocity vector on the lower face of direction d of each padded cell (R24), for <v^i_;j>
+  std::vector<S> vface[3];
+  if (P.vterms)
+    for (int d = 0; d < D; ++d) vface[d].assign(NC * D, S(0.0));
   // boundary outflow per row of the upper x boundary (R19)
   std::vector<S> phi_row((size_t)L.n[1] * L.n[2], S(0.0));
   // boundary outflow per direction and row (R13), 6 quantities each
@@ -1043,6 +1211,10 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
             if (tr) solver = ORC_HLLE;
           }
           gas_flux(solver, D, gam, WLr, WRr, fl, vstar);
+          if (P.vterms) {  // R24: v* normal, the upwind state's velocity transverse
+            const S* Wu = val(vstar) >= 0.0 ? WLr : WRr;
+            for (int q = 0; q < D; ++q) vface[d][ir * D + (d + q) % D] = q == 0 ? vstar : Wu[2 + q];
+          }
           double Aph, Ah[3], hn;
           face_geometry(P, geo, d, f, cl, Aph, Ah, hn);
           // gas fluxes into covariant components
@@ -1167,6 +1339,41 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
           if (D > 1) dU[o + 2] += g122 * R21 + g221 * R12 + g222 * R22 + g332 * R33;
         }
       }
+  if (P.vterms) {
+    // velocity-dependent radiation terms (R23-R27): <v^i_;j> from the face velocities (R25), then
+    // the work terms and frequency fluxes per cell; vwork = sum_cells V sum_g dE_g/dt of them
+    std::vector<double> wcell;
+    for (int k = L.ng[2]; k < L.ng[2] + L.n[2]; ++k)
+      for (int j = L.ng[1]; j < L.ng[1] + L.n[1]; ++j)
+        for (int i = L.ng[0]; i < L.ng[0] + L.n[0]; ++i) {
+          const size_t id = L.idx(i, j, k);
+          S V[3][3];
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) V[a][b] = 0.0;
+          for (int b = 0; b < D; ++b) {
+            const size_t iu = L.idx(i + (b == 0), j + (b == 1), k + (b == 2));
+            for (int a = 0; a < D; ++a) V[a][b] = (vface[b][iu * D + a] - vface[b][id * D + a]) / geo.dir[b].dx;
+          }
+          if (vgrad)
+            for (int a = 0; a < D; ++a)
+              for (int b = 0; b < D; ++b) (*vgrad)[id * 9 + 3 * a + b] = V[a][b];
+          S de = velocity_terms(P, gr, D, V, &R[id * G * NRV], &dU[id * NV + NG]);
+          const double Vol = geo.dir[0].vol[i] * geo.dir[1].vol[j] * geo.dir[2].vol[k];
+          wcell.push_back(Vol * val(de));
+        }
+    if (vwork) {
+      double sum = 0.0;
+      for (double w : wcell) sum += w;
+      *vwork = sum;
+    }
+  } else if (vwork) {
+    *vwork = 0.0;
+  }
+  if (P.frozen_gas)  // test aid (R28): the gas state does not change
+    for (int k = L.ng[2]; k < L.ng[2] + L.n[2]; ++k)
+      for (int j = L.ng[1]; j < L.ng[1] + L.n[1]; ++j)
+        for (int i = L.ng[0]; i < L.ng[0] + L.n[0]; ++i)
+          for (int v = 0; v < NG; ++v) dU[L.idx(i, j, k) * NV + v] = 0.0;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1217,8 +1424,10 @@ static int couple_all(const Oracle& O, std::vector<S>& U, double dt, double* wor
 // dt (Phi(U^n) + Phi(U^(1)))/2, the same weights the update gives the boundary fluxes.
 // When bud is non-null the step's budget terms are added to it (R13): bud[0..5] the boundary
 // outflows of explicit_rhs weighted as the update weighs them (dt/2 for each stage), bud[6] the
-// coupling work and bud[7] the energy added by the positivity floor of E_g (the stage-1
-// interaction enters U^(n+1) with the weight 1/2 of U^(1), the stage-2 one with weight 1).
+// coupling work, bud[7] the energy added by the positivity floor of E_g (the stage-1
+// interaction enters U^(n+1) with the weight 1/2 of U^(1), the stage-2 one with weight 1) and
+// bud[8] the radiation energy added by the velocity-dependent terms (R27), weighted as the
+// boundary outflows.
 template <class S>
 static int rk2_step(const Oracle& O, std::vector<S>& U, double dt, S* J = nullptr, double* bud = nullptr) {
   const Layout& L = O.L;
@@ -1226,13 +1435,13 @@ static int rk2_step(const Oracle& O, std::vector<S>& U, double dt, S* J = nullpt
   std::vector<S> U0 = U, dU(N), U1(N);
   int status = 0;
   S phi0 = 0.0, phi1 = 0.0;
-  double bf0[6], bf1[6], w1[2] = {0.0, 0.0}, w2[2] = {0.0, 0.0};
+  double bf0[6], bf1[6], w1[2] = {0.0, 0.0}, w2[2] = {0.0, 0.0}, vw0 = 0.0, vw1 = 0.0;
   fill_ghosts(O.P, L, U0);
-  explicit_rhs(O.P, O.geo, L, O.gr, U0, dU, J ? &phi0 : nullptr, bud ? bf0 : nullptr);
+  explicit_rhs(O.P, O.geo, L, O.gr, U0, dU, J ? &phi0 : nullptr, bud ? bf0 : nullptr, bud ? &vw0 : nullptr);
   for (size_t q = 0; q < N; ++q) U1[q] = U0[q] + dt * dU[q];
   if (O.P.couple) status |= couple_all(O, U1, dt, bud ? w1 : nullptr);
   fill_ghosts(O.P, L, U1);
-  explicit_rhs(O.P, O.geo, L, O.gr, U1, dU, J ? &phi1 : nullptr, bud ? bf1 : nullptr);
+  explicit_rhs(O.P, O.geo, L, O.gr, U1, dU, J ? &phi1 : nullptr, bud ? bf1 : nullptr, bud ? &vw1 : nullptr);
   for (size_t q = 0; q < N; ++q) U[q] = 0.5 * U0[q] + 0.5 * (U1[q] + dt * dU[q]);
   if (O.P.couple) status |= couple_all(O, U, O.P.r10_full_dt ? dt : 0.5 * dt, bud ? w2 : nullptr);
   if (J) *J += dt * (0.5 * phi0 + 0.5 * phi1);
@@ -1240,6 +1449,7 @@ static int rk2_step(const Oracle& O, std::vector<S>& U, double dt, S* J = nullpt
     for (int q = 0; q < 6; ++q) bud[q] += 0.5 * dt * bf0[q] + 0.5 * dt * bf1[q];
     bud[6] += 0.5 * w1[0] + w2[0];
     bud[7] += 0.5 * w1[1] + w2[1];
+    bud[8] += 0.5 * dt * vw0 + 0.5 * dt * vw1;
   }
   return status;
 }
@@ -1332,17 +1542,19 @@ int orc_run(const orc_params* P, double* state, double dt, int nsteps) {
   return status;
 }
 
-// Run with budgets (R13): like orc_run, and budget[0..7] receives the boundary outflows of mass,
+// Run with budgets (R13): like orc_run, and budget[0..8] receives the boundary outflows of mass,
 // momentum 1..3 (including radiation momentum / c^2), total energy and radiation energy, the
-// coupling work and the energy added by the positivity floor of E_g, accumulated over the steps,
-// so that for every conserved total T(0) - T(nsteps) = outflow (+ work - floor energy for the
-// total energy).
+// coupling work, the energy added by the positivity floor of E_g and the radiation energy added
+// by the velocity-dependent terms, accumulated over the steps, so that for every conserved total
+// T(0) - T(nsteps) = outflow (+ work - floor energy - velocity-term energy for the total energy).
+// The flux equations' velocity terms change the radiation momentum too; with vterms on, the
+// momentum totals do not close (the comoving-frame equations are not momentum-conservative).
 int orc_run_budget(const orc_params* P, double* state, double dt, int nsteps, double* budget) {
   Oracle O;
   setup(O, P);
   std::vector<double> U;
   unpack(O, state, U, (const double*)nullptr);
-  for (int q = 0; q < 8; ++q) budget[q] = 0.0;
+  for (int q = 0; q < 9; ++q) budget[q] = 0.0;
   int status = 0;
   for (int s = 0; s < nsteps; ++s) status |= rk2_step(O, U, dt, (double*)nullptr, budget);
   pack(O, U, state, (double*)nullptr);
@@ -1489,6 +1701,39 @@ int orc_init_equilibrium(const orc_params* P, const double* prim, double* state)
 }
 
 // ---- unit-level entry points used by the pins ----
+// Velocity-dependent terms of one cell (R23-R27): V = <v^i_;j> row-major (9 values, indices < D
+// used), rad = G groups of (E, physical F_1..F_D); out (same layout) receives their time
+// derivatives.  Returns sum_g dE_g/dt.
+double orc_vterms(const orc_params* P, const double* V, const double* rad, double* out) {
+  Groups gr = make_groups(*P);
+  const int D = P->dims;
+  double Vm[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Vm[a][b] = (a < D && b < D) ? V[3 * a + b] : 0.0;
+  for (int q = 0; q < gr.G * (1 + D); ++q) out[q] = 0.0;
+  return velocity_terms(*P, gr, D, Vm, rad, out);
+}
+// <v^i_;j> of every cell of a state (R24-R25), out[cell][3][3] (x-fastest cells).
+int orc_vgrad(const orc_params* P, const double* state, double* out) {
+  Oracle O;
+  setup(O, P);
+  O.P.vterms = 1;
+  std::vector<double> U, dU, vg;
+  unpack(O, state, U, (const double*)nullptr);
+  dU.assign(U.size(), 0.0);
+  vg.assign(O.L.ncell_p * 9, 0.0);
+  fill_ghosts(O.P, O.L, U);
+  explicit_rhs(O.P, O.geo, O.L, O.gr, U, dU, (double*)nullptr, nullptr, nullptr, &vg);
+  const Layout& L = O.L;
+  for (int k = 0; k < L.n[2]; ++k)
+    for (int j = 0; j < L.n[1]; ++j)
+      for (int i = 0; i < L.n[0]; ++i) {
+        const size_t c = ((size_t)k * L.n[1] + j) * L.n[0] + i;
+        const size_t id = L.idx(i + L.ng[0], j + L.ng[1], k + L.ng[2]);
+        for (int q = 0; q < 9; ++q) out[c * 9 + q] = vg[id * 9 + q];
+      }
+  return 0;
+}
 double orc_planck_band(double a, double b) { init_bernoulli(); return planck_band(a, b); }
 double orc_planck_lower(double x) { init_bernoulli(); return planck_lower(x); }
 double orc_planck_upper(double x) { init_bernoulli(); return planck_upper(x); }

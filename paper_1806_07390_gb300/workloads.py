@@ -58,6 +58,7 @@ class Problem:
     rad_recon_order: int = 1
     riemann: str = "hllc"      # gas Riemann solver: "hllc", "hlle" or "llf" (Sec. 5.2)
     shock_guard: float = 0.0   # carbuncle guard pressure-jump threshold (0: off)
+    vterms: int = 0            # 1: velocity-dependent radiation terms (Sec. 3.2, 5.2; Cartesian)
     couple: int = 1
     newton_maxit: int = 50
     bisect_maxit: int = 200
