@@ -369,6 +369,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-vterms", action="store_true",
+                    help="skip the headline form timed with the velocity-dependent terms on")
     ap.add_argument("--shape", default=None,
                     help="cells per direction, comma list (a smaller grid of the same recipe, for "
                          "profiler captures; the default is the workload's full size)")
@@ -402,6 +404,11 @@ def main():
         forms[name] = gen(precision=name)[0]
     zg = pbh.ncell * pbh.ngroups
     peak, peak_kind = load_peaks()
+    # the headline form once more with the velocity-dependent radiation terms (Cartesian grids)
+    pbv = None
+    if not args.no_vterms and pbh.geom == "cart":
+        pbv = gen(precision=head)[0]
+        pbv.vterms = 1
 
     results = {}
     with ClockSampler(dev) as clk:
@@ -410,6 +417,9 @@ def main():
             gf, msf, stf, lf, ktf = time_form(pbf, prim, args.steps, args.warmup, dist)
             results[name] = (msf, stf, lf, ktf)
             gf.close()
+        if pbv is not None:
+            gv, msv, stv, lv, ktv = time_form(pbv, prim, args.steps, args.warmup, dist)
+            gv.close()
     clocks = clk.summary()
 
     sech = msh / 1e3
@@ -487,7 +497,7 @@ def main():
             "roofline": roofline(head, kth),
             "e2e": {"value": world * zg * 2 * e2e_steps / e2e_sec, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launchesh + sum(r[2] for r in results.values()),
+            "gpu_launches": launchesh + sum(r[2] for r in results.values()) + (lv if pbv is not None else 0),
             "clocks": clocks, "status": int(sth), "forms": {}}
     for name, (msf, stf, lf, ktf) in results.items():
         secf = msf / 1e3
@@ -495,6 +505,23 @@ def main():
                                "ms_per_step": msf / args.steps, "note": FORM_NOTE[name],
                                "roofline": roofline(name, ktf), "status": int(stf),
                                "speedup_of_headline": msf / msh}
+    if pbv is not None:
+        # velocity-term kernel: reads the stage input's radiation rows and reads and writes the
+        # stage output's (3 G (1 + D) words per cell per launch); its time is the interval after
+        # the radiation/update kernel less the interaction kernel's time without the terms
+        b = 8 if head == "fp64" else 4
+        vb = 3.0 * b * pbh.ngroups * (1 + pbh.dims) * pbh.ncell
+        per = lambda kt: kt["couple_ms"] / max(kt["couple_launches"], 1)  # noqa: E731
+        vms = per(ktv) - per(kth)
+        line["vterms"] = {
+            "note": "headline form with the velocity-dependent radiation terms (work terms and "
+                    "frequency-space fluxes) in each stage's operator: one more kernel per stage",
+            "value": whole_job_rate(zg * 2 * args.steps, world, msv / 1e3), "unit": UNIT,
+            "ms_per_step": msv / args.steps, "extra_ms_per_step": (msv - msh) / args.steps,
+            "status": int(stv),
+            "kernel": {"name": "vterm_kernel", "avg_launch_ms": vms, "bytes_per_launch": vb,
+                       "achieved": vb / (vms / 1e3) / 1e9 if vms > 0 else None, "unit": "GB/s",
+                       "frac": vb / (vms / 1e3) / 1e9 / peak if vms > 0 else None}}
     if not args.no_adjoint and args.workload == "kh2d":
         line["adjoint"] = time_adjoint()
     if rank == 0 and not args.no_cpu and not dist:

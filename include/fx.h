@@ -49,7 +49,7 @@ enum { FX_CART = 0, FX_SPH = 1 };       /* Cartesian, or spherical (x1 -> r, x2 
 enum { FX_MAP_ID = 0, FX_MAP_EXP = 1, FX_MAP_SINH = 2 };
 enum { FX_FP64 = 0, FX_FP32 = 1, FX_FP32_F64NEWTON = 2 }; /* precision forms (see fx_params)  */
 enum { FX_HLLC = 0, FX_HLLE = 1, FX_LLF = 2 };            /* gas Riemann solvers (Sec. 5.2)   */
-enum { FX_NTOTALS = 6, FX_NBUDGET = 8 };
+enum { FX_NTOTALS = 6, FX_NBUDGET = 9 };
 
 /* Grid, physics and solver parameters (plain data, copied at fx_grid_create).
  *   dims, n[d]         number of dimensions (1..3) and cells per direction (n[d] ignored for
@@ -91,6 +91,15 @@ enum { FX_NTOTALS = 6, FX_NBUDGET = 8 };
  *                      and with FX_HLLC a face of direction d takes HLLE when one of its cells
  *                      has such a face in another direction.  The adjoint needs FX_HLLC without
  *                      the guard (otherwise FX_ERR_UNSUPPORTED).
+ *   vterms             1 = the velocity-dependent radiation terms of the comoving-frame moment
+ *                      equations (Sec. 3.2, their group form; Sec. 5.2; Step 2 of Sec. 6) in
+ *                      each stage's explicit operator: the work terms -v^i_;j P^j_i (energy) and
+ *                      -v^i_;j F_i (flux), and the upwind frequency-space fluxes of nu P and
+ *                      nu Q (Q: the M1 heat-flux tensor, Q_ijk = cE [(f-q)/2 (n_i d_jk + n_j d_ik
+ *                      + n_k d_ij) + (5q-3f)/2 n_i n_j n_k], q = f (2 + 3 chi)/5), with
+ *                      <v^i_;j> from the face velocities (v* normal, the upwind state's
+ *                      transverse components).  Cartesian grids only (FX_ERR_UNSUPPORTED
+ *                      otherwise); the adjoint returns FX_ERR_UNSUPPORTED with it.  0 = off.
  */
 typedef struct {
   int dims;
@@ -112,6 +121,7 @@ typedef struct {
   double map_rt;
   int riemann;
   double shock_guard;
+  int vterms;
 } fx_params;
 
 /* State layout (upload, download, and the device copy inside the workspace): ncell = prod n[d],
@@ -169,10 +179,12 @@ fx_status fx_conserved_totals(fx_grid* h, double out[FX_NTOTALS]);
  *   covariant, meaningful as a budget on Cartesian grids);
  *   out[6] the energy the gas gives up to the flux absorption, sum_cells V (1/c^2) v . sum_g
  *   (F_g^new - F_g^-) (weight 1/2 after stage 1, 1 after stage 2);
- *   out[7] the radiation energy the silent positivity floor of E_g adds (same weights).
+ *   out[7] the radiation energy the silent positivity floor of E_g adds (same weights);
+ *   out[8] the radiation energy the velocity-dependent terms add (vterms; weighted as out[4]).
  * Then, from the totals T of fx_conserved_totals at two times, T_mass(0) - T_mass(n) = out[0],
- * T_mom(0) - T_mom(n) = out[1..3] (Cartesian), T_E(0) - T_E(n) = out[4] + out[6] - out[7], to
- * round-off in FX_FP64 (in the FP32 forms, to the FP32 state's rounding).
+ * T_mom(0) - T_mom(n) = out[1..3] (Cartesian, without vterms: the flux equations' velocity
+ * terms are not momentum-conservative), T_E(0) - T_E(n) = out[4] + out[6] - out[7] - out[8],
+ * to round-off in FX_FP64 (in the FP32 forms, to the FP32 state's rounding).
  * fx_budgets_enable(h, 1) zeroes the accumulators (enqueued on the bound stream) and starts
  * accumulating; fx_budgets_enable(h, 0) stops (the default: the accumulation costs the kernels
  * registers and reductions, and the adjoint passes never add to it).  fx_budgets synchronises
@@ -187,8 +199,8 @@ fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is
 
 /* Number of kernel launches enqueued by one fx_step(dt, 1) call (per RK stage: the gas face
  * kernel, the radiation/update kernel, with the interaction on the interaction kernel, with
- * the carbuncle guard on the shock-flag kernel, and the objective's reduction while it is
- * enabled). */
+ * the carbuncle guard on the shock-flag kernel, with vterms the velocity-term kernel, and the
+ * objective's reduction while it is enabled). */
 int fx_launches_per_step(const fx_grid* h);
 
 /* Planes of the slowest axis that one block of the radiation/update kernel marches over: 32 (or
@@ -200,13 +212,14 @@ int fx_march_chunk(const fx_grid* h);
 /* Per-kernel device timing (instrumentation, not part of the method).  While enabled, every
  * stage that fx_step enqueues records four CUDA events on the bound stream: before the gas face
  * kernel, after it, after the radiation/update kernel, and after the interaction kernel (one
- * thread per cell, in every form; with the interaction off the last two events coincide).
+ * thread per cell, in every form; with the interaction off the last two events coincide; with
+ * vterms the velocity-term kernel runs between the last two events).
  * fx_kernel_timing_enable(h, on) switches this on or off and discards what was recorded.
  * fx_kernel_timing_read(h, out) waits for the last recorded event and writes
  * out[0] = total milliseconds of the radiation/update kernel, out[1] = its launches,
  * out[2] = total milliseconds of the gas face kernel, out[3] = its launches,
- * out[4] = total milliseconds of the interaction kernel, out[5] = its launches (0 with the
- * interaction off), summed over the stages recorded since
+ * out[4] = total milliseconds of the interaction kernel (with vterms, plus the velocity-term
+ * kernel), out[5] = its launches (0 with both off), summed over the stages recorded since
  * enable or the previous read; it then starts a new record.  Each duration includes the launch
  * gap between the bracketing events (~1 us).  Both return FX_ERR_ARG for a null handle or output
  * and FX_ERR_CUDA when an event call fails. */

@@ -16,6 +16,7 @@
 
 #include "../../include/fx.h"
 #include "fx_adjoint.cuh"
+#include "fx_vterms.cuh"
 #include "fx_launch.h"
 
 using namespace fx;
@@ -107,9 +108,10 @@ struct fx_grid {
   int64_t ncell = 0;
   std::vector<double> tab[3];  // [NTAB][n+4] per direction (FP64 master copy)
   GroupConst gc{};
+  VtConst vtc{};
   PlanckParams pk{};
   // workspace layout (byte offsets)
-  size_t ws_bytes = 0, off_status = 0, off_tab[3] = {0, 0, 0}, off_gc = 0, off_A = 0, off_B = 0,
+  size_t ws_bytes = 0, off_status = 0, off_tab[3] = {0, 0, 0}, off_gc = 0, off_vtc = 0, off_A = 0, off_B = 0,
          off_tot = 0;
   size_t state_bytes = 0, elem = 8;
   unsigned char* ws = nullptr;
@@ -122,7 +124,7 @@ struct fx_grid {
   int ptab_nu = 0;
   float ptab_u0 = 0.0f;
   size_t off_ptab = 0;
-  size_t off_faces = 0;           // gas face buffer [dir][NG+1][faces of dir]
+  size_t off_faces = 0;           // gas face buffer [dir][NG+1 (+D-1 with vterms)][faces of dir]
   size_t off_opk = 0;             // opacity factors of the stage input [K, S][cells]
   size_t off_sflag = 0;           // shock flags of the stage input [cells] (carbuncle guard)
   int64_t face_off[3] = {0, 0, 0};
@@ -615,6 +617,7 @@ StageArgs<R> stage_args(fx_grid* h) {
   a.g = h->dg;
   for (int d = 0; d < 3; ++d) a.tab[d] = dev_tab<R>(h, d < h->D ? d : 0);
   a.gc = reinterpret_cast<const GroupConst*>(h->ws + h->off_gc);
+  a.vtc = reinterpret_cast<const VtConst*>(h->ws + h->off_vtc);
   a.faces = reinterpret_cast<const R*>(h->ws + h->off_faces);
   a.faces_out = reinterpret_cast<R*>(h->ws + h->off_faces);
   a.opk = reinterpret_cast<R*>(h->ws + h->off_opk);
@@ -958,6 +961,8 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
     return FX_ERR_ARG;
   if (P.rad_recon_order != 1 && P.rad_recon_order != 2) return FX_ERR_ARG;
   if (P.riemann < FX_HLLC || P.riemann > FX_LLF || !(P.shock_guard >= 0.0)) return FX_ERR_ARG;
+  if (P.vterms != 0 && P.vterms != 1) return FX_ERR_ARG;
+  if (P.vterms && P.geom != FX_CART) return FX_ERR_UNSUPPORTED;  // built for Cartesian grids
   if (!(P.gamma > 1.0) || !(P.c_light > 0.0) || !(P.a_rad > 0.0)) return FX_ERR_ARG;
   if (!half_integer(P.kap_rho_exp) || !half_integer(P.kap_T_exp)) return FX_ERR_UNSUPPORTED;
   if (!(P.eps_min > 0.0) || !(P.eps_max > P.eps_min)) return FX_ERR_ARG;
@@ -1017,6 +1022,9 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   g.couple = P.couple;
   g.riemann = P.riemann;
   g.shock_guard = P.shock_guard;
+  g.vterms = P.vterms;
+  for (int d = 0; d < 3; ++d)
+    g.inv_dx[d] = d < P.dims ? (double)P.n[d] / (P.x_hi[d] - P.x_lo[d]) : 1.0;
 
   for (int d = 0; d < P.dims; ++d) build_table(P, d, h->tab[d]);
   for (int j = 0; j <= h->G; ++j)
@@ -1024,6 +1032,7 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   for (int j = 0; j < h->G; ++j)
     h->gc.efac[j] = std::pow(std::sqrt(h->gc.edge[j] * h->gc.edge[j + 1]), P.kap_eps_exp);
   for (int j = 0; j <= MAXG; ++j) h->gc.edge32[j] = (float)h->gc.edge[j];
+  vt_constants(h->gc.edge, h->G, h->vtc);
   for (int j = 0; j < MAXG; ++j) h->gc.efac32[j] = (float)h->gc.efac[j];
   planck_coefficients(h->pk);
   {
@@ -1042,12 +1051,14 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   h->off_status = off; off = align_up(off + 64);
   for (int d = 0; d < P.dims; ++d) { h->off_tab[d] = off; off = align_up(off + h->tab[d].size() * h->elem); }
   h->off_gc = off; off = align_up(off + sizeof(GroupConst));
+  h->off_vtc = off; off = align_up(off + sizeof(VtConst));
   h->off_ptab = off; off = align_up(off + h->ptab.size() * sizeof(float4));
   {
     int64_t fo = 0;
     for (int d = 0; d < P.dims; ++d) {
       h->face_off[d] = fo;
-      fo += (int64_t)(2 + P.dims + 1) * faces_along(g.n, d);
+      // fluxes and v*, then (velocity terms on) the D - 1 transverse face velocities
+      fo += (int64_t)(2 + P.dims + 1 + (P.vterms ? P.dims - 1 : 0)) * faces_along(g.n, d);
     }
     h->off_faces = off;
     off = align_up(off + (size_t)fo * h->elem);
@@ -1118,7 +1129,8 @@ fx_status fx_budgets(fx_grid* h, double out[FX_NBUDGET]) {
 int fx_launches_per_step(const fx_grid* h) {
   if (!h) return 0;
   const bool split = h->P.couple != 0;  // the interaction kernel runs in every form
-  return 2 * (2 + (split ? 1 : 0) + (h->objective ? 1 : 0) + (h->P.shock_guard > 0.0 ? 1 : 0));
+  return 2 * (2 + (split ? 1 : 0) + (h->objective ? 1 : 0) + (h->P.shock_guard > 0.0 ? 1 : 0) +
+              (h->P.vterms ? 1 : 0));
 }
 
 fx_status fx_objective_enable(fx_grid* h, int on) {
@@ -1165,6 +1177,8 @@ static fx_status adjoint_entry(fx_grid* h, double dt, int nsteps, int k, void* a
     return fail(h, FX_ERR_UNSUPPORTED, "the adjoint supports the linear radiation reconstruction");
   if (h->P.riemann != FX_HLLC || h->P.shock_guard > 0.0)
     return fail(h, FX_ERR_UNSUPPORTED, "the adjoint supports HLLC without the carbuncle guard");
+  if (h->P.vterms)
+    return fail(h, FX_ERR_UNSUPPORTED, "the adjoint does not include the velocity-dependent terms");
   if (!adj_ws || adj_bytes < adj_layout(h, nsteps, k).bytes || (reinterpret_cast<uintptr_t>(adj_ws) % kAlign) != 0)
     return fail(h, FX_ERR_WORKSPACE, "adjoint workspace missing, too small or not 256-byte aligned");
   unsigned char* ws = static_cast<unsigned char*>(adj_ws);
@@ -1317,6 +1331,8 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "Planck table upload");
   e = cudaMemcpyAsync(h->ws + h->off_gc, &h->gc, sizeof(GroupConst), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + h->off_vtc, &h->vtc, sizeof(VtConst), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "group constants upload");
   return FX_OK;
@@ -1491,7 +1507,8 @@ fx_status fx_kernel_timing_read(fx_grid* h, double out[6]) {
   if (h->nev == 0) return FX_OK;
   cudaError_t e = cudaEventSynchronize(h->ev[h->nev - 1]);
   if (e != cudaSuccess) return cuda_fail(h, e, "timing read");
-  const bool split = h->P.couple != 0;  // the interaction kernel runs in every form
+  // the interval after the radiation/update kernel holds the velocity-term and interaction kernels
+  const bool split = h->P.couple != 0 || h->P.vterms != 0;
   for (size_t i = 0; i < h->nev; i += 4) {
     float face = 0.f, stage = 0.f, inter = 0.f;
     e = cudaEventElapsedTime(&face, h->ev[i], h->ev[i + 1]);

@@ -5,7 +5,8 @@
 // cell once, for both of its faces.  It also forms every cell's opacity factors.
 // The stage kernel then uses the fluxes for the gas divergence, the contact speeds to upwind the
 // radiation advection (Eq. 19), and the opacity factors for the ε correction of the radiation
-// fluxes.
+// fluxes; with the velocity-dependent radiation terms on, the kernel also stores each face's
+// transverse velocity for their velocity gradient (fx_vterms.cuh).
 #pragma once
 #include "fx_device.cuh"
 
@@ -170,6 +171,13 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
   for (int c = 0; c < D; ++c) out[(uint32_t)(1 + (DIR + c) % D) * nf + uf] = fl[1 + c];
   out[(uint32_t)(NG - 1) * nf + uf] = fl[1 + D];
   out[(uint32_t)NG * nf + uf] = vs;
+  if (g.vterms) {
+    // face velocity vector for the velocity-dependent radiation terms: v* normal, the transverse
+    // components of the state on the v* upwind side (rotated order, rows NG + 1 .. NG + D - 1)
+    const R* up = vs >= R(0) ? Lr : Rr;
+#pragma unroll
+    for (int c = 1; c < D; ++c) out[(uint32_t)(NG + c) * nf + uf] = up[2 + c];
+  }
 }
 
 // Carbuncle guard (Sec. 5.2; reading R22): for every cell of the stage input, bit e of sflag is

@@ -6,6 +6,7 @@
 #include "fx_couple.cuh"
 #include "fx_couple64.cuh"
 #include "fx_stage.cuh"
+#include "fx_vterms.cuh"
 
 namespace fx {
 
@@ -38,8 +39,9 @@ template <int D, int GL, int NGL> struct TileShape {
 };
 
 // Enqueue one stage (state type R, D dimensions, Newton/bookkeeping type NT; SPH: the 2-d
-// spherical grid) on stream s: the gas face kernel, the radiation/update kernel and, with the
-// interaction on, the interaction kernel (one thread per cell).  When non-null, `mid` is recorded after the
+// spherical grid) on stream s: the gas face kernel, the radiation/update kernel, with the
+// velocity-dependent terms on the velocity-term kernel, and with the interaction on the
+// interaction kernel (one thread per cell).  When non-null, `mid` is recorded after the
 // face kernel and `mid2` after the radiation/update kernel (per-kernel timing).  Returns the CUDA
 // error of the launches.
 template <class R, int D, class NT, bool SPH>
@@ -118,6 +120,15 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
   if (e != cudaSuccess) return e;
   if (mid2) {
     e = cudaEventRecord(mid2, s);
+    if (e != cudaSuccess) return e;
+  }
+  // the velocity-dependent radiation terms of the stage input, added to the explicit update
+  // before the interaction (one thread per cell)
+  if (a.g.vterms) {
+    constexpr int CPB = VT_THREADS / GP;  // cells of one x row per block, GP lanes each
+    const dim3 vg((unsigned)(a.g.n[1] * a.g.n[2]), (unsigned)((a.g.n[0] + CPB - 1) / CPB), 1);
+    vterm_kernel<R, D, GP><<<vg, VT_THREADS, 0, s>>>(a);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   // the interaction, one thread per cell (FP32 state: couple_kernel; FP64 state: couple64_kernel)

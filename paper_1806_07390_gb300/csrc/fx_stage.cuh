@@ -60,10 +60,13 @@ struct PlanckTable {
   int si, sg;
 };
 
+struct VtConst;  // frequency constants of the velocity-dependent terms (fx_vterms.cuh)
+
 template <class R> struct StageArgs {
   DevGrid g;
   PlanckTable ptab;
-  const R* faces;      // gas face fluxes and contact speeds [dir][NG+1][faces of dir]
+  const R* faces;      // gas face fluxes and contact speeds [dir][NG+1][faces of dir], then, with
+                       // the velocity terms on, D-1 rows of transverse face velocities
   R* faces_out;        // the same buffer, written by gas_face_kernel
   R* opk;              // opacity factors K = kappa0 rho^a T^b, S = sigma0 rho of every cell of the
                        // stage input [2][ncell]: gas_face_kernel writes, stage_kernel reads
@@ -77,6 +80,7 @@ template <class R> struct StageArgs {
   R* out;              // result (may alias neither input)
   const R* tab[3];     // per-direction reconstruction/divergence tables [NTAB][n_d + 4]
   const GroupConst* gc;
+  const VtConst* vtc;  // per-group constants of the velocity-dependent terms
   PlanckParams pk;
   unsigned* status;
   double dt;           // stage step
@@ -94,7 +98,8 @@ template <class R> struct StageArgs {
   // Budgets (reading R13; null when not accumulated): [0] mass, [1..3] momentum (with the
   // radiation momentum / c^2), [4] total energy and [5] radiation energy that leave through the
   // non-periodic boundaries, [6] the energy the gas gives up to the flux absorption, [7] the
-  // radiation energy the positivity floor of E_g adds.  bw_flux weighs this stage's boundary
+  // radiation energy the positivity floor of E_g adds, [8] the radiation energy the
+  // velocity-dependent terms add.  bw_flux weighs this stage's boundary
   // fluxes (dt/2), bw_cpl its interaction (1/2 after stage 1, 1 after stage 2), as the RK
   // combination weighs them in U^(n+1).
   double* budget;

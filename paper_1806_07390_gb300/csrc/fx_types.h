@@ -10,7 +10,7 @@ constexpr int NPLANCK_LO = 27;    // FP64 Bernoulli-series terms (x < XSPLIT, er
 constexpr int NPLANCK_LO32 = 13;  // FP32 Bernoulli-series terms (error < 1e-8)
 constexpr int NPLANCK_UP = 48;    // cap of the FP64 exponential series (x >= XSPLIT: 14 terms)
 constexpr double XSPLIT = 3.0;    // lower/upper Planck series switch
-constexpr int NBUDGET = 8;        // budget accumulators per row (see StageArgs::budget)
+constexpr int NBUDGET = 9;        // budget accumulators per row (see StageArgs::budget)
 constexpr int BUDGET_SLOTS = 64;  // rows of budget accumulators that blocks add to (summed when read)
 constexpr int PTAB_PER_OCT = 32;  // FP32 Planck band tables: nodes per octave of T
 constexpr double PTAB_XMAX = 88.0;   // below T = eps_min/88 every band underflows in FP32
@@ -40,6 +40,8 @@ struct DevGrid {
   int rad_order;  // radiation reconstruction: 1 linear with the MC limiter, 2 the gas's parabola
   int riemann;        // gas solver: 0 HLLC, 1 HLLE, 2 local Lax-Friedrichs
   double shock_guard; // carbuncle guard pressure-jump threshold (0: off)
+  int vterms;         // velocity-dependent radiation terms on (Cartesian grids)
+  double inv_dx[3];   // 1 / cell width per direction (Cartesian)
 };
 
 }  // namespace fx

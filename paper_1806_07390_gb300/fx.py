@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "FX_OK", -1: "FX_ERR_ARG", -2: "FX_ERR_CUDA", -3: "FX_ERR_WOR
                 -7: "FX_ERR_UNSUPPORTED"}
 FX_FP64, FX_FP32, FX_FP32_F64NEWTON = 0, 1, 2
 NTOTALS = 6
-NBUDGET = 8
+NBUDGET = 9
 
 # every symbol include/fx.h declares
 EXPORTS = ["fx_grid_create", "fx_bind_workspace", "fx_state_elems", "fx_state_upload",
@@ -55,7 +55,7 @@ class FxParams(ctypes.Structure):
         ("newton_maxit", ctypes.c_int), ("bisect_maxit", ctypes.c_int),
         ("newton_rtol", ctypes.c_double), ("rho_floor", ctypes.c_double),
         ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double), ("map_rt", ctypes.c_double),
-        ("riemann", ctypes.c_int), ("shock_guard", ctypes.c_double),
+        ("riemann", ctypes.c_int), ("shock_guard", ctypes.c_double), ("vterms", ctypes.c_int),
     ]
 
 
@@ -135,6 +135,7 @@ def params(pb: Problem) -> FxParams:
     P.newton_maxit, P.bisect_maxit, P.newton_rtol = pb.newton_maxit, pb.bisect_maxit, pb.newton_rtol
     P.rho_floor, P.p_floor, P.E_floor = pb.rho_floor, pb.p_floor, pb.E_floor
     P.riemann, P.shock_guard = RIEMANN_CODES[pb.riemann], pb.shock_guard
+    P.vterms = pb.vterms
     return P
 
 
@@ -238,7 +239,8 @@ class Grid:
 
     def budgets(self) -> np.ndarray:
         """Budget terms accumulated since the reset (synchronising): boundary outflows of mass,
-        momentum 1..3, total energy and radiation energy; coupling work; floor energy."""
+        momentum 1..3, total energy and radiation energy; coupling work; floor energy; the
+        radiation energy the velocity-dependent terms add."""
         out = np.zeros(NBUDGET)
         self._check(self.L.fx_budgets(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out

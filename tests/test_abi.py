@@ -67,6 +67,26 @@ def test_create_validates_parameters(L):
     assert create(pb3)[0] == -1
 
 
+def test_velocity_terms_parameters(L):
+    # vterms: 0 or 1; Cartesian grids only; one more kernel per stage; the face buffer holds the
+    # transverse face velocities on top of the fluxes and contact speeds
+    pb, _ = W.kh_2d(nx=16, ny=12, ngroups=4)
+    st0, h0, ws0 = create(pb)
+    pb.vterms = 1
+    st1, h1, ws1 = create(pb)
+    assert st0 == 0 and st1 == 0
+    assert L.fx_launches_per_step(h1) == L.fx_launches_per_step(h0) + 2
+    faces = (16 + 1) * 12 + 16 * (12 + 1)  # faces of the two directions
+    assert ws1 - ws0 >= faces * 8 and ws1 - ws0 <= faces * 8 + 4 * 256
+    L.fx_grid_destroy(h0)
+    L.fx_grid_destroy(h1)
+    pb.vterms = 2
+    assert create(pb)[0] == -1
+    pb2, _ = W.spherical_2d(nr=16, nth=8, ngroups=4)
+    pb2.vterms = 1
+    assert create(pb2)[0] == -7  # FX_ERR_UNSUPPORTED
+
+
 def test_unbound_handle_reports_workspace_error(L):
     pb, _ = W.sod_1d(n=16, ngroups=3)
     st, h, _ = create(pb)

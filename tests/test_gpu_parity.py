@@ -353,7 +353,7 @@ def test_budgets_match_the_oracle_and_close(fxmod, case):
     bud = g.budgets()
     t1 = g.totals()
     g.close()
-    scale = np.array([abs(t0[0])] * 4 + [abs(t0[4])] * 4)
+    scale = np.array([abs(t0[0])] * 4 + [abs(t0[4])] * 5)
     assert np.all(np.abs(bud - rbud) <= 1e-12 * scale), (bud, rbud)
     assert abs(t0[0] - t1[0] - bud[0]) <= 1e-13 * abs(t0[0])
     for q in range(pb.dims):
