@@ -194,13 +194,40 @@ fx_status fx_conserved_totals(fx_grid* h, double out[FX_NTOTALS]);
 fx_status fx_budgets_enable(fx_grid* h, int on);
 fx_status fx_budgets(fx_grid* h, double out[FX_NBUDGET]);
 
-/* Copy the state out, converting to dst_precision, to host (synchronous) or device memory. */
+/* Boundary layers: fixed and time-dependent boundary states, and reflecting walls on part of a
+ * side, as boxes of grid cells that the library overwrites before each stage and after each
+ * step (the double Mach reflection of Sec. 8.4 puts two such layers of cells on its fixed and
+ * moving-shock sides).  A layer is one box [lo, hi) of cells and one rule:
+ *   FX_LAYER_FRONT: state A where x - x0 - (y - y0) cot_alpha - speed t <= 0, else state B,
+ *     with x, y the cell centre (y = 0 in 1-d) and t the time of the overwritten state.  A and B
+ *     are primitives (rho, p, v_1..v_D, T_rad): E_g = B_g(T_rad), F_g = 0.  A fixed state is a
+ *     front far away (x0 = 1e30, A = B).
+ *   FX_LAYER_MIRROR: cell i along direction d takes the values of cell 2m - 1 - i, with the d
+ *     components of momentum and radiation flux negated (a reflecting wall at the face m - 1/2).
+ * Boxes may not overlap, and no mirror may read a cell of a box (otherwise FX_ERR_ARG).  The
+ * layers apply at time t0 + the sum of the dt of the fx_step calls since: the stage-1 input at
+ * t, the stage-2 input and the step's result at t + dt.  n = 0 removes them; at most 8 layers;
+ * Cartesian grids only (FX_ERR_UNSUPPORTED); the adjoint returns FX_ERR_UNSUPPORTED while layers
+ * are set.  Totals and budgets include the layer cells.  Returns the sticky status first,
+ * FX_ERR_WORKSPACE without a workspace. */
+enum { FX_LAYER_FRONT = 0, FX_LAYER_MIRROR = 1 };
+typedef struct {
+  int kind;
+  int d, m;
+  int64_t lo[3], hi[3];
+  double x0, y0, cot_alpha, speed;
+  double A[6], B[6];
+} fx_layer;
+fx_status fx_boundary_layers(fx_grid* h, const fx_layer* layers, int n, double t0);
+
+/* Copy the state out, converting to dst_precision, to host (synchronous) or device memory. *//* Copy the state out, converting to dst_precision, to host (synchronous) or device memory. */
 fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is_device);
 
 /* Number of kernel launches enqueued by one fx_step(dt, 1) call (per RK stage: the gas face
  * kernel, the radiation/update kernel, with the interaction on the interaction kernel, with
  * the carbuncle guard on the shock-flag kernel, with vterms the velocity-term kernel, and the
- * objective's reduction while it is enabled). */
+ * objective's reduction while it is enabled; per step, with boundary layers, three layer
+ * launches). */
 int fx_launches_per_step(const fx_grid* h);
 
 /* Planes of the slowest axis that one block of the radiation/update kernel marches over: 32 (or

@@ -30,6 +30,13 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class OrcLayer(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("d", ctypes.c_int), ("m", ctypes.c_int),
+                ("lo", ctypes.c_int * 3), ("hi", ctypes.c_int * 3), ("x0", ctypes.c_double),
+                ("y0", ctypes.c_double), ("cot_alpha", ctypes.c_double), ("speed", ctypes.c_double),
+                ("A", ctypes.c_double * 6), ("B", ctypes.c_double * 6)]
+
+
 class OrcParams(ctypes.Structure):
     _fields_ = [
         ("dims", ctypes.c_int), ("n", ctypes.c_int * 3), ("geom", ctypes.c_int),
@@ -45,7 +52,8 @@ class OrcParams(ctypes.Structure):
         ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double), ("nthreads", ctypes.c_int),
         ("map_rt", ctypes.c_double), ("r10_full_dt", ctypes.c_int), ("riemann", ctypes.c_int),
         ("shock_guard", ctypes.c_double), ("vterms", ctypes.c_int), ("frozen_gas", ctypes.c_int),
-        ("edges", ctypes.c_void_p), ("inflow", ctypes.c_void_p),
+        ("edges", ctypes.c_void_p), ("inflow", ctypes.c_void_p), ("nlayers", ctypes.c_int),
+        ("layers", ctypes.c_void_p), ("t0", ctypes.c_double),
     ]
 
 
@@ -91,8 +99,28 @@ def lib():
     return _lib
 
 
+def layer_structs(layers):
+    """Boundary layers (reading R29) as oracle structs: dictionaries with kind "front" or
+    "mirror", box lo/hi, and the front (x0, y0, cot_alpha, speed, primitive states A, B) or mirror
+    (d, m) parameters."""
+    arr = (OrcLayer * max(len(layers), 1))()
+    for q, ly in enumerate(layers):
+        L = arr[q]
+        L.kind = {"front": 0, "mirror": 1}[ly["kind"]]
+        for d in range(3):
+            L.lo[d], L.hi[d] = ly["lo"][d], ly["hi"][d]
+        L.d, L.m = ly.get("d", 0), ly.get("m", 0)
+        L.x0, L.y0 = ly.get("x0", 0.0), ly.get("y0", 0.0)
+        L.cot_alpha, L.speed = ly.get("cot_alpha", 0.0), ly.get("speed", 0.0)
+        for k, v in enumerate(ly.get("A", ())):
+            L.A[k] = v
+        for k, v in enumerate(ly.get("B", ())):
+            L.B[k] = v
+    return arr
+
+
 def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0, r10_full_dt: int = 0,
-           edges=None, inflow=None, frozen_gas: int = 0) -> OrcParams:
+           edges=None, inflow=None, frozen_gas: int = 0, layers=None, t0: float = 0.0) -> OrcParams:
     """Oracle parameters of a problem.  edges (G + 1 group edges), inflow (E_g then the normal
     F_g of a radiation inflow through the lower x boundary) and frozen_gas are the oracle-only
     test aids of reading R28."""
@@ -135,6 +163,12 @@ def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0, r10_full_dt: int
         keep.append(f)
         P.inflow = f.ctypes.data
         P.bc_lo[0] = 4  # ORC_INFLOW
+    if layers:
+        arr = layer_structs(layers)
+        keep.append(arr)
+        P.nlayers = len(layers)
+        P.layers = ctypes.addressof(arr)
+        P.t0 = t0
     P._keep = keep  # the arrays must outlive the calls that read P
     return P
 

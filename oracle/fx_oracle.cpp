@@ -72,6 +72,12 @@
 //   R28 test aids for the Doppler-shift test of Sec. 9 (oracle only): explicit group edges, a
 //      lower-x radiation inflow boundary (fixed E_g, F_g in the ghosts, gas as outflow) and a
 //      frozen gas state (the velocity field held fixed, as the test's stated profile is).
+//   R29 boundary layers (the double Mach reflection of Sec. 8.4): fixed and time-dependent
+//      boundary states and a reflecting wall on part of a side are cell boxes of the grid that
+//      are overwritten before each stage and after each step, either with one of two states
+//      split by a moving straight front (x - x0 - (y - y0) cot(alpha) - s t <= 0: state A) or
+//      with the mirror image of the interior across a plane (normal momentum and flux negated).
+//      The stage-2 input and the step's result take the time t + dt.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -157,6 +163,15 @@ enum { ORC_OUTFLOW = 0, ORC_PERIODIC = 1, ORC_REFLECT = 2, ORC_AXIS = 3, ORC_INF
 enum { ORC_CART = 0, ORC_SPH = 1 };
 enum { ORC_MAP_ID = 0, ORC_MAP_EXP = 1, ORC_MAP_SINH = 2 };
 enum { ORC_HLLC = 0, ORC_HLLE = 1, ORC_LLF = 2 };
+enum { ORC_LAYER_FRONT = 0, ORC_LAYER_MIRROR = 1 };
+struct orc_layer {
+  int kind;            // ORC_LAYER_FRONT or ORC_LAYER_MIRROR
+  int d;               // mirror: direction of the mirror plane's normal
+  int m;               // mirror: cell i along d takes cell 2m - 1 - i (interior indices)
+  int lo[3], hi[3];    // interior cell box [lo, hi) that the layer overwrites
+  double x0, y0, cot_alpha, speed;  // front: x - x0 - (y - y0) cot_alpha - speed t <= 0 -> A
+  double A[6], B[6];   // front: primitive states (rho, p, v_1..v_D, T_rad; E_g = B_g(T_rad), F = 0)
+};
 struct orc_params {
   int dims;
   int n[3];
@@ -186,6 +201,9 @@ struct orc_params {
   const double* edges;      // test aid (R28): G + 1 group edges, or null for the log spacing
   const double* inflow;     // test aid (R28): with bc ORC_INFLOW, the ghosts' E_g (G values) and
                             // normal F_g (G values)
+  int nlayers;              // boundary layers (R29), applied in order
+  const orc_layer* layers;
+  double t0;                // time of the initial state (front positions of the layers)
 };
 }
 
@@ -1386,6 +1404,50 @@ struct Oracle {
   Groups gr;
 };
 
+// Boundary layers (R29) at time t: every cell of each layer's box is overwritten, by the front's
+// state A or B (conserved from primitives; E_g = B_g(T_rad), F = 0) or by the mirror image of
+// the interior across the layer's plane (normal momentum and flux components negated).
+template <class S>
+static void apply_layers(const Oracle& O, std::vector<S>& U, double t) {
+  const orc_params& P = O.P;
+  const Layout& L = O.L;
+  for (int q = 0; q < P.nlayers; ++q) {
+    const orc_layer& ly = P.layers[q];
+    for (int k = ly.lo[2]; k < ly.hi[2]; ++k)
+      for (int j = ly.lo[1]; j < ly.hi[1]; ++j)
+        for (int i = ly.lo[0]; i < ly.hi[0]; ++i) {
+          const int c[3] = {i, j, k};
+          S* u = &U[L.idx(i + L.ng[0], j + L.ng[1], k + L.ng[2]) * L.NV];
+          if (ly.kind == ORC_LAYER_MIRROR) {
+            int sc[3] = {i, j, k};
+            sc[ly.d] = 2 * ly.m - 1 - c[ly.d];
+            const S* src = &U[L.idx(sc[0] + L.ng[0], sc[1] + L.ng[1], sc[2] + L.ng[2]) * L.NV];
+            for (int v = 0; v < L.NV; ++v) u[v] = src[v];
+            u[1 + ly.d] = -u[1 + ly.d];
+            for (int g = 0; g < L.G; ++g) u[L.NG + (size_t)g * L.NRV + 1 + ly.d] = -u[L.NG + (size_t)g * L.NRV + 1 + ly.d];
+            continue;
+          }
+          const double x = O.geo.dir[0].xc[i + L.ng[0]], y = L.D > 1 ? O.geo.dir[1].xc[j + L.ng[1]] : 0.0;
+          const double f = x - ly.x0 - (y - ly.y0) * ly.cot_alpha - ly.speed * t;
+          const double* w = f <= 0.0 ? ly.A : ly.B;
+          const double rho = w[0], p = w[1];
+          double ke = 0.0;
+          u[0] = rho;
+          for (int d = 0; d < L.D; ++d) {
+            u[1 + d] = rho * w[2 + d];
+            ke += 0.5 * rho * w[2 + d] * w[2 + d];
+          }
+          u[L.NG - 1] = p / (P.gamma - 1.0) + ke;
+          for (int g = 0; g < L.G; ++g) {
+            double B, dB;
+            planck_group(P, O.gr, g, w[2 + L.D], B, dB);
+            u[L.NG + (size_t)g * L.NRV] = B;
+            for (int d = 0; d < L.D; ++d) u[L.NG + (size_t)g * L.NRV + 1 + d] = 0.0;
+          }
+        }
+  }
+}
+
 // When work is non-null, work[0] receives sum_cells V (1/c^2) v . sum_g (F_g^new - F_g^-), the
 // energy the gas gives up to the flux absorption (Eq. 32; R13), and work[1] the radiation energy
 // that the positivity floor of E_g adds (R18), each summed over cells in a fixed order.
@@ -1429,9 +1491,12 @@ static int couple_all(const Oracle& O, std::vector<S>& U, double dt, double* wor
 // bud[8] the radiation energy added by the velocity-dependent terms (R27), weighted as the
 // boundary outflows.
 template <class S>
-static int rk2_step(const Oracle& O, std::vector<S>& U, double dt, S* J = nullptr, double* bud = nullptr) {
+static int rk2_step(const Oracle& O, std::vector<S>& U, double dt, S* J = nullptr, double* bud = nullptr,
+                    double* t = nullptr) {
   const Layout& L = O.L;
   const size_t N = L.ncell_p * L.NV;
+  const double t1 = t ? *t + dt : 0.0;  // time of the stage-2 input and of the result
+  if (t) apply_layers(O, U, *t);
   std::vector<S> U0 = U, dU(N), U1(N);
   int status = 0;
   S phi0 = 0.0, phi1 = 0.0;
@@ -1440,10 +1505,15 @@ static int rk2_step(const Oracle& O, std::vector<S>& U, double dt, S* J = nullpt
   explicit_rhs(O.P, O.geo, L, O.gr, U0, dU, J ? &phi0 : nullptr, bud ? bf0 : nullptr, bud ? &vw0 : nullptr);
   for (size_t q = 0; q < N; ++q) U1[q] = U0[q] + dt * dU[q];
   if (O.P.couple) status |= couple_all(O, U1, dt, bud ? w1 : nullptr);
+  if (t) apply_layers(O, U1, t1);
   fill_ghosts(O.P, L, U1);
   explicit_rhs(O.P, O.geo, L, O.gr, U1, dU, J ? &phi1 : nullptr, bud ? bf1 : nullptr, bud ? &vw1 : nullptr);
   for (size_t q = 0; q < N; ++q) U[q] = 0.5 * U0[q] + 0.5 * (U1[q] + dt * dU[q]);
   if (O.P.couple) status |= couple_all(O, U, O.P.r10_full_dt ? dt : 0.5 * dt, bud ? w2 : nullptr);
+  if (t) {
+    apply_layers(O, U, t1);
+    *t = t1;
+  }
   if (J) *J += dt * (0.5 * phi0 + 0.5 * phi1);
   if (bud) {
     for (int q = 0; q < 6; ++q) bud[q] += 0.5 * dt * bf0[q] + 0.5 * dt * bf1[q];
@@ -1537,7 +1607,8 @@ int orc_run(const orc_params* P, double* state, double dt, int nsteps) {
   std::vector<double> U;
   unpack(O, state, U, (const double*)nullptr);
   int status = 0;
-  for (int s = 0; s < nsteps; ++s) status |= rk2_step(O, U, dt);
+  double t = P->t0;
+  for (int s = 0; s < nsteps; ++s) status |= rk2_step(O, U, dt, (double*)nullptr, nullptr, P->nlayers ? &t : nullptr);
   pack(O, U, state, (double*)nullptr);
   return status;
 }

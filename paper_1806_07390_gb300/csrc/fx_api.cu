@@ -17,6 +17,7 @@
 #include "../../include/fx.h"
 #include "fx_adjoint.cuh"
 #include "fx_vterms.cuh"
+#include "fx_layers.cuh"
 #include "fx_launch.h"
 
 using namespace fx;
@@ -109,6 +110,9 @@ struct fx_grid {
   std::vector<double> tab[3];  // [NTAB][n+4] per direction (FP64 master copy)
   GroupConst gc{};
   VtConst vtc{};
+  LayerSet layers{};      // boundary layers (n = 0: none); the device copy sits at off_layers
+  size_t off_layers = 0;
+  double time = 0.0;      // time of the state (advanced by fx_step), for the layers' fronts
   PlanckParams pk{};
   // workspace layout (byte offsets)
   size_t ws_bytes = 0, off_status = 0, off_tab[3] = {0, 0, 0}, off_gc = 0, off_vtc = 0, off_A = 0, off_B = 0,
@@ -714,11 +718,31 @@ fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
   set_stage(h, a2, 2, dt);
   a1.in = A; a1.base = nullptr; a1.out = B;
   a2.in = B; a2.base = A; a2.out = A;
+  // boundary layers: the stage-1 input at t, the stage-2 input and the result at t + dt
+  const LayerSet* ls = reinterpret_cast<const LayerSet*>(h->ws + h->off_layers);
+  auto layers = [&](R* U, double t) -> fx_status {
+    if (h->layers.n == 0) return FX_OK;
+    int nmax = 1;
+    for (int q = 0; q < h->layers.n; ++q) {
+      const LayerDev& L = h->layers.L[q];
+      const int64_t nb = (int64_t)(L.hi[0] - L.lo[0]) * (L.hi[1] - L.lo[1]) * (L.hi[2] - L.lo[2]);
+      nmax = std::max(nmax, (int)std::min<int64_t>((nb + LAYER_THREADS - 1) / LAYER_THREADS, 4096));
+    }
+    layer_kernel<R><<<dim3((unsigned)nmax, (unsigned)h->layers.n, 1), LAYER_THREADS, 0, h->stream>>>(ls, U, h->dg, t);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FX_OK : cuda_fail(h, e, "boundary layer launch");
+  };
   for (int s = 0; s < nsteps; ++s) {
-    fx_status st = launch_one_stage<R, NT>(h, a1, "stage 1 launch");
+    const double t1 = h->time + dt;
+    fx_status st = layers(A, h->time);
     if (st != FX_OK) return st;
+    st = launch_one_stage<R, NT>(h, a1, "stage 1 launch");
+    if (st != FX_OK) return st;
+    if ((st = layers(B, t1)) != FX_OK) return st;
     st = launch_one_stage<R, NT>(h, a2, "stage 2 launch");
     if (st != FX_OK) return st;
+    if ((st = layers(A, t1)) != FX_OK) return st;
+    h->time = t1;
   }
   return FX_OK;
 }
@@ -1089,6 +1113,7 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   h->off_phi = off; off = align_up(off + (size_t)h->phi_rows * h->G * h->elem);
   h->off_obj = off; off = align_up(off + 8 * sizeof(double));
   h->off_bud = off; off = align_up(off + (size_t)BUDGET_SLOTS * NBUDGET * sizeof(double));
+  h->off_layers = off; off = align_up(off + sizeof(LayerSet));
   h->ws_bytes = off;
   *workspace_bytes = off;
   *out = h;
@@ -1126,11 +1151,90 @@ fx_status fx_budgets(fx_grid* h, double out[FX_NBUDGET]) {
   return FX_OK;
 }
 
+fx_status fx_boundary_layers(fx_grid* h, const fx_layer* layers, int n, double t0) {
+  if (!h || n < 0 || n > MAX_LAYERS || (n > 0 && !layers) || !std::isfinite(t0)) return FX_ERR_ARG;
+  if (h->sticky != FX_OK) return h->sticky;
+  if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  if (n > 0 && h->P.geom != FX_CART) return fail(h, FX_ERR_UNSUPPORTED, "boundary layers need a Cartesian grid");
+  const int D = h->D, G = h->G, NG = 2 + D;
+  const int64_t nn[3] = {h->P.n[0], D > 1 ? h->P.n[1] : 1, D > 2 ? h->P.n[2] : 1};
+  LayerSet S{};
+  S.n = n;
+  for (int d = 0; d < 3; ++d) {
+    S.x_lo[d] = d < D ? h->P.x_lo[d] : 0.0;
+    S.dx[d] = d < D ? (h->P.x_hi[d] - h->P.x_lo[d]) / (double)h->P.n[d] : 1.0;
+  }
+  for (int q = 0; q < n; ++q) {
+    const fx_layer& L = layers[q];
+    if (L.kind != FX_LAYER_FRONT && L.kind != FX_LAYER_MIRROR) return fail(h, FX_ERR_ARG, "layer kind");
+    for (int d = 0; d < 3; ++d)
+      if (L.lo[d] < 0 || L.hi[d] > nn[d] || L.lo[d] >= L.hi[d]) return fail(h, FX_ERR_ARG, "layer box outside the grid or empty");
+    for (int r = 0; r < q; ++r) {  // boxes must not overlap
+      const fx_layer& O = layers[r];
+      bool sep = false;
+      for (int d = 0; d < 3; ++d) sep = sep || L.hi[d] <= O.lo[d] || O.hi[d] <= L.lo[d];
+      if (!sep) return fail(h, FX_ERR_ARG, "layer boxes overlap");
+    }
+    LayerDev& Ld = S.L[q];
+    Ld.kind = L.kind;
+    for (int d = 0; d < 3; ++d) { Ld.lo[d] = (int)L.lo[d]; Ld.hi[d] = (int)L.hi[d]; }
+    if (L.kind == FX_LAYER_MIRROR) {
+      if (L.d < 0 || L.d >= D) return fail(h, FX_ERR_ARG, "mirror direction");
+      Ld.d = L.d;
+      Ld.m = L.m;
+    } else {
+      Ld.x0 = L.x0; Ld.y0 = L.y0; Ld.cot = L.cot_alpha; Ld.speed = L.speed;
+      // conserved states from the primitives (rho, p, v_1..v_D, T_rad): E_g = B_g(T_rad), F = 0
+      const double* P2[2] = {L.A, L.B};
+      double* U2[2] = {Ld.UA, Ld.UB};
+      for (int w = 0; w < 2; ++w) {
+        const double* pr = P2[w];
+        if (!(pr[0] > 0.0) || !(pr[1] > 0.0) || !(pr[2 + D] > 0.0)) return fail(h, FX_ERR_ARG, "layer state");
+        double ke = 0.0;
+        U2[w][0] = pr[0];
+        for (int d = 0; d < D; ++d) {
+          U2[w][1 + d] = pr[0] * pr[2 + d];
+          ke += 0.5 * pr[0] * pr[2 + d] * pr[2 + d];
+        }
+        U2[w][NG - 1] = pr[1] / (h->P.gamma - 1.0) + ke;
+        const double T = pr[2 + D];
+        for (int k = 0; k < G; ++k)
+          U2[w][NG + k] = h->P.a_rad * 0.15398973382026502 * T * T * T * T *
+                          host_band(h->pk, h->gc.edge[k] / T, h->gc.edge[k + 1] / T);
+      }
+    }
+  }
+  // every mirror source lies in the grid and outside every box
+  for (int q = 0; q < n; ++q) {
+    const fx_layer& L = layers[q];
+    if (L.kind != FX_LAYER_MIRROR) continue;
+    for (int64_t i = L.lo[L.d]; i < L.hi[L.d]; ++i) {
+      const int64_t si = 2 * (int64_t)L.m - 1 - i;
+      if (si < 0 || si >= nn[L.d]) return fail(h, FX_ERR_ARG, "mirror source outside the grid");
+      for (int r = 0; r < n; ++r) {
+        const fx_layer& O = layers[r];
+        // the mirror images of the box's cells along d form the box with [si] in place of [i]
+        int64_t lo[3] = {L.lo[0], L.lo[1], L.lo[2]}, hi[3] = {L.hi[0], L.hi[1], L.hi[2]};
+        lo[L.d] = si; hi[L.d] = si + 1;
+        bool sep = false;
+        for (int d = 0; d < 3; ++d) sep = sep || hi[d] <= O.lo[d] || O.hi[d] <= lo[d];
+        if (!sep) return fail(h, FX_ERR_ARG, "a mirror reads a layer box");
+      }
+    }
+  }
+  h->layers = S;
+  h->time = t0;
+  cudaError_t e = cudaMemcpyAsync(h->ws + h->off_layers, &h->layers, sizeof(LayerSet), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "boundary layer upload");
+  return FX_OK;
+}
+
 int fx_launches_per_step(const fx_grid* h) {
   if (!h) return 0;
   const bool split = h->P.couple != 0;  // the interaction kernel runs in every form
   return 2 * (2 + (split ? 1 : 0) + (h->objective ? 1 : 0) + (h->P.shock_guard > 0.0 ? 1 : 0) +
-              (h->P.vterms ? 1 : 0));
+              (h->P.vterms ? 1 : 0)) + (h->layers.n > 0 ? 3 : 0);
 }
 
 fx_status fx_objective_enable(fx_grid* h, int on) {
@@ -1179,6 +1283,7 @@ static fx_status adjoint_entry(fx_grid* h, double dt, int nsteps, int k, void* a
     return fail(h, FX_ERR_UNSUPPORTED, "the adjoint supports HLLC without the carbuncle guard");
   if (h->P.vterms)
     return fail(h, FX_ERR_UNSUPPORTED, "the adjoint does not include the velocity-dependent terms");
+  if (h->layers.n > 0) return fail(h, FX_ERR_UNSUPPORTED, "the adjoint does not include boundary layers");
   if (!adj_ws || adj_bytes < adj_layout(h, nsteps, k).bytes || (reinterpret_cast<uintptr_t>(adj_ws) % kAlign) != 0)
     return fail(h, FX_ERR_WORKSPACE, "adjoint workspace missing, too small or not 256-byte aligned");
   unsigned char* ws = static_cast<unsigned char*>(adj_ws);

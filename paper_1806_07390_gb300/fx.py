@@ -33,13 +33,21 @@ EXPORTS = ["fx_grid_create", "fx_bind_workspace", "fx_state_elems", "fx_state_up
            "fx_kernel_timing_enable", "fx_kernel_timing_read", "fx_objective_enable",
            "fx_boundary_energy_out", "fx_set_kappa0", "fx_state_set_density",
            "fx_adjoint_workspace_bytes", "fx_adjoint_forward", "fx_adjoint_backward", "fx_adjoint",
-           "fx_budgets_enable", "fx_budgets", "fx_last_error", "fx_clear_error", "fx_grid_destroy"]
+           "fx_budgets_enable", "fx_budgets", "fx_boundary_layers", "fx_last_error", "fx_clear_error",
+           "fx_grid_destroy"]
 
 
 class FxError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
+
+
+class FxLayer(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("d", ctypes.c_int), ("m", ctypes.c_int),
+                ("lo", ctypes.c_int64 * 3), ("hi", ctypes.c_int64 * 3), ("x0", ctypes.c_double),
+                ("y0", ctypes.c_double), ("cot_alpha", ctypes.c_double), ("speed", ctypes.c_double),
+                ("A", ctypes.c_double * 6), ("B", ctypes.c_double * 6)]
 
 
 class FxParams(ctypes.Structure):
@@ -101,6 +109,7 @@ def lib() -> ctypes.CDLL:
                                           ctypes.c_double, vp, vp, dp]
         L.fx_adjoint.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, sz, vp, vp, dp, dp]
         L.fx_budgets_enable.argtypes = [vp, ctypes.c_int]
+        L.fx_boundary_layers.argtypes = [vp, ctypes.POINTER(FxLayer), ctypes.c_int, ctypes.c_double]
         L.fx_budgets.argtypes = [vp, dp]
         L.fx_last_error.argtypes = [vp]
         L.fx_last_error.restype = ctypes.c_char_p
@@ -232,6 +241,24 @@ class Grid:
         out = np.zeros(NTOTALS)
         self._check(self.L.fx_conserved_totals(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
+
+    def boundary_layers(self, layers, t0: float = 0.0) -> None:
+        """Set the boundary layers (dictionaries: kind "front" or "mirror", box lo/hi, and the
+        front's x0, y0, cot_alpha, speed and primitive states A, B, or the mirror's d, m)."""
+        arr = (FxLayer * max(len(layers), 1))()
+        for q, ly in enumerate(layers):
+            L = arr[q]
+            L.kind = {"front": 0, "mirror": 1}[ly["kind"]]
+            for d in range(3):
+                L.lo[d], L.hi[d] = ly["lo"][d], ly["hi"][d]
+            L.d, L.m = ly.get("d", 0), ly.get("m", 0)
+            L.x0, L.y0 = ly.get("x0", 0.0), ly.get("y0", 0.0)
+            L.cot_alpha, L.speed = ly.get("cot_alpha", 0.0), ly.get("speed", 0.0)
+            for k, v in enumerate(ly.get("A", ())):
+                L.A[k] = v
+            for k, v in enumerate(ly.get("B", ())):
+                L.B[k] = v
+        self._check(self.L.fx_boundary_layers(self.h, arr, len(layers), float(t0)))
 
     def budgets_enable(self, on: bool = True) -> None:
         """Start (zeroing them) or stop accumulating the budgets of reading R13 in fx_step."""

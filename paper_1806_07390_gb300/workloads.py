@@ -257,6 +257,52 @@ def spherical_2d(nr: int = 640, nth: int = 128, ngroups: int = 20, nsteps: int =
     return _finish(pb, _flat(rho, p, z, z, p / rho))
 
 
+def double_mach(nx: int = 520, ny: int = 160, t_end: float = 0.2, ngroups: int = 1,
+                shock_guard: float = 0.5, precision: str = "fp64"):
+    """Double Mach reflection (Sec. 8.4; Woodward & Colella 1984): a Mach-10 oblique shock at
+    alpha = 60 degrees to a reflecting wall, on [0, 3.25 nx/520] x [0, 1] with nx x ny cells
+    (gamma = 1.4; pre-shock (rho, p, v) = (1.4, 1, 0, 0), post-shock (8, 116.5, 8.25 sin alpha,
+    -8.25 cos alpha)).  The grid carries two extra cell layers on the left, bottom and top sides
+    that the boundary layers overwrite before each stage: the post-shock state on the left and on
+    the bottom for x <= x0 = 1/6, the mirror image of the interior (reflecting wall) on the bottom
+    for x > x0, and on the top the post-shock state behind the shock's exact position
+    x0 + y cot(alpha) + 10 t / sin(alpha), the pre-shock state ahead of it; outflow on the right.
+    One group of inert radiation (kappa = 0, no interaction) at T_rad = 0.01.
+
+    Returns (problem, prim, layers): the layers as plain dictionaries (kind "front" or "mirror",
+    box lo/hi in cell indices, and the front or mirror parameters)."""
+    dx = 1.0 / ny
+    alpha = math.pi / 3.0
+    pre = (1.4, 1.0, 0.0, 0.0)
+    post = (8.0, 116.5, 8.25 * math.sin(alpha), -8.25 * math.cos(alpha))
+    tr = 0.01
+    n = (nx + 2, ny + 4, 1)
+    pb = Problem(name=f"dmr_{nx}x{ny}", dims=2, n=n, x_lo=(-2 * dx, -2 * dx, 0.0),
+                 x_hi=(nx * dx, 1.0 + 2 * dx, 1.0), bc_lo=("outflow",) * 3, bc_hi=("outflow",) * 3,
+                 ngroups=ngroups, gamma=1.4, kappa0=0.0, kap_rho_exp=0.0, kap_T_exp=0.0,
+                 kap_eps_exp=0.0, c_light=20.0, couple=0, riemann="hllc", shock_guard=shock_guard,
+                 precision=precision)
+    x0, cot, speed = 1.0 / 6.0, 1.0 / math.tan(alpha), 10.0 / math.sin(alpha)
+    x = pb.cell_centres(0)[None, :] * np.ones((n[1], 1))
+    y = pb.cell_centres(1)[:, None] * np.ones((1, n[0]))
+    behind = x - x0 - y * cot <= 0.0
+    fields = [np.where(behind, post[q], pre[q]) for q in range(4)]
+    prim = _flat(*fields, np.full(x.shape, tr))
+    pb.dt = float(pb.cfl / _max_inverse_crossing(pb, prim))
+    pb.nsteps = int(math.ceil(t_end / pb.dt))
+    ifront = int(np.searchsorted(pb.cell_centres(0), x0, side="right"))  # first cell with x > x0
+    A, B = post + (tr,), pre + (tr,)
+    fixed = dict(kind="front", x0=1e30, y0=0.0, cot_alpha=0.0, speed=0.0, A=A, B=A)
+    layers = [
+        dict(fixed, lo=(0, 0, 0), hi=(2, n[1], 1)),                        # left: post-shock
+        dict(fixed, lo=(2, 0, 0), hi=(ifront, 2, 1)),                      # bottom, x <= x0
+        dict(kind="mirror", d=1, m=2, lo=(ifront, 0, 0), hi=(n[0], 2, 1)),  # bottom wall
+        dict(kind="front", lo=(2, n[1] - 2, 0), hi=(n[0], n[1], 1), x0=x0, y0=0.0,
+             cot_alpha=cot, speed=speed, A=A, B=B),                        # top: moving shock
+    ]
+    return pb, prim, layers
+
+
 WORKLOADS = {
     "sod1d": sod_1d,
     "kh2d": kh_2d,
