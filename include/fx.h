@@ -151,7 +151,9 @@ fx_status fx_state_upload(fx_grid* h, const void* src, int src_precision, int sr
 
 /* Build the state from primitives (Sec. 5.1 variables): prim is [3+dims][ncell] doubles with
  * rows rho, p, vhat_1..vhat_D (physical velocity), T_rad.  Radiation starts in local
- * equilibrium, E_g = B_g(T_rad) (Planck group energy), F_g = 0.  Host or device pointer. */
+ * equilibrium, E_g = B_g(T_rad) (Planck group energy), F_g = 0.  Host or device pointer: host
+ * primitives are staged through the second state buffer, as many cells at a time as fit, and the
+ * call synchronises; device primitives are read on the bound stream. */
 fx_status fx_state_init_equilibrium(fx_grid* h, const double* prim, int prim_is_device);
 
 /* Enqueue nsteps SSP-RK2 steps of size dt on the bound stream (asynchronous).  Returns FX_OK

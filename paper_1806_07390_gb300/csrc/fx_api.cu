@@ -427,21 +427,22 @@ template <class R> const R* dev_tab(const fx_grid* h, int d) {
 }
 
 // ------------------------------------------------------------------ helper kernels
+// Cells c0 .. c0 + nc - 1 from primitive rows of stride ps (row r of cell c at prim[r ps + c - c0]).
 template <class R>
-__global__ void k_init_equilibrium(const double* prim, R* out, DevGrid g, const GroupConst* gcp,
-                                   const R* tab0, const R* tab1, PlanckParams pk, int geom) {
+__global__ void k_init_equilibrium(const double* prim, int64_t c0, int64_t nc, int64_t ps, R* out, DevGrid g,
+                                   const GroupConst* gcp, PlanckParams pk) {
   const int64_t ncell = g.ncell;
   const int G = g.G, D = g.D, NG = 2 + D;
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= ncell * (G + 1)) return;
-  int64_t c = t / (G + 1);
+  if (t >= nc * (G + 1)) return;
+  const int64_t cl = t / (G + 1), c = c0 + cl;
   int j = (int)(t % (G + 1));
-  double rho = prim[c], p = prim[ncell + c], Tr = prim[(int64_t)(2 + D) * ncell + c];
+  double rho = prim[cl], p = prim[ps + cl], Tr = prim[(int64_t)(2 + D) * ps + cl];
   if (j == G) {  // gas of this cell
     double ke = 0.0;
     out[c] = (R)rho;
     for (int q = 0; q < D; ++q) {
-      double vh = prim[(int64_t)(2 + q) * ncell + c];
+      double vh = prim[(int64_t)(2 + q) * ps + cl];
       out[(int64_t)(1 + q) * ncell + c] = (R)(rho * vh);
       ke += 0.5 * rho * vh * vh;
     }
@@ -455,7 +456,6 @@ __global__ void k_init_equilibrium(const double* prim, R* out, DevGrid g, const 
   double B = g.a_rad * 0.15398973382026502 * Tr * Tr * Tr * Tr * planck_band(lo, hi);
   out[(int64_t)NG * ncell + c * G + j] = (R)B;
   for (int q = 0; q < D; ++q) out[(int64_t)NG * ncell + ((int64_t)(1 + q) * ncell + c) * G + j] = R(0);
-  (void)tab0; (void)tab1; (void)geom;
 }
 
 template <class S, class T>
@@ -1478,28 +1478,34 @@ fx_status fx_state_init_equilibrium(fx_grid* h, const double* prim, int prim_is_
   if (!h || !prim) return FX_ERR_ARG;
   if (h->sticky != FX_OK) return h->sticky;
   if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
-  const int D = h->D;
-  const size_t pbytes = (size_t)(3 + D) * h->ncell * sizeof(double);
-  const double* dprim = prim;
-  cudaError_t e;
-  if (!prim_is_device) {
-    // stage the primitives in the second state buffer (free between steps)
-    if (pbytes > h->state_bytes) return fail(h, FX_ERR_UNSUPPORTED, "primitives do not fit the scratch buffer; pass a device pointer");
-    e = cudaMemcpyAsync(h->ws + h->off_B, prim, pbytes, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "primitive upload");
-    dprim = reinterpret_cast<const double*>(h->ws + h->off_B);
-  }
-  const int64_t nt = h->ncell * (h->G + 1);
-  const int nb = (int)((nt + 255) / 256);
+  const int D = h->D, NP = 3 + D;
   const GroupConst* gc = reinterpret_cast<const GroupConst*>(h->ws + h->off_gc);
-  if (h->elem == 8)
-    k_init_equilibrium<double><<<nb, 256, 0, h->stream>>>(dprim, (double*)(h->ws + h->off_A), h->dg, gc,
-                                                          nullptr, nullptr, h->pk, h->P.geom);
-  else
-    k_init_equilibrium<float><<<nb, 256, 0, h->stream>>>(dprim, (float*)(h->ws + h->off_A), h->dg, gc,
-                                                         nullptr, nullptr, h->pk, h->P.geom);
-  e = cudaGetLastError();
+  // host primitives go through the second state buffer (free between steps), as many cells at a
+  // time as fit: one copy per primitive row of the chunk, then the kernel for the chunk's cells
+  const int64_t chunk = prim_is_device ? h->ncell
+                        : std::min<int64_t>(h->ncell, (int64_t)(h->state_bytes / ((size_t)NP * sizeof(double))));
+  if (chunk < 1) return fail(h, FX_ERR_UNSUPPORTED, "the state buffer cannot hold one cell's primitives");
+  double* scratch = reinterpret_cast<double*>(h->ws + h->off_B);
+  cudaError_t e = cudaSuccess;
+  for (int64_t c0 = 0; c0 < h->ncell && e == cudaSuccess; c0 += chunk) {
+    const int64_t nc = std::min<int64_t>(chunk, h->ncell - c0);
+    const double* dprim = prim;
+    int64_t ps = h->ncell;
+    if (!prim_is_device) {
+      for (int r = 0; r < NP && e == cudaSuccess; ++r)
+        e = cudaMemcpyAsync(scratch + (size_t)r * nc, prim + (size_t)r * h->ncell + c0, (size_t)nc * sizeof(double),
+                            cudaMemcpyHostToDevice, h->stream);
+      if (e != cudaSuccess) break;
+      dprim = scratch;
+      ps = nc;
+    }
+    const int nb = (int)((nc * (h->G + 1) + 255) / 256);
+    if (h->elem == 8)
+      k_init_equilibrium<double><<<nb, 256, 0, h->stream>>>(dprim, c0, nc, ps, (double*)(h->ws + h->off_A), h->dg, gc, h->pk);
+    else
+      k_init_equilibrium<float><<<nb, 256, 0, h->stream>>>(dprim, c0, nc, ps, (float*)(h->ws + h->off_A), h->dg, gc, h->pk);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess && !prim_is_device) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "equilibrium initialisation");
   return FX_OK;
@@ -1720,11 +1726,11 @@ extern "C" fx_status fx_state_init_equilibrium_noalloc(fx_grid* h, const double*
   const GroupConst* gc = reinterpret_cast<const GroupConst*>(stage);
   const double* dprim = reinterpret_cast<const double*>(stage + kNoAllocGcBytes);
   if (state_precision == FX_FP64)
-    k_init_equilibrium<double><<<nb, 256, 0, s>>>(dprim, static_cast<double*>(state), h->dg, gc,
-                                                  nullptr, nullptr, h->pk, h->P.geom);
+    k_init_equilibrium<double><<<nb, 256, 0, s>>>(dprim, 0, h->ncell, h->ncell, static_cast<double*>(state),
+                                                  h->dg, gc, h->pk);
   else
-    k_init_equilibrium<float><<<nb, 256, 0, s>>>(dprim, static_cast<float*>(state), h->dg, gc,
-                                                 nullptr, nullptr, h->pk, h->P.geom);
+    k_init_equilibrium<float><<<nb, 256, 0, s>>>(dprim, 0, h->ncell, h->ncell, static_cast<float*>(state),
+                                                 h->dg, gc, h->pk);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "equilibrium initialisation (no-alloc)");
   return FX_OK;

@@ -79,6 +79,25 @@ def test_layers_in_3d(fxmod, precision, tol):
         H.assert_parity(pb, got, ref, tol, natural=True)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_host_primitives_staged_in_chunks(fxmod, precision):
+    # one group in FP32: a cell's five FP64 primitives need more room than its state row, so the
+    # host primitives go through the scratch buffer in several chunks; the state equals the one
+    # built from device primitives, and the oracle's
+    import torch
+    pb, prim, _ = W.double_mach(nx=64, ny=20, precision=precision)
+    g = fxmod.Grid(pb)
+    g.init_equilibrium(prim)
+    host = g.download()
+    g.init_equilibrium(torch.from_numpy(np.ascontiguousarray(prim)).cuda())
+    dev = g.download()
+    g.close()
+    assert np.array_equal(host, dev)
+    ref = oracle.init_equilibrium(pb, prim)
+    tol = 1e-14 if precision == "fp64" else 1e-6
+    np.testing.assert_allclose(host, ref, rtol=tol, atol=1e-30 * pb.a_rad)
+
+
 def test_layer_validation_and_adjoint(fxmod):
     pb, prim, layers = W.double_mach(nx=26, ny=8, t_end=0.01)
     g = fxmod.Grid(pb)
