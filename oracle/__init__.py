@@ -53,7 +53,8 @@ class OrcParams(ctypes.Structure):
         ("map_rt", ctypes.c_double), ("r10_full_dt", ctypes.c_int), ("riemann", ctypes.c_int),
         ("shock_guard", ctypes.c_double), ("vterms", ctypes.c_int), ("frozen_gas", ctypes.c_int),
         ("edges", ctypes.c_void_p), ("inflow", ctypes.c_void_p), ("nlayers", ctypes.c_int),
-        ("layers", ctypes.c_void_p), ("t0", ctypes.c_double),
+        ("layers", ctypes.c_void_p), ("t0", ctypes.c_double), ("species", ctypes.c_int),
+        ("xi0", ctypes.c_double),
     ]
 
 
@@ -151,6 +152,9 @@ def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0, r10_full_dt: int
     P.shock_guard = pb.shock_guard
     P.vterms = pb.vterms
     P.frozen_gas = frozen_gas
+    P.species, P.xi0 = pb.species, pb.xi0
+    if pb.species > 1 and (pb.vterms or pb.geom != "cart" or layers):
+        raise ValueError("three species: Cartesian grids, without the velocity terms or layers")
     keep = []
     if edges is not None:
         e = np.ascontiguousarray(edges, dtype=np.float64)

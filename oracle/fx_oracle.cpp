@@ -23,7 +23,7 @@
 //   * the objective J: RK-weighted radiation energy leaving through the upper x boundary (R19),
 //     with its tangent (initial-state and kappa0 directions) through the dual-number instantiation
 //
-// Readings where the paper is silent or ambiguous (numbered R1-R28, the labels the tests use):
+// Readings where the paper is silent or ambiguous (numbered R1-R33, the labels the tests use):
 //   R1 radiation reconstructed linearly with an MC slope limiter in moment form (Sec. 2 says linear).
 //   R2 face-interval monotonicity reset: clamp the face value so that the quadratic through the
 //      two neighbouring centroids and the face is monotone (zero slope at the nearer endpoint).
@@ -78,6 +78,20 @@
 //      split by a moving straight front (x - x0 - (y - y0) cot(alpha) - s t <= 0: state A) or
 //      with the mirror image of the interior across a plane (normal momentum and flux negated).
 //      The stage-2 input and the step's result take the time t + dt.
+//   R30 three neutrino species (nu_e, anti-nu_e, nu_x) with the same groups; lepton number per
+//      unit energy xi = -xi0/eps_g, +xi0/eps_g, 0 at the group centre (Sec. 3.2's xi with
+//      1/N_A -> xi0).
+//   R31 synthetic opacities and emissivities for the two-equation coupling (no neutrino tables):
+//      every species has the photon opacity law kappa_g; the equilibrium channel energy is
+//      w_s(Y_e) B_g(T), w = 2 Y_e, 2 (1 - Y_e), 1; j = c kappa w B (Kirchhoff).
+//   R32 composition rho Y_e advected with the gas: its face flux is the gas mass flux times the
+//      parabolic reconstruction of Y_e on the v* upwind side (the HLLC passive-scalar flux; the
+//      same with every solver).
+//   R33 two-equation Newton with the analytic Jacobian (the paper forms it by finite
+//      differences), backtracking on the residual norm scaled by u^- + sum E^- and rho Y_e^- +
+//      sum |xi| E^-; fallback: alternating bisections in T (fixed Y_e) and Y_e in [0, 1] (fixed
+//      T); u and rho Y_e by conservation, so total energy and total lepton number
+//      rho Y_e - sum xi E (a nu_e, xi < 0, carries -xi E) are conserved to round-off.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -204,6 +218,10 @@ struct orc_params {
   int nlayers;              // boundary layers (R29), applied in order
   const orc_layer* layers;
   double t0;                // time of the initial state (front positions of the layers)
+  int species;              // 1 (photons) or 3 (nu_e, anti-nu_e, nu_x: the two-equation coupling
+                            // in (T, Y_e) and the composition rho Y_e; R30-R33)
+  double xi0;               // lepton number per unit energy: xi = -xi0/eps_g (nu_e), +xi0/eps_g
+                            // (anti-nu_e), 0 (nu_x)
 };
 }
 
@@ -456,13 +474,17 @@ static void face_geometry(const orc_params& P, const Geometry& G, int d, int f, 
 // ---------------------------------------------------------------------------------------------
 struct Layout {
   int D, G, NG, NRV, NV;
+  int NX = 0, IX = -1;  // composition variables (rho Y_e with three species) and the index of rho Y_e
   int np[3], ng[3], n[3];
   size_t ncell_p;
   size_t idx(int i, int j, int k) const { return ((size_t)k * np[1] + j) * np[0] + i; }
 };
 static Layout make_layout(const orc_params& P, const Geometry& geo) {
   Layout L;
-  L.D = P.dims; L.G = P.ngroups; L.NG = 2 + P.dims; L.NRV = 1 + P.dims; L.NV = L.NG + L.G * L.NRV;
+  L.D = P.dims; L.G = (P.species > 1 ? P.species : 1) * P.ngroups; L.NG = 2 + P.dims; L.NRV = 1 + P.dims;
+  L.NX = P.species > 1 ? 1 : 0;
+  L.NV = L.NG + L.G * L.NRV + L.NX;
+  L.IX = L.NX ? L.NV - 1 : -1;
   for (int d = 0; d < 3; ++d) { L.np[d] = geo.dir[d].np; L.ng[d] = geo.dir[d].ng; L.n[d] = geo.dir[d].n; }
   L.ncell_p = (size_t)L.np[0] * L.np[1] * L.np[2];
   return L;
@@ -808,30 +830,37 @@ template <class S> static void m1_pressure_full(int D, double c, S E, const S* F
 // Opacity kappa_g = kappa0 rho^a T^b eps_g^d, scattering sigma = sigma0 rho.
 // ---------------------------------------------------------------------------------------------
 struct Groups {
-  int G;
-  std::vector<double> edge, centre;
+  int G;        // radiation channels: species x groups, species-major
+  int Gs = 0;   // groups per species (channel k is group k % Gs of species k / Gs)
+  int S = 1;    // species
+  std::vector<double> edge, centre;  // per group
   double dkappa0 = 0.0;  // tangent of kappa0 (the dual-number instantiation only)
 };
 static Groups make_groups(const orc_params& P) {
   Groups g;
-  g.G = P.ngroups;
-  g.edge.resize(g.G + 1);
-  g.centre.resize(g.G);
-  for (int k = 0; k <= g.G; ++k)
-    g.edge[k] = P.edges ? P.edges[k] : P.eps_min * std::pow(P.eps_max / P.eps_min, (double)k / g.G);
-  for (int k = 0; k < g.G; ++k) g.centre[k] = std::sqrt(g.edge[k] * g.edge[k + 1]);
+  g.S = P.species > 1 ? P.species : 1;
+  g.Gs = P.ngroups;
+  g.G = g.S * g.Gs;
+  g.edge.resize(g.Gs + 1);
+  g.centre.resize(g.Gs);
+  for (int k = 0; k <= g.Gs; ++k)
+    g.edge[k] = P.edges ? P.edges[k] : P.eps_min * std::pow(P.eps_max / P.eps_min, (double)k / g.Gs);
+  for (int k = 0; k < g.Gs; ++k) g.centre[k] = std::sqrt(g.edge[k] * g.edge[k + 1]);
   return g;
 }
 static inline double kappa0_of(const orc_params& P, const Groups&, double) { return P.kappa0; }
 static inline Dual kappa0_of(const orc_params& P, const Groups& gr, const Dual&) { return Dual(P.kappa0, gr.dkappa0); }
+// channel g: the opacity of its group (every species has the same opacity, R31)
 template <class S> static S kappa_of(const orc_params& P, const Groups& gr, int g, S rho, S T) {
-  return kappa0_of(P, gr, rho) * pow(rho, P.kap_rho_exp) * pow(T, P.kap_T_exp) * std::pow(gr.centre[g], P.kap_eps_exp);
+  return kappa0_of(P, gr, rho) * pow(rho, P.kap_rho_exp) * pow(T, P.kap_T_exp) *
+         std::pow(gr.centre[g % gr.Gs], P.kap_eps_exp);
 }
 template <class S> static S sigma_of(const orc_params& P, S rho) { return P.sigma0 * rho; }
 
 // Planck group energy density B_g(T) and dB_g/dT.
 template <class S> static void planck_group(const orc_params& P, const Groups& gr, int g, S T, S& B, S& dB) {
   const double norm = 15.0 / (PI * PI * PI * PI);
+  g = g % gr.Gs;  // channel -> group
   S a = gr.edge[g] / T, b = gr.edge[g + 1] / T;
   S I = planck_band(a, b);
   S T3 = T * T * T;
@@ -1104,6 +1133,181 @@ static int couple_cell(const orc_params& P, const Groups& gr, int D, const doubl
 }
 
 // ---------------------------------------------------------------------------------------------
+// Two-equation interaction in (T, Y_e) for three neutrino species (Sec. 5.3, the core-collapse
+// form of Eqs. 24-27; R30-R33).  Channel k is group g = k % Gs of species s = k / Gs.  The
+// equilibrium energy of a channel is w_s(Y_e) B_g(T) with w = 2 Y_e (nu_e), 2 (1 - Y_e)
+// (anti-nu_e), 1 (nu_x) (R31), the emissivity j = c kappa w B (Kirchhoff), and the lepton number
+// per unit energy xi = -xi0/eps_g, +xi0/eps_g, 0 (R30).  Inner update per channel (Eq. 25):
+//   E_k = (E_k^- + c dt kappa w B) / (1 + c dt kappa);
+// outer residuals  r_E = u(T) - u^- + sum_k (E_k - E_k^-),  r_X = rho (Y_e - Y_e^-) - sum_k xi_k
+// (E_k - E_k^-), solved by Newton with the analytic Jacobian and backtracking on the scaled
+// residual norm, with alternating one-variable bisections as the fallback (R33).  The gas energy
+// and rho Y_e are then updated by conservation: u = u^- - sum dE, rho Y_e = (rho Y_e)^- + sum xi dE.
+// ---------------------------------------------------------------------------------------------
+template <class S> static S ye_w(int s, S Ye) { return s == 0 ? 2.0 * Ye : (s == 1 ? 2.0 * (1.0 - Ye) : S(1.0)); }
+static double ye_dw(int s) { return s == 0 ? 2.0 : (s == 1 ? -2.0 : 0.0); }
+static double ye_xi(const orc_params& P, const Groups& gr, int k) {
+  const int s = k / gr.Gs;
+  const double e = gr.centre[k % gr.Gs];
+  return s == 0 ? -P.xi0 / e : (s == 1 ? P.xi0 / e : 0.0);
+}
+
+template <class S>
+static int couple_cell_ye(const orc_params& P, const Groups& gr, int D, const double h[3], S* U, double dt,
+                          int IX, double* work = nullptr) {
+  double floor_add = 0.0;
+  const int G = gr.G, NG = 2 + D, NRV = 1 + D;
+  const double c = P.c_light, cv = 1.0 / (P.gamma - 1.0);
+  int status = 0;
+  S rho = U[0];
+  if (val(rho) < P.rho_floor) { rho = P.rho_floor; U[0] = rho; status |= 2; }
+  S ke = 0.0;
+  for (int q = 0; q < D; ++q) { S vh = U[1 + q] / (rho * h[q]); ke += 0.5 * rho * vh * vh; }
+  S u_m = U[NG - 1] - ke;
+  const double u_floor = P.p_floor / (P.gamma - 1.0);
+  if (val(u_m) < u_floor) { u_m = u_floor; U[NG - 1] = ke + u_m; status |= 2; }
+  const S X_m = U[IX];  // (rho Y_e)^-
+  const S Y_m = X_m / rho;
+  std::vector<S> Em(G), En(G);
+  S Esum = 0.0, Lsum = 0.0;
+  for (int k = 0; k < G; ++k) {
+    S& E = U[NG + k * NRV];
+    if (val(E) < P.E_floor) { floor_add += P.E_floor - val(E); E = P.E_floor; }
+    Em[k] = E;
+    Esum += E;
+    Lsum += std::fabs(ye_xi(P, gr, k)) * E;
+  }
+  // residuals and Jacobian at (T, Y)
+  auto eval = [&](S T, S Y, S& rE, S& rX, S J[2][2], bool keep) {
+    S dE = 0.0, dX = 0.0, eT = 0.0, eY = 0.0, xT = 0.0, xY = 0.0;
+    for (int k = 0; k < G; ++k) {
+      const int s = k / gr.Gs;
+      S B, dB;
+      planck_group(P, gr, k, T, B, dB);
+      const S w = ye_w(s, Y);
+      const double dw = ye_dw(s), xi = ye_xi(P, gr, k);
+      S kap = kappa_of(P, gr, k, rho, T);
+      S tau = c * dt * kap, dtau = tau * (P.kap_T_exp / T);
+      S Eq = w * B;
+      S Ek = (Em[k] + tau * Eq) / (1.0 + tau);
+      S dT_ = (tau * w * dB + dtau * (Eq - Ek)) / (1.0 + tau);
+      S dY_ = tau * dw * B / (1.0 + tau);
+      dE += Ek - Em[k];
+      dX += xi * (Ek - Em[k]);
+      eT += dT_;
+      eY += dY_;
+      xT += xi * dT_;
+      xY += xi * dY_;
+      if (keep) En[k] = Ek;
+    }
+    rE = rho * cv * T - u_m + dE;
+    rX = rho * (Y - Y_m) - dX;
+    J[0][0] = rho * cv + eT;
+    J[0][1] = eY;
+    J[1][0] = -xT;
+    J[1][1] = rho - xY;
+  };
+  const double sE = val(u_m) + val(Esum), sX = std::fabs(val(X_m)) + val(Lsum) + 1e-300;
+  auto norm2 = [&](S rE, S rX) { const double a = val(rE) / sE, b = val(rX) / sX; return a * a + b * b; };
+  S T = u_m / (rho * cv), Y = Y_m;
+  S rE, rX, J[2][2];
+  eval(T, Y, rE, rX, J, false);
+  bool ok = false;
+  for (int it = 0; it < P.newton_maxit; ++it) {
+    if (norm2(rE, rX) <= 1e-28) { ok = true; break; }
+    S det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    S dT = -(J[1][1] * rE - J[0][1] * rX) / det;
+    S dY = -(J[0][0] * rX - J[1][0] * rE) / det;
+    if (std::fabs(val(dT)) <= P.newton_rtol * val(T) && std::fabs(val(dY)) <= P.newton_rtol * std::max(val(Y), 1e-3)) {
+      T = T + dT;
+      Y = Y + dY;
+      ok = true;
+      break;
+    }
+    double lam = 1.0;
+    bool acc = false;
+    const double n0 = norm2(rE, rX);
+    for (int ls = 0; ls < 40; ++ls) {
+      S Tt = T + lam * dT, Yt = Y + lam * dY;
+      if (val(Tt) > 0.0 && val(Yt) >= 0.0 && val(Yt) <= 1.0) {
+        S rEt, rXt, Jt[2][2];
+        eval(Tt, Yt, rEt, rXt, Jt, false);
+        if (norm2(rEt, rXt) < n0) {
+          T = Tt; Y = Yt; rE = rEt; rX = rXt;
+          J[0][0] = Jt[0][0]; J[0][1] = Jt[0][1]; J[1][0] = Jt[1][0]; J[1][1] = Jt[1][1];
+          acc = true;
+          break;
+        }
+      }
+      lam *= 0.5;
+    }
+    if (!acc) break;
+  }
+  if (!ok) {
+    // alternating bisections: r_E in T at fixed Y, then r_X in Y in [0, 1] at fixed T (R33)
+    for (int round = 0; round < 20 && !ok; ++round) {
+      S Jd[2][2], r1, r2;
+      S lo = 0.5 * T, hi = 2.0 * T;
+      eval(lo, Y, r1, r2, Jd, false);
+      for (int k = 0; k < 200 && val(r1) > 0.0; ++k) { lo = 0.5 * lo; eval(lo, Y, r1, r2, Jd, false); }
+      S rh;
+      eval(hi, Y, rh, r2, Jd, false);
+      for (int k = 0; k < 200 && val(rh) < 0.0; ++k) { hi = 2.0 * hi; eval(hi, Y, rh, r2, Jd, false); }
+      for (int k = 0; k < P.bisect_maxit && val(hi) - val(lo) > P.newton_rtol * val(hi); ++k) {
+        S mid = 0.5 * (lo + hi), rm;
+        eval(mid, Y, rm, r2, Jd, false);
+        if (val(rm) > 0.0) hi = mid; else lo = mid;
+      }
+      T = 0.5 * (lo + hi);
+      S ylo = 0.0, yhi = 1.0;
+      for (int k = 0; k < P.bisect_maxit && val(yhi) - val(ylo) > P.newton_rtol; ++k) {
+        S mid = 0.5 * (ylo + yhi), rm;
+        eval(T, mid, r1, rm, Jd, false);
+        if (val(rm) > 0.0) yhi = mid; else ylo = mid;
+      }
+      Y = 0.5 * (ylo + yhi);
+      eval(T, Y, rE, rX, J, false);
+      if (norm2(rE, rX) <= 1e-24) ok = true;
+    }
+    if (!ok) status |= 1;
+  }
+  // channel energies at the accepted (T, Y_e); gas energy and composition by conservation
+  eval(T, Y, rE, rX, J, true);
+  S dEsum = 0.0, dXsum = 0.0;
+  for (int k = 0; k < G; ++k) {
+    dEsum += En[k] - Em[k];
+    dXsum += ye_xi(P, gr, k) * (En[k] - Em[k]);
+    U[NG + k * NRV] = En[k];
+  }
+  U[NG - 1] = ke + (u_m - dEsum);
+  U[IX] = X_m + dXsum;
+  // momentum coupling (Eq. 28, Eqs. 31-32) over every channel, opacities at the accepted T
+  S vcon[3];
+  for (int q = 0; q < D; ++q) vcon[q] = U[1 + q] / (rho * h[q] * h[q]);
+  S dm[3] = {0.0, 0.0, 0.0}, dwork = 0.0;
+  S sig = sigma_of(P, rho);
+  for (int k = 0; k < G; ++k) {
+    S kap = kappa_of(P, gr, k, rho, T);
+    S fac = 1.0 / (1.0 + c * dt * (kap + sig));
+    for (int q = 0; q < D; ++q) {
+      S& F = U[NG + k * NRV + 1 + q];
+      S Fn = F * fac;
+      S dF = Fn - F;
+      dm[q] += dF;
+      dwork += vcon[q] * dF;
+      F = Fn;
+    }
+  }
+  for (int q = 0; q < D; ++q) U[1 + q] = U[1 + q] - dm[q] / (c * c);
+  U[NG - 1] = U[NG - 1] - dwork / (c * c);
+  if (work) {
+    work[0] = val(dwork) / (c * c);
+    work[1] = floor_add;
+  }
+  return status;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Explicit operator L(U): flux divergence + geometric sources (Sec. 4, Eq. 8, Eq. 9).
 // U must have its ghosts filled.  dU gets -(1/V) sum_faces A.F + <S> for all interior cells.
 // ---------------------------------------------------------------------------------------------
@@ -1125,7 +1329,7 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
   std::vector<S> net[3];
   // primitives on all padded cells: rho, p, vhat[D]; radiation E, Fhat[D]; total opacity per group
   const size_t NC = L.ncell_p;
-  const int NW = 2 + D;
+  const int NW = 2 + D + L.NX;  // rho, p, vhat_1..vhat_D (and Y_e)
   std::vector<S> W(NC * NW), R(NC * (size_t)G * NRV), chi(NC * (size_t)G);
   std::vector<S> Pr(NC * (size_t)G * 4);  // radiation pressure entries for sources: P00 P11 P22 P01
   for (int k = 0; k < L.np[2]; ++k)
@@ -1143,6 +1347,7 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
         w[0] = rho;
         for (int q = 0; q < D; ++q) { w[2 + q] = u[1 + q] / (rho * h[q]); ke += 0.5 * rho * w[2 + q] * w[2 + q]; }
         w[1] = (gam - 1.0) * (u[NG - 1] - ke);
+        if (L.NX) w[2 + D] = u[L.IX] / rho;  // Y_e
         S T = w[1] / rho;
         for (int g = 0; g < G; ++g) {
           S* rr = &R[(id * G + g) * NRV];
@@ -1208,7 +1413,7 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
           };
           StencilGeo gL = stencil_geo(ad, f - 1), gR = stencil_geo(ad, f);
           // gas: reconstruct rho, p, vhat (R5); left state = upper face of cell f-1, right = lower of f
-          S WL[5] = {0, 0, 0, 0, 0}, WR[5] = {0, 0, 0, 0, 0};
+          S WL[6] = {0, 0, 0, 0, 0, 0}, WR[6] = {0, 0, 0, 0, 0, 0};
           for (int v = 0; v < NW; ++v) {
             S a1, b1, a2, b2;
             recon_parabolic(P, gL, W[nb(0, -1) * NW + v], W[il * NW + v], W[ir * NW + v], a1, b1);
@@ -1229,6 +1434,14 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
             if (tr) solver = ORC_HLLE;
           }
           gas_flux(solver, D, gam, WLr, WRr, fl, vstar);
+          if (L.NX) {
+            // composition (R32): the mass flux times the reconstructed Y_e on the v* upwind side
+            double Aph0, Ah0[3], hn0;
+            face_geometry(P, geo, d, f, cl, Aph0, Ah0, hn0);
+            const S fx = fl[0] * Aph0 * (val(vstar) >= 0.0 ? WL[2 + D] : WR[2 + D]);
+            acc[il * NV + L.IX] += fx;
+            acc[ir * NV + L.IX] -= fx;
+          }
           if (P.vterms) {  // R24: v* normal, the upwind state's velocity transverse
             const S* Wu = val(vstar) >= 0.0 ? WLr : WRr;
             for (int q = 0; q < D; ++q) vface[d][ir * D + (d + q) % D] = q == 0 ? vstar : Wu[2 + q];
@@ -1466,7 +1679,8 @@ static int couple_all(const Oracle& O, std::vector<S>& U, double dt, double* wor
         cell_h(O.P, O.geo, i, j, h);
         const size_t id = L.idx(i, j, k);
         double w[2] = {0.0, 0.0};
-        status |= couple_cell(O.P, O.gr, L.D, h, &U[id * L.NV], dt, work ? w : nullptr);
+        status |= L.NX ? couple_cell_ye(O.P, O.gr, L.D, h, &U[id * L.NV], dt, L.IX, work ? w : nullptr)
+                       : couple_cell(O.P, O.gr, L.D, h, &U[id * L.NV], dt, work ? w : nullptr);
         if (work) {
           const double V = O.geo.dir[0].vol[i] * O.geo.dir[1].vol[j] * O.geo.dir[2].vol[k];
           wcell[2 * id] = w[0] * V;
@@ -1548,6 +1762,10 @@ static void unpack(const Oracle& O, const double* ext, std::vector<S>& U, const 
             size_t e = L.NG * ncell + ((size_t)v * ncell + c) * L.G + g;
             set_scalar(U[id * L.NV + L.NG + g * L.NRV + v], ext[e], ext_tangent, e);
           }
+        for (int x = 0; x < L.NX; ++x) {  // composition block after the radiation block
+          size_t e = (L.NG + (size_t)L.NRV * L.G + x) * ncell + c;
+          set_scalar(U[id * L.NV + L.IX + x], ext[e], ext_tangent, e);
+        }
       }
 }
 template <class S>
@@ -1570,6 +1788,11 @@ static void pack(const Oracle& O, const std::vector<S>& U, double* ext, double* 
             ext[e] = val(U[id * L.NV + L.NG + g * L.NRV + v]);
             if (ext_tangent) ext_tangent[e] = tangent_of(U[id * L.NV + L.NG + g * L.NRV + v]);
           }
+        for (int x = 0; x < L.NX; ++x) {
+          size_t e = (L.NG + (size_t)L.NRV * L.G + x) * ncell + c;
+          ext[e] = val(U[id * L.NV + L.IX + x]);
+          if (ext_tangent) ext_tangent[e] = tangent_of(U[id * L.NV + L.IX + x]);
+        }
       }
 }
 
@@ -1597,7 +1820,8 @@ extern "C" {
 // Number of doubles in the external state layout.
 size_t orc_state_size(const orc_params* P) {
   size_t ncell = (size_t)P->n[0] * (P->dims > 1 ? P->n[1] : 1) * (P->dims > 2 ? P->n[2] : 1);
-  return ncell * (2 + P->dims + (size_t)P->ngroups * (1 + P->dims));
+  const size_t S = P->species > 1 ? P->species : 1;
+  return ncell * (2 + P->dims + S * P->ngroups * (1 + P->dims) + (S > 1 ? 1 : 0));
 }
 
 // Advance `state` (external layout) by nsteps SSP-RK2 steps of size dt.  Returns status bits.
@@ -1761,12 +1985,16 @@ int orc_init_equilibrium(const orc_params* P, const double* prim, double* state)
           ke += 0.5 * rho * vh * vh;
         }
         state[(1 + D) * ncell + c] = p / (P->gamma - 1.0) + ke;
+        // with three species: prim row 3 + D is Y_e; channel energies w_s(Y_e) B_g(T_rad) (R31)
+        const double Ye = L.NX ? prim[(3 + D) * ncell + c] : 0.0;
         for (int g = 0; g < L.G; ++g) {
           double B, dB;
           planck_group(O.P, O.gr, g, Tr, B, dB);
+          if (L.NX) B *= ye_w(g / O.gr.Gs, Ye);
           state[L.NG * ncell + (0 * ncell + c) * L.G + g] = B;
           for (int q = 0; q < D; ++q) state[L.NG * ncell + ((size_t)(1 + q) * ncell + c) * L.G + g] = 0.0;
         }
+        if (L.NX) state[(L.NG + (size_t)L.NRV * L.G) * ncell + c] = rho * Ye;
       }
   return 0;
 }

@@ -59,6 +59,8 @@ class Problem:
     riemann: str = "hllc"      # gas Riemann solver: "hllc", "hlle" or "llf" (Sec. 5.2)
     shock_guard: float = 0.0   # carbuncle guard pressure-jump threshold (0: off)
     vterms: int = 0            # 1: velocity-dependent radiation terms (Sec. 3.2, 5.2; Cartesian)
+    species: int = 1           # 1 (photons) or 3 (neutrino species; composition rho Y_e)
+    xi0: float = 0.0           # lepton number per unit energy (three species)
     couple: int = 1
     newton_maxit: int = 50
     bisect_maxit: int = 200
@@ -76,8 +78,18 @@ class Problem:
         return int(np.prod(self.n[: self.dims]))
 
     @property
+    def nchan(self) -> int:
+        """Radiation channels: species x groups (species-major)."""
+        return self.species * self.ngroups
+
+    @property
+    def ncomp(self) -> int:
+        """Composition variables after the radiation block (rho Y_e with three species)."""
+        return 1 if self.species > 1 else 0
+
+    @property
     def nvar(self) -> int:
-        return 2 + self.dims + self.ngroups * (1 + self.dims)
+        return 2 + self.dims + self.nchan * (1 + self.dims) + self.ncomp
 
     @property
     def shape(self) -> Tuple[int, ...]:
@@ -303,12 +315,36 @@ def double_mach(nx: int = 520, ny: int = 160, t_end: float = 0.2, ngroups: int =
     return pb, prim, layers
 
 
+def neutrino_2d(nx: int = 512, ny: int = 512, ngroups: int = 8, nsteps: int = 50, seed: int = 5,
+                precision: str = "fp64"):
+    """Three neutrino species in a periodic 2-d box for the two-equation (T, Y_e) interaction:
+    groups over eps in [0.01, 10] kT0, rho = exp(0.5 delta), a seeded Gaussian random field
+    delta (k^-3), p = 1, Y_e = 0.3 + 0.1 sin(2 pi x) sin(2 pi y), shear flow v_x = 0.3 sin(2 pi y),
+    radiation at 1.5 T in the Y_e-weighted equilibrium, kappa = 3 rho T^-1.5 eps^-2, xi0 = 0.05.
+    prim rows: rho, p, v_x, v_y, T_rad, Y_e."""
+    pb = Problem(name=f"nu2d_{nx}x{ny}x{ngroups}g", dims=2, n=(nx, ny, 1), x_lo=(0.0, 0.0, 0.0),
+                 x_hi=(1.0, 1.0, 1.0), bc_lo=("periodic",) * 3, bc_hi=("periodic",) * 3,
+                 ngroups=ngroups, gamma=4.0 / 3.0, kappa0=3.0, kap_rho_exp=1.0, kap_T_exp=-1.5,
+                 kap_eps_exp=-2.0, nsteps=nsteps, species=3, xi0=0.05, precision=precision)
+    delta = gaussian_random_field((ny, nx), -3.0, seed)
+    rho = np.exp(0.5 * delta)
+    x = pb.cell_centres(0)[None, :] * np.ones((ny, 1))
+    y = pb.cell_centres(1)[:, None] * np.ones((1, nx))
+    p = np.ones((ny, nx))
+    vx = 0.3 * np.sin(2 * np.pi * y)
+    vy = np.zeros((ny, nx))
+    ye = 0.3 + 0.1 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+    pb, prim = _finish(pb, _flat(rho, p, vx, vy, 1.5 * p / rho))
+    return pb, np.concatenate([prim, _flat(ye)])
+
+
 WORKLOADS = {
     "sod1d": sod_1d,
     "kh2d": kh_2d,
     "lognormal3d": lognormal_3d,
     "blobs2d": blobs_2d,
     "sph2d": spherical_2d,
+    "nu2d": neutrino_2d,
 }
 
 

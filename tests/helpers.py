@@ -8,15 +8,17 @@ from paper_1806_07390_gb300.workloads import Problem, sub_cells, window, window_
 
 def fields(pb: Problem, state: np.ndarray):
     """Yield (name, array) per conserved field of an external-layout state."""
-    N, G, D = pb.ncell, pb.ngroups, pb.dims
+    N, G, D = pb.ncell, pb.nchan, pb.dims
     NG = 2 + D
     names = ["rho"] + [f"m{q}" for q in range(D)] + ["rhoe"]
     for v in range(NG):
         yield names[v], state[v * N:(v + 1) * N]
-    rad = state[NG * N:].reshape(1 + D, N, G)
+    rad = state[NG * N:(NG + (1 + D) * G) * N].reshape(1 + D, N, G)
     yield "E", rad[0].reshape(-1)
     for q in range(D):
         yield f"F{q}", rad[1 + q].reshape(-1)
+    if pb.ncomp:
+        yield "rhoYe", state[(NG + (1 + D) * G) * N:]
 
 
 def natural_scales(pb: Problem, ref: np.ndarray):
@@ -25,6 +27,8 @@ def natural_scales(pb: Problem, ref: np.ndarray):
     f = dict(fields(pb, ref))
     mom = np.sqrt(np.abs(f["rho"] * f["rhoe"]))
     sc = {"rho": f["rho"], "rhoe": f["rhoe"], "E": f["E"]}
+    if "rhoYe" in f:
+        sc["rhoYe"] = f["rhoYe"]
     for q in range(pb.dims):
         sc[f"m{q}"] = mom
         sc[f"F{q}"] = pb.c_light * f["E"]
@@ -70,11 +74,12 @@ def assert_parity(pb, got, ref, l1_tol, max_tol=None, skip=(), natural=False):
 
 def gather_cells(pb: Problem, state: np.ndarray, cells: np.ndarray) -> np.ndarray:
     """External-layout state restricted to the given cells (same layout, ncell = len(cells))."""
-    N, G, D = pb.ncell, pb.ngroups, pb.dims
+    N, G, D = pb.ncell, pb.nchan, pb.dims
     NG = 2 + D
     gas = state[: NG * N].reshape(NG, N)[:, cells]
-    rad = state[NG * N:].reshape(1 + D, N, G)[:, cells, :]
-    return np.concatenate([gas.reshape(-1), rad.reshape(-1)])
+    rad = state[NG * N:(NG + (1 + D) * G) * N].reshape(1 + D, N, G)[:, cells, :]
+    comp = state[(NG + (1 + D) * G) * N:].reshape(pb.ncomp, N)[:, cells]
+    return np.concatenate([gas.reshape(-1), rad.reshape(-1), comp.reshape(-1)])
 
 
 def rho_tangent(pb: Problem, state: np.ndarray, drho: np.ndarray) -> np.ndarray:
