@@ -100,6 +100,15 @@ enum { FX_NTOTALS = 6, FX_NBUDGET = 9 };
  *                      <v^i_;j> from the face velocities (v* normal, the upwind state's
  *                      transverse components).  Cartesian grids only (FX_ERR_UNSUPPORTED
  *                      otherwise); the adjoint returns FX_ERR_UNSUPPORTED with it.  0 = off.
+ *   species, xi0       0 or 1: one radiation species (photons).  3: neutrinos (nu_e, anti-nu_e,
+ *                      nu_x), each with the ngroups groups (3 ngroups <= 32 channels, species-
+ *                      major), the composition rho Y_e advected with the gas, and the two-equation
+ *                      interaction in (T, Y_e) of Sec. 5.3: the equilibrium channel energy
+ *                      w_s(Y_e) B_g(T) with w = 2 Y_e, 2 (1 - Y_e), 1 (synthetic emissivities,
+ *                      every species with the opacity law above), and the lepton number per unit
+ *                      energy xi = -xi0/eps_g, +xi0/eps_g, 0, so that rho Y_e - sum xi E is
+ *                      conserved.  FX_FP64 and Cartesian grids only, without vterms, budgets,
+ *                      boundary layers or the adjoint (FX_ERR_UNSUPPORTED).
  */
 typedef struct {
   int dims;
@@ -122,12 +131,16 @@ typedef struct {
   int riemann;
   double shock_guard;
   int vterms;
+  int species;
+  double xi0;
 } fx_params;
 
 /* State layout (upload, download, and the device copy inside the workspace): ncell = prod n[d],
  * cells in x-fastest order.  Gas block [2+dims][ncell]: rho, covariant momentum rho v_1..v_D,
- * total energy rho e.  Then the radiation block [1+dims][ncell][ngroups] (group innermost):
- * E_g, covariant F_g1..F_gD.  fx_state_elems() gives the element count. */
+ * total energy rho e.  Then the radiation block [1+dims][ncell][channels] (channel innermost;
+ * channels = ngroups, or 3 ngroups species-major with three species): E, covariant F_1..F_D.
+ * With three species, then the composition block [1][ncell]: rho Y_e.  fx_state_elems() gives
+ * the element count. */
 
 /* Validate parameters, build the geometry and reconstruction tables (host, FP64) and return the
  * workspace size in bytes the caller must provide.  *out receives the new handle (NULL on
@@ -149,8 +162,10 @@ size_t fx_state_elems(const fx_grid* h);
  * synchronous) or device memory (src_is_device = 1, enqueued on the bound stream). */
 fx_status fx_state_upload(fx_grid* h, const void* src, int src_precision, int src_is_device);
 
-/* Build the state from primitives (Sec. 5.1 variables): prim is [3+dims][ncell] doubles with
- * rows rho, p, vhat_1..vhat_D (physical velocity), T_rad.  Radiation starts in local
+/* Build the state from primitives (Sec. 5.1 variables): prim is [3+dims][ncell] doubles ([4+dims]
+ * with three species) with
+ * rows rho, p, vhat_1..vhat_D (physical velocity), T_rad (and Y_e with three species: channel
+ * energies w_s(Y_e) B_g(T_rad), composition rho Y_e).  Radiation starts in local
  * equilibrium, E_g = B_g(T_rad) (Planck group energy), F_g = 0.  Host or device pointer: host
  * primitives are staged through the second state buffer, as many cells at a time as fit, and the
  * call synchronises; device primitives are read on the bound stream. */

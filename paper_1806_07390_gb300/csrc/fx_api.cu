@@ -438,9 +438,10 @@ __global__ void k_init_equilibrium(const double* prim, int64_t c0, int64_t nc, i
   const int64_t cl = t / (G + 1), c = c0 + cl;
   int j = (int)(t % (G + 1));
   double rho = prim[cl], p = prim[ps + cl], Tr = prim[(int64_t)(2 + D) * ps + cl];
-  if (j == G) {  // gas of this cell
+  if (j == G) {  // gas of this cell (and, with three species, rho Y_e from prim row 3 + D)
     double ke = 0.0;
     out[c] = (R)rho;
+    if (g.species > 1) out[(int64_t)(NG + (1 + D) * G) * ncell + c] = (R)(rho * prim[(int64_t)(3 + D) * ps + cl]);
     for (int q = 0; q < D; ++q) {
       double vh = prim[(int64_t)(2 + q) * ps + cl];
       out[(int64_t)(1 + q) * ncell + c] = (R)(rho * vh);
@@ -451,9 +452,14 @@ __global__ void k_init_equilibrium(const double* prim, int64_t c0, int64_t nc, i
   }
   const GroupConst& gc = *gcp;
   double invT = 1.0 / Tr;
-  PlanckEdge<double> lo = planck_edge64(gc.edge[j] * invT, pk.c64);
-  PlanckEdge<double> hi = planck_edge64(gc.edge[j + 1] * invT, pk.c64);
+  const int gg = j % g.Gs, sp = j / g.Gs;  // group and species of channel j
+  PlanckEdge<double> lo = planck_edge64(gc.edge[gg] * invT, pk.c64);
+  PlanckEdge<double> hi = planck_edge64(gc.edge[gg + 1] * invT, pk.c64);
   double B = g.a_rad * 0.15398973382026502 * Tr * Tr * Tr * Tr * planck_band(lo, hi);
+  if (g.species > 1) {  // equilibrium weight 2 Y_e, 2 (1 - Y_e), 1
+    const double Ye = prim[(int64_t)(3 + D) * ps + cl];
+    B *= sp == 0 ? 2.0 * Ye : (sp == 1 ? 2.0 * (1.0 - Ye) : 1.0);
+  }
   out[(int64_t)NG * ncell + c * G + j] = (R)B;
   for (int q = 0; q < D; ++q) out[(int64_t)NG * ncell + ((int64_t)(1 + q) * ncell + c) * G + j] = R(0);
 }
@@ -987,29 +993,37 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   if (P.riemann < FX_HLLC || P.riemann > FX_LLF || !(P.shock_guard >= 0.0)) return FX_ERR_ARG;
   if (P.vterms != 0 && P.vterms != 1) return FX_ERR_ARG;
   if (P.vterms && P.geom != FX_CART) return FX_ERR_UNSUPPORTED;  // built for Cartesian grids
+  if (P.species != 0 && P.species != 1 && P.species != 3) return FX_ERR_ARG;
+  const int NS = P.species > 1 ? P.species : 1;  // species
+  if (NS > 1) {
+    if (!(P.xi0 >= 0.0) || !std::isfinite(P.xi0)) return FX_ERR_ARG;
+    // three species: FP64 state, Cartesian grid, without the velocity terms, 3 ngroups <= 32
+    if (P.precision != FX_FP64 || P.geom != FX_CART || P.vterms || NS * P.ngroups > MAXG) return FX_ERR_UNSUPPORTED;
+  }
+  const int NCH = NS * P.ngroups;  // radiation channels
   if (!(P.gamma > 1.0) || !(P.c_light > 0.0) || !(P.a_rad > 0.0)) return FX_ERR_ARG;
   if (!half_integer(P.kap_rho_exp) || !half_integer(P.kap_T_exp)) return FX_ERR_UNSUPPORTED;
   if (!(P.eps_min > 0.0) || !(P.eps_max > P.eps_min)) return FX_ERR_ARG;
   if (P.newton_maxit < 1 || P.bisect_maxit < 0 || !(P.newton_rtol > 0.0)) return FX_ERR_ARG;
   if (!(P.rho_floor > 0.0) || !(P.p_floor > 0.0) || !(P.E_floor > 0.0)) return FX_ERR_ARG;
   {
-    const int GP = P.ngroups <= 8 ? 8 : (P.ngroups <= 16 ? 16 : 32);
+    const int GP = NCH <= 8 ? 8 : (NCH <= 16 ? 16 : 32);
     size_t smem = 0;
     if (P.precision == FX_FP64)
-      smem = P.dims == 1 ? stage_smem<double, 1>(GP, P.ngroups)
-           : P.dims == 2 ? stage_smem<double, 2>(GP, P.ngroups) : stage_smem<double, 3>(GP, P.ngroups);
+      smem = P.dims == 1 ? stage_smem<double, 1>(GP, NCH)
+           : P.dims == 2 ? stage_smem<double, 2>(GP, NCH) : stage_smem<double, 3>(GP, NCH);
     else
-      smem = P.dims == 1 ? stage_smem<float, 1>(GP, P.ngroups)
-           : P.dims == 2 ? stage_smem<float, 2>(GP, P.ngroups) : stage_smem<float, 3>(GP, P.ngroups);
+      smem = P.dims == 1 ? stage_smem<float, 1>(GP, NCH)
+           : P.dims == 2 ? stage_smem<float, 2>(GP, NCH) : stage_smem<float, 3>(GP, NCH);
     if (smem > 227 * 1024) return FX_ERR_UNSUPPORTED;  // per-block shared memory of sm_103a
   }
 
   fx_grid* h = new fx_grid();
   h->P = P;
   h->D = P.dims;
-  h->G = P.ngroups;
-  h->GP = P.ngroups <= 8 ? 8 : (P.ngroups <= 16 ? 16 : 32);
-  h->NV = 2 + P.dims + P.ngroups * (1 + P.dims);
+  h->G = NCH;
+  h->GP = NCH <= 8 ? 8 : (NCH <= 16 ? 16 : 32);
+  h->NV = 2 + P.dims + NCH * (1 + P.dims) + (NS > 1 ? 1 : 0);  // + the composition block
   h->ncell = 1;
   for (int d = 0; d < P.dims; ++d) h->ncell *= P.n[d];
   h->elem = P.precision == FX_FP64 ? 8 : 4;
@@ -1021,7 +1035,10 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
 
   DevGrid& g = h->dg;
   g.D = P.dims;
-  g.G = P.ngroups;
+  g.G = NCH;
+  g.species = NS;
+  g.Gs = P.ngroups;
+  g.xi0 = P.xi0;
   for (int d = 0; d < 3; ++d) {
     g.n[d] = d < P.dims ? (int)P.n[d] : 1;
     g.bc_lo[d] = d < P.dims ? P.bc_lo[d] : FX_PERIODIC;
@@ -1051,12 +1068,15 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
     g.inv_dx[d] = d < P.dims ? (double)P.n[d] / (P.x_hi[d] - P.x_lo[d]) : 1.0;
 
   for (int d = 0; d < P.dims; ++d) build_table(P, d, h->tab[d]);
-  for (int j = 0; j <= h->G; ++j)
-    h->gc.edge[j] = P.eps_min * std::pow(P.eps_max / P.eps_min, (double)j / h->G);
-  for (int j = 0; j < h->G; ++j)
-    h->gc.efac[j] = std::pow(std::sqrt(h->gc.edge[j] * h->gc.edge[j + 1]), P.kap_eps_exp);
+  // group edges; the opacity factor eps_g^d per channel (channel k is group k % ngroups)
+  for (int j = 0; j <= P.ngroups; ++j)
+    h->gc.edge[j] = P.eps_min * std::pow(P.eps_max / P.eps_min, (double)j / P.ngroups);
+  for (int j = 0; j < h->G; ++j) {
+    const int gg = j % P.ngroups;
+    h->gc.efac[j] = std::pow(std::sqrt(h->gc.edge[gg] * h->gc.edge[gg + 1]), P.kap_eps_exp);
+  }
   for (int j = 0; j <= MAXG; ++j) h->gc.edge32[j] = (float)h->gc.edge[j];
-  vt_constants(h->gc.edge, h->G, h->vtc);
+  vt_constants(h->gc.edge, P.ngroups, h->vtc);
   for (int j = 0; j < MAXG; ++j) h->gc.efac32[j] = (float)h->gc.efac[j];
   planck_coefficients(h->pk);
   {
@@ -1128,6 +1148,7 @@ fx_status fx_budgets_enable(fx_grid* h, int on) {
   if (!h) return FX_ERR_ARG;
   if (h->sticky != FX_OK) return h->sticky;
   if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
+  if (on && h->dg.species > 1) return fail(h, FX_ERR_UNSUPPORTED, "budgets with one radiation species");
   h->budgets = on != 0;
   cudaError_t e = cudaMemsetAsync(h->ws + h->off_bud, 0, (size_t)BUDGET_SLOTS * NBUDGET * sizeof(double), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "budget reset");
@@ -1156,6 +1177,7 @@ fx_status fx_boundary_layers(fx_grid* h, const fx_layer* layers, int n, double t
   if (h->sticky != FX_OK) return h->sticky;
   if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
   if (n > 0 && h->P.geom != FX_CART) return fail(h, FX_ERR_UNSUPPORTED, "boundary layers need a Cartesian grid");
+  if (n > 0 && h->dg.species > 1) return fail(h, FX_ERR_UNSUPPORTED, "boundary layers carry no composition");
   const int D = h->D, G = h->G, NG = 2 + D;
   const int64_t nn[3] = {h->P.n[0], D > 1 ? h->P.n[1] : 1, D > 2 ? h->P.n[2] : 1};
   LayerSet S{};
@@ -1234,7 +1256,7 @@ int fx_launches_per_step(const fx_grid* h) {
   if (!h) return 0;
   const bool split = h->P.couple != 0;  // the interaction kernel runs in every form
   return 2 * (2 + (split ? 1 : 0) + (h->objective ? 1 : 0) + (h->P.shock_guard > 0.0 ? 1 : 0) +
-              (h->P.vterms ? 1 : 0)) + (h->layers.n > 0 ? 3 : 0);
+              (h->P.vterms ? 1 : 0) + (h->dg.species > 1 ? 1 : 0)) + (h->layers.n > 0 ? 3 : 0);
 }
 
 fx_status fx_objective_enable(fx_grid* h, int on) {
@@ -1284,6 +1306,7 @@ static fx_status adjoint_entry(fx_grid* h, double dt, int nsteps, int k, void* a
   if (h->P.vterms)
     return fail(h, FX_ERR_UNSUPPORTED, "the adjoint does not include the velocity-dependent terms");
   if (h->layers.n > 0) return fail(h, FX_ERR_UNSUPPORTED, "the adjoint does not include boundary layers");
+  if (h->dg.species > 1) return fail(h, FX_ERR_UNSUPPORTED, "the adjoint supports one radiation species");
   if (!adj_ws || adj_bytes < adj_layout(h, nsteps, k).bytes || (reinterpret_cast<uintptr_t>(adj_ws) % kAlign) != 0)
     return fail(h, FX_ERR_WORKSPACE, "adjoint workspace missing, too small or not 256-byte aligned");
   unsigned char* ws = static_cast<unsigned char*>(adj_ws);
@@ -1478,7 +1501,7 @@ fx_status fx_state_init_equilibrium(fx_grid* h, const double* prim, int prim_is_
   if (!h || !prim) return FX_ERR_ARG;
   if (h->sticky != FX_OK) return h->sticky;
   if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
-  const int D = h->D, NP = 3 + D;
+  const int D = h->D, NP = 3 + D + (h->dg.species > 1 ? 1 : 0);
   const GroupConst* gc = reinterpret_cast<const GroupConst*>(h->ws + h->off_gc);
   // host primitives go through the second state buffer (free between steps), as many cells at a
   // time as fit: one copy per primitive row of the chunk, then the kernel for the chunk's cells
@@ -1692,7 +1715,7 @@ extern "C" fx_status fx_state_init_equilibrium_noalloc(fx_grid* h, const double*
   if (!h || !prim || !state) return FX_ERR_ARG;
   if (state_precision != FX_FP64 && state_precision != FX_FP32) return fail(h, FX_ERR_ARG, "state precision must be FX_FP64 or FX_FP32");
   if (h->sticky != FX_OK) return h->sticky;
-  const size_t pbytes = (size_t)(3 + h->D) * h->ncell * sizeof(double);
+  const size_t pbytes = (size_t)(3 + h->D + (h->dg.species > 1 ? 1 : 0)) * h->ncell * sizeof(double);
   if (pbytes > kNoAllocBytes - kNoAllocGcBytes)
     return fail(h, FX_ERR_UNSUPPORTED,
                 "fx_state_init_equilibrium_noalloc: the primitives (" + std::to_string(pbytes) +

@@ -1,0 +1,256 @@
+// Three neutrino species (Sec. 3.2; Sec. 5.3 in the core-collapse form): the composition rho Y_e
+// and the two-equation interaction in (T, Y_e), FP64 state, Cartesian grids.
+//
+// The radiation channels are the groups of the three species (nu_e, anti-nu_e, nu_x), species-
+// major; the gas face and radiation/update kernels transport them like groups.  rho Y_e lives in
+// a block after the radiation block.
+//   comp_kernel: its finite-volume update and RK combination (the gas mass flux times the
+//     reconstructed Y_e on the v* upwind side of each face, the HLLC passive-scalar flux);
+//   couple_ye64_kernel: the interaction, one thread per cell.  Inner backward-Euler update of
+//     every channel at (T, Y_e), with the equilibrium energy w_s(Y_e) B_g(T), w = 2 Y_e,
+//     2 (1 - Y_e), 1, and the lepton number per unit energy xi = -xi0/eps_g, +xi0/eps_g, 0;
+//     outer residuals r_E = u(T) - u^- + sum dE and r_X = rho (Y_e - Y_e^-) - sum xi dE, solved
+//     by Newton with the analytic Jacobian and backtracking on the scaled residual norm, with
+//     alternating one-variable bisections as the fallback; then u and rho Y_e by conservation
+//     and the flux absorption with its momentum and energy feedback.  The decisions follow the
+//     oracle's two-equation interaction in the same order.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fx_stage.cuh"
+
+namespace fx {
+
+// ---- composition ----------------------------------------------------------------------------
+template <class R, int D>
+__global__ void __launch_bounds__(256) comp_kernel(const __grid_constant__ StageArgs<R> A) {
+  constexpr int NG = 2 + D;
+  const DevGrid& g = A.g;
+  const uint32_t ncell = (uint32_t)g.ncell;
+  const uint32_t c = blockIdx.x * 256u + threadIdx.x;
+  if (c >= ncell) return;
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const int ix = (int)(c % (uint32_t)n0), iy = (int)((c / (uint32_t)n0) % (uint32_t)n1);
+  const int iz = (int)(c / ((uint32_t)n0 * n1));
+  const uint32_t XO = (uint32_t)(NG + (1 + D) * g.G) * ncell;
+  // Y_e of the cell at offset k along direction d (ghosts from the boundary rules)
+  auto ye = [&](int d, int k) -> R {
+    int x3[3] = {ix, iy, iz};
+    bool f = false;
+    x3[d] = min(max(bc_map(x3[d] + k, g.n[d], g.bc_lo[d], g.bc_hi[d], f), 0), g.n[d] - 1);
+    const uint32_t ci = ((uint32_t)x3[2] * n1 + x3[1]) * n0 + x3[0];
+    return A.in[XO + ci] / A.in[ci];
+  };
+  R net = R(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int nd = g.n[d], i = d == 0 ? ix : (d == 1 ? iy : iz);
+    const Tab<R> tt{A.tab[d], nd + 4, A.uniform[d] ? A.urow[d] : nullptr};
+    R y[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) y[k] = ye(d, k - 2);
+    R am, bm, a0, b0, ap, bp;
+    recon_parabolic(tt, bc_pad(i - 1), y[0], y[1], y[2], am, bm);
+    recon_parabolic(tt, bc_pad(i), y[1], y[2], y[3], a0, b0);
+    recon_parabolic(tt, bc_pad(i + 1), y[2], y[3], y[4], ap, bp);
+    (void)am;
+    (void)bp;
+    const uint32_t ex = (uint32_t)(n0 + (d == 0)), ey = (uint32_t)(n1 + (d == 1));
+    const uint32_t nf = ex * ey * (uint32_t)(n2 + (d == 2));
+    const uint32_t lf = ((uint32_t)iz * ey + (uint32_t)iy) * ex + (uint32_t)ix;
+    const uint32_t uf = lf + (d == 0 ? 1u : (d == 1 ? ex : ex * ey));
+    const R* fr = A.faces + (uint32_t)A.face_off[d];
+    const R mlo = fr[lf], mhi = fr[uf];
+    const R vlo = fr[(uint32_t)NG * nf + lf], vhi = fr[(uint32_t)NG * nf + uf];
+    const R flo = mlo * (vlo >= R(0) ? bm : a0), fhi = mhi * (vhi >= R(0) ? b0 : ap);
+    net += (fhi - flo) * R(g.inv_dx[d]);
+  }
+  const R u = A.in[XO + c] - R(A.dt) * net;
+  const bool stage2 = A.base != nullptr;
+  const R r = stage2 ? R(A.alpha) * A.base[XO + c] + (R(1) - R(A.alpha)) * u : u;
+  if (!isfinite(r)) atomicOr(A.status, ST_NONFINITE);
+  A.out[XO + c] = r;
+}
+
+// ---- two-equation interaction ---------------------------------------------------------------
+constexpr int CPLYE_THREADS = 128;
+
+inline size_t couple_ye_smem_bytes(int G) { return (size_t)2 * CPLYE_THREADS * (size_t)(G + 1) * sizeof(double); }
+
+__device__ __forceinline__ double ye_w(int s, double Y) { return s == 0 ? 2.0 * Y : (s == 1 ? 2.0 * (1.0 - Y) : 1.0); }
+__device__ __forceinline__ double ye_dw(int s) { return s == 0 ? 2.0 : (s == 1 ? -2.0 : 0.0); }
+
+template <int D>
+__global__ void __launch_bounds__(CPLYE_THREADS) couple_ye64_kernel(const __grid_constant__ StageArgs<double> A) {
+  constexpr int NG = 2 + D, NRV = 1 + D;
+  extern __shared__ __align__(16) unsigned char ye_raw[];
+  const DevGrid& g = A.g;
+  const int G = g.G, Gs = g.Gs, RS = G + 1;
+  double* Em = reinterpret_cast<double*>(ye_raw) + threadIdx.x * RS;  // E^- of the cell's channels
+  double* En = Em + CPLYE_THREADS * RS;                              // the last evaluation's E
+  const uint32_t ncell = (uint32_t)g.ncell;
+  const uint32_t c = blockIdx.x * CPLYE_THREADS + threadIdx.x;
+  if (c >= ncell) return;
+  const double cl = g.c, dt = A.dts, cv = 1.0 / (g.gamma - 1.0), xi0 = g.xi0;
+  double* U = A.out;
+  const uint32_t rad = (uint32_t)NG * ncell, XO = (uint32_t)(NG + NRV * G) * ncell;
+  const GroupConst& gc = *A.gc;
+  unsigned st = 0;
+  double rho = U[c];
+  if (rho < g.rho_floor) { rho = g.rho_floor; U[c] = rho; st |= ST_FLOOR; }
+  double ke = 0.0;
+#pragma unroll
+  for (int q = 0; q < D; ++q) { const double vh = U[(1 + q) * ncell + c] / rho; ke += 0.5 * rho * vh * vh; }
+  double u_m = U[(NG - 1) * ncell + c] - ke;
+  const double u_floor = g.p_floor / (g.gamma - 1.0);
+  if (u_m < u_floor) { u_m = u_floor; U[(NG - 1) * ncell + c] = ke + u_m; st |= ST_FLOOR; }
+  const double X_m = U[XO + c], Y_m = X_m / rho;
+  double Esum = 0.0, Lsum = 0.0;
+  for (int k = 0; k < G; ++k) {
+    double E = U[rad + c * (uint32_t)G + k];
+    if (E < g.E_floor) E = g.E_floor;
+    Em[k] = E;
+    Esum += E;
+    const int s = k / Gs;
+    if (s < 2) Lsum += fabs(xi0 / sqrt(gc.edge[k % Gs] * gc.edge[k % Gs + 1])) * E;
+  }
+  const double norm = g.a_rad * 0.15398973382026502;  // a_R 15/pi^4
+  const double kpre = g.kappa0 * hpow(rho, g.kap_rho_h);
+  auto xi_of = [&](int k) -> double {
+    const int s = k / Gs;
+    const double e = sqrt(gc.edge[k % Gs] * gc.edge[k % Gs + 1]);
+    return s == 0 ? -xi0 / e : (s == 1 ? xi0 / e : 0.0);
+  };
+  // residuals and Jacobian at (T, Y); with keep, the channel energies into En
+  auto eval = [&](double T, double Y, double& rE, double& rX, double J[2][2], bool keep) {
+    double dE = 0.0, dX = 0.0, eT = 0.0, eY = 0.0, xT = 0.0, xY = 0.0;
+    const double invT = 1.0 / T, T3 = T * T * T;
+    const double kT = kpre * hpow(T, g.kap_T_h);
+    for (int gg = 0; gg < Gs; ++gg) {
+      const PlanckEdge<double> lo = planck_edge64(gc.edge[gg] * invT, A.pk.c64);
+      const PlanckEdge<double> hi = planck_edge64(gc.edge[gg + 1] * invT, A.pk.c64);
+      const double I = planck_band(lo, hi);
+      const double B = norm * T3 * T * I, dB = norm * (4.0 * T3 * I + T3 * (lo.w - hi.w));
+      const double kap = kT * gc.efac[gg];
+      const double tau = cl * dt * kap, dtau = tau * (0.5 * g.kap_T_h * invT);
+      for (int s = 0; s < 3; ++s) {
+        const int k = s * Gs + gg;
+        const double w = ye_w(s, Y), dw = ye_dw(s), xi = xi_of(k);
+        const double Eq = w * B;
+        const double Ek = (Em[k] + tau * Eq) / (1.0 + tau);
+        const double dT_ = (tau * w * dB + dtau * (Eq - Ek)) / (1.0 + tau);
+        const double dY_ = tau * dw * B / (1.0 + tau);
+        dE += Ek - Em[k];
+        dX += xi * (Ek - Em[k]);
+        eT += dT_;
+        eY += dY_;
+        xT += xi * dT_;
+        xY += xi * dY_;
+        if (keep) En[k] = Ek;
+      }
+    }
+    rE = rho * cv * T - u_m + dE;
+    rX = rho * (Y - Y_m) - dX;
+    J[0][0] = rho * cv + eT;
+    J[0][1] = eY;
+    J[1][0] = -xT;
+    J[1][1] = rho - xY;
+  };
+  const double sE = u_m + Esum, sX = fabs(X_m) + Lsum + 1e-300;
+  auto norm2 = [&](double rE, double rX) { const double a = rE / sE, b = rX / sX; return a * a + b * b; };
+  double T = u_m / (rho * cv), Y = Y_m, rE, rX, J[2][2];
+  eval(T, Y, rE, rX, J, false);
+  bool ok = false;
+  for (int it = 0; it < g.newton_maxit; ++it) {
+    if (norm2(rE, rX) <= 1e-28) { ok = true; break; }
+    const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double dT = -(J[1][1] * rE - J[0][1] * rX) / det;
+    const double dY = -(J[0][0] * rX - J[1][0] * rE) / det;
+    if (fabs(dT) <= g.newton_rtol * T && fabs(dY) <= g.newton_rtol * fmax(Y, 1e-3)) {
+      T = T + dT;
+      Y = Y + dY;
+      ok = true;
+      break;
+    }
+    double lam = 1.0;
+    bool acc = false;
+    const double n0 = norm2(rE, rX);
+    for (int ls = 0; ls < 40; ++ls) {
+      const double Tt = T + lam * dT, Yt = Y + lam * dY;
+      if (Tt > 0.0 && Yt >= 0.0 && Yt <= 1.0) {
+        double rEt, rXt, Jt[2][2];
+        eval(Tt, Yt, rEt, rXt, Jt, false);
+        if (norm2(rEt, rXt) < n0) {
+          T = Tt; Y = Yt; rE = rEt; rX = rXt;
+          J[0][0] = Jt[0][0]; J[0][1] = Jt[0][1]; J[1][0] = Jt[1][0]; J[1][1] = Jt[1][1];
+          acc = true;
+          break;
+        }
+      }
+      lam *= 0.5;
+    }
+    if (!acc) break;
+  }
+  if (!ok) {
+    for (int round = 0; round < 20 && !ok; ++round) {
+      double Jd[2][2], r1, r2, rh, rm;
+      double lo = 0.5 * T, hi = 2.0 * T;
+      eval(lo, Y, r1, r2, Jd, false);
+      for (int k = 0; k < 200 && r1 > 0.0; ++k) { lo = 0.5 * lo; eval(lo, Y, r1, r2, Jd, false); }
+      eval(hi, Y, rh, r2, Jd, false);
+      for (int k = 0; k < 200 && rh < 0.0; ++k) { hi = 2.0 * hi; eval(hi, Y, rh, r2, Jd, false); }
+      for (int k = 0; k < g.bisect_maxit && hi - lo > g.newton_rtol * hi; ++k) {
+        const double mid = 0.5 * (lo + hi);
+        eval(mid, Y, rm, r2, Jd, false);
+        if (rm > 0.0) hi = mid; else lo = mid;
+      }
+      T = 0.5 * (lo + hi);
+      double ylo = 0.0, yhi = 1.0;
+      for (int k = 0; k < g.bisect_maxit && yhi - ylo > g.newton_rtol; ++k) {
+        const double mid = 0.5 * (ylo + yhi);
+        eval(T, mid, r1, rm, Jd, false);
+        if (rm > 0.0) yhi = mid; else ylo = mid;
+      }
+      Y = 0.5 * (ylo + yhi);
+      eval(T, Y, rE, rX, J, false);
+      if (norm2(rE, rX) <= 1e-24) ok = true;
+    }
+    if (!ok) st |= ST_NEWTON;
+  }
+  // channel energies at the accepted (T, Y_e); u and rho Y_e by conservation
+  eval(T, Y, rE, rX, J, true);
+  double dEsum = 0.0, dXsum = 0.0;
+  for (int k = 0; k < G; ++k) {
+    dEsum += En[k] - Em[k];
+    dXsum += xi_of(k) * (En[k] - Em[k]);
+    U[rad + c * (uint32_t)G + k] = En[k];
+  }
+  U[(NG - 1) * ncell + c] = ke + (u_m - dEsum);
+  U[XO + c] = X_m + dXsum;
+  // flux absorption (Eq. 28) with its momentum and energy feedback (Eqs. 31-32)
+  double vcon[D], dm[D], dwork = 0.0;
+#pragma unroll
+  for (int q = 0; q < D; ++q) { vcon[q] = U[(1 + q) * ncell + c] / rho; dm[q] = 0.0; }
+  const double sig = g.sigma0 * rho;
+  const double kT = kpre * hpow(T, g.kap_T_h);
+  for (int k = 0; k < G; ++k) {
+    const double fac = 1.0 / (1.0 + cl * dt * (kT * gc.efac[k % Gs] + sig));
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      double* Fp = U + rad + (uint32_t)(1 + q) * ncell * (uint32_t)G + c * (uint32_t)G + k;
+      const double F = *Fp, Fn = F * fac, dF = Fn - F;
+      dm[q] += dF;
+      dwork += vcon[q] * dF;
+      *Fp = Fn;
+    }
+  }
+  const double ic2 = 1.0 / (cl * cl);
+#pragma unroll
+  for (int q = 0; q < D; ++q) U[(1 + q) * ncell + c] -= dm[q] * ic2;
+  U[(NG - 1) * ncell + c] -= dwork * ic2;
+  bool bad = !isfinite(U[(NG - 1) * ncell + c]) || !isfinite(U[XO + c]);
+  if (bad) st |= ST_NONFINITE;
+  if (st) atomicOr(A.status, st);
+}
+
+}  // namespace fx

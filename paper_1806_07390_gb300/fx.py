@@ -64,6 +64,7 @@ class FxParams(ctypes.Structure):
         ("newton_rtol", ctypes.c_double), ("rho_floor", ctypes.c_double),
         ("p_floor", ctypes.c_double), ("E_floor", ctypes.c_double), ("map_rt", ctypes.c_double),
         ("riemann", ctypes.c_int), ("shock_guard", ctypes.c_double), ("vterms", ctypes.c_int),
+        ("species", ctypes.c_int), ("xi0", ctypes.c_double),
     ]
 
 
@@ -145,6 +146,7 @@ def params(pb: Problem) -> FxParams:
     P.rho_floor, P.p_floor, P.E_floor = pb.rho_floor, pb.p_floor, pb.E_floor
     P.riemann, P.shock_guard = RIEMANN_CODES[pb.riemann], pb.shock_guard
     P.vterms = pb.vterms
+    P.species, P.xi0 = pb.species, pb.xi0
     return P
 
 

@@ -87,6 +87,26 @@ def test_velocity_terms_parameters(L):
     assert create(pb2)[0] == -7  # FX_ERR_UNSUPPORTED
 
 
+def test_three_species_parameters(L):
+    # species: 0/1 or 3; three species need the FP64 state, a Cartesian grid and at most 32
+    # channels; the state gains a composition block; one more kernel per stage
+    pb, _ = W.neutrino_2d(nx=16, ny=12, ngroups=8)
+    st, h, ws = create(pb)
+    assert st == 0
+    assert L.fx_state_elems(h) == pb.state_size() == pb.ncell * (4 + 3 * 24 + 1)
+    pb1, _ = W.kh_2d(nx=16, ny=12, ngroups=4)
+    h1 = create(pb1)[1]
+    assert L.fx_launches_per_step(h) == L.fx_launches_per_step(h1) + 2
+    L.fx_grid_destroy(h)
+    L.fx_grid_destroy(h1)
+    for kw, code in ((dict(species=2), -1), (dict(precision="fp32"), -7), (dict(ngroups=11), -7),
+                     (dict(vterms=1), -7), (dict(xi0=-1.0), -1)):
+        pb2, _ = W.neutrino_2d(nx=16, ny=12, ngroups=8)
+        for k, v in kw.items():
+            setattr(pb2, k, v)
+        assert create(pb2)[0] == code, kw
+
+
 def test_unbound_handle_reports_workspace_error(L):
     pb, _ = W.sod_1d(n=16, ngroups=3)
     st, h, _ = create(pb)

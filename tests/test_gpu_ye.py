@@ -1,0 +1,89 @@
+"""GPU parity of the three-species form (neutrinos: the composition rho Y_e and the two-equation
+(T, Y_e) interaction of Sec. 5.3; readings R30-R33) with the FP64 oracle, through the C ABI.
+
+FP64 bars (relative L1 <= 1e-10, max-norm <= 1e-8 per field, rho Y_e included) on the neutrino
+box in 2-d, a 1-d tube with reflecting and outflow ends and a 3-d box; total lepton number
+rho Y_e - sum xi E conserved to round-off on the periodic box; the equilibrium initial state
+against the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_07390_gb300 import workloads as W
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fxmod():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_07390_gb300 import build, fx
+    build.build()
+    return fx
+
+
+def xi_of(pb):
+    e = pb.eps_min * (pb.eps_max / pb.eps_min) ** (np.arange(pb.ngroups + 1) / pb.ngroups)
+    cen = np.sqrt(e[:-1] * e[1:])
+    return np.concatenate([-pb.xi0 / cen, pb.xi0 / cen, np.zeros(pb.ngroups)])
+
+
+def lepton(pb, s):
+    N, G, D = pb.ncell, pb.nchan, pb.dims
+    NG = 2 + D
+    E = s[NG * N:(NG + G) * N].reshape(N, G)
+    X = s[(NG + (1 + D) * G) * N:]
+    return X.sum() - (E * xi_of(pb)[None, :]).sum()
+
+
+def case(name):
+    if name == "box2d":
+        pb, prim = W.neutrino_2d(nx=44, ny=36, ngroups=8, nsteps=5)
+    elif name == "tube1d":
+        pb, prim = W.neutrino_2d(nx=4, ny=4, ngroups=6)
+        pb = W.Problem(**{**pb.__dict__, "dims": 1, "n": (90, 1, 1), "bc_lo": ("reflect",) * 3,
+                          "bc_hi": ("outflow",) * 3, "nsteps": 6})
+        x = pb.cell_centres(0)
+        rho = 1.0 + 0.5 * np.tanh((x - 0.5) / 0.05)
+        p = np.ones_like(x)
+        prim = np.stack([rho, p, 0.2 * np.sin(2 * np.pi * x), 1.5 * p / rho, 0.25 + 0.15 * x])
+    else:
+        pb, prim = W.neutrino_2d(nx=4, ny=4, ngroups=4)
+        n = (10, 9, 8)
+        pb = W.Problem(**{**pb.__dict__, "dims": 3, "n": n, "nsteps": 3})
+        rng = np.random.default_rng(9)
+        N = int(np.prod(n))
+        rho = rng.uniform(0.6, 1.8, N)
+        p = rng.uniform(0.7, 1.3, N)
+        v = rng.uniform(-0.2, 0.2, (3, N))
+        prim = np.vstack([rho, p, v, 1.4 * p / rho, rng.uniform(0.15, 0.45, N)])
+    # the light-crossing step of this grid (the generator's step was for its own grid)
+    pb.dt = 0.3 * min(1.0 / pb.n[d] for d in range(pb.dims)) / pb.c_light / pb.dims
+    return pb, np.ascontiguousarray(prim, dtype=np.float64)
+
+
+@pytest.mark.parametrize("name", ["box2d", "tube1d", "box3d"])
+def test_three_species_fp64(fxmod, name):
+    pb, prim = case(name)
+    s0 = oracle.init_equilibrium(pb, prim)
+    ref, rst = oracle.run(pb, s0, pb.dt, pb.nsteps, nthreads=8)
+    g = fxmod.Grid(pb)
+    g.init_equilibrium(prim)
+    init = g.download()
+    g.step(pb.dt, pb.nsteps)
+    st = g.status()
+    got = g.download()
+    g.close()
+    assert st == 0 and rst == 0
+    np.testing.assert_allclose(init, s0, rtol=1e-13, atol=1e-300)
+    H.assert_parity(pb, got, ref, 1e-10, 1e-8)
+    if name == "box2d":  # periodic: total lepton number conserved
+        L0, L1 = lepton(pb, s0), lepton(pb, got)
+        assert abs(L1 - L0) <= 1e-13 * abs(L0)
+        # and the interaction moved it between gas and radiation
+        X0 = s0[-pb.ncell:].sum()
+        assert abs(got[-pb.ncell:].sum() - X0) > 1e-6 * abs(X0)
