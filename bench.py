@@ -207,6 +207,8 @@ WORKLOADS = {
     "blobs2d": (W.blobs_2d, "fp32", "2-d density blobs, 512x512 cells x 8 groups",
                 ((128, 128), (248, 248), 4)),
     "sod1d": (W.sod_1d, "fp64", "1-d radiating Sod tube, 512 cells x 12 groups", None),
+    "nu2d": (W.neutrino_2d, "fp64", "2-d periodic box, three neutrino species, 512x512 cells x "
+             "(3 x 8) channels, two-equation (T, Y_e) interaction", None),
     "dmr": (lambda precision, nx=520, ny=160: _with_layers(W.double_mach(nx=nx, ny=ny, precision=precision)),
             "fp32", "double Mach reflection, 520x160 cells (+ boundary layers) x 1 inert group, "
             "HLLC with the carbuncle guard", None),
@@ -230,6 +232,8 @@ def sized(name, gen, shape):
         return lambda precision: W.sod_1d(n=shape[0], precision=precision)
     if name == "dmr":
         return lambda precision: gen(precision, nx=shape[0], ny=shape[1])
+    if name == "nu2d":
+        return lambda precision: W.neutrino_2d(nx=shape[0], ny=shape[1], precision=precision)
     return lambda precision: gen(shape=tuple(shape), precision=precision)
 
 
@@ -328,9 +332,9 @@ def cpu_baseline(pb64, prim, spec, budget_s=15.0):
         if time.perf_counter() - t0 > budget_s or nst >= 50:
             break
     sec = time.perf_counter() - t0
-    zgs = sub.ncell * sub.ngroups * 2 * nst
+    zgs = sub.ncell * sub.nchan * 2 * nst
     return {"value": zgs / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{what} x {sub.ngroups} groups, {nst} FP64 steps, OpenMP over cells"}
+            "sample": f"{what} x {sub.nchan} groups, {nst} FP64 steps, OpenMP over cells"}
 
 
 def run_reference(args):
@@ -356,7 +360,7 @@ def run_reference(args):
     for i in range(steps):
         s, _ = oracle.run(sub, s, sub.dt, 1, nthreads=cores, layers=lay, t0=(warmup + i) * sub.dt)
     sec = time.perf_counter() - t0
-    zgs = sub.ncell * sub.ngroups * 2 * steps
+    zgs = sub.ncell * sub.nchan * 2 * steps
     val = zgs / sec
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * sec / steps,
@@ -365,7 +369,7 @@ def run_reference(args):
             "config": {"workload": f"{args.workload}: {desc} (oracle sample: {what})",
                        "precision": "fp64"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{what} x {sub.ngroups} groups, {steps} FP64 steps"},
+                             "sample": f"{what} x {sub.nchan} groups, {steps} FP64 steps"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -417,12 +421,14 @@ def main():
     for name in [f for f in args.forms.split(",") if f and f != head]:
         if name == "fp64" and args.no_fp64:
             continue
+        if pbh.species > 1 and name != "fp64":
+            continue  # three species: the FP64 state only
         forms[name] = gen(precision=name)[0]
-    zg = pbh.ncell * pbh.ngroups
+    zg = pbh.ncell * pbh.nchan  # zone-groups (zone-channels with three species)
     peak, peak_kind = load_peaks()
     # the headline form once more with the velocity-dependent radiation terms (Cartesian grids)
     pbv = None
-    if not args.no_vterms and pbh.geom == "cart":
+    if not args.no_vterms and pbh.geom == "cart" and pbh.species == 1:
         pbv = gen(precision=head)[0]
         pbv.vterms = 1
 
@@ -440,7 +446,7 @@ def main():
 
     sech = msh / 1e3
     value = whole_job_rate(zg * 2 * args.steps, world, sech)
-    nv = pbh.nvar
+    nv = pbh.nvar - pbh.ncomp  # the variables the radiation/update kernel moves
 
     sm_max = 2070.0
     try:
