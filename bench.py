@@ -207,7 +207,7 @@ WORKLOADS = {
     "blobs2d": (W.blobs_2d, "fp32", "2-d density blobs, 512x512 cells x 8 groups",
                 ((128, 128), (248, 248), 4)),
     "sod1d": (W.sod_1d, "fp64", "1-d radiating Sod tube, 512 cells x 12 groups", None),
-    "nu2d": (W.neutrino_2d, "fp64", "2-d periodic box, three neutrino species, 512x512 cells x "
+    "nu2d": (W.neutrino_2d, "fp32n64", "2-d periodic box, three neutrino species, 512x512 cells x "
              "(3 x 8) channels, two-equation (T, Y_e) interaction", None),
     "dmr": (lambda precision, nx=520, ny=160: _with_layers(W.double_mach(nx=nx, ny=ny, precision=precision)),
             "fp32", "double Mach reflection, 520x160 cells (+ boundary layers) x 1 inert group, "
@@ -421,8 +421,6 @@ def main():
     for name in [f for f in args.forms.split(",") if f and f != head]:
         if name == "fp64" and args.no_fp64:
             continue
-        if pbh.species > 1 and name != "fp64":
-            continue  # three species: the FP64 state only
         forms[name] = gen(precision=name)[0]
     zg = pbh.ncell * pbh.nchan  # zone-groups (zone-channels with three species)
     peak, peak_kind = load_peaks()

@@ -107,8 +107,9 @@ enum { FX_NTOTALS = 6, FX_NBUDGET = 9 };
  *                      w_s(Y_e) B_g(T) with w = 2 Y_e, 2 (1 - Y_e), 1 (synthetic emissivities,
  *                      every species with the opacity law above), and the lepton number per unit
  *                      energy xi = -xi0/eps_g, +xi0/eps_g, 0, so that rho Y_e - sum xi E is
- *                      conserved.  FX_FP64 and Cartesian grids only, without vterms, budgets,
- *                      boundary layers or the adjoint (FX_ERR_UNSUPPORTED).
+ *                      conserved.  Cartesian grids only, without vterms, budgets, boundary
+ *                      layers or the adjoint (FX_ERR_UNSUPPORTED); in the FP32 forms the
+ *                      interaction computes in FP64 and stores the FP32 state.
  */
 typedef struct {
   int dims;

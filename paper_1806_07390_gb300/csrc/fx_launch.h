@@ -132,21 +132,17 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // three species: the composition's update, then the two-equation interaction (FP64 state)
+  // three species: the composition's update, then the two-equation interaction (FP64 arithmetic)
   if (a.g.species > 1) {
     comp_kernel<R, D><<<(unsigned)((a.g.ncell + 255) / 256), 256, 0, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess || !a.g.couple) return e;
-    if constexpr (std::is_same<R, double>::value) {
-      auto ck = couple_ye64_kernel<D>;
-      const size_t cs = couple_ye_smem_bytes(a.g.G);
-      e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
-      if (e != cudaSuccess) return e;
-      ck<<<(unsigned)((a.g.ncell + CPLYE_THREADS - 1) / CPLYE_THREADS), CPLYE_THREADS, cs, s>>>(a);
-      return cudaGetLastError();
-    } else {
-      return cudaErrorInvalidValue;  // the host admits three species with the FP64 state only
-    }
+    auto ck = couple_ye_kernel<R, D>;
+    const size_t cs = couple_ye_smem_bytes(a.g.G);
+    e = cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
+    if (e != cudaSuccess) return e;
+    ck<<<(unsigned)((a.g.ncell + CPLYE_THREADS - 1) / CPLYE_THREADS), CPLYE_THREADS, cs, s>>>(a);
+    return cudaGetLastError();
   }
   // the interaction, one thread per cell (FP32 state: couple_kernel; FP64 state: couple64_kernel)
   if (a.g.couple) {

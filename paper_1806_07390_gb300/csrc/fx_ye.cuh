@@ -1,12 +1,13 @@
 // Three neutrino species (Sec. 3.2; Sec. 5.3 in the core-collapse form): the composition rho Y_e
-// and the two-equation interaction in (T, Y_e), FP64 state, Cartesian grids.
+// and the two-equation interaction in (T, Y_e), Cartesian grids.
 //
 // The radiation channels are the groups of the three species (nu_e, anti-nu_e, nu_x), species-
 // major; the gas face and radiation/update kernels transport them like groups.  rho Y_e lives in
 // a block after the radiation block.
 //   comp_kernel: its finite-volume update and RK combination (the gas mass flux times the
 //     reconstructed Y_e on the v* upwind side of each face, the HLLC passive-scalar flux);
-//   couple_ye64_kernel: the interaction, one thread per cell.  Inner backward-Euler update of
+//   couple_ye_kernel: the interaction, one thread per cell, in FP64 arithmetic for the FP64
+//     and the FP32 state alike (the FP32 forms store the result in FP32).  Inner backward-Euler update of
 //     every channel at (T, Y_e), with the equilibrium energy w_s(Y_e) B_g(T), w = 2 Y_e,
 //     2 (1 - Y_e), 1, and the lepton number per unit energy xi = -xi0/eps_g, +xi0/eps_g, 0;
 //     outer residuals r_E = u(T) - u^- + sum dE and r_X = rho (Y_e - Y_e^-) - sum xi dE, solved
@@ -80,8 +81,8 @@ inline size_t couple_ye_smem_bytes(int G) { return (size_t)2 * CPLYE_THREADS * (
 __device__ __forceinline__ double ye_w(int s, double Y) { return s == 0 ? 2.0 * Y : (s == 1 ? 2.0 * (1.0 - Y) : 1.0); }
 __device__ __forceinline__ double ye_dw(int s) { return s == 0 ? 2.0 : (s == 1 ? -2.0 : 0.0); }
 
-template <int D>
-__global__ void __launch_bounds__(CPLYE_THREADS) couple_ye64_kernel(const __grid_constant__ StageArgs<double> A) {
+template <class R, int D>
+__global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_constant__ StageArgs<R> A) {
   constexpr int NG = 2 + D, NRV = 1 + D;
   extern __shared__ __align__(16) unsigned char ye_raw[];
   const DevGrid& g = A.g;
@@ -92,18 +93,18 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye64_kernel(const __grid
   const uint32_t c = blockIdx.x * CPLYE_THREADS + threadIdx.x;
   if (c >= ncell) return;
   const double cl = g.c, dt = A.dts, cv = 1.0 / (g.gamma - 1.0), xi0 = g.xi0;
-  double* U = A.out;
+  R* U = A.out;
   const uint32_t rad = (uint32_t)NG * ncell, XO = (uint32_t)(NG + NRV * G) * ncell;
   const GroupConst& gc = *A.gc;
   unsigned st = 0;
   double rho = U[c];
-  if (rho < g.rho_floor) { rho = g.rho_floor; U[c] = rho; st |= ST_FLOOR; }
+  if (rho < g.rho_floor) { rho = g.rho_floor; U[c] = (R)rho; st |= ST_FLOOR; }
   double ke = 0.0;
 #pragma unroll
   for (int q = 0; q < D; ++q) { const double vh = U[(1 + q) * ncell + c] / rho; ke += 0.5 * rho * vh * vh; }
   double u_m = U[(NG - 1) * ncell + c] - ke;
   const double u_floor = g.p_floor / (g.gamma - 1.0);
-  if (u_m < u_floor) { u_m = u_floor; U[(NG - 1) * ncell + c] = ke + u_m; st |= ST_FLOOR; }
+  if (u_m < u_floor) { u_m = u_floor; U[(NG - 1) * ncell + c] = (R)(ke + u_m); st |= ST_FLOOR; }
   const double X_m = U[XO + c], Y_m = X_m / rho;
   double Esum = 0.0, Lsum = 0.0;
   for (int k = 0; k < G; ++k) {
@@ -223,10 +224,11 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye64_kernel(const __grid
   for (int k = 0; k < G; ++k) {
     dEsum += En[k] - Em[k];
     dXsum += xi_of(k) * (En[k] - Em[k]);
-    U[rad + c * (uint32_t)G + k] = En[k];
+    U[rad + c * (uint32_t)G + k] = (R)En[k];
   }
-  U[(NG - 1) * ncell + c] = ke + (u_m - dEsum);
-  U[XO + c] = X_m + dXsum;
+  // (kept in FP64 until the momentum feedback below, then stored once)
+  double ue = ke + (u_m - dEsum);
+  U[XO + c] = (R)(X_m + dXsum);
   // flux absorption (Eq. 28) with its momentum and energy feedback (Eqs. 31-32)
   double vcon[D], dm[D], dwork = 0.0;
 #pragma unroll
@@ -237,18 +239,19 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye64_kernel(const __grid
     const double fac = 1.0 / (1.0 + cl * dt * (kT * gc.efac[k % Gs] + sig));
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-      double* Fp = U + rad + (uint32_t)(1 + q) * ncell * (uint32_t)G + c * (uint32_t)G + k;
+      R* Fp = U + rad + (uint32_t)(1 + q) * ncell * (uint32_t)G + c * (uint32_t)G + k;
       const double F = *Fp, Fn = F * fac, dF = Fn - F;
       dm[q] += dF;
       dwork += vcon[q] * dF;
-      *Fp = Fn;
+      *Fp = (R)Fn;
     }
   }
   const double ic2 = 1.0 / (cl * cl);
 #pragma unroll
-  for (int q = 0; q < D; ++q) U[(1 + q) * ncell + c] -= dm[q] * ic2;
-  U[(NG - 1) * ncell + c] -= dwork * ic2;
-  bool bad = !isfinite(U[(NG - 1) * ncell + c]) || !isfinite(U[XO + c]);
+  for (int q = 0; q < D; ++q) U[(1 + q) * ncell + c] = (R)((double)U[(1 + q) * ncell + c] - dm[q] * ic2);
+  ue -= dwork * ic2;
+  U[(NG - 1) * ncell + c] = (R)ue;
+  bool bad = !isfinite(ue) || !isfinite((double)U[XO + c]);
   if (bad) st |= ST_NONFINITE;
   if (st) atomicOr(A.status, st);
 }

@@ -88,7 +88,7 @@ def test_velocity_terms_parameters(L):
 
 
 def test_three_species_parameters(L):
-    # species: 0/1 or 3; three species need the FP64 state, a Cartesian grid and at most 32
+    # species: 0/1 or 3; three species need a Cartesian grid, no velocity terms and at most 32
     # channels; the state gains a composition block; one more kernel per stage
     pb, _ = W.neutrino_2d(nx=16, ny=12, ngroups=8)
     st, h, ws = create(pb)
@@ -99,8 +99,8 @@ def test_three_species_parameters(L):
     assert L.fx_launches_per_step(h) == L.fx_launches_per_step(h1) + 2
     L.fx_grid_destroy(h)
     L.fx_grid_destroy(h1)
-    for kw, code in ((dict(species=2), -1), (dict(precision="fp32"), -7), (dict(ngroups=11), -7),
-                     (dict(vterms=1), -7), (dict(xi0=-1.0), -1)):
+    for kw, code in ((dict(species=2), -1), (dict(ngroups=11), -7), (dict(vterms=1), -7),
+                     (dict(xi0=-1.0), -1)):
         pb2, _ = W.neutrino_2d(nx=16, ny=12, ngroups=8)
         for k, v in kw.items():
             setattr(pb2, k, v)

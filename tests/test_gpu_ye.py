@@ -87,3 +87,20 @@ def test_three_species_fp64(fxmod, name):
         # and the interaction moved it between gas and radiation
         X0 = s0[-pb.ncell:].sum()
         assert abs(got[-pb.ncell:].sum() - X0) > 1e-6 * abs(X0)
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp32n64"])
+@pytest.mark.parametrize("name", ["box2d", "box3d"])
+def test_three_species_fp32_forms(fxmod, name, form):
+    pb, prim = case(name)
+    pb.precision = form
+    s0 = oracle.init_equilibrium(pb, prim)
+    ref, rst = oracle.run(pb, s0, pb.dt, pb.nsteps, nthreads=8)
+    g = fxmod.Grid(pb)
+    g.init_equilibrium(prim)
+    g.step(pb.dt, pb.nsteps)
+    st = g.status()
+    got = g.download()
+    g.close()
+    assert st == 0 and rst == 0
+    H.assert_parity(pb, got, ref, 1e-5, natural=True)
