@@ -32,7 +32,9 @@ __host__ __device__ constexpr int tile_cells(int D, int GL, int NGL) {
   return (D == 2 && GL == 8 && NGL == 2) ? 20 : 256 / GL;
 }
 
-// Tile shape of the stage kernel for D dimensions, GL lanes per cell and NGL groups per lane.
+// Tile shape of the stage kernel for D dimensions, GL lanes per cell and NGL groups per lane.  (In
+// 3-d an 8 x 8 tile of 512 threads, one block per SM, halves the tile-edge share of the 8 x 4 tile
+// but was slower: lognormal3d stage kernel 17.06 ms against 16.44.)
 template <int D, int GL, int NGL> struct TileShape {
   static constexpr int TC = tile_cells(D, GL, NGL);         // cells per tile
   static constexpr int TX = (D == 3) ? (TC >= 16 ? TC / 4 : TC / 2) : TC;

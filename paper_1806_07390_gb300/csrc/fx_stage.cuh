@@ -413,8 +413,8 @@ inline size_t stage_smem_bytes(int G) {
 //   B  each cell is reconstructed once per direction from the four-plane shared ring;
 //   C  the M1/HLL radiation fluxes of the cell's lower faces and of its march face k+1/2, using
 //      the contact speeds of the gas faces (Eq. 19);
-//   D  divergence (gas fluxes from the face buffer), RK combine, store of plane k (and, in the
-//      FP64 form, the interaction).
+//   D  divergence (gas fluxes from the face buffer), RK combine, store of plane k (the
+//      interaction follows in a kernel of its own).
 // B | C and C | D are block barriers; in 3-d also A | B (its face fluxes share shared memory with
 // the face states).  SPH selects the spherical (r, theta) geometry of a 2-d grid at compile time
 // (the host launches the instantiation that matches the grid): the Cartesian kernel carries none
