@@ -128,6 +128,7 @@ struct fx_grid {
   int ptab_nu = 0;
   float ptab_u0 = 0.0f;
   size_t off_ptab = 0;
+  size_t off_hrow = 0;            // FP64 scale-factor rows T_HA, T_HB per direction (curvilinear)
   size_t off_faces = 0;           // gas face buffer [dir][NG+1 (+D-1 with vterms)][faces of dir]
   size_t off_opk = 0;             // opacity factors of the stage input [K, S][cells]
   size_t off_sflag = 0;           // shock flags of the stage input [cells] (carbuncle guard)
@@ -422,15 +423,28 @@ void build_planck_table(const fx_params& P, const GroupConst& gc, const PlanckPa
 // cache line when their temperatures differ, node-major keeps a lane's groups together.
 bool ptab_node_major(const fx_grid* h) { return h->D <= 2 && h->G >= 16; }
 
+// The FP64 scale-factor rows T_HA, T_HB of every direction, as k_init_equilibrium reads them.
+std::vector<double> hrows(const fx_grid* h) {
+  std::vector<double> out;
+  for (int d = 0; d < h->D; ++d) {
+    const size_t np = (size_t)h->P.n[d] + 4;
+    for (int e : {T_HA, T_HB}) out.insert(out.end(), h->tab[d].begin() + e * np, h->tab[d].begin() + (e + 1) * np);
+  }
+  return out;
+}
+
 template <class R> const R* dev_tab(const fx_grid* h, int d) {
   return reinterpret_cast<const R*>(h->ws + h->off_tab[d]);
 }
 
 // ------------------------------------------------------------------ helper kernels
 // Cells c0 .. c0 + nc - 1 from primitive rows of stride ps (row r of cell c at prim[r ps + c - c0]).
+// hrow (null on Cartesian grids): per direction d, the FP64 rows T_HA and T_HB of its table
+// (n_d + 4 entries each, padded), whose products over the directions are the cell's scale factors
+// h_0, h_1: the momentum is covariant, rho vhat_q h_q.
 template <class R>
 __global__ void k_init_equilibrium(const double* prim, int64_t c0, int64_t nc, int64_t ps, R* out, DevGrid g,
-                                   const GroupConst* gcp, PlanckParams pk) {
+                                   const GroupConst* gcp, PlanckParams pk, const double* hrow) {
   const int64_t ncell = g.ncell;
   const int G = g.G, D = g.D, NG = 2 + D;
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -442,9 +456,20 @@ __global__ void k_init_equilibrium(const double* prim, int64_t c0, int64_t nc, i
     double ke = 0.0;
     out[c] = (R)rho;
     if (g.species > 1) out[(int64_t)(NG + (1 + D) * G) * ncell + c] = (R)(rho * prim[(int64_t)(3 + D) * ps + cl]);
+    double hq[3] = {1.0, 1.0, 1.0};
+    if (hrow) {
+      const int64_t i3[3] = {c % g.n[0], (c / g.n[0]) % g.n[1], c / ((int64_t)g.n[0] * g.n[1])};
+      const double* r = hrow;
+      for (int d = 0; d < D; ++d) {
+        const int np = g.n[d] + 4;
+        hq[0] *= r[i3[d] + 2];
+        hq[1] *= r[np + i3[d] + 2];
+        r += 2 * np;
+      }
+    }
     for (int q = 0; q < D; ++q) {
       double vh = prim[(int64_t)(2 + q) * ps + cl];
-      out[(int64_t)(1 + q) * ncell + c] = (R)(rho * vh);
+      out[(int64_t)(1 + q) * ncell + c] = (R)(rho * vh * (q < 2 ? hq[q] : 1.0));
       ke += 0.5 * rho * vh * vh;
     }
     out[(int64_t)(NG - 1) * ncell + c] = (R)(p / (g.gamma - 1.0) + ke);
@@ -997,8 +1022,8 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   const int NS = P.species > 1 ? P.species : 1;  // species
   if (NS > 1) {
     if (!(P.xi0 >= 0.0) || !std::isfinite(P.xi0)) return FX_ERR_ARG;
-    // three species: Cartesian grid, without the velocity terms, 3 ngroups <= 32
-    if (P.geom != FX_CART || P.vterms || NS * P.ngroups > MAXG) return FX_ERR_UNSUPPORTED;
+    // three species: without the velocity terms, 3 ngroups <= 32
+    if (P.vterms || NS * P.ngroups > MAXG) return FX_ERR_UNSUPPORTED;
   }
   const int NCH = NS * P.ngroups;  // radiation channels
   if (!(P.gamma > 1.0) || !(P.c_light > 0.0) || !(P.a_rad > 0.0)) return FX_ERR_ARG;
@@ -1095,6 +1120,11 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   h->off_status = off; off = align_up(off + 64);
   for (int d = 0; d < P.dims; ++d) { h->off_tab[d] = off; off = align_up(off + h->tab[d].size() * h->elem); }
   h->off_gc = off; off = align_up(off + sizeof(GroupConst));
+  {
+    size_t nh = 0;
+    for (int d = 0; d < P.dims; ++d) nh += 2 * (size_t)(P.n[d] + 4);
+    h->off_hrow = off; off = align_up(off + nh * sizeof(double));
+  }
   h->off_vtc = off; off = align_up(off + sizeof(VtConst));
   h->off_ptab = off; off = align_up(off + h->ptab.size() * sizeof(float4));
   {
@@ -1461,6 +1491,11 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
   e = cudaMemcpyAsync(h->ws + h->off_gc, &h->gc, sizeof(GroupConst), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->ws + h->off_vtc, &h->vtc, sizeof(VtConst), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    const std::vector<double> hr = hrows(h);
+    e = cudaMemcpyAsync(h->ws + h->off_hrow, hr.data(), hr.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // hr is a local
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "group constants upload");
   return FX_OK;
@@ -1523,10 +1558,11 @@ fx_status fx_state_init_equilibrium(fx_grid* h, const double* prim, int prim_is_
       ps = nc;
     }
     const int nb = (int)((nc * (h->G + 1) + 255) / 256);
+    const double* hr = h->P.geom != FX_CART ? reinterpret_cast<const double*>(h->ws + h->off_hrow) : nullptr;
     if (h->elem == 8)
-      k_init_equilibrium<double><<<nb, 256, 0, h->stream>>>(dprim, c0, nc, ps, (double*)(h->ws + h->off_A), h->dg, gc, h->pk);
+      k_init_equilibrium<double><<<nb, 256, 0, h->stream>>>(dprim, c0, nc, ps, (double*)(h->ws + h->off_A), h->dg, gc, h->pk, hr);
     else
-      k_init_equilibrium<float><<<nb, 256, 0, h->stream>>>(dprim, c0, nc, ps, (float*)(h->ws + h->off_A), h->dg, gc, h->pk);
+      k_init_equilibrium<float><<<nb, 256, 0, h->stream>>>(dprim, c0, nc, ps, (float*)(h->ws + h->off_A), h->dg, gc, h->pk, hr);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && !prim_is_device) e = cudaStreamSynchronize(h->stream);
@@ -1716,7 +1752,12 @@ extern "C" fx_status fx_state_init_equilibrium_noalloc(fx_grid* h, const double*
   if (state_precision != FX_FP64 && state_precision != FX_FP32) return fail(h, FX_ERR_ARG, "state precision must be FX_FP64 or FX_FP32");
   if (h->sticky != FX_OK) return h->sticky;
   const size_t pbytes = (size_t)(3 + h->D + (h->dg.species > 1 ? 1 : 0)) * h->ncell * sizeof(double);
-  if (pbytes > kNoAllocBytes - kNoAllocGcBytes)
+  // curvilinear grids: the scale-factor rows T_HA, T_HB of each direction, staged after the
+  // primitives straight from the handle's tables (nothing is allocated)
+  size_t hbytes = 0;
+  if (h->P.geom != FX_CART)
+    for (int d = 0; d < h->D; ++d) hbytes += 2 * (size_t)(h->P.n[d] + 4) * sizeof(double);
+  if (pbytes + hbytes > kNoAllocBytes - kNoAllocGcBytes)
     return fail(h, FX_ERR_UNSUPPORTED,
                 "fx_state_init_equilibrium_noalloc: the primitives (" + std::to_string(pbytes) +
                     " bytes) exceed its fixed device staging array (" +
@@ -1743,17 +1784,29 @@ extern "C" fx_status fx_state_init_equilibrium_noalloc(fx_grid* h, const double*
   e = cudaMemcpyAsync(stage, &h->gc, sizeof(GroupConst), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(stage + kNoAllocGcBytes, prim, pbytes, cudaMemcpyHostToDevice, s);
+  if (hbytes) {
+    size_t off = kNoAllocGcBytes + pbytes;
+    for (int d = 0; d < h->D && e == cudaSuccess; ++d) {
+      const size_t np = (size_t)h->P.n[d] + 4;
+      for (int row : {T_HA, T_HB}) {
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(stage + off, h->tab[d].data() + row * np, np * sizeof(double), cudaMemcpyHostToDevice, s);
+        off += np * sizeof(double);
+      }
+    }
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "staging copy");
   const int64_t nt = h->ncell * (h->G + 1);
   const int nb = (int)((nt + 255) / 256);
   const GroupConst* gc = reinterpret_cast<const GroupConst*>(stage);
   const double* dprim = reinterpret_cast<const double*>(stage + kNoAllocGcBytes);
+  const double* dh = hbytes ? reinterpret_cast<const double*>(stage + kNoAllocGcBytes + pbytes) : nullptr;
   if (state_precision == FX_FP64)
     k_init_equilibrium<double><<<nb, 256, 0, s>>>(dprim, 0, h->ncell, h->ncell, static_cast<double*>(state),
-                                                  h->dg, gc, h->pk);
+                                                  h->dg, gc, h->pk, dh);
   else
     k_init_equilibrium<float><<<nb, 256, 0, s>>>(dprim, 0, h->ncell, h->ncell, static_cast<float*>(state),
-                                                 h->dg, gc, h->pk);
+                                                 h->dg, gc, h->pk, dh);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "equilibrium initialisation (no-alloc)");
   return FX_OK;

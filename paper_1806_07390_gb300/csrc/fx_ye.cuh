@@ -1,5 +1,5 @@
 // Three neutrino species (Sec. 3.2; Sec. 5.3 in the core-collapse form): the composition rho Y_e
-// and the two-equation interaction in (T, Y_e), Cartesian grids.
+// and the two-equation interaction in (T, Y_e), on Cartesian and spherical grids.
 //
 // The radiation channels are the groups of the three species (nu_e, anti-nu_e, nu_x), species-
 // major; the gas face and radiation/update kernels transport them like groups.  rho Y_e lives in
@@ -64,7 +64,16 @@ __global__ void __launch_bounds__(256) comp_kernel(const __grid_constant__ Stage
     const R mlo = fr[lf], mhi = fr[uf];
     const R vlo = fr[(uint32_t)NG * nf + lf], vhi = fr[(uint32_t)NG * nf + uf];
     const R flo = mlo * (vlo >= R(0) ? bm : a0), fhi = mhi * (vhi >= R(0) ? b0 : ap);
-    net += (fhi - flo) * R(g.inv_dx[d]);
+    // area/volume factors of the two faces (Eq. 8 with a separable volume element): this
+    // direction's own, times the cross factors of the other directions (1 on Cartesian grids)
+    R cross = R(1);
+#pragma unroll
+    for (int e = 0; e < D; ++e)
+      if (e != d) {
+        const Tab<R> te{A.tab[e], g.n[e] + 4, A.uniform[e] ? A.urow[e] : nullptr};
+        cross *= te(T_XS, bc_pad(e == 0 ? ix : (e == 1 ? iy : iz)));
+      }
+    net += (fhi * tt(T_FR, bc_pad(i)) - flo * tt(T_FL, bc_pad(i))) * cross;
   }
   const R u = A.in[XO + c] - R(A.dt) * net;
   const bool stage2 = A.base != nullptr;
@@ -99,9 +108,22 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   unsigned st = 0;
   double rho = U[c];
   if (rho < g.rho_floor) { rho = g.rho_floor; U[c] = (R)rho; st |= ST_FLOOR; }
+  // scale factors h_0, h_1 of the cell (1 on Cartesian grids): momentum and flux are covariant
+  double hq[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) hq[q] = 1.0;
+  if (g.geom != 0) {
+    const int i3[3] = {(int)(c % (uint32_t)g.n[0]), (int)((c / (uint32_t)g.n[0]) % (uint32_t)g.n[1]), 0};
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const Tab<R> td{A.tab[d], g.n[d] + 4, A.uniform[d] ? A.urow[d] : nullptr};
+      hq[0] *= (double)td(T_HA, bc_pad(i3[d]));
+      if (D > 1) hq[D > 1 ? 1 : 0] *= (double)td(T_HB, bc_pad(i3[d]));
+    }
+  }
   double ke = 0.0;
 #pragma unroll
-  for (int q = 0; q < D; ++q) { const double vh = U[(1 + q) * ncell + c] / rho; ke += 0.5 * rho * vh * vh; }
+  for (int q = 0; q < D; ++q) { const double vh = U[(1 + q) * ncell + c] / (rho * hq[q]); ke += 0.5 * rho * vh * vh; }
   double u_m = U[(NG - 1) * ncell + c] - ke;
   const double u_floor = g.p_floor / (g.gamma - 1.0);
   if (u_m < u_floor) { u_m = u_floor; U[(NG - 1) * ncell + c] = (R)(ke + u_m); st |= ST_FLOOR; }
@@ -232,7 +254,7 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   // flux absorption (Eq. 28) with its momentum and energy feedback (Eqs. 31-32)
   double vcon[D], dm[D], dwork = 0.0;
 #pragma unroll
-  for (int q = 0; q < D; ++q) { vcon[q] = U[(1 + q) * ncell + c] / rho; dm[q] = 0.0; }
+  for (int q = 0; q < D; ++q) { vcon[q] = U[(1 + q) * ncell + c] / (rho * hq[q] * hq[q]); dm[q] = 0.0; }
   const double sig = g.sigma0 * rho;
   const double kT = kpre * hpow(T, g.kap_T_h);
   for (int k = 0; k < G; ++k) {

@@ -338,6 +338,34 @@ def neutrino_2d(nx: int = 512, ny: int = 512, ngroups: int = 8, nsteps: int = 50
     return pb, np.concatenate([prim, _flat(ye)])
 
 
+def neutrino_sph2d(nr: int = 320, nth: int = 64, ngroups: int = 8, nsteps: int = 50, seed: int = 6,
+                   precision: str = "fp64"):
+    """Three neutrino species on the 2-d spherical (r, theta) grid: the log-r atmosphere of
+    spherical_2d (r in [1, 1000], rho ~ r^-2, p ~ r^-2.5, reflecting centre, outflow outer
+    boundary, polar axes) with a slow radial outflow v_r = 0.02 c_s (r / 1000) (1 + 0.1 cos theta),
+    Y_e falling from 0.45 at the centre to 0.2 outside, radiation at 1.2 T in the Y_e-weighted
+    equilibrium, xi0 = 0.02.  prim rows: rho, p, v_r, v_theta, T_rad, Y_e."""
+    x0, x1 = 0.0, math.log(1000.0)
+    pb = Problem(name=f"nusph2d_{nr}x{nth}x{ngroups}g", dims=2, n=(nr, nth, 1),
+                 x_lo=(x0, 0.0, 0.0), x_hi=(x1, math.pi, 1.0),
+                 bc_lo=("reflect", "axis", "periodic"), bc_hi=("outflow", "axis", "periodic"),
+                 ngroups=ngroups, gamma=4.0 / 3.0, kappa0=1e2, kap_rho_exp=2.0, kap_T_exp=-1.5,
+                 kap_eps_exp=-2.0, geom="sph", map1="exp", nsteps=nsteps, species=3, xi0=0.02,
+                 precision=precision)
+    rng = np.random.default_rng(seed)
+    xi = rng.uniform(-1.0, 1.0, size=nth)
+    r = np.exp(pb.cell_centres(0))[None, :]
+    th = pb.cell_centres(1)[:, None]
+    rho = r ** -2.0 * (1.0 + 1e-3 * xi[:, None])
+    p = r ** -2.5 * np.ones((nth, 1))
+    cs = np.sqrt(pb.gamma * p / rho)
+    vr = 0.02 * cs * (r / 1000.0) * (1.0 + 0.1 * np.cos(th))
+    vt = np.zeros_like(rho)
+    ye = 0.2 + 0.25 * np.exp(-np.log(r) / 2.0) * np.ones((nth, 1))
+    pb, prim = _finish(pb, _flat(rho, p, vr, vt, 1.2 * p / rho))
+    return pb, np.concatenate([prim, _flat(ye)])
+
+
 WORKLOADS = {
     "sod1d": sod_1d,
     "kh2d": kh_2d,

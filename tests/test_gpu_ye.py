@@ -104,3 +104,54 @@ def test_three_species_fp32_forms(fxmod, name, form):
     g.close()
     assert st == 0 and rst == 0
     H.assert_parity(pb, got, ref, 1e-5, natural=True)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32n64", 1e-5)])
+def test_three_species_spherical(fxmod, precision, tol):
+    # the spherical grid: composition fluxes with the area/volume factors, covariant momentum
+    # and flux in the interaction, and the initial momentum with the scale factors
+    pb, prim = W.neutrino_sph2d(nr=48, nth=20, ngroups=6, nsteps=6, precision=precision)
+    s0 = oracle.init_equilibrium(pb, prim)
+    ref, rst = oracle.run(pb, s0, pb.dt, pb.nsteps, nthreads=8)
+    g = fxmod.Grid(pb)
+    g.init_equilibrium(prim)
+    init = g.download()
+    g.step(pb.dt, pb.nsteps)
+    st = g.status()
+    got = g.download()
+    g.close()
+    assert st == 0 and rst == 0
+    if precision == "fp64":
+        np.testing.assert_allclose(init, s0, rtol=1e-13, atol=1e-300)
+        H.assert_parity(pb, got, ref, tol, 1e-8)
+    else:
+        H.assert_parity(pb, got, ref, tol, natural=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_spherical_initial_momentum_is_covariant(fxmod, precision):
+    # a spherical grid with flow: the equilibrium initialisation stores rho vhat_q h_q, as the
+    # oracle does (host-staged, device and no-allocation paths)
+    import torch
+    pb, prim = W.spherical_2d(nr=40, nth=16, ngroups=5, precision=precision)
+    prim = np.array(prim, copy=True)
+    prim[2] = 0.1 * np.sqrt(pb.gamma * prim[1] / prim[0])
+    prim[3] = 0.05 * np.sqrt(pb.gamma * prim[1] / prim[0])
+    ref = oracle.init_equilibrium(pb, prim)
+    g = fxmod.Grid(pb)
+    g.init_equilibrium(prim)
+    host = g.download()
+    g.init_equilibrium(torch.from_numpy(np.ascontiguousarray(prim)).cuda())
+    dev = g.download()
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    st = torch.empty(g.nelem, dtype=dt, device="cuda")
+    code = g.L.fx_state_init_equilibrium_noalloc(g.h, np.ascontiguousarray(prim).ctypes.data_as(
+        __import__("ctypes").c_void_p), __import__("ctypes").c_void_p(st.data_ptr()),
+        0 if precision == "fp64" else 1, __import__("ctypes").c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert code == 0
+    na = st.double().cpu().numpy()
+    g.close()
+    tol = 1e-13 if precision == "fp64" else 2e-7
+    for a in (host, dev, na):
+        np.testing.assert_allclose(a, ref, rtol=tol, atol=1e-300)
