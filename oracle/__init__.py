@@ -125,8 +125,6 @@ def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0, r10_full_dt: int
     """Oracle parameters of a problem.  edges (G + 1 group edges), inflow (E_g then the normal
     F_g of a radiation inflow through the lower x boundary) and frozen_gas are the oracle-only
     test aids of reading R28."""
-    if pb.vterms and pb.geom != "cart":
-        raise ValueError("the velocity-dependent terms are built for Cartesian grids only")
     P = OrcParams()
     P.dims = pb.dims
     for d in range(3):

@@ -58,7 +58,13 @@
 //      solver), transverse components those of the reconstructed state on the v* upwind side
 //      (v* >= 0: left), the transverse velocity of the HLLC face state.
 //   R25 <v^i_;j> on Cartesian grids: (v^i at the upper j face - v^i at the lower j face) / dx^j,
-//      the derivative of the linear intracell profile; Gamma = 0.  Curvilinear grids: not built.
+//      the derivative of the linear intracell profile; Gamma = 0.
+//   R34 on the spherical (r, theta) grid: <v^i_;j> = (difference of the coordinate component
+//      v^i = vhat_i/h_i over the two j faces)/dx^j + <Gamma^i_jk> v^k(centroid), v^k from the
+//      linear profile of v^k along k, the <Gamma> those of the geometric sources (R15); face values
+//      with the faces' h on radial faces and the cell's on theta faces; then the physical tensor
+//      V_ab = V^a_b h_a/h_b with the cell's h, including V_phiphi = <Gamma^3_31> v^1 +
+//      <Gamma^3_32> v^2 (the contraction with the physical M1 P and Q, F_phi = 0, in 3 dimensions).
 //   R26 frequency fluxes: the spectral density x_g = X_g / dnu_g of each component of P (E
 //      equation) and Q (F equations) is reconstructed linearly in nu about the group midpoint
 //      with the MC limiter of R1 (zero slope in the first and last group), upwinded per component
@@ -916,9 +922,10 @@ template <class S> static S mc_limit(S sL, S sR, S sC) {
 }
 
 // rad: the cell's radiation variables, group by group (E_g, physical F_g1..F_gD); their time
-// derivatives from these terms are added to out (same layout).  Returns sum_g dE_g/dt.
+// derivatives from these terms are added to out (same layout).  DT >= D is the dimension of the
+// tensors (3 on the spherical grid: its phi-phi components with F_phi = 0).  Returns sum_g dE_g/dt.
 template <class S>
-static S velocity_terms(const orc_params& P, const Groups& gr, int D, const S V[3][3], const S* rad, S* out) {
+static S velocity_terms(const orc_params& P, const Groups& gr, int D, int DT, const S V[3][3], const S* rad, S* out) {
   const int G = gr.G, NRV = 1 + D;
   const double c = P.c_light;
   // spectral densities of the components: xp[g][i][j] = P_ij / dnu_g, xq[g][k][j][i] = Q_kji / dnu_g
@@ -928,7 +935,9 @@ static S velocity_terms(const orc_params& P, const Groups& gr, int D, const S V[
     dnu[g] = gr.edge[g + 1] - gr.edge[g];
     mid[g] = 0.5 * (gr.edge[g] + gr.edge[g + 1]);
     S Pt[3][3], Qt[3][3][3];
-    m1_moments(D, c, rad[g * NRV], &rad[g * NRV + 1], Pt, Qt);
+    S Fp[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < D; ++q) Fp[q] = rad[g * NRV + 1 + q];
+    m1_moments(DT, c, rad[g * NRV], Fp, Pt, Qt);
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) {
         Pc[g * 9 + 3 * i + j] = Pt[i][j];
@@ -960,8 +969,8 @@ static S velocity_terms(const orc_params& P, const Groups& gr, int D, const S V[
   for (int e = 1; e < G; ++e) {
     const double nu = gr.edge[e];
     S sE = 0.0;
-    for (int i = 0; i < D; ++i)
-      for (int j = 0; j < D; ++j) {
+    for (int i = 0; i < DT; ++i)
+      for (int j = 0; j < DT; ++j) {
         const S v = V[i][j];
         const S xe = val(v) < 0.0 ? phi[(e - 1) * 9 + 3 * i + j] : plo[e * 9 + 3 * i + j];
         sE += v * xe;
@@ -969,8 +978,8 @@ static S velocity_terms(const orc_params& P, const Groups& gr, int D, const S V[
     fE[e] = nu * sE;
     for (int j = 0; j < D; ++j) {
       S sF = 0.0;
-      for (int i = 0; i < D; ++i)
-        for (int k = 0; k < D; ++k) {
+      for (int i = 0; i < DT; ++i)
+        for (int k = 0; k < DT; ++k) {
           const S v = V[i][k];
           const S xe = val(v) < 0.0 ? qhi[(e - 1) * 27 + 9 * k + 3 * j + i] : qlo[e * 27 + 9 * k + 3 * j + i];
           sF += v * xe;
@@ -981,8 +990,8 @@ static S velocity_terms(const orc_params& P, const Groups& gr, int D, const S V[
   S dEsum = 0.0;
   for (int g = 0; g < G; ++g) {
     S work = 0.0;
-    for (int i = 0; i < D; ++i)
-      for (int j = 0; j < D; ++j) work += V[i][j] * Pc[g * 9 + 3 * i + j];
+    for (int i = 0; i < DT; ++i)
+      for (int j = 0; j < DT; ++j) work += V[i][j] * Pc[g * 9 + 3 * i + j];
     S dE = (fE[g + 1] - fE[g]) - work;
     out[g * NRV] += dE;
     dEsum += dE;
@@ -1581,14 +1590,56 @@ static void explicit_rhs(const orc_params& P, const Geometry& geo, const Layout&
           S V[3][3];
           for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) V[a][b] = 0.0;
-          for (int b = 0; b < D; ++b) {
-            const size_t iu = L.idx(i + (b == 0), j + (b == 1), k + (b == 2));
-            for (int a = 0; a < D; ++a) V[a][b] = (vface[b][iu * D + a] - vface[b][id * D + a]) / geo.dir[b].dx;
+          int DT = D;
+          if (P.geom == ORC_SPH) {
+            // R34: coordinate components v^1 = vhat_r/h_1, v^2 = vhat_theta/h_2 on the faces, the
+            // linear profiles' differences and centroid values, the volume-averaged connection
+            // coefficients of the geometric sources, then physical components V_ab = V^a_b h_a/h_b
+            const Dir& Rd = geo.dir[0];
+            const Dir& Td = geo.dir[1];
+            const size_t iur = L.idx(i + 1, j, k), iut = L.idx(i, j + 1, k);
+            const double xl = Rd.xf[i], xr = Rd.xf[i + 1];
+            const double h1 = geo.h1c[i], h2 = geo.h2c[i];
+            const S u1l = vface[0][id * D + 0] / drmap(P, xl), u1r = vface[0][iur * D + 0] / drmap(P, xr);
+            const S u2l = vface[0][id * D + 1] / rmap(P, xl), u2r = vface[0][iur * D + 1] / rmap(P, xr);
+            const S t1l = vface[1][id * D + 0] / h1, t1r = vface[1][iut * D + 0] / h1;
+            const S t2l = vface[1][id * D + 1] / h2, t2r = vface[1][iut * D + 1] / h2;
+            const double fr = 0.5 + Rd.m1[i] / Rd.dx, ft = 0.5 + Td.m1[j] / Td.dx;
+            const S v1 = u1l + (u1r - u1l) * fr, v2 = t2l + (t2r - t2l) * ft;  // <v^1>, <v^2>
+            const S V11 = (u1r - u1l) / Rd.dx + geo.G111[i] * v1;
+            const S V12 = (t1r - t1l) / Td.dx + geo.G122[i] * v2;
+            const S V21 = (u2r - u2l) / Rd.dx + geo.G221[i] * v2;
+            const S V22 = (t2r - t2l) / Td.dx + geo.G221[i] * v1 + geo.G222[j] * v2;
+            const S V33 = geo.G221[i] * v1 + geo.G332[j] * v2;
+            V[0][0] = V11;
+            V[0][1] = V12 * (h1 / h2);
+            V[1][0] = V21 * (h2 / h1);
+            V[1][1] = V22;
+            V[2][2] = V33;
+            DT = 3;
+          } else {
+            for (int b = 0; b < D; ++b) {
+              const size_t iu = L.idx(i + (b == 0), j + (b == 1), k + (b == 2));
+              for (int a = 0; a < D; ++a) V[a][b] = (vface[b][iu * D + a] - vface[b][id * D + a]) / geo.dir[b].dx;
+            }
           }
           if (vgrad)
-            for (int a = 0; a < D; ++a)
-              for (int b = 0; b < D; ++b) (*vgrad)[id * 9 + 3 * a + b] = V[a][b];
-          S de = velocity_terms(P, gr, D, V, &R[id * G * NRV], &dU[id * NV + NG]);
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b) (*vgrad)[id * 9 + 3 * a + b] = V[a][b];
+          S de;
+          if (P.geom == ORC_SPH) {
+            // physical flux derivatives, then covariant (dF_j = h_j dFhat_j)
+            std::vector<S> tmp((size_t)G * NRV, S(0.0));
+            de = velocity_terms(P, gr, D, DT, V, &R[id * G * NRV], tmp.data());
+            double hh[3];
+            cell_h(P, geo, i, j, hh);
+            for (int g = 0; g < G; ++g) {
+              dU[id * NV + NG + g * NRV] += tmp[g * NRV];
+              for (int q = 0; q < D; ++q) dU[id * NV + NG + g * NRV + 1 + q] += hh[q] * tmp[g * NRV + 1 + q];
+            }
+          } else {
+            de = velocity_terms(P, gr, D, DT, V, &R[id * G * NRV], &dU[id * NV + NG]);
+          }
           const double Vol = geo.dir[0].vol[i] * geo.dir[1].vol[j] * geo.dir[2].vol[k];
           wcell.push_back(Vol * val(de));
         }
@@ -2010,7 +2061,7 @@ double orc_vterms(const orc_params* P, const double* V, const double* rad, doubl
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) Vm[a][b] = (a < D && b < D) ? V[3 * a + b] : 0.0;
   for (int q = 0; q < gr.G * (1 + D); ++q) out[q] = 0.0;
-  return velocity_terms(*P, gr, D, Vm, rad, out);
+  return velocity_terms(*P, gr, D, D, Vm, rad, out);
 }
 // <v^i_;j> of every cell of a state (R24-R25), out[cell][3][3] (x-fastest cells).
 int orc_vgrad(const orc_params* P, const double* state, double* out) {

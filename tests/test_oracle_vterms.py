@@ -268,6 +268,69 @@ def test_energy_budget_closes_with_the_velocity_terms():
     assert abs(t0[4] - t1[4] - bud[4] - bud[6] + bud[7] + bud[8]) <= 1e-14 * abs(t0[4])
 
 
+# ------------------------------------------------------------------ spherical grid (R34)
+def sph_problem(nr, nth, G=2, vterms=1, c=50.0):
+    return W.Problem(name="sphv", dims=2, n=(nr, nth, 1), x_lo=(0.0, 0.3, 0), x_hi=(math.log(10.0), math.pi - 0.3, 1),
+                     bc_lo=("outflow",) * 3, bc_hi=("outflow",) * 3, ngroups=G, gamma=4 / 3, kappa0=0.0,
+                     kap_rho_exp=0.0, kap_T_exp=0.0, kap_eps_exp=0.0, c_light=c, couple=0, geom="sph",
+                     map1="exp", vterms=vterms, eps_min=1e-2, eps_max=40.0)
+
+
+def sph_state(pb, vr, vt):
+    nr, nth = pb.n[0], pb.n[1]
+    N = nr * nth
+    prim = np.stack([np.ones(N), np.ones(N), np.ravel(vr), np.ravel(vt), np.ones(N)])
+    return oracle.init_equilibrium(pb, prim)
+
+
+def test_spherical_velocity_gradient():
+    # Homologous flow v = H r: grad v = H I (rr, theta-theta and phi-phi entries), exact up to
+    # the reconstruction of v*; a uniform Cartesian flow v = v0 z: grad v = 0, every component
+    # converging at second order in L1 (the TVD clip at the extremum of v_theta at the equator is
+    # a local first-order error there)
+    H, v0 = 0.3, 0.4
+    ehom, euni = [], []
+    for nr, nth in ((32, 16), (64, 32), (128, 64)):
+        pb = sph_problem(nr, nth)
+        r = np.exp(pb.cell_centres(0))[None, :] * np.ones((nth, 1))
+        th = pb.cell_centres(1)[:, None] * np.ones((1, nr))
+        vg = oracle.vgrad(pb, sph_state(pb, H * r, 0 * r)).reshape(nth, nr, 3, 3)[3:-3, 3:-3]
+        ehom.append(max(np.abs(vg[..., a, a] / H - 1).max() for a in range(3)))
+        assert np.abs(vg[..., 0, 1]).max() == 0.0 and np.abs(vg[..., 1, 0]).max() == 0.0
+        vg = oracle.vgrad(pb, sph_state(pb, v0 * np.cos(th), -v0 * np.sin(th))).reshape(nth, nr, 3, 3)[3:-3, 3:-3]
+        euni.append(np.abs(vg).mean() / v0)
+    assert ehom[-1] < 2e-4 and ehom[0] / ehom[1] > 3.5 and ehom[1] / ehom[2] > 3.5, ehom
+    assert euni[0] / euni[1] > 3.0 and euni[1] / euni[2] > 3.0, euni
+
+
+def test_spherical_homologous_expansion():
+    # A uniform Planck field in homologous flow v = H r (frozen gas, no opacity): the comoving
+    # field stays uniform, cools as exp(-4 H t) (the divergence of vE gives 3 H, the work term
+    # v:P = H E) and redshifts as E_nu(t) = exp(-3 H t) E_nu(0)(nu exp(H t)).  Measured before
+    # light from either boundary reaches the cells at 3 < r < 6.
+    H, t_end = 0.5, 0.1
+    etot, espec = [], []
+    for nr, nth, G in ((32, 8, 24), (64, 16, 48)):
+        pb = sph_problem(nr, nth, G=G, c=20.0)
+        r = np.exp(pb.cell_centres(0))
+        s = sph_state(pb, H * r[None, :] * np.ones((nth, 1)), np.zeros((nth, nr)))
+        dt = 0.2 * min(math.log(10) / nr, 0.3 * (math.pi - 0.6) / nth) / pb.c_light
+        nst = int(math.ceil(t_end / dt))
+        out, st = oracle.run(pb, s, t_end / nst, nst, nthreads=8, frozen_gas=1)
+        assert st == 0
+        N = pb.ncell
+        E0 = s[4 * N:4 * N + N * G].reshape(nth, nr, G)
+        E1 = out[4 * N:4 * N + N * G].reshape(nth, nr, G)
+        e = log_edges(pb)
+        b = math.exp(H * t_end)
+        ref = planck_bands(pb, e, scale=b) / b * math.exp(-3 * H * t_end)
+        Em = E1[nth // 2][(r > 3.0) & (r < 6.0)]
+        etot.append(np.abs(Em.sum(-1) / E0[0, 0].sum() / math.exp(-4 * H * t_end) - 1).max())
+        espec.append((np.abs(Em - ref[None, :]).max(-1) / ref.max()).max())
+    assert etot[1] < 1e-4 and etot[0] / etot[1] > 3.5, etot
+    assert espec[1] < 3e-3 and espec[0] / espec[1] > 2.5, espec
+
+
 # ------------------------------------------------------------------ Doppler-shift test (Sec. 9)
 def doppler_run(ng_lin):
     """Sec. 9's Doppler-shift test (reading R28): 50 cells on [0, 10] cm, rho = 1, no opacity,
