@@ -98,8 +98,11 @@ enum { FX_NTOTALS = 6, FX_NBUDGET = 9 };
  *                      nu Q (Q: the M1 heat-flux tensor, Q_ijk = cE [(f-q)/2 (n_i d_jk + n_j d_ik
  *                      + n_k d_ij) + (5q-3f)/2 n_i n_j n_k], q = f (2 + 3 chi)/5), with
  *                      <v^i_;j> from the face velocities (v* normal, the upwind state's
- *                      transverse components).  Cartesian grids only (FX_ERR_UNSUPPORTED
- *                      otherwise); the adjoint returns FX_ERR_UNSUPPORTED with it.  0 = off.
+ *                      transverse components).  Cartesian grids: the face differences over dx.
+ *                      Spherical grids: the coordinate components' differences plus the
+ *                      volume-averaged connection coefficients times the centroid velocity, in
+ *                      physical components with the phi-phi entry (3-d tensors, F_phi = 0).
+ *                      The adjoint returns FX_ERR_UNSUPPORTED with it.  0 = off.
  *   species, xi0       0 or 1: one radiation species (photons).  3: neutrinos (nu_e, anti-nu_e,
  *                      nu_x), each with the ngroups groups (3 ngroups <= 32 channels, species-
  *                      major), the composition rho Y_e advected with the gas, and the two-equation
@@ -107,8 +110,8 @@ enum { FX_NTOTALS = 6, FX_NBUDGET = 9 };
  *                      w_s(Y_e) B_g(T) with w = 2 Y_e, 2 (1 - Y_e), 1 (synthetic emissivities,
  *                      every species with the opacity law above), and the lepton number per unit
  *                      energy xi = -xi0/eps_g, +xi0/eps_g, 0, so that rho Y_e - sum xi E is
- *                      conserved.  Cartesian grids only, without vterms, budgets, boundary
- *                      layers or the adjoint (FX_ERR_UNSUPPORTED); in the FP32 forms the
+ *                      conserved.  Cartesian and spherical grids, without vterms, budgets,
+ *                      boundary layers or the adjoint (FX_ERR_UNSUPPORTED); in the FP32 forms the
  *                      interaction computes in FP64 and stores the FP32 state.
  */
 typedef struct {

@@ -216,7 +216,7 @@ struct orc_params {
                             // the inconsistent alternative to reading R10 (the R10 pin must fail it)
   int riemann;              // gas Riemann solver: ORC_HLLC (default), ORC_HLLE or ORC_LLF (R21)
   double shock_guard;       // carbuncle guard (R22): pressure-jump threshold; 0 = off
-  int vterms;               // 1: the velocity-dependent radiation terms (R23-R27; Cartesian)
+  int vterms;               // 1: the velocity-dependent radiation terms (R23-R27, R34)
   int frozen_gas;           // test aid (R28): the gas state is held fixed
   const double* edges;      // test aid (R28): G + 1 group edges, or null for the log spacing
   const double* inflow;     // test aid (R28): with bc ORC_INFLOW, the ghosts' E_g (G values) and

@@ -274,7 +274,7 @@ void build_table(const fx_params& P, int d, std::vector<double>& T) {
     put(T_VOL, ip, mo[ip + 1].w0);
     const double xl_abs = xc[ip + 1] - 0.5 * h, xr_abs = xc[ip + 1] + 0.5 * h;
     const double ell = h * (mu1[1] - mu1[0]);  // centroid gap of the lower face
-    for (int e : {T_XS, T_X1, T_X2, T_XH, T_HA, T_HB}) put(e, ip, 1.0);
+    for (int e : {T_XS, T_X1, T_X2, T_XH, T_HA, T_HB, T_QI, T_RI}) put(e, ip, 1.0);
     for (int e : {T_GA, T_GB, T_GC}) put(e, ip, 0.0);
     if (P.geom == FX_CART || d >= 2) {
       for (int e : {T_FL, T_FR, T_FL1, T_FR1, T_FL2, T_FR2}) put(e, ip, 1.0 / h);
@@ -292,6 +292,10 @@ void build_table(const fx_params& P, int d, std::vector<double>& T) {
       put(T_FL2, ip, rl * rl * rl / Vr);
       put(T_FR2, ip, rr * rr * rr / Vr);
       put(T_ELL, ip, ell * ql);
+      // (interior faces have r > 0: the host rejects grids that reach r = 0; a ghost face of an
+      // identity map may sit at r = 0, a row the velocity terms never read)
+      put(T_QI, ip, 1.0 / ql);
+      put(T_RI, ip, rl != 0.0 ? 1.0 / rl : 0.0);
       // theta faces of this radial cell: Int r dr/dx1, Int r (dr/dx1)^2, Int r^2 dr/dx1 over it
       auto gl = [&](auto f) {  // 8-point Gauss-Legendre on the cell
         static const double xg[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
@@ -1017,7 +1021,6 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   if (P.rad_recon_order != 1 && P.rad_recon_order != 2) return FX_ERR_ARG;
   if (P.riemann < FX_HLLC || P.riemann > FX_LLF || !(P.shock_guard >= 0.0)) return FX_ERR_ARG;
   if (P.vterms != 0 && P.vterms != 1) return FX_ERR_ARG;
-  if (P.vterms && P.geom != FX_CART) return FX_ERR_UNSUPPORTED;  // built for Cartesian grids
   if (P.species != 0 && P.species != 1 && P.species != 3) return FX_ERR_ARG;
   const int NS = P.species > 1 ? P.species : 1;  // species
   if (NS > 1) {

@@ -43,6 +43,9 @@ enum TabEntry {
   // Volume-averaged connection coefficients carried by this direction (Appendix D): radial
   // <Gamma^1_11>, <Gamma^2_21> = <Gamma^3_31>, <Gamma^1_22>; polar <Gamma^2_22>, <Gamma^3_32>.
   T_GA, T_GB, T_GC,
+  // Radial map at the cell's lower face (spherical radial direction; 1 elsewhere): 1 / (dr/dx1)
+  // and 1 / r, the factors that turn a face's physical velocity into coordinate components.
+  T_QI, T_RI,
   NTAB
 };
 

@@ -126,11 +126,11 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
     if (e != cudaSuccess) return e;
   }
   // the velocity-dependent radiation terms of the stage input, added to the explicit update
-  // before the interaction (one thread per cell)
+  // before the interaction (one lane per group)
   if (a.g.vterms) {
     constexpr int CPB = VT_THREADS / GP;  // cells of one x row per block, GP lanes each
     const dim3 vg((unsigned)(a.g.n[1] * a.g.n[2]), (unsigned)((a.g.n[0] + CPB - 1) / CPB), 1);
-    vterm_kernel<R, D, GP><<<vg, VT_THREADS, 0, s>>>(a);
+    vterm_kernel<R, D, GP, SPH><<<vg, VT_THREADS, 0, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

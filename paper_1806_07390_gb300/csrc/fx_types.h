@@ -40,8 +40,8 @@ struct DevGrid {
   int rad_order;  // radiation reconstruction: 1 linear with the MC limiter, 2 the gas's parabola
   int riemann;        // gas solver: 0 HLLC, 1 HLLE, 2 local Lax-Friedrichs
   double shock_guard; // carbuncle guard pressure-jump threshold (0: off)
-  int vterms;         // velocity-dependent radiation terms on (Cartesian grids)
-  double inv_dx[3];   // 1 / cell width per direction (Cartesian)
+  int vterms;         // velocity-dependent radiation terms on
+  double inv_dx[3];   // 1 / cell width per direction (in x, the coordinate)
   int species;        // 1, or 3: G = 3 Gs channels, composition rho Y_e, (T, Y_e) interaction
   int Gs;             // groups per species (channel k is group k % Gs of species k / Gs)
   double xi0;         // lepton number per unit energy of the nu_e / anti-nu_e channels

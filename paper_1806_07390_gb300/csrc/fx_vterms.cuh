@@ -1,7 +1,7 @@
 // Velocity-dependent radiation terms (Sec. 3.2, the group form of the moment equations; Sec. 5.2;
-// Step 2 of Sec. 6), Cartesian grids: one lane per group, after the radiation/update kernel and
-// before the interaction.  For the stage input U and the cell's volume-averaged velocity gradient
-// V_ij = <v^i_;j>, the terms are
+// Step 2 of Sec. 6), Cartesian and spherical grids: one lane per group, after the radiation/update
+// kernel and before the interaction.  For the stage input U and the cell's volume-averaged
+// velocity gradient V_ij = <v^i_;j>, the terms are
 //   dE_g/dt   = -V_ij P_g^ij + V_ij [(nu P^ij)_{g+1/2} - (nu P^ij)_{g-1/2}],
 //   dF_gj/dt  = -V_ij F_g^i  + V_ik [(nu Q^kji)_{g+1/2} - (nu Q^kji)_{g-1/2}],
 // with the M1 pressure tensor P, the heat-flux tensor Q = cE [(f - q)/2 (n d + d n + ...) +
@@ -12,9 +12,10 @@
 // the stage's explicit operator, so the kernel adds w dt (terms of U) to the stage output in place
 // (w = 1 in stage 1, 1/2 in stage 2: the weights of the SSP-RK2 combination).
 //
-// V_ij = (v^i on the upper j face - v^i on the lower j face) / dx_j, from the face velocities the
-// gas face kernel stores: the contact speed v* as the normal component and the transverse
-// components of the reconstructed state on the v* upwind side.
+// On Cartesian grids V_ij = (v^i on the upper j face - v^i on the lower j face) / dx_j, from the
+// face velocities the gas face kernel stores: the contact speed v* as the normal component and the
+// transverse components of the reconstructed state on the v* upwind side (the spherical form is
+// described at the kernel).
 #pragma once
 #include "fx_stage.cuh"
 
@@ -126,11 +127,22 @@ inline void vt_constants(const double* edge, int G, VtConst& v) {
 // 256/GP consecutive cells of one x row (grid: rows y, z by x tiles): each lane forms its
 // group's P and Q components and spectral densities, takes its neighbours' through warp
 // shuffles for the limited slopes, and the flux through its upper edge from the lane above.
+//
+// SPH: the 2-d spherical (r, theta) grid.  The tensors are those of 3 dimensions (DT = 3, with
+// F_phi = 0 and the V_phiphi entry), in physical components: the state's covariant flux
+// F_q = h_q Fhat_q (cell scale factors) is divided by h_q on entry, and the physical derivative
+// of Fhat_q multiplied by h_q on exit.  The gradient takes the coordinate components
+// v^1 = vhat_r / h_1, v^2 = vhat_theta / h_2 on the faces (radial faces: the face's dr/dx1 and r;
+// theta faces: the cell's h), differences them over the cell, adds the volume-averaged
+// connection coefficients times the coordinate velocity at the centroid (linear profile between
+// the two faces), and turns V^a_b into physical components V^a_b h_a / h_b.
 constexpr int VT_THREADS = 256;
 
-template <class R, int D, int GP>
+template <class R, int D, int GP, bool SPH>
 __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant__ StageArgs<R> A) {
-  using VC = VtComp<D>;
+  static_assert(!SPH || D == 2, "the spherical grid is 2-d");
+  constexpr int DT = SPH ? 3 : D;  // dimension of the tensors
+  using VC = VtComp<DT>;
   constexpr int NG = 2 + D, NP = VC::NP, NC = VC::NC, CPB = VT_THREADS / GP;
   const DevGrid& g = A.g;
   const int G = g.G;
@@ -142,8 +154,8 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
   const int iy = (int)(blockIdx.x % (unsigned)g.n[1]), iz = (int)(blockIdx.x / (unsigned)g.n[1]);
   // 32-bit offsets: the host keeps every state offset below 2^32
   const uint32_t cc = ((uint32_t)iz * g.n[1] + (uint32_t)iy) * g.n[0] + (uint32_t)ix;
-  // velocity gradient from the face velocities (rows NG + ((i - j) mod D) of direction j)
-  R V[D][D];
+  // face velocities: component i of a face of direction j sits in row NG + ((i - j) mod D)
+  R vl[D][D], vu[D][D];  // [j][i]: lower / upper face of direction j, component i
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     const uint32_t ex = (uint32_t)(g.n[0] + (j == 0)), ey = (uint32_t)(g.n[1] + (j == 1));
@@ -151,32 +163,76 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
     const uint32_t lf = ((uint32_t)iz * ey + (uint32_t)iy) * ex + (uint32_t)ix;
     const uint32_t uf = lf + (j == 0 ? 1u : (j == 1 ? ex : ex * ey));
     const R* fr = A.faces + (uint32_t)A.face_off[j];
-    const R idx = R(g.inv_dx[j]);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       const uint32_t row = (uint32_t)(NG + (i - j + D) % D) * nf;
-      V[i][j] = (__ldg(fr + row + uf) - __ldg(fr + row + lf)) * idx;
+      vl[j][i] = __ldg(fr + row + lf);
+      vu[j][i] = __ldg(fr + row + uf);
     }
   }
-  // this lane's group of the stage input
+  R V[DT][DT];
+#pragma unroll
+  for (int i = 0; i < DT; ++i)
+#pragma unroll
+    for (int j = 0; j < DT; ++j) V[i][j] = R(0);
+  R h[DT];  // cell scale factors of the flux components (1 on Cartesian grids)
+#pragma unroll
+  for (int q = 0; q < DT; ++q) h[q] = R(1);
+  if constexpr (SPH) {
+    const Tab<R> tr{A.tab[0], g.n[0] + 4, A.uniform[0] ? A.urow[0] : nullptr};
+    const Tab<R> tq{A.tab[1], g.n[1] + 4, A.uniform[1] ? A.urow[1] : nullptr};
+    const int ipr = ix + 2, ipt = iy + 2;
+    const R idr = R(g.inv_dx[0]), idt = R(g.inv_dx[1]);
+    h[0] = tr(T_HA, ipr);
+    h[1] = tr(T_HB, ipr);
+    const R ih1 = R(1) / h[0], ih2 = R(1) / h[1];
+    // coordinate components on the radial faces (the faces' own dr/dx1 and r) ...
+    const R u1l = vl[0][0] * tr(T_QI, ipr), u1r = vu[0][0] * tr(T_QI, ipr + 1);
+    const R u2l = vl[0][1] * tr(T_RI, ipr), u2r = vu[0][1] * tr(T_RI, ipr + 1);
+    // ... and on the theta faces (the cell's h)
+    const R t1l = vl[1][0] * ih1, t1r = vu[1][0] * ih1;
+    const R t2l = vl[1][1] * ih2, t2r = vu[1][1] * ih2;
+    // centroid values of the linear profiles: the centroid lies (c - x_L) / dx along the cell
+    const R v1 = u1l + (u1r - u1l) * (-tr(T_DL, ipr) * idr);
+    const R v2 = t2l + (t2r - t2l) * (-tq(T_DL, ipt) * idt);
+    const R g111 = tr(T_GA, ipr), g221 = tr(T_GB, ipr), g122 = tr(T_GC, ipr);
+    const R g222 = tq(T_GA, ipt), g332 = tq(T_GB, ipt);
+    V[0][0] = (u1r - u1l) * idr + g111 * v1;
+    V[0][1] = ((t1r - t1l) * idt + g122 * v2) * (h[0] * ih2);
+    V[1][0] = ((u2r - u2l) * idr + g221 * v2) * (h[1] * ih1);
+    V[1][1] = (t2r - t2l) * idt + g221 * v1 + g222 * v2;
+    V[2][2] = g221 * v1 + g332 * v2;
+  } else {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const R idx = R(g.inv_dx[j]);
+#pragma unroll
+      for (int i = 0; i < D; ++i) V[i][j] = (vu[j][i] - vl[j][i]) * idx;
+    }
+  }
+  // this lane's group of the stage input (physical flux components)
   const uint32_t rad = (uint32_t)NG * ncell, gid = cc * (uint32_t)G + (uint32_t)lane,
                  vstr = ncell * (uint32_t)G;
-  R E = R(0), F[D];
+  R E = R(0), F[DT];
 #pragma unroll
-  for (int q = 0; q < D; ++q) F[q] = R(0);
+  for (int q = 0; q < DT; ++q) F[q] = R(0);
   if (act) {
     E = A.in[rad + gid];
 #pragma unroll
     for (int q = 0; q < D; ++q) F[q] = A.in[rad + (uint32_t)(1 + q) * vstr + gid];
+    if constexpr (SPH) {
+#pragma unroll
+      for (int q = 0; q < D; ++q) F[q] = F[q] / h[q];
+    }
   }
   R x[NC];
-  vt_moments<R, D>(A.k(R(0)).c, E, F, x);
+  vt_moments<R, DT>(A.k(R(0)).c, E, F, x);
   // work terms V_ij P^ij and sum_i V_ij F^i
   R wE = R(0), wF[D];
 #pragma unroll
-  for (int i = 0; i < D; ++i)
+  for (int i = 0; i < DT; ++i)
 #pragma unroll
-    for (int j = 0; j < D; ++j) wE += V[i][j] * x[vt_sym2(i, j, D)];
+    for (int j = 0; j < DT; ++j) wE += V[i][j] * x[vt_sym2(i, j, DT)];
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     R s2 = R(0);
@@ -211,10 +267,10 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
   if (act && lane > 0) {
     const R el = A.gc->edge_of(lane, R(0));
 #pragma unroll
-    for (int i = 0; i < D; ++i)
+    for (int i = 0; i < DT; ++i)
 #pragma unroll
-      for (int j = 0; j < D; ++j) {
-        const int m = vt_sym2(i, j, D);
+      for (int j = 0; j < DT; ++j) {
+        const int m = vt_sym2(i, j, DT);
         fE += V[i][j] * (V[i][j] < R(0) ? hp[m] : x[m]);
       }
     fE *= el;
@@ -222,10 +278,10 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
     for (int j = 0; j < D; ++j) {
       R sF = R(0);
 #pragma unroll
-      for (int i = 0; i < D; ++i)
+      for (int i = 0; i < DT; ++i)
 #pragma unroll
-        for (int kk = 0; kk < D; ++kk) {
-          const int m = NP + vt_sym3(kk, j, i, D);
+        for (int kk = 0; kk < DT; ++kk) {
+          const int m = NP + vt_sym3(kk, j, i, DT);
           sF += V[i][kk] * (V[i][kk] < R(0) ? hp[m] : x[m]);
         }
       fF[j] = sF * el;
@@ -252,22 +308,30 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       R* of = A.out + rad + (uint32_t)(1 + j) * vstr + gid;
-      const R f = *of + wdt * (uF[j] - fF[j] - wF[j]);
+      R dF = uF[j] - fF[j] - wF[j];
+      if constexpr (SPH) dF *= h[j];  // covariant component
+      const R f = *of + wdt * dF;
       bad |= !isfinite(f);
       *of = f;
     }
   }
   if (bad) atomicOr(A.status, ST_NONFINITE);
   if (A.budget != nullptr) {
-    // radiation energy the terms add, weighted as the RK combination weighs this stage
-    double e = act ? (double)dE : 0.0;
+    // radiation energy the terms add, weighted as the RK combination weighs this stage; each
+    // lane weighs its own cell's volume (a warp spans 32/GP cells, of different volumes on the
+    // spherical grid)
+    double vol = 1.0;
+    if constexpr (SPH) {
+      vol = (double)Tab<R>{A.tab[0], g.n[0] + 4, A.uniform[0] ? A.urow[0] : nullptr}(T_VOL, ix + 2) *
+            (double)Tab<R>{A.tab[1], g.n[1] + 4, A.uniform[1] ? A.urow[1] : nullptr}(T_VOL, iy + 2);
+    } else {
+      for (int d = 0; d < D; ++d) vol /= g.inv_dx[d];
+    }
+    double e = act ? (double)dE * vol : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if ((threadIdx.x & 31) == 0) {
-      double vol = 1.0;
-      for (int d = 0; d < D; ++d) vol /= g.inv_dx[d];
-      atomicAdd(A.budget + (blockIdx.x % BUDGET_SLOTS) * NBUDGET + 8, e * vol * A.bw_flux);
-    }
+    if ((threadIdx.x & 31) == 0)
+      atomicAdd(A.budget + (blockIdx.x % BUDGET_SLOTS) * NBUDGET + 8, e * A.bw_flux);
   }
 }
 

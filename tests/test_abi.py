@@ -68,8 +68,8 @@ def test_create_validates_parameters(L):
 
 
 def test_velocity_terms_parameters(L):
-    # vterms: 0 or 1; Cartesian grids only; one more kernel per stage; the face buffer holds the
-    # transverse face velocities on top of the fluxes and contact speeds
+    # vterms: 0 or 1; Cartesian and spherical grids; one more kernel per stage; the face buffer
+    # holds the transverse face velocities on top of the fluxes and contact speeds
     pb, _ = W.kh_2d(nx=16, ny=12, ngroups=4)
     st0, h0, ws0 = create(pb)
     pb.vterms = 1
@@ -83,8 +83,13 @@ def test_velocity_terms_parameters(L):
     pb.vterms = 2
     assert create(pb)[0] == -1
     pb2, _ = W.spherical_2d(nr=16, nth=8, ngroups=4)
+    st2, h2, _ = create(pb2)
     pb2.vterms = 1
-    assert create(pb2)[0] == -7  # FX_ERR_UNSUPPORTED
+    st3, h3, _ = create(pb2)
+    assert st2 == 0 and st3 == 0
+    assert L.fx_launches_per_step(h3) == L.fx_launches_per_step(h2) + 2
+    L.fx_grid_destroy(h2)
+    L.fx_grid_destroy(h3)
 
 
 def test_three_species_parameters(L):
@@ -232,7 +237,7 @@ def test_spherical_tables_match_oracle_geometry(L, map1):
     names = ["WA0", "WA1", "WA2", "WB0", "WB1", "WB2", "SL2", "TL2", "SR2", "TR2", "AL0", "AL1",
              "AL2", "AR0", "AR1", "AR2", "RHL", "RHR", "IL", "IR", "IC", "DL", "DR", "FL", "FR",
              "ELL", "VOL", "FL1", "FR1", "FL2", "FR2", "XS", "X1", "X2", "XH", "HA", "HB", "GA",
-             "GB", "GC"]
+             "GB", "GC", "QI", "RI"]
     e = {nm: i for i, nm in enumerate(names)}
     assert ntab == len(names)
     vol_r, _, _ = oracle.geometry(pb, 0)
@@ -250,4 +255,9 @@ def test_spherical_tables_match_oracle_geometry(L, map1):
     rf = np.exp(xf) if map1 == "exp" else pb.map_rt * np.sinh(xf / pb.map_rt)
     np.testing.assert_allclose(T[0][e["FL"]], rf[:-1] ** 2 / vol_r, rtol=1e-13)
     np.testing.assert_allclose(T[0][e["FR2"]], rf[1:] ** 3 / vol_r, rtol=1e-13)
+    # the radial map at the lower faces for the velocity gradient: 1 / (dr/dx1) and 1 / r
+    qf = np.exp(xf) if map1 == "exp" else np.cosh(xf / pb.map_rt)
+    np.testing.assert_allclose(T[0][e["QI"]], 1.0 / qf[:-1], rtol=1e-14)
+    np.testing.assert_allclose(T[0][e["RI"]], 1.0 / rf[:-1], rtol=1e-14)
+    assert np.all(T[1][e["QI"]] == 1.0) and np.all(T[1][e["RI"]] == 1.0)
     L.fx_grid_destroy(h)

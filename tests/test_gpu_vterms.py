@@ -5,7 +5,8 @@ Bars as for the rest of the path: FP64 relative L1 <= 1e-10 and max-norm <= 1e-8
 FP32 forms at 1e-4 against each field's natural scale.  The inputs have strong velocity
 gradients: a shear layer (kh2d) and random states whose velocities change sign from cell to
 cell, on periodic, outflow and reflecting boundaries, in 1, 2 and 3 dimensions, with odd group
-counts and the largest group count (32).
+counts and the largest group count (32); on the spherical (r, theta) grid (log-r and sinh radial
+maps, reflecting inner boundary, both polar axes) with random velocities and fluxes.
 """
 import numpy as np
 import pytest
@@ -118,3 +119,64 @@ def test_velocity_terms_have_no_adjoint(fxmod):
         g.adjoint_forward(ws, pb.dt, 2, 1)
     assert ei.value.status == -7
     g.close()
+
+
+def sph_case(map1, precision, seed=31):
+    """Spherical grid with random physical velocities (up to 0.3 of the sound speed, changing
+    sign from cell to cell) and random physical fluxes (|F| up to 0.6 cE), stored covariant."""
+    pb, prim = W.spherical_2d(nr=40, nth=22, ngroups=9, nsteps=3, precision=precision, map1=map1)
+    pb.vterms = 1
+    rng = np.random.default_rng(seed)
+    N, G = pb.ncell, pb.ngroups
+    prim = np.array(prim, copy=True)
+    cs = np.sqrt(pb.gamma * prim[1] / prim[0])
+    prim[2] = rng.uniform(-0.3, 0.3, N) * cs
+    prim[3] = rng.uniform(-0.3, 0.3, N) * cs
+    s = oracle.init_equilibrium(pb, prim)
+    # the cell scale factors: the covariant momentum of rho = 1, vhat = (1, 1)
+    unit = np.array(prim, copy=True)
+    unit[0], unit[2], unit[3] = 1.0, 1.0, 1.0
+    hs = oracle.init_equilibrium(pb, unit)[N:3 * N].reshape(2, N)
+    E = s[4 * N:4 * N + N * G].reshape(N, G)
+    ang = rng.uniform(0, 2 * np.pi, (N, G))
+    mag = rng.uniform(0, 0.6, (N, G)) * pb.c_light * E
+    s[4 * N + N * G:4 * N + 2 * N * G] = (hs[0][:, None] * mag * np.cos(ang)).ravel()
+    s[4 * N + 2 * N * G:] = (hs[1][:, None] * mag * np.sin(ang)).ravel()
+    return pb, s
+
+
+@pytest.mark.parametrize("map1", ["exp", "sinh"])
+def test_velocity_terms_spherical_fp64(fxmod, map1):
+    pb, s = sph_case(map1, "fp64")
+    got, ref = run_both(fxmod, pb, s)
+    H.assert_parity(pb, got, ref, FP64_L1, FP64_MAX)
+    pb.vterms = 0
+    plain, _ = oracle.run(pb, s, pb.dt, pb.nsteps, nthreads=8)
+    rad = slice(4 * pb.ncell, None)
+    assert np.abs(plain[rad] - ref[rad]).max() > 1e3 * FP64_MAX * np.abs(ref[rad]).max()
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp32n64"])
+def test_velocity_terms_spherical_fp32_forms(fxmod, form):
+    pb, s = sph_case("exp", form)
+    got, ref = run_both(fxmod, pb, s)
+    H.assert_parity(pb, got, ref, 1e-4, natural=True)
+
+
+def test_velocity_terms_spherical_budget(fxmod):
+    # the radiation energy the terms add on the spherical grid (cell volumes from the geometry)
+    pb, s = sph_case("exp", "fp64")
+    _, rst, rbud = oracle.run_budget(pb, s, pb.dt, 2, nthreads=8)
+    g = fxmod.Grid(pb)
+    g.upload(s)
+    t0 = g.totals()
+    g.budgets_enable(True)
+    g.step(pb.dt, 2)
+    assert g.status() == 0 and rst == 0
+    bud = g.budgets()
+    t1 = g.totals()
+    g.close()
+    assert abs(bud[8]) > 1e-8 * abs(t0[4])
+    assert abs(bud[8] - rbud[8]) <= 1e-10 * abs(rbud[8]), (bud[8], rbud[8])
+    # energy closes with it (the boundary fluxes, absorption work, floor and velocity terms)
+    assert abs(t0[4] - t1[4] - bud[4] - bud[6] + bud[7] + bud[8]) <= 1e-13 * abs(t0[4])

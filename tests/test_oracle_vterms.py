@@ -331,6 +331,58 @@ def test_spherical_homologous_expansion():
     assert espec[1] < 3e-3 and espec[0] / espec[1] > 2.5, espec
 
 
+def test_lab_frame_flux_continuity_at_a_transparent_shock():
+    # Sec. 9's continuity test: a steady point source (a radial beam entering at the inner
+    # boundary), no opacity, and the imposed core-collapse-like velocity field with a standing
+    # shock at r_s = 1 (v = -0.1 v_s r / r_s inside, v = -v_s (sqrt(r_max/r) - 1)/(sqrt(r_max/r_s)
+    # - 1) outside, v_s = 0.1 c, r_max = 10 r_s; frozen gas).  The comoving r^2 E jumps at the
+    # shock; Lorentz-transformed to the lab frame (E_lab = gamma^2 (E + 2 beta F/c + beta^2 P_rr))
+    # it is flat to the first zone's value, as a transparent medium requires.  Two light-crossing
+    # times on a log-r grid from 0.3 to 10 (96 cells) and a 4-cell equatorial wedge.
+    c, vs, r_in, nr, nth = 1.0, 0.1, 0.3, 96, 4
+    x0, x1 = math.log(r_in), math.log(10.0)
+    pb = W.Problem(name="labflux", dims=2, n=(nr, nth, 1), x_lo=(x0, math.pi / 2 - 0.4, 0),
+                   x_hi=(x1, math.pi / 2 + 0.4, 1), bc_lo=("outflow", "reflect", "periodic"),
+                   bc_hi=("outflow", "reflect", "periodic"), ngroups=1, gamma=4 / 3, kappa0=0.0,
+                   kap_rho_exp=0.0, kap_T_exp=0.0, kap_eps_exp=0.0, c_light=c, couple=0, geom="sph",
+                   map1="exp", vterms=1)
+    N, dx = pb.ncell, (x1 - x0) / nr
+    r = np.exp(pb.cell_centres(0))
+    v = np.where(r < 1.0, -0.1 * vs * r, -vs * (np.sqrt(10.0 / r) - 1) / (math.sqrt(10.0) - 1))
+    prim = np.stack([np.ones(N), np.full(N, 1e-3), np.tile(v, nth), np.zeros(N), np.full(N, 1e-3)])
+    s = oracle.init_equilibrium(pb, prim)
+    s[4 * N:] = 0.0
+    s[4 * N:5 * N] = 1e-8
+    # the inflow ghosts: E = 1 and a beam's covariant flux h_1 c E, h_1 of the ghost next to the
+    # boundary (log map: h_1^2 = (3/5)(e^{5b} - e^{5a})/(e^{3b} - e^{3a}) on [a, b])
+    a, b = x0 - dx, x0
+    h1g = math.sqrt(0.6 * (math.exp(5 * b) - math.exp(5 * a)) / (math.exp(3 * b) - math.exp(3 * a)))
+    dt0 = 0.15 * r_in * dx / c
+    nst = int(math.ceil(20.0 / dt0))
+    out, st = oracle.run(pb, s, 20.0 / nst, nst, nthreads=8, inflow=np.array([1.0, 0.999 * c * h1g]),
+                         frozen_gas=1)
+    assert st == 0
+    unit = np.array(prim, copy=True)
+    unit[0], unit[2], unit[3] = 1.0, 1.0, 1.0
+    h1 = oracle.init_equilibrium(pb, unit)[N:2 * N].reshape(nth, nr)[nth // 2]
+    E = out[4 * N:5 * N].reshape(nth, nr)[nth // 2]
+    F = out[5 * N:6 * N].reshape(nth, nr)[nth // 2] / h1
+    f = np.clip(F / (c * E), 0.0, 1.0)
+    chi = (3 + 4 * f * f) / (5 + 2 * np.sqrt(4 - 3 * f * f))
+    beta = v / c
+    Elab = (E + 2 * beta * F / c + beta ** 2 * chi * E) / (1 - beta ** 2)
+    y, yl = r ** 2 * E, r ** 2 * Elab
+    k = int(np.searchsorted(r, 1.0))  # first cell outside the shock
+    inside, outside = slice(k - 5, k - 2), slice(k + 2, k + 5)
+    jump = y[outside].mean() / y[inside].mean() - 1
+    jump_lab = yl[outside].mean() / yl[inside].mean() - 1
+    away = np.r_[0:k - 2, k + 2:nr]  # the shock's two cells on each side smear the profile
+    flat = np.abs(yl[away] / yl[0] - 1).max()
+    assert jump > 0.15, jump
+    assert abs(jump_lab) < 0.02, jump_lab
+    assert flat < 0.035, flat
+
+
 # ------------------------------------------------------------------ Doppler-shift test (Sec. 9)
 def doppler_run(ng_lin):
     """Sec. 9's Doppler-shift test (reading R28): 50 cells on [0, 10] cm, rho = 1, no opacity,
