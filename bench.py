@@ -35,7 +35,7 @@ UNIT = "zone-group-stages/s"
 # DRAM bytes per launch (mean of the two RK stages) of the radiation/update kernel and of the
 # interaction kernel, from the committed ncu capture profiles/traffic_kh2d_1024x1024x16.txt; None
 # where not captured for the current kernels.
-TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": 570.7e6}}
+TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": None}}
 TRAFFIC_INTERACTION = {"kh2d": {"fp32n64": 371.2e6}}
 # FP64 lane operations (DFMA + DADD + DMUL thread instructions) per zone-group of the FP64 form's
 # radiation/update and interaction kernels, from the committed ncu capture
@@ -539,7 +539,8 @@ def main():
             "value": whole_job_rate(zg * 2 * args.steps, world, msv / 1e3), "unit": UNIT,
             "ms_per_step": msv / args.steps, "extra_ms_per_step": (msv - msh) / args.steps,
             "status": int(stv),
-            "kernel": {"name": "vterm_kernel", "avg_launch_ms": vms, "bytes_per_launch": vb,
+            "kernel": {"name": "vterm_kernel2" if head != "fp64" and pbh.nchan > 8 else "vterm_kernel",
+                       "avg_launch_ms": vms, "bytes_per_launch": vb,
                        "achieved": vb / (vms / 1e3) / 1e9 if vms > 0 else None, "unit": "GB/s",
                        "frac": vb / (vms / 1e3) / 1e9 / peak if vms > 0 else None}}
     if not args.no_adjoint and args.workload == "kh2d":

@@ -136,9 +136,7 @@ __device__ __forceinline__ void recon_linear_c(const MCCoef<R>& c, V pm, V p0, V
   V s = V(R(0));
   if constexpr (std::is_same<V, float>::value) {
     // FP32: the limited slope computed unconditionally and selected (no divergent branch)
-    const V sC = (pp - pm) * c.ic;
-    const V m = fmin(fmin(R(2) * fabs(sL), R(2) * fabs(sR)), fabs(sC));
-    s = sL * sR > R(0) ? (sC > R(0) ? m : -m) : V(R(0));
+    s = mc_slope(sL, sR, (pp - pm) * c.ic);
   } else if (sL * sR > R(0)) {
     V sC = (pp - pm) * c.ic;
     V m = fmin(fmin(R(2) * fabs(sL), R(2) * fabs(sR)), fabs(sC));
@@ -152,10 +150,7 @@ __device__ __forceinline__ void recon_linear_c(const MCCoef<R>& c, V pm, V p0, V
 // group).
 template <class R>
 __device__ __forceinline__ void recon_linear_c(const MCCoef<R>& c, F2 pm, F2 p0, F2 pp, F2& a, F2& b) {
-  const F2 sL = (p0 - pm) * c.il, sR = (pp - p0) * c.ir, sC = (pp - pm) * c.ic;
-  const F2 m = vmin(vmin(R(2) * vabs(sL), R(2) * vabs(sR)), vabs(sC));
-  const F2 pr = sL * sR;
-  const F2 s(pr.x > R(0) ? (sC.x > R(0) ? m.x : -m.x) : R(0), pr.y > R(0) ? (sC.y > R(0) ? m.y : -m.y) : R(0));
+  const F2 s = mc_slope((p0 - pm) * c.il, (pp - p0) * c.ir, (pp - pm) * c.ic);
   a = vfma(s, c.dl, p0);
   b = vfma(s, c.dr, p0);
 }

@@ -128,9 +128,16 @@ static cudaError_t launch_gp(const StageArgs<R>& a, cudaStream_t s, cudaEvent_t 
   // the velocity-dependent radiation terms of the stage input, added to the explicit update
   // before the interaction (one lane per group)
   if (a.g.vterms) {
-    constexpr int CPB = VT_THREADS / GP;  // cells of one x row per block, GP lanes each
-    const dim3 vg((unsigned)(a.g.n[1] * a.g.n[2]), (unsigned)((a.g.n[0] + CPB - 1) / CPB), 1);
-    vterm_kernel<R, D, GP, SPH><<<vg, VT_THREADS, 0, s>>>(a);
+    if constexpr (std::is_same<R, float>::value && GP >= 16) {
+      // FP32 forms from 9 groups: two groups per lane, GP/2 lanes per cell
+      constexpr int CPB = VT_THREADS / (GP / 2);
+      const dim3 vg((unsigned)(a.g.n[1] * a.g.n[2]), (unsigned)((a.g.n[0] + CPB - 1) / CPB), 1);
+      vterm_kernel2<D, GP / 2, SPH><<<vg, VT_THREADS, 0, s>>>(a);
+    } else {
+      constexpr int CPB = VT_THREADS / GP;  // cells of one x row per block, GP lanes each
+      const dim3 vg((unsigned)(a.g.n[1] * a.g.n[2]), (unsigned)((a.g.n[0] + CPB - 1) / CPB), 1);
+      vterm_kernel<R, D, GP, SPH><<<vg, VT_THREADS, 0, s>>>(a);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -81,6 +81,22 @@ __device__ __forceinline__ F2 vsel_gt(F2 x, float t, F2 a, F2 b) {
   return F2(x.x > t ? a.x : b.x, x.y > t ? a.y : b.y);
 }
 
+// Slope of the MC limiter from the one-sided slopes sL, sR and the centred slope sC: the least of
+// 2|sL|, 2|sR| and |sC|, with the common sign of sL and sR, and zero where their signs differ or
+// one is zero.  Where sL and sR share a sign, sC has it too (the centred difference is the sum
+// of the two one-sided ones, each scaled by a positive reciprocal distance), so the sign factor
+// (-1, 0 or 1, exact) replaces the product test and the selects.  FP32 and the pair.
+__device__ __forceinline__ float mc_slope(float sL, float sR, float sC) {
+  const float m = fminf(2.0f * fminf(fabsf(sL), fabsf(sR)), fabsf(sC));
+  return m * (copysignf(0.5f, sL) + copysignf(0.5f, sR));
+}
+__device__ __forceinline__ F2 mc_slope(F2 sL, F2 sR, F2 sC) {
+  const F2 m2 = F2(fminf(fabsf(sL.x), fabsf(sR.x)), fminf(fabsf(sL.y), fabsf(sR.y))) * 2.0f;
+  const F2 m(fminf(m2.x, fabsf(sC.x)), fminf(m2.y, fabsf(sC.y)));
+  return m * (F2(copysignf(0.5f, sL.x), copysignf(0.5f, sL.y)) +
+              F2(copysignf(0.5f, sR.x), copysignf(0.5f, sR.y)));
+}
+
 // A value of type V from the values of the lane's two groups (the pair, or the first value), and
 // component j of a value.
 __device__ __forceinline__ float vpair(float a, float, float) { return a; }

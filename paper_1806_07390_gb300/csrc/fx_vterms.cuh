@@ -138,23 +138,14 @@ inline void vt_constants(const double* edge, int G, VtConst& v) {
 // the two faces), and turns V^a_b into physical components V^a_b h_a / h_b.
 constexpr int VT_THREADS = 256;
 
-template <class R, int D, int GP, bool SPH>
-__global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant__ StageArgs<R> A) {
-  static_assert(!SPH || D == 2, "the spherical grid is 2-d");
-  constexpr int DT = SPH ? 3 : D;  // dimension of the tensors
-  using VC = VtComp<DT>;
-  constexpr int NG = 2 + D, NP = VC::NP, NC = VC::NC, CPB = VT_THREADS / GP;
+// The cell's velocity gradient V (physical components, DT x DT) and the scale factors h of the
+// flux components (1 on Cartesian grids), from the face velocities: component i of a face of
+// direction j sits in row NG + ((i - j) mod D) of direction j's face block.
+template <class R, int D, bool SPH, int DT>
+__device__ __forceinline__ void vt_gradient(const StageArgs<R>& A, int ix, int iy, int iz, R (&V)[DT][DT],
+                                            R (&h)[DT]) {
+  constexpr int NG = 2 + D;
   const DevGrid& g = A.g;
-  const int G = g.G;
-  const uint32_t ncell = (uint32_t)g.ncell;
-  const int lane = (int)(threadIdx.x % GP);
-  const int x0 = (int)(blockIdx.y * CPB + threadIdx.x / GP);
-  const bool cok = x0 < g.n[0], act = cok && lane < G;
-  const int ix = cok ? x0 : g.n[0] - 1;  // every lane takes part in the shuffles
-  const int iy = (int)(blockIdx.x % (unsigned)g.n[1]), iz = (int)(blockIdx.x / (unsigned)g.n[1]);
-  // 32-bit offsets: the host keeps every state offset below 2^32
-  const uint32_t cc = ((uint32_t)iz * g.n[1] + (uint32_t)iy) * g.n[0] + (uint32_t)ix;
-  // face velocities: component i of a face of direction j sits in row NG + ((i - j) mod D)
   R vl[D][D], vu[D][D];  // [j][i]: lower / upper face of direction j, component i
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -170,12 +161,10 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
       vu[j][i] = __ldg(fr + row + uf);
     }
   }
-  R V[DT][DT];
 #pragma unroll
   for (int i = 0; i < DT; ++i)
 #pragma unroll
     for (int j = 0; j < DT; ++j) V[i][j] = R(0);
-  R h[DT];  // cell scale factors of the flux components (1 on Cartesian grids)
 #pragma unroll
   for (int q = 0; q < DT; ++q) h[q] = R(1);
   if constexpr (SPH) {
@@ -210,13 +199,53 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
       for (int i = 0; i < D; ++i) V[i][j] = (vu[j][i] - vl[j][i]) * idx;
     }
   }
+}
+
+// Volume of cell (ix, iy) (the budget's weight).
+template <class R, int D, bool SPH>
+__device__ __forceinline__ double vt_volume(const StageArgs<R>& A, int ix, int iy) {
+  const DevGrid& g = A.g;
+  if constexpr (SPH) {
+    return (double)Tab<R>{A.tab[0], g.n[0] + 4, A.uniform[0] ? A.urow[0] : nullptr}(T_VOL, ix + 2) *
+           (double)Tab<R>{A.tab[1], g.n[1] + 4, A.uniform[1] ? A.urow[1] : nullptr}(T_VOL, iy + 2);
+  } else {
+    double vol = 1.0;
+    for (int d = 0; d < D; ++d) vol /= g.inv_dx[d];
+    return vol;
+  }
+}
+
+template <class R, int D, int GP, bool SPH>
+__global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant__ StageArgs<R> A) {
+  static_assert(!SPH || D == 2, "the spherical grid is 2-d");
+  constexpr int DT = SPH ? 3 : D;  // dimension of the tensors
+  using VC = VtComp<DT>;
+  constexpr int NG = 2 + D, NP = VC::NP, NC = VC::NC, CPB = VT_THREADS / GP;
+  const DevGrid& g = A.g;
+  const int G = g.G;
+  const uint32_t ncell = (uint32_t)g.ncell;
+  const int lane = (int)(threadIdx.x % GP);
+  const int x0 = (int)(blockIdx.y * CPB + threadIdx.x / GP);
+  const bool cok = x0 < g.n[0], act = cok && lane < G;
+  const int ix = cok ? x0 : g.n[0] - 1;  // every lane takes part in the shuffles
+  const int iy = (int)(blockIdx.x % (unsigned)g.n[1]), iz = (int)(blockIdx.x / (unsigned)g.n[1]);
+  // 32-bit offsets: the host keeps every state offset below 2^32
+  const uint32_t cc = ((uint32_t)iz * g.n[1] + (uint32_t)iy) * g.n[0] + (uint32_t)ix;
+  R V[DT][DT], h[DT];
+  vt_gradient<R, D, SPH, DT>(A, ix, iy, iz, V, h);
   // this lane's group of the stage input (physical flux components)
   const uint32_t rad = (uint32_t)NG * ncell, gid = cc * (uint32_t)G + (uint32_t)lane,
                  vstr = ncell * (uint32_t)G;
-  R E = R(0), F[DT];
+  R E = R(0), F[DT], oE = R(0), oF[D];
 #pragma unroll
   for (int q = 0; q < DT; ++q) F[q] = R(0);
+#pragma unroll
+  for (int q = 0; q < D; ++q) oF[q] = R(0);
   if (act) {
+    // the stage output this lane updates, read here so that its latency overlaps the work
+    oE = A.out[rad + gid];
+#pragma unroll
+    for (int q = 0; q < D; ++q) oF[q] = A.out[rad + (uint32_t)(1 + q) * vstr + gid];
     E = A.in[rad + gid];
 #pragma unroll
     for (int q = 0; q < D; ++q) F[q] = A.in[rad + (uint32_t)(1 + q) * vstr + gid];
@@ -301,18 +330,16 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
     if (top) uF[j] = R(0);
   }
   if (act) {
-    R* o = A.out + rad + gid;
-    const R e = *o + wdt * dE;
+    const R e = oE + wdt * dE;
     bad |= !isfinite(e);
-    *o = e;
+    A.out[rad + gid] = e;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      R* of = A.out + rad + (uint32_t)(1 + j) * vstr + gid;
       R dF = uF[j] - fF[j] - wF[j];
       if constexpr (SPH) dF *= h[j];  // covariant component
-      const R f = *of + wdt * dF;
+      const R f = oF[j] + wdt * dF;
       bad |= !isfinite(f);
-      *of = f;
+      A.out[rad + (uint32_t)(1 + j) * vstr + gid] = f;
     }
   }
   if (bad) atomicOr(A.status, ST_NONFINITE);
@@ -320,16 +347,222 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
     // radiation energy the terms add, weighted as the RK combination weighs this stage; each
     // lane weighs its own cell's volume (a warp spans 32/GP cells, of different volumes on the
     // spherical grid)
-    double vol = 1.0;
-    if constexpr (SPH) {
-      vol = (double)Tab<R>{A.tab[0], g.n[0] + 4, A.uniform[0] ? A.urow[0] : nullptr}(T_VOL, ix + 2) *
-            (double)Tab<R>{A.tab[1], g.n[1] + 4, A.uniform[1] ? A.urow[1] : nullptr}(T_VOL, iy + 2);
-    } else {
-      for (int d = 0; d < D; ++d) vol /= g.inv_dx[d];
-    }
-    double e = act ? (double)dE * vol : 0.0;
+    double e = act ? (double)dE * vt_volume<R, D, SPH>(A, ix, iy) : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0)
+      atomicAdd(A.budget + (blockIdx.x % BUDGET_SLOTS) * NBUDGET + 8, e * A.bw_flux);
+  }
+}
+
+// Two groups per lane (the FP32 forms from 9 groups): lane l of a cell owns groups 2l and 2l + 1
+// as one packed FP32 pair (fx_pair.cuh), GQ lanes per cell (a power of two >= G/2), 256/GQ cells
+// of one x row per block, four blocks per SM (64 registers).  The closure runs per group; the spectral densities, limited slopes,
+// upwind edge values, work terms and the update run on the pair.  A group's neighbour across the
+// lane boundary comes by one shuffle each way (group 2l - 1 is the lane below's second, 2l + 2
+// the lane above's first); the flux through the edge between a lane's two groups needs none.
+// vt_moments for the pair: the closure per group (a group without flux or energy takes f = 0:
+// chi = 1/3, q = 0, the isotropic P = E/3 and Q = 0 of the one-group form), the components on
+// the pair.
+template <int D>
+__device__ __forceinline__ void vt_moments2(float c, F2 E, const F2* F, F2* x) {
+  using VC = VtComp<D>;
+  F2 F2s(0.0f);
+#pragma unroll
+  for (int q = 0; q < D; ++q) F2s = vfma(F[q], F[q], F2s);
+  float iF[2], av[2], bv[2], qav[2], qbv[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const float Fs = s ? F2s.y : F2s.x, Es = s ? E.y : E.x;
+    const bool ok = Fs > 0.0f && Es > 0.0f;
+    const float i1 = ok ? rsqrtf(Fs) : 0.0f, cE = c * Es;
+    const float f = ok ? fminf(Fs * i1 * __fdividef(1.0f, cE), 1.0f) : 0.0f, f2 = f * f;
+    const float chi = (3.0f + 4.0f * f2) * __fdividef(1.0f, 5.0f + 2.0f * sqrtf(4.0f - 3.0f * f2));
+    const float q = f * (2.0f + 3.0f * chi) * 0.2f;
+    iF[s] = i1;
+    av[s] = 0.5f * (1.0f - chi);
+    bv[s] = 0.5f * (3.0f * chi - 1.0f);
+    qav[s] = 0.5f * (f - q) * cE;
+    qbv[s] = 0.5f * (5.0f * q - 3.0f * f) * cE;
+  }
+  const F2 a(av[0], av[1]), b(bv[0], bv[1]), qa(qav[0], qav[1]), qb(qbv[0], qbv[1]);
+  F2 n[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) n[i] = F[i] * F2(iF[0], iF[1]);
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      const F2 nn = n[i] * n[j];
+      x[vt_sym2(i, j, D)] = E * (i == j ? vfma(b, nn, a) : b * nn);
+#pragma unroll
+      for (int k = j; k < D; ++k) {
+        F2 t(0.0f);
+        if (j == k) t = t + n[i];
+        if (i == k) t = t + n[j];
+        if (i == j) t = t + n[k];
+        x[VC::NP + vt_sym3(i, j, k, D)] = vfma(qb, nn * n[k], qa * t);
+      }
+    }
+}
+
+template <int D, int GQ, bool SPH>
+__global__ void __launch_bounds__(VT_THREADS, 4) vterm_kernel2(const __grid_constant__ StageArgs<float> A) {
+  static_assert(!SPH || D == 2, "the spherical grid is 2-d");
+  using R = float;
+  constexpr int DT = SPH ? 3 : D;
+  using VC = VtComp<DT>;
+  constexpr int NG = 2 + D, NP = VC::NP, NC = VC::NC, CPB = VT_THREADS / GQ;
+  constexpr unsigned FULL = 0xffffffffu;
+  const DevGrid& g = A.g;
+  const int G = g.G;
+  const uint32_t ncell = (uint32_t)g.ncell;
+  const int lane = (int)(threadIdx.x % GQ);
+  const int x0 = (int)(blockIdx.y * CPB + threadIdx.x / GQ);
+  const bool cok = x0 < g.n[0];
+  const int ga = 2 * lane, gb = ga + 1;
+  const bool acta = cok && ga < G, actb = cok && gb < G;
+  const int ix = cok ? x0 : g.n[0] - 1;  // every lane takes part in the shuffles
+  const int iy = (int)(blockIdx.x % (unsigned)g.n[1]), iz = (int)(blockIdx.x / (unsigned)g.n[1]);
+  const uint32_t cc = ((uint32_t)iz * g.n[1] + (uint32_t)iy) * g.n[0] + (uint32_t)ix;
+  R V[DT][DT], h[DT];
+  vt_gradient<R, D, SPH, DT>(A, ix, iy, iz, V, h);
+  // the two groups of the stage input (physical flux components)
+  const uint32_t rad = (uint32_t)NG * ncell, gia = cc * (uint32_t)G + (uint32_t)ga,
+                 vstr = ncell * (uint32_t)G;
+  R Ea = 0.0f, Eb = 0.0f, Fa[DT], Fb[DT], oE[2] = {0.0f, 0.0f}, oF[2][D];
+#pragma unroll
+  for (int q = 0; q < DT; ++q) { Fa[q] = 0.0f; Fb[q] = 0.0f; }
+#pragma unroll
+  for (int q = 0; q < D; ++q) { oF[0][q] = 0.0f; oF[1][q] = 0.0f; }
+  // the stage output the lane updates, read first so that its latency overlaps the work
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+    if (t ? actb : acta) {
+      oE[t] = A.out[rad + gia + t];
+#pragma unroll
+      for (int q = 0; q < D; ++q) oF[t][q] = A.out[rad + (uint32_t)(1 + q) * vstr + gia + t];
+    }
+  if (acta) {
+    Ea = A.in[rad + gia];
+#pragma unroll
+    for (int q = 0; q < D; ++q) Fa[q] = A.in[rad + (uint32_t)(1 + q) * vstr + gia];
+  }
+  if (actb) {
+    Eb = A.in[rad + gia + 1];
+#pragma unroll
+    for (int q = 0; q < D; ++q) Fb[q] = A.in[rad + (uint32_t)(1 + q) * vstr + gia + 1];
+  }
+  if constexpr (SPH) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) { Fa[q] = Fa[q] / h[q]; Fb[q] = Fb[q] / h[q]; }
+  }
+  F2 x[NC];
+  {
+    F2 Fp[DT];
+#pragma unroll
+    for (int q = 0; q < DT; ++q) Fp[q] = F2(Fa[q], Fb[q]);
+    vt_moments2<DT>(A.k(R(0)).c, F2(Ea, Eb), Fp, x);
+  }
+  // work terms V_ij P^ij and sum_i V_ij F^i
+  F2 wE(0.0f), wF[D];
+#pragma unroll
+  for (int i = 0; i < DT; ++i)
+#pragma unroll
+    for (int j = 0; j < DT; ++j)
+      if (!SPH || i == j || (i < 2 && j < 2)) wE = vfma(F2(V[i][j]), x[vt_sym2(i, j, DT)], wE);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    F2 s2(0.0f);
+#pragma unroll
+    for (int i = 0; i < D; ++i) s2 = vfma(F2(V[i][j]), F2(Fa[i], Fb[i]), s2);
+    wF[j] = s2;
+  }
+  // per-group frequency constants
+  const VtConst& vc = *A.vtc;
+  const int ka = acta ? ga : 0, kb = actb ? gb : 0;
+  auto cpair = [&](int e) { return F2(acta ? vc.c32[e][ka] : 0.0f, actb ? vc.c32[e][kb] : 0.0f); };
+  const F2 inu = cpair(VT_INU), lm = cpair(VT_LMID), hm = cpair(VT_HMID), cm = cpair(VT_CMID);
+  const F2 mlo = cpair(VT_MLO), mhi = cpair(VT_MHI);
+  // spectral densities, limited slopes, values at each group's lower (x[m] after) and upper edge
+  F2 hi[NC];
+#pragma unroll
+  for (int m = 0; m < NC; ++m) {
+    const F2 xc = x[m] * inu;
+    const float below = __shfl_up_sync(FULL, xc.y, 1, GQ);   // group 2l - 1
+    const float above = __shfl_down_sync(FULL, xc.x, 1, GQ); // group 2l + 2
+    const F2 xm(below, xc.x), xp(xc.y, above);
+    // (the first and last groups and absent ones have zero midpoint constants: zero slope)
+    const F2 sl = mc_slope((xc - xm) * lm, (xp - xc) * hm, (xp - xm) * cm);
+    x[m] = vfma(-sl, mlo, xc);
+    hi[m] = vfma(sl, mhi, xc);
+  }
+  // fluxes through the lower edges of the two groups: edge 2l takes, per component pair, the
+  // upper-edge value of group 2l - 1 (the lane below's second) when V_ij < 0, else group 2l's
+  // lower-edge value; edge 2l + 1 takes group 2l's upper-edge value or group 2l + 1's lower-edge
+  // value
+  float hb[NC];
+#pragma unroll
+  for (int m = 0; m < NC; ++m) hb[m] = __shfl_up_sync(FULL, hi[m].y, 1, GQ);
+  const F2 el((acta && ga > 0) ? A.gc->edge_of(ga, R(0)) : 0.0f, actb ? A.gc->edge_of(gb, R(0)) : 0.0f);
+  F2 fE(0.0f), fF[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) fF[j] = F2(0.0f);
+#pragma unroll
+  for (int i = 0; i < DT; ++i)
+#pragma unroll
+    for (int j = 0; j < DT; ++j) {
+      if (SPH && i != j && (i >= 2 || j >= 2)) continue;  // V_ij = 0 there
+      const int m = vt_sym2(i, j, DT);
+      fE = vfma(F2(V[i][j]), V[i][j] < 0.0f ? F2(hb[m], hi[m].x) : x[m], fE);
+    }
+  fE = fE * el;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    F2 sF(0.0f);
+#pragma unroll
+    for (int i = 0; i < DT; ++i)
+#pragma unroll
+      for (int kk = 0; kk < DT; ++kk) {
+        if (SPH && i != kk && (i >= 2 || kk >= 2)) continue;
+        const int m = NP + vt_sym3(kk, j, i, DT);
+        sF = vfma(F2(V[i][kk]), V[i][kk] < 0.0f ? F2(hb[m], hi[m].x) : x[m], sF);
+      }
+    fF[j] = sF * el;
+  }
+  // fluxes through the upper edges: group 2l's is group 2l + 1's lower-edge flux; group
+  // 2l + 1's the lane above's first (none through the top edge of the range)
+  const bool topb = gb + 1 >= G;
+  float up = __shfl_down_sync(FULL, fE.x, 1, GQ);
+  const F2 uE(fE.y, topb ? 0.0f : up);
+  const F2 dE = uE - fE - wE;
+  const R wdt = R(A.dt) * (R(1) - R(A.alpha));  // w = 1 (stage 1) or 1/2 (stage 2)
+  F2 dF[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    up = __shfl_down_sync(FULL, fF[j].x, 1, GQ);
+    dF[j] = F2(fF[j].y, topb ? 0.0f : up) - fF[j] - wF[j];
+    if constexpr (SPH) dF[j] = dF[j] * h[j];  // covariant component
+  }
+  bool bad = false;
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+    if (t ? actb : acta) {
+      const R e = fmaf(wdt, vget(dE, t), oE[t]);
+      bad |= !isfinite(e);
+      A.out[rad + gia + t] = e;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const R f = fmaf(wdt, vget(dF[j], t), oF[t][j]);
+        bad |= !isfinite(f);
+        A.out[rad + (uint32_t)(1 + j) * vstr + gia + t] = f;
+      }
+    }
+  if (bad) atomicOr(A.status, ST_NONFINITE);
+  if (A.budget != nullptr) {
+    double e = ((acta ? (double)dE.x : 0.0) + (actb ? (double)dE.y : 0.0)) * vt_volume<R, D, SPH>(A, ix, iy);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(FULL, e, o);
     if ((threadIdx.x & 31) == 0)
       atomicAdd(A.budget + (blockIdx.x % BUDGET_SLOTS) * NBUDGET + 8, e * A.bw_flux);
   }

@@ -84,8 +84,10 @@ def test_velocity_terms_fp64(fxmod, name):
 
 
 @pytest.mark.parametrize("form", ["fp32", "fp32n64"])
-@pytest.mark.parametrize("name", ["kh", "rand2d", "rand3d"])
+@pytest.mark.parametrize("name", ["kh", "kh_g32", "rand1d", "rand2d", "rand3d"])
 def test_velocity_terms_fp32_forms(fxmod, name, form):
+    # from 9 groups the FP32 forms take two groups per lane (8 lanes per cell for kh's 16 and
+    # rand2d's 13 groups, 16 lanes for 32 groups); rand1d (7) and rand3d (5) one group per lane
     pb, s = case(name, form)
     got, ref = run_both(fxmod, pb, s)
     H.assert_parity(pb, got, ref, 1e-4, natural=True)
