@@ -646,6 +646,7 @@ Consts<T> make_consts(const fx_grid* h, double dt, double dts, double alpha, boo
   // FP32 iterates stop at FP32 resolution (the paper's own tolerance is 1e-6, Sec. 5.3)
   k.rtol = (T)(fp32_newton ? std::max(P.newton_rtol, 2e-7) : P.newton_rtol);
   k.atol = (T)(fp32_newton ? 1e-7 : 1e-14);
+  for (int d = 0; d < 3; ++d) k.idx[d] = (T)h->dg.inv_dx[d];
   return k;
 }
 

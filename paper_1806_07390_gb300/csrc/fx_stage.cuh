@@ -38,6 +38,7 @@ template <class T> struct Consts {
   T kappa0, sigma0, rho_floor, u_floor, E_floor, aN;  // aN = a_R 15/pi^4
   T cdts, dt, alpha, beta;                 // c * coupling step, stage step, RK weights
   T rtol, atol;                            // coupling convergence tolerances
+  T idx[3];                                // 1 / cell width per direction (in x, the coordinate)
 };
 
 // Planck series coefficients (universal constants), passed by value in the kernel parameters.

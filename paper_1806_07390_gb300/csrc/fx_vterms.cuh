@@ -171,7 +171,7 @@ __device__ __forceinline__ void vt_gradient(const StageArgs<R>& A, int ix, int i
     const Tab<R> tr{A.tab[0], g.n[0] + 4, A.uniform[0] ? A.urow[0] : nullptr};
     const Tab<R> tq{A.tab[1], g.n[1] + 4, A.uniform[1] ? A.urow[1] : nullptr};
     const int ipr = ix + 2, ipt = iy + 2;
-    const R idr = R(g.inv_dx[0]), idt = R(g.inv_dx[1]);
+    const R idr = A.k(R(0)).idx[0], idt = A.k(R(0)).idx[1];
     h[0] = tr(T_HA, ipr);
     h[1] = tr(T_HB, ipr);
     const R ih1 = R(1) / h[0], ih2 = R(1) / h[1];
@@ -194,7 +194,7 @@ __device__ __forceinline__ void vt_gradient(const StageArgs<R>& A, int ix, int i
   } else {
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      const R idx = R(g.inv_dx[j]);
+      const R idx = A.k(R(0)).idx[j];
 #pragma unroll
       for (int i = 0; i < D; ++i) V[i][j] = (vu[j][i] - vl[j][i]) * idx;
     }
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
   R uE = __shfl_down_sync(0xffffffffu, fE, 1, GP);
   if (top) uE = R(0);
   const R dE = uE - fE - wE;
-  const R wdt = R(A.dt) * (R(1) - R(A.alpha));  // w = 1 (stage 1) or 1/2 (stage 2)
+  const R wdt = A.k(R(0)).dt * A.k(R(0)).beta;  // w = 1 (stage 1) or 1/2 (stage 2)
   bool bad = false;
   R uF[D];
 #pragma unroll
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(VT_THREADS, 4) vterm_kernel2(const __grid_cons
   float up = __shfl_down_sync(FULL, fE.x, 1, GQ);
   const F2 uE(fE.y, topb ? 0.0f : up);
   const F2 dE = uE - fE - wE;
-  const R wdt = R(A.dt) * (R(1) - R(A.alpha));  // w = 1 (stage 1) or 1/2 (stage 2)
+  const R wdt = A.k(R(0)).dt * A.k(R(0)).beta;  // w = 1 (stage 1) or 1/2 (stage 2)
   F2 dF[D];
 #pragma unroll
   for (int j = 0; j < D; ++j) {

@@ -75,9 +75,10 @@ __global__ void __launch_bounds__(256) comp_kernel(const __grid_constant__ Stage
       }
     net += (fhi * tt(T_FR, bc_pad(i)) - flo * tt(T_FL, bc_pad(i))) * cross;
   }
-  const R u = A.in[XO + c] - R(A.dt) * net;
+  const auto& K = A.k(R(0));  // the step and RK weights in R (no per-thread conversions)
+  const R u = A.in[XO + c] - K.dt * net;
   const bool stage2 = A.base != nullptr;
-  const R r = stage2 ? R(A.alpha) * A.base[XO + c] + (R(1) - R(A.alpha)) * u : u;
+  const R r = stage2 ? K.alpha * A.base[XO + c] + K.beta * u : u;
   if (!isfinite(r)) atomicOr(A.status, ST_NONFINITE);
   A.out[XO + c] = r;
 }
