@@ -319,7 +319,7 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<R>& A, int64_t f) {
   const Tab<R> t{A.tab[DIR], nd + 4, A.uniform[DIR] ? A.urow[DIR] : nullptr};
   // adjoint of the face flux of state variable j: dJ/dF = -b dt fr(L) lam_pre(L) + b dt fl(R) lam_pre(R)
   const bool inL = id >= 1, inR = id < nd;
-  const R bdt = R((1.0 - A.alpha) * A.dt);
+  const R bdt = KR.beta * KR.dt;  // (1 - alpha) dt: the weights 1, 1/2 are exact in R
   const R cL = inL ? -bdt * t(T_FR, bc_pad(id - 1)) : R(0);
   const R cR = inR ? bdt * t(T_FL, bc_pad(id)) : R(0);
   const bool objective = DIR == 0 && id == n0 && A.wJ != R(0);
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const __grid_constant__ A
   }
   lU[NG - 1] = lpW * KR.gm1;
 
-  const R al = R(A.alpha), be = R(1.0 - A.alpha);
+  const R al = KR.alpha, be = KR.beta;
   if (active) {
     if (lane < NG) {
       R val = lU[0];
