@@ -35,8 +35,8 @@ UNIT = "zone-group-stages/s"
 # DRAM bytes per launch (mean of the two RK stages) of the radiation/update kernel and of the
 # interaction kernel, from the committed ncu capture profiles/traffic_kh2d_1024x1024x16.txt; None
 # where not captured for the current kernels.
-TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": None}}
-TRAFFIC_INTERACTION = {"kh2d": {"fp32n64": 371.2e6}}
+TRAFFIC_PER_LAUNCH = {"kh2d": {"fp32n64": 570.6e6}}
+TRAFFIC_INTERACTION = {"kh2d": {"fp32n64": 370.9e6}}
 # FP64 lane operations (DFMA + DADD + DMUL thread instructions) per zone-group of the FP64 form's
 # radiation/update and interaction kernels, from the committed ncu capture
 # profiles/fp64_pipe_kh2d_512x512x16.txt (kh2d recipe at 512 x 512 cells x 16 groups).
