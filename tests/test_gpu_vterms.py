@@ -40,8 +40,8 @@ def case(name, precision):
         pb, prim = W.kh_2d(nx=26, ny=22, ngroups=32, nsteps=2, precision=precision)
         pb.vterms = 1
         return pb, oracle.init_equilibrium(pb, prim)
-    if name == "rand1d":
-        pb, _ = W.sod_1d(n=70, ngroups=7, precision=precision)
+    if name in ("rand1d", "rand1d_g12"):
+        pb, _ = W.sod_1d(n=70, ngroups=7 if name == "rand1d" else 12, precision=precision)
         pb.bc_lo = ("reflect", "outflow", "outflow")
         pb.c_light, pb.nsteps = 6.0, 4
     elif name == "rand2d":
@@ -50,7 +50,8 @@ def case(name, precision):
         pb.bc_hi = ("outflow", "periodic", "periodic")
         pb.c_light = 5.0
     else:
-        pb, _ = W.lognormal_3d(shape=(11, 9, 8), ngroups=5, nsteps=2, precision=precision)
+        pb, _ = W.lognormal_3d(shape=(11, 9, 8), ngroups=5 if name == "rand3d" else 11, nsteps=2,
+                               precision=precision)
         pb.bc_lo = ("outflow", "reflect", "periodic")
         pb.bc_hi = ("reflect", "outflow", "periodic")
         pb.c_light = 5.0
@@ -71,7 +72,7 @@ def run_both(fxmod, pb, s):
     return got, ref
 
 
-@pytest.mark.parametrize("name", ["kh", "kh_g32", "rand1d", "rand2d", "rand3d"])
+@pytest.mark.parametrize("name", ["kh", "kh_g32", "rand1d", "rand2d", "rand3d", "rand3d_g11"])
 def test_velocity_terms_fp64(fxmod, name):
     pb, s = case(name, "fp64")
     got, ref = run_both(fxmod, pb, s)
@@ -84,10 +85,11 @@ def test_velocity_terms_fp64(fxmod, name):
 
 
 @pytest.mark.parametrize("form", ["fp32", "fp32n64"])
-@pytest.mark.parametrize("name", ["kh", "kh_g32", "rand1d", "rand2d", "rand3d"])
+@pytest.mark.parametrize("name", ["kh", "kh_g32", "rand1d", "rand1d_g12", "rand2d", "rand3d", "rand3d_g11"])
 def test_velocity_terms_fp32_forms(fxmod, name, form):
-    # from 9 groups the FP32 forms take two groups per lane (8 lanes per cell for kh's 16 and
-    # rand2d's 13 groups, 16 lanes for 32 groups); rand1d (7) and rand3d (5) one group per lane
+    # from 9 groups the FP32 forms take two groups per lane (8 lanes per cell for kh's 16,
+    # rand2d's 13, rand1d_g12's 12 and rand3d_g11's 11 groups, 16 lanes for 32 groups); rand1d
+    # (7) and rand3d (5) one group per lane
     pb, s = case(name, form)
     got, ref = run_both(fxmod, pb, s)
     H.assert_parity(pb, got, ref, 1e-4, natural=True)
