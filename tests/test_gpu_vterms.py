@@ -125,10 +125,10 @@ def test_velocity_terms_have_no_adjoint(fxmod):
     g.close()
 
 
-def sph_case(map1, precision, seed=31):
+def sph_case(map1, precision, seed=31, ngroups=9):
     """Spherical grid with random physical velocities (up to 0.3 of the sound speed, changing
     sign from cell to cell) and random physical fluxes (|F| up to 0.6 cE), stored covariant."""
-    pb, prim = W.spherical_2d(nr=40, nth=22, ngroups=9, nsteps=3, precision=precision, map1=map1)
+    pb, prim = W.spherical_2d(nr=40, nth=22, ngroups=ngroups, nsteps=3, precision=precision, map1=map1)
     pb.vterms = 1
     rng = np.random.default_rng(seed)
     N, G = pb.ncell, pb.ngroups
@@ -160,9 +160,11 @@ def test_velocity_terms_spherical_fp64(fxmod, map1):
     assert np.abs(plain[rad] - ref[rad]).max() > 1e3 * FP64_MAX * np.abs(ref[rad]).max()
 
 
+@pytest.mark.parametrize("ngroups", [9, 20])
 @pytest.mark.parametrize("form", ["fp32", "fp32n64"])
-def test_velocity_terms_spherical_fp32_forms(fxmod, form):
-    pb, s = sph_case("exp", form)
+def test_velocity_terms_spherical_fp32_forms(fxmod, form, ngroups):
+    # two groups per lane on 8 (9 groups) and 16 (20 groups, the spherical workload's) lanes
+    pb, s = sph_case("exp", form, ngroups=ngroups)
     got, ref = run_both(fxmod, pb, s)
     H.assert_parity(pb, got, ref, 1e-4, natural=True)
 
