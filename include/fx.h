@@ -110,9 +110,12 @@ enum { FX_NTOTALS = 6, FX_NBUDGET = 9 };
  *                      w_s(Y_e) B_g(T) with w = 2 Y_e, 2 (1 - Y_e), 1 (synthetic emissivities,
  *                      every species with the opacity law above), and the lepton number per unit
  *                      energy xi = -xi0/eps_g, +xi0/eps_g, 0, so that rho Y_e - sum xi E is
- *                      conserved.  Cartesian and spherical grids, without vterms, budgets,
- *                      boundary layers or the adjoint (FX_ERR_UNSUPPORTED); in the FP32 forms the
- *                      interaction computes in FP64 and stores the FP32 state.
+ *                      conserved.  Cartesian and spherical grids.  With vterms each species'
+ *                      groups form their own chain in frequency; the terms leave rho Y_e
+ *                      unchanged while moving energy between groups of different xi, so they do
+ *                      not conserve rho Y_e - sum xi E.  Without budgets, boundary layers or the
+ *                      adjoint (FX_ERR_UNSUPPORTED); in the FP32 forms the interaction computes
+ *                      in FP64 and stores the FP32 state.
  */
 typedef struct {
   int dims;

@@ -151,8 +151,8 @@ def params(pb: Problem, nthreads: int = 1, r3_literal: int = 0, r10_full_dt: int
     P.vterms = pb.vterms
     P.frozen_gas = frozen_gas
     P.species, P.xi0 = pb.species, pb.xi0
-    if pb.species > 1 and (pb.vterms or layers):
-        raise ValueError("three species: without the velocity terms or layers")
+    if pb.species > 1 and layers:
+        raise ValueError("three species: without boundary layers")
     keep = []
     if edges is not None:
         e = np.ascontiguousarray(edges, dtype=np.float64)

@@ -98,6 +98,10 @@
 //      sum |xi| E^-; fallback: alternating bisections in T (fixed Y_e) and Y_e in [0, 1] (fixed
 //      T); u and rho Y_e by conservation, so total energy and total lepton number
 //      rho Y_e - sum xi E (a nu_e, xi < 0, carries -xi E) are conserved to round-off.
+//   R35 three species with the velocity terms: each species' groups form their own chain in
+//      frequency (the frequency fluxes of R26 per species, none between species); the terms act
+//      on the energy moments only, leaving rho Y_e unchanged, so rho Y_e - sum xi E is not
+//      conserved by them (the frequency fluxes move energy between groups of different xi).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -921,12 +925,14 @@ template <class S> static S mc_limit(S sL, S sR, S sC) {
   return val(sC) > 0.0 ? m : -m;
 }
 
-// rad: the cell's radiation variables, group by group (E_g, physical F_g1..F_gD); their time
-// derivatives from these terms are added to out (same layout).  DT >= D is the dimension of the
-// tensors (3 on the spherical grid: its phi-phi components with F_phi = 0).  Returns sum_g dE_g/dt.
+// One species: rad holds its radiation variables, group by group (E_g, physical F_g1..F_gD);
+// their time derivatives from these terms are added to out (same layout).  DT >= D is the
+// dimension of the tensors (3 on the spherical grid: its phi-phi components with F_phi = 0).
+// Returns sum_g dE_g/dt.
 template <class S>
-static S velocity_terms(const orc_params& P, const Groups& gr, int D, int DT, const S V[3][3], const S* rad, S* out) {
-  const int G = gr.G, NRV = 1 + D;
+static S velocity_terms_species(const orc_params& P, const Groups& gr, int D, int DT, const S V[3][3],
+                                const S* rad, S* out) {
+  const int G = gr.Gs, NRV = 1 + D;
   const double c = P.c_light;
   // spectral densities of the components: xp[g][i][j] = P_ij / dnu_g, xq[g][k][j][i] = Q_kji / dnu_g
   std::vector<S> xp((size_t)G * 9), xq((size_t)G * 27), Pc((size_t)G * 9);
@@ -1000,6 +1006,18 @@ static S velocity_terms(const orc_params& P, const Groups& gr, int D, int DT, co
       for (int i = 0; i < D; ++i) wF += V[i][j] * rad[g * NRV + 1 + i];
       out[g * NRV + 1 + j] += (fF[(g + 1) * 3 + j] - fF[g * 3 + j]) - wF;
     }
+  }
+  return dEsum;
+}
+
+// The velocity-dependent terms of one cell for all channels: each species' groups form their own
+// chain in frequency (R35), with no flux between species.
+template <class S>
+static S velocity_terms(const orc_params& P, const Groups& gr, int D, int DT, const S V[3][3], const S* rad, S* out) {
+  S dEsum = 0.0;
+  for (int sp = 0; sp < gr.S; ++sp) {
+    const size_t o = (size_t)sp * gr.Gs * (1 + D);
+    dEsum += velocity_terms_species(P, gr, D, DT, V, rad + o, out + o);
   }
   return dEsum;
 }

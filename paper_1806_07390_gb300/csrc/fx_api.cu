@@ -1026,8 +1026,8 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
   const int NS = P.species > 1 ? P.species : 1;  // species
   if (NS > 1) {
     if (!(P.xi0 >= 0.0) || !std::isfinite(P.xi0)) return FX_ERR_ARG;
-    // three species: without the velocity terms, 3 ngroups <= 32
-    if (P.vterms || NS * P.ngroups > MAXG) return FX_ERR_UNSUPPORTED;
+    // three species: 3 ngroups <= 32 channels
+    if (NS * P.ngroups > MAXG) return FX_ERR_UNSUPPORTED;
   }
   const int NCH = NS * P.ngroups;  // radiation channels
   if (!(P.gamma > 1.0) || !(P.c_light > 0.0) || !(P.a_rad > 0.0)) return FX_ERR_ARG;

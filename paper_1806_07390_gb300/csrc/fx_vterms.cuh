@@ -8,7 +8,8 @@
 // (5q - 3f)/2 n n n], q = f (2 + 3 chi)/5, and the intergroup values taken, per component pair
 // (i, j), from the group below the edge when V_ij < 0 and from the group above otherwise, each
 // the limited (MC) linear reconstruction of the spectral density P_g/dnu_g (Q_g/dnu_g) about the
-// group's midpoint in nu, with no flux through the ends of the group range.  The terms belong to
+// group's midpoint in nu, with no flux through the ends of the group range (of each species'
+// range with three neutrino species: their groups form separate chains).  The terms belong to
 // the stage's explicit operator, so the kernel adds w dt (terms of U) to the stage output in place
 // (w = 1 in stage 1, 1/2 in stage 2: the weights of the SSP-RK2 combination).
 //
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
   const int G = g.G;
   const uint32_t ncell = (uint32_t)g.ncell;
   const int lane = (int)(threadIdx.x % GP);
+  const int kg = lane % g.Gs;  // group of the lane's channel (species-major channels)
   const int x0 = (int)(blockIdx.y * CPB + threadIdx.x / GP);
   const bool cok = x0 < g.n[0], act = cok && lane < G;
   const int ix = cok ? x0 : g.n[0] - 1;  // every lane takes part in the shuffles
@@ -269,12 +271,12 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
     for (int i = 0; i < D; ++i) s2 += V[i][j] * F[i];
     wF[j] = s2;
   }
-  const int k = act ? lane : 0;
+  const int k = act ? kg : 0;
   const VtConst& vc = *A.vtc;
   const R inu = act ? vc.of(VT_INU, k, R(0)) : R(0);
   const R lm = vc.of(VT_LMID, k, R(0)), hm = vc.of(VT_HMID, k, R(0)), cm = vc.of(VT_CMID, k, R(0));
   const R mlo = vc.of(VT_MLO, k, R(0)), mhi = vc.of(VT_MHI, k, R(0));
-  const bool inner = act && lane > 0 && lane + 1 < G;
+  const bool inner = act && kg > 0 && kg + 1 < g.Gs;
   // spectral densities, limited slopes, values at the group's lower (x[m] after) and upper edge
   R hi[NC];
 #pragma unroll
@@ -293,8 +295,8 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
   R hp[NC];
 #pragma unroll
   for (int m = 0; m < NC; ++m) hp[m] = __shfl_up_sync(0xffffffffu, hi[m], 1, GP);
-  if (act && lane > 0) {
-    const R el = A.gc->edge_of(lane, R(0));
+  if (act && kg > 0) {  // no flux through the lower end of a species' group range
+    const R el = A.gc->edge_of(kg, R(0));
 #pragma unroll
     for (int i = 0; i < DT; ++i)
 #pragma unroll
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
     }
   }
   // flux through the upper edge: the lane above's lower-edge flux (none through the top edge)
-  const bool top = lane + 1 >= G;
+  const bool top = lane + 1 >= G || kg + 1 >= g.Gs;  // the upper end of the range
   R uE = __shfl_down_sync(0xffffffffu, fE, 1, GP);
   if (top) uE = R(0);
   const R dE = uE - fE - wE;
@@ -421,6 +423,7 @@ __global__ void __launch_bounds__(VT_THREADS, 4) vterm_kernel2(const __grid_cons
   const int x0 = (int)(blockIdx.y * CPB + threadIdx.x / GQ);
   const bool cok = x0 < g.n[0];
   const int ga = 2 * lane, gb = ga + 1;
+  const int kga = ga % g.Gs, kgb = gb % g.Gs;  // groups of the two channels (species-major)
   const bool acta = cok && ga < G, actb = cok && gb < G;
   const int ix = cok ? x0 : g.n[0] - 1;  // every lane takes part in the shuffles
   const int iy = (int)(blockIdx.x % (unsigned)g.n[1]), iz = (int)(blockIdx.x / (unsigned)g.n[1]);
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(VT_THREADS, 4) vterm_kernel2(const __grid_cons
   }
   // per-group frequency constants
   const VtConst& vc = *A.vtc;
-  const int ka = acta ? ga : 0, kb = actb ? gb : 0;
+  const int ka = acta ? kga : 0, kb = actb ? kgb : 0;
   auto cpair = [&](int e) { return F2(acta ? vc.c32[e][ka] : 0.0f, actb ? vc.c32[e][kb] : 0.0f); };
   const F2 inu = cpair(VT_INU), lm = cpair(VT_LMID), hm = cpair(VT_HMID), cm = cpair(VT_CMID);
   const F2 mlo = cpair(VT_MLO), mhi = cpair(VT_MHI);
@@ -504,7 +507,8 @@ __global__ void __launch_bounds__(VT_THREADS, 4) vterm_kernel2(const __grid_cons
   float hb[NC];
 #pragma unroll
   for (int m = 0; m < NC; ++m) hb[m] = __shfl_up_sync(FULL, hi[m].y, 1, GQ);
-  const F2 el((acta && ga > 0) ? A.gc->edge_of(ga, R(0)) : 0.0f, actb ? A.gc->edge_of(gb, R(0)) : 0.0f);
+  // (no flux through the lower end of a species' group range)
+  const F2 el((acta && kga > 0) ? A.gc->edge_of(kga, R(0)) : 0.0f, (actb && kgb > 0) ? A.gc->edge_of(kgb, R(0)) : 0.0f);
   F2 fE(0.0f), fF[D];
 #pragma unroll
   for (int j = 0; j < D; ++j) fF[j] = F2(0.0f);
@@ -532,7 +536,7 @@ __global__ void __launch_bounds__(VT_THREADS, 4) vterm_kernel2(const __grid_cons
   }
   // fluxes through the upper edges: group 2l's is group 2l + 1's lower-edge flux; group
   // 2l + 1's the lane above's first (none through the top edge of the range)
-  const bool topb = gb + 1 >= G;
+  const bool topb = gb + 1 >= G || kgb + 1 >= g.Gs;
   float up = __shfl_down_sync(FULL, fE.x, 1, GQ);
   const F2 uE(fE.y, topb ? 0.0f : up);
   const F2 dE = uE - fE - wE;

@@ -93,8 +93,8 @@ def test_velocity_terms_parameters(L):
 
 
 def test_three_species_parameters(L):
-    # species: 0/1 or 3; three species need a Cartesian grid, no velocity terms and at most 32
-    # channels; the state gains a composition block; one more kernel per stage
+    # species: 0/1 or 3; three species need at most 32 channels (the velocity terms are allowed);
+    # the state gains a composition block; one more kernel per stage
     pb, _ = W.neutrino_2d(nx=16, ny=12, ngroups=8)
     st, h, ws = create(pb)
     assert st == 0
@@ -104,12 +104,15 @@ def test_three_species_parameters(L):
     assert L.fx_launches_per_step(h) == L.fx_launches_per_step(h1) + 2
     L.fx_grid_destroy(h)
     L.fx_grid_destroy(h1)
-    for kw, code in ((dict(species=2), -1), (dict(ngroups=11), -7), (dict(vterms=1), -7),
+    for kw, code in ((dict(species=2), -1), (dict(ngroups=11), -7), (dict(vterms=1), 0),
                      (dict(xi0=-1.0), -1)):
         pb2, _ = W.neutrino_2d(nx=16, ny=12, ngroups=8)
         for k, v in kw.items():
             setattr(pb2, k, v)
-        assert create(pb2)[0] == code, kw
+        st2, h2, _ = create(pb2)
+        assert st2 == code, kw
+        if st2 == 0:
+            L.fx_grid_destroy(h2)
 
 
 def test_unbound_handle_reports_workspace_error(L):

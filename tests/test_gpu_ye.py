@@ -155,3 +155,39 @@ def test_spherical_initial_momentum_is_covariant(fxmod, precision):
     tol = 1e-13 if precision == "fp64" else 2e-7
     for a in (host, dev, na):
         np.testing.assert_allclose(a, ref, rtol=tol, atol=1e-300)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32n64"])
+@pytest.mark.parametrize("name", ["box2d", "sph"])
+def test_three_species_with_velocity_terms(fxmod, name, precision):
+    # reading R35: each species' groups their own frequency chain.  box2d: random gas, E and F
+    # per channel, 5 groups per species (15 channels: with two groups per lane, lane pairs
+    # straddle the species boundaries); sph: the spherical neutrino atmosphere, 6 groups per
+    # species (18 channels, 16 lanes per cell)
+    from tests.test_oracle_ye import species_vterms_problem, species_vterms_state
+    if name == "box2d":
+        pb = species_vterms_problem(couple=1)
+        pb.precision = precision
+        s0 = species_vterms_state(pb, seed=3)
+        pb.dt, pb.nsteps = 0.3 / max(pb.n[:2]) / pb.c_light, 4
+    else:
+        pb, prim = W.neutrino_sph2d(nr=48, nth=20, ngroups=6, nsteps=4, precision=precision)
+        pb.vterms = 1
+        s0 = oracle.init_equilibrium(pb, prim)
+    ref, rst = oracle.run(pb, s0, pb.dt, pb.nsteps, nthreads=8)
+    g = fxmod.Grid(pb)
+    g.upload(s0)
+    g.step(pb.dt, pb.nsteps)
+    st = g.status()
+    got = g.download()
+    g.close()
+    assert st == 0 and rst == 0
+    if precision == "fp64":
+        H.assert_parity(pb, got, ref, 1e-10, 1e-8)
+    else:
+        H.assert_parity(pb, got, ref, 1e-4, natural=True)
+    # the terms change the radiation by far more than the bar
+    pb.vterms = 0
+    plain, _ = oracle.run(pb, s0, pb.dt, pb.nsteps, nthreads=8)
+    rad = slice((2 + pb.dims) * pb.ncell, -pb.ncell)
+    assert np.abs(plain[rad] - ref[rad]).max() > 1e-6 * np.abs(ref[rad]).max()
