@@ -425,7 +425,7 @@ void build_planck_table(const fx_params& P, const GroupConst& gc, const PlanckPa
 // groups) 3.77 against 3.47 ms; blobs2d (2-d, 8 groups) 0.033 against 0.029 ms.  A warp's cells
 // read nodes i and i+1 of every group: group-major keeps the lanes' nodes of one group on one
 // cache line when their temperatures differ, node-major keeps a lane's groups together.
-bool ptab_node_major(const fx_grid* h) { return h->D <= 2 && h->G >= 16; }
+bool ptab_node_major(const fx_grid* h) { return h->D <= 2 && h->P.ngroups >= 16; }
 
 // The FP64 scale-factor rows T_HA, T_HB of every direction, as k_init_equilibrium reads them.
 std::vector<double> hrows(const fx_grid* h) {
@@ -671,7 +671,7 @@ StageArgs<R> stage_args(fx_grid* h) {
   a.ptab.tab = reinterpret_cast<const float4*>(h->ws + h->off_ptab);
   a.ptab.nu = h->ptab_nu;
   a.ptab.u0 = h->ptab_u0;
-  a.ptab.si = ptab_node_major(h) ? h->G : 1;
+  a.ptab.si = ptab_node_major(h) ? h->P.ngroups : 1;
   a.ptab.sg = ptab_node_major(h) ? 1 : h->ptab_nu;
   a.pk = h->pk;
   a.status = reinterpret_cast<unsigned*>(h->ws + h->off_status);
@@ -1182,7 +1182,6 @@ fx_status fx_budgets_enable(fx_grid* h, int on) {
   if (!h) return FX_ERR_ARG;
   if (h->sticky != FX_OK) return h->sticky;
   if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
-  if (on && h->dg.species > 1) return fail(h, FX_ERR_UNSUPPORTED, "budgets with one radiation species");
   h->budgets = on != 0;
   cudaError_t e = cudaMemsetAsync(h->ws + h->off_bud, 0, (size_t)BUDGET_SLOTS * NBUDGET * sizeof(double), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "budget reset");
@@ -1482,7 +1481,8 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
     off += align_up((size_t)np * sizeof(double));
   }
   {  // the device copy in the layout ptab_node_major picks; the host keeps the group-major table
-    const int G = h->G, nu = h->ptab_nu;
+    // (one table per group, ngroups of them: with three species the channels share them)
+    const int G = h->P.ngroups, nu = h->ptab_nu;
     const bool nmaj = ptab_node_major(h);
     std::vector<float4> nm((size_t)G * nu);
     for (int g = 0; g < G; ++g)

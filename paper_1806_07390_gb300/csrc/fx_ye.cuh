@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   const double u_floor = g.p_floor / (g.gamma - 1.0);
   if (u_m < u_floor) { u_m = u_floor; U[(NG - 1) * ncell + c] = (R)(ke + u_m); st |= ST_FLOOR; }
   const double X_m = U[XO + c], Y_m = X_m / rho;
-  double Esum = 0.0, Lsum = 0.0;
+  double Esum = 0.0, Lsum = 0.0, fadd = 0.0;
   for (int k = 0; k < G; ++k) {
     double E = U[rad + c * (uint32_t)G + k];
-    if (E < g.E_floor) E = g.E_floor;
+    if (E < g.E_floor) { fadd += g.E_floor - E; E = g.E_floor; }
     Em[k] = E;
     Esum += E;
     const int s = k / Gs;
@@ -277,6 +277,15 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   bool bad = !isfinite(ue) || !isfinite((double)U[XO + c]);
   if (bad) st |= ST_NONFINITE;
   if (st) atomicOr(A.status, st);
+  if (A.budget != nullptr) {
+    // (reading R13) the energy the gas gives up to the flux absorption and the energy the E
+    // floor adds, weighted as the RK combination weighs this stage's interaction; one add per
+    // cell into the block's budget row (the budgets are a diagnostic, off in production runs)
+    const double wv = cell_volume(A, c) * A.bw_cpl;
+    double* row = A.budget + (size_t)(blockIdx.x % BUDGET_SLOTS) * NBUDGET;
+    if (dwork != 0.0) atomicAdd(row + 6, dwork * ic2 * wv);
+    if (fadd != 0.0) atomicAdd(row + 7, fadd * wv);
+  }
 }
 
 }  // namespace fx

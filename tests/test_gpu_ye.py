@@ -191,3 +191,46 @@ def test_three_species_with_velocity_terms(fxmod, name, precision):
     plain, _ = oracle.run(pb, s0, pb.dt, pb.nsteps, nthreads=8)
     rad = slice((2 + pb.dims) * pb.ncell, -pb.ncell)
     assert np.abs(plain[rad] - ref[rad]).max() > 1e-6 * np.abs(ref[rad]).max()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32n64", 1e-6)])
+def test_three_species_budgets(fxmod, precision, tol):
+    # budgets with three species and the velocity terms: the flux-absorption work and the E floor
+    # of the two-equation interaction and the terms' radiation energy equal the oracle's, and the
+    # total energy closes with them (periodic box)
+    from tests.test_oracle_ye import species_vterms_problem, species_vterms_state
+    pb = species_vterms_problem(couple=1)
+    pb.precision = precision
+    s0 = species_vterms_state(pb, seed=3)
+    dt = 0.3 / max(pb.n[:2]) / pb.c_light
+    _, rst, rbud = oracle.run_budget(pb, s0, dt, 3, nthreads=8)
+    g = fxmod.Grid(pb)
+    g.upload(s0)
+    t0 = g.totals()
+    g.budgets_enable(True)
+    g.step(dt, 3)
+    assert g.status() == 0 and rst == 0
+    bud = g.budgets()
+    t1 = g.totals()
+    g.close()
+    assert abs(bud[6]) > 1e-6 * abs(t0[4]) and abs(bud[8]) > 1e-6 * abs(t0[4])
+    assert np.all(np.abs(bud - rbud) <= tol * abs(t0[4])), (bud, rbud)
+    closure = abs(t0[4] - t1[4] - bud[4] - bud[6] + bud[7] + bud[8])
+    assert closure <= (1e-13 if precision == "fp64" else 1e-6) * abs(t0[4]), closure
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32n64"])
+def test_three_species_totals_after_upload(fxmod, precision):
+    # the conserved totals of an uploaded three-species state, every form, on a grid small enough
+    # that a write past the Planck table's workspace region would reach the totals' cell volumes
+    from tests.test_oracle_ye import species_vterms_problem, species_vterms_state
+    pb = species_vterms_problem(couple=1)
+    pb.precision = precision
+    s0 = species_vterms_state(pb, seed=3)
+    g = fxmod.Grid(pb)
+    g.upload(s0)
+    t = g.totals()
+    g.close()
+    ref = oracle.totals(pb, s0)
+    np.testing.assert_allclose(t, ref, rtol=1e-13 if precision == "fp64" else 1e-6,
+                               atol=1e-12 * np.abs(ref).max())
