@@ -145,25 +145,30 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
     const double e = sqrt(gc.edge[k % Gs] * gc.edge[k % Gs + 1]);
     return s == 0 ? -xi0 / e : (s == 1 ? xi0 / e : 0.0);
   };
-  // residuals and Jacobian at (T, Y); with keep, the channel energies into En
+  // residuals and Jacobian at (T, Y); with keep, the channel energies into En.  A band edge is
+  // evaluated once (the upper edge of group g is the lower edge of g + 1), and the backward-Euler
+  // factor 1/(1 + tau) and xi once per group (the three species share the group's opacity)
   auto eval = [&](double T, double Y, double& rE, double& rX, double J[2][2], bool keep) {
     double dE = 0.0, dX = 0.0, eT = 0.0, eY = 0.0, xT = 0.0, xY = 0.0;
     const double invT = 1.0 / T, T3 = T * T * T;
     const double kT = kpre * hpow(T, g.kap_T_h);
+    PlanckEdge<double> lo = planck_edge64(gc.edge[0] * invT, A.pk.c64);
     for (int gg = 0; gg < Gs; ++gg) {
-      const PlanckEdge<double> lo = planck_edge64(gc.edge[gg] * invT, A.pk.c64);
       const PlanckEdge<double> hi = planck_edge64(gc.edge[gg + 1] * invT, A.pk.c64);
       const double I = planck_band(lo, hi);
       const double B = norm * T3 * T * I, dB = norm * (4.0 * T3 * I + T3 * (lo.w - hi.w));
+      lo = hi;
       const double kap = kT * gc.efac[gg];
       const double tau = cl * dt * kap, dtau = tau * (0.5 * g.kap_T_h * invT);
+      const double inv = 1.0 / (1.0 + tau);
+      const double xg = xi0 / sqrt(gc.edge[gg] * gc.edge[gg + 1]);
       for (int s = 0; s < 3; ++s) {
         const int k = s * Gs + gg;
-        const double w = ye_w(s, Y), dw = ye_dw(s), xi = xi_of(k);
+        const double w = ye_w(s, Y), dw = ye_dw(s), xi = s == 0 ? -xg : (s == 1 ? xg : 0.0);
         const double Eq = w * B;
-        const double Ek = (Em[k] + tau * Eq) / (1.0 + tau);
-        const double dT_ = (tau * w * dB + dtau * (Eq - Ek)) / (1.0 + tau);
-        const double dY_ = tau * dw * B / (1.0 + tau);
+        const double Ek = (Em[k] + tau * Eq) * inv;
+        const double dT_ = (tau * w * dB + dtau * (Eq - Ek)) * inv;
+        const double dY_ = tau * dw * B * inv;
         dE += Ek - Em[k];
         dX += xi * (Ek - Em[k]);
         eT += dT_;
