@@ -114,8 +114,9 @@ enum { FX_NTOTALS = 6, FX_NBUDGET = 9 };
  *                      groups form their own chain in frequency; the terms leave rho Y_e
  *                      unchanged while moving energy between groups of different xi, so they do
  *                      not conserve rho Y_e - sum xi E.  Without boundary layers or the adjoint
- *                      (FX_ERR_UNSUPPORTED); in the FP32 forms the interaction computes in FP64
- *                      and stores the FP32 state.
+ *                      (FX_ERR_UNSUPPORTED); in the FP32 forms the interaction iterates in FP64
+ *                      on the FP32 Planck band table, to FP32 resolution, and stores the FP32
+ *                      state.
  */
 typedef struct {
   int dims;

@@ -7,7 +7,9 @@
 //   comp_kernel: its finite-volume update and RK combination (the gas mass flux times the
 //     reconstructed Y_e on the v* upwind side of each face, the HLLC passive-scalar flux);
 //   couple_ye_kernel: the interaction, one thread per cell, in FP64 arithmetic for the FP64
-//     and the FP32 state alike (the FP32 forms store the result in FP32).  Inner backward-Euler update of
+//     and the FP32 state alike (the FP32 forms store the result in FP32); with the FP32 state
+//     the band energies B_g(T) come from the FP32 Planck band table (as in the one-species FP32
+//     interaction) and the iteration stops at FP32 resolution.  Inner backward-Euler update of
 //     every channel at (T, Y_e), with the equilibrium energy w_s(Y_e) B_g(T), w = 2 Y_e,
 //     2 (1 - Y_e), 1, and the lepton number per unit energy xi = -xi0/eps_g, +xi0/eps_g, 0;
 //     outer residuals r_E = u(T) - u^- + sum dE and r_X = rho (Y_e - Y_e^-) - sum xi dE, solved
@@ -18,6 +20,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "fx_couple.cuh"
 #include "fx_stage.cuh"
 
 namespace fx {
@@ -101,11 +104,15 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   double* En = Em + CPLYE_THREADS * RS;                              // the last evaluation's E
   const uint32_t ncell = (uint32_t)g.ncell;
   const uint32_t c = blockIdx.x * CPLYE_THREADS + threadIdx.x;
+  const GroupConst& gc = *A.gc;
+  // 1 / eps_g of each group (centre sqrt(eps_{g-1/2} eps_{g+1/2})), once per block
+  __shared__ double s_icen[MAXG];
+  for (int j = threadIdx.x; j < Gs; j += CPLYE_THREADS) s_icen[j] = 1.0 / sqrt(gc.edge[j] * gc.edge[j + 1]);
+  __syncthreads();
   if (c >= ncell) return;
   const double cl = g.c, dt = A.dts, cv = 1.0 / (g.gamma - 1.0), xi0 = g.xi0;
   R* U = A.out;
   const uint32_t rad = (uint32_t)NG * ncell, XO = (uint32_t)(NG + NRV * G) * ncell;
-  const GroupConst& gc = *A.gc;
   unsigned st = 0;
   double rho = U[c];
   if (rho < g.rho_floor) { rho = g.rho_floor; U[c] = (R)rho; st |= ST_FLOOR; }
@@ -136,32 +143,45 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
     Em[k] = E;
     Esum += E;
     const int s = k / Gs;
-    if (s < 2) Lsum += fabs(xi0 / sqrt(gc.edge[k % Gs] * gc.edge[k % Gs + 1])) * E;
+    if (s < 2) Lsum += fabs(xi0 * s_icen[k % Gs]) * E;
   }
   const double norm = g.a_rad * 0.15398973382026502;  // a_R 15/pi^4
   const double kpre = g.kappa0 * hpow(rho, g.kap_rho_h);
   auto xi_of = [&](int k) -> double {
     const int s = k / Gs;
-    const double e = sqrt(gc.edge[k % Gs] * gc.edge[k % Gs + 1]);
-    return s == 0 ? -xi0 / e : (s == 1 ? xi0 / e : 0.0);
+    const double xg = xi0 * s_icen[k % Gs];
+    return s == 0 ? -xg : (s == 1 ? xg : 0.0);
   };
   // residuals and Jacobian at (T, Y); with keep, the channel energies into En.  A band edge is
   // evaluated once (the upper edge of group g is the lower edge of g + 1), and the backward-Euler
   // factor 1/(1 + tau) and xi once per group (the three species share the group's opacity)
+  constexpr bool F32 = std::is_same<R, float>::value;
   auto eval = [&](double T, double Y, double& rE, double& rX, double J[2][2], bool keep) {
     double dE = 0.0, dX = 0.0, eT = 0.0, eY = 0.0, xT = 0.0, xY = 0.0;
     const double invT = 1.0 / T, T3 = T * T * T;
     const double kT = kpre * hpow(T, g.kap_T_h);
-    PlanckEdge<double> lo = planck_edge64(gc.edge[0] * invT, A.pk.c64);
+    PlanckEdge<double> lo{};
+    PlanckAt pa{};
+    if constexpr (F32) pa = planck_at(A.ptab, A.kf.aN, (float)T);
+    else lo = planck_edge64(gc.edge[0] * invT, A.pk.c64);
     for (int gg = 0; gg < Gs; ++gg) {
-      const PlanckEdge<double> hi = planck_edge64(gc.edge[gg + 1] * invT, A.pk.c64);
-      const double I = planck_band(lo, hi);
-      const double B = norm * T3 * T * I, dB = norm * (4.0 * T3 * I + T3 * (lo.w - hi.w));
-      lo = hi;
+      double B, dB;
+      if constexpr (F32) {
+        float Bf, dBf;
+        planck_group(A.ptab, pa, gg, gc.edge32, Bf, dBf);
+        B = Bf;
+        dB = dBf;
+      } else {
+        const PlanckEdge<double> hi = planck_edge64(gc.edge[gg + 1] * invT, A.pk.c64);
+        const double I = planck_band(lo, hi);
+        B = norm * T3 * T * I;
+        dB = norm * (4.0 * T3 * I + T3 * (lo.w - hi.w));
+        lo = hi;
+      }
       const double kap = kT * gc.efac[gg];
       const double tau = cl * dt * kap, dtau = tau * (0.5 * g.kap_T_h * invT);
       const double inv = 1.0 / (1.0 + tau);
-      const double xg = xi0 / sqrt(gc.edge[gg] * gc.edge[gg + 1]);
+      const double xg = xi0 * s_icen[gg];
       for (int s = 0; s < 3; ++s) {
         const int k = s * Gs + gg;
         const double w = ye_w(s, Y), dw = ye_dw(s), xi = s == 0 ? -xg : (s == 1 ? xg : 0.0);
@@ -185,17 +205,21 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
     J[1][0] = -xT;
     J[1][1] = rho - xY;
   };
+  // stopping tests: FP64 resolution for the FP64 state; with the FP32 band table, the FP32
+  // forms' tolerances (relative step 2e-7 at least, residual 1e-7)
+  const double rtol = F32 ? A.kd.rtol : g.newton_rtol;
+  const double n2ok = F32 ? A.kd.atol * A.kd.atol : 1e-28, n2fb = F32 ? n2ok : 1e-24;
   const double sE = u_m + Esum, sX = fabs(X_m) + Lsum + 1e-300;
   auto norm2 = [&](double rE, double rX) { const double a = rE / sE, b = rX / sX; return a * a + b * b; };
   double T = u_m / (rho * cv), Y = Y_m, rE, rX, J[2][2];
   eval(T, Y, rE, rX, J, false);
   bool ok = false;
   for (int it = 0; it < g.newton_maxit; ++it) {
-    if (norm2(rE, rX) <= 1e-28) { ok = true; break; }
+    if (norm2(rE, rX) <= n2ok) { ok = true; break; }
     const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
     const double dT = -(J[1][1] * rE - J[0][1] * rX) / det;
     const double dY = -(J[0][0] * rX - J[1][0] * rE) / det;
-    if (fabs(dT) <= g.newton_rtol * T && fabs(dY) <= g.newton_rtol * fmax(Y, 1e-3)) {
+    if (fabs(dT) <= rtol * T && fabs(dY) <= rtol * fmax(Y, 1e-3)) {
       T = T + dT;
       Y = Y + dY;
       ok = true;
@@ -228,21 +252,21 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
       for (int k = 0; k < 200 && r1 > 0.0; ++k) { lo = 0.5 * lo; eval(lo, Y, r1, r2, Jd, false); }
       eval(hi, Y, rh, r2, Jd, false);
       for (int k = 0; k < 200 && rh < 0.0; ++k) { hi = 2.0 * hi; eval(hi, Y, rh, r2, Jd, false); }
-      for (int k = 0; k < g.bisect_maxit && hi - lo > g.newton_rtol * hi; ++k) {
+      for (int k = 0; k < g.bisect_maxit && hi - lo > rtol * hi; ++k) {
         const double mid = 0.5 * (lo + hi);
         eval(mid, Y, rm, r2, Jd, false);
         if (rm > 0.0) hi = mid; else lo = mid;
       }
       T = 0.5 * (lo + hi);
       double ylo = 0.0, yhi = 1.0;
-      for (int k = 0; k < g.bisect_maxit && yhi - ylo > g.newton_rtol; ++k) {
+      for (int k = 0; k < g.bisect_maxit && yhi - ylo > rtol; ++k) {
         const double mid = 0.5 * (ylo + yhi);
         eval(T, mid, r1, rm, Jd, false);
         if (rm > 0.0) yhi = mid; else ylo = mid;
       }
       Y = 0.5 * (ylo + yhi);
       eval(T, Y, rE, rX, J, false);
-      if (norm2(rE, rX) <= 1e-24) ok = true;
+      if (norm2(rE, rX) <= n2fb) ok = true;
     }
     if (!ok) st |= ST_NEWTON;
   }
