@@ -115,8 +115,8 @@ enum { FX_NTOTALS = 6, FX_NBUDGET = 9 };
  *                      unchanged while moving energy between groups of different xi, so they do
  *                      not conserve rho Y_e - sum xi E.  Without boundary layers or the adjoint
  *                      (FX_ERR_UNSUPPORTED); in the FP32 forms the interaction iterates in FP64
- *                      on the FP32 Planck band table, to FP32 resolution, and stores the FP32
- *                      state.
+ *                      on the FP32 Planck band table with FP32 channel arithmetic, to FP32
+ *                      resolution, and stores the FP32 state.
  */
 typedef struct {
   int dims;

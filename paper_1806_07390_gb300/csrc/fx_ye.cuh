@@ -6,10 +6,11 @@
 // a block after the radiation block.
 //   comp_kernel: its finite-volume update and RK combination (the gas mass flux times the
 //     reconstructed Y_e on the v* upwind side of each face, the HLLC passive-scalar flux);
-//   couple_ye_kernel: the interaction, one thread per cell, in FP64 arithmetic for the FP64
+//   couple_ye_kernel: the interaction, one thread per cell, the iterate in FP64 for the FP64
 //     and the FP32 state alike (the FP32 forms store the result in FP32); with the FP32 state
 //     the band energies B_g(T) come from the FP32 Planck band table (as in the one-species FP32
-//     interaction) and the iteration stops at FP32 resolution.  Inner backward-Euler update of
+//     interaction), the channel arithmetic is FP32 and the iteration stops at FP32 resolution.
+//     Inner backward-Euler update of
 //     every channel at (T, Y_e), with the equilibrium energy w_s(Y_e) B_g(T), w = 2 Y_e,
 //     2 (1 - Y_e), 1, and the lepton number per unit energy xi = -xi0/eps_g, +xi0/eps_g, 0;
 //     outer residuals r_E = u(T) - u^- + sum dE and r_X = rho (Y_e - Y_e^-) - sum xi dE, solved
@@ -180,22 +181,50 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
       }
       const double kap = kT * gc.efac[gg];
       const double tau = cl * dt * kap, dtau = tau * (0.5 * g.kap_T_h * invT);
-      const double inv = 1.0 / (1.0 + tau);
       const double xg = xi0 * s_icen[gg];
-      for (int s = 0; s < 3; ++s) {
-        const int k = s * Gs + gg;
-        const double w = ye_w(s, Y), dw = ye_dw(s), xi = s == 0 ? -xg : (s == 1 ? xg : 0.0);
-        const double Eq = w * B;
-        const double Ek = (Em[k] + tau * Eq) * inv;
-        const double dT_ = (tau * w * dB + dtau * (Eq - Ek)) * inv;
-        const double dY_ = tau * dw * B * inv;
-        dE += Ek - Em[k];
-        dX += xi * (Ek - Em[k]);
-        eT += dT_;
-        eY += dY_;
-        xT += xi * dT_;
-        xY += xi * dY_;
-        if (keep) En[k] = Ek;
+      if constexpr (F32) {
+        // the FP32 forms: the three species' channel arithmetic in FP32, the group's partial
+        // sums added to the FP64 sums once
+        const float tf = (float)tau, dtf = (float)dtau, invf = frcp(1.0f + tf), xf = (float)xg;
+        const float Bf = (float)B, dBf = (float)dB, Yf = (float)Y;
+        float sE = 0.0f, sX = 0.0f, sT = 0.0f, sY = 0.0f, qT = 0.0f, qY = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          const int k = s * Gs + gg;
+          const float w = s == 0 ? 2.0f * Yf : (s == 1 ? 2.0f * (1.0f - Yf) : 1.0f);
+          const float dw = s == 0 ? 2.0f : (s == 1 ? -2.0f : 0.0f);
+          const float xi = s == 0 ? -xf : (s == 1 ? xf : 0.0f);
+          const float Emk = (float)Em[k], Eq = w * Bf;
+          const float Ek = (Emk + tf * Eq) * invf;
+          const float dT_ = (tf * w * dBf + dtf * (Eq - Ek)) * invf;
+          const float dY_ = tf * dw * Bf * invf;
+          const float d = Ek - Emk;
+          sE += d;
+          sX += xi * d;
+          sT += dT_;
+          sY += dY_;
+          qT += xi * dT_;
+          qY += xi * dY_;
+          if (keep) En[k] = (double)Ek;
+        }
+        dE += sE; dX += sX; eT += sT; eY += sY; xT += qT; xY += qY;
+      } else {
+        const double inv = 1.0 / (1.0 + tau);
+        for (int s = 0; s < 3; ++s) {
+          const int k = s * Gs + gg;
+          const double w = ye_w(s, Y), dw = ye_dw(s), xi = s == 0 ? -xg : (s == 1 ? xg : 0.0);
+          const double Eq = w * B;
+          const double Ek = (Em[k] + tau * Eq) * inv;
+          const double dT_ = (tau * w * dB + dtau * (Eq - Ek)) * inv;
+          const double dY_ = tau * dw * B * inv;
+          dE += Ek - Em[k];
+          dX += xi * (Ek - Em[k]);
+          eT += dT_;
+          eY += dY_;
+          xT += xi * dT_;
+          xY += xi * dY_;
+          if (keep) En[k] = Ek;
+        }
       }
     }
     rE = rho * cv * T - u_m + dE;
