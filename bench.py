@@ -127,8 +127,11 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-def time_form(pb, prim, steps, warmup, dist):
-    """Device-timed K steps of one precision form with inputs resident in HBM."""
+def time_form(pb, prim, steps, warmup, dist, graph_replay=False):
+    """Device-timed K steps of one precision form with inputs resident in HBM.  The timed region
+    carries the per-kernel CUDA events (the roofline's kernel durations), so fx_step launches
+    the kernels one by one there.  With graph_replay, K more steps follow without the per-kernel
+    events, which fx_step replays as a captured CUDA graph of a step (returned in kt)."""
     import torch
 
     from paper_1806_07390_gb300 import fx
@@ -156,6 +159,16 @@ def time_form(pb, prim, steps, warmup, dist):
     ms = e0.elapsed_time(e1)
     kt = g.kernel_times()
     g.kernel_timing(False)
+    if graph_replay:
+        g.step(pb.dt, 1)  # the first step without events captures the graph
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(s)
+        for _ in range(steps):
+            g.step(pb.dt, 1)
+        f1.record(s)
+        f1.synchronize()
+        kt["graph_ms"] = max_over_ranks(f0.elapsed_time(f1)) if dist else f0.elapsed_time(f1)
     st = g.status()
     if dist:
         ms = max_over_ranks(ms)
@@ -432,7 +445,8 @@ def main():
 
     results = {}
     with ClockSampler(dev) as clk:
-        gh, msh, sth, launchesh, kth = time_form(pbh, prim, args.steps, args.warmup, dist)
+        gh, msh, sth, launchesh, kth = time_form(pbh, prim, args.steps, args.warmup, dist,
+                                                 graph_replay=True)
         for name, pbf in forms.items():
             gf, msf, stf, lf, ktf = time_form(pbf, prim, args.steps, args.warmup, dist)
             results[name] = (msf, stf, lf, ktf)
@@ -521,6 +535,12 @@ def main():
             "gpu_launches_all_timed_regions": launchesh + sum(r[2] for r in results.values()) +
                                               (lv if pbv is not None else 0),
             "clocks": clocks, "status": int(sth), "forms": {}}
+    if "graph_ms" in kth:
+        line["graph_replay"] = {
+            "note": "the same form and steps right after the timed region, without the per-kernel "
+                    "events: fx_step replays one captured CUDA graph per step",
+            "ms_per_step": kth["graph_ms"] / args.steps,
+            "value": whole_job_rate(zg * 2 * args.steps, world, kth["graph_ms"] / 1e3), "unit": UNIT}
     for name, (msf, stf, lf, ktf) in results.items():
         secf = msf / 1e3
         line["forms"][name] = {"value": whole_job_rate(zg * 2 * args.steps, world, secf), "unit": UNIT,

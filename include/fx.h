@@ -181,7 +181,11 @@ fx_status fx_state_init_equilibrium(fx_grid* h, const double* prim, int prim_is_
 
 /* Enqueue nsteps SSP-RK2 steps of size dt on the bound stream (asynchronous).  Returns FX_OK
  * unless arguments are invalid, a launch fails or an earlier error is pending; device-side
- * conditions (Newton failure, floors, non-finite values) are reported by fx_sync(). */
+ * conditions (Newton failure, floors, non-finite values) are reported by fx_sync().  Without
+ * boundary layers, per-kernel timing and the objective, a step is captured once as a CUDA graph
+ * (on a stream the library creates) and replayed per step; the capture is kept while dt, the
+ * workspace, the budgets flag, kappa0 and the march chunk stay the same.  If capture fails the
+ * kernels are launched one by one, with no status set. */
 fx_status fx_step(fx_grid* h, double dt, int nsteps);
 
 /* Wait for the bound stream and return the sticky status, including device-side conditions

@@ -144,6 +144,15 @@ struct fx_grid {
   bool objective = false;
   size_t off_phi = 0, off_obj = 0;
   size_t off_bud = 0;  // budgets (reading R13): rows of FP64 accumulators, see StageArgs::budget
+  // One step (both stages) as a CUDA graph, replayed by fx_step while nothing that its launches
+  // capture changes: the step, the workspace, the budgets flag, kappa0 and the march chunk (the
+  // key).  Captured on the handle's own stream (capture is not available on the legacy default
+  // stream), launched on the bound one.  Not used with boundary layers, per-kernel timing or the
+  // objective (their launches change from step to step or need host events).
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  struct StepKey { double dt, kappa0; const void* ws; int budgets, chunk; } step_key{};
+  bool graphs_ok = true;  // false after a capture failed: launch directly from then on
   bool budgets = false;  // accumulate the budgets during fx_step
   int64_t phi_rows = 0;
   double phi_area = 0.0;
@@ -738,6 +747,46 @@ fx_status launch_one_stage(fx_grid* h, const StageArgs<R>& a, const char* what) 
   return FX_OK;
 }
 
+// One step's launches (stage 1, stage 2) captured as a CUDA graph on the handle's own stream;
+// null when the stream, the capture or the instantiation fails (fx_step then launches directly;
+// the failure sets no sticky status).
+template <class R, class NT>
+cudaGraphExec_t capture_step(fx_grid* h, const StageArgs<R>& a1, const StageArgs<R>& a2) {
+  if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    h->cap_stream = nullptr;
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  auto launch = [&](const StageArgs<R>& a) -> cudaError_t {
+    switch (h->D) {
+      case 1: return launch_stage<R, 1, NT, false>(a, h->GP, h->cap_stream, nullptr, nullptr);
+      case 2:
+        return h->P.geom == FX_SPH ? launch_stage<R, 2, NT, true>(a, h->GP, h->cap_stream, nullptr, nullptr)
+                                   : launch_stage<R, 2, NT, false>(a, h->GP, h->cap_stream, nullptr, nullptr);
+      default: return launch_stage<R, 3, NT, false>(a, h->GP, h->cap_stream, nullptr, nullptr);
+    }
+  };
+  // the step waits for the bound stream's earlier work through the graph launch itself
+  if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  cudaError_t e = launch(a1);
+  if (e == cudaSuccess) e = launch(a2);
+  cudaGraph_t gph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &gph);
+  if (e == cudaSuccess) e = ee;
+  cudaGraphExec_t ex = nullptr;
+  if (e == cudaSuccess && gph) e = cudaGraphInstantiate(&ex, gph, 0);
+  if (gph) cudaGraphDestroy(gph);
+  if (e != cudaSuccess || !ex) {
+    if (ex) cudaGraphExecDestroy(ex);
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return ex;
+}
+
 template <class R, class NT>
 fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
   StageArgs<R> a = stage_args<R>(h);
@@ -768,6 +817,26 @@ fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FX_OK : cuda_fail(h, e, "boundary layer launch");
   };
+  if (h->graphs_ok && !h->timing && !a.phi_out && h->layers.n == 0 && nsteps > 0) {
+    const fx_grid::StepKey key{dt, h->P.kappa0, h->ws, h->budgets ? 1 : 0, h->chunk};
+    if (h->step_exec && std::memcmp(&key, &h->step_key, sizeof(key)) != 0) {
+      cudaGraphExecDestroy(h->step_exec);
+      h->step_exec = nullptr;
+    }
+    if (!h->step_exec) {
+      h->step_exec = capture_step<R, NT>(h, a1, a2);
+      h->step_key = key;
+      if (!h->step_exec) h->graphs_ok = false;
+    }
+    if (h->step_exec) {
+      for (int s = 0; s < nsteps; ++s) {
+        const cudaError_t e = cudaGraphLaunch(h->step_exec, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step graph launch");
+        h->time += dt;
+      }
+      return FX_OK;
+    }
+  }
   for (int s = 0; s < nsteps; ++s) {
     const double t1 = h->time + dt;
     fx_status st = layers(A, h->time);
@@ -1445,6 +1514,10 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
     return fail(h, FX_ERR_WORKSPACE, "workspace missing, too small or not 256-byte aligned");
   h->ws = static_cast<unsigned char*>(dev_ptr);
   h->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (h->step_exec) {  // its launches point into the previous workspace
+    cudaGraphExecDestroy(h->step_exec);
+    h->step_exec = nullptr;
+  }
   cudaError_t e;
   if (!h->h_status) {
     e = cudaMallocHost(&h->h_status, sizeof(unsigned));
@@ -1704,6 +1777,8 @@ fx_status fx_kernel_timing_read(fx_grid* h, double out[6]) {
 
 void fx_grid_destroy(fx_grid* h) {
   if (!h) return;
+  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t x : h->ev) cudaEventDestroy(x);
   if (h->h_status) cudaFreeHost(h->h_status);
   delete h;
