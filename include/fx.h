@@ -182,10 +182,10 @@ fx_status fx_state_init_equilibrium(fx_grid* h, const double* prim, int prim_is_
 /* Enqueue nsteps SSP-RK2 steps of size dt on the bound stream (asynchronous).  Returns FX_OK
  * unless arguments are invalid, a launch fails or an earlier error is pending; device-side
  * conditions (Newton failure, floors, non-finite values) are reported by fx_sync().  Without
- * boundary layers, per-kernel timing and the objective, a step is captured once as a CUDA graph
- * (on a stream the library creates) and replayed per step; the capture is kept while dt, the
- * workspace, the budgets flag, kappa0 and the march chunk stay the same.  If capture fails the
- * kernels are launched one by one, with no status set. */
+ * per-kernel timing and the objective, a step is captured once as a CUDA graph (on a stream the
+ * library creates) and replayed per step; the capture is kept while dt, the workspace, the
+ * budgets flag, kappa0, the march chunk and the boundary layers stay the same.  If capture
+ * fails the kernels are launched one by one, with no status set. */
 fx_status fx_step(fx_grid* h, double dt, int nsteps);
 
 /* Wait for the bound stream and return the sticky status, including device-side conditions
@@ -249,14 +249,16 @@ typedef struct {
 } fx_layer;
 fx_status fx_boundary_layers(fx_grid* h, const fx_layer* layers, int n, double t0);
 
-/* Copy the state out, converting to dst_precision, to host (synchronous) or device memory. *//* Copy the state out, converting to dst_precision, to host (synchronous) or device memory. */
+/* Copy the state out, converting to dst_precision, to host (synchronous) or device memory. */
 fx_status fx_state_download(fx_grid* h, void* dst, int dst_precision, int dst_is_device);
 
 /* Number of kernel launches enqueued by one fx_step(dt, 1) call (per RK stage: the gas face
- * kernel, the radiation/update kernel, with the interaction on the interaction kernel, with
- * the carbuncle guard on the shock-flag kernel, with vterms the velocity-term kernel, and the
+ * kernel, the radiation/update kernel, with the interaction on the interaction kernel (the
+ * two-equation one with three species), with the carbuncle guard on the shock-flag kernel, with
+ * vterms the velocity-term kernel, with three species the composition kernel, and the
  * objective's reduction while it is enabled; per step, with boundary layers, three layer
- * launches). */
+ * launches and the advance of the layers' time).  A step replayed as a captured graph launches
+ * the same kernels. */
 int fx_launches_per_step(const fx_grid* h);
 
 /* Planes of the slowest axis that one block of the radiation/update kernel marches over: 32 (or

@@ -747,6 +747,27 @@ fx_status launch_one_stage(fx_grid* h, const StageArgs<R>& a, const char* what) 
   return FX_OK;
 }
 
+// Boundary layers of state U at the step's time + toff, and the end-of-step advance of the
+// layers' time (no status set: the caller reports a failed launch).
+template <class R>
+cudaError_t launch_layers(fx_grid* h, R* U, double toff, cudaStream_t st) {
+  if (h->layers.n == 0) return cudaSuccess;
+  int nmax = 1;
+  for (int q = 0; q < h->layers.n; ++q) {
+    const LayerDev& L = h->layers.L[q];
+    const int64_t nb = (int64_t)(L.hi[0] - L.lo[0]) * (L.hi[1] - L.lo[1]) * (L.hi[2] - L.lo[2]);
+    nmax = std::max(nmax, (int)std::min<int64_t>((nb + LAYER_THREADS - 1) / LAYER_THREADS, 4096));
+  }
+  const LayerSet* ls = reinterpret_cast<const LayerSet*>(h->ws + h->off_layers);
+  layer_kernel<R><<<dim3((unsigned)nmax, (unsigned)h->layers.n, 1), LAYER_THREADS, 0, st>>>(ls, U, h->dg, toff);
+  return cudaGetLastError();
+}
+inline cudaError_t launch_layer_advance(fx_grid* h, double dt, cudaStream_t st) {
+  if (h->layers.n == 0) return cudaSuccess;
+  layer_advance<<<1, 32, 0, st>>>(reinterpret_cast<LayerSet*>(h->ws + h->off_layers), dt);
+  return cudaGetLastError();
+}
+
 // One step's launches (stage 1, stage 2) captured as a CUDA graph on the handle's own stream;
 // null when the stream, the capture or the instantiation fails (fx_step then launches directly;
 // the failure sets no sticky status).
@@ -771,8 +792,15 @@ cudaGraphExec_t capture_step(fx_grid* h, const StageArgs<R>& a1, const StageArgs
     (void)cudaGetLastError();
     return nullptr;
   }
-  cudaError_t e = launch(a1);
+  R* A = const_cast<R*>(a1.in);
+  R* B = a1.out;
+  const double dt = a1.dt;
+  cudaError_t e = launch_layers<R>(h, A, 0.0, h->cap_stream);
+  if (e == cudaSuccess) e = launch(a1);
+  if (e == cudaSuccess) e = launch_layers<R>(h, B, dt, h->cap_stream);
   if (e == cudaSuccess) e = launch(a2);
+  if (e == cudaSuccess) e = launch_layers<R>(h, A, dt, h->cap_stream);
+  if (e == cudaSuccess) e = launch_layer_advance(h, dt, h->cap_stream);
   cudaGraph_t gph = nullptr;
   const cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &gph);
   if (e == cudaSuccess) e = ee;
@@ -803,21 +831,13 @@ fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
   set_stage(h, a2, 2, dt);
   a1.in = A; a1.base = nullptr; a1.out = B;
   a2.in = B; a2.base = A; a2.out = A;
-  // boundary layers: the stage-1 input at t, the stage-2 input and the result at t + dt
-  const LayerSet* ls = reinterpret_cast<const LayerSet*>(h->ws + h->off_layers);
-  auto layers = [&](R* U, double t) -> fx_status {
-    if (h->layers.n == 0) return FX_OK;
-    int nmax = 1;
-    for (int q = 0; q < h->layers.n; ++q) {
-      const LayerDev& L = h->layers.L[q];
-      const int64_t nb = (int64_t)(L.hi[0] - L.lo[0]) * (L.hi[1] - L.lo[1]) * (L.hi[2] - L.lo[2]);
-      nmax = std::max(nmax, (int)std::min<int64_t>((nb + LAYER_THREADS - 1) / LAYER_THREADS, 4096));
-    }
-    layer_kernel<R><<<dim3((unsigned)nmax, (unsigned)h->layers.n, 1), LAYER_THREADS, 0, h->stream>>>(ls, U, h->dg, t);
-    cudaError_t e = cudaGetLastError();
+  // boundary layers: the stage-1 input at the step's time t, the stage-2 input and the result at
+  // t + dt; then t advances on the device
+  auto layers = [&](R* U, double toff) -> fx_status {
+    const cudaError_t e = launch_layers<R>(h, U, toff, h->stream);
     return e == cudaSuccess ? FX_OK : cuda_fail(h, e, "boundary layer launch");
   };
-  if (h->graphs_ok && !h->timing && !a.phi_out && h->layers.n == 0 && nsteps > 0) {
+  if (h->graphs_ok && !h->timing && !a.phi_out && nsteps > 0) {
     const fx_grid::StepKey key{dt, h->P.kappa0, h->ws, h->budgets ? 1 : 0, h->chunk};
     if (h->step_exec && std::memcmp(&key, &h->step_key, sizeof(key)) != 0) {
       cudaGraphExecDestroy(h->step_exec);
@@ -838,16 +858,17 @@ fx_status enqueue_steps(fx_grid* h, double dt, int nsteps) {
     }
   }
   for (int s = 0; s < nsteps; ++s) {
-    const double t1 = h->time + dt;
-    fx_status st = layers(A, h->time);
+    fx_status st = layers(A, 0.0);
     if (st != FX_OK) return st;
     st = launch_one_stage<R, NT>(h, a1, "stage 1 launch");
     if (st != FX_OK) return st;
-    if ((st = layers(B, t1)) != FX_OK) return st;
+    if ((st = layers(B, dt)) != FX_OK) return st;
     st = launch_one_stage<R, NT>(h, a2, "stage 2 launch");
     if (st != FX_OK) return st;
-    if ((st = layers(A, t1)) != FX_OK) return st;
-    h->time = t1;
+    if ((st = layers(A, dt)) != FX_OK) return st;
+    const cudaError_t e = launch_layer_advance(h, dt, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "boundary layer launch");
+    h->time += dt;
   }
   return FX_OK;
 }
@@ -1346,8 +1367,13 @@ fx_status fx_boundary_layers(fx_grid* h, const fx_layer* layers, int n, double t
       }
     }
   }
+  S.t = t0;
   h->layers = S;
   h->time = t0;
+  if (h->step_exec) {  // a captured step holds the previous layer launches
+    cudaGraphExecDestroy(h->step_exec);
+    h->step_exec = nullptr;
+  }
   cudaError_t e = cudaMemcpyAsync(h->ws + h->off_layers, &h->layers, sizeof(LayerSet), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "boundary layer upload");
@@ -1358,7 +1384,7 @@ int fx_launches_per_step(const fx_grid* h) {
   if (!h) return 0;
   const bool split = h->P.couple != 0;  // the interaction kernel runs in every form
   return 2 * (2 + (split ? 1 : 0) + (h->objective ? 1 : 0) + (h->P.shock_guard > 0.0 ? 1 : 0) +
-              (h->P.vterms ? 1 : 0) + (h->dg.species > 1 ? 1 : 0)) + (h->layers.n > 0 ? 3 : 0);
+              (h->P.vterms ? 1 : 0) + (h->dg.species > 1 ? 1 : 0)) + (h->layers.n > 0 ? 4 : 0);
 }
 
 fx_status fx_objective_enable(fx_grid* h, int on) {

@@ -23,13 +23,17 @@ struct LayerSet {
   int n;
   double x_lo[3], dx[3];
   LayerDev L[MAX_LAYERS];
+  double t;  // time at the start of the current step (device copy: advanced by layer_advance)
 };
 
-// Grid row y = layer; the cells of its box strided over the row's blocks.
+// Grid row y = layer; the cells of its box strided over the row's blocks.  The layers are set at
+// time S->t + toff (toff = 0 for the stage-1 input, dt for the stage-2 input and the result), so
+// that a step's launches do not change from step to step (a captured graph replays them).
 template <class R>
-__global__ void __launch_bounds__(LAYER_THREADS) layer_kernel(const LayerSet* S, R* U, const DevGrid g, double t) {
+__global__ void __launch_bounds__(LAYER_THREADS) layer_kernel(const LayerSet* S, R* U, const DevGrid g, double toff) {
   const int q = blockIdx.y;
   if (q >= S->n) return;
+  const double t = S->t + toff;
   const LayerDev& L = S->L[q];
   const int D = g.D, G = g.G, NG = 2 + D;
   const int bx = L.hi[0] - L.lo[0], by = L.hi[1] - L.lo[1], bz = L.hi[2] - L.lo[2];
@@ -65,6 +69,12 @@ __global__ void __launch_bounds__(LAYER_THREADS) layer_kernel(const LayerSet* S,
       for (int v = 1; v <= D; ++v) U[NG * ncell + (v * ncell + c) * G + k] = R(0);
     }
   }
+}
+
+// The end of a step: the layers' time advances by dt (one thread, after the step's last layer
+// launch on the same stream).
+__global__ void layer_advance(LayerSet* S, double dt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) S->t = S->t + dt;
 }
 
 }  // namespace fx

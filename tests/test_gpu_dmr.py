@@ -46,9 +46,9 @@ def test_double_mach_reflection(fxmod, precision, tol, guard):
     ref, rst = oracle.run(pb, s0, pb.dt, pb.nsteps, nthreads=8, layers=layers)
     got, st, nl = run_gpu(fxmod, pb, s0, layers)
     assert st == 0 and rst == 0
-    # per step: two stages of faces, radiation/update (+ shock flags with the guard), and three
-    # layer launches
-    assert nl == 2 * (2 + (guard > 0)) + 3
+    # per step: two stages of faces, radiation/update (+ shock flags with the guard), three
+    # layer launches and the layers' time advance
+    assert nl == 2 * (2 + (guard > 0)) + 4
     if precision == "fp64":
         H.assert_parity(pb, got, ref, tol, 1e-8)
     else:
