@@ -101,8 +101,11 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   extern __shared__ __align__(16) unsigned char ye_raw[];
   const DevGrid& g = A.g;
   const int G = g.G, Gs = g.Gs, RS = G + 1;
-  double* Em = reinterpret_cast<double*>(ye_raw) + threadIdx.x * RS;  // E^- of the cell's channels
-  double* En = Em + CPLYE_THREADS * RS;                              // the last evaluation's E
+  // E^- of the cell's channels and the last evaluation's E: FP32 rows in the FP32 forms (their
+  // values are FP32 state values), FP64 rows in the FP64 form
+  using RT = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
+  RT* Em = reinterpret_cast<RT*>(ye_raw) + threadIdx.x * RS;
+  RT* En = Em + CPLYE_THREADS * RS;
   const uint32_t ncell = (uint32_t)g.ncell;
   const uint32_t c = blockIdx.x * CPLYE_THREADS + threadIdx.x;
   const GroupConst& gc = *A.gc;
@@ -141,7 +144,8 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   for (int k = 0; k < G; ++k) {
     double E = U[rad + c * (uint32_t)G + k];
     if (E < g.E_floor) { fadd += g.E_floor - E; E = g.E_floor; }
-    Em[k] = E;
+    Em[k] = (RT)E;
+    E = Em[k];  // (the FP32 forms: the floor as the FP32 state stores it)
     Esum += E;
     const int s = k / Gs;
     if (s < 2) Lsum += fabs(xi0 * s_icen[k % Gs]) * E;
@@ -157,36 +161,21 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   // evaluated once (the upper edge of group g is the lower edge of g + 1), and the backward-Euler
   // factor 1/(1 + tau) and xi once per group (the three species share the group's opacity)
   constexpr bool F32 = std::is_same<R, float>::value;
+  // FP32 forms: the opacity, tau and xi of each group in FP32 from the FP32 constants
+  const float kpref = (float)kpre, cdtf = (float)(cl * dt), xi0f = (float)xi0;
   auto eval = [&](double T, double Y, double& rE, double& rX, double J[2][2], bool keep) {
     double dE = 0.0, dX = 0.0, eT = 0.0, eY = 0.0, xT = 0.0, xY = 0.0;
-    const double invT = 1.0 / T, T3 = T * T * T;
-    const double kT = kpre * hpow(T, g.kap_T_h);
-    PlanckEdge<double> lo{};
-    PlanckAt pa{};
-    if constexpr (F32) pa = planck_at(A.ptab, A.kf.aN, (float)T);
-    else lo = planck_edge64(gc.edge[0] * invT, A.pk.c64);
-    for (int gg = 0; gg < Gs; ++gg) {
-      double B, dB;
-      if constexpr (F32) {
+    if constexpr (F32) {
+      // the three species' channel arithmetic in FP32 on the FP32 band table; each group's
+      // partial sums are added to the FP64 sums once
+      const float Tf = (float)T, Yf = (float)Y;
+      const PlanckAt pa = planck_at(A.ptab, A.kf.aN, Tf);
+      const float kTf = kpref * hpow(Tf, g.kap_T_h), hTf = 0.5f * (float)g.kap_T_h * pa.invT;
+      for (int gg = 0; gg < Gs; ++gg) {
         float Bf, dBf;
         planck_group(A.ptab, pa, gg, gc.edge32, Bf, dBf);
-        B = Bf;
-        dB = dBf;
-      } else {
-        const PlanckEdge<double> hi = planck_edge64(gc.edge[gg + 1] * invT, A.pk.c64);
-        const double I = planck_band(lo, hi);
-        B = norm * T3 * T * I;
-        dB = norm * (4.0 * T3 * I + T3 * (lo.w - hi.w));
-        lo = hi;
-      }
-      const double kap = kT * gc.efac[gg];
-      const double tau = cl * dt * kap, dtau = tau * (0.5 * g.kap_T_h * invT);
-      const double xg = xi0 * s_icen[gg];
-      if constexpr (F32) {
-        // the FP32 forms: the three species' channel arithmetic in FP32, the group's partial
-        // sums added to the FP64 sums once
-        const float tf = (float)tau, dtf = (float)dtau, invf = frcp(1.0f + tf), xf = (float)xg;
-        const float Bf = (float)B, dBf = (float)dB, Yf = (float)Y;
+        const float tf = cdtf * (kTf * gc.efac32[gg]), dtf = tf * hTf, invf = frcp(1.0f + tf);
+        const float xf = xi0f * (float)s_icen[gg];
         float sE = 0.0f, sX = 0.0f, sT = 0.0f, sY = 0.0f, qT = 0.0f, qY = 0.0f;
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
@@ -205,10 +194,23 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
           sY += dY_;
           qT += xi * dT_;
           qY += xi * dY_;
-          if (keep) En[k] = (double)Ek;
+          if (keep) En[k] = (RT)Ek;
         }
         dE += sE; dX += sX; eT += sT; eY += sY; xT += qT; xY += qY;
-      } else {
+      }
+    } else {
+      const double invT = 1.0 / T, T3 = T * T * T;
+      const double kT = kpre * hpow(T, g.kap_T_h);
+      PlanckEdge<double> lo = planck_edge64(gc.edge[0] * invT, A.pk.c64);
+      for (int gg = 0; gg < Gs; ++gg) {
+        const PlanckEdge<double> hi = planck_edge64(gc.edge[gg + 1] * invT, A.pk.c64);
+        const double I = planck_band(lo, hi);
+        const double B = norm * T3 * T * I;
+        const double dB = norm * (4.0 * T3 * I + T3 * (lo.w - hi.w));
+        lo = hi;
+        const double kap = kT * gc.efac[gg];
+        const double tau = cl * dt * kap, dtau = tau * (0.5 * g.kap_T_h * invT);
+        const double xg = xi0 * s_icen[gg];
         const double inv = 1.0 / (1.0 + tau);
         for (int s = 0; s < 3; ++s) {
           const int k = s * Gs + gg;
@@ -303,8 +305,9 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   eval(T, Y, rE, rX, J, true);
   double dEsum = 0.0, dXsum = 0.0;
   for (int k = 0; k < G; ++k) {
-    dEsum += En[k] - Em[k];
-    dXsum += xi_of(k) * (En[k] - Em[k]);
+    const double dk = (double)En[k] - (double)Em[k];  // exact for the FP32 rows
+    dEsum += dk;
+    dXsum += xi_of(k) * dk;
     U[rad + c * (uint32_t)G + k] = (R)En[k];
   }
   // (kept in FP64 until the momentum feedback below, then stored once)
