@@ -40,7 +40,10 @@ typedef enum {
   FX_ERR_NEWTON = -4,      /* the coupling's Newton and bisection failed in some cell      */
   FX_ERR_FLOOR = -5,       /* a density, pressure or radiation-energy floor was applied   */
   FX_ERR_NONFINITE = -6,   /* a non-finite value appeared in the state                     */
-  FX_ERR_UNSUPPORTED = -7  /* parameters outside what this build supports                  */
+  FX_ERR_UNSUPPORTED = -7, /* parameters outside what this build supports                  */
+  FX_ERR_BOUNDS = -8       /* debug build (FX_BOUNDS_CHECK) only: a kernel index fell outside
+                              its buffer; the access went to the buffer's first element instead
+                              and fx_last_error() names the first such index and its site      */
 } fx_status;
 
 enum { FX_OUTFLOW = 0, FX_PERIODIC = 1, FX_REFLECT = 2, FX_AXIS = 3 }; /* Sec. 7.5 */

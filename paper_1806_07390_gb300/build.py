@@ -1,4 +1,9 @@
-"""Build the CUDA library libfx.so in-tree for sm_103a (nvcc, translation units in parallel)."""
+"""Build the CUDA library libfx.so in-tree for sm_103a (nvcc, translation units in parallel).
+
+build(bounds_check=True) builds the debug variant libfx_bc.so instead: every kernel index that the
+sources mark is checked against its buffer's extent, and an index outside it is reported as
+FX_ERR_BOUNDS (with the site) instead of being accessed.  Load it by setting FX_LIBRARY to its path
+before importing the binding."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -12,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfx.so")
+LIB_BC = os.path.join(HERE, "libfx_bc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -41,21 +47,25 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(verbose: bool = False, extra: list[str] | None = None, bounds_check: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    flags = list(extra or []) + (["-DFX_BOUNDS_CHECK"] if bounds_check else [])
+    out = LIB_BC if bounds_check else LIB
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra or []), srcs))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, flags), srcs))
+    tmp = out + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", out)
+    return out
 
 
 if __name__ == "__main__":
-    build(verbose=True, extra=sys.argv[1:])
+    args = sys.argv[1:]
+    bc = "--bounds-check" in args
+    build(verbose=True, extra=[a for a in args if a != "--bounds-check"], bounds_check=bc)

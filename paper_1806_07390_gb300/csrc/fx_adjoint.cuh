@@ -43,6 +43,10 @@ template <class R> struct AdjArgs {
   int accumulate_in;
   double dt, alpha;   // stage step and RK weight of U_base
   R wJ;               // weight of the boundary outflow of this stage in J (dt/2; 0 if unused)
+#ifdef FX_BOUNDS_CHECK
+  unsigned* status;   // status word, and the elements of a state, for the index checks of the
+  int64_t n_state;    // debug build
+#endif
   R phi_area;         // area of one upper-x boundary face
   Consts<double> kd;
   Consts<float> kf;
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(256) adj_couple_kernel(const __grid_constant__
 
   R u[NG], lo[NG];
   {
-    const R a = A.pre[gv * ncell + c], b = A.lam_out[gv * ncell + c];
+    const R a = A.pre[FXI(gv * ncell + c, A.n_state)], b = A.lam_out[FXI(gv * ncell + c, A.n_state)];
 #pragma unroll
     for (int v = 0; v < NG; ++v) {
       u[v] = __shfl_sync(0xffffffffu, a, v, GP);
@@ -95,21 +99,21 @@ __global__ void __launch_bounds__(256) adj_couple_kernel(const __grid_constant__
   }
   R E = R(0), F[3] = {R(0), R(0), R(0)}, lEo = R(0), lFo[3] = {R(0), R(0), R(0)};
   if (has) {
-    E = A.pre[NG * ncell + c * G + gl];
-    lEo = A.lam_out[NG * ncell + c * G + gl];
+    E = A.pre[FXI(NG * ncell + c * G + gl, A.n_state)];
+    lEo = A.lam_out[FXI(NG * ncell + c * G + gl, A.n_state)];
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-      F[q] = A.pre[NG * ncell + ((1 + q) * ncell + c) * G + gl];
-      lFo[q] = A.lam_out[NG * ncell + ((1 + q) * ncell + c) * G + gl];
+      F[q] = A.pre[FXI(NG * ncell + ((1 + q) * ncell + c) * G + gl, A.n_state)];
+      lFo[q] = A.lam_out[FXI(NG * ncell + ((1 + q) * ncell + c) * G + gl, A.n_state)];
     }
   }
   if (!g.couple) {  // no interaction: U_out = U_pre
     if (active) {
-      if (lane < NG) A.lam_pre[lane * ncell + c] = A.lam_out[lane * ncell + c];
+      if (lane < NG) A.lam_pre[FXI(lane * ncell + c, A.n_state)] = A.lam_out[FXI(lane * ncell + c, A.n_state)];
       if (has) {
-        A.lam_pre[NG * ncell + c * G + gl] = lEo;
+        A.lam_pre[FXI(NG * ncell + c * G + gl, A.n_state)] = lEo;
 #pragma unroll
-        for (int q = 0; q < D; ++q) A.lam_pre[NG * ncell + ((1 + q) * ncell + c) * G + gl] = lFo[q];
+        for (int q = 0; q < D; ++q) A.lam_pre[FXI(NG * ncell + ((1 + q) * ncell + c) * G + gl, A.n_state)] = lFo[q];
       }
     }
     block_partial(0.0, A.kpart);
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(256) adj_couple_kernel(const __grid_constant__
   // on its input
   const bool floored = has && E < KR.E_floor;
   if (floored) E = KR.E_floor;
-  const R T = A.tstar[c];
+  const R T = A.tstar[FXI(c, ncell)];
   const R rho = u[0], irho = R(1) / rho, rhoe = u[NG - 1];
   R m[3] = {R(0), R(0), R(0)}, ke = R(0);
 #pragma unroll
@@ -199,12 +203,12 @@ __global__ void __launch_bounds__(256) adj_couple_kernel(const __grid_constant__
 #pragma unroll
       for (int q = 0; q < D; ++q) if (lane == 1 + q) val = lm[q];
       if (lane == NG - 1) val = lrhoe;
-      A.lam_pre[lane * ncell + c] = val;
+      A.lam_pre[FXI(lane * ncell + c, A.n_state)] = val;
     }
     if (has) {
-      A.lam_pre[NG * ncell + c * G + gl] = floored ? R(0) : lE;
+      A.lam_pre[FXI(NG * ncell + c * G + gl, A.n_state)] = floored ? R(0) : lE;
 #pragma unroll
-      for (int q = 0; q < D; ++q) A.lam_pre[NG * ncell + ((1 + q) * ncell + c) * G + gl] = lF[q];
+      for (int q = 0; q < D; ++q) A.lam_pre[FXI(NG * ncell + ((1 + q) * ncell + c) * G + gl, A.n_state)] = lF[q];
     }
   }
   block_partial((active && lane == 0) ? (double)lk0 : 0.0, A.kpart);
@@ -307,7 +311,7 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<R>& A, int64_t f) {
     fl[m] = flip;
     R u[NG];
 #pragma unroll
-    for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + ci[m]];
+    for (int v = 0; v < NG; ++v) u[v] = A.in[FXI(v * ncell + ci[m], A.n_state)];
     if (flip) u[1 + DIR] = -u[1 + DIR];
     const R rho = u[0], irho = R(1) / rho;
     R ke = R(0);
@@ -369,8 +373,8 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<R>& A, int64_t f) {
 #pragma unroll
     for (int v = 0; v < NRV; ++v) {
       R lj = R(0);
-      if (inL) lj += cL * A.lam_pre[NG * ncell + (v * ncell + ci[1]) * G + gg];
-      if (inR) lj += cR * A.lam_pre[NG * ncell + (v * ncell + ci[2]) * G + gg];
+      if (inL) lj += cL * A.lam_pre[FXI(NG * ncell + (v * ncell + ci[1]) * G + gg, A.n_state)];
+      if (inR) lj += cR * A.lam_pre[FXI(NG * ncell + (v * ncell + ci[2]) * G + gg, A.n_state)];
       if (v == 0 && objective) lj += A.wJ * A.phi_area;
       lout[v] = lj;
       any = any || lj != R(0);
@@ -381,7 +385,7 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<R>& A, int64_t f) {
     for (int m = 0; m < 4; ++m)
 #pragma unroll
       for (int v = 0; v < NRV; ++v) {
-        R val = A.in[NG * ncell + (v * ncell + ci[m]) * G + gg];
+        R val = A.in[FXI(NG * ncell + (v * ncell + ci[m]) * G + gg, A.n_state)];
         Q[m][v] = (v == 1 + DIR && fl[m]) ? -val : val;
       }
     Dn<R, 3> qb[NRV], qa[NRV];
@@ -437,8 +441,8 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<R>& A, int64_t f) {
       const R ltau = -leps / (tau * tau);
       const R lchi = R(0.5) * ell * ltau;
       if (lchi != R(0)) {
-        atomicAdd(lw_chi + (size_t)ci[1] * G + gg, lchi);
-        atomicAdd(lw_chi + (size_t)ci[2] * G + gg, lchi);
+        atomicAdd(FXP(lw_chi, (size_t)ci[1] * G + gg, (size_t)ncell * G), lchi);
+        atomicAdd(FXP(lw_chi, (size_t)ci[2] * G + gg, (size_t)ncell * G), lchi);
       }
     }
     // reconstruction: left state from cells id-2..id, right state from id-1..id+1
@@ -455,7 +459,7 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<R>& A, int64_t f) {
 #pragma unroll
       for (int v = 0; v < NRV; ++v) {
         const R l = (v == 1 + DIR && fl[m]) ? -lQ[m][v] : lQ[m][v];
-        if (l != R(0)) atomicAdd(lw_rad + ((size_t)v * ncell + ci[m]) * G + gg, l);
+        if (l != R(0)) atomicAdd(FXP(lw_rad, ((size_t)v * ncell + ci[m]) * G + gg, (size_t)NRV * ncell * G), l);
       }
   }
 
@@ -466,8 +470,8 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<R>& A, int64_t f) {
 #pragma unroll
     for (int v = 0; v < NG; ++v) {
       R lj = R(0);
-      if (inL) lj += cL * A.lam_pre[v * ncell + ci[1]];
-      if (inR) lj += cR * A.lam_pre[v * ncell + ci[2]];
+      if (inL) lj += cL * A.lam_pre[FXI(v * ncell + ci[1], A.n_state)];
+      if (inR) lj += cR * A.lam_pre[FXI(v * ncell + ci[2], A.n_state)];
       lg[v] = lj;
     }
     lfl[0] = lg[0];
@@ -498,7 +502,7 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<R>& A, int64_t f) {
 #pragma unroll
     for (int v = 0; v < NW; ++v) {
       const R l = (v == 2 + DIR && fl[m]) ? -lW[m][v] : lW[m][v];
-      if (l != R(0)) atomicAdd(lw_gas + (size_t)v * ncell + ci[m], l);
+      if (l != R(0)) atomicAdd(FXP(lw_gas, (size_t)v * ncell + ci[m], (size_t)NW * ncell), l);
     }
   (void)bW;
   (void)aW;
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const __grid_constant__ A
 
   R u[NG], lw[NW];
   {
-    const R a = A.in[gv * ncell + c], b = lw_gas[gv * ncell + c];
+    const R a = A.in[FXI(gv * ncell + c, A.n_state)], b = lw_gas[FXI(gv * ncell + c, (size_t)NW * ncell)];
 #pragma unroll
     for (int v = 0; v < NG; ++v) {
       u[v] = __shfl_sync(0xffffffffu, a, v, GP);
@@ -551,7 +555,7 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const __grid_constant__ A
   const R p = KR.gm1 * (u[NG - 1] - R(0.5) * ke);
   const R T = p * irho;
   // opacity: chi_g = kappa0 rho^a T^b eps_g^d + sigma0 rho (kappa = 0 where T <= 0)
-  const R lchi = has ? lw_chi[(size_t)c * G + gl] : R(0);
+  const R lchi = has ? lw_chi[FXI((size_t)c * G + gl, (size_t)ncell * G)] : R(0);
   R c1 = lchi * KR.sigma0, c2 = R(0), c3 = R(0);
   if (T > R(0) && has) {
     const R K0 = hpow(rho, g.kap_rho_h) * hpow(T, g.kap_T_h);
@@ -582,19 +586,19 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const __grid_constant__ A
 #pragma unroll
       for (int v = 1; v < NG; ++v) if (lane == v) val = lU[v];
       const size_t o = (size_t)lane * ncell + c;
-      const R lp = A.lam_pre[o];
+      const R lp = A.lam_pre[FXI(o, A.n_state)];
       const R li = be * lp + val;
-      if (A.accumulate_in) A.lam_in[o] += li; else A.lam_in[o] = li;
-      if (A.lam_base) A.lam_base[o] = al * lp;
+      if (A.accumulate_in) A.lam_in[FXI(o, A.n_state)] += li; else A.lam_in[FXI(o, A.n_state)] = li;
+      if (A.lam_base) A.lam_base[FXI(o, A.n_state)] = al * lp;
     }
     if (has) {
 #pragma unroll
       for (int v = 0; v < NRV; ++v) {
         const size_t o = (size_t)NG * ncell + ((size_t)v * ncell + c) * G + gl;
-        const R lp = A.lam_pre[o];
-        const R li = be * lp + lw_rad[((size_t)v * ncell + c) * G + gl];
-        if (A.accumulate_in) A.lam_in[o] += li; else A.lam_in[o] = li;
-        if (A.lam_base) A.lam_base[o] = al * lp;
+        const R lp = A.lam_pre[FXI(o, A.n_state)];
+        const R li = be * lp + lw_rad[FXI(((size_t)v * ncell + c) * G + gl, (size_t)NRV * ncell * G)];
+        if (A.accumulate_in) A.lam_in[FXI(o, A.n_state)] += li; else A.lam_in[FXI(o, A.n_state)] = li;
+        if (A.lam_base) A.lam_base[FXI(o, A.n_state)] = al * lp;
       }
     }
   }

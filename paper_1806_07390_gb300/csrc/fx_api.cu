@@ -133,6 +133,7 @@ struct fx_grid {
   size_t off_opk = 0;             // opacity factors of the stage input [K, S][cells]
   size_t off_sflag = 0;           // shock flags of the stage input [cells] (carbuncle guard)
   int64_t face_off[3] = {0, 0, 0};
+  int64_t faces_elems = 0;
   bool uniform[3] = {false, false, false};
   // per-kernel timing: one event triple (before the face kernel, between, after the stage
   // kernel) per stage launch since timing was enabled; events are pooled across reads
@@ -175,6 +176,23 @@ fx_status fail(fx_grid* h, fx_status s, const std::string& msg) {
 }
 fx_status cuda_fail(fx_grid* h, cudaError_t e, const char* where) {
   return fail(h, FX_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// The first out-of-range index that the index checks of the debug build recorded in the status
+// region (words: bits, site, index, extent), as "index i outside [0, n) at file:line".
+std::string bounds_message(const unsigned* w) {
+  static const char* const files[] = {"fx_stage.cuh", "fx_gas.cuh",  "fx_couple.cuh", "fx_couple64.cuh",
+                                      "fx_ye.cuh",    "fx_vterms.cuh", "fx_adjoint.cuh", "fx_layers.cuh",
+                                      "fx_device.cuh", "fx_api.cu"};
+  const unsigned tag = w[1] >> 16, line = w[1] & 0xffffu;
+  std::string file = "tag " + std::to_string(tag);
+  for (const char* f : files)
+    if (fxb_file_tag(f) == tag) file = f;
+  long long i, n;
+  std::memcpy(&i, w + 2, sizeof i);
+  std::memcpy(&n, w + 4, sizeof n);
+  return "index " + std::to_string(i) + " outside [0, " + std::to_string(n) + ") at " + file + ":" +
+         std::to_string(line) + " (index checks of the debug build)";
 }
 
 bool half_integer(double x) { return std::fabs(2.0 * x - std::round(2.0 * x)) < 1e-12; }
@@ -684,6 +702,12 @@ StageArgs<R> stage_args(fx_grid* h) {
   a.ptab.sg = ptab_node_major(h) ? 1 : h->ptab_nu;
   a.pk = h->pk;
   a.status = reinterpret_cast<unsigned*>(h->ws + h->off_status);
+#ifdef FX_BOUNDS_CHECK
+  a.ptab.n = (int)h->ptab.size();
+  a.ptab.status = a.status;
+  a.n_state = h->ncell * h->NV;
+  a.n_faces = h->faces_elems;
+#endif
   a.chunk = h->chunk;
   a.phi_area = (R)h->phi_area;
   return a;
@@ -994,6 +1018,10 @@ fx_status adjoint_impl(fx_grid* h, double dt, int nsteps, int k, unsigned char* 
   b.gc = a.gc;
   b.pk = a.pk;
   b.ptab = a.ptab;
+#ifdef FX_BOUNDS_CHECK
+  b.status = a.status;
+  b.n_state = a.n_state;
+#endif
   b.lam_w = LW;
   b.kpart = kpart;
   b.phi_area = (R)h->phi_area;
@@ -1229,6 +1257,7 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
       fo += (int64_t)(2 + P.dims + 1 + (P.vterms ? P.dims - 1 : 0)) * faces_along(g.n, d);
     }
     h->off_faces = off;
+    h->faces_elems = fo;
     off = align_up(off + (size_t)fo * h->elem);
   }
   h->off_opk = off;
@@ -1546,7 +1575,7 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
   }
   cudaError_t e;
   if (!h->h_status) {
-    e = cudaMallocHost(&h->h_status, sizeof(unsigned));
+    e = cudaMallocHost(&h->h_status, 6 * sizeof(unsigned));
     if (e != cudaSuccess) return cuda_fail(h, e, "pinned status word");
   }
   e = cudaMemsetAsync(h->ws + h->off_status, 0, 64, h->stream);
@@ -1686,10 +1715,11 @@ fx_status fx_step(fx_grid* h, double dt, int nsteps) {
 fx_status fx_sync(fx_grid* h) {
   if (!h) return FX_ERR_ARG;
   if (!has_ws(h)) return fail(h, FX_ERR_WORKSPACE, "no workspace bound");
-  cudaError_t e = cudaMemcpyAsync(h->h_status, h->ws + h->off_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = cudaMemcpyAsync(h->h_status, h->ws + h->off_status, 6 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "synchronise");
   unsigned s = *h->h_status;
+  if (s & ST_BOUNDS) return fail(h, FX_ERR_BOUNDS, bounds_message(h->h_status));
   if (s & ST_NONFINITE) return fail(h, FX_ERR_NONFINITE, "non-finite value in the state");
   if (s & ST_NEWTON) return fail(h, FX_ERR_NEWTON, "coupling Newton/bisection did not converge");
   if (s & ST_FLOOR) return fail(h, FX_ERR_FLOOR, "a density, pressure or radiation floor was applied");

@@ -79,8 +79,8 @@ __device__ __forceinline__ void planck_group(const PlanckTable& ptab, const Plan
                                              const float* edge, float& B, float& dB) {
   float I, dLdu;
   if (p.mode == 1) {
-    const float4 p0 = __ldg(ptab.tab + p.i * ptab.si + g * ptab.sg);
-    const float4 p1 = __ldg(ptab.tab + (p.i + 1) * ptab.si + g * ptab.sg);
+    const float4 p0 = __ldg(FXP_AT(ptab.status, ptab.tab, p.i * ptab.si + g * ptab.sg, ptab.n));
+    const float4 p1 = __ldg(FXP_AT(ptab.status, ptab.tab, (p.i + 1) * ptab.si + g * ptab.sg, ptab.n));
     // node values relative to floor(L) of the left node (small numbers, full FP32 precision);
     // I = 2^(L - floor L) 2^floor(L), the second factor exact from the table
     const float d1 = (p1.z - p0.z) + p1.x;
@@ -165,13 +165,13 @@ __global__ void __launch_bounds__(CPL_THREADS, 7) couple_kernel(StageArgs<float>
     s_ed[j] = A.gc->edge32[j];
   }
   // the block's E rows: the contiguous range [c0 G, (c0 + nc) G) (the F rows follow the Newton)
-  stage_rows<true>(A.out + (size_t)NG * ncell + (size_t)c0 * G, srow, nc, G, RS);
+  stage_rows<true>(FXPR(A.out, (size_t)NG * ncell + (size_t)c0 * G, nc * G, A.n_state), srow, nc, G, RS);
   float rho_f = 1.0f, m_f[3] = {0.0f, 0.0f, 0.0f}, rhoe_f = 1.0f;
   if (act) {
-    rho_f = A.out[cid];
+    rho_f = A.out[FXI(cid, A.n_state)];
 #pragma unroll
-    for (int q = 0; q < D; ++q) m_f[q] = A.out[(1 + q) * ncell + cid];
-    rhoe_f = A.out[(NG - 1) * ncell + cid];
+    for (int q = 0; q < D; ++q) m_f[q] = A.out[FXI((1 + q) * ncell + cid, A.n_state)];
+    rhoe_f = A.out[FXI((NG - 1) * ncell + cid, A.n_state)];
   }
   // covariant components: physical = m_q / h_q on the spherical (r, theta) grid
   const bool sph = (D == 2) && g.geom != 0;
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(CPL_THREADS, 7) couple_kernel(StageArgs<float>
     }
     if (!ok) st |= ST_NEWTON;
     Tst = Tm + (LT)dl;
-    if (A.tstar_out != nullptr) A.tstar_out[cid] = Tst;
+    if (A.tstar_out != nullptr) A.tstar_out[FXI(cid, ncell)] = Tst;
 
     // ---- the accepted group energies (from the kept first evaluation when it is the accepted
     // point, else evaluated again), and the group sum of their changes as a float pair (the sum
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(CPL_THREADS, 7) couple_kernel(StageArgs<float>
   __syncthreads();
 #pragma unroll
   for (int v = 1; v < NRV; ++v)
-    stage_rows<true>(A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, srow + v * CPL_THREADS * RS, nc, G, RS);
+    stage_rows<true>(FXPR(A.out, (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, nc * G, A.n_state), srow + v * CPL_THREADS * RS, nc, G, RS);
   __syncthreads();
   if (work) {
     // ---- flux absorption at the converged temperature (Eq. 28) and the group sums of the flux
@@ -433,10 +433,10 @@ __global__ void __launch_bounds__(CPL_THREADS, 7) couple_kernel(StageArgs<float>
     // (through the group sums of the flux changes), so the rows need no scan of their own when
     // the interaction ran.
     float chk = rho_f + rhoe_f;
-    A.out[cid] = rho_f;
+    A.out[FXI(cid, A.n_state)] = rho_f;
 #pragma unroll
-    for (int q = 0; q < D; ++q) { A.out[(1 + q) * ncell + cid] = m_f[q]; chk += m_f[q]; }
-    A.out[(NG - 1) * ncell + cid] = rhoe_f;
+    for (int q = 0; q < D; ++q) { A.out[FXI((1 + q) * ncell + cid, A.n_state)] = m_f[q]; chk += m_f[q]; }
+    A.out[FXI((NG - 1) * ncell + cid, A.n_state)] = rhoe_f;
     if (!work) {
       for (int v = 0; v < NRV; ++v) {
         const float* rv = srow + (v * CPL_THREADS + t) * RS;
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(CPL_THREADS, 7) couple_kernel(StageArgs<float>
   // write the rows back
 #pragma unroll
   for (int v = 0; v < NRV; ++v)
-    stage_rows<false>(A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, srow + v * CPL_THREADS * RS, nc, G, RS);
+    stage_rows<false>(FXPR(A.out, (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, nc * G, A.n_state), srow + v * CPL_THREADS * RS, nc, G, RS);
 }
 
 }  // namespace fx

@@ -88,13 +88,13 @@ __global__ void __launch_bounds__(CPL64_THREADS) couple64_kernel(StageArgs<doubl
     if (j < G) s_ef[j] = A.gc->efac[j];
     s_ed[j] = A.gc->edge[j];
   }
-  stage_rows64<true>(A.out + (size_t)NG * ncell + (size_t)c0 * G, srow, nc, G, RS);
+  stage_rows64<true>(FXPR(A.out, (size_t)NG * ncell + (size_t)c0 * G, nc * G, A.n_state), srow, nc, G, RS);
   double rho = 1.0, m[3] = {0.0, 0.0, 0.0}, rhoe = 1.0;
   if (act) {
-    rho = A.out[cid];
+    rho = A.out[FXI(cid, A.n_state)];
 #pragma unroll
-    for (int q = 0; q < D; ++q) m[q] = A.out[(1 + q) * ncell + cid];
-    rhoe = A.out[(NG - 1) * ncell + cid];
+    for (int q = 0; q < D; ++q) m[q] = A.out[FXI((1 + q) * ncell + cid, A.n_state)];
+    rhoe = A.out[FXI((NG - 1) * ncell + cid, A.n_state)];
   }
   // covariant components: physical = m_q / h_q on the spherical (r, theta) grid
   const bool sph = (D == 2) && g.geom != 0;
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(CPL64_THREADS) couple64_kernel(StageArgs<doubl
       if (!ok) st |= ST_NEWTON;
     }
     Tst = Tm + dl;
-    if (A.tstar_out != nullptr) A.tstar_out[cid] = Tst;
+    if (A.tstar_out != nullptr) A.tstar_out[FXI(cid, ncell)] = Tst;
     // ---- the group energies at the accepted temperature and the gas energy by conservation (R12)
     double dEsum = 0.0;
     for (int j = 0; j < G; ++j) {
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(CPL64_THREADS) couple64_kernel(StageArgs<doubl
   __syncthreads();
 #pragma unroll
   for (int v = 1; v < NRV; ++v)
-    stage_rows64<true>(A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, srow + v * CPL64_THREADS * RS, nc, G, RS);
+    stage_rows64<true>(FXPR(A.out, (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, nc * G, A.n_state), srow + v * CPL64_THREADS * RS, nc, G, RS);
   __syncthreads();
   if (work) {
     // ---- flux absorption at the converged temperature (Eq. 28) and its momentum and energy
@@ -284,10 +284,10 @@ __global__ void __launch_bounds__(CPL64_THREADS) couple64_kernel(StageArgs<doubl
     // A NaN or inf anywhere in the cell's outputs makes chk non-finite (with the interaction on,
     // a non-finite E_g or F_g reaches the gas energy or momentum through the group sums)
     double chk = rho + rhoe;
-    A.out[cid] = rho;
+    A.out[FXI(cid, A.n_state)] = rho;
 #pragma unroll
-    for (int q = 0; q < D; ++q) { A.out[(1 + q) * ncell + cid] = m[q]; chk += m[q]; }
-    A.out[(NG - 1) * ncell + cid] = rhoe;
+    for (int q = 0; q < D; ++q) { A.out[FXI((1 + q) * ncell + cid, A.n_state)] = m[q]; chk += m[q]; }
+    A.out[FXI((NG - 1) * ncell + cid, A.n_state)] = rhoe;
     if (!work) {
       for (int v = 0; v < NRV; ++v) {
         const double* rv = srow + (v * CPL64_THREADS + t) * RS;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(CPL64_THREADS) couple64_kernel(StageArgs<doubl
   __syncthreads();
 #pragma unroll
   for (int v = 0; v < NRV; ++v)
-    stage_rows64<false>(A.out + (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, srow + v * CPL64_THREADS * RS, nc, G, RS);
+    stage_rows64<false>(FXPR(A.out, (size_t)NG * ncell + ((size_t)v * ncell + c0) * G, nc * G, A.n_state), srow + v * CPL64_THREADS * RS, nc, G, RS);
 }
 
 }  // namespace fx

@@ -87,7 +87,7 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
     const uint32_t ci = ((uint32_t)c2 * n1 + c1) * n0 + c0;
     R u[NG];
 #pragma unroll
-    for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + ci];
+    for (int v = 0; v < NG; ++v) u[v] = A.in[FXI(v * ncell + ci, A.n_state)];
     if (flip) u[1 + DIR] = -u[1 + DIR];
     if (sph) {  // physical components m_q / h_q (the 2-d spherical grid is r x theta)
       const int cr = DIR == 0 ? id : x, ct = DIR == 1 ? id : i1;
@@ -99,11 +99,11 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
 #pragma unroll
     for (int q = 0; q < D; ++q) {
       const R vq = u[1 + q] * irho;
-      sw[2 + q][c] = vq;
+      sw[2 + q][FXI(c, FACE_WCELLS)] = vq;
       ke += u[1 + q] * vq;
     }
-    sw[0][c] = rho;
-    sw[1][c] = KR.gm1 * (u[NG - 1] - R(0.5) * ke);
+    sw[0][FXI(c, FACE_WCELLS)] = rho;
+    sw[1][FXI(c, FACE_WCELLS)] = KR.gm1 * (u[NG - 1] - R(0.5) * ke);
   }
   __syncthreads();
   if (DIR == 0) {
@@ -111,10 +111,10 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
     // cell (each cell is a face owner of exactly one x tile), for the radiation/update kernel
     const int r = t, id = d0 - 1 + r;
     if (r >= 1 && id < n0) {
-      const R rho = sw[0][r + 1], T = sw[1][r + 1] * frcp(rho);
+      const R rho = sw[0][FXI(r + 1, FACE_WCELLS)], T = sw[1][FXI(r + 1, FACE_WCELLS)] * frcp(rho);
       const uint32_t ci = ((uint32_t)i2 * n1 + i1) * n0 + (uint32_t)id;
-      A.opk[ci] = T > R(0) ? KR.kappa0 * hpow(rho, g.kap_rho_h) * hpow(T, g.kap_T_h) : R(0);
-      A.opk[ncell + ci] = KR.sigma0 * rho;
+      A.opk[FXI(ci, 2 * ncell)] = T > R(0) ? KR.kappa0 * hpow(rho, g.kap_rho_h) * hpow(T, g.kap_T_h) : R(0);
+      A.opk[FXI(ncell + ci, 2 * ncell)] = KR.sigma0 * rho;
     }
   }
   // ---- each thread reconstructs one cell along DIR (row r: cell d0 - 1 + r): the upper-face
@@ -123,14 +123,14 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
   const Tab<R> tt{A.tab[DIR], nd + 4, A.uniform[DIR] ? A.urow[DIR] : nullptr};
   const int lx = t % LX, r = t / LX;
   const int id = d0 - 1 + r;
-  auto w = [&](int v, int k) -> R { return sw[v][k * LX + lx]; };  // k: cell d0 - 2 + k
+  auto w = [&](int v, int k) -> R { return sw[v][FXI(k * LX + lx, FACE_WCELLS)]; };  // k: cell d0 - 2 + k
   R Ra[NW];
 #pragma unroll
   for (int v = 0; v < NW; ++v) {
     R a, b;
     recon_parabolic(tt, bc_pad(id), w(v, r), w(v, r + 1), w(v, r + 2), a, b);
     Ra[v] = a;
-    sb[v][r * LX + lx] = b;
+    sb[v][FXI(r * LX + lx, FACE_BCELLS)] = b;
   }
   __syncthreads();
   // ---- HLLC through the cell's lower face (rows 1 .. LD): left state = upper face of the cell
@@ -141,7 +141,7 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
 #pragma unroll
   for (int v = 0; v < NW; ++v) {
     const int slot = v < 2 ? v : 2 + (v - 2 - DIR + D) % D;  // rotated position of variable v
-    Lr[slot] = sb[v][(r - 1) * LX + lx];
+    Lr[slot] = sb[v][FXI((r - 1) * LX + lx, FACE_BCELLS)];
     Rr[slot] = Ra[v];
   }
   int solver = g.riemann;
@@ -154,7 +154,7 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
       bool flip = false;
       const int cd = min(max(bc_map(id - 1 + s2, nd, g.bc_lo[DIR], g.bc_hi[DIR], flip), 0), nd - 1);
       const int c0 = DIR == 0 ? cd : x, c1 = DIR == 1 ? cd : i1, c2 = DIR == 2 ? cd : i2;
-      fl2 |= A.sflag[((uint32_t)c2 * n1 + c1) * n0 + c0];
+      fl2 |= A.sflag[FXI(((uint32_t)c2 * n1 + c1) * n0 + c0, ncell)];
     }
     if (fl2 & ~(1u << DIR)) solver = 1;
   }
@@ -166,17 +166,19 @@ __device__ __forceinline__ void gas_faces_tile(const StageArgs<R>& A, unsigned t
                     : DIR == 1 ? ((uint32_t)i2 * ey + (uint32_t)id) * n0 + (uint32_t)x
                                : ((uint32_t)id * n1 + (uint32_t)i1) * n0 + (uint32_t)x;
   R* out = A.faces_out + A.face_off[DIR];
-  out[uf] = fl[0];
+  const uint32_t n_out = (uint32_t)(NG + 1 + (g.vterms ? D - 1 : 0)) * nf;  // this direction's block
+  (void)n_out;
+  out[FXI(uf, n_out)] = fl[0];
 #pragma unroll
-  for (int c = 0; c < D; ++c) out[(uint32_t)(1 + (DIR + c) % D) * nf + uf] = fl[1 + c];
-  out[(uint32_t)(NG - 1) * nf + uf] = fl[1 + D];
-  out[(uint32_t)NG * nf + uf] = vs;
+  for (int c = 0; c < D; ++c) out[FXI((uint32_t)(1 + (DIR + c) % D) * nf + uf, n_out)] = fl[1 + c];
+  out[FXI((uint32_t)(NG - 1) * nf + uf, n_out)] = fl[1 + D];
+  out[FXI((uint32_t)NG * nf + uf, n_out)] = vs;
   if (g.vterms) {
     // face velocity vector for the velocity-dependent radiation terms: v* normal, the transverse
     // components of the state on the v* upwind side (rotated order, rows NG + 1 .. NG + D - 1)
     const R* up = vs >= R(0) ? Lr : Rr;
 #pragma unroll
-    for (int c = 1; c < D; ++c) out[(uint32_t)(NG + c) * nf + uf] = up[2 + c];
+    for (int c = 1; c < D; ++c) out[FXI((uint32_t)(NG + c) * nf + uf, n_out)] = up[2 + c];
   }
 }
 
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(256) shock_flag_kernel(const __grid_constant__
     const uint32_t ci = ((uint32_t)mz * n1 + my) * n0 + mx;
     R u[NG];
 #pragma unroll
-    for (int v = 0; v < NG; ++v) u[v] = A.in[v * ncell + ci];
+    for (int v = 0; v < NG; ++v) u[v] = A.in[FXI(v * ncell + ci, A.n_state)];
     if (sph) {  // physical components with the scale factors of the (ghost) position
       u[1] *= frcp(t0(T_HA, bc_pad(x)) * t1(T_HA, bc_pad(y)));
       if (D >= 2) u[2] *= frcp(t0(T_HB, bc_pad(x)) * t1(T_HB, bc_pad(y)));
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(256) shock_flag_kernel(const __grid_constant__
     const bool sm = fmax(p0, pm) > thr * fmin(p0, pm), sp = fmax(p0, pp) > thr * fmin(p0, pp);
     if (sm || sp) fl |= (unsigned char)(1u << e);
   }
-  A.sflag[c] = fl;
+  A.sflag[FXI(c, ncell)] = fl;
 }
 
 // One block per tile; grid row y is the direction (tiles beyond a direction's count return).

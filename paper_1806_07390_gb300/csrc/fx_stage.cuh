@@ -14,6 +14,7 @@
 #pragma once
 #include <type_traits>
 
+#include "fx_check.cuh"
 #include "fx_device.cuh"
 #include "fx_pair.cuh"
 
@@ -59,6 +60,10 @@ struct PlanckTable {
   int nu;
   float u0;
   int si, sg;
+#ifdef FX_BOUNDS_CHECK
+  int n;             // entries (nu x groups), for the index checks of the debug build
+  unsigned* status;  // status word those checks report to
+#endif
 };
 
 struct VtConst;  // frequency constants of the velocity-dependent terms (fx_vterms.cuh)
@@ -84,6 +89,10 @@ template <class R> struct StageArgs {
   const VtConst* vtc;  // per-group constants of the velocity-dependent terms
   PlanckParams pk;
   unsigned* status;
+#ifdef FX_BOUNDS_CHECK
+  int64_t n_state;     // elements of a state (in, base, out, pre_out) and of the gas face buffer,
+  int64_t n_faces;     // for the index checks of the debug build
+#endif
   double dt;           // stage step
   double dts;          // coupling step (dt after stage 1, dt/2 after stage 2; reading R10)
   double alpha;        // 0 (stage 1) or 1/2 (stage 2)
@@ -252,8 +261,8 @@ struct LanePlanck {
     } else {
       const int i = (int)s;
       const float t = s - (float)i;
-      const float4 p0 = __ldg(ptab.tab + i * ptab.si + lane * ptab.sg);
-      const float4 p1 = __ldg(ptab.tab + (i + 1) * ptab.si + lane * ptab.sg);
+      const float4 p0 = __ldg(FXP_AT(ptab.status, ptab.tab, i * ptab.si + lane * ptab.sg, ptab.n));
+      const float4 p1 = __ldg(FXP_AT(ptab.status, ptab.tab, (i + 1) * ptab.si + lane * ptab.sg, ptab.n));
       const float t2 = t * t, t3 = t2 * t;
       // node values relative to floor(L) of the left node: small numbers, full FP32 precision
       const float d1 = (p1.z - p0.z) + p1.x;
@@ -480,6 +489,15 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   R* const sbg = sm + L.sbg;  // stage-2 base (gas)
   R* const scr = sm + L.scar; // 2-d: march carry (own cell's upper march-face state, march flux)
   R* const sgf = sm + L.sgf;  // gas-face values of the cell's faces, by plane parity
+  // extents of the shared arrays and of the opacity factors, for the index checks of the debug
+  // build (FXI)
+  const int n_st = L.pk - L.st, n_pk = L.rbx - L.pk, n_rbx = L.rax - L.rbx, n_rax = L.rby - L.rax;
+  const int n_rby = L.ray - L.rby, n_ray = D == 3 ? NRV * TX * GS : 0, n_sg = L.sbr - L.sg;
+  const int n_rfx = NRV * NFX * GS, n_rfy = NRV * NFY * GS, n_sbr = L.sbg - L.sbr;
+  const int n_sbg = L.scar - L.sbg, n_scr = L.sgf - L.scar, n_sgf = L.end - L.sgf;
+  const uint32_t n_opk = 2 * ncell;
+  (void)n_st; (void)n_pk; (void)n_rbx; (void)n_rax; (void)n_rby; (void)n_ray; (void)n_sg;
+  (void)n_rfx; (void)n_rfy; (void)n_sbr; (void)n_sbg; (void)n_scr; (void)n_sgf; (void)n_opk;
   GroupConst* sgc = reinterpret_cast<GroupConst*>(
       (reinterpret_cast<uintptr_t>(sm + L.end) + 15) & ~static_cast<uintptr_t>(15));
   for (int i = tid; i < (int)(sizeof(GroupConst) / sizeof(int)); i += NTH)
@@ -510,9 +528,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   };
   auto scell = [&](int sx, int sy) -> int { return (D == 3 ? (sy + 2) * PX : 0) + sx + 2; };
   auto rad_at = [&](int slot, int v, int sc, int gg) -> R& {
-    return st[((slot * NRV + v) * PC + sc) * GS + gg];
+    return st[FXI(((slot * NRV + v) * PC + sc) * GS + gg, n_st)];
   };
-  auto gas_at = [&](int slot, int v, int sc) -> R& { return sgr[(slot * NG + v) * PC + sc]; };
+  auto gas_at = [&](int slot, int v, int sc) -> R& { return sgr[FXI((slot * NG + v) * PC + sc, n_sg)]; };
   constexpr bool sph = SPH;  // spherical (r, theta): x = r, march = theta
   // scale factor of component q of the cell with x index ix on plane k
   auto hfac = [&](int q, int ix, int k) -> R {
@@ -531,9 +549,9 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       const uint32_t gc_ = map_cell(sx, sy, k, fl);
       const int sc = scell(sx, sy);
 #pragma unroll
-      for (int v = 0; v < NG; ++v) gas_at(slot, v, sc) = A.in[v * ncell + gc_];
-      pk[(slot * 2 + 0) * PC + sc] = A.opk[gc_];
-      pk[(slot * 2 + 1) * PC + sc] = A.opk[ncell + gc_];
+      for (int v = 0; v < NG; ++v) gas_at(slot, v, sc) = A.in[FXI(v * ncell + gc_, A.n_state)];
+      pk[FXI((slot * 2 + 0) * PC + sc, n_pk)] = A.opk[FXI(gc_, n_opk)];
+      pk[FXI((slot * 2 + 1) * PC + sc, n_pk)] = A.opk[FXI(ncell + gc_, n_opk)];
     }
     for (int t = tid; t < ncl * GP; t += NTH) {
       const int i = t / GP, gg = t % GP;
@@ -545,7 +563,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       const int sc = scell(sx, sy);
 #pragma unroll
       for (int v = 0; v < NRV; ++v) {
-        R val = A.in[NG * ncell + (v * ncell + gc_) * G + gg];
+        R val = A.in[FXI(NG * ncell + (v * ncell + gc_) * G + gg, A.n_state)];
         if (v >= 1 && fl[v - 1]) val = -val;
         if (sph && v >= 1) val *= frcp(hfac(v - 1, x0 + sx, k));  // physical component
         rad_at(slot, v, sc, gg) = val;
@@ -592,7 +610,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       R q[NGL];
 #pragma unroll
       for (int j = 0; j < NGL; ++j) {
-        R val = A.in[NG * ncell + (v * ncell + gc_) * G + gj[j]];
+        R val = A.in[FXI(NG * ncell + (v * ncell + gc_) * G + gj[j], A.n_state)];
         q[j] = (v >= 1 && fl[v - 1]) ? -val : val;
         if (sph && v >= 1) q[j] *= frcp(hfac(v - 1, gx, k));  // physical component
       }
@@ -614,14 +632,14 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       if (hasj[j]) {
 #pragma unroll
         for (int v = 0; v < NRV; ++v)
-          cp_async(&rad_at(slot, v, sc_own, gj[j]), A.in + NG * ncell + (v * ncell + gc_) * G + gj[j]);
+          cp_async(&rad_at(slot, v, sc_own, gj[j]), FXP(A.in, NG * ncell + (v * ncell + gc_) * G + gj[j], A.n_state));
       }
     }
     if (lane == 0) {
 #pragma unroll
-      for (int v = 0; v < NG; ++v) cp_async(&gas_at(slot, v, sc_own), A.in + v * ncell + gc_);
-      cp_async(&pk[(slot * 2 + 0) * PC + sc_own], A.opk + gc_);
-      cp_async(&pk[(slot * 2 + 1) * PC + sc_own], A.opk + ncell + gc_);
+      for (int v = 0; v < NG; ++v) cp_async(&gas_at(slot, v, sc_own), FXP(A.in, v * ncell + gc_, A.n_state));
+      cp_async(&pk[FXI((slot * 2 + 0) * PC + sc_own, n_pk)], FXP(A.opk, gc_, n_opk));
+      cp_async(&pk[FXI((slot * 2 + 1) * PC + sc_own, n_pk)], FXP(A.opk, ncell + gc_, n_opk));
     }
     for (int t = tid; t < NHALO * GP; t += NTH) {
       const int i = t / GP, gg = t % GP;
@@ -632,7 +650,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       const uint32_t c = map_cell(sx, sy, P, f);
       const int sc = scell(sx, sy);
 #pragma unroll
-      for (int v = 0; v < NRV; ++v) cp_async(&rad_at(slot, v, sc, gg), A.in + NG * ncell + (v * ncell + c) * G + gg);
+      for (int v = 0; v < NRV; ++v) cp_async(&rad_at(slot, v, sc, gg), FXP(A.in, NG * ncell + (v * ncell + c) * G + gg, A.n_state));
     }
     // halo opacity factors: in 2-d the lower halo cells (-2, -1) by the first warp and the upper
     // ones (TX, TX+1) by the last, the warps whose edge cells read them in phase C (so that their
@@ -646,8 +664,8 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       bool f[3];
       const uint32_t c = map_cell(sx, sy, P, f);
       const int sc = scell(sx, sy);
-      cp_async(&pk[(slot * 2 + 0) * PC + sc], A.opk + c);
-      cp_async(&pk[(slot * 2 + 1) * PC + sc], A.opk + ncell + c);
+      cp_async(&pk[FXI((slot * 2 + 0) * PC + sc, n_pk)], FXP(A.opk, c, n_opk));
+      cp_async(&pk[FXI((slot * 2 + 1) * PC + sc, n_pk)], FXP(A.opk, ncell + c, n_opk));
     }
   };
   auto finish_plane = [&](int P) {
@@ -691,8 +709,8 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   };
   // stage-2 base of the thread's cell on plane P, staged at the end of the previous step and read
   // back by the same thread in D
-  auto base_r = [&](int v, int j) -> R& { return sbr[(v * TC + tcell) * GS + gj[j]]; };
-  auto base_g = [&]() -> R& { return sbg[gvar * TC + tcell]; };
+  auto base_r = [&](int v, int j) -> R& { return sbr[FXI((v * TC + tcell) * GS + gj[j], n_sbr)]; };
+  auto base_g = [&]() -> R& { return sbg[FXI(gvar * TC + tcell, n_sbg)]; };
   auto issue_base = [&](int P) {
     if (A.base == nullptr || !cell_in) return;
     const uint32_t c = D == 1 ? (uint32_t)gx : D == 2 ? (uint32_t)P * nx + gx : ((uint32_t)P * ny + gy) * nx + gx;
@@ -700,10 +718,10 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
     for (int j = 0; j < NGL; ++j) {
       if (hasj[j]) {
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) cp_async(&base_r(v, j), A.base + NG * ncell + (v * ncell + c) * G + gj[j]);
+        for (int v = 0; v < NRV; ++v) cp_async(&base_r(v, j), FXP(A.base, NG * ncell + (v * ncell + c) * G + gj[j], A.n_state));
       }
     }
-    if (lane < NG) cp_async(&base_g(), A.base + gvar * ncell + c);
+    if (lane < NG) cp_async(&base_g(), FXP(A.base, gvar * ncell + c, A.n_state));
   };
 
   // radiation flux through a face along d: QL = left cell's upper-face state, QR = right cell's
@@ -756,7 +774,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   };
   const V efv = vpair(ef[0], ef[NGL - 1], V());
   auto chi_v = [&](int slot, int sc) {
-    return vfma(efv, V(pk[(slot * 2) * PC + sc]), V(pk[(slot * 2 + 1) * PC + sc]));
+    return vfma(efv, V(pk[FXI((slot * 2) * PC + sc, n_pk)]), V(pk[FXI((slot * 2 + 1) * PC + sc, n_pk)]));
   };
   auto recon_rad_v = [&](const MCCoef<R>& c, const Tab<R>& t, int ip, const V* Qm, const V* Q0, const V* Qp,
                          V* a, V* b) {
@@ -815,10 +833,10 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   const uint32_t nfd[3] = {(uint32_t)(nx + 1) * (D > 1 ? ny : 1) * (D > 2 ? nz : 1),
                            (uint32_t)nx * (ny + 1) * (D > 2 ? nz : 1), (uint32_t)nx * ny * (nz + 1)};
   auto gface = [&](int d, int v, uint32_t f) -> R {
-    return __ldg(A.faces + (uint32_t)A.face_off[d] + v * nfd[d] + f);
+    return __ldg(FXP(A.faces, (uint32_t)A.face_off[d] + v * nfd[d] + f, A.n_faces));
   };
   auto gface_p = [&](int d, int v, uint32_t f) -> const R* {
-    return A.faces + (uint32_t)A.face_off[d] + v * nfd[d] + f;
+    return FXP(A.faces, (uint32_t)A.face_off[d] + v * nfd[d] + f, A.n_faces);
   };
   // 1-d and 2-d: the gas-face values a cell needs on plane P, staged with cp.async one plane
   // ahead into shared slots by plane parity: slots 0-2 the contact speeds of its lower x face, of
@@ -827,7 +845,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   // x and march faces (lane v copies them).  The lanes of a cell read them after their wait and a
   // warp barrier.
   constexpr int GFV = 2 * D;
-  auto gfs = [&](int P, int slot) -> R& { return sgf[((P & 1) * TC + tcell) * LY::NGF + slot]; };
+  auto gfs = [&](int P, int slot) -> R& { return sgf[FXI(((P & 1) * TC + tcell) * LY::NGF + slot, n_sgf)]; };
   auto issue_gf = [&](int P) {
     if constexpr (D <= 2) {
       if (lane == 0) {
@@ -857,7 +875,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
   for (int v = 0; v < NRV; ++v) bm0[v] = rfm_old[v] = V(R(0));
   constexpr bool SCAR = D == 2;
   auto car = [&](int P, int w, int v) -> R* {  // w = 0: upper-face state, 1: lower-face flux
-    return &scr[((((P & 1) * 2 + w) * NRV + v) * TC + tcell) * GS + g0];
+    return &scr[FXI(((((P & 1) * 2 + w) * NRV + v) * TC + tcell) * GS + g0, n_scr)];
   };
 
   // ---------------------------------------------------------------- prologue
@@ -999,21 +1017,21 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       rad_v(s0, sc_own + 1, Qb);
       recon_rad_v(mcx, tx, ipx, Qa, Q0, Qb, ax, bx);
 #pragma unroll
-      for (int v = 0; v < NRV; ++v) stv(&rbx[(v * NFX + ly * (TX + 1) + lx + 1) * GS + g0], bx[v]);
+      for (int v = 0; v < NRV; ++v) stv(&rbx[FXI((v * NFX + ly * (TX + 1) + lx + 1) * GS + g0, n_rbx)], bx[v]);
       if constexpr (NGL == 1) {  // (two groups per lane: after this block, one group per lane)
         if (lx == 0) {  // halo cell -1: its upper-face state is the left state of face 0
           V Qc[NRV], ta[NRV], tb[NRV];
           rad_v(s0, sc_own - 2, Qc);
           recon_rad_v(mc_coef(tx, bc_pad(gx - 1)), tx, bc_pad(gx - 1), Qc, Qa, Q0, ta, tb);
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) stv(&rbx[(v * NFX + ly * (TX + 1)) * GS + g0], tb[v]);
+          for (int v = 0; v < NRV; ++v) stv(&rbx[FXI((v * NFX + ly * (TX + 1)) * GS + g0, n_rbx)], tb[v]);
         }
         if (lx == TX - 1) {  // halo cell TX: its lower-face state is the right state of face TX
           V Qc[NRV], ta[NRV], tb[NRV];
           rad_v(s0, sc_own + 2, Qc);
           recon_rad_v(mc_coef(tx, bc_pad(gx + 1)), tx, bc_pad(gx + 1), Q0, Qb, Qc, ta, tb);
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) stv(&rax[(v * TY + ly) * GS + g0], ta[v]);
+          for (int v = 0; v < NRV; ++v) stv(&rax[FXI((v * TY + ly) * GS + g0, n_rax)], ta[v]);
         }
       }
       if (D == 3) {
@@ -1022,20 +1040,20 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         rad_v(s0, sc_own + PX, Qb3);
         recon_rad_v(mc_coef(ty, bc_pad(gy)), ty, bc_pad(gy), Qa3, Q0, Qb3, ay, by);
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) stv(&rby[(v * NFY + (ly + 1) * TX + lx) * GS + g0], by[v]);
+        for (int v = 0; v < NRV; ++v) stv(&rby[FXI((v * NFY + (ly + 1) * TX + lx) * GS + g0, n_rby)], by[v]);
         if (NGL == 1 && ly == 0) {  // (two groups per lane: after this block, one group per lane)
           V Qc[NRV], ta[NRV], tb[NRV];
           rad_v(s0, sc_own - 2 * PX, Qc);
           recon_rad_v(mc_coef(ty, bc_pad(gy - 1)), ty, bc_pad(gy - 1), Qc, Qa3, Q0, ta, tb);
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) stv(&rby[(v * NFY + lx) * GS + g0], tb[v]);
+          for (int v = 0; v < NRV; ++v) stv(&rby[FXI((v * NFY + lx) * GS + g0, n_rby)], tb[v]);
         }
         if (NGL == 1 && ly == TY - 1) {
           V Qc[NRV], ta[NRV], tb[NRV];
           rad_v(s0, sc_own + 2 * PX, Qc);
           recon_rad_v(mc_coef(ty, bc_pad(gy + 1)), ty, bc_pad(gy + 1), Q0, Qb3, Qc, ta, tb);
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) stv(&ray[(v * TX + lx) * GS + g0], ta[v]);
+          for (int v = 0; v < NRV; ++v) stv(&ray[FXI((v * TX + lx) * GS + g0, n_ray)], ta[v]);
         }
       }
       if (D >= 2) recon_rad_v(mc_coef(tm, bc_pad(k + 1)), tm, bc_pad(k + 1), Q0, Q1, Q2, am1, bm1);
@@ -1057,7 +1075,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         rad_cell(s0, sc0, h, Qe);
         recon_rad(mc_coef(tx, bc_pad(x0 - 1)), tx, bc_pad(x0 - 1), Qc, Qd, Qe, ta, tb);
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rbx[(v * NFX + ly * (TX + 1)) * GS + h] = tb[v];
+        for (int v = 0; v < NRV; ++v) rbx[FXI((v * NFX + ly * (TX + 1)) * GS + h, n_rbx)] = tb[v];
       }
     }
     if (NGL > 1 && lx >= TX - NGL) {
@@ -1070,7 +1088,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         rad_cell(s0, sc1 + 2, h, Qe);
         recon_rad(mc_coef(tx, bc_pad(x0 + TX)), tx, bc_pad(x0 + TX), Qc, Qd, Qe, ta, tb);
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rax[(v * TY + ly) * GS + h] = ta[v];
+        for (int v = 0; v < NRV; ++v) rax[FXI((v * TY + ly) * GS + h, n_rax)] = ta[v];
       }
     }
     // 3-d, two groups per lane: likewise the y halo rows -1 (the upper-face state of each column's
@@ -1087,7 +1105,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         rad_cell(s0, sc0, h, Qe);
         recon_rad(mc_coef(ty, bc_pad(y0 - 1)), ty, bc_pad(y0 - 1), Qc, Qd, Qe, ta, tb);
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rby[(v * NFY + lx) * GS + h] = tb[v];
+        for (int v = 0; v < NRV; ++v) rby[FXI((v * NFY + lx) * GS + h, n_rby)] = tb[v];
       }
     }
     if (D == 3 && NGL > 1 && ly >= TY - NGL) {
@@ -1100,7 +1118,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         rad_cell(s0, sc1 + 2 * PX, h, Qe);
         recon_rad(mc_coef(ty, bc_pad(y0 + TY)), ty, bc_pad(y0 + TY), Qc, Qd, Qe, ta, tb);
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) ray[(v * TX + lx) * GS + h] = ta[v];
+        for (int v = 0; v < NRV; ++v) ray[FXI((v * TX + lx) * GS + h, n_ray)] = ta[v];
       }
     }
     __syncthreads();
@@ -1115,34 +1133,34 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         const int fx = ly * (TX + 1) + lx;
         V QL[NRV], out[NRV];
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) QL[v] = ldv(&rbx[(v * NFX + fx) * GS + g0]);
+        for (int v = 0; v < NRV; ++v) QL[v] = ldv(&rbx[FXI((v * NFX + fx) * GS + g0, n_rbx)]);
         rad_face_v(0, QL, ax, chi_v(s0, sc_own - 1), chi0, ellx, vsx, out);
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) stv(&rfx[(v * NFX + fx) * GS + g0], out[v]);
+        for (int v = 0; v < NRV; ++v) stv(&rfx[FXI((v * NFX + fx) * GS + g0, n_rfx)], out[v]);
         if (NGL == 1 && lx == TX - 1) {
           V QR[NRV];
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) QR[v] = ldv(&rax[(v * TY + ly) * GS + g0]);
+          for (int v = 0; v < NRV; ++v) QR[v] = ldv(&rax[FXI((v * TY + ly) * GS + g0, n_rax)]);
           rad_face_v(0, bx, QR, chi0, chi_v(s0, sc_own + 1), tx(T_ELL, ipx + 1), vsx1, out);
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) stv(&rfx[(v * NFX + fx + 1) * GS + g0], out[v]);
+          for (int v = 0; v < NRV; ++v) stv(&rfx[FXI((v * NFX + fx + 1) * GS + g0, n_rfx)], out[v]);
         }
       }
       if (D == 3) {
         const int fy = ly * TX + lx;
         V QL[NRV], out[NRV];
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) QL[v] = ldv(&rby[(v * NFY + fy) * GS + g0]);
+        for (int v = 0; v < NRV; ++v) QL[v] = ldv(&rby[FXI((v * NFY + fy) * GS + g0, n_rby)]);
         rad_face_v(1, QL, ay, chi_v(s0, sc_own - PX), chi0, ty(T_ELL, bc_pad(gy)), vsy, out);
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) stv(&rfy[(v * NFY + fy) * GS + g0], out[v]);
+        for (int v = 0; v < NRV; ++v) stv(&rfy[FXI((v * NFY + fy) * GS + g0, n_rfy)], out[v]);
         if (NGL == 1 && ly == TY - 1) {
           V QR[NRV];
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) QR[v] = ldv(&ray[(v * TX + lx) * GS + g0]);
+          for (int v = 0; v < NRV; ++v) QR[v] = ldv(&ray[FXI((v * TX + lx) * GS + g0, n_ray)]);
           rad_face_v(1, by, QR, chi0, chi_v(s0, sc_own + PX), ty(T_ELL, bc_pad(gy + 1)), vsy1, out);
 #pragma unroll
-          for (int v = 0; v < NRV; ++v) stv(&rfy[(v * NFY + fy + TX) * GS + g0], out[v]);
+          for (int v = 0; v < NRV; ++v) stv(&rfy[FXI((v * NFY + fy + TX) * GS + g0, n_rfy)], out[v]);
         }
       }
       if (D >= 2) {
@@ -1169,12 +1187,12 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         R QL[NRV], QR[NRV], out[NRV];
 #pragma unroll
         for (int v = 0; v < NRV; ++v) {
-          QL[v] = rbx[(v * NFX + fT) * GS + h];
-          QR[v] = rax[(v * TY + ly) * GS + h];
+          QL[v] = rbx[FXI((v * NFX + fT) * GS + h, n_rbx)];
+          QR[v] = rax[FXI((v * TY + ly) * GS + h, n_rax)];
         }
         const R eh = R(sgc->efac_of(h, R(0)));
-        const R chiL = pk[(s0 * 2) * PC + sc1] * eh + pk[(s0 * 2 + 1) * PC + sc1];
-        const R chiR = pk[(s0 * 2) * PC + sc1 + 1] * eh + pk[(s0 * 2 + 1) * PC + sc1 + 1];
+        const R chiL = pk[FXI((s0 * 2) * PC + sc1, n_pk)] * eh + pk[FXI((s0 * 2 + 1) * PC + sc1, n_pk)];
+        const R chiR = pk[FXI((s0 * 2) * PC + sc1 + 1, n_pk)] * eh + pk[FXI((s0 * 2 + 1) * PC + sc1 + 1, n_pk)];
         R vsT = R(0);
         if (xl < nx) {
           if constexpr (D <= 2) vsT = sgf[((k & 1) * TC + ly * TX + TX - 1) * LY::NGF + 1];
@@ -1182,7 +1200,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         }
         rad_face(0, QL, QR, chiL, chiR, tx(T_ELL, bc_pad(xl) + 1), vsT, out);
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rfx[(v * NFX + fT) * GS + h] = out[v];
+        for (int v = 0; v < NRV; ++v) rfx[FXI((v * NFX + fT) * GS + h, n_rfx)] = out[v];
       }
     }
     // 3-d, two groups per lane: the y face TY of each column (between the tile's last row and the
@@ -1197,17 +1215,17 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         R QL[NRV], QR[NRV], out[NRV];
 #pragma unroll
         for (int v = 0; v < NRV; ++v) {
-          QL[v] = rby[(v * NFY + fT) * GS + h];
-          QR[v] = ray[(v * TX + lx) * GS + h];
+          QL[v] = rby[FXI((v * NFY + fT) * GS + h, n_rby)];
+          QR[v] = ray[FXI((v * TX + lx) * GS + h, n_ray)];
         }
         const R eh = R(sgc->efac_of(h, R(0)));
-        const R chiL = pk[(s0 * 2) * PC + sc1] * eh + pk[(s0 * 2 + 1) * PC + sc1];
-        const R chiR = pk[(s0 * 2) * PC + sc1 + PX] * eh + pk[(s0 * 2 + 1) * PC + sc1 + PX];
+        const R chiL = pk[FXI((s0 * 2) * PC + sc1, n_pk)] * eh + pk[FXI((s0 * 2 + 1) * PC + sc1, n_pk)];
+        const R chiR = pk[FXI((s0 * 2) * PC + sc1 + PX, n_pk)] * eh + pk[FXI((s0 * 2 + 1) * PC + sc1 + PX, n_pk)];
         const R vsT = (yl < ny && gx < nx) ? gface(1, NG, ((uint32_t)k * (ny + 1) + (uint32_t)(yl + 1)) * nx + gxc)
                                            : R(0);
         rad_face(1, QL, QR, chiL, chiR, ty(T_ELL, bc_pad(yl) + 1), vsT, out);
 #pragma unroll
-        for (int v = 0; v < NRV; ++v) rfy[(v * NFY + fT) * GS + h] = out[v];
+        for (int v = 0; v < NRV; ++v) rfy[FXI((v * NFY + fT) * GS + h, n_rfy)] = out[v];
       }
     }
     if constexpr (D == 2 && NGL > 1) {
@@ -1293,11 +1311,11 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
           const int c = v <= 2 ? v : 0;
           V Fp[D], Fm[D];
           R Ap[D], Am[D];
-          Fp[0] = ldv(&rfx[(v * NFX + fxa + 1) * GS + g0]); Ap[0] = fx_r[c];
-          Fm[0] = ldv(&rfx[(v * NFX + fxa) * GS + g0]); Am[0] = fx_l[c];
+          Fp[0] = ldv(&rfx[FXI((v * NFX + fxa + 1) * GS + g0, n_rfx)]); Ap[0] = fx_r[c];
+          Fm[0] = ldv(&rfx[FXI((v * NFX + fxa) * GS + g0, n_rfx)]); Am[0] = fx_l[c];
           if (D == 3) {
-            Fp[1] = ldv(&rfy[(v * NFY + fya + TX) * GS + g0]); Ap[1] = fyr;
-            Fm[1] = ldv(&rfy[(v * NFY + fya) * GS + g0]); Am[1] = fyl;
+            Fp[1] = ldv(&rfy[FXI((v * NFY + fya + TX) * GS + g0, n_rfy)]); Ap[1] = fyr;
+            Fm[1] = ldv(&rfy[FXI((v * NFY + fya) * GS + g0, n_rfy)]); Am[1] = fyl;
           }
           if (D >= 2) {
             Fp[D - 1] = SCAR ? ldv(car(k + 1, 1, v)) : rfm_new[v]; Ap[D - 1] = fm_r[c];
@@ -1356,10 +1374,10 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
             for (int j = 0; j < NGL; ++j) {
               if (!hasj[j]) continue;
               const int gg = gj[j];
-              if (xh) o += (double)(rfx[(v * NFX + fxa + 1) * GS + gg] * fx_r[c]);
-              if (xl) o -= (double)(rfx[(v * NFX + fxa) * GS + gg] * fx_l[c]);
-              if (D == 3 && yh) o += (double)(rfy[(v * NFY + fya + TX) * GS + gg] * fyr);
-              if (D == 3 && yl) o -= (double)(rfy[(v * NFY + fya) * GS + gg] * fyl);
+              if (xh) o += (double)(rfx[FXI((v * NFX + fxa + 1) * GS + gg, n_rfx)] * fx_r[c]);
+              if (xl) o -= (double)(rfx[FXI((v * NFX + fxa) * GS + gg, n_rfx)] * fx_l[c]);
+              if (D == 3 && yh) o += (double)(rfy[FXI((v * NFY + fya + TX) * GS + gg, n_rfy)] * fyr);
+              if (D == 3 && yl) o -= (double)(rfy[FXI((v * NFY + fya) * GS + gg, n_rfy)] * fyl);
               if (D >= 2 && mh) o += (double)((SCAR ? car(k + 1, 1, v)[j] : vget(rfm_new[v], j)) * fm_r[c]);
               if (D >= 2 && ml) o -= (double)((SCAR ? car(k, 1, v)[j] : vget(rfm_old[v], j)) * fm_l[c]);
             }
@@ -1376,12 +1394,12 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
       }
       // recording for the adjoint: the pre-interaction state
       if (A.pre_out != nullptr && cell_in) {
-        if (lane < NG) A.pre_out[lane * ncell + cidx] = ug;
+        if (lane < NG) A.pre_out[FXI(lane * ncell + cidx, A.n_state)] = ug;
 #pragma unroll
         for (int j = 0; j < NGL; ++j) {
           if (hasj[j]) {
 #pragma unroll
-            for (int v = 0; v < NRV; ++v) A.pre_out[NG * ncell + (v * ncell + cidx) * G + gj[j]] = vget(U[v], j);
+            for (int v = 0; v < NRV; ++v) A.pre_out[FXI(NG * ncell + (v * ncell + cidx) * G + gj[j], A.n_state)] = vget(U[v], j);
           }
         }
       }
@@ -1390,12 +1408,12 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
         const uint32_t row = D == 1 ? 0u : D == 2 ? (uint32_t)k : (uint32_t)k * ny + gy;
 #pragma unroll
         for (int j = 0; j < NGL; ++j)
-          if (hasj[j]) A.phi_out[row * G + gj[j]] = rfx[(0 * NFX + fxa + 1) * GS + gj[j]] * A.phi_area;
+          if (hasj[j]) A.phi_out[FXI(row * G + gj[j], (uint32_t)(D >= 2 ? ny : 1) * (D >= 3 ? nz : 1) * G)] = rfx[FXI((0 * NFX + fxa + 1) * GS + gj[j], n_rfx)] * A.phi_area;
       }
       if (cell_in) {
         R chk = R(0);  // a NaN or inf anywhere in the cell's outputs makes this sum non-finite
         if (lane < NG) {
-          A.out[lane * ncell + cidx] = ug;
+          A.out[FXI(lane * ncell + cidx, A.n_state)] = ug;
           chk += ug;
         }
 #pragma unroll
@@ -1404,7 +1422,7 @@ stage_kernel(const __grid_constant__ StageArgs<R> A) {
 #pragma unroll
             for (int v = 0; v < NRV; ++v) {
               const R val = vget(U[v], j);
-              A.out[NG * ncell + (v * ncell + cidx) * G + gj[j]] = val;
+              A.out[FXI(NG * ncell + (v * ncell + cidx) * G + gj[j], A.n_state)] = val;
               chk += val * R(0);
             }
           }

@@ -21,6 +21,7 @@ enum : unsigned {
   ST_NEWTON = 1u,     // Newton and bisection did not converge in some cell
   ST_FLOOR = 2u,      // a floor was applied
   ST_NONFINITE = 4u,  // a non-finite value was produced
+  ST_BOUNDS = 8u,     // an index fell outside its buffer (index checks of the debug build)
 };
 
 // Kernel-side description of the grid (passed by value to every launch).

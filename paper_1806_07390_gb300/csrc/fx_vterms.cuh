@@ -155,11 +155,13 @@ __device__ __forceinline__ void vt_gradient(const StageArgs<R>& A, int ix, int i
     const uint32_t lf = ((uint32_t)iz * ey + (uint32_t)iy) * ex + (uint32_t)ix;
     const uint32_t uf = lf + (j == 0 ? 1u : (j == 1 ? ex : ex * ey));
     const R* fr = A.faces + (uint32_t)A.face_off[j];
+    const uint32_t nfr = (uint32_t)(NG + D) * nf;  // this direction's block (fluxes, v*, D-1 velocities)
+    (void)nfr;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       const uint32_t row = (uint32_t)(NG + (i - j + D) % D) * nf;
-      vl[j][i] = __ldg(fr + row + lf);
-      vu[j][i] = __ldg(fr + row + uf);
+      vl[j][i] = __ldg(FXP(fr, row + lf, nfr));
+      vu[j][i] = __ldg(FXP(fr, row + uf, nfr));
     }
   }
 #pragma unroll
@@ -245,12 +247,12 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
   for (int q = 0; q < D; ++q) oF[q] = R(0);
   if (act) {
     // the stage output this lane updates, read here so that its latency overlaps the work
-    oE = A.out[rad + gid];
+    oE = A.out[FXI(rad + gid, A.n_state)];
 #pragma unroll
-    for (int q = 0; q < D; ++q) oF[q] = A.out[rad + (uint32_t)(1 + q) * vstr + gid];
-    E = A.in[rad + gid];
+    for (int q = 0; q < D; ++q) oF[q] = A.out[FXI(rad + (uint32_t)(1 + q) * vstr + gid, A.n_state)];
+    E = A.in[FXI(rad + gid, A.n_state)];
 #pragma unroll
-    for (int q = 0; q < D; ++q) F[q] = A.in[rad + (uint32_t)(1 + q) * vstr + gid];
+    for (int q = 0; q < D; ++q) F[q] = A.in[FXI(rad + (uint32_t)(1 + q) * vstr + gid, A.n_state)];
     if constexpr (SPH) {
 #pragma unroll
       for (int q = 0; q < D; ++q) F[q] = F[q] / h[q];
@@ -334,14 +336,14 @@ __global__ void __launch_bounds__(VT_THREADS) vterm_kernel(const __grid_constant
   if (act) {
     const R e = oE + wdt * dE;
     bad |= !isfinite(e);
-    A.out[rad + gid] = e;
+    A.out[FXI(rad + gid, A.n_state)] = e;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       R dF = uF[j] - fF[j] - wF[j];
       if constexpr (SPH) dF *= h[j];  // covariant component
       const R f = oF[j] + wdt * dF;
       bad |= !isfinite(f);
-      A.out[rad + (uint32_t)(1 + j) * vstr + gid] = f;
+      A.out[FXI(rad + (uint32_t)(1 + j) * vstr + gid, A.n_state)] = f;
     }
   }
   if (bad) atomicOr(A.status, ST_NONFINITE);
@@ -442,19 +444,19 @@ __global__ void __launch_bounds__(VT_THREADS, 4) vterm_kernel2(const __grid_cons
 #pragma unroll
   for (int t = 0; t < 2; ++t)
     if (t ? actb : acta) {
-      oE[t] = A.out[rad + gia + t];
+      oE[t] = A.out[FXI(rad + gia + t, A.n_state)];
 #pragma unroll
-      for (int q = 0; q < D; ++q) oF[t][q] = A.out[rad + (uint32_t)(1 + q) * vstr + gia + t];
+      for (int q = 0; q < D; ++q) oF[t][q] = A.out[FXI(rad + (uint32_t)(1 + q) * vstr + gia + t, A.n_state)];
     }
   if (acta) {
-    Ea = A.in[rad + gia];
+    Ea = A.in[FXI(rad + gia, A.n_state)];
 #pragma unroll
-    for (int q = 0; q < D; ++q) Fa[q] = A.in[rad + (uint32_t)(1 + q) * vstr + gia];
+    for (int q = 0; q < D; ++q) Fa[q] = A.in[FXI(rad + (uint32_t)(1 + q) * vstr + gia, A.n_state)];
   }
   if (actb) {
-    Eb = A.in[rad + gia + 1];
+    Eb = A.in[FXI(rad + gia + 1, A.n_state)];
 #pragma unroll
-    for (int q = 0; q < D; ++q) Fb[q] = A.in[rad + (uint32_t)(1 + q) * vstr + gia + 1];
+    for (int q = 0; q < D; ++q) Fb[q] = A.in[FXI(rad + (uint32_t)(1 + q) * vstr + gia + 1, A.n_state)];
   }
   if constexpr (SPH) {
 #pragma unroll
@@ -554,12 +556,12 @@ __global__ void __launch_bounds__(VT_THREADS, 4) vterm_kernel2(const __grid_cons
     if (t ? actb : acta) {
       const R e = fmaf(wdt, vget(dE, t), oE[t]);
       bad |= !isfinite(e);
-      A.out[rad + gia + t] = e;
+      A.out[FXI(rad + gia + t, A.n_state)] = e;
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         const R f = fmaf(wdt, vget(dF[j], t), oF[t][j]);
         bad |= !isfinite(f);
-        A.out[rad + (uint32_t)(1 + j) * vstr + gia + t] = f;
+        A.out[FXI(rad + (uint32_t)(1 + j) * vstr + gia + t, A.n_state)] = f;
       }
     }
   if (bad) atomicOr(A.status, ST_NONFINITE);

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) comp_kernel(const __grid_constant__ Stage
     bool f = false;
     x3[d] = min(max(bc_map(x3[d] + k, g.n[d], g.bc_lo[d], g.bc_hi[d], f), 0), g.n[d] - 1);
     const uint32_t ci = ((uint32_t)x3[2] * n1 + x3[1]) * n0 + x3[0];
-    return A.in[XO + ci] / A.in[ci];
+    return A.in[FXI(XO + ci, A.n_state)] / A.in[FXI(ci, A.n_state)];
   };
   R net = R(0);
 #pragma unroll
@@ -65,8 +65,10 @@ __global__ void __launch_bounds__(256) comp_kernel(const __grid_constant__ Stage
     const uint32_t lf = ((uint32_t)iz * ey + (uint32_t)iy) * ex + (uint32_t)ix;
     const uint32_t uf = lf + (d == 0 ? 1u : (d == 1 ? ex : ex * ey));
     const R* fr = A.faces + (uint32_t)A.face_off[d];
-    const R mlo = fr[lf], mhi = fr[uf];
-    const R vlo = fr[(uint32_t)NG * nf + lf], vhi = fr[(uint32_t)NG * nf + uf];
+    const uint32_t nfr = (uint32_t)(NG + 1 + (g.vterms ? D - 1 : 0)) * nf;  // this direction's block
+    (void)nfr;
+    const R mlo = fr[FXI(lf, nfr)], mhi = fr[FXI(uf, nfr)];
+    const R vlo = fr[FXI((uint32_t)NG * nf + lf, nfr)], vhi = fr[FXI((uint32_t)NG * nf + uf, nfr)];
     const R flo = mlo * (vlo >= R(0) ? bm : a0), fhi = mhi * (vhi >= R(0) ? b0 : ap);
     // area/volume factors of the two faces (Eq. 8 with a separable volume element): this
     // direction's own, times the cross factors of the other directions (1 on Cartesian grids)
@@ -80,11 +82,11 @@ __global__ void __launch_bounds__(256) comp_kernel(const __grid_constant__ Stage
     net += (fhi * tt(T_FR, bc_pad(i)) - flo * tt(T_FL, bc_pad(i))) * cross;
   }
   const auto& K = A.k(R(0));  // the step and RK weights in R (no per-thread conversions)
-  const R u = A.in[XO + c] - K.dt * net;
+  const R u = A.in[FXI(XO + c, A.n_state)] - K.dt * net;
   const bool stage2 = A.base != nullptr;
-  const R r = stage2 ? K.alpha * A.base[XO + c] + K.beta * u : u;
+  const R r = stage2 ? K.alpha * A.base[FXI(XO + c, A.n_state)] + K.beta * u : u;
   if (!isfinite(r)) atomicOr(A.status, ST_NONFINITE);
-  A.out[XO + c] = r;
+  A.out[FXI(XO + c, A.n_state)] = r;
 }
 
 // ---- two-equation interaction ---------------------------------------------------------------
@@ -111,15 +113,15 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   const GroupConst& gc = *A.gc;
   // 1 / eps_g of each group (centre sqrt(eps_{g-1/2} eps_{g+1/2})), once per block
   __shared__ double s_icen[MAXG];
-  for (int j = threadIdx.x; j < Gs; j += CPLYE_THREADS) s_icen[j] = 1.0 / sqrt(gc.edge[j] * gc.edge[j + 1]);
+  for (int j = threadIdx.x; j < Gs; j += CPLYE_THREADS) s_icen[FXI(j, MAXG)] = 1.0 / sqrt(gc.edge[j] * gc.edge[j + 1]);
   __syncthreads();
   if (c >= ncell) return;
   const double cl = g.c, dt = A.dts, cv = 1.0 / (g.gamma - 1.0), xi0 = g.xi0;
   R* U = A.out;
   const uint32_t rad = (uint32_t)NG * ncell, XO = (uint32_t)(NG + NRV * G) * ncell;
   unsigned st = 0;
-  double rho = U[c];
-  if (rho < g.rho_floor) { rho = g.rho_floor; U[c] = (R)rho; st |= ST_FLOOR; }
+  double rho = U[FXI(c, A.n_state)];
+  if (rho < g.rho_floor) { rho = g.rho_floor; U[FXI(c, A.n_state)] = (R)rho; st |= ST_FLOOR; }
   // scale factors h_0, h_1 of the cell (1 on Cartesian grids): momentum and flux are covariant
   double hq[D];
 #pragma unroll
@@ -135,26 +137,26 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   }
   double ke = 0.0;
 #pragma unroll
-  for (int q = 0; q < D; ++q) { const double vh = U[(1 + q) * ncell + c] / (rho * hq[q]); ke += 0.5 * rho * vh * vh; }
-  double u_m = U[(NG - 1) * ncell + c] - ke;
+  for (int q = 0; q < D; ++q) { const double vh = U[FXI((1 + q) * ncell + c, A.n_state)] / (rho * hq[q]); ke += 0.5 * rho * vh * vh; }
+  double u_m = U[FXI((NG - 1) * ncell + c, A.n_state)] - ke;
   const double u_floor = g.p_floor / (g.gamma - 1.0);
-  if (u_m < u_floor) { u_m = u_floor; U[(NG - 1) * ncell + c] = (R)(ke + u_m); st |= ST_FLOOR; }
-  const double X_m = U[XO + c], Y_m = X_m / rho;
+  if (u_m < u_floor) { u_m = u_floor; U[FXI((NG - 1) * ncell + c, A.n_state)] = (R)(ke + u_m); st |= ST_FLOOR; }
+  const double X_m = U[FXI(XO + c, A.n_state)], Y_m = X_m / rho;
   double Esum = 0.0, Lsum = 0.0, fadd = 0.0;
   for (int k = 0; k < G; ++k) {
-    double E = U[rad + c * (uint32_t)G + k];
+    double E = U[FXI(rad + c * (uint32_t)G + k, A.n_state)];
     if (E < g.E_floor) { fadd += g.E_floor - E; E = g.E_floor; }
     Em[k] = (RT)E;
     E = Em[k];  // (the FP32 forms: the floor as the FP32 state stores it)
     Esum += E;
     const int s = k / Gs;
-    if (s < 2) Lsum += fabs(xi0 * s_icen[k % Gs]) * E;
+    if (s < 2) Lsum += fabs(xi0 * s_icen[FXI(k % Gs, MAXG)]) * E;
   }
   const double norm = g.a_rad * 0.15398973382026502;  // a_R 15/pi^4
   const double kpre = g.kappa0 * hpow(rho, g.kap_rho_h);
   auto xi_of = [&](int k) -> double {
     const int s = k / Gs;
-    const double xg = xi0 * s_icen[k % Gs];
+    const double xg = xi0 * s_icen[FXI(k % Gs, MAXG)];
     return s == 0 ? -xg : (s == 1 ? xg : 0.0);
   };
   // residuals and Jacobian at (T, Y); with keep, the channel energies into En.  A band edge is
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
         float Bf, dBf;
         planck_group(A.ptab, pa, gg, gc.edge32, Bf, dBf);
         const float tf = cdtf * (kTf * gc.efac32[gg]), dtf = tf * hTf, invf = frcp(1.0f + tf);
-        const float xf = xi0f * (float)s_icen[gg];
+        const float xf = xi0f * (float)s_icen[FXI(gg, MAXG)];
         float sE = 0.0f, sX = 0.0f, sT = 0.0f, sY = 0.0f, qT = 0.0f, qY = 0.0f;
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
         lo = hi;
         const double kap = kT * gc.efac[gg];
         const double tau = cl * dt * kap, dtau = tau * (0.5 * g.kap_T_h * invT);
-        const double xg = xi0 * s_icen[gg];
+        const double xg = xi0 * s_icen[FXI(gg, MAXG)];
         const double inv = 1.0 / (1.0 + tau);
         for (int s = 0; s < 3; ++s) {
           const int k = s * Gs + gg;
@@ -308,22 +310,22 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
     const double dk = (double)En[k] - (double)Em[k];  // exact for the FP32 rows
     dEsum += dk;
     dXsum += xi_of(k) * dk;
-    U[rad + c * (uint32_t)G + k] = (R)En[k];
+    U[FXI(rad + c * (uint32_t)G + k, A.n_state)] = (R)En[k];
   }
   // (kept in FP64 until the momentum feedback below, then stored once)
   double ue = ke + (u_m - dEsum);
-  U[XO + c] = (R)(X_m + dXsum);
+  U[FXI(XO + c, A.n_state)] = (R)(X_m + dXsum);
   // flux absorption (Eq. 28) with its momentum and energy feedback (Eqs. 31-32)
   double vcon[D], dm[D], dwork = 0.0;
 #pragma unroll
-  for (int q = 0; q < D; ++q) { vcon[q] = U[(1 + q) * ncell + c] / (rho * hq[q] * hq[q]); dm[q] = 0.0; }
+  for (int q = 0; q < D; ++q) { vcon[q] = U[FXI((1 + q) * ncell + c, A.n_state)] / (rho * hq[q] * hq[q]); dm[q] = 0.0; }
   const double sig = g.sigma0 * rho;
   const double kT = kpre * hpow(T, g.kap_T_h);
   for (int k = 0; k < G; ++k) {
     const double fac = 1.0 / (1.0 + cl * dt * (kT * gc.efac[k % Gs] + sig));
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-      R* Fp = U + rad + (uint32_t)(1 + q) * ncell * (uint32_t)G + c * (uint32_t)G + k;
+      R* Fp = FXP(U, rad + (uint32_t)(1 + q) * ncell * (uint32_t)G + c * (uint32_t)G + k, A.n_state);
       const double F = *Fp, Fn = F * fac, dF = Fn - F;
       dm[q] += dF;
       dwork += vcon[q] * dF;
@@ -332,10 +334,10 @@ __global__ void __launch_bounds__(CPLYE_THREADS) couple_ye_kernel(const __grid_c
   }
   const double ic2 = 1.0 / (cl * cl);
 #pragma unroll
-  for (int q = 0; q < D; ++q) U[(1 + q) * ncell + c] = (R)((double)U[(1 + q) * ncell + c] - dm[q] * ic2);
+  for (int q = 0; q < D; ++q) U[FXI((1 + q) * ncell + c, A.n_state)] = (R)((double)U[FXI((1 + q) * ncell + c, A.n_state)] - dm[q] * ic2);
   ue -= dwork * ic2;
-  U[(NG - 1) * ncell + c] = (R)ue;
-  bool bad = !isfinite(ue) || !isfinite((double)U[XO + c]);
+  U[FXI((NG - 1) * ncell + c, A.n_state)] = (R)ue;
+  bool bad = !isfinite(ue) || !isfinite((double)U[FXI(XO + c, A.n_state)]);
   if (bad) st |= ST_NONFINITE;
   if (st) atomicOr(A.status, st);
   if (A.budget != nullptr) {

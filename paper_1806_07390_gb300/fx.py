@@ -15,12 +15,13 @@ import numpy as np
 from .workloads import BC_CODES, GEOM_CODES, MAP_CODES, RIEMANN_CODES, Problem
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfx.so")
+# FX_LIBRARY selects another build of the library (the debug build with index checks, libfx_bc.so)
+LIB_PATH = os.environ.get("FX_LIBRARY") or os.path.join(_HERE, "libfx.so")
 
 FX_OK = 0
 STATUS_NAMES = {0: "FX_OK", -1: "FX_ERR_ARG", -2: "FX_ERR_CUDA", -3: "FX_ERR_WORKSPACE",
                 -4: "FX_ERR_NEWTON", -5: "FX_ERR_FLOOR", -6: "FX_ERR_NONFINITE",
-                -7: "FX_ERR_UNSUPPORTED"}
+                -7: "FX_ERR_UNSUPPORTED", -8: "FX_ERR_BOUNDS"}
 FX_FP64, FX_FP32, FX_FP32_F64NEWTON = 0, 1, 2
 NTOTALS = 6
 NBUDGET = 9
