@@ -10,10 +10,12 @@ layers with graph replay, per-kernel timing, the objective, and the adjoint's fo
 backward passes.
 
 Run as a script (python tests/bounds_cases.py OUT.npz) it saves every case's outputs, and status
-under the key "<case>/status".
+under the key "<case>/status"; with --full it runs FULL_CASES instead: one step of the full-size
+kh2d and lognormal3d workloads, whose states it keeps as SHA-256 digests.
 """
 from __future__ import annotations
 
+import hashlib
 import os
 import sys
 
@@ -162,16 +164,34 @@ def _dmr(precision):
     return _forward(pb, prim, nsteps=3, layers=layers)
 
 
-def main(path):
+def _full(pb, prim):
+    # one step at full size in the benchmark's launch configuration: the state's SHA-256 (the
+    # arrays are gigabytes) and the totals
+    st, out = _forward(pb, prim, nsteps=1)
+    if st == 0:
+        out["sha256"] = np.frombuffer(hashlib.sha256(out.pop("state").tobytes()).digest(), dtype=np.uint8)
+    return st, out
+
+
+FULL_CASES = {
+    "kh2d_1024x1024x16_fp32n64": lambda: _full(*W.kh_2d(nx=1024, ny=1024, ngroups=16, nsteps=1,
+                                                       precision="fp32n64")),
+    "lognormal3d_256x256x256x12_fp32n64": lambda: _full(*W.lognormal_3d(n=256, ngroups=12, nsteps=1,
+                                                                        precision="fp32n64")),
+}
+
+
+def main(path, full=False):
+    cases = FULL_CASES if full else CASES
     out = {}
-    for name in case_names():
-        st, arrs = run_case(name)
+    for name in cases:
+        st, arrs = cases[name]()
         out[f"{name}/status"] = np.array([st])
         for k, v in arrs.items():
             out[f"{name}/{k}"] = v
     np.savez(path, **out)
-    print(f"ran {len(case_names())} cases with {fx.LIB_PATH}")
+    print(f"ran {len(cases)} cases with {fx.LIB_PATH}")
 
 
 if __name__ == "__main__":
-    main(sys.argv[1])
+    main(sys.argv[1], full="--full" in sys.argv[2:])

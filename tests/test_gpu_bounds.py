@@ -8,11 +8,11 @@ of accessing it.  Here:
   - every kernel path of the stage update (tests/bounds_cases.py) runs through the debug build
     with no index outside its buffer, and gives the normal build's results: the states bit for
     bit, the sums that use floating-point atomics (budgets, the objective, the adjoint) to their
-    rounding.
+    rounding;
+  - so do one step of the full-size kh2d and lognormal3d workloads (states compared by digest).
 """
 import ctypes
 import os
-import re
 import subprocess
 import sys
 
@@ -69,7 +69,7 @@ def test_probe_reports_the_first_index_outside_the_stated_extent(torch_cuda, tmp
 
 
 def _compare(name, key, a, b):
-    if key == "state":
+    if key in ("state", "sha256"):
         assert a.dtype == b.dtype and np.array_equal(a, b), f"{name}: states differ"
         return
     # sums over blocks with floating-point atomics: equal to their rounding
@@ -78,22 +78,32 @@ def _compare(name, key, a, b):
     assert np.max(np.abs(a - b)) <= tol * scale, f"{name}/{key}: {np.max(np.abs(a - b)) / scale:.2e}"
 
 
-def test_every_kernel_path_stays_inside_its_buffers(torch_cuda, tmp_path):
+def _check_debug_build(tmp_path, cases, full):
     from paper_1806_07390_gb300 import build as B
     lib_bc = B.build(bounds_check=True)
     out = str(tmp_path / "bc.npz")
     env = dict(os.environ, FX_LIBRARY=lib_bc)
-    r = subprocess.run([sys.executable, os.path.join(HERE, "bounds_cases.py"), out], env=env,
-                       capture_output=True, text=True, cwd=ROOT, timeout=900)
+    r = subprocess.run([sys.executable, os.path.join(HERE, "bounds_cases.py"), out] + (["--full"] if full else []),
+                       env=env, capture_output=True, text=True, cwd=ROOT, timeout=900)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
     assert "libfx_bc.so" in r.stdout
     bc = np.load(out)
-    for name in bounds_cases.case_names():
+    for name in cases:
         st = int(bc[f"{name}/status"][0])
         assert st == 0, f"{name}: debug build status {st}"
-        st_n, ref = bounds_cases.run_case(name)
+        st_n, ref = cases[name]()
         assert st_n == 0, f"{name}: normal build status {st_n}"
         keys = sorted(k.split("/", 1)[1] for k in bc.files if k.startswith(name + "/") and not k.endswith("/status"))
         assert keys == sorted(ref), (name, keys, sorted(ref))
         for k in keys:
             _compare(name, k, bc[f"{name}/{k}"], np.asarray(ref[k]))
+
+
+def test_every_kernel_path_stays_inside_its_buffers(torch_cuda, tmp_path):
+    _check_debug_build(tmp_path, bounds_cases.CASES, full=False)
+
+
+def test_full_size_workloads_stay_inside_their_buffers(torch_cuda, tmp_path):
+    # one step of kh2d 1024^2 x 16 and lognormal3d 256^3 x 12 (FP32 + FP64 Newton) in the
+    # benchmark's launch configuration: the largest state offsets and the most blocks
+    _check_debug_build(tmp_path, bounds_cases.FULL_CASES, full=True)
