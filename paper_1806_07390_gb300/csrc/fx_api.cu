@@ -1397,6 +1397,10 @@ fx_status fx_boundary_layers(fx_grid* h, const fx_layer* layers, int n, double t
     }
   }
   S.t = t0;
+#ifdef FX_BOUNDS_CHECK
+  S.status = reinterpret_cast<unsigned*>(h->ws + h->off_status);
+  S.n_state = h->ncell * h->NV;
+#endif
   h->layers = S;
   h->time = t0;
   if (h->step_exec) {  // a captured step holds the previous layer launches
@@ -1630,6 +1634,16 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "group constants upload");
+  if (h->layers.n > 0) {  // the layers' device copy lives in the workspace: set it in the new one
+    LayerSet S = h->layers;
+    S.t = h->time;
+#ifdef FX_BOUNDS_CHECK
+    S.status = reinterpret_cast<unsigned*>(h->ws + h->off_status);
+#endif
+    e = cudaMemcpyAsync(h->ws + h->off_layers, &S, sizeof(LayerSet), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "boundary layer upload");
+  }
   return FX_OK;
 }
 

@@ -5,6 +5,7 @@
 // normal momentum and flux negated).  The boxes do not overlap and no mirror reads a box, so the
 // layers of one launch are independent.
 #pragma once
+#include "fx_check.cuh"
 #include "fx_types.h"
 
 namespace fx {
@@ -24,6 +25,10 @@ struct LayerSet {
   double x_lo[3], dx[3];
   LayerDev L[MAX_LAYERS];
   double t;  // time at the start of the current step (device copy: advanced by layer_advance)
+#ifdef FX_BOUNDS_CHECK
+  unsigned* status;  // status word and state elements for the index checks of the debug build
+  int64_t n_state;
+#endif
 };
 
 // Grid row y = layer; the cells of its box strided over the row's blocks.  The layers are set at
@@ -47,13 +52,13 @@ __global__ void __launch_bounds__(LAYER_THREADS) layer_kernel(const LayerSet* S,
       s3[L.d] = 2 * L.m - 1 - c3[L.d];
       const int64_t cs = ((int64_t)s3[2] * g.n[1] + s3[1]) * g.n[0] + s3[0];
       for (int v = 0; v < NG; ++v) {
-        const R x = U[v * ncell + cs];
-        U[v * ncell + c] = v == 1 + L.d ? -x : x;
+        const R x = U[FXI_AT(S->status, v * ncell + cs, S->n_state)];
+        U[FXI_AT(S->status, v * ncell + c, S->n_state)] = v == 1 + L.d ? -x : x;
       }
       for (int v = 0; v <= D; ++v)
         for (int k = 0; k < G; ++k) {
-          const R x = U[NG * ncell + (v * ncell + cs) * G + k];
-          U[NG * ncell + (v * ncell + c) * G + k] = v == 1 + L.d ? -x : x;
+          const R x = U[FXI_AT(S->status, NG * ncell + (v * ncell + cs) * G + k, S->n_state)];
+          U[FXI_AT(S->status, NG * ncell + (v * ncell + c) * G + k, S->n_state)] = v == 1 + L.d ? -x : x;
         }
       continue;
     }
@@ -63,10 +68,10 @@ __global__ void __launch_bounds__(LAYER_THREADS) layer_kernel(const LayerSet* S,
     const double yc = D > 1 ? __dadd_rn(__dadd_rn(S->x_lo[1], __dmul_rn((double)c3[1], S->dx[1])), __dmul_rn(0.5, S->dx[1])) : 0.0;
     const double f = __dsub_rn(__dsub_rn(__dsub_rn(xc, L.x0), __dmul_rn(__dsub_rn(yc, L.y0), L.cot)), __dmul_rn(L.speed, t));
     const double* W = f <= 0.0 ? L.UA : L.UB;
-    for (int v = 0; v < NG; ++v) U[v * ncell + c] = (R)W[v];
+    for (int v = 0; v < NG; ++v) U[FXI_AT(S->status, v * ncell + c, S->n_state)] = (R)W[v];
     for (int k = 0; k < G; ++k) {
-      U[NG * ncell + c * G + k] = (R)W[NG + k];
-      for (int v = 1; v <= D; ++v) U[NG * ncell + (v * ncell + c) * G + k] = R(0);
+      U[FXI_AT(S->status, NG * ncell + c * G + k, S->n_state)] = (R)W[NG + k];
+      for (int v = 1; v <= D; ++v) U[FXI_AT(S->status, NG * ncell + (v * ncell + c) * G + k, S->n_state)] = R(0);
     }
   }
 }

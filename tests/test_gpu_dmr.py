@@ -116,3 +116,39 @@ def test_layer_validation_and_adjoint(fxmod):
         g.adjoint_forward(ws, pb.dt, 2, 1)
     assert ei.value.status == -7
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32n64"])
+def test_layers_follow_the_handle_to_a_new_workspace(fxmod, precision):
+    # a handle bound again, to zeroed memory, sets its boundary layers there at the handle's
+    # time: two steps, the new workspace with the state uploaded again, two more steps equal four
+    # steps in one workspace bit for bit (zeroed memory without the layers would hold n = 0
+    # layers and leave the boundary cells alone)
+    import ctypes
+    import torch
+    pb, prim, layers = W.double_mach(nx=130, ny=40, t_end=0.05, precision=precision)
+    g = fxmod.Grid(pb)
+    g.init_equilibrium(prim)
+    g.boundary_layers(layers)
+    g.step(pb.dt, 4)
+    assert g.status() == 0
+    ref = g.download()
+    g.close()
+    g = fxmod.Grid(pb)
+    g.init_equilibrium(prim)
+    g.boundary_layers(layers)
+    g.step(pb.dt, 2)
+    mid = g.download()
+    old = g.workspace
+    ws2 = torch.zeros(g.ws_bytes, dtype=torch.uint8, device=old.device)
+    g._check(g.L.fx_bind_workspace(g.h, ctypes.c_void_p(ws2.data_ptr()), g.ws_bytes,
+                                   ctypes.c_void_p(g.stream.cuda_stream)))
+    g.workspace = ws2
+    g.upload(mid)
+    g.step(pb.dt, 2)
+    st = g.status()
+    got = g.download()
+    g.close()
+    del old
+    assert st == 0
+    assert np.array_equal(got, ref)
