@@ -163,8 +163,8 @@ fx_status fx_grid_create(const fx_params* params, fx_grid** out, size_t* workspa
  * 256-byte aligned, and the CUDA stream (cudaStream_t, may be NULL for the default stream) on
  * which all later work of this handle is enqueued.  The caller keeps ownership and must keep
  * the memory alive until fx_grid_destroy.  A handle may be bound again to other memory: the
- * tables and the boundary layers (at the handle's current time) are set in it, the status and
- * budgets start from zero, and the state must be uploaded again. */
+ * tables and the boundary layers (at the handle's current time) are set in it, the status, the
+ * budgets and the objective J start from zero, and the state must be uploaded again. */
 fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_stream);
 
 /* Number of elements of the state in the layout above. */

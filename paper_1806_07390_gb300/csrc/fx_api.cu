@@ -1585,6 +1585,7 @@ fx_status fx_bind_workspace(fx_grid* h, void* dev_ptr, size_t bytes, void* cuda_
   e = cudaMemsetAsync(h->ws + h->off_status, 0, 64, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
   e = cudaMemsetAsync(h->ws + h->off_bud, 0, (size_t)BUDGET_SLOTS * NBUDGET * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->off_obj, 0, 8 * sizeof(double), h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "budget reset");
   {
     const fx_status cs = choose_chunk(h);
