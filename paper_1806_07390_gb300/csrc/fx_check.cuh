@@ -1,14 +1,14 @@
 // Index checks of the debug build.  Compiled with -DFX_BOUNDS_CHECK, FXI(i, n) checks an index i
-// into a buffer of n elements: an index outside [0, n) sets ST_BOUNDS in the launch's status word
-// (A.status: every kernel that uses FXI names its launch arguments A), the first such index of the
-// run records its site (a 16-bit tag of the source file's name, then the line) and the index and n
-// in the words that follow the status bits, and the access goes to element 0 of the buffer
-// instead, which keeps it inside the buffer.  Nothing traps or waits.  FXI_AT(st, i, n) does the
-// same with the status word st, for code outside a kernel's body.  FXP(p, off, n) is the address p
-// + off with off checked as FXI checks an index (FXP_AT with the status word st), and
-// FXPR(p, off, len, n) the start of the range
-// [off, off + len) that a helper walks (len <= n; a range that does not fit starts at p).  In the
-// normal build each is its plain index or address and costs nothing.
+// into a buffer of n elements.  An index outside [0, n) sets ST_BOUNDS in the launch's status word
+// (A.status: every kernel that uses these marks names its launch arguments A); the first such
+// index of the run records its site (a 16-bit tag of the source file's name, then the line), the
+// index and n in the words that follow the status bits; and the access goes to element 0 of the
+// buffer instead, which keeps it inside the buffer.  Nothing traps or waits.
+//   FXI_AT(st, i, n)      as FXI, with the status word st (code outside a kernel's body);
+//   FXP(p, off, n)        the address p + off, off checked as FXI checks an index (FXP_AT: with st);
+//   FXPR(p, off, len, n)  the start of the range [off, off + len) that a helper walks (len <= n; a
+//                         range that does not fit starts at p).
+// In the normal build each is its plain index or address and costs nothing.
 //
 // Layout of the status region (unsigned words, 8-byte aligned): [0] status bits, [1] site of the
 // first out-of-range index, [2..3] that index (int64), [4..5] the buffer's extent (int64).
